@@ -1,0 +1,317 @@
+"""Float64 CPU oracle for the ANI-style energy / force path (FeNNol, arXiv 2405.01491).
+
+TEST INFRASTRUCTURE ONLY.  This package may be imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``; the
+product (``paper_2405_01491_b300``) never imports it, and it imports nothing
+from the product.  The only inputs both sides share are the seeded arrays from
+``paper_2405_01491_b300.synth`` (a module that holds none of the method's
+arithmetic).
+
+Layout:
+  fnn_oracle.c   neighbour graph, AEV, AEV vector-Jacobian and Jacobian-vector
+                 products, in plain C, float64, one loop per definition.
+  this module    ctypes glue, the per-element networks and the energy / force /
+                 virial / loss assembly in numpy float64 (matrix products are
+                 the only library primitive used).
+
+Paper passages followed:
+  * neighbour graph and batching: section II.A (GraphGenerator, GraphFilter,
+    GraphAngularExtension; concatenated batches with a batch index).
+  * switching function (cosine) and radial Gaussian basis: sections II.A, II.B.
+  * ANI AEV + species-dependent networks + per-structure energy sum and forces
+    by differentiation: section II.E (ANI flow diagram) and section II.B
+    (neural networks, ChemicalNet).
+  * angular basis Theta_n = (1/2 + cos(theta - theta_n)/2)^zeta over unordered
+    neighbour pairs {jk}: Appendix A (angular resources).
+  * energy/force MSE loss with per-atom energy normalisation: section IV.
+Readings of unstated details (ANI-2x constants, prefactors, 0.95 damping,
+shift grids, slot order, CELU activation) are listed in the design notes.
+Parity of every function here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(HERE, "fnn_oracle.c")
+
+N_AEV = 1008
+N_RAD = 112
+ELEMENT_OF_Z = {1: 0, 6: 1, 7: 2, 8: 3, 9: 4, 16: 5, 17: 6}
+CELU_ALPHA = 0.1
+
+
+@dataclass(frozen=True)
+class Params:
+    """ANI-2x symmetry-function constants (the model the paper benchmarks, section V.E)."""
+    rc_rad: float = 5.1
+    rc_ang: float = 3.5
+    eta_r: float = 19.7
+    eta_a: float = 12.5
+    zeta: float = 14.1
+    shf_r0: float = 0.8
+    shf_a0: float = 0.8
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta", "shf_r0", "shf_a0")]
+
+
+class _CGraph(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("n_mol", ctypes.c_int32),
+                ("mol_offsets", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("pos", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("pbc", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64), ("ei", ctypes.c_void_p), ("ej", ctypes.c_void_p),
+                ("es", ctypes.c_void_p)]
+
+
+def build(force: bool = False) -> str:
+    """Compile fnn_oracle.c (gcc, -O2, OpenMP, no FP contraction) into oracle/_build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.oracle_neighbors.restype = ctypes.c_int64
+        _lib.oracle_neighbors.argtypes = [ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4 + \
+            [ctypes.c_double, ctypes.c_int64] + [ctypes.c_void_p] * 3
+        for f in ("oracle_aev", "oracle_aev_vjp", "oracle_aev_jvp"):
+            getattr(_lib, f).restype = ctypes.c_int
+        _lib.oracle_aev.argtypes = [ctypes.c_void_p] * 3
+        _lib.oracle_aev_vjp.argtypes = [ctypes.c_void_p] * 5
+        _lib.oracle_aev_jvp.argtypes = [ctypes.c_void_p] * 4
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data
+
+
+def _sys_arrays(s):
+    Z = np.ascontiguousarray(s.Z, np.int32)
+    # float32 inputs widen exactly; float64 inputs (finite-difference pins) pass through
+    pos = np.ascontiguousarray(s.pos, np.float64).reshape(-1, 3)
+    mo = np.ascontiguousarray(s.mol_offsets, np.int32)
+    cell = np.ascontiguousarray(s.cell, np.float64).reshape(-1, 9)
+    pbc = np.ascontiguousarray(s.pbc, np.uint8)
+    return Z, pos, mo, cell, pbc
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def neighbors(s, R: float):
+    """Directed pairs within R (section II.A): arrays i, j (int32) and shift n (int8 [nnz,3]), sorted by (i, j)."""
+    Z, pos, mo, cell, pbc = _sys_arrays(s)
+    L = lib()
+    n = L.oracle_neighbors(s.n_atoms, s.n_mol, _p(mo), _p(pos), _p(cell), _p(pbc), float(R), 0, None, None, None)
+    if n < 0:
+        raise OracleError(f"oracle_neighbors failed with status {n}")
+    ei = np.empty(n, np.int32)
+    ej = np.empty(n, np.int32)
+    es = np.empty((n, 3), np.int8)
+    n2 = L.oracle_neighbors(s.n_atoms, s.n_mol, _p(mo), _p(pos), _p(cell), _p(pbc), float(R), n,
+                            _p(ei), _p(ej), _p(es))
+    assert n2 == n
+    return ei, ej, es
+
+
+class Graph:
+    """The rc_rad neighbour graph of a structure batch, kept alive for the C calls."""
+
+    def __init__(self, s, params: Params = Params()):
+        self.s = s
+        self.params = params
+        self.arrays = _sys_arrays(s)
+        self.ei, self.ej, self.es = neighbors(s, params.rc_rad)
+        Z, pos, mo, cell, pbc = self.arrays
+        self.c = _CGraph(s.n_atoms, s.n_mol, _p(mo), _p(Z), _p(pos), _p(cell), _p(pbc),
+                         self.ei.shape[0], _p(self.ei), _p(self.ej), _p(self.es))
+        self.cp = _CParams(*(getattr(params, f) for f in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta",
+                                                          "shf_r0", "shf_a0")))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def aev(s, params: Params = Params(), graph: Graph | None = None) -> np.ndarray:
+    """AEV [N, 1008] float64: 112 radial slots (element-major, 16 shifts) + 28 x 32 angular slots."""
+    g = graph or Graph(s, params)
+    out = np.empty((s.n_atoms, N_AEV), np.float64)
+    _check(lib().oracle_aev(ctypes.byref(g.c), ctypes.byref(g.cp), _p(out)), "oracle_aev")
+    return out
+
+
+def aev_vjp(s, G: np.ndarray, params: Params = Params(), graph: Graph | None = None):
+    """dE/dx [N,3] and virial [n_mol,3,3] from G = dE/dAEV [N,1008]."""
+    g = graph or Graph(s, params)
+    G = np.ascontiguousarray(G, np.float64)
+    grad = np.empty((s.n_atoms, 3), np.float64)
+    vir = np.empty((s.n_mol, 3, 3), np.float64)
+    _check(lib().oracle_aev_vjp(ctypes.byref(g.c), ctypes.byref(g.cp), _p(G), _p(grad), _p(vir)), "oracle_aev_vjp")
+    return grad, vir
+
+
+def aev_jvp(s, V: np.ndarray, params: Params = Params(), graph: Graph | None = None) -> np.ndarray:
+    """Directional derivative of the AEV [N,1008] along the displacement field V [N,3]."""
+    g = graph or Graph(s, params)
+    V = np.ascontiguousarray(V, np.float64)
+    out = np.empty((s.n_atoms, N_AEV), np.float64)
+    _check(lib().oracle_aev_jvp(ctypes.byref(g.c), ctypes.byref(g.cp), _p(V), _p(out)), "oracle_aev_jvp")
+    return out
+
+
+# ----------------------------------------------------------------------------- networks (numpy, float64)
+
+def celu(z, a=CELU_ALPHA):
+    """CELU(z) = z for z > 0, a (exp(z/a) - 1) otherwise."""
+    return np.where(z > 0, z, a * np.expm1(np.minimum(z, 0.0) / a))
+
+
+def dcelu(z, a=CELU_ALPHA):
+    return np.where(z > 0, 1.0, np.exp(np.minimum(z, 0.0) / a))
+
+
+def d2celu(z, a=CELU_ALPHA):
+    return np.where(z > 0, 0.0, np.exp(np.minimum(z, 0.0) / a) / a)
+
+
+def elements(Z) -> np.ndarray:
+    try:
+        return np.asarray([ELEMENT_OF_Z[int(z)] for z in Z], np.int64)
+    except KeyError as exc:
+        raise OracleError(f"species outside the element table: {exc}") from None
+
+
+def _layers(w, m, e):
+    f64 = lambda a: np.asarray(a, np.float64)
+    return (f64(w.W1[m, e]), f64(w.b1[m, e]), f64(w.W2[m, e]), f64(w.b2[m, e]),
+            f64(w.W3[m, e]), f64(w.b3[m, e]), f64(w.w4[m, e]), float(w.b4[m, e]))
+
+
+def network_energies(A: np.ndarray, Z, w):
+    """Atomic outputs y [N, M] of the per-element networks 1008-256-192-160-1 (CELU, linear output),
+    and dY/dAEV averaged over members: G [N, 1008] = (1/M) sum_m dy_m/daev."""
+    el = elements(Z)
+    N, M = A.shape[0], w.n_members
+    y = np.zeros((N, M))
+    G = np.zeros((N, N_AEV))
+    for e in range(7):
+        rows = np.nonzero(el == e)[0]
+        if rows.size == 0:
+            continue
+        x = A[rows]
+        for m in range(M):
+            W1, b1, W2, b2, W3, b3, w4, b4 = _layers(w, m, e)
+            z1 = x @ W1.T + b1
+            h1 = celu(z1)
+            z2 = h1 @ W2.T + b2
+            h2 = celu(z2)
+            z3 = h2 @ W3.T + b3
+            h3 = celu(z3)
+            y[rows, m] = h3 @ w4 + b4
+            g3 = w4[None, :] * dcelu(z3)
+            g2 = (g3 @ W3) * dcelu(z2)
+            g1 = (g2 @ W2) * dcelu(z1)
+            G[rows] += (g1 @ W1) / M
+    return y, G
+
+
+@dataclass
+class Result:
+    energy: np.ndarray      # [n_mol] float64
+    forces: np.ndarray      # [N, 3]
+    virial: np.ndarray      # [n_mol, 3, 3]
+    atomic: np.ndarray      # [N] member-averaged atomic energies
+    aev: np.ndarray         # [N, 1008]
+
+
+def energy_forces(s, w, params: Params = Params()) -> Result:
+    """E_mol = (1/M) sum_m sum_{i in mol} y_im; F = -dE/dx; virial = -sum_edges d (x) dE/dd (section II.E, V.A)."""
+    g = Graph(s, params)
+    A = aev(s, params, g)
+    y, G = network_energies(A, s.Z, w)
+    e_atom = y.mean(axis=1)
+    mol = np.repeat(np.arange(s.n_mol), np.diff(s.mol_offsets))
+    E = np.zeros(s.n_mol)
+    np.add.at(E, mol, e_atom)
+    grad, vir = aev_vjp(s, G, params, g)
+    return Result(E, -grad, vir, e_atom, A)
+
+
+# ----------------------------------------------------------------------------- training loss (section IV)
+
+FORCE_WEIGHT = 0.99
+ENERGY_WEIGHT = 0.01
+
+
+def loss_and_weight_grads(s, w, E_ref: np.ndarray, F_ref: np.ndarray, params: Params = Params()):
+    """L = 0.99 mean_{i,c} (F - F*)^2 + 0.01 mean_mol ((E - E*) / n_mol)^2 and dL/dtheta.
+
+    The networks are differentiated with float64 torch autograd on the CPU (a
+    library primitive); the AEV enters through the oracle's own Jacobian-vector
+    product: dL_F/dtheta = d/dtheta <-J_aev v, dE/dAEV(theta)>, v = dL/dF.
+    Returns (L, E, F, grads) with grads a dict of arrays shaped like the weights.
+    """
+    import torch
+
+    g = Graph(s, params)
+    A = aev(s, params, g)
+    el = elements(s.Z)
+    N, M = s.n_atoms, w.n_members
+    names = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
+    th = {k: torch.tensor(np.asarray(getattr(w, k), np.float64), requires_grad=True) for k in names}
+    At = torch.tensor(A, requires_grad=True)
+    y = torch.zeros((N, M), dtype=torch.float64)
+    ys = []
+    for e in range(7):
+        rows = np.nonzero(el == e)[0]
+        if rows.size == 0:
+            continue
+        x = At[rows]
+        for m in range(M):
+            # CELU from elementary ops (torch's fused CELU backward carries alpha in single precision)
+            cel = lambda z: torch.where(z > 0, z, CELU_ALPHA * torch.expm1(torch.clamp(z, max=0.0) / CELU_ALPHA))
+            h = cel(x @ th["W1"][m, e].T + th["b1"][m, e])
+            h = cel(h @ th["W2"][m, e].T + th["b2"][m, e])
+            h = cel(h @ th["W3"][m, e].T + th["b3"][m, e])
+            ys.append((rows, m, h @ th["w4"][m, e] + th["b4"][m, e]))
+    for rows, m, v in ys:
+        y = y.index_put((torch.as_tensor(rows), torch.full((rows.size,), m)), v)
+    e_atom = y.mean(dim=1)
+    mol = torch.as_tensor(np.repeat(np.arange(s.n_mol), np.diff(s.mol_offsets)))
+    E = torch.zeros(s.n_mol, dtype=torch.float64).index_add(0, mol, e_atom)
+    G = torch.autograd.grad(E.sum(), At, create_graph=True)[0]           # dE/dAEV(theta)
+    grad_x, _ = aev_vjp(s, G.detach().numpy(), params, g)
+    F = -grad_x
+    n_mol_atoms = np.diff(s.mol_offsets).astype(np.float64)
+    LF = FORCE_WEIGHT * np.mean((F - F_ref) ** 2)
+    LE_t = ENERGY_WEIGHT * torch.mean(((E - torch.as_tensor(E_ref)) / torch.as_tensor(n_mol_atoms)) ** 2)
+    v = FORCE_WEIGHT * 2.0 * (F - F_ref) / F.size                        # dL/dF
+    t = aev_jvp(s, v, params, g)                                         # J_aev v
+    surrogate = LE_t + torch.sum(torch.as_tensor(-t) * G)                # d/dtheta of this = dL/dtheta
+    gr = torch.autograd.grad(surrogate, [th[k] for k in names])
+    L = float(LE_t.detach()) + LF
+    return L, E.detach().numpy(), F, {k: gk.numpy() for k, gk in zip(names, gr)}

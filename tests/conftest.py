@@ -1,0 +1,45 @@
+import functools
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+
+
+@functools.lru_cache(maxsize=None)
+def weights(n_members: int, seed: int = 0):
+    from paper_2405_01491_b300 import synth
+    return synth.xavier_weights(n_members, seed)
+
+
+@functools.lru_cache(maxsize=None)
+def structure(name: str):
+    from paper_2405_01491_b300 import synth
+    return {
+        "gas24": synth.gas24,
+        "water216": synth.water216,
+        "mix23558": synth.mix23558,
+        "batch64": lambda: synth.ragged_batch(64, seed=40),
+        "batch4096": synth.ragged_batch,
+        "box300": lambda: synth.mix_box(300, (300 / 0.1) ** (1 / 3), seed=31),
+        "box1500": lambda: synth.mix_box(1500, (1500 / 0.1) ** (1 / 3), seed=32,
+                                         fractions=synth.MIX7),
+    }[name]()
+
+
+@pytest.fixture
+def W1():
+    return weights(1)
+
+
+@pytest.fixture
+def W2():
+    return weights(2)

@@ -1,0 +1,138 @@
+"""Pins of the oracle's networks, energies, forces, virials and loss gradients.
+
+Library special cases: the per-element networks against torch.nn.Linear + torch.nn.CELU
+in float64; finite differences for forces and weight gradients; conservation laws
+(sum of forces, torque, virial symmetry); extensivity and batch-composition invariance
+(paper section II.A: structures in a batch never interact)."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_01491_b300 import synth
+from conftest import structure, weights
+
+ELEM = {1: 0, 6: 1, 7: 2, 8: 3, 9: 4, 16: 5, 17: 6}
+
+
+def torch_net(w, m, e):
+    net = torch.nn.Sequential(torch.nn.Linear(1008, 256), torch.nn.CELU(0.1), torch.nn.Linear(256, 192),
+                              torch.nn.CELU(0.1), torch.nn.Linear(192, 160), torch.nn.CELU(0.1),
+                              torch.nn.Linear(160, 1)).double()
+    with torch.no_grad():
+        for li, (W, b) in enumerate([(w.W1, w.b1), (w.W2, w.b2), (w.W3, w.b3)]):
+            net[2 * li].weight.copy_(torch.from_numpy(W[m, e].astype(np.float64)))
+            net[2 * li].bias.copy_(torch.from_numpy(b[m, e].astype(np.float64)))
+        net[6].weight.copy_(torch.from_numpy(w.w4[m, e].astype(np.float64))[None])
+        net[6].bias.fill_(float(w.b4[m, e]))
+    return net
+
+
+def test_networks_match_torch_nn():
+    w = weights(2)
+    rng = np.random.default_rng(0)
+    Z = np.array([1, 6, 7, 8, 9, 16, 17, 1, 6, 8], np.int32)
+    A = rng.uniform(0, 1.5, size=(10, 1008))
+    y, G = oracle.network_energies(A, Z, w)
+    for i, z in enumerate(Z):
+        x = torch.tensor(A[i:i + 1], requires_grad=True)
+        tot = 0
+        for m in range(2):
+            out = torch_net(w, m, ELEM[int(z)])(x)[0, 0]
+            assert float(out.detach()) == pytest.approx(y[i, m], rel=1e-12, abs=1e-14)
+            tot = tot + out / 2
+        gx, = torch.autograd.grad(tot, x)
+        # torch's CELU backward carries alpha in single precision (about 1e-8 relative error)
+        np.testing.assert_allclose(G[i], gx[0].numpy(), rtol=1e-6, atol=1e-7 * np.abs(G[i]).max())
+
+
+def test_isolated_atoms_energy_is_network_at_zero():
+    w = weights(2)
+    # atoms 20 A apart: every AEV entry is zero, so E = mean over members of net(0)
+    Z = np.array([6, 8, 17], np.int32)
+    s = synth.Structures(Z, np.array([[0, 0, 0], [20, 0, 0], [0, 20, 0]], np.float32),
+                         np.array([0, 3], np.int32), np.zeros((1, 9), np.float32), np.zeros(1, np.uint8))
+    r = oracle.energy_forces(s, w)
+    want = sum(float(torch_net(w, m, ELEM[int(z)])(torch.zeros(1, 1008, dtype=torch.float64))) / 2
+               for z in Z for m in range(2))
+    assert r.energy[0] == pytest.approx(want, rel=1e-12)
+    assert np.all(r.forces == 0)
+
+
+def _energy(s, w, x):
+    return oracle.energy_forces(synth.Structures(s.Z, x, s.mol_offsets, s.cell, s.pbc), w).energy
+
+
+@pytest.mark.parametrize("name,M", [("gas24", 2), ("box300", 1)])
+def test_forces_are_minus_energy_gradient(name, M):
+    s = structure(name)
+    w = weights(M)
+    r = oracle.energy_forces(s, w)
+    x = s.pos.astype(np.float64)
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        V = rng.normal(size=x.shape)
+        h = 1e-5
+        fd = (_energy(s, w, x + h * V) - _energy(s, w, x - h * V)).sum() / (2 * h)
+        assert -np.sum(r.forces * V) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    np.testing.assert_allclose(r.forces.sum(0), 0, atol=1e-10)
+    vir = r.virial[0]
+    np.testing.assert_allclose(vir, vir.T, atol=1e-9 * max(1, np.abs(vir).max()))
+    if not s.pbc[0]:
+        torque = np.cross(x, r.forces).sum(0)
+        np.testing.assert_allclose(torque, 0, atol=1e-9)
+
+
+def test_batch_composition_invariance():
+    b = structure("batch64")
+    w = weights(1)
+    rb = oracle.energy_forces(b, w)
+    for m in (0, 17, 63):
+        one = b.molecule(m)
+        r1 = oracle.energy_forces(one, w)
+        a0, a1 = b.mol_offsets[m], b.mol_offsets[m + 1]
+        assert r1.energy[0] == pytest.approx(rb.energy[m], rel=1e-12, abs=1e-12)
+        np.testing.assert_allclose(r1.forces, rb.forces[a0:a1], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(r1.virial[0], rb.virial[m], rtol=1e-10, atol=1e-12)
+
+
+def test_supercell_energy_is_extensive():
+    s = structure("box300")
+    w = weights(1)
+    L = float(s.cell[0, 0])
+    x = s.pos.astype(np.float64)
+    big = synth.Structures(np.tile(s.Z, 8), np.concatenate([x + L * np.array(n) for n in itertools.product(range(2), repeat=3)]),
+                           np.array([0, 8 * s.n_atoms], np.int32), (s.cell * 2).astype(np.float64), s.pbc)
+    r = oracle.energy_forces(s, w)
+    rb = oracle.energy_forces(big, w)
+    assert rb.energy[0] == pytest.approx(8 * r.energy[0], rel=1e-10)
+    np.testing.assert_allclose(rb.forces[:s.n_atoms], r.forces, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(rb.virial[0], 8 * r.virial[0], rtol=1e-9, atol=1e-9)
+
+
+def test_loss_weight_gradients_finite_differences():
+    b = structure("batch64").molecule(3)
+    b2 = synth.concat([b, structure("batch64").molecule(5)])
+    w = weights(2)
+    E_ref, F_ref = synth.batch_targets(b2, seed=9)
+    L, E, F, grads = oracle.loss_and_weight_grads(b2, w, E_ref, F_ref)
+    r = oracle.energy_forces(b2, w)
+    np.testing.assert_allclose(E, r.energy, rtol=1e-12)
+    np.testing.assert_allclose(F, r.forces, rtol=1e-10, atol=1e-12)
+    rng = np.random.default_rng(4)
+    names = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
+    for trial in range(2):
+        D = {k: rng.normal(size=getattr(w, k).shape) for k in names}
+        # CELU'' jumps at 0 (0 vs 1/alpha), so the force loss is only C^1 in the weights and the central
+        # difference error is O(h) wherever a pre-activation crosses zero: use tiny steps in float64.
+        h = 1e-7 if trial == 0 else 2e-7
+
+        def Lat(sgn):
+            wp = synth.Weights(*(getattr(w, k).astype(np.float64) + sgn * h * D[k] for k in names))
+            return oracle.loss_and_weight_grads(b2, wp, E_ref, F_ref)[0]
+
+        fd = (Lat(1) - Lat(-1)) / (2 * h)
+        an = sum(float(np.sum(grads[k] * D[k])) for k in names)
+        assert an == pytest.approx(fd, rel=1e-6)
