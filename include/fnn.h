@@ -1,0 +1,187 @@
+/*
+ * fnn.h -- C ABI of the B300 (sm_103a) ANI-style energy / force library.
+ *
+ * The operation (FeNNol, arXiv 2405.01491, section II.E and Fig. ani_diagram):
+ * species (atomic numbers) and coordinates of a batch of concatenated
+ * structures, with a per-structure atom count and optional periodic cell
+ * (section II.A), go in; per-structure energies, per-atom forces and
+ * per-structure virials come out (the energy_and_forces_and_virial call of
+ * section V.A).  Inside: cell-list neighbour search (the O(N) replacement of
+ * the all-pairs GraphGenerator, section II.A / V.E), ANI radial + angular
+ * AEVs (sections II.B, II.E, Appendix A), per-element networks
+ * 1008-256-192-160-1 with CELU (section II.B, ChemicalNet), the per-structure
+ * energy sum, and the analytic adjoint F = -dE/dx (the paper uses jax.grad).
+ *
+ * Conventions shared by every call:
+ *   - Units: A, kcal/mol, kcal/mol/A.
+ *   - Every array argument is owned by the caller; opaque handles are owned
+ *     by the library and released by their *_destroy call.
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary (pinned or pageable) host memory.
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls that take a stream are asynchronous and
+ *     stream-ordered: argument errors are returned at once, while conditions
+ *     detected by the kernels (bad species, too-small cell, capacity
+ *     overflow, non-finite results) are posted to a sticky per-context status
+ *     that fnn_sync() returns and clears.  Results written by a call whose
+ *     kernels posted an error are unspecified.
+ *   - Batches: atoms of structure m are [mol_offsets[m], mol_offsets[m+1]);
+ *     structures never interact (section II.A batch index).
+ *   - Periodic structures use the minimum image convention, orthorhombic
+ *     cells only, every edge longer than 2 * (rc_rad + skin).
+ *   - Elements: H C N O F S Cl (Z = 1 6 7 8 9 16 17), AEV length 1008
+ *     (112 radial: element-major x 16 shifts; 896 angular: 28 element pairs
+ *     x 8 radial shifts x 4 angle sections).  These sizes are compiled in.
+ *   - Per-atom limits of the AEV kernels: at most 160 neighbours within
+ *     rc_rad and 64 within rc_ang (FNN_E_CAPACITY, info = -(atom + 1)).
+ */
+#ifndef FNN_H
+#define FNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fnn_ctx fnn_ctx;
+typedef struct fnn_nlist fnn_nlist;
+
+typedef enum {
+  FNN_OK = 0,
+  FNN_PENDING = 1,
+  FNN_E_INVALID = -1,   /* bad argument (NULL, negative size, inconsistent offsets) */
+  FNN_E_SPECIES = -2,   /* atomic number outside the element table; info = atom */
+  FNN_E_CELL = -3,      /* periodic cell not orthorhombic or an edge <= 2 (rc_rad + skin); info = structure */
+  FNN_E_CAPACITY = -4,  /* neighbour list larger than its capacity; info = entries needed */
+  FNN_E_OOM = -5,       /* device allocation failed */
+  FNN_E_TIMEOUT = -6,   /* a bounded device wait gave up */
+  FNN_E_NONFINITE = -7, /* non-finite coordinate or energy */
+  FNN_E_CUDA = -8,      /* a CUDA runtime call failed; see fnn_last_error */
+  FNN_E_STATE = -9      /* call out of order (e.g. no weights loaded) */
+} fnn_status;
+
+typedef enum {
+  FNN_FP32 = 0, /* network GEMMs in FP32 (SIMT FFMA), FP32 accumulation */
+  FNN_BF16 = 1, /* network GEMMs in BF16 on tcgen05 tensor cores, FP32 accumulation */
+  FNN_FP8 = 2   /* network GEMMs in FP8 e4m3 with per-layer scales, FP32 accumulation */
+} fnn_precision;
+
+/* Symmetry-function constants and ensemble size.  fnn_config_default() fills
+ * the ANI-2x values of the paper's benchmark model (section V.E). */
+typedef struct {
+  double rc_rad;      /* radial cutoff, A (5.1) */
+  double rc_ang;      /* angular cutoff, A (3.5) */
+  double eta_rad;     /* radial Gaussian width, 1/A^2 (19.7) */
+  double eta_ang;     /* angular radial Gaussian width, 1/A^2 (12.5) */
+  double zeta;        /* angular exponent (14.1) */
+  double shift_rad0;  /* first radial shift, A (0.8); shifts are shift_rad0 + k (rc_rad - shift_rad0) / 16 */
+  double shift_ang0;  /* first angular radial shift, A (0.8); shifts shift_ang0 + m (rc_ang - shift_ang0) / 8 */
+  double skin;        /* neighbour-list skin, A; list radius = rc_rad + skin (0 = exact list) */
+  int32_t n_members;  /* ensemble size M, 1..8; the energy is the member average */
+} fnn_config;
+
+/* Network parameters, float32, host memory, row-major W[out][in]:
+ * W1 [M][7][256][1008], b1 [M][7][256], W2 [M][7][192][256], b2 [M][7][192],
+ * W3 [M][7][160][192], b3 [M][7][160], w4 [M][7][160], b4 [M][7]. */
+typedef struct {
+  int32_t n_members;
+  const float *W1, *b1, *W2, *b2, *W3, *b3, *w4, *b4;
+} fnn_weights;
+
+/* A batch of structures, all device pointers, caller-owned. */
+typedef struct {
+  int32_t n_atoms;            /* N >= 0 */
+  int32_t n_mol;              /* >= 1 */
+  const int32_t *mol_offsets; /* [n_mol + 1], mol_offsets[0] = 0, non-decreasing, last = N */
+  const int32_t *Z;           /* [N] atomic numbers */
+  const float *pos;           /* [N][4] x, y, z, (w ignored), A; 16-byte aligned */
+  const float *cell;          /* [n_mol][9] row vectors, or NULL when no structure is periodic */
+  const uint8_t *pbc;         /* [n_mol] 1 = periodic, or NULL = none periodic */
+} fnn_system;
+
+/* Fill *cfg with the ANI-2x constants, skin 0 and M = 1. */
+void fnn_config_default(fnn_config *cfg);
+
+/* Create a context on the current CUDA device.  Returns FNN_E_INVALID for
+ * out-of-range constants (cutoffs <= 0, rc_ang > rc_rad, M outside 1..8). */
+fnn_status fnn_create(fnn_ctx **ctx, const fnn_config *cfg);
+fnn_status fnn_destroy(fnn_ctx *ctx);
+
+/* Copy network parameters to the device (and derive the transposed, BF16 and
+ * FP8 forms).  Exactly one of path (a file written by the Python binding's
+ * save_weights: magic "FNNW", int32 version 1, int32 M, then the eight float32
+ * arrays in the order above, little-endian) and host is non-NULL.
+ * host->n_members must equal the context's M.  Synchronous. */
+fnn_status fnn_load_weights(fnn_ctx *ctx, const char *path, const fnn_weights *host);
+
+/* Neighbour-list handle.  capacity = number of directed entries it can hold
+ * (0 = size from the first system: 160 entries per atom). */
+fnn_status fnn_nlist_create(fnn_ctx *ctx, fnn_nlist **nl, int64_t capacity);
+fnn_status fnn_nlist_destroy(fnn_nlist *nl);
+/* Grow the entry capacity (and the per-atom arrays) ahead of use; synchronous. */
+fnn_status fnn_nlist_reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t capacity);
+
+/*
+ * Directed neighbour list within R = rc_rad + skin (section II.A): entry (i, j, n)
+ * for every ordered pair of distinct atoms of the same structure with
+ * |x_j - x_i + n L|^2 < R^2, n the minimum-image shift (0 when not periodic).
+ * The membership test is the float64 predicate d = (x_j - x_i) + n L per axis,
+ * d2 = (dx*dx + dy*dy) + dz*dz, d2 < R*R, rounded to nearest without
+ * contraction; the kernels prefilter in float32 and re-test a band around R in
+ * float64, so the set is bit-exact with that predicate.  Cell lists: counting
+ * sort of atoms into cells of edge >= R, then a warp per atom scans the 27
+ * surrounding cells (ballot + popc compaction, prefix-sum row offsets).
+ * Also records the species-sorted atom order used by fnn_energy_forces.
+ * Asynchronous on stream; overflow posts FNN_E_CAPACITY (info = entries needed).
+ */
+fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, void *stream);
+
+/* Number of entries of the last build (synchronises the list's stream). */
+fnn_status fnn_nlist_nnz(fnn_nlist *nl, int64_t *nnz);
+
+/* Copy the last list to HOST buffers in CSR form: row_ptr [N+1] (int32), nbr [nnz]
+ * (int32 neighbour index), shift [nnz][3] (int8).  Synchronous.  Returns
+ * FNN_E_CAPACITY with *nnz set when cap < nnz. */
+fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t *nbr, int8_t *shift, int64_t cap,
+                            int64_t *nnz);
+
+/* AEVs [N][1008] float32 (device, caller-owned) from a list built for sys.
+ * Radial slot e*16+k = sum over neighbours j of element e within rc_rad of
+ * 1/4 exp(-eta_rad (r - R_k)^2) fc(r); angular slot 112 + p*32 + m*4 + s = sum
+ * over unordered neighbour pairs {j,k} within rc_ang with element pair p of
+ * 2 ((1 + cos(theta' - theta_s))/2)^zeta exp(-eta_ang ((r_ij + r_ik)/2 - A_m)^2)
+ * fc(r_ij) fc(r_ik), theta' = acos(0.95 cos theta_ijk); fc(r) = cos(pi r/rc)/2 + 1/2.
+ * Asynchronous. */
+fnn_status fnn_aev(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *aev, void *stream);
+
+/* Energies E [n_mol] (float64, device), forces F [N][3] (float32, device) and,
+ * when virial != NULL, virials [n_mol][9] (float64, device, W = -sum over
+ * directed entries of d (x) dE_i/dd, = sum_i x_i (x) F_i for a gas-phase
+ * structure).  E_m = (1/M) sum_members sum_{i in m} y_i, F = -dE/dx by the
+ * analytic adjoint of the networks and the AEV.  Asynchronous. */
+fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec,
+                             double *E, float *F, double *virial, void *stream);
+
+/* The same computation from HOST arrays: copies the inputs to library-owned
+ * device buffers, rebuilds the neighbour list, evaluates, copies E [n_mol],
+ * F [N][3] and (optional) virial [n_mol][9] back to the host arrays, and
+ * synchronises.  Z [N] int32, pos [N][3] float32, mol_offsets [n_mol+1],
+ * cell [n_mol][9] or NULL, pbc [n_mol] or NULL.  Returns the sticky status. */
+fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t n_atoms, int32_t n_mol, const int32_t *mol_offsets,
+                                  const int32_t *Z, const float *pos, const float *cell, const uint8_t *pbc,
+                                  fnn_precision prec, double *E, float *F, double *virial, void *stream);
+
+/* Synchronise the stream, return and clear the sticky device status; *info
+ * (optional) receives its detail (entries needed for FNN_E_CAPACITY, the
+ * offending atom for FNN_E_SPECIES, ...). */
+fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
+
+/* Text of the last host-side error of this context (never NULL). */
+const char *fnn_last_error(const fnn_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FNN_H */

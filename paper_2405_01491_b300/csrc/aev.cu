@@ -1,0 +1,490 @@
+// ANI atomic environment vectors and their adjoint (sections II.A, II.B, II.E; Appendix A).
+//
+// One warp per centre atom.  The warp stages its neighbour row into shared memory bucketed by
+// element (two ballot passes: count per element, then scatter), keeping the entries within
+// rc_rad (radial list) and the subset within rc_ang (angular list).
+//
+// Forward, radial: for each element segment, lane (h, k) = (lane / 16, lane % 16) sums shift k
+// over every other neighbour; one shuffle joins the halves; 16 lanes write 64 contiguous bytes.
+// Forward, angular: element-pair blocks p = (a <= b) in slot order.  Each lane evaluates one
+// triplet (4 section powers, 8 radial Gaussians times the switch product) into a shared staging
+// row; then lane (m, s) = (lane / 4, lane % 4) accumulates sum_t pow_s(t) * gauss_m(t) in a
+// register and writes its slot: one coalesced 128-byte store per block.
+// Adjoint: same staging; the radial and angular partials are chained to dE/dd per neighbour in
+// shared memory, then scattered to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
+#include "fnn_internal.cuh"
+
+namespace fnn {
+
+static constexpr unsigned FULL = 0xffffffffu;
+constexpr int AEV_WARPS = 4;
+
+struct WarpStage {
+  float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
+  float rfc[RAD_CAP];            // radial switch fc(r; rc_rad)
+  int rj[RAD_CAP];               // neighbour atom
+  unsigned char re[RAD_CAP];     // neighbour element
+  unsigned char aidx[ANG_CAP];   // angular entry -> radial entry
+  float afc[ANG_CAP];            // angular switch fc(r; rc_ang)
+  float adfc[ANG_CAP];           // its derivative (adjoint)
+  float stage[32][13];           // per-triplet factors
+  float gacc[RAD_CAP][3];        // dE/dd per radial entry (adjoint)
+  float grad[NRAD];              // radial part of the incoming dE/dAEV row (adjoint)
+};
+
+struct StageArgs {
+  int64_t cap;            // list capacity: entries at or beyond it were never written
+  const float4 *pos;
+  const int32_t *row_ptr, *nbr;
+  const char4 *shift;
+  const uint8_t *elem;
+  const int32_t *atom_mol;
+  const MolGrid *grid;
+};
+
+// Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
+// FNN_E_CAPACITY) when a list overflows.  On return cnt_*/off_* hold per-element counts and
+// segment starts (warp-uniform).
+__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, WarpStage &S, int cnt_r[NE],
+                                int off_r[NE + 1], int cnt_a[NE], int off_a[NE + 1], bool want_dfc,
+                                DevStatus *st) {
+  int lane = threadIdx.x & 31;
+  unsigned lt = (1u << lane) - 1u;
+  int mol = A.atom_mol[i];
+  if (mol < 0) return false;   // atom outside every structure (already posted)
+  float4 pi = A.pos[i];
+  MolGrid g = A.grid[mol];
+  float Lx = g.pbc ? g.Lx : 0.f, Ly = g.pbc ? g.Ly : 0.f, Lz = g.pbc ? g.Lz : 0.f;
+  int k0 = (int)min((int64_t)A.row_ptr[i], A.cap), k1 = (int)min((int64_t)A.row_ptr[i + 1], A.cap);
+#pragma unroll
+  for (int q = 0; q < NE; q++) cnt_r[q] = cnt_a[q] = 0;
+  // pass 1: counts per element
+  for (int kb = k0; kb < k1; kb += 32) {
+    int k = kb + lane;
+    bool vr = false, va = false;
+    int e = 0;
+    if (k < k1) {
+      int j = A.nbr[k];
+      char4 sh = A.shift[k];
+      float4 pj = A.pos[j];
+      float dx = (pj.x - pi.x) + (float)sh.x * Lx;
+      float dy = (pj.y - pi.y) + (float)sh.y * Ly;
+      float dz = (pj.z - pi.z) + (float)sh.z * Lz;
+      float r = sqrtf(dx * dx + dy * dy + dz * dz);
+      vr = r < P.rc_rad;
+      va = r < P.rc_ang;
+      e = A.elem[j];
+    }
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      cnt_r[q] += __popc(__ballot_sync(FULL, vr && e == q));
+      cnt_a[q] += __popc(__ballot_sync(FULL, va && e == q));
+    }
+  }
+  off_r[0] = off_a[0] = 0;
+#pragma unroll
+  for (int q = 0; q < NE; q++) {
+    off_r[q + 1] = off_r[q] + cnt_r[q];
+    off_a[q + 1] = off_a[q] + cnt_a[q];
+  }
+  if (off_r[NE] > RAD_CAP || off_a[NE] > ANG_CAP) {
+    if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
+    return false;
+  }
+  int run_r[NE], run_a[NE];
+#pragma unroll
+  for (int q = 0; q < NE; q++) run_r[q] = run_a[q] = 0;
+  // pass 2: scatter into element segments (stable within an element)
+  for (int kb = k0; kb < k1; kb += 32) {
+    int k = kb + lane;
+    bool vr = false, va = false;
+    int e = 0, j = 0;
+    float dx = 0, dy = 0, dz = 0, r = 0;
+    if (k < k1) {
+      j = A.nbr[k];
+      char4 sh = A.shift[k];
+      float4 pj = A.pos[j];
+      dx = (pj.x - pi.x) + (float)sh.x * Lx;
+      dy = (pj.y - pi.y) + (float)sh.y * Ly;
+      dz = (pj.z - pi.z) + (float)sh.z * Lz;
+      r = sqrtf(dx * dx + dy * dy + dz * dz);
+      vr = r < P.rc_rad;
+      va = r < P.rc_ang;
+      e = A.elem[j];
+    }
+    int pr = -1, pa = -1;
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      unsigned mr = __ballot_sync(FULL, vr && e == q);
+      unsigned ma = __ballot_sync(FULL, va && e == q);
+      if (vr && e == q) pr = off_r[q] + run_r[q] + __popc(mr & lt);
+      if (va && e == q) pa = off_a[q] + run_a[q] + __popc(ma & lt);
+      run_r[q] += __popc(mr);
+      run_a[q] += __popc(ma);
+    }
+    if (pr >= 0) {
+      S.rd[pr] = make_float4(dx, dy, dz, r);
+      S.rfc[pr] = 0.5f * cospif(r / P.rc_rad) + 0.5f;
+      S.rj[pr] = j;
+      S.re[pr] = (unsigned char)e;
+    }
+    if (pa >= 0) {
+      S.aidx[pa] = (unsigned char)pr;
+      S.afc[pa] = 0.5f * cospif(r / P.rc_ang) + 0.5f;
+      if (want_dfc) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r / P.rc_ang);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// (j, k) of the t-th unordered pair j < k among n items, row-major upper triangle
+__device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
+  float b = 2.f * n - 1.f;
+  int jj = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))));
+  jj = max(0, min(jj, n - 2));
+  // start of row j is j (2n - j - 1) / 2
+  while (jj > 0 && jj * (2 * n - jj - 1) / 2 > t) jj--;
+  while ((jj + 1) * (2 * n - jj - 2) / 2 <= t) jj++;
+  j = jj;
+  k = t - jj * (2 * n - jj - 1) / 2 + jj + 1;
+}
+
+__device__ __forceinline__ void triplet_of(int t, int a, int b, int na, int nb, const int off_a[NE + 1], int &ja,
+                                           int &ka) {
+  if (a == b) {
+    int jj, kk;
+    tri_index(t, na, jj, kk);
+    ja = off_a[a] + jj;
+    ka = off_a[a] + kk;
+  } else {
+    ja = off_a[a] + t / nb;
+    ka = off_a[b] + t % nb;
+  }
+}
+
+template <typename OutT>
+__device__ __forceinline__ void store_out(OutT *p, float v);
+template <>
+__device__ __forceinline__ void store_out<float>(float *p, float v) { *p = v; }
+
+struct AevFwdArgs {
+  StageArgs sa;
+  AevParams P;
+  float *out;             // [rows][1008]
+  const int32_t *inv;     // padded row -> atom (-1 padding); NULL = rows are atoms
+  const int32_t *meta;    // META_NPAD when inv != NULL
+  int n_atoms;
+  DevStatus *st;
+};
+
+template <typename OutT>
+__global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
+  __shared__ WarpStage smem[AEV_WARPS];
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  WarpStage &S = smem[wl];
+  const AevParams &P = A.P;
+  int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
+  for (int row = wg; row < nrows; row += nw) {
+    OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
+    int i = A.inv ? A.inv[row] : row;
+    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
+    bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, false, A.st);
+    if (!ok) {
+      for (int c = lane; c < NAEV; c += 32) store_out<OutT>(out + c, 0.f);
+      __syncwarp();
+      continue;
+    }
+    // ---- radial
+    {
+      int h = lane >> 4, k = lane & 15;
+      float Rk = P.shf_r[k];
+#pragma unroll 1
+      for (int q = 0; q < NE; q++) {
+        float acc = 0.f;
+        for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
+          float dr = S.rd[t].w - Rk;
+          acc += expf(-P.eta_r * dr * dr) * S.rfc[t];
+        }
+        acc += __shfl_xor_sync(FULL, acc, 16);
+        if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc);
+      }
+    }
+    // ---- angular
+    {
+      int s_my = lane & 3, m_my = lane >> 2;
+      int p = 0;
+#pragma unroll 1
+      for (int a = 0; a < NE; a++) {
+#pragma unroll 1
+        for (int b = a; b < NE; b++, p++) {
+          int na = cnt_a[a], nb = cnt_a[b];
+          int T = (a == b) ? na * (na - 1) / 2 : na * nb;
+          float acc = 0.f;
+          for (int base = 0; base < T; base += 32) {
+            int t = base + lane;
+            if (t < T) {
+              int ja, ka;
+              triplet_of(t, a, b, na, nb, off_a, ja, ka);
+              float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
+              float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) / (d1.w * d2.w);
+              float c95 = 0.95f * c;
+              float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+#pragma unroll
+              for (int s = 0; s < NSZ; s++) {
+                float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+                S.stage[lane][s] = exp2f(P.zeta * log2f(base_s));
+              }
+              float rbar = 0.5f * (d1.w + d2.w);
+              float fcc = 2.f * S.afc[ja] * S.afc[ka];
+#pragma unroll
+              for (int m = 0; m < NSA; m++) {
+                float dr = rbar - P.shf_a[m];
+                S.stage[lane][4 + m] = expf(-P.eta_a * dr * dr) * fcc;
+              }
+            }
+            __syncwarp();
+            int nt = min(32, T - base);
+            for (int q = 0; q < nt; q++) acc += S.stage[q][s_my] * S.stage[q][4 + m_my];
+            __syncwarp();
+          }
+          store_out<OutT>(out + NRAD + p * 32 + lane, acc);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------- adjoint
+struct AevAdjArgs {
+  StageArgs sa;
+  AevParams P;
+  const float *gaev;      // [rows][1008] dE/dAEV
+  const int32_t *inv;     // padded row -> atom; NULL = rows are atoms
+  const int32_t *meta;
+  int n_atoms;
+  float *F;               // [N][3], accumulated (caller zeroes)
+  double *virial;         // [n_mol][9] accumulated, or NULL
+  DevStatus *st;
+};
+
+__global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
+  __shared__ WarpStage smem[AEV_WARPS];
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  WarpStage &S = smem[wl];
+  const AevParams &P = A.P;
+  int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
+  double vacc[9];
+#pragma unroll
+  for (int q = 0; q < 9; q++) vacc[q] = 0.0;
+  int cur_mol = -1;
+  for (int row = wg; row < nrows; row += nw) {
+    int i = A.inv ? A.inv[row] : row;
+    if (i < 0) continue;
+    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
+    if (!stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st)) continue;
+    const float *G = A.gaev + (size_t)row * NAEV;
+    for (int c = lane; c < NRAD; c += 32) S.grad[c] = G[c];
+    __syncwarp();
+    // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
+    int nrad = off_r[NE];
+    for (int t = lane; t < nrad; t += 32) {
+      float4 d = S.rd[t];
+      float r = d.w;
+      int e = S.re[t];
+      float fc = S.rfc[t];
+      float dfc = -0.5f * P.pi_rc_rad * sinpif(r / P.rc_rad);
+      float dEdr = 0.f;
+#pragma unroll
+      for (int k = 0; k < NSR; k++) {
+        float dr = r - P.shf_r[k];
+        float gk = expf(-P.eta_r * dr * dr);
+        dEdr += S.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
+      }
+      float f = dEdr / r;
+      S.gacc[t][0] = f * d.x;
+      S.gacc[t][1] = f * d.y;
+      S.gacc[t][2] = f * d.z;
+    }
+    __syncwarp();
+    // ---- angular
+    int p = 0;
+#pragma unroll 1
+    for (int a = 0; a < NE; a++) {
+#pragma unroll 1
+      for (int b = a; b < NE; b++, p++) {
+        int na = cnt_a[a], nb = cnt_a[b];
+        int T = (a == b) ? na * (na - 1) / 2 : na * nb;
+        if (T == 0) continue;
+        float Gb[32];
+        {
+          float mine = G[NRAD + p * 32 + lane];
+#pragma unroll
+          for (int q = 0; q < 32; q++) Gb[q] = __shfl_sync(FULL, mine, q);
+        }
+        for (int base = 0; base < T; base += 32) {
+          int t = base + lane;
+          if (t < T) {
+            int ja, ka;
+            triplet_of(t, a, b, na, nb, off_a, ja, ka);
+            int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
+            float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
+            float r1 = d1.w, r2 = d2.w;
+            float inv12 = 1.f / (r1 * r2);
+            float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
+            float c95 = 0.95f * c;
+            float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+            float ds95 = -0.9025f * c / s95;   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
+            float fs[NSZ], dfs[NSZ];
+#pragma unroll
+            for (int s = 0; s < NSZ; s++) {
+              float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+              float f = exp2f(P.zeta * log2f(base_s));
+              fs[s] = f;
+              dfs[s] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
+            }
+            float rbar = 0.5f * (r1 + r2);
+            float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
+#pragma unroll
+            for (int m = 0; m < NSA; m++) {
+              float dr = rbar - P.shf_a[m];
+              float gm = expf(-P.eta_a * dr * dr);
+              float dgm = -2.f * P.eta_a * dr * gm;
+#pragma unroll
+              for (int s = 0; s < NSZ; s++) {
+                H[s] += Gb[m * NSZ + s] * gm;
+                Hd[s] += Gb[m * NSZ + s] * dgm;
+              }
+            }
+            float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
+            float C = f1 * f2;
+            float sH = 0.f, sdH = 0.f, sHd = 0.f;
+#pragma unroll
+            for (int s = 0; s < NSZ; s++) {
+              sH += fs[s] * H[s];
+              sdH += dfs[s] * H[s];
+              sHd += fs[s] * Hd[s];
+            }
+            float dEdc = 2.f * C * sdH;
+            float dEdrbar = 2.f * C * sHd;
+            float dEdC = 2.f * sH;
+            float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
+            float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
+            float a1 = dEdr1 / r1 - dEdc * c / (r1 * r1), b1 = dEdc * inv12;
+            float a2 = dEdr2 / r2 - dEdc * c / (r2 * r2);
+            atomicAdd(&S.gacc[rj1][0], a1 * d1.x + b1 * d2.x);
+            atomicAdd(&S.gacc[rj1][1], a1 * d1.y + b1 * d2.y);
+            atomicAdd(&S.gacc[rj1][2], a1 * d1.z + b1 * d2.z);
+            atomicAdd(&S.gacc[rj2][0], a2 * d2.x + b1 * d1.x);
+            atomicAdd(&S.gacc[rj2][1], a2 * d2.y + b1 * d1.y);
+            atomicAdd(&S.gacc[rj2][2], a2 * d2.z + b1 * d1.z);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    // ---- scatter: F_j -= g, F_i += sum g, W -= d (x) g
+    float ci[3] = {0, 0, 0};
+    float w[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) w[q] = 0.f;
+    for (int t = lane; t < nrad; t += 32) {
+      float g0 = S.gacc[t][0], g1 = S.gacc[t][1], g2 = S.gacc[t][2];
+      int j = S.rj[t];
+      atomicAdd(&A.F[3 * (size_t)j + 0], -g0);
+      atomicAdd(&A.F[3 * (size_t)j + 1], -g1);
+      atomicAdd(&A.F[3 * (size_t)j + 2], -g2);
+      ci[0] += g0; ci[1] += g1; ci[2] += g2;
+      float4 d = S.rd[t];
+      float dv[3] = {d.x, d.y, d.z}, gv[3] = {g0, g1, g2};
+#pragma unroll
+      for (int x = 0; x < 3; x++)
+#pragma unroll
+        for (int y = 0; y < 3; y++) w[3 * x + y] -= dv[x] * gv[y];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int x = 0; x < 3; x++) ci[x] += __shfl_xor_sync(FULL, ci[x], o);
+#pragma unroll
+      for (int q = 0; q < 9; q++) w[q] += __shfl_xor_sync(FULL, w[q], o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.F[3 * (size_t)i + 0], ci[0]);
+      atomicAdd(&A.F[3 * (size_t)i + 1], ci[1]);
+      atomicAdd(&A.F[3 * (size_t)i + 2], ci[2]);
+      if (A.virial) {
+        int mol = A.sa.atom_mol[i];
+        if (mol != cur_mol) {
+          if (cur_mol >= 0)
+            for (int q = 0; q < 9; q++) atomicAdd(&A.virial[9 * (size_t)cur_mol + q], vacc[q]);
+          for (int q = 0; q < 9; q++) vacc[q] = 0.0;
+          cur_mol = mol;
+        }
+        for (int q = 0; q < 9; q++) vacc[q] += (double)w[q];
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && A.virial && cur_mol >= 0)
+    for (int q = 0; q < 9; q++) atomicAdd(&A.virial[9 * (size_t)cur_mol + q], vacc[q]);
+}
+
+static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
+  StageArgs s;
+  s.cap = nl->capacity;
+  s.pos = reinterpret_cast<const float4 *>(sys->pos);
+  s.row_ptr = nl->row_ptr;
+  s.nbr = nl->nbr;
+  s.shift = nl->shift;
+  s.elem = nl->elem;
+  s.atom_mol = nl->atom_mol;
+  s.grid = nl->grid;
+  return s;
+}
+
+static int aev_grid(fnn_ctx *ctx, int64_t rows) {
+  int64_t need = (rows + AEV_WARPS - 1) / AEV_WARPS;
+  int64_t cap = (int64_t)ctx->num_sms * 12;
+  if (need > cap) need = cap;
+  return need < 1 ? 1 : (int)need;
+}
+
+fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *out,
+                              const int32_t *inv, cudaStream_t s) {
+  AevFwdArgs a;
+  a.sa = stage_args(sys, nl);
+  a.P = ctx->aev;
+  a.out = out;
+  a.inv = inv;
+  a.meta = nl->meta;
+  a.n_atoms = sys->n_atoms;
+  a.st = ctx->status;
+  int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
+  if (rows == 0) return FNN_OK;
+  k_aev_forward<float><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  return check_launch(ctx, "aev_forward");
+}
+
+fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,
+                              const int32_t *inv, float *F, double *virial, cudaStream_t s) {
+  AevAdjArgs a;
+  a.sa = stage_args(sys, nl);
+  a.P = ctx->aev;
+  a.gaev = gaev;
+  a.inv = inv;
+  a.meta = nl->meta;
+  a.n_atoms = sys->n_atoms;
+  a.F = F;
+  a.virial = virial;
+  a.st = ctx->status;
+  int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
+  if (rows == 0) return FNN_OK;
+  k_aev_adjoint<<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  return check_launch(ctx, "aev_adjoint");
+}
+
+}  // namespace fnn

@@ -1,0 +1,201 @@
+// Internal definitions shared by the CUDA translation units of libfnn.
+// Nothing here is part of the C ABI (include/fnn.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fnn.h"
+
+namespace fnn {
+
+// ---------------------------------------------------------------------------------------- sizes
+constexpr int NE = 7;                       // elements H C N O F S Cl
+constexpr int NSR = 16;                     // radial shifts
+constexpr int NSA = 8;                      // angular radial shifts
+constexpr int NSZ = 4;                      // angle sections
+constexpr int NRAD = NE * NSR;              // 112
+constexpr int NPAIR = NE * (NE + 1) / 2;    // 28
+constexpr int NAEV = NRAD + NPAIR * NSA * NSZ;  // 1008
+constexpr int H1 = 256, H2 = 192, H3 = 160; // hidden widths
+constexpr int MAXM = 8;                     // ensemble members
+constexpr int ROW_TILE = 128;               // species segments are padded to this many rows
+constexpr int RAD_CAP = 160;                // neighbours within rc_rad handled per atom
+constexpr int ANG_CAP = 64;                 // neighbours within rc_ang handled per atom
+constexpr float CELU_ALPHA = 0.1f;
+
+// element index of an atomic number, -1 when outside the table
+__host__ __device__ inline int element_of(int z) {
+  switch (z) {
+    case 1: return 0;
+    case 6: return 1;
+    case 7: return 2;
+    case 8: return 3;
+    case 9: return 4;
+    case 16: return 5;
+    case 17: return 6;
+    default: return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------------------- status
+// Sticky device-side status: the first error posted wins; fnn_sync reads and clears it.
+struct DevStatus {
+  int code;
+  int pad;
+  long long info;
+};
+
+__device__ inline void post_status(DevStatus *st, int code, long long info) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->info = info;
+}
+
+// ---------------------------------------------------------------------------------------- params
+struct AevParams {
+  float rc_rad, rc_ang;
+  float eta_r, eta_a, zeta;
+  float pi_rc_rad, pi_rc_ang;   // pi / rc
+  float shf_r[NSR];
+  float shf_a[NSA];
+  float cos_z[NSZ], sin_z[NSZ]; // cos / sin of the section centres
+};
+
+// per-structure cell-list geometry
+struct MolGrid {
+  float ox, oy, oz;       // origin of the grid (gas phase: bounding-box minimum; periodic: 0)
+  float ix, iy, iz;       // cells per A along each axis
+  float Lx, Ly, Lz;       // periodic box edges (0 when not periodic)
+  int dx, dy, dz;         // cells per axis
+  int cell_base;          // unused (first cells come from the scanned per-structure counts)
+  int pbc;
+};
+
+// ---------------------------------------------------------------------------------------- handles
+struct DeviceWeights {
+  int M = 0;
+  // FP32, element-major concatenations for the member-fused layers
+  float *W1cat = nullptr;   // [7][M*256][1008]
+  float *b1cat = nullptr;   // [7][M*256]
+  float *W1Tcat = nullptr;  // [7][1008][M*256]
+  float *W2 = nullptr;      // [M][7][192][256]
+  float *b2 = nullptr;      // [M][7][192]
+  float *W2T = nullptr;     // [M][7][256][192]
+  float *W3 = nullptr;      // [M][7][160][192]
+  float *b3 = nullptr;      // [M][7][160]
+  float *W3T = nullptr;     // [M][7][192][160]
+  float *w4 = nullptr;      // [M][7][160]
+  float *b4 = nullptr;      // [M][7]
+  void *tc = nullptr;       // tensor-core forms (mlp_tc.cu)
+};
+
+struct Workspace {
+  size_t rows = 0;          // padded row capacity
+  int M = 0;
+  float *aev = nullptr;     // [rows][1008]
+  float *h1 = nullptr;      // [rows][M*256]
+  float *h2 = nullptr;      // [rows][M*192]
+  float *g3 = nullptr;      // [rows][M*160]
+  float *g2 = nullptr;      // [rows][M*192]
+  float *g1 = nullptr;      // [rows][M*256]
+  float *gaev = nullptr;    // [rows][1008]
+  float *ypart = nullptr;   // [rows][M][4]
+  void *tc = nullptr;       // tensor-core buffers (mlp_tc.cu)
+  size_t tc_rows = 0;
+};
+
+}  // namespace fnn
+
+struct fnn_ctx {
+  fnn_config cfg;
+  fnn::AevParams aev;
+  int device = 0;
+  int num_sms = 148;
+  fnn::DevStatus *status = nullptr;   // device
+  fnn::DeviceWeights w;
+  bool has_weights = false;
+  fnn::Workspace ws;
+  std::string last_error;
+  // host-call staging (fnn_energy_forces_host)
+  struct HostStage {
+    int32_t n_atoms = -1, n_mol = -1;
+    int32_t *Z = nullptr, *mol_offsets = nullptr;
+    float *pos = nullptr, *cell = nullptr;
+    uint8_t *pbc = nullptr;
+    float *pos3 = nullptr;
+    double *E = nullptr, *virial = nullptr;
+    float *F = nullptr;
+    fnn_nlist *nl = nullptr;
+  } host;
+};
+
+struct fnn_nlist {
+  fnn_ctx *ctx = nullptr;
+  int64_t capacity = 0;       // entries
+  int32_t atom_cap = 0, mol_cap = 0, cell_cap = 0, pad_cap = 0;
+  int32_t n_atoms = 0, n_mol = 0;
+  double R = 0.0;
+  bool built = false;
+  cudaStream_t stream = nullptr;
+  // list
+  int32_t *row_ptr = nullptr;   // [N+1]
+  int32_t *nbr = nullptr;       // [cap]
+  char4 *shift = nullptr;       // [cap]
+  // per atom
+  int32_t *atom_mol = nullptr;  // [N]
+  uint8_t *elem = nullptr;      // [N]
+  int32_t *cell_of = nullptr;   // [N]
+  int32_t *cell_tmp = nullptr;  // [N]
+  int32_t *cell_atoms = nullptr;// [N]
+  int32_t *counts = nullptr;    // [N + 1]
+  // per structure
+  fnn::MolGrid *grid = nullptr; // [n_mol]
+  int32_t *mol_cells = nullptr; // [n_mol + 1]
+  // per cell
+  int32_t *cell_count = nullptr;// [cells + 1]
+  int32_t *cell_start = nullptr;// [cells + 1]
+  // species order
+  int32_t *perm = nullptr;      // [N] atom -> padded species-sorted row
+  int32_t *inv = nullptr;       // [pad_cap] row -> atom, -1 for padding
+  int32_t *tile_elem = nullptr; // [pad_cap / 128] element of each 128-row tile, -1 beyond the end
+  int32_t *blk_count = nullptr; // [blocks][8]
+  int32_t *meta = nullptr;      // device scalars, see META_*
+  int32_t *scan_tmp = nullptr;  // scan block sums
+  int64_t scan_tmp_len = 0;
+};
+
+namespace fnn {
+
+enum { META_CELLS = 0, META_NNZ = 1, META_NPAD = 2, META_SEG = 4 /* [8] segment starts */, META_LEN = 16 };
+
+// ---------------------------------------------------------------------------------------- helpers
+#define FNN_CUDA_TRY(ctx, call)                                                        \
+  do {                                                                                 \
+    cudaError_t err__ = (call);                                                        \
+    if (err__ != cudaSuccess) {                                                        \
+      (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(err__);      \
+      return FNN_E_CUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+
+fnn_status check_launch(fnn_ctx *ctx, const char *what);
+
+// exclusive scan of n int32 values in place; total written to *total_dev (device) when non-null
+fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
+                          int64_t tmp_len, cudaStream_t s);
+int64_t scan_tmp_needed(int64_t n);
+
+// kernels' host launchers (defined in their .cu files)
+fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *out,
+                              const int32_t *inv, cudaStream_t s);
+fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,
+                              const int32_t *inv, float *F, double *virial, cudaStream_t s);
+fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s);
+fnn_status mlp_tc_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, fnn_precision prec, cudaStream_t s);
+fnn_status upload_tc_weights(fnn_ctx *ctx, const fnn_weights *hw);
+void free_tc(fnn_ctx *ctx);
+fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s);
+fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows);
+
+}  // namespace fnn

@@ -1,0 +1,256 @@
+// Per-element networks 1008-256-192-160-1 with CELU (section II.B, ChemicalNet) and their
+// input gradient, FP32 form: SIMT FFMA GEMMs over species-sorted, 128-row padded segments.
+//
+// Every product is C[r, n] = sum_k A[r, k] B[n, k] with both operands K-contiguous ("TN"):
+// forward weights are W[out][in], backward weights are stored transposed.  A 128-row tile
+// belongs to one element (tile_elem), blockIdx.z selects the ensemble member.
+//   L1   h1 = CELU(aev W1^T + b1)           all members at once: N = M*256
+//   L2   h2 = CELU(h1_m W2^T + b2)          per member
+//   L3   h3 = CELU(h2_m W3^T + b3); y_m partial = h3 . w4 (per 64-column tile);
+//        g3 = (1/M) w4 * CELU'(z3)          fused epilogue
+//   L3'  g2 = (g3_m W3) * CELU'(z2)         CELU' recovered from h: 1 if h > 0 else 1 + h/alpha
+//   L2'  g1 = (g2_m W2) * CELU'(z1)
+//   L1'  dE/dAEV = g1 W1cat                 K = M*256 sums the members
+#include "fnn_internal.cuh"
+
+namespace fnn {
+
+enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_SCALE = 3 };
+
+struct GemmP {
+  const float *A;
+  long long lda, a_mstride;
+  const float *B;
+  long long ldb, b_estride, b_mstride;
+  float *C;
+  long long ldc, c_mstride;
+  int N, K;
+  const int32_t *tile_elem;
+  const float *bias;
+  long long bias_estride, bias_mstride;
+  const float *aux;              // h of the previous layer (EPI_DCELU)
+  long long ldaux, aux_mstride;
+  const float *w4;               // EPI_L3
+  long long w4_estride, w4_mstride;
+  float *ypart;                  // [rows][M][4]
+  int M;
+  float scale;
+};
+
+constexpr int BM = 128, BN = 64, BK = 16, GNT = 256;
+
+__device__ __forceinline__ float celu(float z) { return z > 0.f ? z : CELU_ALPHA * expm1f(z / CELU_ALPHA); }
+__device__ __forceinline__ float dcelu_from_h(float h) { return h > 0.f ? 1.f : 1.f + h / CELU_ALPHA; }
+
+template <int EPI>
+__global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
+  int e = p.tile_elem[blockIdx.y];
+  if (e < 0) return;
+  const int m = blockIdx.z;
+  const long long row0 = (long long)blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  const float *A = p.A + row0 * p.lda + m * p.a_mstride;
+  const float *B = p.B + e * p.b_estride + m * p.b_mstride;
+
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+
+  // global -> register prefetch
+  const int ar = tid >> 2, akc = (tid & 3) * 4;   // A rows ar, ar + 64
+  const int bn = tid >> 2, bkc = (tid & 3) * 4;   // B row n0 + bn
+  float4 ra[2], rb;
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 2; q++) ra[q] = *reinterpret_cast<const float4 *>(A + (long long)(ar + 64 * q) * p.lda + k0 + akc);
+    if (n0 + bn < p.N)
+      rb = *reinterpret_cast<const float4 *>(B + (long long)(n0 + bn) * p.ldb + k0 + bkc);
+    else
+      rb = make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      As[buf][akc + 0][ar + 64 * q] = ra[q].x;
+      As[buf][akc + 1][ar + 64 * q] = ra[q].y;
+      As[buf][akc + 2][ar + 64 * q] = ra[q].z;
+      As[buf][akc + 3][ar + 64 * q] = ra[q].w;
+    }
+    Bs[buf][bkc + 0][bn] = rb.x;
+    Bs[buf][bkc + 1][bn] = rb.y;
+    Bs[buf][bkc + 2][bn] = rb.z;
+    Bs[buf][bkc + 3][bn] = rb.w;
+  };
+
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+
+  const int nk = p.K / BK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int kt = 0; kt < nk; kt++) {
+    int buf = kt & 1;
+    if (kt + 1 < nk) load((kt + 1) * BK);
+#pragma unroll
+    for (int k = 0; k < BK; k++) {
+      float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
+      float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
+      float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) store(buf ^ 1);
+    __syncthreads();
+  }
+
+  // epilogue
+  float *C = p.C + row0 * p.ldc + m * p.c_mstride;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    int r = ty * 8 + i;
+    float ysum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int n = n0 + tx * 4 + j;
+      if (n >= p.N) continue;
+      float v = acc[i][j];
+      float o;
+      if (EPI == EPI_BIAS_CELU) {
+        o = celu(v + p.bias[e * p.bias_estride + m * p.bias_mstride + n]);
+      } else if (EPI == EPI_L3) {
+        float z = v + p.bias[e * p.bias_estride + m * p.bias_mstride + n];
+        float w = p.w4[e * p.w4_estride + m * p.w4_mstride + n];
+        ysum += celu(z) * w;
+        o = p.scale * w * (z > 0.f ? 1.f : expf(z / CELU_ALPHA));
+      } else if (EPI == EPI_DCELU) {
+        float h = p.aux[(row0 + r) * p.ldaux + m * p.aux_mstride + n];
+        o = v * dcelu_from_h(h);
+      } else {
+        o = v * p.scale;
+      }
+      C[(long long)r * p.ldc + n] = o;
+    }
+    if (EPI == EPI_L3) {
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) ysum += __shfl_xor_sync(0xffffffffu, ysum, o);
+      if (tx == 0) p.ypart[((row0 + r) * p.M + m) * 4 + blockIdx.x] = ysum;
+    }
+  }
+}
+
+template <int EPI>
+static void launch(const GemmP &p, int row_tiles, int members, cudaStream_t s) {
+  dim3 grid((p.N + BN - 1) / BN, row_tiles, members);
+  k_gemm_f32<EPI><<<grid, GNT, 0, s>>>(p);
+}
+
+fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s) {
+  const DeviceWeights &w = ctx->w;
+  Workspace &ws = ctx->ws;
+  const int M = w.M;
+  const int tiles = nl->pad_cap / ROW_TILE;
+  GemmP p{};
+  p.tile_elem = nl->tile_elem;
+  p.M = M;
+  // L1
+  p.A = ws.aev; p.lda = NAEV; p.a_mstride = 0;
+  p.B = w.W1cat; p.ldb = NAEV; p.b_estride = (long long)M * H1 * NAEV; p.b_mstride = 0;
+  p.C = ws.h1; p.ldc = (long long)M * H1; p.c_mstride = 0;
+  p.N = M * H1; p.K = NAEV;
+  p.bias = w.b1cat; p.bias_estride = (long long)M * H1; p.bias_mstride = 0;
+  launch<EPI_BIAS_CELU>(p, tiles, 1, s);
+  // L2
+  p.A = ws.h1; p.lda = (long long)M * H1; p.a_mstride = H1;
+  p.B = w.W2; p.ldb = H1; p.b_estride = (long long)H2 * H1; p.b_mstride = (long long)NE * H2 * H1;
+  p.C = ws.h2; p.ldc = (long long)M * H2; p.c_mstride = H2;
+  p.N = H2; p.K = H1;
+  p.bias = w.b2; p.bias_estride = H2; p.bias_mstride = (long long)NE * H2;
+  launch<EPI_BIAS_CELU>(p, tiles, M, s);
+  // L3 + output layer + g3
+  p.A = ws.h2; p.lda = (long long)M * H2; p.a_mstride = H2;
+  p.B = w.W3; p.ldb = H2; p.b_estride = (long long)H3 * H2; p.b_mstride = (long long)NE * H3 * H2;
+  p.C = ws.g3; p.ldc = (long long)M * H3; p.c_mstride = H3;
+  p.N = H3; p.K = H2;
+  p.bias = w.b3; p.bias_estride = H3; p.bias_mstride = (long long)NE * H3;
+  p.w4 = w.w4; p.w4_estride = H3; p.w4_mstride = (long long)NE * H3;
+  p.ypart = ws.ypart;
+  p.scale = 1.f / (float)M;
+  launch<EPI_L3>(p, tiles, M, s);
+  // L3 backward
+  p.A = ws.g3; p.lda = (long long)M * H3; p.a_mstride = H3;
+  p.B = w.W3T; p.ldb = H3; p.b_estride = (long long)H2 * H3; p.b_mstride = (long long)NE * H2 * H3;
+  p.C = ws.g2; p.ldc = (long long)M * H2; p.c_mstride = H2;
+  p.N = H2; p.K = H3;
+  p.aux = ws.h2; p.ldaux = (long long)M * H2; p.aux_mstride = H2;
+  launch<EPI_DCELU>(p, tiles, M, s);
+  // L2 backward
+  p.A = ws.g2; p.lda = (long long)M * H2; p.a_mstride = H2;
+  p.B = w.W2T; p.ldb = H2; p.b_estride = (long long)H1 * H2; p.b_mstride = (long long)NE * H1 * H2;
+  p.C = ws.g1; p.ldc = (long long)M * H1; p.c_mstride = H1;
+  p.N = H1; p.K = H2;
+  p.aux = ws.h1; p.ldaux = (long long)M * H1; p.aux_mstride = H1;
+  launch<EPI_DCELU>(p, tiles, M, s);
+  // L1 backward: dE/dAEV, K = M*256 sums the members
+  p.A = ws.g1; p.lda = (long long)M * H1; p.a_mstride = 0;
+  p.B = w.W1Tcat; p.ldb = (long long)M * H1; p.b_estride = (long long)NAEV * M * H1; p.b_mstride = 0;
+  p.C = ws.gaev; p.ldc = NAEV; p.c_mstride = 0;
+  p.N = NAEV; p.K = M * H1;
+  p.scale = 1.f;
+  launch<EPI_SCALE>(p, tiles, 1, s);
+  return check_launch(ctx, "mlp_fp32");
+}
+
+// ---------------------------------------------------------------------------- energy reduction
+// E_mol = sum over atoms of (1/M) sum_m (y partials + b4), accumulated in float64 (section II.E).
+__global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, const int32_t *perm,
+                         const uint8_t *elem, const float *ypart, const float *b4, int M, int ntile, double *E,
+                         DevStatus *st) {
+  __shared__ double red[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int mol = blockIdx.x; mol < n_mol; mol += gridDim.x) {
+    int a0 = max(mol_offsets[mol], 0), a1 = min(mol_offsets[mol + 1], n_atoms);
+    double acc = 0.0;
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+      int r = perm[i], e = elem[i];
+      float y = 0.f;
+      for (int m = 0; m < M; m++) {
+        const float *yp = ypart + ((size_t)r * M + m) * 4;
+        float ym = b4[m * NE + e];
+        for (int t = 0; t < ntile; t++) ym += yp[t];
+        y += ym;
+      }
+      acc += (double)y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < nwarp; q++) t += red[q];
+      t /= (double)M;
+      E[mol] = t;
+      if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+    }
+    __syncthreads();
+  }
+}
+
+fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s) {
+  int blocks = sys->n_mol < 8 * ctx->num_sms ? sys->n_mol : 8 * ctx->num_sms;
+  int threads = sys->n_atoms / (sys->n_mol > 0 ? sys->n_mol : 1) > 512 ? 1024 : 128;
+  k_energy<<<blocks, threads, 0, s>>>(sys->n_mol, sys->n_atoms, sys->mol_offsets, nl->perm, nl->elem, ctx->ws.ypart,
+                                      ctx->w.b4, ctx->w.M, (H3 + BN - 1) / BN, E, ctx->status);
+  return check_launch(ctx, "energy_reduce");
+}
+
+}  // namespace fnn

@@ -1,0 +1,700 @@
+// Cell-list neighbour search (section II.A graph semantics; cell lists per section V.E) and the
+// species-sorted atom order used by the networks.
+//
+// Pipeline (one stream, no host synchronisation):
+//   k_check_cover   offsets start at 0, end at N, never decrease
+//   k_mol_setup     per structure: validate species / cell, bounding box, cell-grid geometry
+//   scan            structure cell counts -> first global cell of each structure
+//   k_bin           per atom: cell index, histogram (atomics)
+//   scan            cell counts -> cell starts (counting sort)
+//   k_scatter       atoms into cells; k_sort_cells orders each cell by atom index (determinism)
+//   k_pairs<COUNT>  warp per atom: 27-cell stencil, predicate, ballot + popc count
+//   scan            counts -> CSR row pointers
+//   k_pairs<FILL>   same traversal, ballot-compacted writes at the row pointer
+//   k_elem_*        stable counting sort of atoms by element into 128-row padded segments
+#include <cfloat>
+
+#include "fnn_internal.cuh"
+
+namespace fnn {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------------ scan
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// exclusive scan across a block of NT threads; *total receives the block sum (all threads)
+template <int NT>
+__device__ __forceinline__ int block_excl_scan(int v, int *total) {
+  __shared__ int warp_sums[NT / 32];
+  __shared__ int tot;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < NT / 32 ? warp_sums[lane] : 0;
+    int si = warp_incl_scan(s);
+    if (lane < NT / 32) warp_sums[lane] = si - s;
+    if (lane == NT / 32 - 1) tot = si;
+  }
+  __syncthreads();
+  int r = inc - v + warp_sums[w];
+  *total = tot;
+  __syncthreads();
+  return r;
+}
+
+constexpr int SCAN_NT = 512, SCAN_ITEMS = 4, SCAN_TILE = SCAN_NT * SCAN_ITEMS;
+
+__global__ void k_scan_tiles(int32_t *data, int64_t n, int32_t *tile_sums) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = base + k < n ? data[base + k] : 0;
+    s += v[k];
+  }
+  int tot;
+  int ex = block_excl_scan<SCAN_NT>(s, &tot);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) data[base + k] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of the tile sums in chunks, total to *total_dev
+__global__ void k_scan_top(int32_t *tile_sums, int64_t nt, int32_t *total_dev) {
+  int carry = 0;
+  for (int64_t c = 0; c < nt; c += SCAN_NT) {
+    int64_t k = c + threadIdx.x;
+    int v = k < nt ? tile_sums[k] : 0;
+    int tot;
+    int ex = block_excl_scan<SCAN_NT>(v, &tot);
+    if (k < nt) tile_sums[k] = ex + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+}
+
+__global__ void k_scan_add(int32_t *data, int64_t n, const int32_t *tile_sums) {
+  int add = tile_sums[blockIdx.x];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_NT)
+    if (base + k < n) data[base + k] += add;
+}
+
+int64_t scan_tmp_needed(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
+                          int64_t tmp_len, cudaStream_t s) {
+  if (n <= 0) return FNN_OK;
+  int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nt > tmp_len) {
+    ctx->last_error = "scan scratch too small";
+    return FNN_E_INVALID;
+  }
+  k_scan_tiles<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  k_scan_top<<<1, SCAN_NT, 0, s>>>(tmp, nt, total_dev);
+  k_scan_add<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  return check_launch(ctx, "exclusive_scan");
+}
+
+// ------------------------------------------------------------------------------------- structures
+// offsets must start at 0, end at N and never decrease: otherwise some atom has no structure
+__global__ void k_check_cover(fnn_system sys, DevStatus *st) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= sys.n_mol; m += gridDim.x * blockDim.x) {
+    int a = sys.mol_offsets[m];
+    bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
+    if (m == sys.n_mol) ok = ok && a == sys.n_atoms;
+    if (!ok) post_status(st, FNN_E_INVALID, m);
+  }
+}
+
+constexpr int SETUP_NT = 256;
+
+__global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid *grid, int32_t *mol_cells,
+                                                        int32_t *atom_mol, uint8_t *elem, double R,
+                                                        DevStatus *st) {
+  __shared__ float red[6][SETUP_NT / 32];
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int m = blockIdx.x; m < sys.n_mol; m += gridDim.x) {
+    int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    bool bad = (a0 < 0 || a1 < a0 || a1 > sys.n_atoms);
+    if (bad) {
+      if (threadIdx.x == 0) {
+        post_status(st, FNN_E_INVALID, m);
+        grid[m] = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
+        mol_cells[m] = 1;
+      }
+      continue;
+    }
+    int pbc = sys.pbc ? (sys.pbc[m] != 0) : 0;
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+      atom_mol[i] = m;
+      int e = element_of(sys.Z[i]);
+      if (e < 0) {
+        post_status(st, FNN_E_SPECIES, i);
+        e = 0;
+      }
+      elem[i] = (uint8_t)e;
+      float4 p = pos[i];
+      if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) post_status(st, FNN_E_NONFINITE, i);
+      mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+      mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn[a] = fminf(mn[a], __shfl_xor_sync(FULL, mn[a], o));
+        mx[a] = fmaxf(mx[a], __shfl_xor_sync(FULL, mx[a], o));
+      }
+    }
+    if (lane == 0) {
+      for (int a = 0; a < 3; a++) { red[a][w] = mn[a]; red[3 + a][w] = mx[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < SETUP_NT / 32; k++)
+        for (int a = 0; a < 3; a++) {
+          red[a][0] = fminf(red[a][0], red[a][k]);
+          red[3 + a][0] = fmaxf(red[3 + a][0], red[3 + a][k]);
+        }
+      MolGrid g{};
+      int n = a1 - a0;
+      double edge = R * (1.0 + 1e-4);   // cells at least this wide: fp32 binning error stays far below the margin
+      double ext[3];
+      g.pbc = pbc;
+      if (pbc) {
+        const float *c = sys.cell + 9 * (size_t)m;
+        bool ortho = c[1] == 0.f && c[2] == 0.f && c[3] == 0.f && c[5] == 0.f && c[6] == 0.f && c[7] == 0.f;
+        g.Lx = c[0]; g.Ly = c[4]; g.Lz = c[8];
+        if (!ortho || !((double)g.Lx > 2 * R) || !((double)g.Ly > 2 * R) || !((double)g.Lz > 2 * R)) {
+          post_status(st, FNN_E_CELL, m);
+          g.pbc = 0;  // keep the traversal well-defined; the result is flagged invalid
+          g.Lx = g.Ly = g.Lz = 0.f;
+        }
+        ext[0] = g.Lx; ext[1] = g.Ly; ext[2] = g.Lz;
+        g.ox = g.oy = g.oz = 0.f;
+      }
+      if (!g.pbc) {
+        if (n == 0) {
+          red[0][0] = red[1][0] = red[2][0] = 0.f;
+          red[3][0] = red[4][0] = red[5][0] = 0.f;
+        }
+        g.ox = red[0][0]; g.oy = red[1][0]; g.oz = red[2][0];
+        for (int a = 0; a < 3; a++) ext[a] = (double)red[3 + a][0] - (double)red[a][0];
+      }
+      int d[3];
+      for (int a = 0; a < 3; a++) {
+        double q = ext[a] / edge;
+        d[a] = (q >= 1.0 && q < 1e6) ? (int)floor(q) : 1;
+      }
+      long long limit = n > 0 ? 2LL * n : 1;
+      while ((long long)d[0] * d[1] * d[2] > limit) {
+        int a = (d[0] >= d[1] && d[0] >= d[2]) ? 0 : (d[1] >= d[2] ? 1 : 2);
+        d[a] = d[a] * 3 / 4;
+        if (d[a] < 1) d[a] = 1;
+      }
+      g.dx = d[0]; g.dy = d[1]; g.dz = d[2];
+      g.ix = ext[0] > 0 ? (float)(d[0] / ext[0]) : 0.f;
+      g.iy = ext[1] > 0 ? (float)(d[1] / ext[1]) : 0.f;
+      g.iz = ext[2] > 0 ? (float)(d[2] / ext[2]) : 0.f;
+      grid[m] = g;
+      mol_cells[m] = d[0] * d[1] * d[2];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int axis_cell(float x, float o, float inv, float L, int pbc, int d) {
+  float f;
+  if (pbc) {
+    float xw = x - L * floorf(x / L);
+    f = xw * inv;
+  } else {
+    f = (x - o) * inv;
+  }
+  f = fminf(fmaxf(f, 0.f), (float)(d - 1));
+  return (int)f;
+}
+
+__global__ void k_bin(fnn_system sys, const MolGrid *grid, const int32_t *mol_base, const int32_t *atom_mol,
+                      int32_t *cell_of, int32_t *cell_count) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sys.n_atoms; i += gridDim.x * blockDim.x) {
+    int m = atom_mol[i];
+    if (m < 0) {  // atom outside every structure: inconsistent offsets (posted by k_check_cover)
+      cell_of[i] = -1;
+      continue;
+    }
+    MolGrid g = grid[m];
+    float4 p = pos[i];
+    int cx = axis_cell(p.x, g.ox, g.ix, g.Lx, g.pbc, g.dx);
+    int cy = axis_cell(p.y, g.oy, g.iy, g.Ly, g.pbc, g.dy);
+    int cz = axis_cell(p.z, g.oz, g.iz, g.Lz, g.pbc, g.dz);
+    int c = mol_base[m] + (cz * g.dy + cy) * g.dx + cx;
+    cell_of[i] = c;
+    atomicAdd(&cell_count[c], 1);
+  }
+}
+
+__global__ void k_scatter(int n, const int32_t *cell_of, const int32_t *cell_start, int32_t *cursor,
+                          int32_t *cell_tmp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = cell_of[i];
+    if (c < 0) continue;
+    int k = atomicAdd(&cursor[c], 1);
+    cell_tmp[cell_start[c] + k] = i;
+  }
+}
+
+// one warp per cell: order the cell's atoms by index (rank sort), so traversal order is deterministic
+__global__ void k_sort_cells(const int32_t *meta, const int32_t *cell_start, const int32_t *cell_tmp,
+                             int32_t *cell_atoms) {
+  int lane = threadIdx.x & 31;
+  int ncell = meta[META_CELLS];
+  int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = wg; c < ncell; c += nw) {
+    int s0 = cell_start[c], s1 = cell_start[c + 1];
+    for (int a = s0 + lane; a < s1; a += 32) {
+      int v = cell_tmp[a];
+      int rank = 0;
+      for (int b = s0; b < s1; b++) rank += cell_tmp[b] < v;
+      cell_atoms[s0 + rank] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------- predicate
+struct PredConst {
+  double R2d;   // R*R in double (the membership threshold)
+  float R2f;    // float(R*R)
+  float Rf;
+};
+
+// d2 < R^2 with the float64 semantics of the interface, via a float32 test outside a proven band.
+// The float32 separation carries an absolute per-component error e <= 4u S (u = 2^-24, S the largest
+// magnitude among the coordinates and the image offset); near the threshold the squared distance then
+// errs by at most 2 sqrt(3) e R + 3 e^2 + 4 u R^2.  Twice that bound is the band re-tested in float64.
+__device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, const PredConst &pc, char4 &sh) {
+  float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+  float nx = 0.f, ny = 0.f, nz = 0.f;
+  if (g.pbc) {
+    nx = -rintf(dx / g.Lx);
+    ny = -rintf(dy / g.Ly);
+    nz = -rintf(dz / g.Lz);
+    dx = fmaf(nx, g.Lx, dx);
+    dy = fmaf(ny, g.Ly, dy);
+    dz = fmaf(nz, g.Lz, dz);
+  }
+  sh = make_char4((signed char)nx, (signed char)ny, (signed char)nz, 0);
+  float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float S = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(pj.x))),
+                  fmaxf(fmaxf(fabsf(pj.y), fabsf(pj.z)),
+                        fmaxf(fabsf(nx * g.Lx), fmaxf(fabsf(ny * g.Ly), fabsf(nz * g.Lz)))));
+  const float u = 5.9604645e-8f;
+  float e = 4.f * u * S;
+  float tau = 2.f * (3.4641016f * e * pc.Rf * 1.01f + 3.f * e * e + 4.f * u * pc.R2f) + 1e-30f;
+  if (d2 < pc.R2f - tau) return true;
+  if (d2 > pc.R2f + tau) return false;
+  // exact float64 predicate, rounded to nearest without contraction
+  double rx = __dsub_rn((double)pj.x, (double)pi.x);
+  double ry = __dsub_rn((double)pj.y, (double)pi.y);
+  double rz = __dsub_rn((double)pj.z, (double)pi.z);
+  double ex = __dadd_rn(rx, __dmul_rn((double)nx, (double)g.Lx));
+  double ey = __dadd_rn(ry, __dmul_rn((double)ny, (double)g.Ly));
+  double ez = __dadd_rn(rz, __dmul_rn((double)nz, (double)g.Lz));
+  double D2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return D2 < pc.R2d;
+}
+
+__device__ __forceinline__ int stencil(int c, int d, int pbc, int *out) {
+  if (pbc) {
+    if (d == 1) { out[0] = 0; return 1; }
+    if (d == 2) { out[0] = 0; out[1] = 1; return 2; }
+    out[0] = c == 0 ? d - 1 : c - 1;
+    out[1] = c;
+    out[2] = c == d - 1 ? 0 : c + 1;
+    return 3;
+  }
+  int n = 0;
+  if (c > 0) out[n++] = c - 1;
+  out[n++] = c;
+  if (c + 1 < d) out[n++] = c + 1;
+  return n;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
+                                               const int32_t *atom_mol, const int32_t *cell_of,
+                                               const int32_t *cell_start, const int32_t *cell_atoms,
+                                               PredConst pc, int32_t *counts, const int32_t *row_ptr,
+                                               int32_t *nbr, char4 *shift, int64_t cap, const int32_t *meta) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  int lane = threadIdx.x & 31;
+  unsigned lt = (1u << lane) - 1u;
+  int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_binned = cell_start[meta[META_CELLS]];   // atoms that belong to a structure
+  for (int w = wg; w < n_binned; w += nw) {
+    int i = cell_atoms[w];   // atoms in cell order: neighbouring warps share neighbour cells
+    int m = atom_mol[i];
+    MolGrid g = grid[m];
+    int base = mol_base[m];
+    int cl = cell_of[i] - base;
+    int cx = cl % g.dx, cy = (cl / g.dx) % g.dy, cz = cl / (g.dx * g.dy);
+    int ox[3], oy[3], oz[3];
+    int nox = stencil(cx, g.dx, g.pbc, ox), noy = stencil(cy, g.dy, g.pbc, oy), noz = stencil(cz, g.dz, g.pbc, oz);
+    float4 pi = pos[i];
+    int count = 0;
+    int64_t out = FILL ? (int64_t)row_ptr[i] : 0;
+    for (int a = 0; a < noz; a++)
+      for (int b = 0; b < noy; b++)
+        for (int q = 0; q < nox; q++) {
+          int c = base + (oz[a] * g.dy + oy[b]) * g.dx + ox[q];
+          int s0 = cell_start[c], s1 = cell_start[c + 1];
+          for (int k0 = s0; k0 < s1; k0 += 32) {
+            int k = k0 + lane;
+            bool in = false;
+            int j = -1;
+            char4 sh = make_char4(0, 0, 0, 0);
+            if (k < s1) {
+              j = cell_atoms[k];
+              if (j != i) in = pair_in(pi, pos[j], g, pc, sh);
+            }
+            unsigned mask = __ballot_sync(FULL, in);
+            if (FILL && in) {
+              int64_t idx = out + count + __popc(mask & lt);
+              if (idx < cap) {
+                nbr[idx] = j;
+                shift[idx] = sh;
+              }
+            }
+            count += __popc(mask);
+          }
+        }
+    if (!FILL && lane == 0) counts[i] = count;
+  }
+}
+
+__global__ void k_check_capacity(const int32_t *row_ptr, int n, int64_t cap, int32_t *meta, DevStatus *st) {
+  int64_t nnz = row_ptr[n];
+  meta[META_NNZ] = (int32_t)nnz;
+  if (nnz > cap) post_status(st, FNN_E_CAPACITY, nnz);
+}
+
+// ---------------------------------------------------------------------------- species segments
+constexpr int ELEM_NT = 256;
+
+__global__ void k_elem_count(int n, const uint8_t *elem, int32_t *blk_count) {
+  __shared__ int c[8];
+  if (threadIdx.x < 8) c[threadIdx.x] = 0;
+  __syncthreads();
+  int i = blockIdx.x * ELEM_NT + threadIdx.x;
+  if (i < n) atomicAdd(&c[elem[i]], 1);
+  __syncthreads();
+  if (threadIdx.x < 8) blk_count[blockIdx.x * 8 + threadIdx.x] = c[threadIdx.x];
+}
+
+// single block: per-element exclusive scan over blocks, padded segment starts, tile table
+__global__ void k_elem_scan(int nblk, int32_t *blk_count, int32_t *meta, int32_t *tile_elem, int ntiles_cap) {
+  __shared__ int totals[8];
+  for (int e = 0; e < NE; e++) {
+    int carry = 0;
+    for (int c = 0; c < nblk; c += SCAN_NT) {
+      int k = c + threadIdx.x;
+      int v = k < nblk ? blk_count[k * 8 + e] : 0;
+      int tot;
+      int ex = block_excl_scan<SCAN_NT>(v, &tot);
+      if (k < nblk) blk_count[k * 8 + e] = ex + carry;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) totals[e] = carry;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int e = 0; e < NE; e++) {
+      meta[META_SEG + e] = s;
+      s += (totals[e] + ROW_TILE - 1) / ROW_TILE * ROW_TILE;
+    }
+    meta[META_SEG + NE] = s;
+    meta[META_NPAD] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles_cap; t += blockDim.x) {
+    int r = t * ROW_TILE, e = -1;
+    for (int q = 0; q < NE; q++)
+      if (r >= meta[META_SEG + q] && r < meta[META_SEG + q + 1]) e = q;
+    tile_elem[t] = e;
+  }
+}
+
+__global__ void k_elem_scatter(int n, const uint8_t *elem, const int32_t *blk_off, const int32_t *meta,
+                               int32_t *perm, int32_t *inv) {
+  __shared__ int wcnt[ELEM_NT / 32][8];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int i = blockIdx.x * ELEM_NT + threadIdx.x;
+  int e = i < n ? elem[i] : 7;
+  unsigned lt = (1u << lane) - 1u;
+  int my_rank = 0;
+  for (int q = 0; q < NE; q++) {
+    unsigned mask = __ballot_sync(FULL, e == q);
+    if (lane == 0) wcnt[w][q] = __popc(mask);
+    if (e == q) my_rank = __popc(mask & lt);
+  }
+  __syncthreads();
+  if (i < n) {
+    int before = 0;
+    for (int k = 0; k < w; k++) before += wcnt[k][e];
+    int row = meta[META_SEG + e] + blk_off[blockIdx.x * 8 + e] + before + my_rank;
+    perm[i] = row;
+    inv[row] = i;
+  }
+}
+
+// ------------------------------------------------------------------------------------------ host
+template <typename T>
+static fnn_status grow(fnn_ctx *ctx, T **p, size_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for neighbour-list storage";
+    return FNN_E_OOM;
+  }
+  return FNN_OK;
+}
+
+static fnn_status reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t capacity) {
+  fnn_ctx *ctx = nl->ctx;
+  fnn_status st;
+  if (n_atoms > nl->atom_cap || !nl->perm) {
+    int32_t na = n_atoms > nl->atom_cap ? n_atoms : nl->atom_cap;
+    if ((st = grow(ctx, &nl->row_ptr, (size_t)na + 1)) || (st = grow(ctx, &nl->atom_mol, na)) ||
+        (st = grow(ctx, &nl->elem, na)) || (st = grow(ctx, &nl->cell_of, na)) ||
+        (st = grow(ctx, &nl->cell_tmp, na)) || (st = grow(ctx, &nl->cell_atoms, na)) ||
+        (st = grow(ctx, &nl->counts, (size_t)na + 1)) || (st = grow(ctx, &nl->perm, na)))
+      return st;
+    int32_t pad = (na + ROW_TILE - 1) / ROW_TILE * ROW_TILE + NE * ROW_TILE;
+    int32_t nblk = (na + ELEM_NT - 1) / ELEM_NT + 1;
+    if ((st = grow(ctx, &nl->inv, pad)) || (st = grow(ctx, &nl->tile_elem, pad / ROW_TILE)) ||
+        (st = grow(ctx, &nl->blk_count, (size_t)nblk * 8)))
+      return st;
+    nl->atom_cap = na;
+    nl->pad_cap = pad;
+  }
+  if (n_mol > nl->mol_cap || !nl->grid) {
+    int32_t nm = n_mol > nl->mol_cap ? n_mol : nl->mol_cap;
+    if ((st = grow(ctx, &nl->grid, nm)) || (st = grow(ctx, &nl->mol_cells, (size_t)nm + 1))) return st;
+    nl->mol_cap = nm;
+  }
+  int32_t cells = 2 * nl->atom_cap + nl->mol_cap + 1;
+  if (cells > nl->cell_cap) {
+    if ((st = grow(ctx, &nl->cell_count, (size_t)cells + 1)) || (st = grow(ctx, &nl->cell_start, (size_t)cells + 1)))
+      return st;
+    nl->cell_cap = cells;
+  }
+  int64_t need_tmp = scan_tmp_needed((int64_t)cells + 1);
+  int64_t t2 = scan_tmp_needed((int64_t)nl->atom_cap + 1);
+  int64_t t3 = scan_tmp_needed((int64_t)nl->mol_cap + 1);
+  if (t2 > need_tmp) need_tmp = t2;
+  if (t3 > need_tmp) need_tmp = t3;
+  if (need_tmp > nl->scan_tmp_len) {
+    if ((st = grow(ctx, &nl->scan_tmp, need_tmp))) return st;
+    nl->scan_tmp_len = need_tmp;
+  }
+  if (!nl->meta) {
+    if ((st = grow(ctx, &nl->meta, META_LEN))) return st;
+    cudaMemset(nl->meta, 0, META_LEN * sizeof(int32_t));
+  }
+  if (capacity > nl->capacity) {
+    if ((st = grow(ctx, &nl->nbr, capacity)) || (st = grow(ctx, &nl->shift, capacity))) return st;
+    nl->capacity = capacity;
+  }
+  return FNN_OK;
+}
+
+}  // namespace fnn
+
+using namespace fnn;
+
+extern "C" fnn_status fnn_nlist_create(fnn_ctx *ctx, fnn_nlist **out, int64_t capacity) {
+  if (!ctx || !out || capacity < 0) return FNN_E_INVALID;
+  fnn_nlist *nl = new fnn_nlist();
+  nl->ctx = ctx;
+  if (capacity > 0) {
+    fnn_status st = reserve(nl, 0, 0, capacity);
+    if (st) {
+      fnn_nlist_destroy(nl);
+      return st;
+    }
+  }
+  *out = nl;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_nlist_destroy(fnn_nlist *nl) {
+  if (!nl) return FNN_E_INVALID;
+  void *ptrs[] = {nl->row_ptr, nl->nbr, nl->shift, nl->atom_mol, nl->elem, nl->cell_of, nl->cell_tmp,
+                  nl->cell_atoms, nl->counts, nl->grid, nl->mol_cells, nl->cell_count, nl->cell_start,
+                  nl->perm, nl->inv, nl->tile_elem, nl->blk_count, nl->meta, nl->scan_tmp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete nl;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_nlist_reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t capacity) {
+  if (!nl || n_atoms < 0 || n_mol < 0 || capacity < 0) return FNN_E_INVALID;
+  return reserve(nl, n_atoms, n_mol, capacity);
+}
+
+static fnn_status validate_system(fnn_ctx *ctx, const fnn_system *sys) {
+  if (!sys || sys->n_atoms < 0 || sys->n_mol < 1 || !sys->mol_offsets) {
+    ctx->last_error = "invalid system descriptor";
+    return FNN_E_INVALID;
+  }
+  if (sys->n_atoms > 0 && (!sys->Z || !sys->pos)) {
+    ctx->last_error = "system without species or positions";
+    return FNN_E_INVALID;
+  }
+  if (((uintptr_t)sys->pos & 15) != 0) {
+    ctx->last_error = "positions must be 16-byte aligned float4";
+    return FNN_E_INVALID;
+  }
+  if (sys->pbc && !sys->cell) {
+    ctx->last_error = "pbc flags without cells";
+    return FNN_E_INVALID;
+  }
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, void *stream) {
+  if (!ctx || !nl || nl->ctx != ctx) return FNN_E_INVALID;
+  fnn_status st = validate_system(ctx, sys);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = sys->n_atoms, NM = sys->n_mol;
+  int64_t cap = nl->capacity > 0 ? nl->capacity : (int64_t)160 * (N > 0 ? N : 1) + 1024;
+  if ((st = reserve(nl, N, NM, cap))) return st;
+  const double R = ctx->cfg.rc_rad + ctx->cfg.skin;
+  nl->R = R;
+  nl->n_atoms = N;
+  nl->n_mol = NM;
+  nl->stream = s;
+  nl->built = true;
+
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->meta, 0, META_LEN * sizeof(int32_t), s));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->row_ptr, 0, ((size_t)N + 1) * sizeof(int32_t), s));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->counts, 0, ((size_t)N + 1) * sizeof(int32_t), s));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->mol_cells, 0, ((size_t)NM + 1) * sizeof(int32_t), s));
+  if (N > 0) {
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->elem, 0, (size_t)N, s));
+  }
+  int cover_blocks = (NM + 256) / 256 < 256 ? (NM + 256) / 256 : 256;
+  k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status);
+  int setup_blocks = NM < 4 * ctx->num_sms ? NM : 4 * ctx->num_sms;
+  k_mol_setup<<<setup_blocks, SETUP_NT, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->elem, R,
+                                                ctx->status);
+  if ((st = exclusive_scan(ctx, nl->mol_cells, NM + 1, nl->meta + META_CELLS, nl->scan_tmp, nl->scan_tmp_len, s)))
+    return st;
+  // cells are bounded by 2N + n_mol + 1 by construction (k_mol_setup caps each structure at max(1, 2n))
+  int64_t cells_bound = 2LL * N + NM + 1;
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_start, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+  if (N > 0) {
+    int tb = 256, nb = (N + tb - 1) / tb;
+    k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count);
+    FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->cell_start, nl->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
+                                      cudaMemcpyDeviceToDevice, s));
+    if ((st = exclusive_scan(ctx, nl->cell_start, cells_bound + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
+      return st;
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+    k_scatter<<<nb, tb, 0, s>>>(N, nl->cell_of, nl->cell_start, nl->cell_count, nl->cell_tmp);
+    int wb = (int)((cells_bound * 32 + 255) / 256);
+    if (wb > 16 * ctx->num_sms) wb = 16 * ctx->num_sms;
+    k_sort_cells<<<wb, 256, 0, s>>>(nl->meta, nl->cell_start, nl->cell_tmp, nl->cell_atoms);
+
+    PredConst pc{R * R, (float)(R * R), (float)R};
+    int pb = (int)(((int64_t)N * 32 + 255) / 256);
+    if (pb > 32 * ctx->num_sms) pb = 32 * ctx->num_sms;
+    k_pairs<false><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                      nl->cell_atoms, pc, nl->counts, nullptr, nullptr, nullptr, 0, nl->meta);
+    FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->row_ptr, nl->counts, ((size_t)N + 1) * sizeof(int32_t),
+                                      cudaMemcpyDeviceToDevice, s));
+    if ((st = exclusive_scan(ctx, nl->row_ptr, (int64_t)N + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
+      return st;
+    k_check_capacity<<<1, 1, 0, s>>>(nl->row_ptr, N, nl->capacity, nl->meta, ctx->status);
+    k_pairs<true><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                     nl->cell_atoms, pc, nullptr, nl->row_ptr, nl->nbr, nl->shift, nl->capacity,
+                                     nl->meta);
+  }
+  // species-sorted, 128-row padded order for the networks
+  int nblk = (N + ELEM_NT - 1) / ELEM_NT;
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->inv, 0xff, (size_t)nl->pad_cap * sizeof(int32_t), s));
+  if (nblk > 0) k_elem_count<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count);
+  k_elem_scan<<<1, SCAN_NT, 0, s>>>(nblk, nl->blk_count, nl->meta, nl->tile_elem, nl->pad_cap / ROW_TILE);
+  if (nblk > 0) k_elem_scatter<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count, nl->meta, nl->perm, nl->inv);
+  return check_launch(ctx, "fnn_build_neighbors");
+}
+
+extern "C" fnn_status fnn_nlist_nnz(fnn_nlist *nl, int64_t *nnz) {
+  if (!nl || !nnz) return FNN_E_INVALID;
+  if (!nl->built) {
+    *nnz = 0;
+    return FNN_OK;
+  }
+  int32_t v = 0;
+  FNN_CUDA_TRY(nl->ctx, cudaStreamSynchronize(nl->stream));
+  FNN_CUDA_TRY(nl->ctx, cudaMemcpy(&v, nl->row_ptr + nl->n_atoms, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  *nnz = v;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t *nbr, int8_t *shift, int64_t cap,
+                                       int64_t *nnz) {
+  if (!nl || !nnz) return FNN_E_INVALID;
+  fnn_status st = fnn_nlist_nnz(nl, nnz);
+  if (st) return st;
+  if (*nnz > cap || *nnz > nl->capacity) return FNN_E_CAPACITY;
+  fnn_ctx *ctx = nl->ctx;
+  if (row_ptr)
+    FNN_CUDA_TRY(ctx, cudaMemcpy(row_ptr, nl->row_ptr, ((size_t)nl->n_atoms + 1) * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost));
+  if (nbr && *nnz > 0)
+    FNN_CUDA_TRY(ctx, cudaMemcpy(nbr, nl->nbr, (size_t)*nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (shift && *nnz > 0) {
+    char4 *tmp = (char4 *)malloc((size_t)*nnz * sizeof(char4));
+    if (!tmp) return FNN_E_OOM;
+    cudaError_t e = cudaMemcpy(tmp, nl->shift, (size_t)*nnz * sizeof(char4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      free(tmp);
+      ctx->last_error = cudaGetErrorString(e);
+      return FNN_E_CUDA;
+    }
+    for (int64_t k = 0; k < *nnz; k++) {
+      shift[3 * k] = tmp[k].x;
+      shift[3 * k + 1] = tmp[k].y;
+      shift[3 * k + 2] = tmp[k].z;
+    }
+    free(tmp);
+  }
+  return FNN_OK;
+}

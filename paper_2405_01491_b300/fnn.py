@@ -1,0 +1,290 @@
+"""Thin Python binding of the C ABI in include/fnn.h (argument marshalling only).
+
+Every step of the path runs in libfnn.so's CUDA kernels; torch is used only to
+own device memory and to name the current stream.  Importing this module loads
+the library and raises if it is missing: there is no CPU fallback.
+
+Names follow the C entry points: build_neighbors, nlist_nnz, nlist_export, aev,
+energy_forces, energy_forces_host, sync, load_weights, save_weights.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfnn.so")
+
+FNN_OK, FNN_PENDING = 0, 1
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "E_INVALID", -2: "E_SPECIES", -3: "E_CELL", -4: "E_CAPACITY",
+                -5: "E_OOM", -6: "E_TIMEOUT", -7: "E_NONFINITE", -8: "E_CUDA", -9: "E_STATE"}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+
+class FnnError(RuntimeError):
+    def __init__(self, code: int, msg: str, info: int = 0):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg} (info={info})")
+        self.code = code
+        self.info = info
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("rc_rad", ctypes.c_double), ("rc_ang", ctypes.c_double), ("eta_rad", ctypes.c_double),
+                ("eta_ang", ctypes.c_double), ("zeta", ctypes.c_double), ("shift_rad0", ctypes.c_double),
+                ("shift_ang0", ctypes.c_double), ("skin", ctypes.c_double), ("n_members", ctypes.c_int32)]
+
+
+class CWeights(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in
+                                                   ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")]
+
+
+class CSystem(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("n_mol", ctypes.c_int32), ("mol_offsets", ctypes.c_void_p),
+                ("Z", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("pbc", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2405_01491_b300.build` "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "fnn_config_default": (None, [P]),
+        "fnn_create": (I32, [P, P]),
+        "fnn_destroy": (I32, [P]),
+        "fnn_load_weights": (I32, [P, ctypes.c_char_p, P]),
+        "fnn_nlist_create": (I32, [P, P, I64]),
+        "fnn_nlist_destroy": (I32, [P]),
+        "fnn_nlist_reserve": (I32, [P, I32, I32, I64]),
+        "fnn_build_neighbors": (I32, [P, P, P, P]),
+        "fnn_nlist_nnz": (I32, [P, P]),
+        "fnn_nlist_export": (I32, [P, P, P, P, I64, P]),
+        "fnn_aev": (I32, [P, P, P, P, P]),
+        "fnn_energy_forces": (I32, [P, P, P, I32, P, P, P, P]),
+        "fnn_energy_forces_host": (I32, [P, I32, I32, P, P, P, P, P, I32, P, P, P, P]),
+        "fnn_sync": (I32, [P, P, P]),
+        "fnn_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """fnn_ctx: constants, ensemble size, device parameters and workspaces."""
+
+    def __init__(self, n_members: int = 1, skin: float = 0.0, **overrides):
+        cfg = Config()
+        lib.fnn_config_default(ctypes.byref(cfg))
+        cfg.n_members = n_members
+        cfg.skin = skin
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.h = None
+        h = ctypes.c_void_p()
+        code = lib.fnn_create(ctypes.byref(h), ctypes.byref(cfg))
+        if code != FNN_OK:
+            raise FnnError(code, "fnn_create")
+        self.h = h
+
+    def _check(self, code, what):
+        if code != FNN_OK:
+            raise FnnError(code, f"{what}: {lib.fnn_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def load_weights(ctx: Context, weights=None, path: str | None = None):
+    """fnn_load_weights from a synth.Weights-like object (float32 arrays) or a file."""
+    if path is not None:
+        ctx._check(lib.fnn_load_weights(ctx.h, path.encode(), None), "fnn_load_weights")
+        return
+    arrs = [np.ascontiguousarray(getattr(weights, k), np.float32) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")]
+    cw = CWeights(int(arrs[0].shape[0]), *(a.ctypes.data for a in arrs))
+    ctx._check(lib.fnn_load_weights(ctx.h, None, ctypes.byref(cw)), "fnn_load_weights")
+
+
+def save_weights(path: str, weights):
+    """Write the flat weight file fnn_load_weights reads ("FNNW", version 1, M, eight float32 arrays)."""
+    arrs = [np.ascontiguousarray(getattr(weights, k), np.float32) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")]
+    with open(path, "wb") as f:
+        f.write(b"FNNW" + struct.pack("<ii", 1, int(arrs[0].shape[0])))
+        for a in arrs:
+            f.write(a.astype("<f4").tobytes())
+
+
+@dataclass
+class DeviceSystem:
+    """Device copies of a structure batch in the layout of fnn_system (positions as float4)."""
+    n_atoms: int
+    n_mol: int
+    mol_offsets: object
+    Z: object
+    pos: object
+    cell: object
+    pbc: object
+
+    @classmethod
+    def from_structures(cls, s, device="cuda"):
+        import torch
+        pos4 = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+        pos4[:, :3] = torch.from_numpy(np.asarray(s.pos, np.float32))
+        periodic = bool(np.any(s.pbc))
+        return cls(s.n_atoms, s.n_mol,
+                   torch.from_numpy(np.asarray(s.mol_offsets, np.int32)).to(device),
+                   torch.from_numpy(np.asarray(s.Z, np.int32)).to(device),
+                   pos4.to(device),
+                   torch.from_numpy(np.asarray(s.cell, np.float32).reshape(-1, 9)).to(device) if periodic else None,
+                   torch.from_numpy(np.asarray(s.pbc, np.uint8)).to(device) if periodic else None)
+
+    def c(self):
+        return CSystem(self.n_atoms, self.n_mol, self.mol_offsets.data_ptr(), self.Z.data_ptr(),
+                       self.pos.data_ptr(), self.cell.data_ptr() if self.cell is not None else None,
+                       self.pbc.data_ptr() if self.pbc is not None else None)
+
+
+class NeighborList:
+    """fnn_nlist handle."""
+
+    def __init__(self, ctx: Context, capacity: int = 0):
+        self.ctx = ctx
+        self.h = None
+        h = ctypes.c_void_p()
+        ctx._check(lib.fnn_nlist_create(ctx.h, ctypes.byref(h), int(capacity)), "fnn_nlist_create")
+        self.h = h
+
+    def reserve(self, n_atoms: int, n_mol: int, capacity: int):
+        self.ctx._check(lib.fnn_nlist_reserve(self.h, n_atoms, n_mol, int(capacity)), "fnn_nlist_reserve")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fnn_nlist_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sync(ctx: Context, stream=None):
+    """fnn_sync: (status code, info); clears the sticky status."""
+    info = ctypes.c_int64(0)
+    code = lib.fnn_sync(ctx.h, _stream(stream), ctypes.byref(info))
+    return code, info.value
+
+
+def check(ctx: Context, what: str = "device status", stream=None):
+    code, info = sync(ctx, stream)
+    if code != FNN_OK:
+        raise FnnError(code, f"{what}: {lib.fnn_last_error(ctx.h).decode()}", info)
+
+
+def build_neighbors(ctx: Context, system: DeviceSystem, nl: NeighborList, stream=None, checked: bool = False):
+    """fnn_build_neighbors; with checked=True synchronise, and on overflow grow the list and rebuild once."""
+    cs = system.c()
+    ctx._check(lib.fnn_build_neighbors(ctx.h, ctypes.byref(cs), nl.h, _stream(stream)), "fnn_build_neighbors")
+    if checked:
+        code, info = sync(ctx, stream)
+        if code == -4 and info > 0:
+            nl.reserve(system.n_atoms, system.n_mol, info + info // 4)
+            ctx._check(lib.fnn_build_neighbors(ctx.h, ctypes.byref(cs), nl.h, _stream(stream)), "fnn_build_neighbors")
+            code, info = sync(ctx, stream)
+        if code != FNN_OK:
+            raise FnnError(code, "fnn_build_neighbors", info)
+
+
+def nlist_nnz(nl: NeighborList) -> int:
+    n = ctypes.c_int64(0)
+    nl.ctx._check(lib.fnn_nlist_nnz(nl.h, ctypes.byref(n)), "fnn_nlist_nnz")
+    return n.value
+
+
+def nlist_export(nl: NeighborList, n_atoms: int):
+    """CSR copy of the list on the host: row_ptr [N+1], nbr [nnz], shift [nnz, 3] (int8)."""
+    nnz = nlist_nnz(nl)
+    row_ptr = np.zeros(n_atoms + 1, np.int32)
+    nbr = np.zeros(max(nnz, 1), np.int32)
+    shift = np.zeros((max(nnz, 1), 3), np.int8)
+    got = ctypes.c_int64(0)
+    nl.ctx._check(lib.fnn_nlist_export(nl.h, row_ptr.ctypes.data, nbr.ctypes.data, shift.ctypes.data, max(nnz, 1),
+                                       ctypes.byref(got)), "fnn_nlist_export")
+    return row_ptr, nbr[:nnz], shift[:nnz]
+
+
+def aev(ctx: Context, system: DeviceSystem, nl: NeighborList, out=None, stream=None):
+    """fnn_aev into a float32 device tensor [N, 1008]."""
+    import torch
+    if out is None:
+        out = torch.empty((system.n_atoms, 1008), dtype=torch.float32, device="cuda")
+    cs = system.c()
+    ctx._check(lib.fnn_aev(ctx.h, ctypes.byref(cs), nl.h, _ptr(out), _stream(stream)), "fnn_aev")
+    return out
+
+
+def energy_forces(ctx: Context, system: DeviceSystem, nl: NeighborList, precision: str = "fp32", virial: bool = True,
+                  out=None, stream=None):
+    """fnn_energy_forces: (E [n_mol] float64, F [N,3] float32, virial [n_mol,3,3] float64 or None)."""
+    import torch
+    if out is None:
+        E = torch.empty(system.n_mol, dtype=torch.float64, device="cuda")
+        F = torch.empty((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+        W = torch.empty((system.n_mol, 3, 3), dtype=torch.float64, device="cuda") if virial else None
+    else:
+        E, F, W = out
+    cs = system.c()
+    ctx._check(lib.fnn_energy_forces(ctx.h, ctypes.byref(cs), nl.h, PRECISION[precision], _ptr(E), _ptr(F), _ptr(W),
+                                     _stream(stream)), "fnn_energy_forces")
+    return E, F, W
+
+
+def energy_forces_host(ctx: Context, s, precision: str = "fp32", virial: bool = True, stream=None, out=None):
+    """fnn_energy_forces_host from host arrays (numpy); returns host (E, F, virial)."""
+    Z = np.ascontiguousarray(s.Z, np.int32)
+    pos = np.ascontiguousarray(s.pos, np.float32)
+    mo = np.ascontiguousarray(s.mol_offsets, np.int32)
+    periodic = bool(np.any(s.pbc))
+    cell = np.ascontiguousarray(s.cell, np.float32) if periodic else None
+    pbc = np.ascontiguousarray(s.pbc, np.uint8) if periodic else None
+    if out is None:
+        out = (np.zeros(s.n_mol), np.zeros((s.n_atoms, 3), np.float32), np.zeros((s.n_mol, 3, 3)) if virial else None)
+    E, F, W = out
+    code = lib.fnn_energy_forces_host(ctx.h, s.n_atoms, s.n_mol, mo.ctypes.data, Z.ctypes.data, pos.ctypes.data,
+                                      None if cell is None else cell.ctypes.data,
+                                      None if pbc is None else pbc.ctypes.data, PRECISION[precision],
+                                      E.ctypes.data, F.ctypes.data, None if W is None else W.ctypes.data,
+                                      _stream(stream))
+    ctx._check(code, "fnn_energy_forces_host")
+    return E, F, W

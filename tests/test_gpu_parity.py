@@ -1,0 +1,176 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Neighbour lists: bit-exact (same set of (i, j, shift)).  AEVs: float32 against float64,
+|d| <= 2e-5 * max|AEV| + 1e-6.  Energies and forces of the FP32 form: |dE| / n_atoms(mol)
+<= 1e-4 kcal/mol and max |dF| <= 1e-3 kcal/mol/A (the stated FP32 tolerances).
+Virials: 1e-4 of the largest entry (at least 1)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01491_b300 import synth
+from conftest import structure, weights
+
+pytestmark = pytest.mark.gpu
+
+E_TOL_PER_ATOM = 1e-4
+F_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def fnn():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2405_01491_b300 import fnn as f
+    return f
+
+
+def gpu_list(fnn, s, skin=0.0):
+    ctx = fnn.Context(1, skin=skin)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    row_ptr, nbr, shift = fnn.nlist_export(nl, s.n_atoms)
+    ei = np.repeat(np.arange(s.n_atoms), np.diff(row_ptr))
+    return ctx, ds, nl, (ei, nbr, shift)
+
+
+def as_set(ei, ej, es):
+    return set(zip(ei.tolist(), ej.tolist(), map(tuple, es.tolist())))
+
+
+@pytest.mark.parametrize("name,skin", [("gas24", 0.0), ("water216", 1.0), ("box300", 0.0), ("box1500", 1.0),
+                                       ("batch64", 0.0), ("mix23558", 0.0), ("mix23558", 1.0)])
+def test_neighbor_list_bit_exact(fnn, name, skin):
+    s = structure(name)
+    _, _, _, got = gpu_list(fnn, s, skin)
+    want = oracle.neighbors(s, 5.1 + skin)
+    assert len(got[0]) == len(want[0])
+    assert as_set(*got) == as_set(*want)
+
+
+def test_neighbor_edge_cases(fnn):
+    rng = np.random.default_rng(3)
+    parts = []
+    # empty structure, single atom, two atoms on one axis (zero extent on two axes)
+    parts.append(synth.Structures(np.zeros(0, np.int32), np.zeros((0, 3), np.float32), np.array([0, 0], np.int32),
+                                  np.zeros((1, 9), np.float32), np.zeros(1, np.uint8)))
+    parts.append(synth.Structures(np.array([6], np.int32), np.zeros((1, 3), np.float32), np.array([0, 1], np.int32),
+                                  np.zeros((1, 9), np.float32), np.zeros(1, np.uint8)))
+    parts.append(synth.Structures(np.array([1, 8], np.int32), np.array([[0, 0, 0], [0, 0, 4.0]], np.float32),
+                                  np.array([0, 2], np.int32), np.zeros((1, 9), np.float32), np.zeros(1, np.uint8)))
+    # small periodic box (L = 11.4 A: 2 cells per axis); some atoms outside the primary cell
+    small = synth.random_molecule(rng, 150, periodic=True)
+    small.pos[::4] += np.float32(small.cell[0, 0]) * np.array([1, -2, 0], np.float32)
+    parts.append(small)
+    # sparse gas cluster spread far apart (the cell budget clamps the grid)
+    far = synth.random_molecule(rng, 40)
+    far.pos *= np.float32(25.0)
+    parts.append(far)
+    # pairs placed at r = 5.1 give or take one float32 ulp of the coordinates (predicate band)
+    x = np.array([[10.0, 10.0, 10.0], [15.1, 10.0, 10.0], [10.0, 15.100001, 10.0], [10.0, 10.0, 15.099999]], np.float32)
+    parts.append(synth.Structures(np.array([6, 6, 1, 8], np.int32), x, np.array([0, 4], np.int32),
+                                  np.zeros((1, 9), np.float32), np.zeros(1, np.uint8)))
+    b = synth.concat(parts)
+    _, _, _, got = gpu_list(fnn, b)
+    want = oracle.neighbors(b, 5.1)
+    assert as_set(*got) == as_set(*want)
+
+
+def test_status_codes(fnn):
+    s = structure("box300")
+    ctx = fnn.Context(1)
+    # species outside the table
+    bad = synth.Structures(s.Z.copy(), s.pos, s.mol_offsets, s.cell, s.pbc)
+    bad.Z[7] = 26
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(bad), nl)
+    assert fnn.sync(ctx) == (-2, 7)
+    # cell edge <= 2 (rc + skin)
+    cell = np.zeros((1, 9), np.float32)
+    cell[0, [0, 4, 8]] = 10.0
+    tiny = synth.Structures(s.Z, s.pos, s.mol_offsets, cell, s.pbc)
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(tiny), nl)
+    assert fnn.sync(ctx)[0] == -3
+    # capacity overflow reports the entries needed
+    nl2 = fnn.NeighborList(ctx, capacity=100)
+    ds = fnn.DeviceSystem.from_structures(s)
+    fnn.build_neighbors(ctx, ds, nl2)
+    code, info = fnn.sync(ctx)
+    assert code == -4 and info == len(oracle.neighbors(s, 5.1)[0])
+    assert fnn.sync(ctx) == (0, 0)   # cleared
+    # offsets that leave atoms outside every structure
+    short = synth.Structures(s.Z, s.pos, np.array([0, s.n_atoms - 5], np.int32), s.cell, s.pbc)
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(short), nl)
+    assert fnn.sync(ctx)[0] == -1
+
+
+@pytest.mark.parametrize("name", ["gas24", "water216", "box300", "batch64"])
+def test_aev_parity(fnn, name):
+    s = structure(name)
+    ctx, ds, nl, _ = gpu_list(fnn, s, skin=0.5)
+    A = fnn.aev(ctx, ds, nl).cpu().numpy()
+    fnn.check(ctx)
+    want = oracle.aev(s)
+    tol = 2e-5 * np.abs(want).max() + 1e-6
+    assert np.abs(A - want).max() <= tol
+
+
+def _energy_case(fnn, s, M, skin=0.0, precision="fp32"):
+    w = weights(M)
+    ctx = fnn.Context(M, skin=skin)
+    fnn.load_weights(ctx, w)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    E, F, W = fnn.energy_forces(ctx, ds, nl, precision)
+    fnn.check(ctx)
+    return ctx, ds, nl, E.cpu().numpy(), F.cpu().numpy(), W.cpu().numpy()
+
+
+def _compare(s, r, E, F, W):
+    n_mol_atoms = np.maximum(np.diff(s.mol_offsets), 1)
+    dE = np.abs(E - r.energy) / n_mol_atoms
+    dF = np.abs(F - r.forces).max() if s.n_atoms else 0.0
+    assert dE.max() <= E_TOL_PER_ATOM, dE.max()
+    assert dF <= F_TOL, dF
+    scale = max(1.0, np.abs(r.virial).max())
+    assert np.abs(W.reshape(r.virial.shape) - r.virial).max() <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("name,M,skin", [("gas24", 1, 0.0), ("water216", 8, 1.0), ("box1500", 2, 0.0),
+                                         ("batch64", 1, 0.5)])
+def test_energy_forces_fp32_parity(fnn, name, M, skin):
+    s = structure(name)
+    _, _, _, E, F, W = _energy_case(fnn, s, M, skin)
+    r = oracle.energy_forces(s, weights(M))
+    _compare(s, r, E, F, W)
+
+
+def test_energy_forces_fp32_full_size(fnn):
+    """The 23,558-atom periodic box with the 8-member ensemble, in the launch configuration the benchmark times."""
+    s = structure("mix23558")
+    _, _, _, E, F, W = _energy_case(fnn, s, 8)
+    r = oracle.energy_forces(s, weights(8))
+    _compare(s, r, E, F, W)
+
+
+def test_host_entry_point_matches_device_path(fnn):
+    s = structure("batch64")
+    ctx, ds, nl, E, F, W = _energy_case(fnn, s, 1)
+    Eh, Fh, Wh = fnn.energy_forces_host(ctx, s, "fp32")
+    np.testing.assert_allclose(Eh, E, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(Fh, F, rtol=0, atol=1e-5)
+
+
+def test_neighbor_list_deterministic(fnn):
+    s = structure("box1500")
+    ctx = fnn.Context(1)
+    ds = fnn.DeviceSystem.from_structures(s)
+    outs = []
+    for _ in range(2):
+        nl = fnn.NeighborList(ctx)
+        fnn.build_neighbors(ctx, ds, nl, checked=True)
+        outs.append(fnn.nlist_export(nl, s.n_atoms))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
