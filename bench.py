@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark: energy + forces of the 23,558-atom periodic box (8-member ensemble) on B300.
+
+One step = rebuild the neighbour list (cell lists) + AEVs + the per-element networks
+(forward and input gradient) + float64 energy/virial reductions + the AEV adjoint (forces),
+all through the C ABI on inputs already resident in HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|fp8]
+    python bench.py --impl reference ...   # the float64 CPU oracle on host cores
+
+Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own replica of the box
+(replicas only, no data-path collective); value = atoms of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy+force atom-evals/s (23.6k-atom box, FP32 vs BF16); serve p50/p99 ms"
+UNIT = "atom-evals/s"
+WORKLOAD = ("mix23558: 23,558-atom periodic box, 62.2 A cube, H/C/N/O/S = .50/.30/.08/.10/.02, d_min 0.95 A, "
+            "seed 3; 8-member random-init ensemble (seeded Xavier); neighbour list rebuilt every step (skin 0)")
+FFMA_LANES_PER_SM = 128          # FP32 FMA lanes per SM
+N_SM = 148
+L2_FLUSH_BYTES = 256 << 20       # larger than the 126 MB L2
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "sm_max_mhz": d.get("sm_max_mhz", 2032.0), "src": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0,
+            "src": "fallback"}
+
+
+def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
+    """Algorithmic work of one launch of a kernel: (bound, amount, unit) or None."""
+    if name == "aev_forward":       # positions once, list entries (index + shift), the AEV row written
+        return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B"
+    if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
+        return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
+    gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
+    m = re.match(r"(f32|bf16|fp8)_(l[123])_(fwd|bwd)", name)
+    if m:
+        flops = 2.0 * gemm[m.group(2)] * M * n_atoms
+        return ("alu" if m.group(1) == "f32" else "tensor"), flops, "FLOP"
+    if name in ("pairs_count", "pairs_fill"):
+        return "hbm", n_atoms * 16 + (nnz * 8 if name == "pairs_fill" else 0), "B"
+    return None
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2405_01491_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, digest: str):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[3] == digest:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) == 7 and c[0].replace(".", "").isdigit():
+                rows.append(c)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(float(r[0]) for r in rows), "sm_max_mhz": float(rows[0][1]),
+                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit()) if rows else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_baseline(n_sample: int = 2500, M: int = 8):
+    """The float64 oracle, as it stands, on a periodic box cut from the same recipe (host cores)."""
+    import oracle
+    from paper_2405_01491_b300 import synth
+    s = synth.mix_box(n_sample, (n_sample / 0.1) ** (1 / 3), seed=3)
+    w = synth.xavier_weights(M)
+    t = time.perf_counter()
+    oracle.energy_forces(s, w)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one energy+force evaluation of a {n_sample}-atom periodic box at the same density and "
+                      f"composition, M={M}, float64 (oracle neighbour search is all-pairs), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_sample = 1500
+    times = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(n_sample)
+        if k >= args.warmup:
+            times.append(n_sample / r["value"])
+        base = r
+    v = n_sample / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_atoms": n_sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": f"each step: energy+forces of a {n_sample}-atom periodic box cut from the "
+                                       "same recipe (density 0.1, same composition), M=8, float64"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fnn", choices=["fnn", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2405_01491_b300 import fnn, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    M = 8
+    s = synth.mix23558()
+    w = synth.xavier_weights(M)
+    ctx = fnn.Context(M)
+    fnn.load_weights(ctx, w)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    nnz = fnn.nlist_nnz(nl)
+    E = torch.empty(s.n_mol, dtype=torch.float64, device="cuda")
+    F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    Wv = torch.empty((s.n_mol, 3, 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fnn.build_neighbors(ctx, ds, nl)
+        fnn.energy_forces(ctx, ds, nl, args.precision, out=(E, F, Wv))
+
+    for _ in range(args.warmup):
+        step()
+    fnn.check(ctx, "warm-up")
+
+    # timed region: per-step CUDA events on the launching stream; the L2 flush sits between the events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fnn.profile_read(ctx)
+    fnn.profile_enable(ctx, True)
+    launches0 = fnn.launch_count(ctx)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = fnn.launch_count(ctx) - launches0
+    fnn.profile_enable(ctx, False)
+    prof = fnn.profile_read(ctx)
+    fnn.check(ctx, "timed steps")
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    ms_max = float(t_rank.item())
+    value = world * s.n_atoms / (ms_max * 1e-3)
+
+    # per-kernel work and the roofline of the dominant kernel
+    pk = peaks()
+    ffma_peak = N_SM * FFMA_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    digest = source_digest()
+    kernels = {}
+    for name, (tot_ms, n) in prof.items():
+        entry = {"ms_per_launch": tot_ms / n, "launches_per_step": n / args.steps, "share": None}
+        wk = kernel_work(name, s.n_atoms, nnz, M)
+        if wk:
+            bound, amount, u = wk
+            t = tot_ms / n * 1e-3
+            if u == "B":
+                entry.update(bound=bound, achieved=amount / t / 1e9, unit="GB/s", peak=pk["hbm_gbs"])
+            else:
+                peak = ffma_peak if bound == "alu" else pk["bf16_tflops_sustained"] * (2 if args.precision == "fp8" else 1)
+                entry.update(bound=bound, achieved=amount / t / 1e12, unit="TFLOP/s", peak=peak)
+            entry["frac"] = entry["achieved"] / entry["peak"]
+        kernels[name] = entry
+    total_k = sum(v[0] for v in prof.values())
+    for name in kernels:
+        kernels[name]["share"] = prof[name][0] / total_k if total_k else None
+    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: prof[k][0])
+    d = kernels[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"], "traffic": recorded_traffic(dom, digest),
+            "peak_src": (pk["src"] if d["bound"] != "alu" else
+                         f"FP32 FFMA: {N_SM} SMs x {FFMA_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz")}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hs = synth.Structures(pin(s.Z), pin(s.pos), pin(s.mol_offsets), pin(s.cell), pin(s.pbc), s.name)
+    hout = (pin(np.zeros(s.n_mol)), pin(np.zeros((s.n_atoms, 3), np.float32)), pin(np.zeros((s.n_mol, 3, 3))))
+    for _ in range(max(1, args.warmup)):
+        fnn.energy_forces_host(ctx, hs, args.precision, out=hout)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fnn.energy_forces_host(ctx, hs, args.precision, out=hout)
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    h2d = s.n_atoms * (4 + 12) + (s.n_mol + 1) * 4 + s.n_mol * (36 + 1)
+    d2h = s.n_mol * 8 + s.n_atoms * 12 + s.n_mol * 72
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "members": M, "precision": args.precision,
+                       "list_entries": nnz, "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step (256 MB write outside the step's CUDA events)"},
+            "roofline": roof, "gpu_launches": int(launches),
+            "e2e": {"value": world * s.n_atoms / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk.summary(), "kernels": kernels, "source_digest": digest}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,17 @@ fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t n_atoms, int32_t n_mol, 
  * offending atom for FNN_E_SPECIES, ...). */
 fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
 
+/* Instrumentation (no counterpart in the paper; the tracing the benchmark reads).
+ * fnn_profile_enable: while on, every kernel this context launches is bracketed
+ * by CUDA events on its own stream (a few microseconds of host work per launch).
+ * fnn_profile_read: synchronises the device, then returns per kernel name
+ * (names: cap x 48 chars) the summed device milliseconds and launch counts
+ * since the previous read; *count = number of distinct kernels.
+ * fnn_launch_count: kernels launched by this context since creation. */
+fnn_status fnn_profile_enable(fnn_ctx *ctx, int on);
+fnn_status fnn_profile_read(fnn_ctx *ctx, char *names, double *ms, int64_t *launches, int32_t cap, int32_t *count);
+fnn_status fnn_launch_count(const fnn_ctx *ctx, int64_t *n);
+
 /* Text of the last host-side error of this context (never NULL). */
 const char *fnn_last_error(const fnn_ctx *ctx);
 

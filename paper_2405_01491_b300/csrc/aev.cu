@@ -465,7 +465,10 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   a.st = ctx->status;
   int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
   if (rows == 0) return FNN_OK;
-  k_aev_forward<float><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  {
+    FNN_KERNEL(ctx, "aev_forward", s);
+    k_aev_forward<float><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  }
   return check_launch(ctx, "aev_forward");
 }
 
@@ -483,7 +486,10 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   a.st = ctx->status;
   int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
   if (rows == 0) return FNN_OK;
-  k_aev_adjoint<<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  {
+    FNN_KERNEL(ctx, "aev_adjoint", s);
+    k_aev_adjoint<<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  }
   return check_launch(ctx, "aev_adjoint");
 }
 

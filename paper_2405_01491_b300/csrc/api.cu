@@ -17,6 +17,31 @@ fnn_status check_launch(fnn_ctx *ctx, const char *what) {
   return FNN_OK;
 }
 
+static cudaEvent_t take_event(Profiler &P) {
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+KScope::KScope(fnn_ctx *c, const char *name, cudaStream_t st) : ctx(c), s(st) {
+  ctx->prof.launches++;
+  if (ctx->prof.on) {
+    Profiler::Rec r{name, take_event(ctx->prof), take_event(ctx->prof)};
+    cudaEventRecord(r.a, s);
+    idx = (int)ctx->prof.recs.size();
+    ctx->prof.recs.push_back(r);
+  }
+}
+
+KScope::~KScope() {
+  if (idx >= 0) cudaEventRecord(ctx->prof.recs[idx].b, s);
+}
+
 template <typename T>
 static fnn_status dalloc(fnn_ctx *ctx, T **p, size_t count) {
   if (*p) cudaFree(*p);
@@ -144,6 +169,11 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
     if (p) cudaFree(p);
   if (h.nl) fnn_nlist_destroy(h.nl);
   if (ctx->status) cudaFree(ctx->status);
+  for (auto &r : ctx->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   delete ctx;
   return FNN_OK;
 }
@@ -291,6 +321,7 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(h.Z, Z, (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(h.pos3, pos, (size_t)N * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
     int nb = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
+    FNN_KERNEL(ctx, "pack_pos", s);
     k_pack_pos<<<nb, 256, 0, s>>>(N, h.pos3, (float4 *)h.pos);
   }
   if (pbc) {
@@ -312,6 +343,53 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
     return fnn_energy_forces_host(ctx, N, NM, mol_offsets, Z, pos, cell, pbc, prec, E, F, virial, stream);
   }
   return st;
+}
+
+extern "C" fnn_status fnn_profile_enable(fnn_ctx *ctx, int on) {
+  if (!ctx) return FNN_E_INVALID;
+  ctx->prof.on = on != 0;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_profile_read(fnn_ctx *ctx, char *names, double *ms, int64_t *launches, int32_t cap,
+                                       int32_t *count) {
+  if (!ctx || !count) return FNN_E_INVALID;
+  FNN_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  std::vector<std::string> keys;
+  std::vector<double> tot;
+  std::vector<int64_t> n;
+  for (auto &r : ctx->prof.recs) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    size_t k = 0;
+    while (k < keys.size() && keys[k] != r.name) k++;
+    if (k == keys.size()) {
+      keys.push_back(r.name);
+      tot.push_back(0.0);
+      n.push_back(0);
+    }
+    tot[k] += t;
+    n[k] += 1;
+    ctx->prof.pool.push_back(r.a);
+    ctx->prof.pool.push_back(r.b);
+  }
+  ctx->prof.recs.clear();
+  *count = (int32_t)keys.size();
+  for (int32_t k = 0; k < *count && k < cap; k++) {
+    if (names) {
+      strncpy(names + 48 * k, keys[k].c_str(), 47);
+      names[48 * k + 47] = 0;
+    }
+    if (ms) ms[k] = tot[k];
+    if (launches) launches[k] = n[k];
+  }
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_launch_count(const fnn_ctx *ctx, int64_t *n) {
+  if (!ctx || !n) return FNN_E_INVALID;
+  *n = ctx->prof.launches;
+  return FNN_OK;
 }
 
 extern "C" fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info) {

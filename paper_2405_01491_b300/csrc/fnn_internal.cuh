@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fnn.h"
 
@@ -107,7 +108,22 @@ struct Workspace {
 
 }  // namespace fnn
 
+namespace fnn {
+// Kernel timing: when enabled, each launch is bracketed by CUDA events on its stream.
+struct Profiler {
+  struct Rec {
+    const char *name;
+    cudaEvent_t a, b;
+  };
+  bool on = false;
+  long long launches = 0;        // every kernel this context launched (always counted)
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+}  // namespace fnn
+
 struct fnn_ctx {
+  fnn::Profiler prof;
   fnn_config cfg;
   fnn::AevParams aev;
   int device = 0;
@@ -180,6 +196,18 @@ enum { META_CELLS = 0, META_NNZ = 1, META_NPAD = 2, META_SEG = 4 /* [8] segment 
   } while (0)
 
 fnn_status check_launch(fnn_ctx *ctx, const char *what);
+
+// Scope around one kernel launch: counts it and, when profiling, records events around it.
+struct KScope {
+  fnn_ctx *ctx;
+  cudaStream_t s;
+  int idx = -1;
+  KScope(fnn_ctx *c, const char *name, cudaStream_t st);
+  ~KScope();
+};
+#define FNN_CAT2(a, b) a##b
+#define FNN_CAT(a, b) FNN_CAT2(a, b)
+#define FNN_KERNEL(ctx, name, s) ::fnn::KScope FNN_CAT(kscope_, __LINE__)(ctx, name, s)
 
 // exclusive scan of n int32 values in place; total written to *total_dev (device) when non-null
 fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,

@@ -148,8 +148,9 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
 }
 
 template <int EPI>
-static void launch(const GemmP &p, int row_tiles, int members, cudaStream_t s) {
+static void launch(fnn_ctx *ctx, const char *name, const GemmP &p, int row_tiles, int members, cudaStream_t s) {
   dim3 grid((p.N + BN - 1) / BN, row_tiles, members);
+  FNN_KERNEL(ctx, name, s);
   k_gemm_f32<EPI><<<grid, GNT, 0, s>>>(p);
 }
 
@@ -167,14 +168,14 @@ fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStre
   p.C = ws.h1; p.ldc = (long long)M * H1; p.c_mstride = 0;
   p.N = M * H1; p.K = NAEV;
   p.bias = w.b1cat; p.bias_estride = (long long)M * H1; p.bias_mstride = 0;
-  launch<EPI_BIAS_CELU>(p, tiles, 1, s);
+  launch<EPI_BIAS_CELU>(ctx, "f32_l1_fwd", p, tiles, 1, s);
   // L2
   p.A = ws.h1; p.lda = (long long)M * H1; p.a_mstride = H1;
   p.B = w.W2; p.ldb = H1; p.b_estride = (long long)H2 * H1; p.b_mstride = (long long)NE * H2 * H1;
   p.C = ws.h2; p.ldc = (long long)M * H2; p.c_mstride = H2;
   p.N = H2; p.K = H1;
   p.bias = w.b2; p.bias_estride = H2; p.bias_mstride = (long long)NE * H2;
-  launch<EPI_BIAS_CELU>(p, tiles, M, s);
+  launch<EPI_BIAS_CELU>(ctx, "f32_l2_fwd", p, tiles, M, s);
   // L3 + output layer + g3
   p.A = ws.h2; p.lda = (long long)M * H2; p.a_mstride = H2;
   p.B = w.W3; p.ldb = H2; p.b_estride = (long long)H3 * H2; p.b_mstride = (long long)NE * H3 * H2;
@@ -184,28 +185,28 @@ fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStre
   p.w4 = w.w4; p.w4_estride = H3; p.w4_mstride = (long long)NE * H3;
   p.ypart = ws.ypart;
   p.scale = 1.f / (float)M;
-  launch<EPI_L3>(p, tiles, M, s);
+  launch<EPI_L3>(ctx, "f32_l3_fwd", p, tiles, M, s);
   // L3 backward
   p.A = ws.g3; p.lda = (long long)M * H3; p.a_mstride = H3;
   p.B = w.W3T; p.ldb = H3; p.b_estride = (long long)H2 * H3; p.b_mstride = (long long)NE * H2 * H3;
   p.C = ws.g2; p.ldc = (long long)M * H2; p.c_mstride = H2;
   p.N = H2; p.K = H3;
   p.aux = ws.h2; p.ldaux = (long long)M * H2; p.aux_mstride = H2;
-  launch<EPI_DCELU>(p, tiles, M, s);
+  launch<EPI_DCELU>(ctx, "f32_l3_bwd", p, tiles, M, s);
   // L2 backward
   p.A = ws.g2; p.lda = (long long)M * H2; p.a_mstride = H2;
   p.B = w.W2T; p.ldb = H2; p.b_estride = (long long)H1 * H2; p.b_mstride = (long long)NE * H1 * H2;
   p.C = ws.g1; p.ldc = (long long)M * H1; p.c_mstride = H1;
   p.N = H1; p.K = H2;
   p.aux = ws.h1; p.ldaux = (long long)M * H1; p.aux_mstride = H1;
-  launch<EPI_DCELU>(p, tiles, M, s);
+  launch<EPI_DCELU>(ctx, "f32_l2_bwd", p, tiles, M, s);
   // L1 backward: dE/dAEV, K = M*256 sums the members
   p.A = ws.g1; p.lda = (long long)M * H1; p.a_mstride = 0;
   p.B = w.W1Tcat; p.ldb = (long long)M * H1; p.b_estride = (long long)NAEV * M * H1; p.b_mstride = 0;
   p.C = ws.gaev; p.ldc = NAEV; p.c_mstride = 0;
   p.N = NAEV; p.K = M * H1;
   p.scale = 1.f;
-  launch<EPI_SCALE>(p, tiles, 1, s);
+  launch<EPI_SCALE>(ctx, "f32_l1_bwd", p, tiles, 1, s);
   return check_launch(ctx, "mlp_fp32");
 }
 
@@ -248,6 +249,7 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
 fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s) {
   int blocks = sys->n_mol < 8 * ctx->num_sms ? sys->n_mol : 8 * ctx->num_sms;
   int threads = sys->n_atoms / (sys->n_mol > 0 ? sys->n_mol : 1) > 512 ? 1024 : 128;
+  FNN_KERNEL(ctx, "energy_reduce", s);
   k_energy<<<blocks, threads, 0, s>>>(sys->n_mol, sys->n_atoms, sys->mol_offsets, nl->perm, nl->elem, ctx->ws.ypart,
                                       ctx->w.b4, ctx->w.M, (H3 + BN - 1) / BN, E, ctx->status);
   return check_launch(ctx, "energy_reduce");

@@ -105,9 +105,18 @@ fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total
     ctx->last_error = "scan scratch too small";
     return FNN_E_INVALID;
   }
-  k_scan_tiles<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
-  k_scan_top<<<1, SCAN_NT, 0, s>>>(tmp, nt, total_dev);
-  k_scan_add<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  {
+    FNN_KERNEL(ctx, "scan_tiles", s);
+    k_scan_tiles<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  }
+  {
+    FNN_KERNEL(ctx, "scan_top", s);
+    k_scan_top<<<1, SCAN_NT, 0, s>>>(tmp, nt, total_dev);
+  }
+  {
+    FNN_KERNEL(ctx, "scan_add", s);
+    k_scan_add<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  }
   return check_launch(ctx, "exclusive_scan");
 }
 
@@ -609,10 +618,16 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->elem, 0, (size_t)N, s));
   }
   int cover_blocks = (NM + 256) / 256 < 256 ? (NM + 256) / 256 : 256;
-  k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status);
+  {
+    FNN_KERNEL(ctx, "check_cover", s);
+    k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status);
+  }
   int setup_blocks = NM < 4 * ctx->num_sms ? NM : 4 * ctx->num_sms;
-  k_mol_setup<<<setup_blocks, SETUP_NT, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->elem, R,
-                                                ctx->status);
+  {
+    FNN_KERNEL(ctx, "mol_setup", s);
+    k_mol_setup<<<setup_blocks, SETUP_NT, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->elem, R,
+                                                  ctx->status);
+  }
   if ((st = exclusive_scan(ctx, nl->mol_cells, NM + 1, nl->meta + META_CELLS, nl->scan_tmp, nl->scan_tmp_len, s)))
     return st;
   // cells are bounded by 2N + n_mol + 1 by construction (k_mol_setup caps each structure at max(1, 2n))
@@ -621,37 +636,64 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_start, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
   if (N > 0) {
     int tb = 256, nb = (N + tb - 1) / tb;
-    k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count);
+    {
+      FNN_KERNEL(ctx, "bin", s);
+      k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count);
+    }
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->cell_start, nl->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
     if ((st = exclusive_scan(ctx, nl->cell_start, cells_bound + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
       return st;
     FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
-    k_scatter<<<nb, tb, 0, s>>>(N, nl->cell_of, nl->cell_start, nl->cell_count, nl->cell_tmp);
+    {
+      FNN_KERNEL(ctx, "scatter", s);
+      k_scatter<<<nb, tb, 0, s>>>(N, nl->cell_of, nl->cell_start, nl->cell_count, nl->cell_tmp);
+    }
     int wb = (int)((cells_bound * 32 + 255) / 256);
     if (wb > 16 * ctx->num_sms) wb = 16 * ctx->num_sms;
-    k_sort_cells<<<wb, 256, 0, s>>>(nl->meta, nl->cell_start, nl->cell_tmp, nl->cell_atoms);
+    {
+      FNN_KERNEL(ctx, "sort_cells", s);
+      k_sort_cells<<<wb, 256, 0, s>>>(nl->meta, nl->cell_start, nl->cell_tmp, nl->cell_atoms);
+    }
 
     PredConst pc{R * R, (float)(R * R), (float)R};
     int pb = (int)(((int64_t)N * 32 + 255) / 256);
     if (pb > 32 * ctx->num_sms) pb = 32 * ctx->num_sms;
-    k_pairs<false><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                      nl->cell_atoms, pc, nl->counts, nullptr, nullptr, nullptr, 0, nl->meta);
+    {
+      FNN_KERNEL(ctx, "pairs_count", s);
+      k_pairs<false><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                        nl->cell_atoms, pc, nl->counts, nullptr, nullptr, nullptr, 0, nl->meta);
+    }
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->row_ptr, nl->counts, ((size_t)N + 1) * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
     if ((st = exclusive_scan(ctx, nl->row_ptr, (int64_t)N + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
       return st;
-    k_check_capacity<<<1, 1, 0, s>>>(nl->row_ptr, N, nl->capacity, nl->meta, ctx->status);
-    k_pairs<true><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                     nl->cell_atoms, pc, nullptr, nl->row_ptr, nl->nbr, nl->shift, nl->capacity,
-                                     nl->meta);
+    {
+      FNN_KERNEL(ctx, "check_capacity", s);
+      k_check_capacity<<<1, 1, 0, s>>>(nl->row_ptr, N, nl->capacity, nl->meta, ctx->status);
+    }
+    {
+      FNN_KERNEL(ctx, "pairs_fill", s);
+      k_pairs<true><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                       nl->cell_atoms, pc, nullptr, nl->row_ptr, nl->nbr, nl->shift, nl->capacity,
+                                       nl->meta);
+    }
   }
   // species-sorted, 128-row padded order for the networks
   int nblk = (N + ELEM_NT - 1) / ELEM_NT;
   FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->inv, 0xff, (size_t)nl->pad_cap * sizeof(int32_t), s));
-  if (nblk > 0) k_elem_count<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count);
-  k_elem_scan<<<1, SCAN_NT, 0, s>>>(nblk, nl->blk_count, nl->meta, nl->tile_elem, nl->pad_cap / ROW_TILE);
-  if (nblk > 0) k_elem_scatter<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count, nl->meta, nl->perm, nl->inv);
+  if (nblk > 0) {
+    FNN_KERNEL(ctx, "elem_count", s);
+    k_elem_count<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count);
+  }
+  {
+    FNN_KERNEL(ctx, "elem_scan", s);
+    k_elem_scan<<<1, SCAN_NT, 0, s>>>(nblk, nl->blk_count, nl->meta, nl->tile_elem, nl->pad_cap / ROW_TILE);
+  }
+  if (nblk > 0) {
+    FNN_KERNEL(ctx, "elem_scatter", s);
+    k_elem_scatter<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count, nl->meta, nl->perm, nl->inv);
+  }
   return check_launch(ctx, "fnn_build_neighbors");
 }
 

@@ -70,6 +70,9 @@ def _load():
         "fnn_energy_forces_host": (I32, [P, I32, I32, P, P, P, P, P, I32, P, P, P, P]),
         "fnn_sync": (I32, [P, P, P]),
         "fnn_last_error": (ctypes.c_char_p, [P]),
+        "fnn_profile_enable": (I32, [P, I32]),
+        "fnn_profile_read": (I32, [P, P, P, P, I32, P]),
+        "fnn_launch_count": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -288,3 +291,30 @@ def energy_forces_host(ctx: Context, s, precision: str = "fp32", virial: bool = 
                                       _stream(stream))
     ctx._check(code, "fnn_energy_forces_host")
     return E, F, W
+
+
+def profile_enable(ctx: Context, on: bool = True):
+    """fnn_profile_enable: bracket every kernel of this context with CUDA events on its stream."""
+    ctx._check(lib.fnn_profile_enable(ctx.h, int(on)), "fnn_profile_enable")
+
+
+def profile_read(ctx: Context) -> dict:
+    """fnn_profile_read: {kernel name: (device ms summed, launches)} since the previous read."""
+    cap = 128
+    names = ctypes.create_string_buffer(48 * cap)
+    ms = (ctypes.c_double * cap)()
+    n = (ctypes.c_int64 * cap)()
+    count = ctypes.c_int32(0)
+    ctx._check(lib.fnn_profile_read(ctx.h, names, ms, n, cap, ctypes.byref(count)), "fnn_profile_read")
+    out = {}
+    for k in range(min(count.value, cap)):
+        name = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (ms[k], n[k])
+    return out
+
+
+def launch_count(ctx: Context) -> int:
+    """fnn_launch_count: kernels this context has launched since it was created."""
+    n = ctypes.c_int64(0)
+    ctx._check(lib.fnn_launch_count(ctx.h, ctypes.byref(n)), "fnn_launch_count")
+    return n.value
