@@ -178,6 +178,39 @@ fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t n_atoms, int32_t n_mol, 
  * offending atom for FNN_E_SPECIES, ...). */
 fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
 
+/*
+ * Allocation-free neighbour list (no counterpart in the paper).
+ *
+ * For callers that may not allocate device memory themselves or through this
+ * library -- for example code running inside a host framework that hands out
+ * all device memory from its own pool, or a latency-sensitive loop in which
+ * cudaMalloc/cudaFree would synchronise the device and stall other streams.
+ * Builds the same directed list as fnn_build_neighbors (same predicate, same
+ * kernels) for at most FNN_STATIC_MAX_ATOMS atoms in at most FNN_STATIC_MAX_MOL
+ * structures, with list radius R, and needs no context.  All scratch lives in
+ * one array of about 0.3 MB compiled into the library, which every GPU that
+ * loads the library keeps until the process exits; the call itself allocates
+ * nothing.
+ *   sys      device system, as for fnn_build_neighbors.
+ *   row_ptr  device int32 [N+1] (caller-owned), CSR row offsets.
+ *   nbr      device int32 [cap], neighbour indices.
+ *   shift4   device int8 [cap][4], 4-byte aligned: image shift x, y, z and a zero byte.
+ *   nnz      host; receives the number of entries (also when it exceeds cap).
+ * Returns FNN_E_CAPACITY at once, touching nothing, when n_atoms or n_mol is
+ * above the limit; FNN_E_CAPACITY after the build when nnz > cap (entries
+ * beyond cap are not written); otherwise the device status (FNN_E_SPECIES,
+ * FNN_E_CELL, ...).  Synchronises the stream before returning.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array per device: calls that overlap on
+ * the GPU (several streams or threads at once) race and corrupt each other's
+ * lists; each call clears the parts that must start at zero.
+ */
+#define FNN_STATIC_MAX_ATOMS 8192
+#define FNN_STATIC_MAX_MOL 256
+fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R, int32_t *row_ptr, int32_t *nbr, int8_t *shift4,
+                                      int64_t cap, int64_t *nnz, void *stream);
+
 /* Instrumentation (no counterpart in the paper; the tracing the benchmark reads).
  * fnn_profile_enable: while on, every kernel this context launches is bracketed
  * by CUDA events on its own stream (a few microseconds of host work per launch).

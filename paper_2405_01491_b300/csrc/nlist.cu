@@ -740,3 +740,136 @@ extern "C" fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t 
   }
   return FNN_OK;
 }
+
+// ------------------------------------------------------------------ allocation-free list build
+// fnn_build_neighbors_static: the same kernels as fnn_build_neighbors, with every scratch array
+// (structure grids, cell counts and starts, per-atom cell data, scan partials, status) carved from
+// one file-scope device array instead of library allocations.  For callers that may not allocate
+// device memory; sizes are capped at FNN_STATIC_MAX_ATOMS atoms and FNN_STATIC_MAX_MOL structures.
+#include <mutex>
+
+namespace fnn {
+namespace {
+
+constexpr int NS_MAX_ATOMS = FNN_STATIC_MAX_ATOMS;
+constexpr int NS_MAX_MOL = FNN_STATIC_MAX_MOL;
+constexpr int NS_MAX_CELLS = 2 * NS_MAX_ATOMS + NS_MAX_MOL + 1;   // k_mol_setup caps a structure at 2n cells
+constexpr int NS_SCAN_TMP = 64;
+
+struct StaticScratch {
+  DevStatus status;
+  int32_t meta[META_LEN];
+  int32_t scan_tmp[NS_SCAN_TMP];
+  MolGrid grid[NS_MAX_MOL];
+  int32_t mol_cells[NS_MAX_MOL + 1];
+  int32_t atom_mol[NS_MAX_ATOMS];
+  int32_t cell_of[NS_MAX_ATOMS];
+  int32_t cell_tmp[NS_MAX_ATOMS];
+  int32_t cell_atoms[NS_MAX_ATOMS];
+  int32_t cell_count[NS_MAX_CELLS + 1];
+  int32_t cell_start[NS_MAX_CELLS + 1];
+  uint8_t elem[NS_MAX_ATOMS];
+};
+
+// The scratch every call shares (about 0.3 MB on every device that loads the library).
+static __device__ __align__(256) unsigned char g_nl_scratch[sizeof(StaticScratch)];
+
+constexpr int NS_MAX_DEVICES = 64;
+std::mutex g_nl_scratch_mu;
+StaticScratch *g_nl_scratch_dev[NS_MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device; looked up once per device.
+cudaError_t static_scratch(StaticScratch **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NS_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_nl_scratch_mu);
+  if (!g_nl_scratch_dev[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_nl_scratch);
+    if (e != cudaSuccess) return e;
+    g_nl_scratch_dev[dev] = reinterpret_cast<StaticScratch *>(p);
+  }
+  *out = g_nl_scratch_dev[dev];
+  return cudaSuccess;
+}
+
+cudaError_t scan_in_place(int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp, cudaStream_t s) {
+  int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (n <= 0) return cudaSuccess;
+  if (nt > NS_SCAN_TMP) return cudaErrorInvalidValue;
+  k_scan_tiles<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  k_scan_top<<<1, SCAN_NT, 0, s>>>(tmp, nt, total_dev);
+  k_scan_add<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace fnn
+
+#define FNN_STATIC_TRY(call)                 \
+  do {                                       \
+    if ((call) != cudaSuccess) {             \
+      cudaGetLastError();                    \
+      return FNN_E_CUDA;                     \
+    }                                        \
+  } while (0)
+
+extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R, int32_t *row_ptr, int32_t *nbr,
+                                                 int8_t *shift4, int64_t cap, int64_t *nnz, void *stream) {
+  if (!sys || !row_ptr || !nnz || sys->n_atoms < 0 || sys->n_mol < 1 || !sys->mol_offsets || !(R > 0) ||
+      cap < 0 || (cap > 0 && (!nbr || !shift4)) || ((uintptr_t)shift4 & 3) != 0 || ((uintptr_t)sys->pos & 15) != 0 ||
+      (sys->n_atoms > 0 && (!sys->Z || !sys->pos)) || (sys->pbc && !sys->cell))
+    return FNN_E_INVALID;
+  *nnz = 0;
+  if (sys->n_atoms > NS_MAX_ATOMS || sys->n_mol > NS_MAX_MOL) return FNN_E_CAPACITY;  // beyond the static scratch
+  StaticScratch *S = nullptr;
+  FNN_STATIC_TRY(static_scratch(&S));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = sys->n_atoms, NM = sys->n_mol;
+  const int64_t cells_bound = 2LL * N + NM + 1;
+
+  // clear everything that must start at zero (the array keeps the previous call's contents)
+  FNN_STATIC_TRY(cudaMemsetAsync(&S->status, 0, sizeof(DevStatus), s));
+  FNN_STATIC_TRY(cudaMemsetAsync(S->meta, 0, sizeof(S->meta), s));
+  FNN_STATIC_TRY(cudaMemsetAsync(S->mol_cells, 0, ((size_t)NM + 1) * sizeof(int32_t), s));
+  FNN_STATIC_TRY(cudaMemsetAsync(row_ptr, 0, ((size_t)N + 1) * sizeof(int32_t), s));
+  if (N > 0) {
+    FNN_STATIC_TRY(cudaMemsetAsync(S->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
+    FNN_STATIC_TRY(cudaMemsetAsync(S->elem, 0, (size_t)N, s));
+  }
+  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status);
+  k_mol_setup<<<NM, SETUP_NT, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->elem, R, &S->status);
+  FNN_STATIC_TRY(scan_in_place(S->mol_cells, NM + 1, S->meta + META_CELLS, S->scan_tmp, s));
+  FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+  FNN_STATIC_TRY(cudaMemsetAsync(S->cell_start, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+  if (N > 0) {
+    const int nb = (N + 255) / 256;
+    k_bin<<<nb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_count);
+    FNN_STATIC_TRY(cudaMemcpyAsync(S->cell_start, S->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
+                                   cudaMemcpyDeviceToDevice, s));
+    FNN_STATIC_TRY(scan_in_place(S->cell_start, cells_bound + 1, nullptr, S->scan_tmp, s));
+    FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
+    k_scatter<<<nb, 256, 0, s>>>(N, S->cell_of, S->cell_start, S->cell_count, S->cell_tmp);
+    k_sort_cells<<<(int)((cells_bound * 32 + 255) / 256), 256, 0, s>>>(S->meta, S->cell_start, S->cell_tmp,
+                                                                       S->cell_atoms);
+    PredConst pc{R * R, (float)(R * R), (float)R};
+    const int pb = (N * 32 + 255) / 256;
+    k_pairs<false><<<pb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_start,
+                                      S->cell_atoms, pc, row_ptr, nullptr, nullptr, nullptr, 0, S->meta);
+    FNN_STATIC_TRY(scan_in_place(row_ptr, (int64_t)N + 1, nullptr, S->scan_tmp, s));
+    k_check_capacity<<<1, 1, 0, s>>>(row_ptr, N, cap, S->meta, &S->status);
+    k_pairs<true><<<pb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_start,
+                                     S->cell_atoms, pc, nullptr, row_ptr, nbr, reinterpret_cast<char4 *>(shift4), cap,
+                                     S->meta);
+  }
+  FNN_STATIC_TRY(cudaGetLastError());
+  int32_t total = 0;
+  DevStatus st{};
+  FNN_STATIC_TRY(cudaMemcpyAsync(&total, row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FNN_STATIC_TRY(cudaMemcpyAsync(&st, &S->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  FNN_STATIC_TRY(cudaStreamSynchronize(s));
+  *nnz = total;
+  return (fnn_status)st.code;
+}

@@ -73,6 +73,7 @@ def _load():
         "fnn_profile_enable": (I32, [P, I32]),
         "fnn_profile_read": (I32, [P, P, P, P, I32, P]),
         "fnn_launch_count": (I32, [P, P]),
+        "fnn_build_neighbors_static": (I32, [P, ctypes.c_double, P, P, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
