@@ -50,6 +50,8 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
     """Algorithmic work of one launch of a kernel: (bound, amount, unit) or None."""
     if name == "aev_forward":       # positions once, list entries (index + shift), the AEV row written
         return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B"
+    if name == "aev_forward_bf16":  # the same with a bf16 AEV row
+        return "hbm", n_atoms * (16 + 2016) + nnz * 8, "B"
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
         return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
@@ -129,44 +131,108 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def cpu_baseline(n_sample: int = 2500, M: int = 8):
-    """The float64 oracle, as it stands, on a periodic box cut from the same recipe (host cores)."""
+def oracle_full(M: int = 8, min_seconds: float = 10.0, max_reps: int = 3):
+    """The float64 oracle, as it stands, on the whole benchmark box (host cores); repeated until about
+    min_seconds of CPU work has been timed.  Returns (cpu_baseline entry, oracle result)."""
     import oracle
     from paper_2405_01491_b300 import synth
-    s = synth.mix_box(n_sample, (n_sample / 0.1) ** (1 / 3), seed=3)
+    s = synth.mix23558()
     w = synth.xavier_weights(M)
-    t = time.perf_counter()
-    oracle.energy_forces(s, w)
-    dt = time.perf_counter() - t
+    times, res = [], None
+    while len(times) < max_reps and sum(times) < min_seconds:
+        t = time.perf_counter()
+        res = oracle.energy_forces(s, w)
+        times.append(time.perf_counter() - t)
+    dt = statistics.mean(times)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one energy+force evaluation of a {n_sample}-atom periodic box at the same density and "
-                      f"composition, M={M}, float64 (oracle neighbour search is all-pairs), {dt:.1f} s"}
+    entry = {"value": s.n_atoms / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{len(times)} full energy+force evaluation(s) of the same 23,558-atom box, M={M}, float64 "
+                       f"(all-pairs neighbour search), {dt:.1f} s each"}
+    return entry, res
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_sample = 1500
     times = []
-    base = None
+    entry = None
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(n_sample)
+        e, _ = oracle_full(min_seconds=0.0, max_reps=1)
         if k >= args.warmup:
-            times.append(n_sample / r["value"])
-        base = r
-    v = n_sample / statistics.mean(times)
+            times.append(23558 / e["value"])
+        entry = e
+    v = 23558 / statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_atoms": n_sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
-                             "sample": f"each step: energy+forces of a {n_sample}-atom periodic box cut from the "
-                                       "same recipe (density 0.1, same composition), M=8, float64"},
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": entry["cores"], "kind": "oracle",
+                             "sample": "each step: one float64 energy+force evaluation of the whole 23,558-atom box"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
+    """K timed steps of one form: per-step CUDA events (L2 flushed outside them), per-kernel events."""
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fnn.build_neighbors(ctx, ds, nl)
+        fnn.energy_forces(ctx, ds, nl, form, out=(E, F, Wv))
+
+    for _ in range(warmup):
+        step()
+    fnn.check(ctx, f"warm-up {form}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    fnn.profile_read(ctx)
+    fnn.profile_enable(ctx, True)
+    launches0 = fnn.launch_count(ctx)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = fnn.launch_count(ctx) - launches0
+    fnn.profile_enable(ctx, False)
+    prof = fnn.profile_read(ctx)
+    fnn.check(ctx, f"timed steps {form}")
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return ms, prof, launches, clk.summary()
+
+
+def kernel_table(prof, steps, n_atoms, nnz, M, form, pk):
+    ffma_peak = N_SM * FFMA_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    tensor_peak = pk["bf16_tflops_sustained"] * (2 if form == "fp8" else 1)
+    kernels = {}
+    total = sum(v[0] for v in prof.values())
+    for name, (tot_ms, n) in prof.items():
+        entry = {"ms_per_launch": tot_ms / n, "launches_per_step": n / steps, "share": tot_ms / total if total else None}
+        wk = kernel_work(name, n_atoms, nnz, M)
+        if wk:
+            bound, amount, u = wk
+            t = tot_ms / n * 1e-3
+            if u == "B":
+                entry.update(bound=bound, achieved=amount / t / 1e9, unit="GB/s", peak=pk["hbm_gbs"])
+            else:
+                entry.update(bound=bound, achieved=amount / t / 1e12, unit="TFLOP/s",
+                             peak=ffma_peak if bound == "alu" else tensor_peak)
+            entry["frac"] = entry["achieved"] / entry["peak"]
+        kernels[name] = entry
+    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: prof[k][0])
+    d = kernels[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"],
+            "peak_src": (f"FP32 FFMA: {N_SM} SMs x {FFMA_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz"
+                         if d["bound"] == "alu" else
+                         f"{pk['src']} {'HBM copy' if d['bound'] == 'hbm' else 'bf16 sustained'}")}
+    return kernels, roof
 
 
 def main():
@@ -175,7 +241,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fnn", choices=["fnn", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
+                    help="form whose throughput is the headline value")
+    ap.add_argument("--forms", default="fp32,bf16", help="forms timed and reported (comma separated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -198,6 +266,12 @@ def main():
         if dist:
             dist.barrier()
 
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     M = 8
     s = synth.mix23558()
     w = synth.xavier_weights(M)
@@ -211,71 +285,21 @@ def main():
     F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device="cuda")
     Wv = torch.empty((s.n_mol, 3, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step():
-        fnn.build_neighbors(ctx, ds, nl)
-        fnn.energy_forces(ctx, ds, nl, args.precision, out=(E, F, Wv))
-
-    for _ in range(args.warmup):
-        step()
-    fnn.check(ctx, "warm-up")
-
-    # timed region: per-step CUDA events on the launching stream; the L2 flush sits between the events
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    fnn.profile_read(ctx)
-    fnn.profile_enable(ctx, True)
-    launches0 = fnn.launch_count(ctx)
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    launches = fnn.launch_count(ctx) - launches0
-    fnn.profile_enable(ctx, False)
-    prof = fnn.profile_read(ctx)
-    fnn.check(ctx, "timed steps")
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    ms_max = float(t_rank.item())
-    value = world * s.n_atoms / (ms_max * 1e-3)
-
-    # per-kernel work and the roofline of the dominant kernel
     pk = peaks()
-    ffma_peak = N_SM * FFMA_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
-    digest = source_digest()
-    kernels = {}
-    for name, (tot_ms, n) in prof.items():
-        entry = {"ms_per_launch": tot_ms / n, "launches_per_step": n / args.steps, "share": None}
-        wk = kernel_work(name, s.n_atoms, nnz, M)
-        if wk:
-            bound, amount, u = wk
-            t = tot_ms / n * 1e-3
-            if u == "B":
-                entry.update(bound=bound, achieved=amount / t / 1e9, unit="GB/s", peak=pk["hbm_gbs"])
-            else:
-                peak = ffma_peak if bound == "alu" else pk["bf16_tflops_sustained"] * (2 if args.precision == "fp8" else 1)
-                entry.update(bound=bound, achieved=amount / t / 1e12, unit="TFLOP/s", peak=peak)
-            entry["frac"] = entry["achieved"] / entry["peak"]
-        kernels[name] = entry
-    total_k = sum(v[0] for v in prof.values())
-    for name in kernels:
-        kernels[name]["share"] = prof[name][0] / total_k if total_k else None
-    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: prof[k][0])
-    d = kernels[dom]
-    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": recorded_traffic(dom, digest),
-            "peak_src": (pk["src"] if d["bound"] != "alu" else
-                         f"FP32 FFMA: {N_SM} SMs x {FFMA_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz")}
+    forms = [f for f in args.forms.split(",") if f]
+    if args.precision not in forms:
+        forms.insert(0, args.precision)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
+    results = {}
+    for form in forms:
+        ms, prof, launches, clocks = time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, args.steps,
+                                               args.warmup, barrier)
+        fnn.energy_forces(ctx, ds, nl, form, out=(E, F, Wv))
+        fnn.check(ctx, form)
+        results[form] = dict(ms=max_over_ranks(ms), prof=prof, launches=launches, clocks=clocks,
+                             E=E.cpu().numpy().copy(), F=F.cpu().numpy().copy())
+
+    # end to end through the C ABI with host buffers (copies inside the timed region), headline form
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hs = synth.Structures(pin(s.Z), pin(s.pos), pin(s.mol_offsets), pin(s.cell), pin(s.pbc), s.name)
     hout = (pin(np.zeros(s.n_mol)), pin(np.zeros((s.n_atoms, 3), np.float32)), pin(np.zeros((s.n_mol, 3, 3))))
@@ -285,26 +309,41 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         fnn.energy_forces_host(ctx, hs, args.precision, out=hout)
-    t_e2e = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps)
     h2d = s.n_atoms * (4 + 12) + (s.n_mol + 1) * 4 + s.n_mol * (36 + 1)
     d2h = s.n_mol * 8 + s.n_atoms * 12 + s.n_mol * 72
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision],
-            "data": "synthetic",
+    base, ref = (None, None)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, ref = oracle_full(M)
+
+    head = results[args.precision]
+    kernels, roof = kernel_table(head["prof"], args.steps, s.n_atoms, nnz, M, args.precision, pk)
+    roof["traffic"] = recorded_traffic(roof["kernel"], source_digest())
+    form_report = {}
+    for form, r in results.items():
+        ks, rf = kernel_table(r["prof"], args.steps, s.n_atoms, nnz, M, form, pk)
+        entry = {"value": world * s.n_atoms / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "gpu_launches": r["launches"],
+                 "dominant": rf}
+        if ref is not None:
+            entry["max_dE_per_atom"] = float(np.abs(r["E"] - ref.energy).max() / s.n_atoms)
+            entry["max_dF"] = float(np.abs(r["F"] - ref.forces).max())
+            entry["rms_rel_dF"] = float(np.sqrt(np.mean((r["F"] - ref.forces) ** 2) / np.mean(ref.forces ** 2)))
+        form_report[form] = entry
+
+    line = {"metric": METRIC, "value": world * s.n_atoms / (head["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "members": M, "precision": args.precision,
                        "list_entries": nnz, "parallelism": f"replicas x{world}",
                        "l2": "flushed before every timed step (256 MB write outside the step's CUDA events)"},
-            "roofline": roof, "gpu_launches": int(launches),
-            "e2e": {"value": world * s.n_atoms / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "roofline": roof, "gpu_launches": int(head["launches"]),
+            "e2e": {"value": world * s.n_atoms / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "clocks": clk.summary(), "kernels": kernels, "source_digest": digest}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+            "clocks": head["clocks"], "forms": form_report, "kernels": kernels, "source_digest": source_digest()}
+    if base is not None:
+        line["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

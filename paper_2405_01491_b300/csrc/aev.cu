@@ -12,12 +12,21 @@
 // register and writes its slot: one coalesced 128-byte store per block.
 // Adjoint: same staging; the radial and angular partials are chained to dE/dd per neighbour in
 // shared memory, then scattered to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
+#include <cuda_bf16.h>
+
 #include "fnn_internal.cuh"
 
 namespace fnn {
 
 static constexpr unsigned FULL = 0xffffffffu;
 constexpr int AEV_WARPS = 4;
+
+// 2^x on the special-function unit (ex2.approx.ftz: about 2 ulp; arguments here are <= 0)
+__device__ __forceinline__ float exp2f_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 struct WarpStage {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
@@ -167,6 +176,8 @@ template <typename OutT>
 __device__ __forceinline__ void store_out(OutT *p, float v);
 template <>
 __device__ __forceinline__ void store_out<float>(float *p, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16 *p, float v) { *p = __float2bfloat16(v); }
 
 struct AevFwdArgs {
   StageArgs sa;
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
         float acc = 0.f;
         for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
           float dr = S.rd[t].w - Rk;
-          acc += expf(-P.eta_r * dr * dr) * S.rfc[t];
+          acc += __expf(-P.eta_r * dr * dr) * S.rfc[t];
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
         if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc);
@@ -234,14 +245,14 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
 #pragma unroll
               for (int s = 0; s < NSZ; s++) {
                 float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
-                S.stage[lane][s] = exp2f(P.zeta * log2f(base_s));
+                S.stage[lane][s] = exp2f_fast(P.zeta * __log2f(base_s));
               }
               float rbar = 0.5f * (d1.w + d2.w);
               float fcc = 2.f * S.afc[ja] * S.afc[ka];
 #pragma unroll
               for (int m = 0; m < NSA; m++) {
                 float dr = rbar - P.shf_a[m];
-                S.stage[lane][4 + m] = expf(-P.eta_a * dr * dr) * fcc;
+                S.stage[lane][4 + m] = __expf(-P.eta_a * dr * dr) * fcc;
               }
             }
             __syncwarp();
@@ -301,7 +312,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
 #pragma unroll
       for (int k = 0; k < NSR; k++) {
         float dr = r - P.shf_r[k];
-        float gk = expf(-P.eta_r * dr * dr);
+        float gk = __expf(-P.eta_r * dr * dr);
         dEdr += S.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
       }
       float f = dEdr / r;
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
 #pragma unroll
             for (int s = 0; s < NSZ; s++) {
               float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
-              float f = exp2f(P.zeta * log2f(base_s));
+              float f = exp2f_fast(P.zeta * __log2f(base_s));
               fs[s] = f;
               dfs[s] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
             }
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
 #pragma unroll
             for (int m = 0; m < NSA; m++) {
               float dr = rbar - P.shf_a[m];
-              float gm = expf(-P.eta_a * dr * dr);
+              float gm = __expf(-P.eta_a * dr * dr);
               float dgm = -2.f * P.eta_a * dr * gm;
 #pragma unroll
               for (int s = 0; s < NSZ; s++) {
@@ -470,6 +481,25 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
     k_aev_forward<float><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward");
+}
+
+fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, __nv_bfloat16 *out,
+                                   const int32_t *inv, cudaStream_t s) {
+  AevFwdArgs a;
+  a.sa = stage_args(sys, nl);
+  a.P = ctx->aev;
+  a.out = reinterpret_cast<float *>(out);
+  a.inv = inv;
+  a.meta = nl->meta;
+  a.n_atoms = sys->n_atoms;
+  a.st = ctx->status;
+  int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
+  if (rows == 0) return FNN_OK;
+  {
+    FNN_KERNEL(ctx, "aev_forward_bf16", s);
+    k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  }
+  return check_launch(ctx, "aev_forward_bf16");
 }
 
 fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,

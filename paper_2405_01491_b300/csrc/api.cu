@@ -64,7 +64,8 @@ fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows) {
   if ((st = dalloc(ctx, &ws.aev, rows * NAEV)) || (st = dalloc(ctx, &ws.h1, rows * M * H1)) ||
       (st = dalloc(ctx, &ws.h2, rows * M * H2)) || (st = dalloc(ctx, &ws.g3, rows * M * H3)) ||
       (st = dalloc(ctx, &ws.g2, rows * M * H2)) || (st = dalloc(ctx, &ws.g1, rows * M * H1)) ||
-      (st = dalloc(ctx, &ws.gaev, rows * NAEV)) || (st = dalloc(ctx, &ws.ypart, rows * M * 4))) {
+      (st = dalloc(ctx, &ws.gaev, rows * NAEV)) || (st = dalloc(ctx, &ws.ypart, rows * M * 4)) ||
+      (st = dalloc(ctx, &ws.e_atom, rows))) {
     ws.rows = 0;
     return st;
   }
@@ -87,6 +88,7 @@ static void free_workspace(Workspace &ws) {
   float *ptrs[] = {ws.aev, ws.h1, ws.h2, ws.g3, ws.g2, ws.g1, ws.gaev, ws.ypart};
   for (float *p : ptrs)
     if (p) cudaFree(p);
+  if (ws.e_atom) cudaFree(ws.e_atom);
   void *tc = ws.tc;
   size_t tr = ws.tc_rows;
   ws = Workspace();
@@ -221,7 +223,8 @@ static fnn_status load_weights_host(fnn_ctx *ctx, const fnn_weights *hw) {
       (st = upload(ctx, &w.w4, w4)) || (st = upload(ctx, &w.b4, b4)))
     return st;
   w.M = M;
-  if ((st = upload_tc_weights(ctx, hw))) return st;
+  if ((st = upload_tc_weights(ctx, M, W1cat.data(), W1Tcat.data(), W2.data(), W2T.data(), W3.data(), W3T.data())))
+    return st;
   ctx->has_weights = true;
   return FNN_OK;
 }
@@ -279,13 +282,13 @@ extern "C" fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, con
   cudaStream_t s = (cudaStream_t)stream;
   fnn_status st;
   if ((st = ensure_workspace(ctx, nl->pad_cap))) return st;
-  if ((st = launch_aev_forward(ctx, sys, nl, ctx->ws.aev, nl->inv, s))) return st;
-  if (prec == FNN_FP32)
-    st = mlp_fp32_forward_backward(ctx, nl, s);
-  else
-    st = mlp_tc_forward_backward(ctx, nl, prec, s);
-  if (st) return st;
-  if ((st = energy_reduce(ctx, sys, nl, E, s))) return st;
+  if (prec == FNN_FP32) {
+    if ((st = launch_aev_forward(ctx, sys, nl, ctx->ws.aev, nl->inv, s))) return st;
+    if ((st = mlp_fp32_forward_backward(ctx, nl, s))) return st;
+    if ((st = energy_reduce(ctx, sys, nl, E, s))) return st;
+  } else if ((st = tc_energy(ctx, sys, nl, prec, E, s))) {
+    return st;
+  }
   FNN_CUDA_TRY(ctx, cudaMemsetAsync(F, 0, (size_t)sys->n_atoms * 3 * sizeof(float), s));
   if (virial) FNN_CUDA_TRY(ctx, cudaMemsetAsync(virial, 0, (size_t)sys->n_mol * 9 * sizeof(double), s));
   return launch_aev_adjoint(ctx, sys, nl, ctx->ws.gaev, nl->inv, F, virial, s);

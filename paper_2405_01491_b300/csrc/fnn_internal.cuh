@@ -102,6 +102,7 @@ struct Workspace {
   float *g1 = nullptr;      // [rows][M*256]
   float *gaev = nullptr;    // [rows][1008]
   float *ypart = nullptr;   // [rows][M][4]
+  double *e_atom = nullptr; // [rows] member-averaged atomic energies (atom order)
   void *tc = nullptr;       // tensor-core buffers (mlp_tc.cu)
   size_t tc_rows = 0;
 };
@@ -220,10 +221,14 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
 fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,
                               const int32_t *inv, float *F, double *virial, cudaStream_t s);
 fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s);
-fnn_status mlp_tc_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, fnn_precision prec, cudaStream_t s);
-fnn_status upload_tc_weights(fnn_ctx *ctx, const fnn_weights *hw);
+fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
+                     cudaStream_t s);
+fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const float *W1Tcat, const float *W2,
+                             const float *W2T, const float *W3, const float *W3T);
 void free_tc(fnn_ctx *ctx);
 fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s);
+fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
+                              int ntile, double *E, cudaStream_t s);
 fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows);
 
 }  // namespace fnn

@@ -211,26 +211,34 @@ fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStre
 }
 
 // ---------------------------------------------------------------------------- energy reduction
-// E_mol = sum over atoms of (1/M) sum_m (y partials + b4), accumulated in float64 (section II.E).
-__global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, const int32_t *perm,
-                         const uint8_t *elem, const float *ypart, const float *b4, int M, int ntile, double *E,
+// e_i = (1/M) sum_m (y partials + b4) per atom (wide, row order), then E_mol = sum over the structure's
+// contiguous atoms in float64, one block per structure, fixed order (section II.E).
+__global__ void k_atom_energy(int n_rows, const int32_t *meta, const int32_t *inv, const uint8_t *elem,
+                              const float *ypart, const float *b4, int M, int ntile, double *e_atom) {
+  int rows = min(n_rows, meta[META_NPAD]);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    int i = inv[r];
+    if (i < 0) continue;
+    int e = elem[i];
+    float y = 0.f;
+    for (int m = 0; m < M; m++) {
+      const float *yp = ypart + ((size_t)r * M + m) * 4;
+      float ym = b4[m * NE + e];
+      for (int t = 0; t < ntile; t++) ym += yp[t];
+      y += ym;
+    }
+    e_atom[i] = (double)y / (double)M;
+  }
+}
+
+__global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, const double *e_atom, double *E,
                          DevStatus *st) {
   __shared__ double red[32];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int mol = blockIdx.x; mol < n_mol; mol += gridDim.x) {
     int a0 = max(mol_offsets[mol], 0), a1 = min(mol_offsets[mol + 1], n_atoms);
     double acc = 0.0;
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-      int r = perm[i], e = elem[i];
-      float y = 0.f;
-      for (int m = 0; m < M; m++) {
-        const float *yp = ypart + ((size_t)r * M + m) * 4;
-        float ym = b4[m * NE + e];
-        for (int t = 0; t < ntile; t++) ym += yp[t];
-        y += ym;
-      }
-      acc += (double)y;
-    }
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc += e_atom[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[w] = acc;
@@ -238,7 +246,6 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int q = 0; q < nwarp; q++) t += red[q];
-      t /= (double)M;
       E[mol] = t;
       if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
     }
@@ -246,13 +253,24 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
   }
 }
 
-fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s) {
+fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
+                              int ntile, double *E, cudaStream_t s) {
+  {
+    int rows = nl->pad_cap;
+    int blocks = (rows + 255) / 256;
+    FNN_KERNEL(ctx, "atom_energy", s);
+    k_atom_energy<<<blocks, 256, 0, s>>>(rows, nl->meta, nl->inv, nl->elem, ypart, ctx->w.b4, ctx->w.M, ntile,
+                                         ctx->ws.e_atom);
+  }
   int blocks = sys->n_mol < 8 * ctx->num_sms ? sys->n_mol : 8 * ctx->num_sms;
   int threads = sys->n_atoms / (sys->n_mol > 0 ? sys->n_mol : 1) > 512 ? 1024 : 128;
   FNN_KERNEL(ctx, "energy_reduce", s);
-  k_energy<<<blocks, threads, 0, s>>>(sys->n_mol, sys->n_atoms, sys->mol_offsets, nl->perm, nl->elem, ctx->ws.ypart,
-                                      ctx->w.b4, ctx->w.M, (H3 + BN - 1) / BN, E, ctx->status);
+  k_energy<<<blocks, threads, 0, s>>>(sys->n_mol, sys->n_atoms, sys->mol_offsets, ctx->ws.e_atom, E, ctx->status);
   return check_launch(ctx, "energy_reduce");
+}
+
+fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s) {
+  return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, (H3 + BN - 1) / BN, E, s);
 }
 
 }  // namespace fnn

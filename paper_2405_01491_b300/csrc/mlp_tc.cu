@@ -1,22 +1,229 @@
-// Tensor-core (tcgen05) forms of the per-element networks: BF16 and FP8 with FP32 accumulation.
-#include "fnn_internal.cuh"
+// Tensor-core (tcgen05) BF16 form of the per-element networks (section II.B) with FP32 accumulation.
+//
+// Same products as the FP32 form (mlp_simt.cu), on 128 x NT tiles of tc_gemm.cuh:
+//   L1  h1 = CELU(aev W1cat^T + b1)              NT = 256, N = M*256, K = 1008
+//   L2  h2 = CELU(h1_m W2^T + b2)                NT = 192 per member
+//   L3  g3 = (1/M) w4 CELU'(z3), y_m = h3 . w4   NT = 160 per member (whole row in one tile)
+//   L3' g2 = (g3_m W3) * CELU'(z2)               NT = 192
+//   L2' g1 = (g2_m W2) * CELU'(z1)               NT = 256
+//   L1' dE/dAEV = g1 W1cat                       NT = 256, N = 1008, K = M*256, fp32 out
+// Activations between layers are bf16 in HBM; operands reach shared memory by TMA (3-D tensor maps
+// whose middle coordinate selects the member, so each member's K range ends in zero fill).
+#include <cudaTypedefs.h>
+
+#include <vector>
+
+#include "tc_gemm.cuh"
 
 namespace fnn {
 
-fnn_status upload_tc_weights(fnn_ctx *ctx, const fnn_weights *hw) {
-  (void)ctx;
-  (void)hw;
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D bf16 tensor map: dims (d0 innermost, d1, d2), byte strides of d1 and d2, box (b0, b1, b2), 128-byte swizzle
+bool encode3d(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
+              uint32_t b0, uint32_t b1, uint32_t b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t str[2] = {s1, s2};
+  cuuint32_t box[3] = {b0, b1, b2}, es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, str, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcState {
+  int M = 0;
+  __nv_bfloat16 *wbuf = nullptr;
+  __nv_bfloat16 *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
+  CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
+  __nv_bfloat16 *abuf = nullptr;
+  size_t rows = 0;
+  __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+};
+
+TcState *state(fnn_ctx *ctx) {
+  if (!ctx->w.tc) ctx->w.tc = new TcState();
+  return static_cast<TcState *>(ctx->w.tc);
+}
+
+template <int NT, int EPI>
+fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B, const tc::Args &a,
+                  dim3 grid, cudaStream_t s) {
+  static bool attr_set = false;
+  const size_t sm = tc::smem_bytes<NT>();
+  if (!attr_set) {
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma<NT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  FNN_KERNEL(ctx, name, s);
+  tc::k_umma<NT, EPI><<<grid, tc::THREADS, sm, s>>>(A, B, a);
+  return check_launch(ctx, name);
+}
+
+}  // namespace
+
+void free_tc(fnn_ctx *ctx) {
+  TcState *t = static_cast<TcState *>(ctx->w.tc);
+  if (!t) return;
+  if (t->wbuf) cudaFree(t->wbuf);
+  if (t->abuf) cudaFree(t->abuf);
+  delete t;
+  ctx->w.tc = nullptr;
+}
+
+// bf16 copies of the layer matrices in the FP32 form's layouts (host arrays given in those layouts)
+fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const float *W1Tcat, const float *W2,
+                             const float *W2T, const float *W3, const float *W3T) {
+  TcState *t = state(ctx);
+  if (t->wbuf) cudaFree(t->wbuf);
+  t->wbuf = nullptr;
+  const size_t n1 = (size_t)NE * M * H1 * NAEV, n2 = (size_t)M * NE * H2 * H1, n3 = (size_t)M * NE * H3 * H2;
+  const size_t total = 2 * (n1 + n2 + n3);
+  std::vector<__nv_bfloat16> h(total);
+  size_t o = 0;
+  const float *src[6] = {W1cat, W1Tcat, W2, W2T, W3, W3T};
+  const size_t len[6] = {n1, n1, n2, n2, n3, n3};
+  size_t off[6];
+  for (int k = 0; k < 6; k++) {
+    off[k] = o;
+    for (size_t i = 0; i < len[k]; i++) h[o + i] = __float2bfloat16(src[k][i]);
+    o += len[k];
+  }
+  if (cudaMalloc(&t->wbuf, total * sizeof(__nv_bfloat16)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for bf16 weights";
+    return FNN_E_OOM;
+  }
+  FNN_CUDA_TRY(ctx, cudaMemcpy(t->wbuf, h.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+  t->W1 = t->wbuf + off[0];
+  t->W1T = t->wbuf + off[1];
+  t->W2 = t->wbuf + off[2];
+  t->W2T = t->wbuf + off[3];
+  t->W3 = t->wbuf + off[4];
+  t->W3T = t->wbuf + off[5];
+  t->M = M;
+  const uint64_t G = (uint64_t)M * NE;
+  bool ok = encode3d(&t->mW1, t->W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 256, 1) &&
+            encode3d(&t->mW1T, t->W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2, 64,
+                     256, 1) &&
+            encode3d(&t->mW2, t->W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, H2, 1) &&
+            encode3d(&t->mW2T, t->W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, H1, 1) &&
+            encode3d(&t->mW3, t->W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 64, H3, 1) &&
+            encode3d(&t->mW3T, t->W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 64, H2, 1);
+  if (!ok) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the weight maps";
+    return FNN_E_CUDA;
+  }
   return FNN_OK;
 }
 
-void free_tc(fnn_ctx *ctx) { (void)ctx; }
+static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows) {
+  TcState *t = state(ctx);
+  const int M = t->M;
+  if (t->abuf && rows <= t->rows) return FNN_OK;
+  rows = rows + rows / 8;
+  if (t->abuf) cudaFree(t->abuf);
+  t->abuf = nullptr;
+  const size_t per_row = NAEV + (size_t)M * (H1 + H2 + H3 + H2 + H1);
+  if (cudaMalloc(&t->abuf, rows * per_row * sizeof(__nv_bfloat16)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for bf16 activations";
+    return FNN_E_OOM;
+  }
+  t->rows = rows;
+  __nv_bfloat16 *p = t->abuf;
+  t->aev = p; p += rows * NAEV;
+  t->h1 = p; p += rows * M * H1;
+  t->h2 = p; p += rows * M * H2;
+  t->g3 = p; p += rows * M * H3;
+  t->g2 = p; p += rows * M * H2;
+  t->g1 = p;
+  const uint64_t R = rows;
+  bool ok = encode3d(&t->mAev, t->aev, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 128) &&
+            encode3d(&t->mH1, t->h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128) &&
+            encode3d(&t->mH2, t->h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
+            encode3d(&t->mG3, t->g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 64, 1, 128) &&
+            encode3d(&t->mG2, t->g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
+            encode3d(&t->mG1, t->g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128);
+  if (!ok) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the activation maps";
+    return FNN_E_CUDA;
+  }
+  return FNN_OK;
+}
 
-fnn_status mlp_tc_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, fnn_precision prec, cudaStream_t s) {
-  (void)nl;
-  (void)prec;
-  (void)s;
-  ctx->last_error = "tensor-core precision forms are not built yet";
-  return FNN_E_INVALID;
+fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, __nv_bfloat16 *out,
+                                   const int32_t *inv, cudaStream_t s);
+
+// AEV (bf16) -> six tcgen05 GEMMs -> member-averaged energies; leaves dE/dAEV (fp32) in ws.gaev
+fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
+                     cudaStream_t s) {
+  if (prec != FNN_BF16) {
+    ctx->last_error = "FP8 form is not built yet";
+    return FNN_E_INVALID;
+  }
+  TcState *t = state(ctx);
+  if (!t->wbuf || t->M != ctx->w.M) {
+    ctx->last_error = "bf16 weights missing";
+    return FNN_E_STATE;
+  }
+  fnn_status st;
+  if ((st = tc_workspace(ctx, nl->pad_cap))) return st;
+  if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->aev, nl->inv, s))) return st;
+  const DeviceWeights &w = ctx->w;
+  const int M = w.M;
+  const unsigned tiles = (unsigned)(nl->pad_cap / ROW_TILE);
+  tc::Args a{};
+  a.tile_elem = nl->tile_elem;
+  a.st = ctx->status;
+  a.M = M;
+  // L1: all members at once
+  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
+  a.out = t->h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
+  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
+  if ((st = launch<256, tc::EPI_BIAS_CELU>(ctx, "bf16_l1_fwd", t->mAev, t->mW1, a, dim3(M, tiles, 1), s))) return st;
+  // L2
+  a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
+  a.out = t->h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
+  if ((st = launch<192, tc::EPI_BIAS_CELU>(ctx, "bf16_l2_fwd", t->mH1, t->mW2, a, dim3(1, tiles, M), s))) return st;
+  // L3 + output layer
+  a.K = H2; a.N = H3;
+  a.out = t->g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
+  a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
+  a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
+  a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
+  if ((st = launch<160, tc::EPI_L3>(ctx, "bf16_l3_fwd", t->mH2, t->mW3, a, dim3(1, tiles, M), s))) return st;
+  // L3 backward
+  a.K = H3; a.N = H2;
+  a.out = t->g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.aux = t->h2; a.ldaux = (long long)M * H2; a.aux_mstride = H2;
+  if ((st = launch<192, tc::EPI_DCELU>(ctx, "bf16_l3_bwd", t->mG3, t->mW3T, a, dim3(1, tiles, M), s))) return st;
+  // L2 backward
+  a.K = H2; a.N = H1;
+  a.out = t->g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
+  a.aux = t->h1; a.ldaux = (long long)M * H1; a.aux_mstride = H1;
+  if ((st = launch<256, tc::EPI_DCELU>(ctx, "bf16_l2_bwd", t->mG2, t->mW2T, a, dim3(1, tiles, M), s))) return st;
+  // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
+  a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
+  a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
+  if ((st = launch<256, tc::EPI_F32>(ctx, "bf16_l1_bwd", t->mG1, t->mW1T, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
+    return st;
+  return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 1, E, s);
 }
 
 }  // namespace fnn

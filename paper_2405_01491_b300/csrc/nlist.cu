@@ -131,7 +131,7 @@ __global__ void k_check_cover(fnn_system sys, DevStatus *st) {
   }
 }
 
-constexpr int SETUP_NT = 256;
+constexpr int SETUP_NT = 512;
 
 __global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid *grid, int32_t *mol_cells,
                                                         int32_t *atom_mol, uint8_t *elem, double R,
@@ -152,18 +152,34 @@ __global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid 
     }
     int pbc = sys.pbc ? (sys.pbc[m] != 0) : 0;
     float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-      atom_mol[i] = m;
-      int e = element_of(sys.Z[i]);
-      if (e < 0) {
-        post_status(st, FNN_E_SPECIES, i);
-        e = 0;
+    for (int i0 = a0 + threadIdx.x; i0 < a1; i0 += 4 * blockDim.x) {
+      // four atoms per thread in flight: the loads are issued before any is used
+      int zz[4];
+      float4 pp[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        int i = i0 + u * blockDim.x;
+        if (i < a1) {
+          zz[u] = sys.Z[i];
+          pp[u] = pos[i];
+        }
       }
-      elem[i] = (uint8_t)e;
-      float4 p = pos[i];
-      if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) post_status(st, FNN_E_NONFINITE, i);
-      mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
-      mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        int i = i0 + u * blockDim.x;
+        if (i >= a1) continue;
+        atom_mol[i] = m;
+        int e = element_of(zz[u]);
+        if (e < 0) {
+          post_status(st, FNN_E_SPECIES, i);
+          e = 0;
+        }
+        elem[i] = (uint8_t)e;
+        float4 p = pp[u];
+        if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) post_status(st, FNN_E_NONFINITE, i);
+        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+      }
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
