@@ -324,7 +324,8 @@ def main():
     for form, r in results.items():
         ks, rf = kernel_table(r["prof"], args.steps, s.n_atoms, nnz, M, form, pk)
         entry = {"value": world * s.n_atoms / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "gpu_launches": r["launches"],
-                 "dominant": rf}
+                 "dominant": rf, "kernel_ms": {k: round(v["ms_per_launch"] * v["launches_per_step"], 4)
+                                               for k, v in ks.items()}}
         if ref is not None:
             entry["max_dE_per_atom"] = float(np.abs(r["E"] - ref.energy).max() / s.n_atoms)
             entry["max_dF"] = float(np.abs(r["F"] - ref.forces).max())

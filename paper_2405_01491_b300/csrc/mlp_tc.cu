@@ -61,8 +61,14 @@ TcState *state(fnn_ctx *ctx) {
 }
 
 template <int NT, int EPI>
-fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B, const tc::Args &a,
-                  dim3 grid, cudaStream_t s) {
+fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B, tc::Args a,
+                  dim3 tiles, cudaStream_t s) {
+  // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
+  a.n_ntiles = (int)tiles.x;
+  a.n_rowtiles = (int)tiles.y;
+  a.n_members = (int)tiles.z;
+  const long long T = (long long)tiles.x * tiles.y * tiles.z;
+  dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
   static bool attr_set = false;
   const size_t sm = tc::smem_bytes<NT>();
   if (!attr_set) {

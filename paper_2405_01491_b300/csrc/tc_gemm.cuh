@@ -5,10 +5,12 @@
 //                      ring guarded by full/empty mbarriers
 //   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (K = 16 each) per stage, accumulator in TMEM
 //                      (128 lanes x NT fp32 columns); tcgen05.commit frees the stage
-//   warps 2-5          epilogue: tcgen05.ld 32 lanes x 16 columns at a time (warp w reads TMEM lane
-//                      quarter w % 4), fused bias/CELU, CELU', output-layer dot, store
-// Every mbarrier wait is bounded; on timeout the CTA posts FNN_E_TIMEOUT, drains what it issued,
-// frees its TMEM and returns.
+//   warps 2-17         epilogue: tcgen05.ld 32 lanes x 16 columns at a time (warp w reads TMEM lane
+//                      quarter w % 4; the four warps of a quarter take every fourth 16-column chunk),
+//                      fused bias/CELU, CELU', output-layer dot, store
+// Persistent: one CTA per SM walks the tile grid; two TMEM accumulators overlap the epilogue of one
+// tile with the MMAs of the next.  Every mbarrier wait is bounded; on timeout the CTA posts
+// FNN_E_TIMEOUT, drains what it issued, frees its TMEM and returns.
 #pragma once
 
 #include <cuda.h>
@@ -23,7 +25,8 @@ constexpr int STAGES = 4;
 constexpr int BM = 128;         // rows per tile (UMMA M)
 constexpr int BK = 64;          // K per stage: 64 bf16 = one 128-byte swizzle row
 constexpr int TMEM_COLS = 256;  // accumulator columns allocated (NT <= 256)
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 16;   // four per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 2000000000LL;  // clock64 cycles (about a second) before a wait gives up
 
 enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_F32 = 3 };
@@ -131,6 +134,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 struct Args {
   int K;                       // reduction length
   int N;                       // valid output columns of the whole product
+  int n_ntiles, n_rowtiles, n_members;  // tile grid: t -> (n tile fastest, row tile, member)
   int a_by_member;             // A's middle coordinate = member (else 0)
   int b_by_member;             // B's group coordinate = member * 7 + element (else element)
   const int32_t *tile_elem;    // element of each 128-row tile (-1: skip)
@@ -152,7 +156,9 @@ template <int NT>
 struct Smem {
   __nv_bfloat16 A[STAGES][BM * BK];
   __nv_bfloat16 B[STAGES][NT * BK];
-  uint64_t full[STAGES], empty[STAGES], done;
+  alignas(16) float vec[2][NT];  // bias and output-layer weights of the tile being drained
+  float ypart[4][BM];            // output-layer partial sums of the four warps of each lane quarter
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin;
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -164,31 +170,59 @@ constexpr size_t smem_bytes() {
 
 __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z / CELU_ALPHA) - 1.f); }
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h / CELU_ALPHA; }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
+// OR of a predicate over the epilogue threads (named barrier 1): keeps their control flow uniform
+__device__ __forceinline__ bool epi_any(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "n"(32 * EPI_WARPS)
+      : "memory");
+  return r != 0;
+}
 
+// tile t of the flattened grid -> (n tile, row tile, member); false when the row tile is padding
+__device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &rt, int &m, int &e) {
+  nt = t % p.n_ntiles;
+  int rest = t / p.n_ntiles;
+  rt = rest % p.n_rowtiles;
+  m = rest / p.n_rowtiles;
+  e = p.tile_elem[rt];
+  return e >= 0;
+}
+
+// Persistent: one CTA per SM walks tiles t = blockIdx.x, + gridDim.x, ...  Two TMEM accumulators
+// (columns [0, 256) and [256, 512)) let the epilogue drain tile i while the MMAs of tile i+1 run.
 template <int NT, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
-  const int e = p.tile_elem[blockIdx.y];
-  if (e < 0) return;
   extern __shared__ uint8_t smem_raw[];
   Smem<NT> &S = *reinterpret_cast<Smem<NT> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = blockIdx.z;
-  const int row0 = blockIdx.y * BM, n0 = blockIdx.x * NT;
   const int nkb = (p.K + BK - 1) / BK;
+  const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
+  volatile int *abort_flag = &S.abort_flag;
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
-    mbar_init(&S.done, 1);
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&S.acc_full[a], 1);
+      mbar_init(&S.acc_empty[a], EPI_WARPS);   // one arrival per epilogue warp
+    }
+    mbar_init(&S.fin, 1);
     S.abort_flag = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(&S.tmem_base, TMEM_COLS);
+    tmem_alloc(&S.tmem_base, 2 * TMEM_COLS);
     tmem_relinquish();
   }
   fence_before();
@@ -197,57 +231,95 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = S.tmem_base;
 
   if (warp == 0) {
-    if (lane == 0) {  // ---- TMA producer
-      const int a_mid = p.a_by_member ? m : 0;
-      const int b_grp = p.b_by_member ? m * NE + e : e;
-      int issued = 0;
-      for (int kb = 0; kb < nkb; kb++) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&S.empty[s], ((kb / STAGES) - 1) & 1)) {
-          S.abort_flag = 1;
-          break;
+    if (lane == 0) {  // ---- TMA producer: one continuous stage ring across this CTA's tiles
+      long long g = 0, issued = 0;
+      for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
+        int nt, rt, m, e;
+        if (!tile_coords(p, t, nt, rt, m, e)) continue;
+        const int a_mid = p.a_by_member ? m : 0;
+        const int b_grp = p.b_by_member ? m * NE + e : e;
+        for (int kb = 0; kb < nkb; kb++, g++) {
+          const int s = (int)(g % STAGES);
+          if (g >= STAGES && !mbar_wait(&S.empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BK * 2));
+          tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
+          tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, nt * NT, b_grp);
+          issued = g + 1;
         }
-        if (*(volatile int *)&S.abort_flag) break;
-        mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BK * 2));
-        tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, row0);
-        tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, n0, b_grp);
-        issued = kb + 1;
       }
       // drain: every issued load must land before the CTA can exit
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; kb++)
-        if (!mbar_wait(&S.full[kb % STAGES], (kb / STAGES) & 1)) S.abort_flag = 1;
+      for (long long q = (issued > STAGES ? issued - STAGES : 0); q < issued; q++)
+        if (!mbar_wait(&S.full[q % STAGES], (uint32_t)((q / STAGES) & 1))) *abort_flag = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
       const uint32_t idesc = idesc_bf16(BM, NT);
-      for (int kb = 0; kb < nkb; kb++) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&S.full[s], (kb / STAGES) & 1)) {
-          S.abort_flag = 1;
+      long long g = 0;
+      int cnt = 0;
+      for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
+        int nt, rt, m, e;
+        if (!tile_coords(p, t, nt, rt, m, e)) continue;
+        const int a = cnt & 1;
+        if (cnt >= 2 && !mbar_wait(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
+          *abort_flag = 1;
           break;
         }
-        if (*(volatile int *)&S.abort_flag) break;
         fence_after();
-        const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
+        const uint32_t d = tmem + (uint32_t)(a * TMEM_COLS);
+        for (int kb = 0; kb < nkb; kb++, g++) {
+          const int s = (int)(g % STAGES);
+          if (!mbar_wait(&S.full[s], (uint32_t)((g / STAGES) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          fence_after();
+          const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
-        for (int k = 0; k < BK / 16; k++)
-          mma_bf16(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
-        mma_commit(&S.empty[s]);
+          for (int k = 0; k < BK / 16; k++)
+            mma_bf16(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+          mma_commit(&S.empty[s]);
+        }
+        if (*abort_flag) break;
+        mma_commit(&S.acc_full[a]);  // accumulator a complete once these MMAs finish
+        cnt++;
       }
-      mma_commit(&S.done);  // arrives once every MMA issued above has completed
+      // every MMA issued above must be complete before TMEM can be released
+      mma_commit(&S.fin);
+      if (!mbar_wait(&S.fin, 0)) *abort_flag = 1;
     }
-  } else {  // ---- epilogue warps 2..5
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&S.done, 0));
-    fence_after();
-    if (!ok) S.abort_flag = 1;
-    const int q = warp & 3;
+  } else {  // ---- epilogue warps 2 .. 2 + EPI_WARPS - 1
+    const int q = warp & 3;                 // TMEM lane quarter this warp may read
+    const int part = (warp - 2) >> 2;       // which of the quarter's four warps: chunks part, part + 4, ...
     const int r = q * 32 + lane;
-    const long long row = (long long)row0 + r;
-    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
-    float ysum = 0.f;
-    if (ok) {
+    const int et = threadIdx.x - 64;        // 0 .. 32 * EPI_WARPS - 1
+    int cnt = 0;
+    for (int t = blockIdx.x; t < T; t += gridDim.x) {
+      int nt, rt, m, e;
+      if (!tile_coords(p, t, nt, rt, m, e)) continue;
+      const int a = cnt & 1;
+      const int n0 = nt * NT;
+      // stage this tile's bias (and output-layer) vectors while the MMAs run
+      epi_sync();
+      if (EPI == EPI_BIAS_CELU || EPI == EPI_L3)
+        for (int c = et; c < NT; c += 32 * EPI_WARPS) {
+          S.vec[0][c] = (n0 + c < p.N) ? p.bias[e * p.bias_estride + m * p.bias_mstride + n0 + c] : 0.f;
+          if (EPI == EPI_L3) S.vec[1][c] = (n0 + c < p.N) ? p.w4[e * p.w4_estride + m * p.w4_mstride + n0 + c] : 0.f;
+        }
+      epi_sync();
+      const bool failed = epi_any(!mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1)));
+      fence_after();
+      if (failed) {
+        *abort_flag = 1;
+        break;
+      }
+      const long long row = (long long)rt * BM + r;
+      const uint32_t tbase = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)(q * 32) << 16);
+      float ysum = 0.f;
 #pragma unroll 1
-      for (int c = 0; c < NT; c += 16) {
+      for (int c = 16 * part; c < NT; c += 64) {
         float v[16];
         tmem_ld16(tbase + c, v);
         const int n = n0 + c;
@@ -260,19 +332,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                 make_float4(v[j] * p.scale, v[j + 1] * p.scale, v[j + 2] * p.scale, v[j + 3] * p.scale);
         } else {
           __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + row * p.ldo + m * p.o_mstride + n;
-          alignas(16) __nv_bfloat16 ob[16];
+          float f[16];
           if (EPI == EPI_BIAS_CELU) {
-            const float *b = p.bias + e * p.bias_estride + m * p.bias_mstride + n;
 #pragma unroll
-            for (int j = 0; j < 16; j++) ob[j] = __float2bfloat16(celu_f(v[j] + b[j]));
+            for (int j = 0; j < 16; j += 4) {
+              const float4 b = *reinterpret_cast<const float4 *>(&S.vec[0][c + j]);
+              f[j] = celu_f(v[j] + b.x);
+              f[j + 1] = celu_f(v[j + 1] + b.y);
+              f[j + 2] = celu_f(v[j + 2] + b.z);
+              f[j + 3] = celu_f(v[j + 3] + b.w);
+            }
           } else if (EPI == EPI_L3) {
-            const float *b = p.bias + e * p.bias_estride + m * p.bias_mstride + n;
-            const float *w = p.w4 + e * p.w4_estride + m * p.w4_mstride + n;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-              float z = v[j] + b[j];
-              ysum += celu_f(z) * w[j];
-              ob[j] = __float2bfloat16(p.scale * w[j] * (z > 0.f ? 1.f : __expf(z / CELU_ALPHA)));
+              const float z = v[j] + S.vec[0][c + j], w = S.vec[1][c + j];
+              const float ez = __expf(fminf(z, 0.f) / CELU_ALPHA);
+              ysum += (z > 0.f ? z : CELU_ALPHA * (ez - 1.f)) * w;
+              f[j] = p.scale * w * (z > 0.f ? 1.f : ez);
             }
           } else {  // EPI_DCELU
             const __nv_bfloat16 *h = p.aux + row * p.ldaux + m * p.aux_mstride + n;
@@ -280,21 +356,33 @@ __global__ void __launch_bounds__(THREADS, 1)
             *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(h);
             *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(h + 8);
 #pragma unroll
-            for (int j = 0; j < 16; j++) ob[j] = __float2bfloat16(v[j] * dcelu_h(__bfloat162float(hb[j])));
+            for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(__bfloat162float(hb[j]));
           }
+          alignas(16) __nv_bfloat162 ob[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) ob[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
           *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(ob);
-          *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(ob + 8);
+          *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(ob + 4);
         }
       }
-      if (EPI == EPI_L3) p.ypart[(row * p.M + m) * 4] = ysum;
+      if (EPI == EPI_L3) {
+        S.ypart[part][r] = ysum;
+        epi_sync();
+        if (part == 0) p.ypart[(row * p.M + m) * 4] = S.ypart[0][r] + S.ypart[1][r] + S.ypart[2][r] + S.ypart[3][r];
+      }
+      // accumulator a may be overwritten once every epilogue warp has read it
+      fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.acc_empty[a])) : "memory");
+      cnt++;
     }
   }
   fence_before();
   __syncthreads();
-  if (S.abort_flag && threadIdx.x == 0) post_status(p.st, FNN_E_TIMEOUT, blockIdx.y);
+  if (*abort_flag && threadIdx.x == 0) post_status(p.st, FNN_E_TIMEOUT, blockIdx.x);
   if (warp == 1) {
     fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, 2 * TMEM_COLS);
   }
 }
 
