@@ -30,6 +30,12 @@ METRIC = "energy+force atom-evals/s (23.6k-atom box, FP32 vs BF16); serve p50/p9
 UNIT = "atom-evals/s"
 WORKLOAD = ("mix23558: 23,558-atom periodic box, 62.2 A cube, H/C/N/O/S = .50/.30/.08/.10/.02, d_min 0.95 A, "
             "seed 3; 8-member random-init ensemble (seeded Xavier); neighbour list rebuilt every step (skin 0)")
+PRECISION_NOTE = {
+    "fp32x3": "FP32-accurate networks on tcgen05: operands split into bf16 hi + lo, hi*hi + hi*lo + lo*hi "
+              "accumulated in FP32; AEV, reductions and adjoint in FP32/FP64",
+    "fp32": "networks on SIMT FP32 FFMA",
+    "bf16": "networks in BF16 on tcgen05 with FP32 accumulation",
+}
 FFMA_LANES_PER_SM = 128          # FP32 FMA lanes per SM
 N_SM = 148
 L2_FLUSH_BYTES = 256 << 20       # larger than the 126 MB L2
@@ -50,14 +56,14 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
     """Algorithmic work of one launch of a kernel: (bound, amount, unit) or None."""
     if name == "aev_forward":       # positions once, list entries (index + shift), the AEV row written
         return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B"
-    if name == "aev_forward_bf16":  # the same with a bf16 AEV row
-        return "hbm", n_atoms * (16 + 2016) + nnz * 8, "B"
+    if name in ("aev_forward_bf16", "aev_forward_x3"):  # bf16 AEV row (x3: hi and lo rows)
+        return "hbm", n_atoms * (16 + (4032 if name.endswith("x3") else 2016)) + nnz * 8, "B"
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
         return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
-    m = re.match(r"(f32|bf16|fp8)_(l[123])_(fwd|bwd)", name)
+    m = re.match(r"(f32|bf16|fp8|x3)_(l[123])_(fwd|bwd)", name)
     if m:
-        flops = 2.0 * gemm[m.group(2)] * M * n_atoms
+        flops = 2.0 * gemm[m.group(2)] * M * n_atoms * (3 if m.group(1) == "x3" else 1)
         return ("alu" if m.group(1) == "f32" else "tensor"), flops, "FLOP"
     if name in ("pairs_count", "pairs_fill"):
         return "hbm", n_atoms * 16 + (nnz * 8 if name == "pairs_fill" else 0), "B"
@@ -241,9 +247,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fnn", choices=["fnn", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
+    ap.add_argument("--precision", default="fp32x3", choices=["fp32", "fp32x3", "bf16", "fp8"],
                     help="form whose throughput is the headline value")
-    ap.add_argument("--forms", default="fp32,bf16", help="forms timed and reported (comma separated)")
+    ap.add_argument("--forms", default="fp32x3,fp32,bf16", help="forms timed and reported (comma separated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -335,8 +341,9 @@ def main():
     line = {"metric": METRIC, "value": world * s.n_atoms / (head["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp32x3": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "members": M, "precision": args.precision,
+                       "precision_note": PRECISION_NOTE.get(args.precision, ""),
                        "list_entries": nnz, "parallelism": f"replicas x{world}",
                        "l2": "flushed before every timed step (256 MB write outside the step's CUDA events)"},
             "roofline": roof, "gpu_launches": int(head["launches"]),

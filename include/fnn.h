@@ -65,7 +65,10 @@ typedef enum {
 typedef enum {
   FNN_FP32 = 0, /* network GEMMs in FP32 (SIMT FFMA), FP32 accumulation */
   FNN_BF16 = 1, /* network GEMMs in BF16 on tcgen05 tensor cores, FP32 accumulation */
-  FNN_FP8 = 2   /* network GEMMs in FP8 e4m3 with per-layer scales, FP32 accumulation */
+  FNN_FP8 = 2,  /* network GEMMs in FP8 e4m3 with per-layer scales, FP32 accumulation */
+  FNN_FP32X3 = 3 /* FP32-accurate network GEMMs on tcgen05 tensor cores: every operand split into
+                    bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated in FP32 (relative error
+                    of a product about 2^-16, within the FP32 tolerances of the energies and forces) */
 } fnn_precision;
 
 /* Symmetry-function constants and ensemble size.  fnn_config_default() fills

@@ -6,12 +6,14 @@
 //
 // Forward, radial: for each element segment, lane (h, k) = (lane / 16, lane % 16) sums shift k
 // over every other neighbour; one shuffle joins the halves; 16 lanes write 64 contiguous bytes.
-// Forward, angular: element-pair blocks p = (a <= b) in slot order.  Each lane evaluates one
-// triplet (4 section powers, 8 radial Gaussians times the switch product) into a shared staging
-// row; then lane (m, s) = (lane / 4, lane % 4) accumulates sum_t pow_s(t) * gauss_m(t) in a
-// register and writes its slot: one coalesced 128-byte store per block.
-// Adjoint: same staging; the radial and angular partials are chained to dE/dd per neighbour in
-// shared memory, then scattered to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
+// Forward, angular: all unordered pairs j < k of the element-sorted angular list in batches of 32.
+// Each lane evaluates one triplet (4 section powers, 8 radial Gaussians times the switch product)
+// into a shared staging row; then lane (m, s) = (lane / 4, lane % 4) sums pow_s(t) * gauss_m(t)
+// over the batch, keeping runs of equal element pair in a register and flushing them to a per-warp
+// accumulator of the 896 angular slots, stored with coalesced writes at the end.
+// Adjoint: same staging and enumeration; per triplet the lane reads its pair's 32 gradient slots
+// from a padded shared row, chains the partials to dE/dd per neighbour in shared memory, then the
+// warp scatters them to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
 #include <cuda_bf16.h>
 
 #include "fnn_internal.cuh"
@@ -28,17 +30,28 @@ __device__ __forceinline__ float exp2f_fast(float x) {
   return y;
 }
 
-struct WarpStage {
+// per-warp staging of one centre atom's neighbours, bucketed by element
+struct NbrStage {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
   float rfc[RAD_CAP];            // radial switch fc(r; rc_rad)
   int rj[RAD_CAP];               // neighbour atom
   unsigned char re[RAD_CAP];     // neighbour element
   unsigned char aidx[ANG_CAP];   // angular entry -> radial entry
+  unsigned char ae[ANG_CAP];     // angular entry element
   float afc[ANG_CAP];            // angular switch fc(r; rc_ang)
   float adfc[ANG_CAP];           // its derivative (adjoint)
-  float stage[32][13];           // per-triplet factors
-  float gacc[RAD_CAP][3];        // dE/dd per radial entry (adjoint)
-  float grad[NRAD];              // radial part of the incoming dE/dAEV row (adjoint)
+};
+constexpr int GSTRIDE = 36;      // padded row of one element pair's 32 angular slots (distinct banks per pair)
+struct FwdStage {
+  NbrStage nb;
+  float stage[32][13];           // per-triplet factors: 4 section powers, 8 Gaussians x switches, pair index
+  float acc[NPAIR * 32];         // angular accumulators of the atom
+};
+struct AdjStage {
+  NbrStage nb;
+  float gacc[RAD_CAP][3];        // dE/dd per radial entry
+  float grad[NRAD];              // radial part of the incoming dE/dAEV row
+  float gang[NPAIR * GSTRIDE];   // angular part, one padded row per element pair
 };
 
 struct StageArgs {
@@ -54,7 +67,7 @@ struct StageArgs {
 // Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
 // FNN_E_CAPACITY) when a list overflows.  On return cnt_*/off_* hold per-element counts and
 // segment starts (warp-uniform).
-__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, WarpStage &S, int cnt_r[NE],
+__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStage &S, int cnt_r[NE],
                                 int off_r[NE + 1], int cnt_a[NE], int off_a[NE + 1], bool want_dfc,
                                 DevStatus *st) {
   int lane = threadIdx.x & 31;
@@ -139,6 +152,7 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, W
     }
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
+      S.ae[pa] = (unsigned char)e;
       S.afc[pa] = 0.5f * cospif(r / P.rc_ang) + 0.5f;
       if (want_dfc) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r / P.rc_ang);
     }
@@ -159,18 +173,8 @@ __device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
   k = t - jj * (2 * n - jj - 1) / 2 + jj + 1;
 }
 
-__device__ __forceinline__ void triplet_of(int t, int a, int b, int na, int nb, const int off_a[NE + 1], int &ja,
-                                           int &ka) {
-  if (a == b) {
-    int jj, kk;
-    tri_index(t, na, jj, kk);
-    ja = off_a[a] + jj;
-    ka = off_a[a] + kk;
-  } else {
-    ja = off_a[a] + t / nb;
-    ka = off_a[b] + t % nb;
-  }
-}
+// slot block of the element pair (a, b), a <= b, in row-major upper-triangle order
+__device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
 template <typename OutT>
 __device__ __forceinline__ void store_out(OutT *p, float v);
@@ -183,27 +187,38 @@ struct AevFwdArgs {
   StageArgs sa;
   AevParams P;
   float *out;             // [rows][1008]
+  __nv_bfloat16 *out_lo;  // low bf16 half of a split output, or NULL
   const int32_t *inv;     // padded row -> atom (-1 padding); NULL = rows are atoms
   const int32_t *meta;    // META_NPAD when inv != NULL
   int n_atoms;
   DevStatus *st;
 };
 
+// rounding residual of a bf16 store (the lo term of a hi / lo split)
+__device__ __forceinline__ void store_lo(__nv_bfloat16 *lo, size_t c, float v) {
+  if (lo) lo[c] = __float2bfloat16(v - __bfloat162float(__float2bfloat16(v)));
+}
+
 template <typename OutT>
 __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
-  __shared__ WarpStage smem[AEV_WARPS];
+  __shared__ FwdStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  WarpStage &S = smem[wl];
+  FwdStage &W = smem[wl];
+  NbrStage &S = W.nb;
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
   for (int row = wg; row < nrows; row += nw) {
     OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
+    __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
     int i = A.inv ? A.inv[row] : row;
     int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
     bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, false, A.st);
     if (!ok) {
-      for (int c = lane; c < NAEV; c += 32) store_out<OutT>(out + c, 0.f);
+      for (int c = lane; c < NAEV; c += 32) {
+        store_out<OutT>(out + c, 0.f);
+        store_lo(lo, c, 0.f);
+      }
       __syncwarp();
       continue;
     }
@@ -219,49 +234,63 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
           acc += __expf(-P.eta_r * dr * dr) * S.rfc[t];
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
-        if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc);
+        if (lane < 16) {
+          store_out<OutT>(out + q * NSR + k, 0.25f * acc);
+          store_lo(lo, q * NSR + k, 0.25f * acc);
+        }
       }
     }
-    // ---- angular
+    // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch.
+    // The producer lane evaluates one triplet; lane (m, s) then sums pow_s * gauss_m over the batch,
+    // holding a run of equal element pair in a register and flushing it to the pair's accumulator.
     {
-      int s_my = lane & 3, m_my = lane >> 2;
-      int p = 0;
-#pragma unroll 1
-      for (int a = 0; a < NE; a++) {
-#pragma unroll 1
-        for (int b = a; b < NE; b++, p++) {
-          int na = cnt_a[a], nb = cnt_a[b];
-          int T = (a == b) ? na * (na - 1) / 2 : na * nb;
-          float acc = 0.f;
-          for (int base = 0; base < T; base += 32) {
-            int t = base + lane;
-            if (t < T) {
-              int ja, ka;
-              triplet_of(t, a, b, na, nb, off_a, ja, ka);
-              float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
-              float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) / (d1.w * d2.w);
-              float c95 = 0.95f * c;
-              float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+      const int s_my = lane & 3, m_my = lane >> 2;
+      for (int c = lane; c < NPAIR * 32; c += 32) W.acc[c] = 0.f;
+      const int n = off_a[NE];
+      const int T = n * (n - 1) / 2;
+      int run_p = -1;
+      float racc = 0.f;
+      for (int base = 0; base < T; base += 32) {
+        const int t = base + lane;
+        if (t < T) {
+          int ja, ka;
+          tri_index(t, n, ja, ka);
+          const float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) / (d1.w * d2.w);
+          const float c95 = 0.95f * c;
+          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
 #pragma unroll
-              for (int s = 0; s < NSZ; s++) {
-                float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
-                S.stage[lane][s] = exp2f_fast(P.zeta * __log2f(base_s));
-              }
-              float rbar = 0.5f * (d1.w + d2.w);
-              float fcc = 2.f * S.afc[ja] * S.afc[ka];
-#pragma unroll
-              for (int m = 0; m < NSA; m++) {
-                float dr = rbar - P.shf_a[m];
-                S.stage[lane][4 + m] = __expf(-P.eta_a * dr * dr) * fcc;
-              }
-            }
-            __syncwarp();
-            int nt = min(32, T - base);
-            for (int q = 0; q < nt; q++) acc += S.stage[q][s_my] * S.stage[q][4 + m_my];
-            __syncwarp();
+          for (int s = 0; s < NSZ; s++) {
+            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+            W.stage[lane][s] = exp2f_fast(P.zeta * __log2f(base_s));
           }
-          store_out<OutT>(out + NRAD + p * 32 + lane, acc);
+          const float rbar = 0.5f * (d1.w + d2.w);
+          const float fcc = 2.f * S.afc[ja] * S.afc[ka];
+#pragma unroll
+          for (int m = 0; m < NSA; m++) {
+            const float dr = rbar - P.shf_a[m];
+            W.stage[lane][4 + m] = __expf(-P.eta_a * dr * dr) * fcc;
+          }
+          W.stage[lane][12] = __int_as_float(pair_of(S.ae[ja], S.ae[ka]));   // e_j <= e_k: sorted list
         }
+        __syncwarp();
+        const int nt = min(32, T - base);
+        for (int q = 0; q < nt; q++) {
+          const int p = __float_as_int(W.stage[q][12]);
+          if (p != run_p) {
+            if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+            racc = 0.f;
+            run_p = p;
+          }
+          racc += W.stage[q][s_my] * W.stage[q][4 + m_my];
+        }
+        __syncwarp();
+      }
+      if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+      __syncwarp();
+      for (int c = lane; c < NPAIR * 32; c += 32) {
+        store_out<OutT>(out + NRAD + c, W.acc[c]);
+        store_lo(lo, NRAD + c, W.acc[c]);
       }
     }
     __syncwarp();
@@ -282,9 +311,10 @@ struct AevAdjArgs {
 };
 
 __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
-  __shared__ WarpStage smem[AEV_WARPS];
+  __shared__ AdjStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  WarpStage &S = smem[wl];
+  AdjStage &W = smem[wl];
+  NbrStage &S = W.nb;
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
@@ -298,7 +328,8 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
     int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
     if (!stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st)) continue;
     const float *G = A.gaev + (size_t)row * NAEV;
-    for (int c = lane; c < NRAD; c += 32) S.grad[c] = G[c];
+    for (int c = lane; c < NRAD; c += 32) W.grad[c] = G[c];
+    for (int p = 0; p < NPAIR; p++) W.gang[p * GSTRIDE + lane] = G[NRAD + p * 32 + lane];
     __syncwarp();
     // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
     int nrad = off_r[NE];
@@ -313,86 +344,74 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
       for (int k = 0; k < NSR; k++) {
         float dr = r - P.shf_r[k];
         float gk = __expf(-P.eta_r * dr * dr);
-        dEdr += S.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
+        dEdr += W.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
       }
       float f = dEdr / r;
-      S.gacc[t][0] = f * d.x;
-      S.gacc[t][1] = f * d.y;
-      S.gacc[t][2] = f * d.z;
+      W.gacc[t][0] = f * d.x;
+      W.gacc[t][1] = f * d.y;
+      W.gacc[t][2] = f * d.z;
     }
     __syncwarp();
-    // ---- angular
-    int p = 0;
-#pragma unroll 1
-    for (int a = 0; a < NE; a++) {
-#pragma unroll 1
-      for (int b = a; b < NE; b++, p++) {
-        int na = cnt_a[a], nb = cnt_a[b];
-        int T = (a == b) ? na * (na - 1) / 2 : na * nb;
-        if (T == 0) continue;
-        float Gb[32];
-        {
-          float mine = G[NRAD + p * 32 + lane];
+    // ---- angular: the same flat enumeration as the forward pass, one triplet per lane
+    {
+      const int n = off_a[NE];
+      const int T = n * (n - 1) / 2;
+      for (int base = 0; base < T; base += 32) {
+        const int t = base + lane;
+        if (t < T) {
+          int ja, ka;
+          tri_index(t, n, ja, ka);
+          const int p = pair_of(S.ae[ja], S.ae[ka]);
+          const float *Gp = &W.gang[p * GSTRIDE];
+          const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
+          const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
+          const float r1 = d1.w, r2 = d2.w;
+          const float inv12 = 1.f / (r1 * r2);
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
+          const float c95 = 0.95f * c;
+          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+          const float ds95 = -0.9025f * c / s95;   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
+          float fs[NSZ], dfs[NSZ];
 #pragma unroll
-          for (int q = 0; q < 32; q++) Gb[q] = __shfl_sync(FULL, mine, q);
-        }
-        for (int base = 0; base < T; base += 32) {
-          int t = base + lane;
-          if (t < T) {
-            int ja, ka;
-            triplet_of(t, a, b, na, nb, off_a, ja, ka);
-            int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
-            float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
-            float r1 = d1.w, r2 = d2.w;
-            float inv12 = 1.f / (r1 * r2);
-            float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
-            float c95 = 0.95f * c;
-            float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
-            float ds95 = -0.9025f * c / s95;   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
-            float fs[NSZ], dfs[NSZ];
-#pragma unroll
-            for (int s = 0; s < NSZ; s++) {
-              float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
-              float f = exp2f_fast(P.zeta * __log2f(base_s));
-              fs[s] = f;
-              dfs[s] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
-            }
-            float rbar = 0.5f * (r1 + r2);
-            float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
-#pragma unroll
-            for (int m = 0; m < NSA; m++) {
-              float dr = rbar - P.shf_a[m];
-              float gm = __expf(-P.eta_a * dr * dr);
-              float dgm = -2.f * P.eta_a * dr * gm;
-#pragma unroll
-              for (int s = 0; s < NSZ; s++) {
-                H[s] += Gb[m * NSZ + s] * gm;
-                Hd[s] += Gb[m * NSZ + s] * dgm;
-              }
-            }
-            float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
-            float C = f1 * f2;
-            float sH = 0.f, sdH = 0.f, sHd = 0.f;
-#pragma unroll
-            for (int s = 0; s < NSZ; s++) {
-              sH += fs[s] * H[s];
-              sdH += dfs[s] * H[s];
-              sHd += fs[s] * Hd[s];
-            }
-            float dEdc = 2.f * C * sdH;
-            float dEdrbar = 2.f * C * sHd;
-            float dEdC = 2.f * sH;
-            float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
-            float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
-            float a1 = dEdr1 / r1 - dEdc * c / (r1 * r1), b1 = dEdc * inv12;
-            float a2 = dEdr2 / r2 - dEdc * c / (r2 * r2);
-            atomicAdd(&S.gacc[rj1][0], a1 * d1.x + b1 * d2.x);
-            atomicAdd(&S.gacc[rj1][1], a1 * d1.y + b1 * d2.y);
-            atomicAdd(&S.gacc[rj1][2], a1 * d1.z + b1 * d2.z);
-            atomicAdd(&S.gacc[rj2][0], a2 * d2.x + b1 * d1.x);
-            atomicAdd(&S.gacc[rj2][1], a2 * d2.y + b1 * d1.y);
-            atomicAdd(&S.gacc[rj2][2], a2 * d2.z + b1 * d1.z);
+          for (int s = 0; s < NSZ; s++) {
+            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+            const float f = exp2f_fast(P.zeta * __log2f(base_s));
+            fs[s] = f;
+            dfs[s] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
           }
+          const float rbar = 0.5f * (r1 + r2);
+          float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
+#pragma unroll
+          for (int m = 0; m < NSA; m++) {
+            const float dr = rbar - P.shf_a[m];
+            const float gm = __expf(-P.eta_a * dr * dr);
+            const float dgm = -2.f * P.eta_a * dr * gm;
+            const float4 g4 = *reinterpret_cast<const float4 *>(Gp + m * NSZ);
+            H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
+            Hd[0] += g4.x * dgm; Hd[1] += g4.y * dgm; Hd[2] += g4.z * dgm; Hd[3] += g4.w * dgm;
+          }
+          const float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
+          const float C = f1 * f2;
+          float sH = 0.f, sdH = 0.f, sHd = 0.f;
+#pragma unroll
+          for (int s = 0; s < NSZ; s++) {
+            sH += fs[s] * H[s];
+            sdH += dfs[s] * H[s];
+            sHd += fs[s] * Hd[s];
+          }
+          const float dEdc = 2.f * C * sdH;
+          const float dEdrbar = 2.f * C * sHd;
+          const float dEdC = 2.f * sH;
+          const float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
+          const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
+          const float a1 = dEdr1 / r1 - dEdc * c / (r1 * r1), b1 = dEdc * inv12;
+          const float a2 = dEdr2 / r2 - dEdc * c / (r2 * r2);
+          atomicAdd(&W.gacc[rj1][0], a1 * d1.x + b1 * d2.x);
+          atomicAdd(&W.gacc[rj1][1], a1 * d1.y + b1 * d2.y);
+          atomicAdd(&W.gacc[rj1][2], a1 * d1.z + b1 * d2.z);
+          atomicAdd(&W.gacc[rj2][0], a2 * d2.x + b1 * d1.x);
+          atomicAdd(&W.gacc[rj2][1], a2 * d2.y + b1 * d1.y);
+          atomicAdd(&W.gacc[rj2][2], a2 * d2.z + b1 * d1.z);
         }
       }
     }
@@ -403,7 +422,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
 #pragma unroll
     for (int q = 0; q < 9; q++) w[q] = 0.f;
     for (int t = lane; t < nrad; t += 32) {
-      float g0 = S.gacc[t][0], g1 = S.gacc[t][1], g2 = S.gacc[t][2];
+      float g0 = W.gacc[t][0], g1 = W.gacc[t][1], g2 = W.gacc[t][2];
       int j = S.rj[t];
       atomicAdd(&A.F[3 * (size_t)j + 0], -g0);
       atomicAdd(&A.F[3 * (size_t)j + 1], -g1);
@@ -470,6 +489,7 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   a.sa = stage_args(sys, nl);
   a.P = ctx->aev;
   a.out = out;
+  a.out_lo = nullptr;
   a.inv = inv;
   a.meta = nl->meta;
   a.n_atoms = sys->n_atoms;
@@ -484,11 +504,12 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
 }
 
 fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, __nv_bfloat16 *out,
-                                   const int32_t *inv, cudaStream_t s) {
+                                   __nv_bfloat16 *out_lo, const int32_t *inv, cudaStream_t s) {
   AevFwdArgs a;
   a.sa = stage_args(sys, nl);
   a.P = ctx->aev;
   a.out = reinterpret_cast<float *>(out);
+  a.out_lo = out_lo;
   a.inv = inv;
   a.meta = nl->meta;
   a.n_atoms = sys->n_atoms;
@@ -496,7 +517,7 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
   int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
   if (rows == 0) return FNN_OK;
   {
-    FNN_KERNEL(ctx, "aev_forward_bf16", s);
+    FNN_KERNEL(ctx, out_lo ? "aev_forward_x3" : "aev_forward_bf16", s);
     k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_bf16");

@@ -44,15 +44,21 @@ bool encode3d(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// One half (hi or lo) of the bf16 operands: the BF16 form uses the hi half only (bf16(x) is exactly the
+// hi term of the split), the three-term FP32 form uses both.
+struct Half {
+  __nv_bfloat16 *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
+  CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
+  __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+};
+
 struct TcState {
   int M = 0;
   __nv_bfloat16 *wbuf = nullptr;
-  __nv_bfloat16 *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
-  CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
   __nv_bfloat16 *abuf = nullptr;
   size_t rows = 0;
-  __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
-  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+  Half h[2];   // [0] hi, [1] lo
 };
 
 TcState *state(fnn_ctx *ctx) {
@@ -60,9 +66,9 @@ TcState *state(fnn_ctx *ctx) {
   return static_cast<TcState *>(ctx->w.tc);
 }
 
-template <int NT, int EPI>
-fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B, tc::Args a,
-                  dim3 tiles, cudaStream_t s) {
+template <int NT, int EPI, bool SPLIT>
+fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B,
+                  const CUtensorMap &A_lo, const CUtensorMap &B_lo, tc::Args a, dim3 tiles, cudaStream_t s) {
   // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
   a.n_ntiles = (int)tiles.x;
   a.n_rowtiles = (int)tiles.y;
@@ -72,11 +78,12 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CU
   static bool attr_set = false;
   const size_t sm = tc::smem_bytes<NT>();
   if (!attr_set) {
-    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma<NT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    FNN_CUDA_TRY(ctx,
+                 cudaFuncSetAttribute(tc::k_umma<NT, EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI><<<grid, tc::THREADS, sm, s>>>(A, B, a);
+  tc::k_umma<NT, EPI, SPLIT><<<grid, tc::THREADS, sm, s>>>(A, B, A_lo, B_lo, a);
   return check_launch(ctx, name);
 }
 
@@ -91,144 +98,175 @@ void free_tc(fnn_ctx *ctx) {
   ctx->w.tc = nullptr;
 }
 
-// bf16 copies of the layer matrices in the FP32 form's layouts (host arrays given in those layouts)
+// bf16 hi and lo halves of the layer matrices in the FP32 form's layouts (host arrays in those layouts):
+// hi = bf16(w), lo = bf16(w - hi)
 fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const float *W1Tcat, const float *W2,
                              const float *W2T, const float *W3, const float *W3T) {
   TcState *t = state(ctx);
   if (t->wbuf) cudaFree(t->wbuf);
   t->wbuf = nullptr;
   const size_t n1 = (size_t)NE * M * H1 * NAEV, n2 = (size_t)M * NE * H2 * H1, n3 = (size_t)M * NE * H3 * H2;
-  const size_t total = 2 * (n1 + n2 + n3);
-  std::vector<__nv_bfloat16> h(total);
-  size_t o = 0;
+  const size_t half = 2 * (n1 + n2 + n3);
+  std::vector<__nv_bfloat16> h(2 * half);
   const float *src[6] = {W1cat, W1Tcat, W2, W2T, W3, W3T};
   const size_t len[6] = {n1, n1, n2, n2, n3, n3};
-  size_t off[6];
+  size_t off[6], o = 0;
   for (int k = 0; k < 6; k++) {
     off[k] = o;
-    for (size_t i = 0; i < len[k]; i++) h[o + i] = __float2bfloat16(src[k][i]);
+    for (size_t i = 0; i < len[k]; i++) {
+      const __nv_bfloat16 hi = __float2bfloat16(src[k][i]);
+      h[o + i] = hi;
+      h[half + o + i] = __float2bfloat16(src[k][i] - __bfloat162float(hi));
+    }
     o += len[k];
   }
-  if (cudaMalloc(&t->wbuf, total * sizeof(__nv_bfloat16)) != cudaSuccess) {
+  if (cudaMalloc(&t->wbuf, 2 * half * sizeof(__nv_bfloat16)) != cudaSuccess) {
     cudaGetLastError();
     ctx->last_error = "cudaMalloc failed for bf16 weights";
     return FNN_E_OOM;
   }
-  FNN_CUDA_TRY(ctx, cudaMemcpy(t->wbuf, h.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
-  t->W1 = t->wbuf + off[0];
-  t->W1T = t->wbuf + off[1];
-  t->W2 = t->wbuf + off[2];
-  t->W2T = t->wbuf + off[3];
-  t->W3 = t->wbuf + off[4];
-  t->W3T = t->wbuf + off[5];
+  FNN_CUDA_TRY(ctx, cudaMemcpy(t->wbuf, h.data(), 2 * half * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
   t->M = M;
   const uint64_t G = (uint64_t)M * NE;
-  bool ok = encode3d(&t->mW1, t->W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 256, 1) &&
-            encode3d(&t->mW1T, t->W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2, 64,
-                     256, 1) &&
-            encode3d(&t->mW2, t->W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, H2, 1) &&
-            encode3d(&t->mW2T, t->W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, H1, 1) &&
-            encode3d(&t->mW3, t->W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 64, H3, 1) &&
-            encode3d(&t->mW3T, t->W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 64, H2, 1);
-  if (!ok) {
-    ctx->last_error = "cuTensorMapEncodeTiled failed for the weight maps";
-    return FNN_E_CUDA;
+  for (int q = 0; q < 2; q++) {
+    Half &H = t->h[q];
+    __nv_bfloat16 *base = t->wbuf + q * half;
+    H.W1 = base + off[0]; H.W1T = base + off[1]; H.W2 = base + off[2];
+    H.W2T = base + off[3]; H.W3 = base + off[4]; H.W3T = base + off[5];
+    bool ok =
+        encode3d(&H.mW1, H.W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 256, 1) &&
+        encode3d(&H.mW1T, H.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2, 64, 256,
+                 1) &&
+        encode3d(&H.mW2, H.W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, H2, 1) &&
+        encode3d(&H.mW2T, H.W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, H1, 1) &&
+        encode3d(&H.mW3, H.W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 64, H3, 1) &&
+        encode3d(&H.mW3T, H.W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 64, H2, 1);
+    if (!ok) {
+      ctx->last_error = "cuTensorMapEncodeTiled failed for the weight maps";
+      return FNN_E_CUDA;
+    }
   }
   return FNN_OK;
 }
 
-static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows) {
+static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
   TcState *t = state(ctx);
   const int M = t->M;
-  if (t->abuf && rows <= t->rows) return FNN_OK;
+  const bool have = t->abuf && rows <= t->rows && (halves == 1 || t->h[1].aev);
+  if (have) return FNN_OK;
   rows = rows + rows / 8;
   if (t->abuf) cudaFree(t->abuf);
   t->abuf = nullptr;
+  t->h[1].aev = nullptr;
   const size_t per_row = NAEV + (size_t)M * (H1 + H2 + H3 + H2 + H1);
-  if (cudaMalloc(&t->abuf, rows * per_row * sizeof(__nv_bfloat16)) != cudaSuccess) {
+  if (cudaMalloc(&t->abuf, 2 * rows * per_row * sizeof(__nv_bfloat16)) != cudaSuccess) {
     cudaGetLastError();
     ctx->last_error = "cudaMalloc failed for bf16 activations";
     return FNN_E_OOM;
   }
   t->rows = rows;
-  __nv_bfloat16 *p = t->abuf;
-  t->aev = p; p += rows * NAEV;
-  t->h1 = p; p += rows * M * H1;
-  t->h2 = p; p += rows * M * H2;
-  t->g3 = p; p += rows * M * H3;
-  t->g2 = p; p += rows * M * H2;
-  t->g1 = p;
   const uint64_t R = rows;
-  bool ok = encode3d(&t->mAev, t->aev, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 128) &&
-            encode3d(&t->mH1, t->h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128) &&
-            encode3d(&t->mH2, t->h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
-            encode3d(&t->mG3, t->g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 64, 1, 128) &&
-            encode3d(&t->mG2, t->g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
-            encode3d(&t->mG1, t->g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128);
-  if (!ok) {
-    ctx->last_error = "cuTensorMapEncodeTiled failed for the activation maps";
-    return FNN_E_CUDA;
+  for (int q = 0; q < 2; q++) {
+    Half &H = t->h[q];
+    __nv_bfloat16 *p = t->abuf + q * rows * per_row;
+    H.aev = p; p += rows * NAEV;
+    H.h1 = p; p += rows * M * H1;
+    H.h2 = p; p += rows * M * H2;
+    H.g3 = p; p += rows * M * H3;
+    H.g2 = p; p += rows * M * H2;
+    H.g1 = p;
+    bool ok = encode3d(&H.mAev, H.aev, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 128) &&
+              encode3d(&H.mH1, H.h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128) &&
+              encode3d(&H.mH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
+              encode3d(&H.mG3, H.g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 64, 1, 128) &&
+              encode3d(&H.mG2, H.g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
+              encode3d(&H.mG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128);
+    if (!ok) {
+      ctx->last_error = "cuTensorMapEncodeTiled failed for the activation maps";
+      return FNN_E_CUDA;
+    }
   }
   return FNN_OK;
 }
 
 fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, __nv_bfloat16 *out,
-                                   const int32_t *inv, cudaStream_t s);
+                                   __nv_bfloat16 *out_lo, const int32_t *inv, cudaStream_t s);
 
-// AEV (bf16) -> six tcgen05 GEMMs -> member-averaged energies; leaves dE/dAEV (fp32) in ws.gaev
-fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
-                     cudaStream_t s) {
-  if (prec != FNN_BF16) {
-    ctx->last_error = "FP8 form is not built yet";
-    return FNN_E_INVALID;
-  }
-  TcState *t = state(ctx);
-  if (!t->wbuf || t->M != ctx->w.M) {
-    ctx->last_error = "bf16 weights missing";
-    return FNN_E_STATE;
-  }
-  fnn_status st;
-  if ((st = tc_workspace(ctx, nl->pad_cap))) return st;
-  if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->aev, nl->inv, s))) return st;
+namespace {
+
+template <bool SPLIT>
+fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_t s) {
   const DeviceWeights &w = ctx->w;
+  const Half &H = t->h[0], &L = t->h[SPLIT ? 1 : 0];
   const int M = w.M;
   const unsigned tiles = (unsigned)(nl->pad_cap / ROW_TILE);
+  const char *nm[6] = {SPLIT ? "x3_l1_fwd" : "bf16_l1_fwd", SPLIT ? "x3_l2_fwd" : "bf16_l2_fwd",
+                       SPLIT ? "x3_l3_fwd" : "bf16_l3_fwd", SPLIT ? "x3_l3_bwd" : "bf16_l3_bwd",
+                       SPLIT ? "x3_l2_bwd" : "bf16_l2_bwd", SPLIT ? "x3_l1_bwd" : "bf16_l1_bwd"};
+  fnn_status st;
   tc::Args a{};
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
   a.M = M;
   // L1: all members at once
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
-  a.out = t->h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
+  a.out = H.h1; a.out_lo = L.h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch<256, tc::EPI_BIAS_CELU>(ctx, "bf16_l1_fwd", t->mAev, t->mW1, a, dim3(M, tiles, 1), s))) return st;
+  if ((st = launch<256, tc::EPI_BIAS_CELU, SPLIT>(ctx, nm[0], H.mAev, H.mW1, L.mAev, L.mW1, a, dim3(M, tiles, 1), s)))
+    return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
-  a.out = t->h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.out = H.h2; a.out_lo = L.h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
-  if ((st = launch<192, tc::EPI_BIAS_CELU>(ctx, "bf16_l2_fwd", t->mH1, t->mW2, a, dim3(1, tiles, M), s))) return st;
+  if ((st = launch<192, tc::EPI_BIAS_CELU, SPLIT>(ctx, nm[1], H.mH1, H.mW2, L.mH1, L.mW2, a, dim3(1, tiles, M), s)))
+    return st;
   // L3 + output layer
   a.K = H2; a.N = H3;
-  a.out = t->g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
+  a.out = H.g3; a.out_lo = L.g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
   a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
   a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
   a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
-  if ((st = launch<160, tc::EPI_L3>(ctx, "bf16_l3_fwd", t->mH2, t->mW3, a, dim3(1, tiles, M), s))) return st;
+  if ((st = launch<160, tc::EPI_L3, SPLIT>(ctx, nm[2], H.mH2, H.mW3, L.mH2, L.mW3, a, dim3(1, tiles, M), s)))
+    return st;
   // L3 backward
   a.K = H3; a.N = H2;
-  a.out = t->g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
-  a.aux = t->h2; a.ldaux = (long long)M * H2; a.aux_mstride = H2;
-  if ((st = launch<192, tc::EPI_DCELU>(ctx, "bf16_l3_bwd", t->mG3, t->mW3T, a, dim3(1, tiles, M), s))) return st;
+  a.out = H.g2; a.out_lo = L.g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.aux = H.h2; a.aux_lo = L.h2; a.ldaux = (long long)M * H2; a.aux_mstride = H2;
+  if ((st = launch<192, tc::EPI_DCELU, SPLIT>(ctx, nm[3], H.mG3, H.mW3T, L.mG3, L.mW3T, a, dim3(1, tiles, M), s)))
+    return st;
   // L2 backward
   a.K = H2; a.N = H1;
-  a.out = t->g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
-  a.aux = t->h1; a.ldaux = (long long)M * H1; a.aux_mstride = H1;
-  if ((st = launch<256, tc::EPI_DCELU>(ctx, "bf16_l2_bwd", t->mG2, t->mW2T, a, dim3(1, tiles, M), s))) return st;
+  a.out = H.g1; a.out_lo = L.g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
+  a.aux = H.h1; a.aux_lo = L.h1; a.ldaux = (long long)M * H1; a.aux_mstride = H1;
+  if ((st = launch<256, tc::EPI_DCELU, SPLIT>(ctx, nm[4], H.mG2, H.mW2T, L.mG2, L.mW2T, a, dim3(1, tiles, M), s)))
+    return st;
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
-  if ((st = launch<256, tc::EPI_F32>(ctx, "bf16_l1_bwd", t->mG1, t->mW1T, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
-    return st;
+  return launch<256, tc::EPI_F32, SPLIT>(ctx, nm[5], H.mG1, H.mW1T, L.mG1, L.mW1T, a,
+                                         dim3((NAEV + 255) / 256, tiles, 1), s);
+}
+
+}  // namespace
+
+// AEV (bf16, or hi/lo pairs) -> six tcgen05 GEMMs -> member-averaged energies; dE/dAEV (fp32) in ws.gaev
+fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
+                     cudaStream_t s) {
+  if (prec != FNN_BF16 && prec != FNN_FP32X3) {
+    ctx->last_error = "FP8 form is not built yet";
+    return FNN_E_INVALID;
+  }
+  const bool split = prec == FNN_FP32X3;
+  TcState *t = state(ctx);
+  if (!t->wbuf || t->M != ctx->w.M) {
+    ctx->last_error = "bf16 weights missing";
+    return FNN_E_STATE;
+  }
+  fnn_status st;
+  if ((st = tc_workspace(ctx, nl->pad_cap, split ? 2 : 1))) return st;
+  if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->h[0].aev, split ? t->h[1].aev : nullptr, nl->inv, s))) return st;
+  st = split ? run_layers<true>(ctx, t, nl, s) : run_layers<false>(ctx, t, nl, s);
+  if (st) return st;
   return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 1, E, s);
 }
 

@@ -150,6 +150,10 @@ struct Args {
   int M;
   float scale;
   DevStatus *st;
+  // three-term split (SPLIT kernels): x w ~ x_hi w_hi + x_hi w_lo + x_lo w_hi, K segments in that order;
+  // bf16 outputs are written as a hi / lo pair (out, out_lo) and the aux input is read as aux + aux_lo
+  void *out_lo;
+  const __nv_bfloat16 *aux_lo;
 };
 
 template <int NT>
@@ -197,14 +201,16 @@ __device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &
 
 // Persistent: one CTA per SM walks tiles t = blockIdx.x, + gridDim.x, ...  Two TMEM accumulators
 // (columns [0, 256) and [256, 512)) let the epilogue drain tile i while the MMAs of tile i+1 run.
-template <int NT, int EPI>
+template <int NT, int EPI, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args p) {
+    k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
   extern __shared__ uint8_t smem_raw[];
   Smem<NT> &S = *reinterpret_cast<Smem<NT> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkb = (p.K + BK - 1) / BK;
+  const int nkb_seg = (p.K + BK - 1) / BK;
+  const int nkb = SPLIT ? 3 * nkb_seg : nkb_seg;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
   volatile int *abort_flag = &S.abort_flag;
 
@@ -245,8 +251,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BK * 2));
-          tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
-          tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, nt * NT, b_grp);
+          const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
+          tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
+          tma_load_3d(S.B[s], seg == 1 ? &tmB_lo : &tmB, &S.full[s], kk * BK, nt * NT, b_grp);
           issued = g + 1;
         }
       }
@@ -351,18 +358,37 @@ __global__ void __launch_bounds__(THREADS, 1)
               f[j] = p.scale * w * (z > 0.f ? 1.f : ez);
             }
           } else {  // EPI_DCELU
-            const __nv_bfloat16 *h = p.aux + row * p.ldaux + m * p.aux_mstride + n;
+            const long long ao = row * p.ldaux + m * p.aux_mstride + n;
             alignas(16) __nv_bfloat16 hb[16];
-            *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(h);
-            *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(h + 8);
+            *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux + ao);
+            *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux + ao + 8);
+            float hv[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(__bfloat162float(hb[j]));
+            for (int j = 0; j < 16; j++) hv[j] = __bfloat162float(hb[j]);
+            if (SPLIT) {
+              *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao);
+              *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao + 8);
+#pragma unroll
+              for (int j = 0; j < 16; j++) hv[j] += __bfloat162float(hb[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(hv[j]);
           }
           alignas(16) __nv_bfloat162 ob[8];
 #pragma unroll
           for (int j = 0; j < 8; j++) ob[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
           *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(ob);
           *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(ob + 4);
+          if (SPLIT) {  // low part: the rounding residual of the high part
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const float2 hi = __bfloat1622float2(ob[j]);
+              ob[j] = __floats2bfloat162_rn(f[2 * j] - hi.x, f[2 * j + 1] - hi.y);
+            }
+            __nv_bfloat16 *ol = reinterpret_cast<__nv_bfloat16 *>(p.out_lo) + row * p.ldo + m * p.o_mstride + n;
+            *reinterpret_cast<uint4 *>(ol) = *reinterpret_cast<const uint4 *>(ob);
+            *reinterpret_cast<uint4 *>(ol + 8) = *reinterpret_cast<const uint4 *>(ob + 4);
+          }
         }
       }
       if (EPI == EPI_L3) {

@@ -138,19 +138,24 @@ def _compare(s, r, E, F, W):
     assert np.abs(W.reshape(r.virial.shape) - r.virial).max() <= 1e-4 * scale
 
 
+FP32_FORMS = ["fp32", "fp32x3"]   # SIMT FFMA, and the three-term bf16 split on tensor cores
+
+
+@pytest.mark.parametrize("precision", FP32_FORMS)
 @pytest.mark.parametrize("name,M,skin", [("gas24", 1, 0.0), ("water216", 8, 1.0), ("box1500", 2, 0.0),
                                          ("batch64", 1, 0.5)])
-def test_energy_forces_fp32_parity(fnn, name, M, skin):
+def test_energy_forces_fp32_parity(fnn, name, M, skin, precision):
     s = structure(name)
-    _, _, _, E, F, W = _energy_case(fnn, s, M, skin)
+    _, _, _, E, F, W = _energy_case(fnn, s, M, skin, precision=precision)
     r = oracle.energy_forces(s, weights(M))
     _compare(s, r, E, F, W)
 
 
-def test_energy_forces_fp32_full_size(fnn):
+@pytest.mark.parametrize("precision", FP32_FORMS)
+def test_energy_forces_fp32_full_size(fnn, precision):
     """The 23,558-atom periodic box with the 8-member ensemble, in the launch configuration the benchmark times."""
     s = structure("mix23558")
-    _, _, _, E, F, W = _energy_case(fnn, s, 8)
+    _, _, _, E, F, W = _energy_case(fnn, s, 8, precision=precision)
     r = oracle.energy_forces(s, weights(8))
     _compare(s, r, E, F, W)
 
