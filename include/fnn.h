@@ -182,6 +182,68 @@ fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t n_atoms, int32_t n_mol, 
 fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
 
 /*
+ * NVE velocity Verlet on the device (the native engine's NVE integrator, section V.D):
+ * n_steps force evaluations at x_0 .. x_{n-1}.  After evaluation k every atom does v += a dt/2
+ * (completing step k) and, unless k is the last, v += a dt/2 and x += v dt (a = F/m, masses
+ * H 1.008 C 12.011 N 14.007 O 15.999 F 18.998 S 32.06 Cl 35.45 amu, 1 kcal/mol/A/amu = 4.184e-4
+ * A/fs^2).  pos, vel: device [N][4] (w unused), updated in place (pos replaces sys->pos); the list is
+ * rebuilt before evaluations 0, rebuild_every, 2 rebuild_every, ... (use a context skin of at least
+ * the largest displacement between rebuilds).  E_hist: device [n_steps][n_mol] float64, or NULL.
+ * F: device [N][3], the forces of the last evaluation.  Asynchronous.
+ */
+fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl, fnn_precision prec,
+                      int32_t n_steps, double dt_fs, int32_t rebuild_every, double *E_hist, float *F, void *stream);
+
+/*
+ * Continuous-batching MD service (SURVEY serving form).  A scheduler thread keeps a ragged batch of
+ * structures on the device and advances all of them one velocity-Verlet step per batch step (one
+ * neighbour-list/AEV/network/adjoint pass over the whole batch); between batch steps it retires
+ * finished structures and admits queued requests, in arrival order, while the batch's estimated
+ * device memory stays within hbm_budget_bytes.  A structure's results do not depend on the rest of
+ * the batch.  The server uses ctx (weights, constants, skin) exclusively while it exists: make no
+ * other calls on that context meanwhile.
+ */
+typedef struct fnn_server fnn_server;
+
+typedef struct {
+  int32_t n_atoms;
+  const int32_t *Z;     /* host [n] atomic numbers */
+  const float *pos;     /* host [n][3] */
+  const float *vel;     /* host [n][3] A/fs, or NULL = at rest */
+  const float *cell;    /* host [9] orthorhombic cell (periodic, minimum image), or NULL = gas phase */
+  int32_t n_steps;      /* force evaluations (MD steps) */
+  double dt_fs;         /* time step */
+} fnn_request;
+
+typedef struct {
+  double *energies;     /* host [n_steps] energy after each evaluation, or NULL */
+  float *pos, *vel, *forces;  /* host [n][3] final state, or NULL */
+  double latency_ms;    /* completion minus submission */
+  double queue_ms;      /* admission minus submission */
+  int32_t n_steps_done;
+} fnn_result;
+
+typedef struct {
+  int64_t atom_evals;       /* atoms evaluated, summed over batch steps */
+  int64_t batch_steps;
+  int64_t admitted;
+  int64_t max_batch_atoms;
+  int64_t pending;          /* requests waiting for admission */
+  double bytes_per_atom;    /* the admission estimate */
+} fnn_serve_counters;
+
+fnn_status fnn_serve_create(fnn_server **srv, fnn_ctx *ctx, size_t hbm_budget_bytes, fnn_precision prec,
+                            int32_t rebuild_every);
+/* Copies the request; never blocks on the GPU.  FNN_E_OOM when the structure alone exceeds the budget. */
+fnn_status fnn_serve_submit(fnn_server *srv, const fnn_request *req, uint64_t *ticket);
+/* FNN_OK and the result (copied into the caller's buffers) once the request is done; FNN_PENDING if it
+ * is not done within timeout_us (0 = do not wait).  A ticket's result can be taken once. */
+fnn_status fnn_serve_poll(fnn_server *srv, uint64_t ticket, fnn_result *res, int64_t timeout_us);
+fnn_status fnn_serve_stats(fnn_server *srv, fnn_serve_counters *stats);
+/* Finishes every admitted and queued request, then releases the server. */
+fnn_status fnn_serve_destroy(fnn_server *srv);
+
+/*
  * Allocation-free neighbour list (no counterpart in the paper).
  *
  * For callers that may not allocate device memory themselves or through this

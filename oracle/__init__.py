@@ -315,3 +315,35 @@ def loss_and_weight_grads(s, w, E_ref: np.ndarray, F_ref: np.ndarray, params: Pa
     gr = torch.autograd.grad(surrogate, [th[k] for k in names])
     L = float(LE_t.detach()) + LF
     return L, E.detach().numpy(), F, {k: gk.numpy() for k, gk in zip(names, gr)}
+
+
+# ----------------------------------------------------------------------------- dynamics (section V.D)
+
+# atomic masses (amu), element order H C N O F S Cl
+MASS = {0: 1.008, 1: 12.011, 2: 14.007, 3: 15.999, 4: 18.998, 5: 32.06, 6: 35.45}
+ACCEL = 4.184e-4   # (kcal/mol/A) / amu in A/fs^2
+
+
+def velocity_verlet(s, w, v0, n_steps: int, dt: float, params: Params = Params()):
+    """NVE velocity Verlet, the integrator of the paper's native MD engine for NVE runs (section V.D):
+    n_steps force evaluations at x_0 .. x_{n-1}; between evaluations
+    v <- v + a dt/2, x <- x + v dt, then after the next evaluation v <- v + a dt/2.
+    Returns (energies [n_steps, n_mol], final positions, final velocities v_{n-1}, final forces)."""
+    el = elements(s.Z)
+    m = np.asarray([MASS[int(e)] for e in el])[:, None]
+    x = np.asarray(s.pos, np.float64).copy()
+    v = np.asarray(v0, np.float64).copy()
+    energies = []
+    F = None
+    for k in range(n_steps):
+        st = type(s)(s.Z, x, s.mol_offsets, s.cell, s.pbc)
+        r = energy_forces(st, w, params)
+        energies.append(r.energy)
+        a = r.forces / m * ACCEL
+        if k > 0:
+            v = v + 0.5 * dt * a          # completes the previous step's velocity
+        F = r.forces
+        if k < n_steps - 1:
+            v = v + 0.5 * dt * a
+            x = x + dt * v
+    return np.asarray(energies), x, v, F

@@ -150,6 +150,7 @@ struct fnn_ctx {
 struct fnn_nlist {
   fnn_ctx *ctx = nullptr;
   int64_t capacity = 0;       // entries
+  bool auto_size = false;     // created without a capacity: grows to 160 entries per atom with the system
   int32_t atom_cap = 0, mol_cap = 0, cell_cap = 0, pad_cap = 0;
   int32_t n_atoms = 0, n_mol = 0;
   double R = 0.0;

@@ -563,6 +563,7 @@ extern "C" fnn_status fnn_nlist_create(fnn_ctx *ctx, fnn_nlist **out, int64_t ca
   if (!ctx || !out || capacity < 0) return FNN_E_INVALID;
   fnn_nlist *nl = new fnn_nlist();
   nl->ctx = ctx;
+  nl->auto_size = capacity == 0;
   if (capacity > 0) {
     fnn_status st = reserve(nl, 0, 0, capacity);
     if (st) {
@@ -617,6 +618,7 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   cudaStream_t s = (cudaStream_t)stream;
   const int N = sys->n_atoms, NM = sys->n_mol;
   int64_t cap = nl->capacity > 0 ? nl->capacity : (int64_t)160 * (N > 0 ? N : 1) + 1024;
+  if (nl->auto_size && cap < (int64_t)160 * N + 1024) cap = (int64_t)160 * N + 1024;
   if ((st = reserve(nl, N, NM, cap))) return st;
   const double R = ctx->cfg.rc_rad + ctx->cfg.skin;
   nl->R = R;

@@ -43,6 +43,22 @@ class CWeights(ctypes.Structure):
                                                    ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")]
 
 
+class CRequest(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("Z", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p),
+                ("cell", ctypes.c_void_p), ("n_steps", ctypes.c_int32), ("dt_fs", ctypes.c_double)]
+
+
+class CResult(ctypes.Structure):
+    _fields_ = [("energies", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("n_steps_done", ctypes.c_int32)]
+
+
+class CServeCounters(ctypes.Structure):
+    _fields_ = [("atom_evals", ctypes.c_int64), ("batch_steps", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("max_batch_atoms", ctypes.c_int64), ("pending", ctypes.c_int64), ("bytes_per_atom", ctypes.c_double)]
+
+
 class CSystem(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int32), ("n_mol", ctypes.c_int32), ("mol_offsets", ctypes.c_void_p),
                 ("Z", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("pbc", ctypes.c_void_p)]
@@ -74,6 +90,12 @@ def _load():
         "fnn_profile_read": (I32, [P, P, P, P, I32, P]),
         "fnn_launch_count": (I32, [P, P]),
         "fnn_build_neighbors_static": (I32, [P, ctypes.c_double, P, P, P, I64, P, P]),
+        "fnn_md_run": (I32, [P, P, P, P, P, I32, I32, ctypes.c_double, I32, P, P, P]),
+        "fnn_serve_create": (I32, [P, P, ctypes.c_size_t, I32, I32]),
+        "fnn_serve_submit": (I32, [P, P, P]),
+        "fnn_serve_poll": (I32, [P, ctypes.c_uint64, P, I64]),
+        "fnn_serve_stats": (I32, [P, P]),
+        "fnn_serve_destroy": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -319,3 +341,81 @@ def launch_count(ctx: Context) -> int:
     n = ctypes.c_int64(0)
     ctx._check(lib.fnn_launch_count(ctx.h, ctypes.byref(n)), "fnn_launch_count")
     return n.value
+
+
+def md_run(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision: str, n_steps: int, dt_fs: float,
+           rebuild_every: int = 10, E_hist=None, F=None, stream=None):
+    """fnn_md_run: NVE velocity Verlet on the device; system.pos and vel ([N,4] float32) advance in place.
+    Returns (E_hist [n_steps, n_mol] float64, F [N,3] of the last evaluation)."""
+    import torch
+    if E_hist is None:
+        E_hist = torch.empty((n_steps, system.n_mol), dtype=torch.float64, device="cuda")
+    if F is None:
+        F = torch.empty((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+    cs = system.c()
+    ctx._check(lib.fnn_md_run(ctx.h, ctypes.byref(cs), _ptr(system.pos), _ptr(vel), nl.h, PRECISION[precision],
+                              int(n_steps), float(dt_fs), int(rebuild_every), _ptr(E_hist), _ptr(F), _stream(stream)),
+               "fnn_md_run")
+    return E_hist, F
+
+
+class Server:
+    """fnn_serve_*: continuous-batching MD service on a context (used exclusively while it lives)."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, precision: str = "bf16", rebuild_every: int = 10):
+        self.ctx = ctx
+        self.h = None
+        h = ctypes.c_void_p()
+        ctx._check(lib.fnn_serve_create(ctypes.byref(h), ctx.h, int(budget_bytes), PRECISION[precision],
+                                        int(rebuild_every)), "fnn_serve_create")
+        self.h = h
+        self.n = {}
+
+    def submit(self, s, vel=None, n_steps: int = 10, dt_fs: float = 0.5) -> int:
+        """Queue one structure (a single-molecule synth.Structures); returns its ticket."""
+        Z = np.ascontiguousarray(s.Z, np.int32)
+        pos = np.ascontiguousarray(s.pos, np.float32)
+        v = None if vel is None else np.ascontiguousarray(vel, np.float32)
+        cell = np.ascontiguousarray(s.cell[0], np.float32) if bool(s.pbc[0]) else None
+        rq = CRequest(s.n_atoms, Z.ctypes.data, pos.ctypes.data, None if v is None else v.ctypes.data,
+                      None if cell is None else cell.ctypes.data, int(n_steps), float(dt_fs))
+        t = ctypes.c_uint64(0)
+        code = lib.fnn_serve_submit(self.h, ctypes.byref(rq), ctypes.byref(t))
+        if code != FNN_OK:
+            raise FnnError(code, "fnn_serve_submit")
+        self.n[t.value] = (s.n_atoms, int(n_steps))
+        return t.value
+
+    def poll(self, ticket: int, timeout_s: float = 0.0):
+        """The result dict once done, else None (after waiting up to timeout_s)."""
+        n, k = self.n[ticket]
+        out = {"energies": np.zeros(k), "pos": np.zeros((n, 3), np.float32), "vel": np.zeros((n, 3), np.float32),
+               "forces": np.zeros((n, 3), np.float32)}
+        r = CResult(out["energies"].ctypes.data, out["pos"].ctypes.data, out["vel"].ctypes.data,
+                    out["forces"].ctypes.data, 0.0, 0.0, 0)
+        code = lib.fnn_serve_poll(self.h, ticket, ctypes.byref(r), int(timeout_s * 1e6))
+        if code == FNN_PENDING:
+            return None
+        if code != FNN_OK:
+            raise FnnError(code, "fnn_serve_poll")
+        del self.n[ticket]
+        out.update(latency_ms=r.latency_ms, queue_ms=r.queue_ms, n_steps_done=r.n_steps_done)
+        return out
+
+    def stats(self) -> dict:
+        c = CServeCounters()
+        code = lib.fnn_serve_stats(self.h, ctypes.byref(c))
+        d = {f: getattr(c, f) for f, _ in CServeCounters._fields_}
+        d["status"] = code
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fnn_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

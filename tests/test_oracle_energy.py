@@ -136,3 +136,29 @@ def test_loss_weight_gradients_finite_differences():
         fd = (Lat(1) - Lat(-1)) / (2 * h)
         an = sum(float(np.sum(grads[k] * D[k])) for k in names)
         assert an == pytest.approx(fd, rel=1e-6)
+
+
+def test_velocity_verlet_conserves_energy_and_is_time_reversible():
+    """Pins of the reference integrator: with a small step the total energy of an isolated molecule is
+    conserved to second order in dt, and running back from the end (velocities negated) returns the
+    starting positions (velocity Verlet is time reversible)."""
+    s = structure("gas24")
+    w = weights(1)
+    rng = np.random.default_rng(8)
+    v0 = rng.normal(scale=0.003, size=(s.n_atoms, 3))
+    el = oracle.elements(s.Z)
+    m = np.asarray([oracle.MASS[int(e)] for e in el])[:, None]
+    kin = lambda v: 0.5 * np.sum(m * v * v) / oracle.ACCEL   # kcal/mol
+
+    def drift(dt):
+        E, x, v, F = oracle.velocity_verlet(s, w, v0, 21, dt)
+        e0 = E[0, 0] + kin(v0)
+        e1 = E[-1, 0] + kin(v)
+        return abs(e1 - e0), x, v
+
+    d1, x1, v1 = drift(0.2)
+    d2, _, _ = drift(0.1)
+    assert d2 < d1 / 2.5          # second-order integrator: halving dt cuts the error about 4x
+    back = synth.Structures(s.Z, x1, s.mol_offsets, s.cell, s.pbc)
+    _, x0, _, _ = oracle.velocity_verlet(back, w, -v1, 21, 0.2)
+    np.testing.assert_allclose(x0, s.pos.astype(np.float64), atol=1e-9)
