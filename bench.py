@@ -94,25 +94,57 @@ def recorded_traffic(kernel: str, digest: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """SM clocks and throttle reasons sampled during the timed region: NVML from a background thread every
+    2 ms (the timed regions are tens of milliseconds), nvidia-smi at 200 ms if NVML is unavailable."""
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40, "sw_power_cap": 0x4}
 
     def __init__(self, index: int):
         self.index = index
+        self.rows = []
+        self.max_mhz = None
+        self._stop = None
         self.proc = None
 
+    def _nvml_loop(self, pynvml, h):
+        while not self._stop.is_set():
+            try:
+                mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+                reasons = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+                power = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
+                self.rows.append((mhz, reasons, power))
+            except Exception:
+                pass
+            self._stop.wait(0.002)
+
     def __enter__(self):
+        import threading
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+            import pynvml
+            pynvml.nvmlInit()
+            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            self._stop = threading.Event()
+            self.thread = threading.Thread(target=self._nvml_loop, args=(pynvml, h), daemon=True)
+            self.thread.start()
+            self.mode = "nvml"
+        except Exception:
+            self.mode = "nvidia-smi"
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                              "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                             stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                self.proc = None
         return self
 
     def __exit__(self, *exc):
+        if self.mode == "nvml":
+            self._stop.set()
+            self.thread.join(timeout=2)
+            return
         self.out = ""
         if self.proc:
             self.proc.terminate()
@@ -121,20 +153,21 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 self.out, _ = self.proc.communicate()
-
-    def summary(self):
-        rows = []
-        for line in (getattr(self, "out", "") or "").splitlines():
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
             c = [x.strip() for x in line.split(",")]
             if len(c) == 7 and c[0].replace(".", "").isdigit():
-                rows.append(c)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(float(r[0]) for r in rows), "sm_max_mhz": float(rows[0][1]),
-                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit()) if rows else None,
-                "samples": len(rows), "reasons": reasons}
+                bits = sum(self.REASONS[names[k]] for k in range(4) if c[3 + k].lower() == "active")
+                self.max_mhz = float(c[1])
+                self.rows.append((float(c[0]), bits, float(c[2]) if c[2].replace(".", "").isdigit() else 0.0))
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "source": self.mode}
+        reasons = sorted({n for _, bits, _ in self.rows for n, b in self.REASONS.items() if bits & b})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": self.max_mhz,
+                "power_w_max": max(r[2] for r in self.rows), "samples": len(self.rows), "reasons": reasons,
+                "source": self.mode}
 
 
 def oracle_full(M: int = 8, min_seconds: float = 10.0, max_reps: int = 3):
@@ -178,6 +211,74 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serve_bench(fnn, torch, synth, duration_s=2.0, rate_hz=2000.0, pool_n=128, budget=120 << 30, n_steps=10,
+                dt=0.5, one_requests=64):
+    """Serving stream: Poisson arrivals of structures with log-uniform sizes 8..20000 atoms (periodic above 500),
+    each 10 velocity-Verlet steps, one ensemble member; BF16 served form with continuous batching under an HBM
+    budget, against the FP32-accurate form run batch-of-one (each request alone, sequentially)."""
+    import numpy as np
+    w1 = synth.xavier_weights(1)
+    pool = synth.request_pool(pool_n, seed=5)
+    vels = [synth.maxwell_boltzmann(p.Z, 300.0, seed=k) for k, p in enumerate(pool)]
+    rng = np.random.Generator(np.random.PCG64([5, 2]))
+    stream, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            break
+        stream.append((t, int(rng.integers(pool_n))))
+    ctx = fnn.Context(1, skin=1.0)
+    fnn.load_weights(ctx, w1)
+    srv = fnn.Server(ctx, budget, "bf16", rebuild_every=10)
+    for k in range(4):                                   # warm-up (allocations, first launches)
+        srv.poll(srv.submit(pool[k], vels[k], n_steps, dt), timeout_s=300)
+    t0 = time.perf_counter()
+    tickets = []
+    for t_arr, k in stream:
+        while time.perf_counter() - t0 < t_arr:
+            pass
+        tickets.append((srv.submit(pool[k], vels[k], n_steps, dt), k))
+    res = [(srv.poll(tk, timeout_s=600), k) for tk, k in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_ms"] for r, _ in res if r is not None])
+    evals = sum(pool[k].n_atoms * n_steps for _, k in stream)
+    out = {"requests": len(stream), "completed": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "atom_evals_per_s": evals / wall,
+           "offered_atom_evals_per_s": evals / duration_s, "arrival_window_s": duration_s, "wall_s": wall,
+           "rate_hz": rate_hz, "members": 1, "precision": "bf16", "max_batch_atoms": st["max_batch_atoms"],
+           "batch_steps": st["batch_steps"], "mean_atoms": float(np.mean([pool[k].n_atoms for _, k in stream])),
+           "pool": f"{pool_n} structures, n = round(exp(U(ln 8, ln 20000))), periodic above 500 atoms, seed 5",
+           "budget_bytes": budget, "status": st["status"]}
+    # batch-of-one FP32 form: the first requests of the same stream, each alone
+    ctx1 = fnn.Context(1, skin=1.0)
+    fnn.load_weights(ctx1, w1)
+    one = []
+    evals1 = 0
+    t_all = 0.0
+    for _, k in stream[:one_requests]:
+        s = pool[k]
+        ds = fnn.DeviceSystem.from_structures(s)
+        vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+        vel[:, :3] = torch.from_numpy(vels[k])
+        vel = vel.cuda()
+        nl = fnn.NeighborList(ctx1)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        fnn.md_run(ctx1, ds, vel, nl, "fp32x3", n_steps, dt, 10)
+        fnn.check(ctx1, "batch-of-one")
+        dt_req = time.perf_counter() - ta
+        one.append(1e3 * dt_req)
+        t_all += dt_req
+        evals1 += s.n_atoms * n_steps
+    one = np.array(one[1:] if len(one) > 1 else one)   # the first call carries one-time set-up
+    out["batch_of_one"] = {"precision": "fp32x3", "requests": len(one), "p50_ms": float(np.percentile(one, 50)),
+                           "p99_ms": float(np.percentile(one, 99)), "atom_evals_per_s": evals1 / t_all,
+                           "note": "each request alone on the GPU, no queueing, sequential"}
+    return out
 
 
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
@@ -251,6 +352,8 @@ def main():
                     help="form whose throughput is the headline value")
     ap.add_argument("--forms", default="fp32x3,fp32,bf16", help="forms timed and reported (comma separated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -322,6 +425,9 @@ def main():
     base, ref = (None, None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, ref = oracle_full(M)
+    serve = None
+    if world == 1 and not args.no_serve:
+        serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds)
 
     head = results[args.precision]
     kernels, roof = kernel_table(head["prof"], args.steps, s.n_atoms, nnz, M, args.precision, pk)
@@ -352,6 +458,8 @@ def main():
             "clocks": head["clocks"], "forms": form_report, "kernels": kernels, "source_digest": source_digest()}
     if base is not None:
         line["cpu_baseline"] = base
+    if serve is not None:
+        line["serve"] = serve
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
