@@ -106,10 +106,13 @@ class ClockSampler:
         self.proc = None
 
     def _nvml_loop(self, pynvml, h):
+        get = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(pynvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self._reasons = get
         while not self._stop.is_set():
             try:
                 mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                reasons = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+                reasons = self._reasons(h)
                 power = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
                 self.rows.append((mhz, reasons, power))
             except Exception:

@@ -159,6 +159,12 @@ fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t *nbr, int8_
  * Asynchronous. */
 fnn_status fnn_aev(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *aev, void *stream);
 
+/* Tangent of the AEVs along a displacement field: T [N][1008] = (dAEV/dx) . V with V [N][3] (device,
+ * float32): for every slot, the directional derivative of the symmetry function above (chain rule
+ * through r_ij, r_ik and cos theta_ijk).  The force term of a training loss needs it (section IV:
+ * dL_F/dtheta = -d/dtheta <T(dL/dF), dE/dAEV(theta)>).  Asynchronous. */
+fnn_status fnn_aev_jvp(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *T, void *stream);
+
 /* Energies E [n_mol] (float64, device), forces F [N][3] (float32, device) and,
  * when virial != NULL, virials [n_mol][9] (float64, device, W = -sum over
  * directed entries of d (x) dE_i/dd, = sum_i x_i (x) F_i for a gas-phase
@@ -176,13 +182,31 @@ fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t n_atoms, int32_t n_mol, 
                                   const int32_t *Z, const float *pos, const float *cell, const uint8_t *pbc,
                                   fnn_precision prec, double *E, float *F, double *virial, void *stream);
 
+/* Parameter gradients, float32, device, same layout as fnn_weights (caller-owned, ACCUMULATED into:
+ * zero them first). */
+typedef struct {
+  float *W1, *b1, *W2, *b2, *W3, *b3, *w4, *b4;
+} fnn_grads;
+
+/*
+ * Gradient of a training loss L(E, F) with respect to the network parameters (section IV: force
+ * and energy terms), given dL/dE [n_mol] (float64, device) and dL/dF [N][3] (float32, device, atom
+ * order) at the current parameters:
+ *   dL/dtheta = dL/dE . dE/dtheta - d/dtheta <J v, dE/dAEV>,  v = dL/dF,  J = dAEV/dx,
+ * the second term by a forward-mode tangent of the networks along J v (fnn_aev_jvp) and one reverse
+ * sweep over the primal and tangent activations.  FP32 arithmetic; the list must be built for sys.
+ * Adds into g (zero it first).  Asynchronous on stream.
+ */
+fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
+                           const float *dLdF, const fnn_grads *g, void *stream);
+
 /* Synchronise the stream, return and clear the sticky device status; *info
  * (optional) receives its detail (entries needed for FNN_E_CAPACITY, the
  * offending atom for FNN_E_SPECIES, ...). */
 fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
 
 /*
- * NVE velocity Verlet on the device (the native engine's NVE integrator, section V.D; SURVEY a9):
+ * NVE velocity Verlet on the device (the native engine's NVE integrator, section V.D):
  * n_steps force evaluations at x_0 .. x_{n-1}.  After evaluation k every atom does v += a dt/2
  * (completing step k) and, unless k is the last, v += a dt/2 and x += v dt (a = F/m, masses
  * H 1.008 C 12.011 N 14.007 O 15.999 F 18.998 S 32.06 Cl 35.45 amu, 1 kcal/mol/A/amu = 4.184e-4
@@ -195,7 +219,7 @@ fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *ve
                       int32_t n_steps, double dt_fs, int32_t rebuild_every, double *E_hist, float *F, void *stream);
 
 /*
- * Continuous-batching MD service (SURVEY serving form).  A scheduler thread keeps a ragged batch of
+ * Continuous-batching MD service.  A scheduler thread keeps a ragged batch of
  * structures on the device and advances all of them one velocity-Verlet step per batch step (one
  * neighbour-list/AEV/network/adjoint pass over the whole batch); between batch steps it retires
  * finished structures and admits queued requests, in arrival order, while the batch's estimated

@@ -463,6 +463,141 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
     for (int q = 0; q < 9; q++) atomicAdd(&A.virial[9 * (size_t)cur_mol + q], vacc[q]);
 }
 
+// ------------------------------------------------------------------------------- tangent (JVP)
+// t = (dAEV/dx) . V: the directional derivative of every AEV entry along a displacement field V.
+// Radial: d/dt [T_k(r)] = T_k'(r) rdot, rdot = d.(v_j - v_i) / r.  Angular: with c = cos theta,
+// cdot = (d2.vd1 + d1.vd2) / (r1 r2) - c (r1dot / r1 + r2dot / r2),
+// d/dt [2 f_s g_m C] = fdot_s (2 g_m C) + f_s (2 (gdot_m C + g_m Cdot)); same enumeration as the forward.
+struct TanStage {
+  NbrStage nb;
+  float4 rv[RAD_CAP];            // v_j - v_i, rdot
+  float2 rt[RAD_CAP];            // fc(r) rdot, fc'(r) rdot   (radial switch)
+  float stage[32][25];           // f_s, fdot_s, 2 g_m C, 2 (gdot_m C + g_m Cdot), pair index
+  float acc[NPAIR * 32];
+};
+
+struct AevTanArgs {
+  StageArgs sa;
+  AevParams P;
+  const float *V;         // [N][3] displacement field
+  float *out;             // [rows][1008]
+  const int32_t *inv;     // padded row -> atom; NULL = rows are atoms
+  const int32_t *meta;
+  int n_atoms;
+  DevStatus *st;
+};
+
+constexpr int TAN_WARPS = 2;   // 15 KB of staging per warp: two warps keep the block under 48 KB
+
+__global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
+  __shared__ TanStage smem[TAN_WARPS];
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  TanStage &W = smem[wl];
+  NbrStage &S = W.nb;
+  const AevParams &P = A.P;
+  int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  int wg = blockIdx.x * TAN_WARPS + wl, nw = gridDim.x * TAN_WARPS;
+  for (int row = wg; row < nrows; row += nw) {
+    float *out = A.out + (size_t)row * NAEV;
+    int i = A.inv ? A.inv[row] : row;
+    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
+    bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st);
+    if (!ok) {
+      for (int c = lane; c < NAEV; c += 32) out[c] = 0.f;
+      __syncwarp();
+      continue;
+    }
+    const float vix = A.V[3 * (size_t)i], viy = A.V[3 * (size_t)i + 1], viz = A.V[3 * (size_t)i + 2];
+    const int nrad = off_r[NE];
+    for (int t = lane; t < nrad; t += 32) {
+      const int j = S.rj[t];
+      const float4 d = S.rd[t];
+      const float vx = A.V[3 * (size_t)j] - vix, vy = A.V[3 * (size_t)j + 1] - viy, vz = A.V[3 * (size_t)j + 2] - viz;
+      const float rdot = (d.x * vx + d.y * vy + d.z * vz) / d.w;
+      W.rv[t] = make_float4(vx, vy, vz, rdot);
+      const float dfc = -0.5f * P.pi_rc_rad * sinpif(d.w / P.rc_rad);
+      W.rt[t] = make_float2(S.rfc[t] * rdot, dfc * rdot);
+    }
+    __syncwarp();
+    // ---- radial
+    {
+      int h = lane >> 4, k = lane & 15;
+      float Rk = P.shf_r[k];
+#pragma unroll 1
+      for (int q = 0; q < NE; q++) {
+        float acc = 0.f;
+        for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
+          const float dr = S.rd[t].w - Rk;
+          const float2 ft = W.rt[t];
+          acc += __expf(-P.eta_r * dr * dr) * (-2.f * P.eta_r * dr * ft.x + ft.y);
+        }
+        acc += __shfl_xor_sync(FULL, acc, 16);
+        if (lane < 16) out[q * NSR + k] = 0.25f * acc;
+      }
+    }
+    // ---- angular
+    {
+      const int s_my = lane & 3, m_my = lane >> 2;
+      for (int c = lane; c < NPAIR * 32; c += 32) W.acc[c] = 0.f;
+      const int n = off_a[NE];
+      const int T = n * (n - 1) / 2;
+      int run_p = -1;
+      float racc = 0.f;
+      for (int base = 0; base < T; base += 32) {
+        const int t = base + lane;
+        if (t < T) {
+          int ja, ka;
+          tri_index(t, n, ja, ka);
+          const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
+          const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
+          const float r1 = d1.w, r2 = d2.w, inv12 = 1.f / (r1 * r2);
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
+          const float cdot = (d2.x * v1.x + d2.y * v1.y + d2.z * v1.z + d1.x * v2.x + d1.y * v2.y + d1.z * v2.z) * inv12 -
+                             c * (v1.w / r1 + v2.w / r2);
+          const float c95 = 0.95f * c;
+          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+          const float ds95 = -0.9025f * c / s95;
+#pragma unroll
+          for (int sidx = 0; sidx < NSZ; sidx++) {
+            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[sidx] + s95 * P.sin_z[sidx]);
+            const float f = exp2f_fast(P.zeta * __log2f(base_s));
+            W.stage[lane][sidx] = f;
+            W.stage[lane][4 + sidx] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[sidx] + ds95 * P.sin_z[sidx]) * cdot;
+          }
+          const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
+          const float f1 = S.afc[ja], f2 = S.afc[ka];
+          const float C = f1 * f2, Cdot = S.adfc[ja] * v1.w * f2 + f1 * S.adfc[ka] * v2.w;
+#pragma unroll
+          for (int m = 0; m < NSA; m++) {
+            const float dr = rbar - P.shf_a[m];
+            const float g = __expf(-P.eta_a * dr * dr);
+            const float gdot = -2.f * P.eta_a * dr * g * rbdot;
+            W.stage[lane][8 + m] = 2.f * g * C;
+            W.stage[lane][16 + m] = 2.f * (gdot * C + g * Cdot);
+          }
+          W.stage[lane][24] = __int_as_float(pair_of(S.ae[ja], S.ae[ka]));
+        }
+        __syncwarp();
+        const int nt = min(32, T - base);
+        for (int q = 0; q < nt; q++) {
+          const int p = __float_as_int(W.stage[q][24]);
+          if (p != run_p) {
+            if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+            racc = 0.f;
+            run_p = p;
+          }
+          racc += W.stage[q][4 + s_my] * W.stage[q][8 + m_my] + W.stage[q][s_my] * W.stage[q][16 + m_my];
+        }
+        __syncwarp();
+      }
+      if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+      __syncwarp();
+      for (int c = lane; c < NPAIR * 32; c += 32) out[NRAD + c] = W.acc[c];
+    }
+    __syncwarp();
+  }
+}
+
 static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
   StageArgs s;
   s.cap = nl->capacity;
@@ -542,6 +677,26 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
     k_aev_adjoint<<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_adjoint");
+}
+
+fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
+                              const int32_t *inv, cudaStream_t s) {
+  AevTanArgs a;
+  a.sa = stage_args(sys, nl);
+  a.P = ctx->aev;
+  a.V = V;
+  a.out = out;
+  a.inv = inv;
+  a.meta = nl->meta;
+  a.n_atoms = sys->n_atoms;
+  a.st = ctx->status;
+  int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
+  if (rows == 0) return FNN_OK;
+  {
+    FNN_KERNEL(ctx, "aev_tangent", s);
+    k_aev_tangent<<<2 * aev_grid(ctx, rows), TAN_WARPS * 32, 0, s>>>(a);
+  }
+  return check_launch(ctx, "aev_tangent");
 }
 
 }  // namespace fnn

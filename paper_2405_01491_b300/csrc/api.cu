@@ -165,6 +165,7 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   free_weights(ctx->w);
   free_workspace(ctx->ws);
   free_tc(ctx);
+  free_train(ctx);
   auto &h = ctx->host;
   void *hp[] = {h.Z, h.mol_offsets, h.pos, h.cell, h.pbc, h.pos3, h.E, h.virial, h.F};
   for (void *p : hp)
@@ -265,6 +266,16 @@ extern "C" fnn_status fnn_aev(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
     return FNN_E_STATE;
   }
   return launch_aev_forward(ctx, sys, nl, aev, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" fnn_status fnn_aev_jvp(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *T,
+                                  void *stream) {
+  if (!ctx || !sys || !nl || !V || !T) return FNN_E_INVALID;
+  if (!nl->built || nl->n_atoms != sys->n_atoms || nl->n_mol != sys->n_mol) {
+    ctx->last_error = "neighbour list was not built for this system";
+    return FNN_E_STATE;
+  }
+  return launch_aev_tangent(ctx, sys, nl, V, T, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec,

@@ -133,6 +133,7 @@ struct fnn_ctx {
   fnn::DeviceWeights w;
   bool has_weights = false;
   fnn::Workspace ws;
+  void *train = nullptr;                // training-gradient buffers (train.cu)
   std::string last_error;
   // host-call staging (fnn_energy_forces_host)
   struct HostStage {
@@ -199,6 +200,30 @@ enum { META_CELLS = 0, META_NNZ = 1, META_NPAD = 2, META_SEG = 4 /* [8] segment 
 
 fnn_status check_launch(fnn_ctx *ctx, const char *what);
 
+// FP32 SIMT product C[r, n] = epi(sum_k A[r, k] B[n, k]) over 128-row species tiles (mlp_simt.cu)
+enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_SCALE = 3, EPI_L3_H = 4 };
+struct GemmP {
+  const float *A;
+  long long lda, a_mstride;
+  const float *B;
+  long long ldb, b_estride, b_mstride;
+  float *C;
+  long long ldc, c_mstride;
+  int N, K;
+  const int32_t *tile_elem;
+  const float *bias;
+  long long bias_estride, bias_mstride;
+  const float *aux;              // h of the previous layer (EPI_DCELU)
+  long long ldaux, aux_mstride;
+  const float *w4;               // EPI_L3, EPI_L3_H
+  long long w4_estride, w4_mstride;
+  float *ypart;                  // [rows][M][4]
+  int M;
+  float scale;
+};
+fnn_status launch_gemm_f32(fnn_ctx *ctx, const char *name, int epi, const GemmP &p, int row_tiles, int members,
+                           cudaStream_t s);
+
 // Scope around one kernel launch: counts it and, when profiling, records events around it.
 struct KScope {
   fnn_ctx *ctx;
@@ -221,12 +246,15 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
                               const int32_t *inv, cudaStream_t s);
 fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,
                               const int32_t *inv, float *F, double *virial, cudaStream_t s);
+fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
+                              const int32_t *inv, cudaStream_t s);
 fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s);
 fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
                      cudaStream_t s);
 fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const float *W1Tcat, const float *W2,
                              const float *W2T, const float *W3, const float *W3T);
 void free_tc(fnn_ctx *ctx);
+void free_train(fnn_ctx *ctx);
 fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s);
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
                               int ntile, double *E, cudaStream_t s);

@@ -15,28 +15,6 @@
 
 namespace fnn {
 
-enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_SCALE = 3 };
-
-struct GemmP {
-  const float *A;
-  long long lda, a_mstride;
-  const float *B;
-  long long ldb, b_estride, b_mstride;
-  float *C;
-  long long ldc, c_mstride;
-  int N, K;
-  const int32_t *tile_elem;
-  const float *bias;
-  long long bias_estride, bias_mstride;
-  const float *aux;              // h of the previous layer (EPI_DCELU)
-  long long ldaux, aux_mstride;
-  const float *w4;               // EPI_L3
-  long long w4_estride, w4_mstride;
-  float *ypart;                  // [rows][M][4]
-  int M;
-  float scale;
-};
-
 constexpr int BM = 128, BN = 64, BK = 16, GNT = 256;
 
 __device__ __forceinline__ float celu(float z) { return z > 0.f ? z : CELU_ALPHA * expm1f(z / CELU_ALPHA); }
@@ -131,6 +109,11 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
         float w = p.w4[e * p.w4_estride + m * p.w4_mstride + n];
         ysum += celu(z) * w;
         o = p.scale * w * (z > 0.f ? 1.f : expf(z / CELU_ALPHA));
+      } else if (EPI == EPI_L3_H) {   // keep h3 itself (training) and the output-layer partials
+        float z = v + p.bias[e * p.bias_estride + m * p.bias_mstride + n];
+        float h = celu(z);
+        ysum += h * p.w4[e * p.w4_estride + m * p.w4_mstride + n];
+        o = h;
       } else if (EPI == EPI_DCELU) {
         float h = p.aux[(row0 + r) * p.ldaux + m * p.aux_mstride + n];
         o = v * dcelu_from_h(h);
@@ -139,7 +122,7 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
       }
       C[(long long)r * p.ldc + n] = o;
     }
-    if (EPI == EPI_L3) {
+    if (EPI == EPI_L3 || EPI == EPI_L3_H) {
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) ysum += __shfl_xor_sync(0xffffffffu, ysum, o);
       if (tx == 0) p.ypart[((row0 + r) * p.M + m) * 4 + blockIdx.x] = ysum;
@@ -152,6 +135,19 @@ static void launch(fnn_ctx *ctx, const char *name, const GemmP &p, int row_tiles
   dim3 grid((p.N + BN - 1) / BN, row_tiles, members);
   FNN_KERNEL(ctx, name, s);
   k_gemm_f32<EPI><<<grid, GNT, 0, s>>>(p);
+}
+
+fnn_status launch_gemm_f32(fnn_ctx *ctx, const char *name, int epi, const GemmP &p, int row_tiles, int members,
+                           cudaStream_t s) {
+  switch (epi) {
+    case EPI_BIAS_CELU: launch<EPI_BIAS_CELU>(ctx, name, p, row_tiles, members, s); break;
+    case EPI_L3: launch<EPI_L3>(ctx, name, p, row_tiles, members, s); break;
+    case EPI_DCELU: launch<EPI_DCELU>(ctx, name, p, row_tiles, members, s); break;
+    case EPI_SCALE: launch<EPI_SCALE>(ctx, name, p, row_tiles, members, s); break;
+    case EPI_L3_H: launch<EPI_L3_H>(ctx, name, p, row_tiles, members, s); break;
+    default: ctx->last_error = "unknown epilogue"; return FNN_E_INVALID;
+  }
+  return check_launch(ctx, name);
 }
 
 fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s) {

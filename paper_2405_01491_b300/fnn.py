@@ -5,7 +5,9 @@ own device memory and to name the current stream.  Importing this module loads
 the library and raises if it is missing: there is no CPU fallback.
 
 Names follow the C entry points: build_neighbors, nlist_nnz, nlist_export, aev,
-energy_forces, energy_forces_host, sync, load_weights, save_weights.
+aev_jvp, energy_forces, energy_forces_host, param_grads, md_run, Server, sync,
+load_weights, save_weights; energy_forces_autograd wraps energy_forces and
+param_grads as a torch.autograd.Function for training.
 """
 from __future__ import annotations
 
@@ -41,6 +43,19 @@ class Config(ctypes.Structure):
 class CWeights(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in
                                                    ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")]
+
+
+PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
+
+
+def param_shapes(M: int) -> dict:
+    """Shapes of the network parameters of an M-member ensemble (row-major W[out][in], element axis 7)."""
+    return {"W1": (M, 7, 256, 1008), "b1": (M, 7, 256), "W2": (M, 7, 192, 256), "b2": (M, 7, 192),
+            "W3": (M, 7, 160, 192), "b3": (M, 7, 160), "w4": (M, 7, 160), "b4": (M, 7)}
+
+
+class CGrads(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in PARAM_NAMES]
 
 
 class CRequest(ctypes.Structure):
@@ -82,6 +97,8 @@ def _load():
         "fnn_nlist_nnz": (I32, [P, P]),
         "fnn_nlist_export": (I32, [P, P, P, P, I64, P]),
         "fnn_aev": (I32, [P, P, P, P, P]),
+        "fnn_aev_jvp": (I32, [P, P, P, P, P, P]),
+        "fnn_param_grads": (I32, [P, P, P, P, P, P, P]),
         "fnn_energy_forces": (I32, [P, P, P, I32, P, P, P, P]),
         "fnn_energy_forces_host": (I32, [P, I32, I32, P, P, P, P, P, I32, P, P, P, P]),
         "fnn_sync": (I32, [P, P, P]),
@@ -153,6 +170,7 @@ class Context:
 
 def load_weights(ctx: Context, weights=None, path: str | None = None):
     """fnn_load_weights from a synth.Weights-like object (float32 arrays) or a file."""
+    ctx.param_stamp = None
     if path is not None:
         ctx._check(lib.fnn_load_weights(ctx.h, path.encode(), None), "fnn_load_weights")
         return
@@ -278,6 +296,86 @@ def aev(ctx: Context, system: DeviceSystem, nl: NeighborList, out=None, stream=N
     cs = system.c()
     ctx._check(lib.fnn_aev(ctx.h, ctypes.byref(cs), nl.h, _ptr(out), _stream(stream)), "fnn_aev")
     return out
+
+
+def aev_jvp(ctx: Context, system: DeviceSystem, nl: NeighborList, V, out=None, stream=None):
+    """fnn_aev_jvp: directional derivative [N, 1008] of the AEVs along the displacement field V [N, 3] (device)."""
+    import torch
+    if out is None:
+        out = torch.empty((system.n_atoms, 1008), dtype=torch.float32, device="cuda")
+    cs = system.c()
+    ctx._check(lib.fnn_aev_jvp(ctx.h, ctypes.byref(cs), nl.h, _ptr(V), _ptr(out), _stream(stream)), "fnn_aev_jvp")
+    return out
+
+
+def param_grads(ctx: Context, system: DeviceSystem, nl: NeighborList, dLdE, dLdF, grads: dict | None = None,
+                stream=None) -> dict:
+    """fnn_param_grads: ADDS dL/dtheta into grads (float32 device tensors shaped like the weights; zeros
+    when None) for the loss gradients dL/dE [n_mol] float64 and dL/dF [N,3] float32; returns grads."""
+    import torch
+    if grads is None:
+        grads = {k: torch.zeros(v, dtype=torch.float32, device="cuda")
+                 for k, v in param_shapes(ctx.cfg.n_members).items()}
+    dLdE = dLdE.to(torch.float64).contiguous()
+    dLdF = dLdF.to(torch.float32).contiguous()
+    cg = CGrads(*(grads[k].data_ptr() for k in PARAM_NAMES))
+    cs = system.c()
+    ctx._check(lib.fnn_param_grads(ctx.h, ctypes.byref(cs), nl.h, _ptr(dLdE), _ptr(dLdF), ctypes.byref(cg),
+                                   _stream(stream)), "fnn_param_grads")
+    return grads
+
+
+_FUNCTION = None
+
+
+def _function():
+    """torch.autograd.Function over fnn_energy_forces (forward) and fnn_param_grads (backward)."""
+    global _FUNCTION
+    if _FUNCTION is not None:
+        return _FUNCTION
+    import torch
+
+    class EnergyForces(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, ctx, system, nl, *params):
+            _load_params(ctx, params)
+            E, F, _ = energy_forces(ctx, system, nl, "fp32", virial=False)
+            fctx.ctx, fctx.system, fctx.nl = ctx, system, nl
+            fctx.stamp = ctx.param_stamp
+            return E, F
+
+        @staticmethod
+        def backward(fctx, gE, gF):
+            ctx = fctx.ctx
+            if ctx.param_stamp != fctx.stamp:
+                raise RuntimeError("the context's parameters changed between forward and backward")
+            system = fctx.system
+            if gE is None:
+                gE = torch.zeros(system.n_mol, dtype=torch.float64, device="cuda")
+            if gF is None:
+                gF = torch.zeros((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+            g = param_grads(ctx, system, fctx.nl, gE, gF)
+            return (None, None, None) + tuple(g[k] for k in PARAM_NAMES)
+
+    _FUNCTION = EnergyForces
+    return _FUNCTION
+
+
+def _load_params(ctx: Context, params):
+    """Upload the parameter tensors to the context when they differ from what it holds."""
+    stamp = tuple((p.data_ptr(), p._version) for p in params)
+    if getattr(ctx, "param_stamp", None) == stamp:
+        return
+    host = type("W", (), {k: p.detach().float().cpu().numpy() for k, p in zip(PARAM_NAMES, params)})
+    load_weights(ctx, host)
+    ctx.param_stamp = stamp
+
+
+def energy_forces_autograd(ctx: Context, system: DeviceSystem, nl: NeighborList, params):
+    """(E [n_mol] float64, F [N,3] float32) as differentiable functions of params (the eight weight
+    tensors in PARAM_NAMES order, float32): a loss built from E and F back-propagates into the
+    parameters through fnn_param_grads (section IV).  FP32 networks."""
+    return _function().apply(ctx, system, nl, *params)
 
 
 def energy_forces(ctx: Context, system: DeviceSystem, nl: NeighborList, precision: str = "fp32", virial: bool = True,

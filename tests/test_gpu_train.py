@@ -1,0 +1,161 @@
+"""Parity of the training-gradient path (section IV) with the float64 oracle.
+
+AEV tangents T = (dAEV/dx) V: float32 against float64, |d| <= 1e-4 * max|T| + 1e-6 (the
+tangent's chain rule through acos and the 14.1 power amplifies the float32 rounding of
+the AEV terms by at most about 30x).  Parameter gradients of
+L = 0.99 mean (F - F*)^2 + 0.01 mean_mol ((E - E*)/n)^2: each array's error, in the
+2-norm, at most 1e-4 of that array's norm, and every entry within 1e-3 of its largest
+entry: float32 GEMMs over K <= 1008 and float32 sums over every atom of an element
+give relative errors of order sqrt(n) u ~ 1e-5 of the summed magnitudes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01491_b300 import synth
+from conftest import structure, weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fnn():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2405_01491_b300 import fnn as f
+    return f
+
+
+def _setup(fnn, s, M, skin=0.0):
+    ctx = fnn.Context(M, skin=skin)
+    fnn.load_weights(ctx, weights(M))
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    return ctx, ds, nl
+
+
+@pytest.mark.parametrize("name,skin", [("gas24", 0.0), ("water216", 0.5), ("box300", 0.0), ("batch64", 1.0)])
+def test_aev_jvp_parity(fnn, name, skin):
+    import torch
+    s = structure(name)
+    ctx, ds, nl = _setup(fnn, s, 1, skin)
+    V = np.random.default_rng(11).normal(size=(s.n_atoms, 3))
+    T = fnn.aev_jvp(ctx, ds, nl, torch.from_numpy(V.astype(np.float32)).cuda()).cpu().numpy()
+    fnn.check(ctx)
+    want = oracle.aev_jvp(s, V.astype(np.float32).astype(np.float64))
+    tol = 1e-4 * np.abs(want).max() + 1e-6
+    assert np.abs(T - want).max() <= tol, (np.abs(T - want).max(), tol)
+
+
+def _loss_grads(fnn, s, M):
+    """GPU: loss from E, F of the autograd function, gradients by backward.  Oracle: the same loss and
+    gradients in float64."""
+    import torch
+    ctx, ds, nl = _setup(fnn, s, M)
+    w = weights(M)
+    params = [torch.tensor(np.asarray(getattr(w, k), np.float32), device="cuda", requires_grad=True)
+              for k in fnn.PARAM_NAMES]
+    E_ref, F_ref = synth.batch_targets(s)
+    n = torch.tensor(np.maximum(np.diff(s.mol_offsets), 1), dtype=torch.float64, device="cuda")
+    E, F = fnn.energy_forces_autograd(ctx, ds, nl, params)
+    Et = torch.tensor(E_ref, device="cuda")
+    Ft = torch.tensor(F_ref, dtype=torch.float32, device="cuda")
+    L = 0.99 * torch.mean((F.double() - Ft.double()) ** 2) + 0.01 * torch.mean(((E - Et) / n) ** 2)
+    L.backward()
+    fnn.check(ctx)
+    got = {k: p.grad.cpu().numpy().astype(np.float64) for k, p in zip(fnn.PARAM_NAMES, params)}
+    L_o, _, _, want = oracle.loss_and_weight_grads(s, w, E_ref, F_ref)
+    return float(L), L_o, got, want
+
+
+def _assert_grads(got, want):
+    for k in want:
+        g, r = got[k], want[k]
+        assert g.shape == r.shape, k
+        scale = np.abs(r).max()
+        assert scale > 0, k
+        err = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert err <= 1e-4, (k, err)
+        assert np.abs(g - r).max() <= 1e-3 * scale, (k, np.abs(g - r).max() / scale)
+
+
+@pytest.mark.parametrize("name,M", [("gas24", 1), ("water216", 2), ("batch64", 2)])
+def test_param_grads_parity(fnn, name, M):
+    s = structure(name)
+    L, L_o, got, want = _loss_grads(fnn, s, M)
+    assert L == pytest.approx(L_o, rel=1e-5)
+    _assert_grads(got, want)
+
+
+def test_param_grads_ragged_4096_sampled(fnn):
+    """4096 ragged molecules (8..64 atoms) in the benchmark's launch configuration: the full gradient
+    against the oracle's on the first 48 molecules' loss (gradients are additive over molecules, so
+    the GPU's gradient of the loss restricted to a sub-batch must equal the oracle's there)."""
+    import torch
+    s = structure("batch4096")
+    sub = 48
+    k = int(s.mol_offsets[sub])
+    part = synth.Structures(s.Z[:k], s.pos[:k], s.mol_offsets[:sub + 1], s.cell[:sub], s.pbc[:sub])
+    M = 2
+    ctx, ds, nl = _setup(fnn, s, M)
+    E_ref, F_ref = synth.batch_targets(s)
+    # loss restricted to the first `sub` molecules, with the oracle's normalisations for that sub-batch
+    w = weights(M)
+    params = [torch.tensor(np.asarray(getattr(w, kk), np.float32), device="cuda", requires_grad=True)
+              for kk in fnn.PARAM_NAMES]
+    E, F = fnn.energy_forces_autograd(ctx, ds, nl, params)
+    n = torch.tensor(np.maximum(np.diff(s.mol_offsets[:sub + 1]), 1), dtype=torch.float64, device="cuda")
+    Ft = torch.tensor(F_ref[:k], dtype=torch.float32, device="cuda")
+    L = (0.99 * torch.mean((F[:k].double() - Ft.double()) ** 2)
+         + 0.01 * torch.mean(((E[:sub] - torch.tensor(E_ref[:sub], device="cuda")) / n) ** 2))
+    L.backward()
+    fnn.check(ctx)
+    got = {kk: p.grad.cpu().numpy().astype(np.float64) for kk, p in zip(fnn.PARAM_NAMES, params)}
+    _, _, _, want = oracle.loss_and_weight_grads(part, w, E_ref[:sub], F_ref[:k])
+    _assert_grads(got, want)
+
+
+def test_param_grads_accumulate_and_zero_loss(fnn):
+    """The entry point adds into its outputs; zero loss gradients leave them unchanged."""
+    import torch
+    s = structure("gas24")
+    ctx, ds, nl = _setup(fnn, s, 1)
+    gE = torch.zeros(s.n_mol, dtype=torch.float64, device="cuda")
+    gF = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    g0 = fnn.param_grads(ctx, ds, nl, gE, gF)
+    fnn.check(ctx)
+    assert all(float(v.abs().max()) == 0.0 for v in g0.values())
+    gE = torch.linspace(-1, 1, s.n_mol, dtype=torch.float64, device="cuda")
+    gF = torch.from_numpy(np.random.default_rng(3).normal(size=(s.n_atoms, 3)).astype(np.float32)).cuda()
+    g1 = fnn.param_grads(ctx, ds, nl, gE, gF)
+    g2 = fnn.param_grads(ctx, ds, nl, gE, gF, grads={k: v.clone() for k, v in g1.items()})
+    fnn.check(ctx)
+    for k in g1:
+        torch.testing.assert_close(g2[k], 2 * g1[k], rtol=1e-5, atol=1e-6 * float(g1[k].abs().max()))
+
+
+def test_training_step_decreases_loss(fnn):
+    """A few plain gradient-descent steps on a ragged batch lower the loss (end-to-end use of the
+    autograd function, parameters re-uploaded after every update)."""
+    import torch
+    s = structure("batch64")
+    M = 1
+    ctx, ds, nl = _setup(fnn, s, M)
+    w = weights(M)
+    params = [torch.tensor(np.asarray(getattr(w, k), np.float32), device="cuda", requires_grad=True)
+              for k in fnn.PARAM_NAMES]
+    E_ref, F_ref = synth.batch_targets(s)
+    Et = torch.tensor(E_ref, device="cuda")
+    Ft = torch.tensor(F_ref, dtype=torch.float32, device="cuda")
+    n = torch.tensor(np.maximum(np.diff(s.mol_offsets), 1), dtype=torch.float64, device="cuda")
+    opt = torch.optim.Adam(params, lr=1e-4)
+    losses = []
+    for _ in range(5):
+        opt.zero_grad()
+        E, F = fnn.energy_forces_autograd(ctx, ds, nl, params)
+        L = 0.99 * torch.mean((F.double() - Ft.double()) ** 2) + 0.01 * torch.mean(((E - Et) / n) ** 2)
+        L.backward()
+        opt.step()
+        losses.append(float(L))
+    fnn.check(ctx)
+    assert losses[-1] < losses[0], losses
