@@ -317,6 +317,65 @@ def loss_and_weight_grads(s, w, E_ref: np.ndarray, F_ref: np.ndarray, params: Pa
     return L, E.detach().numpy(), F, {k: gk.numpy() for k, gk in zip(names, gr)}
 
 
+def celu_kink_deltas(s, w, E_ref: np.ndarray, F_ref: np.ndarray, band: float = 2e-5,
+                     params: Params = Params()):
+    """Pre-activations at the CELU kink and what each does to dL/dtheta.
+
+    The force term of the loss (section IV) differentiates dE/dAEV once more, so its parameter
+    gradient holds CELU''(z), which is 0 for z > 0 and exp(z/alpha)/alpha below: a jump of
+    1/alpha at z = 0.  An evaluation whose pre-activation z is within its rounding error of 0
+    may take either side, and both results are gradients of the loss (one-sided limits).
+    For every pre-activation with |z| <= band * (sum_j |W_uj h_j| + |b_u|) this returns
+    (m, e, layer, atom, unit, deltas): deltas[name] [shape of the weight's (m, e) block] is the
+    change of the gradient when that one entry takes the other side.  With zd the tangent of z along
+    J dL/dF and gb = d(-<J dL/dF, dE/dAEV>)/dhd at the entry, the other side changes
+    dL/dz there by -/+ (1/alpha) CELU'(z) zd gb (minus when z <= 0: the term leaves); that
+    change flows down the layers below through W^T and CELU' alone (linear in it)."""
+    g = Graph(s, params)
+    r = energy_forces(s, w, params)
+    v = FORCE_WEIGHT * 2.0 * (r.forces - F_ref) / r.forces.size
+    T = aev_jvp(s, v, params, g)
+    A = r.aev
+    el = elements(s.Z)
+    M = w.n_members
+    out = []
+    for e in range(7):
+        rows = np.nonzero(el == e)[0]
+        if rows.size == 0:
+            continue
+        for m in range(M):
+            W1, b1, W2, b2, W3, b3, w4, _ = _layers(w, m, e)
+            Ws, bs = (W1, W2, W3), (b1, b2, b3)
+            h, hd, z, mag = [A[rows]], [T[rows]], [], []
+            for W, b in zip(Ws, bs):
+                zl = h[-1] @ W.T + b
+                z.append(zl)
+                mag.append(np.abs(h[-1]) @ np.abs(W).T + np.abs(b))
+                hd.append(dcelu(zl) * (hd[-1] @ W.T))
+                h.append(celu(zl))
+            # gb_l = dPhi/dhd_l, Phi's tangent part -<t, G> = -(1/M) sum w4 . hd_3
+            gb = [None, None, None]
+            gb[2] = np.broadcast_to(-w4 / M, hd[3].shape)
+            gb[1] = (dcelu(z[2]) * gb[2]) @ W3
+            gb[0] = (dcelu(z[1]) * gb[1]) @ W2
+            for l in range(3):
+                rr, uu = np.nonzero(np.abs(z[l]) <= band * mag[l])
+                for ri, u in zip(rr, uu):
+                    zv = z[l][ri, u]
+                    d_gz = (1.0 if zv > 0 else -1.0) / CELU_ALPHA * hd[l + 1][ri, u] * gb[l][ri, u]
+                    deltas = {k: np.zeros(np.shape(getattr(w, k))[2:]) for k in ("W1", "b1", "W2", "b2", "W3",
+                                                                                 "b3", "w4", "b4")}
+                    gz = np.zeros(Ws[l].shape[0])
+                    gz[u] = d_gz
+                    for k in range(l, -1, -1):
+                        deltas[f"W{k + 1}"] += np.outer(gz, h[k][ri])
+                        deltas[f"b{k + 1}"] += gz
+                        if k > 0:
+                            gz = dcelu(z[k - 1][ri]) * (gz @ Ws[k])
+                    out.append((m, e, l + 1, int(rows[ri]), int(u), deltas))
+    return out
+
+
 # ----------------------------------------------------------------------------- dynamics (section V.D)
 
 # atomic masses (amu), element order H C N O F S Cl

@@ -69,12 +69,13 @@ __global__ void k_out_reverse(int M, const int32_t *tile_elem, const int32_t *in
     const size_t r = (size_t)tile * ROW_TILE + rr;
     const int i = inv[r];
     const size_t o = r * (size_t)M * H3 + (size_t)m * H3 + n;
-    if (i < 0) {
+    const int mol = i < 0 ? -1 : atom_mol[i];   // -1: padding, or an atom outside every structure
+    if (mol < 0) {
       gb3[o] = 0.f;
       gz3[o] = 0.f;
       continue;
     }
-    const float cE = (float)dLdE[atom_mol[i]] * c;
+    const float cE = (float)dLdE[mol] * c;
     const float h = h3[o], hd = hd3[o];
     const float s1 = dcelu_h(h);
     const float gb = -c * w, g = cE * w;

@@ -6,7 +6,13 @@ the AEV terms by at most about 30x).  Parameter gradients of
 L = 0.99 mean (F - F*)^2 + 0.01 mean_mol ((E - E*)/n)^2: each array's error, in the
 2-norm, at most 1e-4 of that array's norm, and every entry within 1e-3 of its largest
 entry: float32 GEMMs over K <= 1008 and float32 sums over every atom of an element
-give relative errors of order sqrt(n) u ~ 1e-5 of the summed magnitudes."""
+give relative errors of order sqrt(n) u ~ 1e-5 of the summed magnitudes.
+
+The force term's gradient holds CELU''(z), which jumps by 1/alpha at z = 0.  Where a
+pre-activation lies within float32 rounding of 0 (oracle.celu_kink_deltas lists them, with
+the jump each causes), both one-sided values are gradients of the loss; the comparison
+takes, per kink entry, the side the GPU's result is nearest to (least squares over the
+entries of each network, rounded to 0/1) and then applies the tolerances above."""
 import numpy as np
 import pytest
 
@@ -65,7 +71,29 @@ def _loss_grads(fnn, s, M):
     fnn.check(ctx)
     got = {k: p.grad.cpu().numpy().astype(np.float64) for k, p in zip(fnn.PARAM_NAMES, params)}
     L_o, _, _, want = oracle.loss_and_weight_grads(s, w, E_ref, F_ref)
-    return float(L), L_o, got, want
+    want, _ = _resolve_kinks(got, want, oracle.celu_kink_deltas(s, w, E_ref, F_ref))
+    return float(L.detach()), L_o, got, want
+
+
+def _resolve_kinks(got, want, kinks):
+    """The valid gradient nearest to got: want plus the jumps of the kink entries the GPU took on
+    the other side.  Returns it and the number of such entries."""
+    names = list(want)
+    want = {k: v.copy() for k, v in want.items()}
+    blocks = {}
+    for m, e, _l, _atom, _u, d in kinks:
+        blocks.setdefault((m, e), []).append(d)
+    flipped = 0
+    for (m, e), ds in blocks.items():
+        res = np.concatenate([(got[k][m, e] - want[k][m, e]).ravel() for k in names])
+        D = np.stack([np.concatenate([np.ravel(d[k]) for k in names]) for d in ds], axis=1)
+        coef = np.clip(np.rint(np.linalg.lstsq(D, res, rcond=None)[0]), 0, 1)
+        for d, c in zip(ds, coef):
+            if c:
+                flipped += 1
+                for k in names:
+                    want[k][m, e] += d[k]
+    return want, flipped
 
 
 def _assert_grads(got, want):
@@ -112,6 +140,7 @@ def test_param_grads_ragged_4096_sampled(fnn):
     fnn.check(ctx)
     got = {kk: p.grad.cpu().numpy().astype(np.float64) for kk, p in zip(fnn.PARAM_NAMES, params)}
     _, _, _, want = oracle.loss_and_weight_grads(part, w, E_ref[:sub], F_ref[:k])
+    want, _ = _resolve_kinks(got, want, oracle.celu_kink_deltas(part, w, E_ref[:sub], F_ref[:k]))
     _assert_grads(got, want)
 
 
@@ -156,6 +185,6 @@ def test_training_step_decreases_loss(fnn):
         L = 0.99 * torch.mean((F.double() - Ft.double()) ** 2) + 0.01 * torch.mean(((E - Et) / n) ** 2)
         L.backward()
         opt.step()
-        losses.append(float(L))
+        losses.append(float(L.detach()))
     fnn.check(ctx)
     assert losses[-1] < losses[0], losses

@@ -162,3 +162,56 @@ def test_velocity_verlet_conserves_energy_and_is_time_reversible():
     back = synth.Structures(s.Z, x1, s.mol_offsets, s.cell, s.pbc)
     _, x0, _, _ = oracle.velocity_verlet(back, w, -v1, 21, 0.2)
     np.testing.assert_allclose(x0, s.pos.astype(np.float64), atol=1e-9)
+
+
+def test_celu_kink_deltas_are_one_sided_gradient_jumps():
+    """Put one pre-activation exactly on the CELU kink by shifting its bias, then the loss gradients
+    just above and just below it (float64 autograd) differ by the jump celu_kink_deltas predicts."""
+    s = structure("gas24")
+    base = weights(1)
+    names = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
+
+    class W64:
+        n_members = 1
+
+    def with_bias(layer, e, u, value):
+        w = W64()
+        for k in names:
+            setattr(w, k, np.array(getattr(base, k), np.float64))
+        getattr(w, f"b{layer}")[0, e, u] = value
+        return w
+
+    E_ref, F_ref = synth.batch_targets(s)
+    el = oracle.elements(s.Z)
+    A = oracle.aev(s)
+    checked = 0
+    for layer, e in [(1, 1), (2, 0), (3, 3)]:
+        rows = np.nonzero(el == e)[0]
+        W1, b1, W2, b2, W3, b3, _, _ = oracle._layers(base, 0, e)
+        h = A[rows]
+        for W, b in [(W1, b1), (W2, b2), (W3, b3)][:layer]:
+            z = h @ W.T + b
+            h = oracle.celu(z)
+        # moving the row nearest the kink onto it keeps every other row of the unit on its side
+        for u in range(z.shape[1]):
+            ri = int(np.argmin(np.abs(z[:, u])))
+            if np.min(np.abs(np.delete(z[:, u], ri) - z[ri, u]), initial=1.0) < 1e-3:
+                continue
+            b0 = float([b1, b2, b3][layer - 1][u]) - z[ri, u]
+            eps = 1e-9
+            lo, hi = with_bias(layer, e, u, b0 - eps), with_bias(layer, e, u, b0 + eps)
+            g_lo = oracle.loss_and_weight_grads(s, lo, E_ref, F_ref)[3]
+            g_hi = oracle.loss_and_weight_grads(s, hi, E_ref, F_ref)[3]
+            found = [d for (m, ee, l, atom, uu, d) in oracle.celu_kink_deltas(s, lo, E_ref, F_ref)
+                     if (m, ee, l, atom, uu) == (0, e, layer, int(rows[ri]), u)]
+            assert len(found) == 1
+            d = found[0]
+            jump = sum(np.linalg.norm(d[k]) for k in names)
+            assert jump > 0
+            for k in names:
+                np.testing.assert_allclose(g_hi[k][0, e] - g_lo[k][0, e], d[k], rtol=0, atol=1e-6 * jump)
+                other = np.delete(g_hi[k] - g_lo[k], e, axis=1)
+                assert np.abs(other).max() <= 1e-6 * jump
+            checked += 1
+            break
+    assert checked == 3
