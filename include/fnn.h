@@ -173,6 +173,15 @@ fnn_status fnn_aev_jvp(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl,
 fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec,
                              double *E, float *F, double *virial, void *stream);
 
+/* FP8 form (FNN_FP8): e4m3 operands on the tensor cores with per-layer scaling.  Every weight block
+ * (member, element, layer) is scaled by amax/448 at load (the transposed first layer, whose
+ * reduction runs over all members, by one scale per element); every activation tensor of a layer
+ * (AEV, h1, h2 and the three backward tensors) by one scale, 2 amax/448, measured by an FP32
+ * evaluation of sys here.  Conversions round to nearest and saturate.  Synchronises the stream.  An
+ * FP8 call on a context that was never calibrated (or whose weights were reloaded) calibrates on its
+ * own system first. */
+fnn_status fnn_calibrate_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, void *stream);
+
 /* The same computation from HOST arrays: copies the inputs to library-owned
  * device buffers, rebuilds the neighbour list, evaluates, copies E [n_mol],
  * F [N][3] and (optional) virial [n_mol][9] back to the host arrays, and

@@ -15,6 +15,7 @@
 // from a padded shared row, chains the partials to dE/dd per neighbour in shared memory, then the
 // warp scatters them to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fnn_internal.cuh"
 
@@ -177,17 +178,22 @@ __device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
 __device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
 template <typename OutT>
-__device__ __forceinline__ void store_out(OutT *p, float v);
+__device__ __forceinline__ void store_out(OutT *p, float v, float inv);
 template <>
-__device__ __forceinline__ void store_out<float>(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_out<float>(float *p, float v, float) { *p = v; }
 template <>
-__device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16 *p, float v) { *p = __float2bfloat16(v); }
+__device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16(v); }
+template <>   // fp8 e4m3 of v * inv, saturating
+__device__ __forceinline__ void store_out<__nv_fp8_e4m3>(__nv_fp8_e4m3 *p, float v, float inv) {
+  p->__x = __nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
+}
 
 struct AevFwdArgs {
   StageArgs sa;
   AevParams P;
   float *out;             // [rows][1008]
   __nv_bfloat16 *out_lo;  // low bf16 half of a split output, or NULL
+  float out_inv;          // fp8 outputs hold aev * out_inv
   const int32_t *inv;     // padded row -> atom (-1 padding); NULL = rows are atoms
   const int32_t *meta;    // META_NPAD when inv != NULL
   int n_atoms;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
     bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, false, A.st);
     if (!ok) {
       for (int c = lane; c < NAEV; c += 32) {
-        store_out<OutT>(out + c, 0.f);
+        store_out<OutT>(out + c, 0.f, A.out_inv);
         store_lo(lo, c, 0.f);
       }
       __syncwarp();
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
         if (lane < 16) {
-          store_out<OutT>(out + q * NSR + k, 0.25f * acc);
+          store_out<OutT>(out + q * NSR + k, 0.25f * acc, A.out_inv);
           store_lo(lo, q * NSR + k, 0.25f * acc);
         }
       }
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
       if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
       __syncwarp();
       for (int c = lane; c < NPAIR * 32; c += 32) {
-        store_out<OutT>(out + NRAD + c, W.acc[c]);
+        store_out<OutT>(out + NRAD + c, W.acc[c], A.out_inv);
         store_lo(lo, NRAD + c, W.acc[c]);
       }
     }
@@ -625,6 +631,7 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   a.P = ctx->aev;
   a.out = out;
   a.out_lo = nullptr;
+  a.out_inv = 1.f;
   a.inv = inv;
   a.meta = nl->meta;
   a.n_atoms = sys->n_atoms;
@@ -645,6 +652,7 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
   a.P = ctx->aev;
   a.out = reinterpret_cast<float *>(out);
   a.out_lo = out_lo;
+  a.out_inv = 1.f;
   a.inv = inv;
   a.meta = nl->meta;
   a.n_atoms = sys->n_atoms;
@@ -656,6 +664,27 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
     k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_bf16");
+}
+
+fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, uint8_t *out,
+                                  float out_inv, const int32_t *inv, cudaStream_t s) {
+  AevFwdArgs a;
+  a.sa = stage_args(sys, nl);
+  a.P = ctx->aev;
+  a.out = reinterpret_cast<float *>(out);
+  a.out_lo = nullptr;
+  a.out_inv = out_inv;
+  a.inv = inv;
+  a.meta = nl->meta;
+  a.n_atoms = sys->n_atoms;
+  a.st = ctx->status;
+  int64_t rows = inv ? nl->pad_cap : sys->n_atoms;
+  if (rows == 0) return FNN_OK;
+  {
+    FNN_KERNEL(ctx, "aev_forward_fp8", s);
+    k_aev_forward<__nv_fp8_e4m3><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+  }
+  return check_launch(ctx, "aev_forward_fp8");
 }
 
 fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *gaev,

@@ -305,6 +305,19 @@ extern "C" fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, con
   return launch_aev_adjoint(ctx, sys, nl, ctx->ws.gaev, nl->inv, F, virial, s);
 }
 
+extern "C" fnn_status fnn_calibrate_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, void *stream) {
+  if (!ctx || !sys || !nl) return FNN_E_INVALID;
+  if (!ctx->has_weights) {
+    ctx->last_error = "no weights loaded";
+    return FNN_E_STATE;
+  }
+  if (!nl->built || nl->n_atoms != sys->n_atoms || nl->n_mol != sys->n_mol) {
+    ctx->last_error = "neighbour list was not built for this system";
+    return FNN_E_STATE;
+  }
+  return fp8_calibrate(ctx, sys, nl, (cudaStream_t)stream);
+}
+
 __global__ void k_pack_pos(int n, const float *p3, float4 *p4) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p4[i] = make_float4(p3[3 * i], p3[3 * i + 1], p3[3 * i + 2], 0.f);

@@ -254,6 +254,7 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
 fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const float *W1Tcat, const float *W2,
                              const float *W2T, const float *W3, const float *W3T);
 void free_tc(fnn_ctx *ctx);
+fnn_status fp8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, cudaStream_t s);
 void free_train(fnn_ctx *ctx);
 fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s);
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,

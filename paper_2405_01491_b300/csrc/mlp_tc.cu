@@ -9,8 +9,17 @@
 //   L1' dE/dAEV = g1 W1cat                       NT = 256, N = 1008, K = M*256, fp32 out
 // Activations between layers are bf16 in HBM; operands reach shared memory by TMA (3-D tensor maps
 // whose middle coordinate selects the member, so each member's K range ends in zero fill).
+//
+// FP8 form: the same six products with e4m3 operands (tcgen05 kind::f8f6f4) and per-layer scaling.
+// Each weight block (member, element, layer) carries the scale amax / 448 (W1^T one per element, as
+// its K runs over all members); each activation tensor (AEV, h1, h2, g3, g2, g1) one scale per
+// layer, 2 amax / 448 from a calibration evaluation in FP32 (x2 headroom; conversions saturate).  The
+// epilogue multiplies the fp32 accumulator by a_scale * b_scale and writes its output as
+// e4m3(x / out_scale).
 #include <cudaTypedefs.h>
 
+#include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "tc_gemm.cuh"
@@ -33,13 +42,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D bf16 tensor map: dims (d0 innermost, d1, d2), byte strides of d1 and d2, box (b0, b1, b2), 128-byte swizzle
 bool encode3d(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
-              uint32_t b0, uint32_t b1, uint32_t b2) {
+              uint32_t b0, uint32_t b1, uint32_t b2, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
   cuuint64_t str[2] = {s1, s2};
   cuuint32_t box[3] = {b0, b1, b2}, es[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, str, box, es,
+  return enc(m, dt, 3, const_cast<void *>(base), dims, str, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -53,12 +62,28 @@ struct Half {
   CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
 };
 
+// e4m3 operands of the FP8 form and their scales
+struct F8 {
+  uint8_t *wbuf = nullptr;
+  uint8_t *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
+  CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
+  float *wscale = nullptr;   // device [6][M*7] in the order W1, W1T, W2, W2T, W3, W3T; W1T per element only
+  uint8_t *abuf = nullptr;
+  size_t rows = 0;
+  uint8_t *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+  unsigned *amax = nullptr;  // device [6] calibration maxima (float bits)
+  float act[6] = {1, 1, 1, 1, 1, 1};  // scales of aev, h1, h2, g3, g2, g1
+  bool calibrated = false;
+};
+
 struct TcState {
   int M = 0;
   __nv_bfloat16 *wbuf = nullptr;
   __nv_bfloat16 *abuf = nullptr;
   size_t rows = 0;
   Half h[2];   // [0] hi, [1] lo
+  F8 f8;
 };
 
 TcState *state(fnn_ctx *ctx) {
@@ -66,7 +91,7 @@ TcState *state(fnn_ctx *ctx) {
   return static_cast<TcState *>(ctx->w.tc);
 }
 
-template <int NT, int EPI, bool SPLIT>
+template <int NT, int EPI, int MODE>
 fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B,
                   const CUtensorMap &A_lo, const CUtensorMap &B_lo, tc::Args a, dim3 tiles, cudaStream_t s) {
   // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
@@ -79,11 +104,11 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CU
   const size_t sm = tc::smem_bytes<NT>();
   if (!attr_set) {
     FNN_CUDA_TRY(ctx,
-                 cudaFuncSetAttribute(tc::k_umma<NT, EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                 cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI, SPLIT><<<grid, tc::THREADS, sm, s>>>(A, B, A_lo, B_lo, a);
+  tc::k_umma<NT, EPI, MODE><<<grid, tc::THREADS, sm, s>>>(A, B, A_lo, B_lo, a);
   return check_launch(ctx, name);
 }
 
@@ -94,8 +119,78 @@ void free_tc(fnn_ctx *ctx) {
   if (!t) return;
   if (t->wbuf) cudaFree(t->wbuf);
   if (t->abuf) cudaFree(t->abuf);
+  if (t->f8.wbuf) cudaFree(t->f8.wbuf);
+  if (t->f8.wscale) cudaFree(t->f8.wscale);
+  if (t->f8.abuf) cudaFree(t->f8.abuf);
+  if (t->f8.amax) cudaFree(t->f8.amax);
   delete t;
   ctx->w.tc = nullptr;
+}
+
+// e4m3 copies of the six layer matrices, each (member, element) block scaled by its amax / 448
+static fnn_status upload_f8_weights(fnn_ctx *ctx, TcState *t, const float *const src[6], const size_t len[6]) {
+  F8 &f = t->f8;
+  const int M = t->M;
+  if (f.wbuf) cudaFree(f.wbuf);
+  if (f.wscale) cudaFree(f.wscale);
+  f.wbuf = nullptr;
+  f.wscale = nullptr;
+  f.calibrated = false;
+  size_t total = 0, off[6];
+  for (int k = 0; k < 6; k++) {
+    off[k] = total;
+    total += len[k];
+  }
+  std::vector<uint8_t> q(total);
+  std::vector<float> scale((size_t)6 * M * NE, 1.f);
+  // block b of matrix k: element e, member m; returns the indices of its entries through a visitor
+  auto visit = [&](int k, int m, int e, auto fn) {
+    const float *w = src[k];
+    if (k == 0) {          // W1cat [7][M*256][1008]: rows m*256.. of element e
+      const size_t b = ((size_t)e * M + m) * H1 * NAEV;
+      for (size_t i = 0; i < (size_t)H1 * NAEV; i++) fn(b + i, w[b + i]);
+    } else if (k == 1) {   // W1Tcat [7][1008][M*256]: all members of element e
+      const size_t b = (size_t)e * NAEV * M * H1;
+      for (size_t i = 0; i < (size_t)NAEV * M * H1; i++) fn(b + i, w[b + i]);
+    } else {               // [M][7][out][in]
+      const size_t n = (k < 4) ? (size_t)H2 * H1 : (size_t)H3 * H2;
+      const size_t b = ((size_t)m * NE + e) * n;
+      for (size_t i = 0; i < n; i++) fn(b + i, w[b + i]);
+    }
+  };
+  for (int k = 0; k < 6; k++)
+    for (int m = 0; m < (k == 1 ? 1 : M); m++)
+      for (int e = 0; e < NE; e++) {
+        float amax = 0.f;
+        visit(k, m, e, [&](size_t, float x) { amax = fmaxf(amax, fabsf(x)); });
+        const float sc = amax > 0.f ? amax / 448.f : 1.f;
+        scale[(size_t)k * M * NE + (size_t)m * NE + e] = sc;
+        const float inv = 1.f / sc;
+        visit(k, m, e, [&](size_t i, float x) { q[off[k] + i] = __nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3); });
+      }
+  if (cudaMalloc(&f.wbuf, total) != cudaSuccess || cudaMalloc(&f.wscale, scale.size() * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for fp8 weights";
+    return FNN_E_OOM;
+  }
+  FNN_CUDA_TRY(ctx, cudaMemcpy(f.wbuf, q.data(), total, cudaMemcpyHostToDevice));
+  FNN_CUDA_TRY(ctx, cudaMemcpy(f.wscale, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
+  f.W1 = f.wbuf + off[0]; f.W1T = f.wbuf + off[1]; f.W2 = f.wbuf + off[2];
+  f.W2T = f.wbuf + off[3]; f.W3 = f.wbuf + off[4]; f.W3T = f.wbuf + off[5];
+  const uint64_t G = (uint64_t)M * NE;
+  const CUtensorMapDataType U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  bool ok = encode3d(&f.mW1, f.W1, NAEV, (uint64_t)M * H1, NE, NAEV, (uint64_t)M * H1 * NAEV, 128, 256, 1, U8) &&
+            encode3d(&f.mW1T, f.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1, (uint64_t)NAEV * M * H1, 128, 256,
+                     1, U8) &&
+            encode3d(&f.mW2, f.W2, H1, H2, G, H1, (uint64_t)H2 * H1, 128, H2, 1, U8) &&
+            encode3d(&f.mW2T, f.W2T, H2, H1, G, H2, (uint64_t)H1 * H2, 128, H1, 1, U8) &&
+            encode3d(&f.mW3, f.W3, H2, H3, G, H2, (uint64_t)H3 * H2, 128, H3, 1, U8) &&
+            encode3d(&f.mW3T, f.W3T, H3, H2, G, H3, (uint64_t)H2 * H3, 128, H2, 1, U8);
+  if (!ok) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the fp8 weight maps";
+    return FNN_E_CUDA;
+  }
+  return FNN_OK;
 }
 
 // bf16 hi and lo halves of the layer matrices in the FP32 form's layouts (host arrays in those layouts):
@@ -146,7 +241,7 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
       return FNN_E_CUDA;
     }
   }
-  return FNN_OK;
+  return upload_f8_weights(ctx, t, src, len);
 }
 
 static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
@@ -191,11 +286,93 @@ static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
 
 fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, __nv_bfloat16 *out,
                                    __nv_bfloat16 *out_lo, const int32_t *inv, cudaStream_t s);
+fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, uint8_t *out,
+                                  float out_inv, const int32_t *inv, cudaStream_t s);
+
+static fnn_status f8_workspace(fnn_ctx *ctx, size_t rows) {
+  TcState *t = state(ctx);
+  F8 &f = t->f8;
+  const int M = t->M;
+  if (f.abuf && rows <= f.rows) return FNN_OK;
+  rows = rows + rows / 8;
+  if (f.abuf) cudaFree(f.abuf);
+  f.abuf = nullptr;
+  const size_t per_row = NAEV + (size_t)M * (H1 + H2 + H3 + H2 + H1);
+  if (cudaMalloc(&f.abuf, rows * per_row) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for fp8 activations";
+    return FNN_E_OOM;
+  }
+  f.rows = rows;
+  const uint64_t R = rows;
+  uint8_t *p = f.abuf;
+  f.aev = p; p += rows * NAEV;
+  f.h1 = p; p += rows * M * H1;
+  f.h2 = p; p += rows * M * H2;
+  f.g3 = p; p += rows * M * H3;
+  f.g2 = p; p += rows * M * H2;
+  f.g1 = p;
+  const CUtensorMapDataType U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  bool ok = encode3d(&f.mAev, f.aev, NAEV, 1, R, NAEV, NAEV, 128, 1, 128, U8) &&
+            encode3d(&f.mH1, f.h1, H1, M, R, H1, (uint64_t)M * H1, 128, 1, 128, U8) &&
+            encode3d(&f.mH2, f.h2, H2, M, R, H2, (uint64_t)M * H2, 128, 1, 128, U8) &&
+            encode3d(&f.mG3, f.g3, H3, M, R, H3, (uint64_t)M * H3, 128, 1, 128, U8) &&
+            encode3d(&f.mG2, f.g2, H2, M, R, H2, (uint64_t)M * H2, 128, 1, 128, U8) &&
+            encode3d(&f.mG1, f.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1, (uint64_t)M * H1, 128, 1, 128, U8);
+  if (!ok) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the fp8 activation maps";
+    return FNN_E_CUDA;
+  }
+  return FNN_OK;
+}
+
+// max |x| over the rows of live tiles of a [rows][width] fp32 tensor, into *out (float bits)
+__global__ void k_amax(const float *x, long long width, long long n, const int32_t *tile_elem, unsigned *out) {
+  float mx = 0.f;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    if (tile_elem[k / width / ROW_TILE] >= 0) mx = fmaxf(mx, fabsf(x[k]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+// Activation scales of the FP8 form from one FP32 evaluation of this system (synchronises the stream).
+static fnn_status f8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, cudaStream_t s) {
+  TcState *t = state(ctx);
+  F8 &f = t->f8;
+  fnn_status st;
+  if ((st = ensure_workspace(ctx, nl->pad_cap))) return st;
+  Workspace &ws = ctx->ws;
+  if ((st = launch_aev_forward(ctx, sys, nl, ws.aev, nl->inv, s))) return st;
+  if ((st = mlp_fp32_forward_backward(ctx, nl, s))) return st;
+  if (!f.amax) FNN_CUDA_TRY(ctx, cudaMalloc(&f.amax, 6 * sizeof(unsigned)));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(f.amax, 0, 6 * sizeof(unsigned), s));
+  const int M = t->M;
+  const float *src[6] = {ws.aev, ws.h1, ws.h2, ws.g3, ws.g2, ws.g1};
+  const long long width[6] = {NAEV, (long long)M * H1, (long long)M * H2, (long long)M * H3, (long long)M * H2,
+                              (long long)M * H1};
+  for (int k = 0; k < 6; k++) {
+    FNN_KERNEL(ctx, "fp8_amax", s);
+    k_amax<<<2 * ctx->num_sms, 256, 0, s>>>(src[k], width[k], (long long)nl->pad_cap * width[k], nl->tile_elem,
+                                            f.amax + k);
+  }
+  if ((st = check_launch(ctx, "fp8_amax"))) return st;
+  unsigned bits[6];
+  FNN_CUDA_TRY(ctx, cudaMemcpyAsync(bits, f.amax, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  FNN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  for (int k = 0; k < 6; k++) {
+    float a;
+    memcpy(&a, &bits[k], sizeof a);
+    f.act[k] = (a > 0.f && std::isfinite(a)) ? 2.f * a / 448.f : 1.f;
+  }
+  f.calibrated = true;
+  return FNN_OK;
+}
 
 namespace {
 
 template <bool SPLIT>
 fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_t s) {
+  constexpr int MODE = SPLIT ? tc::MODE_SPLIT : tc::MODE_BF16;
   const DeviceWeights &w = ctx->w;
   const Half &H = t->h[0], &L = t->h[SPLIT ? 1 : 0];
   const int M = w.M;
@@ -212,13 +389,13 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
   a.out = H.h1; a.out_lo = L.h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch<256, tc::EPI_BIAS_CELU, SPLIT>(ctx, nm[0], H.mAev, H.mW1, L.mAev, L.mW1, a, dim3(M, tiles, 1), s)))
+  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(ctx, nm[0], H.mAev, H.mW1, L.mAev, L.mW1, a, dim3(M, tiles, 1), s)))
     return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
   a.out = H.h2; a.out_lo = L.h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
-  if ((st = launch<192, tc::EPI_BIAS_CELU, SPLIT>(ctx, nm[1], H.mH1, H.mW2, L.mH1, L.mW2, a, dim3(1, tiles, M), s)))
+  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(ctx, nm[1], H.mH1, H.mW2, L.mH1, L.mW2, a, dim3(1, tiles, M), s)))
     return st;
   // L3 + output layer
   a.K = H2; a.N = H3;
@@ -226,36 +403,101 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
   a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
   a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
-  if ((st = launch<160, tc::EPI_L3, SPLIT>(ctx, nm[2], H.mH2, H.mW3, L.mH2, L.mW3, a, dim3(1, tiles, M), s)))
+  if ((st = launch<160, tc::EPI_L3, MODE>(ctx, nm[2], H.mH2, H.mW3, L.mH2, L.mW3, a, dim3(1, tiles, M), s)))
     return st;
   // L3 backward
   a.K = H3; a.N = H2;
   a.out = H.g2; a.out_lo = L.g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
   a.aux = H.h2; a.aux_lo = L.h2; a.ldaux = (long long)M * H2; a.aux_mstride = H2;
-  if ((st = launch<192, tc::EPI_DCELU, SPLIT>(ctx, nm[3], H.mG3, H.mW3T, L.mG3, L.mW3T, a, dim3(1, tiles, M), s)))
+  if ((st = launch<192, tc::EPI_DCELU, MODE>(ctx, nm[3], H.mG3, H.mW3T, L.mG3, L.mW3T, a, dim3(1, tiles, M), s)))
     return st;
   // L2 backward
   a.K = H2; a.N = H1;
   a.out = H.g1; a.out_lo = L.g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
   a.aux = H.h1; a.aux_lo = L.h1; a.ldaux = (long long)M * H1; a.aux_mstride = H1;
-  if ((st = launch<256, tc::EPI_DCELU, SPLIT>(ctx, nm[4], H.mG2, H.mW2T, L.mG2, L.mW2T, a, dim3(1, tiles, M), s)))
+  if ((st = launch<256, tc::EPI_DCELU, MODE>(ctx, nm[4], H.mG2, H.mW2T, L.mG2, L.mW2T, a, dim3(1, tiles, M), s)))
     return st;
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
-  return launch<256, tc::EPI_F32, SPLIT>(ctx, nm[5], H.mG1, H.mW1T, L.mG1, L.mW1T, a,
+  return launch<256, tc::EPI_F32, MODE>(ctx, nm[5], H.mG1, H.mW1T, L.mG1, L.mW1T, a,
                                          dim3((NAEV + 255) / 256, tiles, 1), s);
+}
+
+// The six products with e4m3 operands; scales as described at the top of this file.
+fnn_status run_layers_f8(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_t s) {
+  constexpr int MODE = tc::MODE_F8;
+  const DeviceWeights &w = ctx->w;
+  const F8 &f = t->f8;
+  const int M = w.M;
+  const long long MNE = (long long)M * NE;
+  const unsigned tiles = (unsigned)(nl->pad_cap / ROW_TILE);
+  fnn_status st;
+  tc::Args a{};
+  a.tile_elem = nl->tile_elem;
+  a.st = ctx->status;
+  a.M = M;
+  // L1: member = n tile
+  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
+  a.out = f.h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
+  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
+  a.a_scale = f.act[0]; a.b_scale = f.wscale; a.b_scale_by = 2; a.out_inv = 1.f / f.act[1];
+  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(ctx, "fp8_l1_fwd", f.mAev, f.mW1, f.mAev, f.mW1, a, dim3(M, tiles, 1), s)))
+    return st;
+  // L2
+  a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
+  a.out = f.h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
+  a.a_scale = f.act[1]; a.b_scale = f.wscale + 2 * MNE; a.b_scale_by = 1; a.out_inv = 1.f / f.act[2];
+  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(ctx, "fp8_l2_fwd", f.mH1, f.mW2, f.mH1, f.mW2, a, dim3(1, tiles, M), s)))
+    return st;
+  // L3 + output layer
+  a.K = H2; a.N = H3;
+  a.out = f.g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
+  a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
+  a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
+  a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
+  a.a_scale = f.act[2]; a.b_scale = f.wscale + 4 * MNE; a.out_inv = 1.f / f.act[3];
+  if ((st = launch<160, tc::EPI_L3, MODE>(ctx, "fp8_l3_fwd", f.mH2, f.mW3, f.mH2, f.mW3, a, dim3(1, tiles, M), s)))
+    return st;
+  // L3 backward
+  a.K = H3; a.N = H2;
+  a.out = f.g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.aux = reinterpret_cast<const __nv_bfloat16 *>(f.h2); a.ldaux = (long long)M * H2; a.aux_mstride = H2;
+  a.aux_scale = f.act[2];
+  a.a_scale = f.act[3]; a.b_scale = f.wscale + 5 * MNE; a.out_inv = 1.f / f.act[4];
+  if ((st = launch<192, tc::EPI_DCELU, MODE>(ctx, "fp8_l3_bwd", f.mG3, f.mW3T, f.mG3, f.mW3T, a, dim3(1, tiles, M), s)))
+    return st;
+  // L2 backward
+  a.K = H2; a.N = H1;
+  a.out = f.g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
+  a.aux = reinterpret_cast<const __nv_bfloat16 *>(f.h1); a.ldaux = (long long)M * H1; a.aux_mstride = H1;
+  a.aux_scale = f.act[1];
+  a.a_scale = f.act[4]; a.b_scale = f.wscale + 3 * MNE; a.out_inv = 1.f / f.act[5];
+  if ((st = launch<256, tc::EPI_DCELU, MODE>(ctx, "fp8_l2_bwd", f.mG2, f.mW2T, f.mG2, f.mW2T, a, dim3(1, tiles, M), s)))
+    return st;
+  // L1 backward: K = M*256 sums the members (one W1^T scale per element); fp32 dE/dAEV
+  a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
+  a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
+  a.a_scale = f.act[5]; a.b_scale = f.wscale + 1 * MNE; a.b_scale_by = 0;
+  return launch<256, tc::EPI_F32, MODE>(ctx, "fp8_l1_bwd", f.mG1, f.mW1T, f.mG1, f.mW1T, a,
+                                        dim3((NAEV + 255) / 256, tiles, 1), s);
 }
 
 }  // namespace
 
+fnn_status fp8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, cudaStream_t s) {
+  TcState *t = state(ctx);
+  if (!t->f8.wbuf || t->M != ctx->w.M) {
+    ctx->last_error = "fp8 weights missing";
+    return FNN_E_STATE;
+  }
+  return f8_calibrate(ctx, sys, nl, s);
+}
+
 // AEV (bf16, or hi/lo pairs) -> six tcgen05 GEMMs -> member-averaged energies; dE/dAEV (fp32) in ws.gaev
 fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
                      cudaStream_t s) {
-  if (prec != FNN_BF16 && prec != FNN_FP32X3) {
-    ctx->last_error = "FP8 form is not built yet";
-    return FNN_E_INVALID;
-  }
   const bool split = prec == FNN_FP32X3;
   TcState *t = state(ctx);
   if (!t->wbuf || t->M != ctx->w.M) {
@@ -263,6 +505,13 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
     return FNN_E_STATE;
   }
   fnn_status st;
+  if (prec == FNN_FP8) {
+    if (!t->f8.calibrated && (st = f8_calibrate(ctx, sys, nl, s))) return st;
+    if ((st = f8_workspace(ctx, nl->pad_cap))) return st;
+    if ((st = launch_aev_forward_fp8(ctx, sys, nl, t->f8.aev, 1.f / t->f8.act[0], nl->inv, s))) return st;
+    if ((st = run_layers_f8(ctx, t, nl, s))) return st;
+    return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 1, E, s);
+  }
   if ((st = tc_workspace(ctx, nl->pad_cap, split ? 2 : 1))) return st;
   if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->h[0].aev, split ? t->h[1].aev : nullptr, nl->inv, s))) return st;
   st = split ? run_layers<true>(ctx, t, nl, s) : run_layers<false>(ctx, t, nl, s);

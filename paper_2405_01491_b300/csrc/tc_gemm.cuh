@@ -1,10 +1,11 @@
 // tcgen05 (5th-generation tensor core) GEMM for the per-element networks, sm_103a.
 //
 // One CTA computes a 128 x NT tile C = A B^T of a "TN" product (both operands K-contiguous):
-//   warp 0 (one lane)  TMA producer: 128x64 A and NTx64 B bf16 tiles, 128-byte swizzle, STAGES-deep
-//                      ring guarded by full/empty mbarriers
-//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (K = 16 each) per stage, accumulator in TMEM
-//                      (128 lanes x NT fp32 columns); tcgen05.commit frees the stage
+//   warp 0 (one lane)  TMA producer: 128 x 128-byte A and NT x 128-byte B tiles (64 bf16 or 128 fp8
+//                      e4m3 elements of K), 128-byte swizzle, STAGES-deep ring guarded by mbarriers
+//   warp 1 (one lane)  MMA issuer: 4 x tcgen05.mma (32 bytes of K each: kind::f16 K = 16, or
+//                      kind::f8f6f4 K = 32) per stage, accumulator in TMEM (128 lanes x NT fp32
+//                      columns); tcgen05.commit frees the stage
 //   warps 2-17         epilogue: tcgen05.ld 32 lanes x 16 columns at a time (warp w reads TMEM lane
 //                      quarter w % 4; the four warps of a quarter take every fourth 16-column chunk),
 //                      fused bias/CELU, CELU', output-layer dot, store
@@ -15,6 +16,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fnn_internal.cuh"
 
@@ -23,13 +25,15 @@ namespace tc {
 
 constexpr int STAGES = 4;
 constexpr int BM = 128;         // rows per tile (UMMA M)
-constexpr int BK = 64;          // K per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int BKB = 128;        // K bytes per stage: one 128-byte swizzle row (64 bf16, 128 fp8)
 constexpr int TMEM_COLS = 256;  // accumulator columns allocated (NT <= 256)
 constexpr int EPI_WARPS = 16;   // four per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 2000000000LL;  // clock64 cycles (about a second) before a wait gives up
 
 enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_F32 = 3 };
+// operand forms: bf16; the three-term bf16 split of an fp32 product; fp8 e4m3 with per-tensor scales
+enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_F8 = 2 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -93,6 +97,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// D[tmem] (+)= A[smem] * B[smem]^T, fp8 e4m3 inputs, fp32 accumulation
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
 // arrive on an mbarrier once every previously issued tcgen05.mma of this thread has completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -129,6 +141,10 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f8f6f4: fp32 accumulator, A and B format E4M3 (code 0 in [7,10) and [10,13)), both K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // ---------------------------------------------------------------------------------- kernel
 struct Args {
@@ -154,12 +170,17 @@ struct Args {
   // bf16 outputs are written as a hi / lo pair (out, out_lo) and the aux input is read as aux + aux_lo
   void *out_lo;
   const __nv_bfloat16 *aux_lo;
+  // fp8 (MODE_F8): A = a8 * a_scale, B = b8 * b_scale[b_scale_sel * NE + e] with sel the tile's
+  // member (b_scale_by = 1), its n tile (2) or 0 (0); fp8 outputs hold x * out_inv; aux is fp8 * aux_scale
+  float a_scale, out_inv, aux_scale;
+  const float *b_scale;
+  int b_scale_by;
 };
 
 template <int NT>
 struct Smem {
-  __nv_bfloat16 A[STAGES][BM * BK];
-  __nv_bfloat16 B[STAGES][NT * BK];
+  uint8_t A[STAGES][BM * BKB];
+  uint8_t B[STAGES][NT * BKB];
   alignas(16) float vec[2][NT];  // bias and output-layer weights of the tile being drained
   float ypart[4][BM];            // output-layer partial sums of the four warps of each lane quarter
   uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin;
@@ -201,7 +222,7 @@ __device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &
 
 // Persistent: one CTA per SM walks tiles t = blockIdx.x, + gridDim.x, ...  Two TMEM accumulators
 // (columns [0, 256) and [256, 512)) let the epilogue drain tile i while the MMAs of tile i+1 run.
-template <int NT, int EPI, bool SPLIT>
+template <int NT, int EPI, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, Args p) {
@@ -209,6 +230,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   Smem<NT> &S = *reinterpret_cast<Smem<NT> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr bool SPLIT = MODE == MODE_SPLIT, F8 = MODE == MODE_F8;
+  constexpr int BK = F8 ? BKB : BKB / 2;   // K elements per stage
   const int nkb_seg = (p.K + BK - 1) / BK;
   const int nkb = SPLIT ? 3 * nkb_seg : nkb_seg;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
@@ -250,7 +273,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BK * 2));
+          mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BKB));
           const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
           tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
           tma_load_3d(S.B[s], seg == 1 ? &tmB_lo : &tmB, &S.full[s], kk * BK, nt * NT, b_grp);
@@ -263,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t idesc = idesc_bf16(BM, NT);
+      const uint32_t idesc = F8 ? idesc_e4m3(BM, NT) : idesc_bf16(BM, NT);
       long long g = 0;
       int cnt = 0;
       for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
@@ -285,8 +308,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           fence_after();
           const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
-          for (int k = 0; k < BK / 16; k++)
-            mma_bf16(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+          for (int k = 0; k < BKB / 32; k++) {
+            if (F8)
+              mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+            else
+              mma_bf16(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+          }
           mma_commit(&S.empty[s]);
         }
         if (*abort_flag) break;
@@ -325,12 +352,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       const long long row = (long long)rt * BM + r;
       const uint32_t tbase = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)(q * 32) << 16);
       float ysum = 0.f;
+      float sc = 1.f;   // dequantisation of the fp8 product
+      if (F8) sc = p.a_scale * p.b_scale[(p.b_scale_by == 1 ? m : p.b_scale_by == 2 ? nt : 0) * NE + e];
 #pragma unroll 1
       for (int c = 16 * part; c < NT; c += 64) {
         float v[16];
         tmem_ld16(tbase + c, v);
         const int n = n0 + c;
         if (n >= p.N) continue;  // N is a multiple of 16 in every use
+        if (F8)
+#pragma unroll
+          for (int j = 0; j < 16; j++) v[j] *= sc;
         if (EPI == EPI_F32) {
           float *o = reinterpret_cast<float *>(p.out) + row * p.ldo + m * p.o_mstride + n;
 #pragma unroll
@@ -338,7 +370,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             *reinterpret_cast<float4 *>(o + j) =
                 make_float4(v[j] * p.scale, v[j + 1] * p.scale, v[j + 2] * p.scale, v[j + 3] * p.scale);
         } else {
-          __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + row * p.ldo + m * p.o_mstride + n;
           float f[16];
           if (EPI == EPI_BIAS_CELU) {
 #pragma unroll
@@ -359,13 +390,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           } else {  // EPI_DCELU
             const long long ao = row * p.ldaux + m * p.aux_mstride + n;
-            alignas(16) __nv_bfloat16 hb[16];
-            *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux + ao);
-            *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux + ao + 8);
             float hv[16];
+            if (F8) {
+              alignas(16) __nv_fp8x2_storage_t hq[8];
+              *reinterpret_cast<uint4 *>(hq) = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(p.aux) + ao);
 #pragma unroll
-            for (int j = 0; j < 16; j++) hv[j] = __bfloat162float(hb[j]);
+              for (int j = 0; j < 8; j++) {
+                const float2 h2 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(hq[j], __NV_E4M3)));
+                hv[2 * j] = h2.x * p.aux_scale;
+                hv[2 * j + 1] = h2.y * p.aux_scale;
+              }
+            } else {
+              alignas(16) __nv_bfloat16 hb[16];
+              *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux + ao);
+              *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux + ao + 8);
+#pragma unroll
+              for (int j = 0; j < 16; j++) hv[j] = __bfloat162float(hb[j]);
+            }
             if (SPLIT) {
+              alignas(16) __nv_bfloat16 hb[16];
               *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao);
               *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao + 8);
 #pragma unroll
@@ -374,6 +417,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(hv[j]);
           }
+          if (F8) {  // saturating round-to-nearest e4m3 of x * out_inv
+            uint8_t *o8 = reinterpret_cast<uint8_t *>(p.out) + row * p.ldo + m * p.o_mstride + n;
+            alignas(16) __nv_fp8x2_storage_t q8[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+              q8[j] = __nv_cvt_float2_to_fp8x2(make_float2(f[2 * j] * p.out_inv, f[2 * j + 1] * p.out_inv),
+                                               __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint4 *>(o8) = *reinterpret_cast<const uint4 *>(q8);
+            continue;
+          }
+          __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + row * p.ldo + m * p.o_mstride + n;
           alignas(16) __nv_bfloat162 ob[8];
 #pragma unroll
           for (int j = 0; j < 8; j++) ob[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);

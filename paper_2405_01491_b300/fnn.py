@@ -99,6 +99,7 @@ def _load():
         "fnn_aev": (I32, [P, P, P, P, P]),
         "fnn_aev_jvp": (I32, [P, P, P, P, P, P]),
         "fnn_param_grads": (I32, [P, P, P, P, P, P, P]),
+        "fnn_calibrate_fp8": (I32, [P, P, P, P]),
         "fnn_energy_forces": (I32, [P, P, P, I32, P, P, P, P]),
         "fnn_energy_forces_host": (I32, [P, I32, I32, P, P, P, P, P, I32, P, P, P, P]),
         "fnn_sync": (I32, [P, P, P]),
@@ -376,6 +377,12 @@ def energy_forces_autograd(ctx: Context, system: DeviceSystem, nl: NeighborList,
     tensors in PARAM_NAMES order, float32): a loss built from E and F back-propagates into the
     parameters through fnn_param_grads (section IV).  FP32 networks."""
     return _function().apply(ctx, system, nl, *params)
+
+
+def calibrate_fp8(ctx: Context, system: DeviceSystem, nl: NeighborList, stream=None):
+    """fnn_calibrate_fp8: per-layer activation scales of the FP8 form from an FP32 evaluation of system."""
+    cs = system.c()
+    ctx._check(lib.fnn_calibrate_fp8(ctx.h, ctypes.byref(cs), nl.h, _stream(stream)), "fnn_calibrate_fp8")
 
 
 def energy_forces(ctx: Context, system: DeviceSystem, nl: NeighborList, precision: str = "fp32", virial: bool = True,

@@ -208,3 +208,49 @@ def test_bf16_and_fp32_forms_agree_on_the_full_box(fnn):
     _, _, _, E16, F16, _ = _energy_case(fnn, s, 8, precision="bf16")
     rel = np.sqrt(np.mean((F16 - F32) ** 2) / np.mean(F32 ** 2))
     assert abs(E16[0] - E32[0]) / s.n_atoms <= 1e-2 and rel <= 3e-2
+
+
+@pytest.mark.parametrize("name,M", [("box1500", 2), ("batch64", 1), ("water216", 8)])
+def test_energy_forces_fp8_error(fnn, name, M):
+    """FP8 (e4m3, per-layer scaling) networks: no stated tolerance, so the error is reported and held
+    to the BF16 bounds scaled by the ratio of the formats' spacings (3-bit against 7-bit stored
+    mantissa: 16x): per-atom energy error below 0.16 kcal/mol, RMS force error below 48% of the RMS force."""
+    s = structure(name)
+    _, _, _, E, F, W = _energy_case(fnn, s, M, precision="fp8")
+    r = oracle.energy_forces(s, weights(M))
+    dE, dF, rel = _form_errors(s, r, E, F)
+    print(f"fp8 {name}: max|dE|/atom={dE:.2e} max|dF|={dF:.2e} rms rel F={rel:.2e}")
+    assert dE <= 0.16 and rel <= 0.48
+
+
+def test_fp8_calibration_on_another_system(fnn):
+    """Scales calibrated on one system serve another; recalibrating on the evaluated system gives the
+    self-calibrated result exactly (the scales are a pure function of the calibration system)."""
+    s, other = structure("box1500"), structure("box300")
+    M = 2
+    ctx = fnn.Context(M)
+    fnn.load_weights(ctx, weights(M))
+    ds, do = fnn.DeviceSystem.from_structures(s), fnn.DeviceSystem.from_structures(other)
+    nl, no = fnn.NeighborList(ctx), fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, do, no, checked=True)
+    fnn.calibrate_fp8(ctx, do, no)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    E1, F1, _ = fnn.energy_forces(ctx, ds, nl, "fp8")
+    fnn.calibrate_fp8(ctx, ds, nl)
+    E2, F2, _ = fnn.energy_forces(ctx, ds, nl, "fp8")
+    fnn.check(ctx)
+    _, _, _, E3, F3, _ = _energy_case(fnn, s, M, precision="fp8")
+    np.testing.assert_array_equal(E2.cpu().numpy(), E3)
+    r = oracle.energy_forces(s, weights(M))
+    for E, F in ((E1, F1), (E2, F2)):
+        dE, _, rel = _form_errors(s, r, E.cpu().numpy(), F.cpu().numpy())
+        assert dE <= 0.16 and rel <= 0.48
+
+
+def test_fp8_and_fp32_forms_agree_on_the_full_box(fnn):
+    s = structure("mix23558")
+    _, _, _, E32, F32, _ = _energy_case(fnn, s, 8, precision="fp32")
+    _, _, _, E8, F8, _ = _energy_case(fnn, s, 8, precision="fp8")
+    rel = np.sqrt(np.mean((F8 - F32) ** 2) / np.mean(F32 ** 2))
+    print(f"fp8 mix23558: |dE|/atom={abs(E8[0] - E32[0]) / s.n_atoms:.2e} rms rel F={rel:.2e}")
+    assert abs(E8[0] - E32[0]) / s.n_atoms <= 0.16 and rel <= 0.48
