@@ -35,6 +35,8 @@ PRECISION_NOTE = {
               "accumulated in FP32; AEV, reductions and adjoint in FP32/FP64",
     "fp32": "networks on SIMT FP32 FFMA",
     "bf16": "networks in BF16 on tcgen05 with FP32 accumulation",
+    "fp8": "networks in FP8 e4m3 on tcgen05 (kind::f8f6f4) with FP32 accumulation; per-layer scales "
+           "(weights amax/448 per block, activations 2 amax/448 from an FP32 calibration evaluation)",
 }
 FFMA_LANES_PER_SM = 128          # FP32 FMA lanes per SM
 N_SM = 148
@@ -58,6 +60,8 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
         return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B"
     if name in ("aev_forward_bf16", "aev_forward_x3"):  # bf16 AEV row (x3: hi and lo rows)
         return "hbm", n_atoms * (16 + (4032 if name.endswith("x3") else 2016)) + nnz * 8, "B"
+    if name == "aev_forward_fp8":   # e4m3 AEV row
+        return "hbm", n_atoms * (16 + 1008) + nnz * 8, "B"
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
         return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
@@ -284,6 +288,62 @@ def serve_bench(fnn, torch, synth, duration_s=2.0, rate_hz=2000.0, pool_n=128, b
     return out
 
 
+def train_bench(fnn, torch, synth, steps, warmup, M=1):
+    """One training step of the 4096-molecule ragged batch (8..64 atoms each): energies and forces through
+    the autograd function, the loss 0.99 mean (F - F*)^2 + 0.01 mean ((E - E*)/n)^2, and its parameter
+    gradients (fnn_param_grads) by backward.  Device-resident inputs; CUDA events around each step."""
+    import numpy as np
+    s = synth.ragged_batch()
+    w = synth.xavier_weights(M)
+    ctx = fnn.Context(M)
+    fnn.load_weights(ctx, w)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    params = [torch.tensor(np.asarray(getattr(w, k), np.float32), device="cuda", requires_grad=True)
+              for k in fnn.PARAM_NAMES]
+    E_ref, F_ref = synth.batch_targets(s)
+    Et = torch.tensor(E_ref, device="cuda")
+    Ft = torch.tensor(F_ref, dtype=torch.float32, device="cuda")
+    n = torch.tensor(np.maximum(np.diff(s.mol_offsets), 1), dtype=torch.float64, device="cuda")
+
+    def step():
+        fnn.build_neighbors(ctx, ds, nl)
+        for p in params:
+            p.grad = None
+        E, F = fnn.energy_forces_autograd(ctx, ds, nl, params)
+        L = 0.99 * torch.mean((F - Ft) ** 2) + 0.01 * torch.mean(((E - Et) / n) ** 2)
+        L.backward()
+        return L
+
+    for _ in range(warmup):
+        step()
+    fnn.check(ctx, "training warm-up")
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    fnn.profile_read(ctx)
+    fnn.profile_enable(ctx, True)
+    l0 = fnn.launch_count(ctx)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        L = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = fnn.launch_count(ctx) - l0
+    fnn.profile_enable(ctx, False)
+    prof = fnn.profile_read(ctx)
+    fnn.check(ctx, "training steps")
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    total = sum(v[0] for v in prof.values())
+    top = sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]
+    return {"workload": f"ragged batch: 4096 molecules, 8-64 atoms, {s.n_atoms} atoms (gas phase)",
+            "members": M, "precision": "fp32", "ms_per_step": ms, "atoms_per_s": s.n_atoms / (ms * 1e-3),
+            "loss": float(L.detach()), "gpu_launches_per_step": launches / steps,
+            "kernel_share": {k: round(v[0] / total, 3) for k, v in top},
+            "note": "forward (E, F) + loss + parameter gradients; the optimizer update is not timed"}
+
+
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
     """K timed steps of one form: per-step CUDA events (L2 flushed outside them), per-kernel events."""
     stream = torch.cuda.current_stream()
@@ -296,8 +356,6 @@ def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, bar
         step()
     fnn.check(ctx, f"warm-up {form}")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    fnn.profile_read(ctx)
-    fnn.profile_enable(ctx, True)
     launches0 = fnn.launch_count(ctx)
     barrier()
     torch.cuda.synchronize()
@@ -310,10 +368,18 @@ def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, bar
         torch.cuda.synchronize()
     barrier()
     launches = fnn.launch_count(ctx) - launches0
-    fnn.profile_enable(ctx, False)
-    prof = fnn.profile_read(ctx)
     fnn.check(ctx, f"timed steps {form}")
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    # per-kernel times: the same steps again with an event pair around every launch (outside the timing above)
+    fnn.profile_read(ctx)
+    fnn.profile_enable(ctx, True)
+    for k in range(steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    fnn.profile_enable(ctx, False)
+    prof = fnn.profile_read(ctx)
+    fnn.check(ctx, f"profiled steps {form}")
     return ms, prof, launches, clk.summary()
 
 
@@ -353,7 +419,8 @@ def main():
     ap.add_argument("--impl", default="fnn", choices=["fnn", "reference"])
     ap.add_argument("--precision", default="fp32x3", choices=["fp32", "fp32x3", "bf16", "fp8"],
                     help="form whose throughput is the headline value")
-    ap.add_argument("--forms", default="fp32x3,fp32,bf16", help="forms timed and reported (comma separated)")
+    ap.add_argument("--forms", default="fp32x3,fp32,bf16,fp8", help="forms timed and reported (comma separated)")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -431,6 +498,9 @@ def main():
     serve = None
     if world == 1 and not args.no_serve:
         serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds)
+    train = None
+    if world == 1 and not args.no_train:
+        train = train_bench(fnn, torch, synth, args.steps, max(3, args.warmup))
 
     head = results[args.precision]
     kernels, roof = kernel_table(head["prof"], args.steps, s.n_atoms, nnz, M, args.precision, pk)
@@ -463,6 +533,8 @@ def main():
         line["cpu_baseline"] = base
     if serve is not None:
         line["serve"] = serve
+    if train is not None:
+        line["train"] = train
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
