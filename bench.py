@@ -69,8 +69,10 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
     if m:
         flops = 2.0 * gemm[m.group(2)] * M * n_atoms * (3 if m.group(1) == "x3" else 1)
         return ("alu" if m.group(1) == "f32" else "tensor"), flops, "FLOP"
-    if name in ("pairs_count", "pairs_fill"):
-        return "hbm", n_atoms * 16 + (nnz * 8 if name == "pairs_fill" else 0), "B"
+    if name in ("pairs_count", "pairs_fill", "pairs_stage"):
+        return "hbm", n_atoms * 16 + (nnz * 8 if name != "pairs_count" else 0), "B"
+    if name == "pairs_compact":     # staged entries read, list entries written
+        return "hbm", nnz * 16, "B"
     return None
 
 

@@ -358,15 +358,18 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
       W.gacc[t][2] = f * d.z;
     }
     __syncwarp();
-    // ---- angular: the same flat enumeration as the forward pass, one triplet per lane
+    // ---- angular: one triplet per lane, enumerated by diagonals (k - j = 1, 2, ...) so that the 32
+    // lanes of a batch mostly hold distinct j and distinct k and their shared-memory atomics on
+    // dE/dd rarely collide (row-major order would send a whole batch to the same row j)
     {
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
       for (int base = 0; base < T; base += 32) {
         const int t = base + lane;
         if (t < T) {
-          int ja, ka;
-          tri_index(t, n, ja, ka);
+          int diag, ka;
+          tri_index(t, n, diag, ka);   // diagonal diag + 1 has as many pairs as row diag of the triangle
+          const int ja = ka - diag - 1;
           const int p = pair_of(S.ae[ja], S.ae[ka]);
           const float *Gp = &W.gang[p * GSTRIDE];
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];

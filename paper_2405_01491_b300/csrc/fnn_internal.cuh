@@ -26,6 +26,9 @@ constexpr int ROW_TILE = 128;               // species segments are padded to th
 constexpr int RAD_CAP = 160;                // neighbours within rc_rad handled per atom
 constexpr int ANG_CAP = 64;                 // neighbours within rc_ang handled per atom
 constexpr float CELU_ALPHA = 0.1f;
+// 1/alpha, exact (10): kernels multiply by it instead of dividing by the rounded 0.1f, which is both
+// closer to the definition and free of the division sequence that dominated the network epilogues
+constexpr float CELU_INV_ALPHA = 10.0f;
 
 // element index of an atomic number, -1 when outside the table
 __host__ __device__ inline int element_of(int z) {
@@ -168,6 +171,8 @@ struct fnn_nlist {
   int32_t *cell_tmp = nullptr;  // [N]
   int32_t *cell_atoms = nullptr;// [N]
   int32_t *counts = nullptr;    // [N + 1]
+  int32_t *stage_nbr = nullptr; // [N][128] first pass of the pair search, one slot per atom
+  char4 *stage_shift = nullptr; // [N][128]
   // per structure
   fnn::MolGrid *grid = nullptr; // [n_mol]
   int32_t *mol_cells = nullptr; // [n_mol + 1]

@@ -17,8 +17,8 @@ namespace fnn {
 
 constexpr int BM = 128, BN = 64, BK = 16, GNT = 256;
 
-__device__ __forceinline__ float celu(float z) { return z > 0.f ? z : CELU_ALPHA * expm1f(z / CELU_ALPHA); }
-__device__ __forceinline__ float dcelu_from_h(float h) { return h > 0.f ? 1.f : 1.f + h / CELU_ALPHA; }
+__device__ __forceinline__ float celu(float z) { return z > 0.f ? z : CELU_ALPHA * expm1f(z * CELU_INV_ALPHA); }
+__device__ __forceinline__ float dcelu_from_h(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
 
 template <int EPI>
 __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
         float z = v + p.bias[e * p.bias_estride + m * p.bias_mstride + n];
         float w = p.w4[e * p.w4_estride + m * p.w4_mstride + n];
         ysum += celu(z) * w;
-        o = p.scale * w * (z > 0.f ? 1.f : expf(z / CELU_ALPHA));
+        o = p.scale * w * (z > 0.f ? 1.f : expf(z * CELU_INV_ALPHA));
       } else if (EPI == EPI_L3_H) {   // keep h3 itself (training) and the output-layer partials
         float z = v + p.bias[e * p.bias_estride + m * p.bias_mstride + n];
         float h = celu(z);

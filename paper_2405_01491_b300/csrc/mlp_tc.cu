@@ -42,14 +42,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D bf16 tensor map: dims (d0 innermost, d1, d2), byte strides of d1 and d2, box (b0, b1, b2), 128-byte swizzle
 bool encode3d(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
-              uint32_t b0, uint32_t b1, uint32_t b2, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
+              uint32_t b0, uint32_t b1, uint32_t b2, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+              CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
   cuuint64_t str[2] = {s1, s2};
   cuuint32_t box[3] = {b0, b1, b2}, es[3] = {1, 1, 1};
   return enc(m, dt, 3, const_cast<void *>(base), dims, str, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -59,7 +60,8 @@ struct Half {
   __nv_bfloat16 *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
   CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
   __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
-  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+  CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;   // operand maps (128-byte rows, swizzled)
+  CUtensorMap eH1, eH2, eG3, eG2, eG1;         // epilogue maps: 32-row x 16-column pieces, unswizzled
 };
 
 // e4m3 operands of the FP8 form and their scales
@@ -72,6 +74,7 @@ struct F8 {
   size_t rows = 0;
   uint8_t *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
   CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;
+  CUtensorMap eH1, eH2, eG3, eG2, eG1;
   unsigned *amax = nullptr;  // device [6] calibration maxima (float bits)
   float act[6] = {1, 1, 1, 1, 1, 1};  // scales of aev, h1, h2, g3, g2, g1
   bool calibrated = false;
@@ -91,9 +94,14 @@ TcState *state(fnn_ctx *ctx) {
   return static_cast<TcState *>(ctx->w.tc);
 }
 
+// Operand, output and aux tensor maps of one product (lo = the split's low halves; unused ones may
+// repeat any valid map).
+struct Maps {
+  const CUtensorMap *A, *B, *A_lo, *B_lo, *O, *O_lo, *X, *X_lo;
+};
+
 template <int NT, int EPI, int MODE>
-fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CUtensorMap &B,
-                  const CUtensorMap &A_lo, const CUtensorMap &B_lo, tc::Args a, dim3 tiles, cudaStream_t s) {
+fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles, cudaStream_t s) {
   // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
   a.n_ntiles = (int)tiles.x;
   a.n_rowtiles = (int)tiles.y;
@@ -101,14 +109,15 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const CUtensorMap &A, const CU
   const long long T = (long long)tiles.x * tiles.y * tiles.z;
   dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
   static bool attr_set = false;
-  const size_t sm = tc::smem_bytes<NT>();
+  const size_t sm = tc::smem_bytes<NT, EPI, MODE>();
   if (!attr_set) {
     FNN_CUDA_TRY(ctx,
                  cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI, MODE><<<grid, tc::THREADS, sm, s>>>(A, B, A_lo, B_lo, a);
+  tc::k_umma<NT, EPI, MODE><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
+                                                          *mp.X_lo, a);
   return check_launch(ctx, name);
 }
 
@@ -276,6 +285,13 @@ static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
               encode3d(&H.mG3, H.g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 64, 1, 128) &&
               encode3d(&H.mG2, H.g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
               encode3d(&H.mG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128);
+    const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE;
+    ok = ok && encode3d(&H.eH1, H.h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 16, 1, 32, BF, NS) &&
+         encode3d(&H.eH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 16, 1, 32, BF, NS) &&
+         encode3d(&H.eG3, H.g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 16, 1, 32, BF, NS) &&
+         encode3d(&H.eG2, H.g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 16, 1, 32, BF, NS) &&
+         encode3d(&H.eG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 16, 1, 32, BF, NS);
     if (!ok) {
       ctx->last_error = "cuTensorMapEncodeTiled failed for the activation maps";
       return FNN_E_CUDA;
@@ -319,6 +335,12 @@ static fnn_status f8_workspace(fnn_ctx *ctx, size_t rows) {
             encode3d(&f.mG3, f.g3, H3, M, R, H3, (uint64_t)M * H3, 128, 1, 128, U8) &&
             encode3d(&f.mG2, f.g2, H2, M, R, H2, (uint64_t)M * H2, 128, 1, 128, U8) &&
             encode3d(&f.mG1, f.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1, (uint64_t)M * H1, 128, 1, 128, U8);
+  const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE;
+  ok = ok && encode3d(&f.eH1, f.h1, H1, M, R, H1, (uint64_t)M * H1, 16, 1, 32, U8, NS) &&
+       encode3d(&f.eH2, f.h2, H2, M, R, H2, (uint64_t)M * H2, 16, 1, 32, U8, NS) &&
+       encode3d(&f.eG3, f.g3, H3, M, R, H3, (uint64_t)M * H3, 16, 1, 32, U8, NS) &&
+       encode3d(&f.eG2, f.g2, H2, M, R, H2, (uint64_t)M * H2, 16, 1, 32, U8, NS) &&
+       encode3d(&f.eG1, f.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1, (uint64_t)M * H1, 16, 1, 32, U8, NS);
   if (!ok) {
     ctx->last_error = "cuTensorMapEncodeTiled failed for the fp8 activation maps";
     return FNN_E_CUDA;
@@ -385,43 +407,44 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
   a.M = M;
-  // L1: all members at once
+  // L1: all members at once; the n tile is the member
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
-  a.out = H.h1; a.out_lo = L.h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
+  a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(ctx, nm[0], H.mAev, H.mW1, L.mAev, L.mW1, a, dim3(M, tiles, 1), s)))
+  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(
+           ctx, nm[0], {&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1}, a, dim3(M, tiles, 1), s)))
     return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
-  a.out = H.h2; a.out_lo = L.h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.o_xm = 0; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
-  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(ctx, nm[1], H.mH1, H.mW2, L.mH1, L.mW2, a, dim3(1, tiles, M), s)))
+  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(
+           ctx, nm[1], {&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2}, a, dim3(1, tiles, M), s)))
     return st;
   // L3 + output layer
   a.K = H2; a.N = H3;
-  a.out = H.g3; a.out_lo = L.g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
   a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
   a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
   a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
-  if ((st = launch<160, tc::EPI_L3, MODE>(ctx, nm[2], H.mH2, H.mW3, L.mH2, L.mW3, a, dim3(1, tiles, M), s)))
+  if ((st = launch<160, tc::EPI_L3, MODE>(
+           ctx, nm[2], {&H.mH2, &H.mW3, &L.mH2, &L.mW3, &H.eG3, &L.eG3, &H.eG3, &L.eG3}, a, dim3(1, tiles, M), s)))
     return st;
-  // L3 backward
-  a.K = H3; a.N = H2;
-  a.out = H.g2; a.out_lo = L.g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
-  a.aux = H.h2; a.aux_lo = L.h2; a.ldaux = (long long)M * H2; a.aux_mstride = H2;
-  if ((st = launch<192, tc::EPI_DCELU, MODE>(ctx, nm[3], H.mG3, H.mW3T, L.mG3, L.mW3T, a, dim3(1, tiles, M), s)))
+  // L3 backward: g2 = (g3 W3) CELU'(h2)
+  a.K = H3; a.N = H2; a.x_y = 1;
+  if ((st = launch<192, tc::EPI_DCELU, MODE>(
+           ctx, nm[3], {&H.mG3, &H.mW3T, &L.mG3, &L.mW3T, &H.eG2, &L.eG2, &H.eH2, &L.eH2}, a, dim3(1, tiles, M), s)))
     return st;
-  // L2 backward
-  a.K = H2; a.N = H1;
-  a.out = H.g1; a.out_lo = L.g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
-  a.aux = H.h1; a.aux_lo = L.h1; a.ldaux = (long long)M * H1; a.aux_mstride = H1;
-  if ((st = launch<256, tc::EPI_DCELU, MODE>(ctx, nm[4], H.mG2, H.mW2T, L.mG2, L.mW2T, a, dim3(1, tiles, M), s)))
+  // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
+  a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0;
+  if ((st = launch<256, tc::EPI_DCELU, MODE>(
+           ctx, nm[4], {&H.mG2, &H.mW2T, &L.mG2, &L.mW2T, &H.eG1, &L.eG1, &H.eH1, &L.eH1}, a, dim3(1, tiles, M), s)))
     return st;
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
-  return launch<256, tc::EPI_F32, MODE>(ctx, nm[5], H.mG1, H.mW1T, L.mG1, L.mW1T, a,
-                                         dim3((NAEV + 255) / 256, tiles, 1), s);
+  return launch<256, tc::EPI_F32, MODE>(ctx, nm[5],
+                                        {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1}, a,
+                                        dim3((NAEV + 255) / 256, tiles, 1), s);
 }
 
 // The six products with e4m3 operands; scales as described at the top of this file.
@@ -439,48 +462,54 @@ fnn_status run_layers_f8(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStre
   a.M = M;
   // L1: member = n tile
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
-  a.out = f.h1; a.ldo = (long long)M * H1; a.o_mstride = 0;
+  a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
   a.a_scale = f.act[0]; a.b_scale = f.wscale; a.b_scale_by = 2; a.out_inv = 1.f / f.act[1];
-  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(ctx, "fp8_l1_fwd", f.mAev, f.mW1, f.mAev, f.mW1, a, dim3(M, tiles, 1), s)))
+  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(
+           ctx, "fp8_l1_fwd", {&f.mAev, &f.mW1, &f.mAev, &f.mW1, &f.eH1, &f.eH1, &f.eH1, &f.eH1}, a,
+           dim3(M, tiles, 1), s)))
     return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
-  a.out = f.h2; a.ldo = (long long)M * H2; a.o_mstride = H2;
+  a.o_xm = 0; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
   a.a_scale = f.act[1]; a.b_scale = f.wscale + 2 * MNE; a.b_scale_by = 1; a.out_inv = 1.f / f.act[2];
-  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(ctx, "fp8_l2_fwd", f.mH1, f.mW2, f.mH1, f.mW2, a, dim3(1, tiles, M), s)))
+  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(
+           ctx, "fp8_l2_fwd", {&f.mH1, &f.mW2, &f.mH1, &f.mW2, &f.eH2, &f.eH2, &f.eH2, &f.eH2}, a,
+           dim3(1, tiles, M), s)))
     return st;
   // L3 + output layer
   a.K = H2; a.N = H3;
-  a.out = f.g3; a.ldo = (long long)M * H3; a.o_mstride = H3;
   a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
   a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
   a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
   a.a_scale = f.act[2]; a.b_scale = f.wscale + 4 * MNE; a.out_inv = 1.f / f.act[3];
-  if ((st = launch<160, tc::EPI_L3, MODE>(ctx, "fp8_l3_fwd", f.mH2, f.mW3, f.mH2, f.mW3, a, dim3(1, tiles, M), s)))
+  if ((st = launch<160, tc::EPI_L3, MODE>(
+           ctx, "fp8_l3_fwd", {&f.mH2, &f.mW3, &f.mH2, &f.mW3, &f.eG3, &f.eG3, &f.eG3, &f.eG3}, a,
+           dim3(1, tiles, M), s)))
     return st;
   // L3 backward
-  a.K = H3; a.N = H2;
-  a.out = f.g2; a.ldo = (long long)M * H2; a.o_mstride = H2;
-  a.aux = reinterpret_cast<const __nv_bfloat16 *>(f.h2); a.ldaux = (long long)M * H2; a.aux_mstride = H2;
+  a.K = H3; a.N = H2; a.x_y = 1;
   a.aux_scale = f.act[2];
   a.a_scale = f.act[3]; a.b_scale = f.wscale + 5 * MNE; a.out_inv = 1.f / f.act[4];
-  if ((st = launch<192, tc::EPI_DCELU, MODE>(ctx, "fp8_l3_bwd", f.mG3, f.mW3T, f.mG3, f.mW3T, a, dim3(1, tiles, M), s)))
+  if ((st = launch<192, tc::EPI_DCELU, MODE>(
+           ctx, "fp8_l3_bwd", {&f.mG3, &f.mW3T, &f.mG3, &f.mW3T, &f.eG2, &f.eG2, &f.eH2, &f.eH2}, a,
+           dim3(1, tiles, M), s)))
     return st;
-  // L2 backward
-  a.K = H2; a.N = H1;
-  a.out = f.g1; a.ldo = (long long)M * H1; a.o_mstride = H1;
-  a.aux = reinterpret_cast<const __nv_bfloat16 *>(f.h1); a.ldaux = (long long)M * H1; a.aux_mstride = H1;
+  // L2 backward, stored member-concatenated
+  a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0;
   a.aux_scale = f.act[1];
   a.a_scale = f.act[4]; a.b_scale = f.wscale + 3 * MNE; a.out_inv = 1.f / f.act[5];
-  if ((st = launch<256, tc::EPI_DCELU, MODE>(ctx, "fp8_l2_bwd", f.mG2, f.mW2T, f.mG2, f.mW2T, a, dim3(1, tiles, M), s)))
+  if ((st = launch<256, tc::EPI_DCELU, MODE>(
+           ctx, "fp8_l2_bwd", {&f.mG2, &f.mW2T, &f.mG2, &f.mW2T, &f.eG1, &f.eG1, &f.eH1, &f.eH1}, a,
+           dim3(1, tiles, M), s)))
     return st;
   // L1 backward: K = M*256 sums the members (one W1^T scale per element); fp32 dE/dAEV
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
   a.a_scale = f.act[5]; a.b_scale = f.wscale + 1 * MNE; a.b_scale_by = 0;
-  return launch<256, tc::EPI_F32, MODE>(ctx, "fp8_l1_bwd", f.mG1, f.mW1T, f.mG1, f.mW1T, a,
+  return launch<256, tc::EPI_F32, MODE>(ctx, "fp8_l1_bwd",
+                                        {&f.mG1, &f.mW1T, &f.mG1, &f.mW1T, &f.mG1, &f.mG1, &f.mG1, &f.mG1}, a,
                                         dim3((NAEV + 255) / 256, tiles, 1), s);
 }
 
@@ -510,13 +539,13 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
     if ((st = f8_workspace(ctx, nl->pad_cap))) return st;
     if ((st = launch_aev_forward_fp8(ctx, sys, nl, t->f8.aev, 1.f / t->f8.act[0], nl->inv, s))) return st;
     if ((st = run_layers_f8(ctx, t, nl, s))) return st;
-    return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 1, E, s);
+    return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, s);
   }
   if ((st = tc_workspace(ctx, nl->pad_cap, split ? 2 : 1))) return st;
   if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->h[0].aev, split ? t->h[1].aev : nullptr, nl->inv, s))) return st;
   st = split ? run_layers<true>(ctx, t, nl, s) : run_layers<false>(ctx, t, nl, s);
   if (st) return st;
-  return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 1, E, s);
+  return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, s);
 }
 
 }  // namespace fnn

@@ -8,9 +8,11 @@
 //   k_bin           per atom: cell index, histogram (atomics)
 //   scan            cell counts -> cell starts (counting sort)
 //   k_scatter       atoms into cells; k_sort_cells orders each cell by atom index (determinism)
-//   k_pairs<COUNT>  warp per atom: 27-cell stencil, predicate, ballot + popc count
+//   k_pairs_stage   warp per atom: 27-cell stencil, predicate, ballot + popc compaction into the
+//                   atom's 128-entry staging slot, and its count
 //   scan            counts -> CSR row pointers
-//   k_pairs<FILL>   same traversal, ballot-compacted writes at the row pointer
+//   k_pairs_compact staged rows copied into the CSR list (rows longer than the slot: traversed again)
+//   (the allocation-free entry point keeps the two-traversal form: k_pairs<COUNT>, scan, k_pairs<FILL>)
 //   k_elem_*        stable counting sort of atoms by element into 128-row padded segments
 #include <cfloat>
 
@@ -416,6 +418,101 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
   }
 }
 
+// One traversal of atom i's stencil (warp-wide).  Entries are written at base + position while below
+// limit; returns the number of neighbours (all of them, written or not).
+__device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid *grid, const int32_t *mol_base,
+                                         const int32_t *atom_mol, const int32_t *cell_of,
+                                         const int32_t *cell_start, const int32_t *cell_atoms, const PredConst &pc,
+                                         int32_t *nbr, char4 *shift, int64_t base, int64_t limit) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int m = atom_mol[i];
+  const MolGrid g = grid[m];
+  const int mb = mol_base[m];
+  const int cl = cell_of[i] - mb;
+  const int cx = cl % g.dx, cy = (cl / g.dx) % g.dy, cz = cl / (g.dx * g.dy);
+  int ox[3], oy[3], oz[3];
+  const int nox = stencil(cx, g.dx, g.pbc, ox), noy = stencil(cy, g.dy, g.pbc, oy), noz = stencil(cz, g.dz, g.pbc, oz);
+  const float4 pi = pos[i];
+  int count = 0;
+  for (int a = 0; a < noz; a++)
+    for (int b = 0; b < noy; b++)
+      for (int q = 0; q < nox; q++) {
+        const int c = mb + (oz[a] * g.dy + oy[b]) * g.dx + ox[q];
+        const int s0 = cell_start[c], s1 = cell_start[c + 1];
+        for (int k0 = s0; k0 < s1; k0 += 32) {
+          const int k = k0 + lane;
+          bool in = false;
+          int j = -1;
+          char4 sh = make_char4(0, 0, 0, 0);
+          if (k < s1) {
+            j = cell_atoms[k];
+            if (j != i) in = pair_in(pi, pos[j], g, pc, sh);
+          }
+          const unsigned mask = __ballot_sync(FULL, in);
+          if (in) {
+            const int64_t idx = base + count + __popc(mask & lt);
+            if (idx < limit) {
+              nbr[idx] = j;
+              shift[idx] = sh;
+            }
+          }
+          count += __popc(mask);
+        }
+      }
+  return count;
+}
+
+constexpr int PAIR_STRIDE = 128;   // staged entries per atom; longer rows are traversed again at compaction
+
+// pass 1: every atom's neighbours into its own PAIR_STRIDE-entry slot of the staging buffer, and its count
+__global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
+                                                     const int32_t *atom_mol, const int32_t *cell_of,
+                                                     const int32_t *cell_start, const int32_t *cell_atoms,
+                                                     PredConst pc, int32_t *counts, int32_t *tnbr, char4 *tshift,
+                                                     const int32_t *meta) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_binned = cell_start[meta[META_CELLS]];
+  for (int w = wg; w < n_binned; w += nw) {
+    const int i = cell_atoms[w];   // cell order: neighbouring warps share neighbour cells
+    const int64_t base = (int64_t)i * PAIR_STRIDE;
+    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, tnbr, tshift,
+                                base, base + PAIR_STRIDE);
+    if (lane == 0) counts[i] = count;
+  }
+}
+
+// pass 2: staged rows copied to their CSR place (row_ptr from the scan of the counts); a row longer than
+// the slot is found again by a second traversal writing straight into the list
+__global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
+                                                       const int32_t *atom_mol, const int32_t *cell_of,
+                                                       const int32_t *cell_start, const int32_t *cell_atoms,
+                                                       PredConst pc, const int32_t *row_ptr, const int32_t *tnbr,
+                                                       const char4 *tshift, int32_t *nbr, char4 *shift, int64_t cap,
+                                                       const int32_t *meta) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_binned = cell_start[meta[META_CELLS]];
+  for (int w = wg; w < n_binned; w += nw) {
+    const int i = cell_atoms[w];
+    const int64_t dst = row_ptr[i];
+    const int n = row_ptr[i + 1] - row_ptr[i];
+    if (n <= PAIR_STRIDE) {
+      const int64_t src = (int64_t)i * PAIR_STRIDE;
+      for (int k = lane; k < n; k += 32)
+        if (dst + k < cap) {
+          nbr[dst + k] = tnbr[src + k];
+          shift[dst + k] = tshift[src + k];
+        }
+    } else {
+      pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, nbr, shift, dst, cap);
+    }
+  }
+}
+
 __global__ void k_check_capacity(const int32_t *row_ptr, int n, int64_t cap, int32_t *meta, DevStatus *st) {
   int64_t nnz = row_ptr[n];
   meta[META_NNZ] = (int32_t)nnz;
@@ -521,6 +618,9 @@ static fnn_status reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t
     if ((st = grow(ctx, &nl->inv, pad)) || (st = grow(ctx, &nl->tile_elem, pad / ROW_TILE)) ||
         (st = grow(ctx, &nl->blk_count, (size_t)nblk * 8)))
       return st;
+    if ((st = grow(ctx, &nl->stage_nbr, (size_t)na * PAIR_STRIDE)) ||
+        (st = grow(ctx, &nl->stage_shift, (size_t)na * PAIR_STRIDE)))
+      return st;
     nl->atom_cap = na;
     nl->pad_cap = pad;
   }
@@ -579,7 +679,8 @@ extern "C" fnn_status fnn_nlist_destroy(fnn_nlist *nl) {
   if (!nl) return FNN_E_INVALID;
   void *ptrs[] = {nl->row_ptr, nl->nbr, nl->shift, nl->atom_mol, nl->elem, nl->cell_of, nl->cell_tmp,
                   nl->cell_atoms, nl->counts, nl->grid, nl->mol_cells, nl->cell_count, nl->cell_start,
-                  nl->perm, nl->inv, nl->tile_elem, nl->blk_count, nl->meta, nl->scan_tmp};
+                  nl->perm, nl->inv, nl->tile_elem, nl->blk_count, nl->meta, nl->scan_tmp, nl->stage_nbr,
+                  nl->stage_shift};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete nl;
@@ -678,9 +779,9 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     int pb = (int)(((int64_t)N * 32 + 255) / 256);
     if (pb > 32 * ctx->num_sms) pb = 32 * ctx->num_sms;
     {
-      FNN_KERNEL(ctx, "pairs_count", s);
-      k_pairs<false><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                        nl->cell_atoms, pc, nl->counts, nullptr, nullptr, nullptr, 0, nl->meta);
+      FNN_KERNEL(ctx, "pairs_stage", s);
+      k_pairs_stage<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                       nl->cell_atoms, pc, nl->counts, nl->stage_nbr, nl->stage_shift, nl->meta);
     }
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->row_ptr, nl->counts, ((size_t)N + 1) * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
@@ -691,10 +792,10 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
       k_check_capacity<<<1, 1, 0, s>>>(nl->row_ptr, N, nl->capacity, nl->meta, ctx->status);
     }
     {
-      FNN_KERNEL(ctx, "pairs_fill", s);
-      k_pairs<true><<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                       nl->cell_atoms, pc, nullptr, nl->row_ptr, nl->nbr, nl->shift, nl->capacity,
-                                       nl->meta);
+      FNN_KERNEL(ctx, "pairs_compact", s);
+      k_pairs_compact<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+                                         nl->cell_atoms, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift, nl->nbr,
+                                         nl->shift, nl->capacity, nl->meta);
     }
   }
   // species-sorted, 128-row padded order for the networks

@@ -23,8 +23,8 @@
 namespace fnn {
 namespace tc {
 
-constexpr int STAGES = 4;
 constexpr int BM = 128;         // rows per tile (UMMA M)
+constexpr int SMEM_LIMIT = 232448;   // dynamic shared memory per block (227 KB)
 constexpr int BKB = 128;        // K bytes per stage: one 128-byte swizzle row (64 bf16, 128 fp8)
 constexpr int TMEM_COLS = 256;  // accumulator columns allocated (NT <= 256)
 constexpr int EPI_WARPS = 16;   // four per TMEM lane quarter
@@ -111,6 +111,22 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// ---------------------------------------------------------------------------------- TMA store
+// tile [smem] -> tensor (bulk group); the source must stay untouched until wait_group.read says so
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   (uint64_t)map),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one committed store group still reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every committed store group complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// make this thread's shared-memory writes visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // 32 TMEM lanes x 16 consecutive fp32 columns: thread t of the warp receives lane (base + t)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
@@ -154,22 +170,21 @@ struct Args {
   int a_by_member;             // A's middle coordinate = member (else 0)
   int b_by_member;             // B's group coordinate = member * 7 + element (else element)
   const int32_t *tile_elem;    // element of each 128-row tile (-1: skip)
-  void *out;                   // bf16 (or fp32 for EPI_F32) [rows][ldo]
+  // EPI_F32: fp32 output written directly, [rows][ldo] with member stride o_mstride
+  float *out;
   long long ldo, o_mstride;
+  // every other epilogue stores 32-row x 16-column pieces through the output tensor map (box 16 x 1 x 32):
+  // columns c.. of rows z.. of tile (nt, rt, m) go to x = o_xm * m + c, y = (o_y == 1: m, 2: nt, else 0);
+  // EPI_DCELU reads its aux input (h of the layer) through the aux map at x = c, y = (x_y == 1: m, else 0)
+  int o_xm, o_y, x_y;
   const float *bias;
   long long bias_estride, bias_mstride;
-  const __nv_bfloat16 *aux;    // h of the previous layer (EPI_DCELU)
-  long long ldaux, aux_mstride;
   const float *w4;             // output layer (EPI_L3)
   long long w4_estride, w4_mstride;
   float *ypart;                // [rows][M][4] (EPI_L3, column 0)
   int M;
   float scale;
   DevStatus *st;
-  // three-term split (SPLIT kernels): x w ~ x_hi w_hi + x_hi w_lo + x_lo w_hi, K segments in that order;
-  // bf16 outputs are written as a hi / lo pair (out, out_lo) and the aux input is read as aux + aux_lo
-  void *out_lo;
-  const __nv_bfloat16 *aux_lo;
   // fp8 (MODE_F8): A = a8 * a_scale, B = b8 * b_scale[b_scale_sel * NE + e] with sel the tile's
   // member (b_scale_by = 1), its n tile (2) or 0 (0); fp8 outputs hold x * out_inv; aux is fp8 * aux_scale
   float a_scale, out_inv, aux_scale;
@@ -177,24 +192,32 @@ struct Args {
   int b_scale_by;
 };
 
-template <int NT>
+// Shared memory of one CTA: the operand ring (1024-byte aligned for the 128-byte swizzle), then each
+// epilogue warp's two output buffers (32 rows x 16 columns; hi and lo halves for the split), then the
+// barriers.  The ring is as deep as the space allows (at most 6).
+template <int NT, int EPI, int MODE>
 struct Smem {
+  static constexpr int OB = EPI == EPI_F32 ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
+  static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
+  static constexpr int OBYTES = OB ? EPI_WARPS * 2 * OB * WBUF : 1024;
+  static constexpr int FIXED = OBYTES + 1024 + 1024;
+  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (BM * BKB + NT * BKB);
+  static constexpr int STAGES = FIT > 6 ? 6 : FIT;
   uint8_t A[STAGES][BM * BKB];
   uint8_t B[STAGES][NT * BKB];
-  alignas(16) float vec[2][NT];  // bias and output-layer weights of the tile being drained
-  float ypart[4][BM];            // output-layer partial sums of the four warps of each lane quarter
-  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin;
+  uint8_t O[OBYTES];
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin, aux_bar[EPI_WARPS][2];
   uint32_t tmem_base;
   int abort_flag;
 };
 
-template <int NT>
+template <int NT, int EPI, int MODE>
 constexpr size_t smem_bytes() {
-  return sizeof(Smem<NT>) + 1024;
+  return sizeof(Smem<NT, EPI, MODE>) + 1024;
 }
 
-__device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z / CELU_ALPHA) - 1.f); }
-__device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h / CELU_ALPHA; }
+__device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
+__device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 // OR of a predicate over the epilogue threads (named barrier 1): keeps their control flow uniform
 __device__ __forceinline__ bool epi_any(bool pred) {
@@ -222,16 +245,25 @@ __device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &
 
 // Persistent: one CTA per SM walks tiles t = blockIdx.x, + gridDim.x, ...  Two TMEM accumulators
 // (columns [0, 256) and [256, 512)) let the epilogue drain tile i while the MMAs of tile i+1 run.
+// Each epilogue warp drains its own 32-row x 16-column pieces of a tile independently (no block-wide
+// barrier): it converts them into one of its two shared-memory buffers and its lane 0 stores the
+// piece with TMA while the warp fills the other buffer.  EPI_DCELU's aux piece is loaded by TMA into
+// the buffer ahead of use and overwritten in place by the result.
 template <int NT, int EPI, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, Args p) {
+           const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
+           const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo,
+           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
-  extern __shared__ uint8_t smem_raw[];
-  Smem<NT> &S = *reinterpret_cast<Smem<NT> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  using SM = Smem<NT, EPI, MODE>;
+  static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
   constexpr bool SPLIT = MODE == MODE_SPLIT, F8 = MODE == MODE_F8;
+  constexpr int STAGES = SM::STAGES;
   constexpr int BK = F8 ? BKB : BKB / 2;   // K elements per stage
+  extern __shared__ uint8_t smem_raw[];
+  SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb_seg = (p.K + BK - 1) / BK;
   const int nkb = SPLIT ? 3 * nkb_seg : nkb_seg;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
@@ -245,6 +277,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int a = 0; a < 2; a++) {
       mbar_init(&S.acc_full[a], 1);
       mbar_init(&S.acc_empty[a], EPI_WARPS);   // one arrival per epilogue warp
+      for (int w = 0; w < EPI_WARPS; w++) mbar_init(&S.aux_bar[w][a], 1);
     }
     mbar_init(&S.fin, 1);
     S.abort_flag = 0;
@@ -328,24 +361,36 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;                 // TMEM lane quarter this warp may read
     const int part = (warp - 2) >> 2;       // which of the quarter's four warps: chunks part, part + 4, ...
     const int r = q * 32 + lane;
-    const int et = threadIdx.x - 64;        // 0 .. 32 * EPI_WARPS - 1
+    const int ew = warp - 2;                // epilogue warp index
+    constexpr int PB = F8 ? 16 * 32 : 32 * 32;   // bytes of one 32 x 16 piece
+    uint8_t *wb = S.O + (size_t)ew * 2 * SM::OB * SM::WBUF;   // this warp's two buffers
+    uint32_t aux_phase[2] = {0u, 0u};
+    unsigned aux_out = 0;                   // lane 0: buffers with an aux load not yet consumed
+    long long gk = 0;                       // pieces drained by this warp (buffer gk & 1)
     int cnt = 0;
+    // lane 0: aux piece (columns col.. col + 15 of tile (rt, m)) into buffer b
+    auto load_aux = [&](int b, int col, int rt, int m) {
+      uint8_t *ob = wb + (size_t)b * SM::OB * SM::WBUF;
+      mbar_expect_tx(&S.aux_bar[ew][b], (uint32_t)(SPLIT ? 2 * PB : PB));
+      const int y = p.x_y == 1 ? m : 0;
+      tma_load_3d(ob, &tmX, &S.aux_bar[ew][b], col, y, rt * BM + q * 32);
+      if (SPLIT) tma_load_3d(ob + SM::WBUF, &tmX_lo, &S.aux_bar[ew][b], col, y, rt * BM + q * 32);
+      aux_out |= 1u << b;
+    };
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
       int nt, rt, m, e;
       if (!tile_coords(p, t, nt, rt, m, e)) continue;
       const int a = cnt & 1;
       const int n0 = nt * NT;
-      // stage this tile's bias (and output-layer) vectors while the MMAs run
-      epi_sync();
-      if (EPI == EPI_BIAS_CELU || EPI == EPI_L3)
-        for (int c = et; c < NT; c += 32 * EPI_WARPS) {
-          S.vec[0][c] = (n0 + c < p.N) ? p.bias[e * p.bias_estride + m * p.bias_mstride + n0 + c] : 0.f;
-          if (EPI == EPI_L3) S.vec[1][c] = (n0 + c < p.N) ? p.w4[e * p.w4_estride + m * p.w4_mstride + n0 + c] : 0.f;
-        }
-      epi_sync();
-      const bool failed = epi_any(!mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1)));
+      const int ncols = min(NT, p.N - n0);
+      // the first aux piece of the tile travels while its MMAs run
+      if (EPI == EPI_DCELU && lane == 0 && 16 * part < ncols) {
+        if (gk >= 2) bulk_wait_read1();
+        load_aux((int)(gk & 1), 16 * part, rt, m);
+      }
+      bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
-      if (failed) {
+      if (!__all_sync(0xffffffffu, ok)) {
         *abort_flag = 1;
         break;
       }
@@ -354,107 +399,145 @@ __global__ void __launch_bounds__(THREADS, 1)
       float ysum = 0.f;
       float sc = 1.f;   // dequantisation of the fp8 product
       if (F8) sc = p.a_scale * p.b_scale[(p.b_scale_by == 1 ? m : p.b_scale_by == 2 ? nt : 0) * NE + e];
+      const float *bias = p.bias + e * p.bias_estride + m * p.bias_mstride + n0;
+      const float *w4 = p.w4 + e * p.w4_estride + m * p.w4_mstride + n0;
+      const int oy = p.o_y == 1 ? m : p.o_y == 2 ? nt : 0;
+      bool abort_now = false;
 #pragma unroll 1
       for (int c = 16 * part; c < NT; c += 64) {
         float v[16];
         tmem_ld16(tbase + c, v);
-        const int n = n0 + c;
-        if (n >= p.N) continue;  // N is a multiple of 16 in every use
+        if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
+        if (EPI == EPI_F32) {
+          float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4 *>(o + j) = make_float4(v[j] * sc * p.scale, v[j + 1] * sc * p.scale,
+                                                             v[j + 2] * sc * p.scale, v[j + 3] * sc * p.scale);
+          continue;
+        }
+        const int b = (int)(gk & 1);
+        uint8_t *ob = wb + (size_t)b * SM::OB * SM::WBUF;
+        if (EPI == EPI_DCELU) {
+          const bool got = mbar_wait(&S.aux_bar[ew][b], aux_phase[b]);
+          aux_phase[b] ^= 1u;
+          if (lane == 0) aux_out &= ~(1u << b);
+          if (!__all_sync(0xffffffffu, got)) {
+            abort_now = true;
+            break;
+          }
+        } else {
+          if (lane == 0 && gk >= 2) bulk_wait_read1();
+          __syncwarp();
+        }
         if (F8)
 #pragma unroll
           for (int j = 0; j < 16; j++) v[j] *= sc;
-        if (EPI == EPI_F32) {
-          float *o = reinterpret_cast<float *>(p.out) + row * p.ldo + m * p.o_mstride + n;
+        float f[16];
+        if (EPI == EPI_BIAS_CELU) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4 *>(o + j) =
-                make_float4(v[j] * p.scale, v[j + 1] * p.scale, v[j + 2] * p.scale, v[j + 3] * p.scale);
-        } else {
-          float f[16];
-          if (EPI == EPI_BIAS_CELU) {
+          for (int j = 0; j < 16; j += 4) {
+            const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c + j));
+            f[j] = celu_f(v[j] + bb.x);
+            f[j + 1] = celu_f(v[j + 1] + bb.y);
+            f[j + 2] = celu_f(v[j + 2] + bb.z);
+            f[j + 3] = celu_f(v[j + 3] + bb.w);
+          }
+        } else if (EPI == EPI_L3) {
 #pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-              const float4 b = *reinterpret_cast<const float4 *>(&S.vec[0][c + j]);
-              f[j] = celu_f(v[j] + b.x);
-              f[j + 1] = celu_f(v[j + 1] + b.y);
-              f[j + 2] = celu_f(v[j + 2] + b.z);
-              f[j + 3] = celu_f(v[j + 3] + b.w);
+          for (int j = 0; j < 16; j += 4) {
+            const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c + j));
+            const float4 ww = __ldg(reinterpret_cast<const float4 *>(w4 + c + j));
+            const float zb[4] = {bb.x, bb.y, bb.z, bb.w}, wv[4] = {ww.x, ww.y, ww.z, ww.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              const float z = v[j + u] + zb[u];
+              const float ez = __expf(fminf(z, 0.f) * CELU_INV_ALPHA);
+              ysum += (z > 0.f ? z : CELU_ALPHA * (ez - 1.f)) * wv[u];
+              f[j + u] = p.scale * wv[u] * (z > 0.f ? 1.f : ez);
             }
-          } else if (EPI == EPI_L3) {
+          }
+        } else {  // EPI_DCELU: aux h of this row and columns, from the buffer
+          float hv[16];
+          if (F8) {
+            alignas(16) __nv_fp8x2_storage_t hq[8];
+            *reinterpret_cast<uint4 *>(hq) = *reinterpret_cast<const uint4 *>(ob + lane * 16);
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-              const float z = v[j] + S.vec[0][c + j], w = S.vec[1][c + j];
-              const float ez = __expf(fminf(z, 0.f) / CELU_ALPHA);
-              ysum += (z > 0.f ? z : CELU_ALPHA * (ez - 1.f)) * w;
-              f[j] = p.scale * w * (z > 0.f ? 1.f : ez);
+            for (int j = 0; j < 8; j++) {
+              const float2 h2 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(hq[j], __NV_E4M3)));
+              hv[2 * j] = h2.x * p.aux_scale;
+              hv[2 * j + 1] = h2.y * p.aux_scale;
             }
-          } else {  // EPI_DCELU
-            const long long ao = row * p.ldaux + m * p.aux_mstride + n;
-            float hv[16];
-            if (F8) {
-              alignas(16) __nv_fp8x2_storage_t hq[8];
-              *reinterpret_cast<uint4 *>(hq) = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(p.aux) + ao);
+          } else {
+            alignas(16) __nv_bfloat16 hb[16];
+            *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(ob + lane * 32);
+            *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(ob + lane * 32 + 16);
 #pragma unroll
-              for (int j = 0; j < 8; j++) {
-                const float2 h2 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(hq[j], __NV_E4M3)));
-                hv[2 * j] = h2.x * p.aux_scale;
-                hv[2 * j + 1] = h2.y * p.aux_scale;
-              }
-            } else {
-              alignas(16) __nv_bfloat16 hb[16];
-              *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux + ao);
-              *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux + ao + 8);
-#pragma unroll
-              for (int j = 0; j < 16; j++) hv[j] = __bfloat162float(hb[j]);
-            }
+            for (int j = 0; j < 16; j++) hv[j] = __bfloat162float(hb[j]);
             if (SPLIT) {
-              alignas(16) __nv_bfloat16 hb[16];
-              *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao);
-              *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(p.aux_lo + ao + 8);
+              *reinterpret_cast<uint4 *>(hb) = *reinterpret_cast<const uint4 *>(ob + SM::WBUF + lane * 32);
+              *reinterpret_cast<uint4 *>(hb + 8) = *reinterpret_cast<const uint4 *>(ob + SM::WBUF + lane * 32 + 16);
 #pragma unroll
               for (int j = 0; j < 16; j++) hv[j] += __bfloat162float(hb[j]);
             }
-#pragma unroll
-            for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(hv[j]);
           }
-          if (F8) {  // saturating round-to-nearest e4m3 of x * out_inv
-            uint8_t *o8 = reinterpret_cast<uint8_t *>(p.out) + row * p.ldo + m * p.o_mstride + n;
-            alignas(16) __nv_fp8x2_storage_t q8[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-              q8[j] = __nv_cvt_float2_to_fp8x2(make_float2(f[2 * j] * p.out_inv, f[2 * j + 1] * p.out_inv),
-                                               __NV_SATFINITE, __NV_E4M3);
-            *reinterpret_cast<uint4 *>(o8) = *reinterpret_cast<const uint4 *>(q8);
-            continue;
-          }
-          __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + row * p.ldo + m * p.o_mstride + n;
-          alignas(16) __nv_bfloat162 ob[8];
+          for (int j = 0; j < 16; j++) f[j] = v[j] * dcelu_h(hv[j]);
+        }
+        if (F8) {  // saturating round-to-nearest e4m3 of x * out_inv
+          alignas(16) __nv_fp8x2_storage_t q8[8];
 #pragma unroll
-          for (int j = 0; j < 8; j++) ob[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-          *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(ob);
-          *reinterpret_cast<uint4 *>(o + 8) = *reinterpret_cast<const uint4 *>(ob + 4);
+          for (int j = 0; j < 8; j++)
+            q8[j] = __nv_cvt_float2_to_fp8x2(make_float2(f[2 * j] * p.out_inv, f[2 * j + 1] * p.out_inv),
+                                             __NV_SATFINITE, __NV_E4M3);
+          *reinterpret_cast<uint4 *>(ob + lane * 16) = *reinterpret_cast<const uint4 *>(q8);
+        } else {
+          alignas(16) __nv_bfloat162 o2[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+          *reinterpret_cast<uint4 *>(ob + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
+          *reinterpret_cast<uint4 *>(ob + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
           if (SPLIT) {  // low part: the rounding residual of the high part
 #pragma unroll
             for (int j = 0; j < 8; j++) {
-              const float2 hi = __bfloat1622float2(ob[j]);
-              ob[j] = __floats2bfloat162_rn(f[2 * j] - hi.x, f[2 * j + 1] - hi.y);
+              const float2 hi = __bfloat1622float2(o2[j]);
+              o2[j] = __floats2bfloat162_rn(f[2 * j] - hi.x, f[2 * j + 1] - hi.y);
             }
-            __nv_bfloat16 *ol = reinterpret_cast<__nv_bfloat16 *>(p.out_lo) + row * p.ldo + m * p.o_mstride + n;
-            *reinterpret_cast<uint4 *>(ol) = *reinterpret_cast<const uint4 *>(ob);
-            *reinterpret_cast<uint4 *>(ol + 8) = *reinterpret_cast<const uint4 *>(ob + 4);
+            *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
+            *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
           }
         }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          const int x = p.o_xm * m + c;
+          tma_store_3d(&tmO, ob, x, oy, rt * BM + q * 32);
+          if (SPLIT) tma_store_3d(&tmO_lo, ob + SM::WBUF, x, oy, rt * BM + q * 32);
+          bulk_commit();
+          if (EPI == EPI_DCELU && c + 64 < ncols) {   // this warp's next aux piece into the other buffer
+            bulk_wait_read1();
+            load_aux(b ^ 1, c + 64, rt, m);
+          }
+        }
+        gk++;
       }
-      if (EPI == EPI_L3) {
-        S.ypart[part][r] = ysum;
-        epi_sync();
-        if (part == 0) p.ypart[(row * p.M + m) * 4] = S.ypart[0][r] + S.ypart[1][r] + S.ypart[2][r] + S.ypart[3][r];
+      if (abort_now) {
+        *abort_flag = 1;
+        break;
       }
+      if (EPI == EPI_L3) p.ypart[(row * p.M + m) * 4 + part] = ysum;
       // accumulator a may be overwritten once every epilogue warp has read it
       fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.acc_empty[a])) : "memory");
       cnt++;
+    }
+    if (lane == 0) {
+      // nothing may still read or write this warp's buffers when the CTA exits
+      bulk_wait_all();
+      for (int b = 0; b < 2; b++)
+        if ((aux_out >> b) & 1u)
+          if (!mbar_wait(&S.aux_bar[ew][b], aux_phase[b])) *abort_flag = 1;
     }
   }
   fence_before();

@@ -52,8 +52,8 @@ static fnn_status train_ws(fnn_ctx *ctx, TrainWs &T, size_t rows) {
   return FNN_OK;
 }
 
-__device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h / CELU_ALPHA; }
-__device__ __forceinline__ float ddcelu_ratio(float h) { return h > 0.f ? 0.f : 1.f / CELU_ALPHA; }
+__device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
+__device__ __forceinline__ float ddcelu_ratio(float h) { return h > 0.f ? 0.f : CELU_INV_ALPHA; }
 
 // output layer: gb3, gz3 per (row, member, unit); dw4 and db4 summed per tile, one atomic per thread
 __global__ void k_out_reverse(int M, const int32_t *tile_elem, const int32_t *inv, const int32_t *atom_mol,
