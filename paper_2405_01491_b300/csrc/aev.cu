@@ -31,6 +31,19 @@ __device__ __forceinline__ float exp2f_fast(float x) {
   return y;
 }
 
+// reciprocal and square root on the special-function unit (rcp.approx / sqrt.approx: about 1 ulp; the
+// arguments are normal numbers: distances above 0.5 A, the section base above 0.1, sin theta' above 0.3)
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // per-warp staging of one centre atom's neighbours, bucketed by element
 struct NbrStage {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
@@ -147,15 +160,15 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
     }
     if (pr >= 0) {
       S.rd[pr] = make_float4(dx, dy, dz, r);
-      S.rfc[pr] = 0.5f * cospif(r / P.rc_rad) + 0.5f;
+      S.rfc[pr] = 0.5f * cospif(r * P.inv_rc_rad) + 0.5f;
       S.rj[pr] = j;
       S.re[pr] = (unsigned char)e;
     }
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
       S.ae[pa] = (unsigned char)e;
-      S.afc[pa] = 0.5f * cospif(r / P.rc_ang) + 0.5f;
-      if (want_dfc) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r / P.rc_ang);
+      S.afc[pa] = 0.5f * cospif(r * P.inv_rc_ang) + 0.5f;
+      if (want_dfc) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
     }
   }
   __syncwarp();
@@ -165,7 +178,7 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
 // (j, k) of the t-th unordered pair j < k among n items, row-major upper triangle
 __device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
   float b = 2.f * n - 1.f;
-  int jj = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * t, 0.f))));
+  int jj = (int)floorf(0.5f * (b - sqrt_fast(fmaxf(b * b - 8.f * t, 0.f))));   // a guess, corrected below
   jj = max(0, min(jj, n - 2));
   // start of row j is j (2n - j - 1) / 2
   while (jj > 0 && jj * (2 * n - jj - 1) / 2 > t) jj--;
@@ -262,9 +275,9 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
           int ja, ka;
           tri_index(t, n, ja, ka);
           const float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
-          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) / (d1.w * d2.w);
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(d1.w * d2.w);
           const float c95 = 0.95f * c;
-          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
+          const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
 #pragma unroll
           for (int s = 0; s < NSZ; s++) {
             const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
@@ -344,7 +357,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
       float r = d.w;
       int e = S.re[t];
       float fc = S.rfc[t];
-      float dfc = -0.5f * P.pi_rc_rad * sinpif(r / P.rc_rad);
+      float dfc = -0.5f * P.pi_rc_rad * sinpif(r * P.inv_rc_rad);
       float dEdr = 0.f;
 #pragma unroll
       for (int k = 0; k < NSR; k++) {
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
         float gk = __expf(-P.eta_r * dr * dr);
         dEdr += W.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
       }
-      float f = dEdr / r;
+      float f = dEdr * rcp_fast(r);
       W.gacc[t][0] = f * d.x;
       W.gacc[t][1] = f * d.y;
       W.gacc[t][2] = f * d.z;
@@ -375,18 +388,18 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
           const float r1 = d1.w, r2 = d2.w;
-          const float inv12 = 1.f / (r1 * r2);
+          const float ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
           const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
           const float c95 = 0.95f * c;
-          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
-          const float ds95 = -0.9025f * c / s95;   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
+          const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+          const float ds95 = -0.9025f * c * rcp_fast(s95);   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
           float fs[NSZ], dfs[NSZ];
 #pragma unroll
           for (int s = 0; s < NSZ; s++) {
             const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
             fs[s] = f;
-            dfs[s] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
+            dfs[s] = P.zeta * f * rcp_fast(base_s) * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
           }
           const float rbar = 0.5f * (r1 + r2);
           float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
@@ -413,8 +426,8 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
           const float dEdC = 2.f * sH;
           const float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
           const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
-          const float a1 = dEdr1 / r1 - dEdc * c / (r1 * r1), b1 = dEdc * inv12;
-          const float a2 = dEdr2 / r2 - dEdc * c / (r2 * r2);
+          const float a1 = (dEdr1 - dEdc * c * ir1) * ir1, b1 = dEdc * inv12;
+          const float a2 = (dEdr2 - dEdc * c * ir2) * ir2;
           atomicAdd(&W.gacc[rj1][0], a1 * d1.x + b1 * d2.x);
           atomicAdd(&W.gacc[rj1][1], a1 * d1.y + b1 * d2.y);
           atomicAdd(&W.gacc[rj1][2], a1 * d1.z + b1 * d2.z);
@@ -522,9 +535,9 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
       const int j = S.rj[t];
       const float4 d = S.rd[t];
       const float vx = A.V[3 * (size_t)j] - vix, vy = A.V[3 * (size_t)j + 1] - viy, vz = A.V[3 * (size_t)j + 2] - viz;
-      const float rdot = (d.x * vx + d.y * vy + d.z * vz) / d.w;
+      const float rdot = (d.x * vx + d.y * vy + d.z * vz) * rcp_fast(d.w);
       W.rv[t] = make_float4(vx, vy, vz, rdot);
-      const float dfc = -0.5f * P.pi_rc_rad * sinpif(d.w / P.rc_rad);
+      const float dfc = -0.5f * P.pi_rc_rad * sinpif(d.w * P.inv_rc_rad);
       W.rt[t] = make_float2(S.rfc[t] * rdot, dfc * rdot);
     }
     __syncwarp();
@@ -559,19 +572,20 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
           tri_index(t, n, ja, ka);
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
-          const float r1 = d1.w, r2 = d2.w, inv12 = 1.f / (r1 * r2);
+          const float r1 = d1.w, r2 = d2.w, ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
           const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
           const float cdot = (d2.x * v1.x + d2.y * v1.y + d2.z * v1.z + d1.x * v2.x + d1.y * v2.y + d1.z * v2.z) * inv12 -
-                             c * (v1.w / r1 + v2.w / r2);
+                             c * (v1.w * ir1 + v2.w * ir2);
           const float c95 = 0.95f * c;
-          const float s95 = sqrtf(fmaxf(1.f - c95 * c95, 0.f));
-          const float ds95 = -0.9025f * c / s95;
+          const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+          const float ds95 = -0.9025f * c * rcp_fast(s95);
 #pragma unroll
           for (int sidx = 0; sidx < NSZ; sidx++) {
             const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[sidx] + s95 * P.sin_z[sidx]);
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
             W.stage[lane][sidx] = f;
-            W.stage[lane][4 + sidx] = P.zeta * f / base_s * 0.5f * (0.95f * P.cos_z[sidx] + ds95 * P.sin_z[sidx]) * cdot;
+            W.stage[lane][4 + sidx] =
+                P.zeta * f * rcp_fast(base_s) * 0.5f * (0.95f * P.cos_z[sidx] + ds95 * P.sin_z[sidx]) * cdot;
           }
           const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
           const float f1 = S.afc[ja], f2 = S.afc[ka];

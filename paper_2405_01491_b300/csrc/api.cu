@@ -142,6 +142,8 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
   P.zeta = (float)c.zeta;
   P.pi_rc_rad = (float)(M_PI / c.rc_rad);
   P.pi_rc_ang = (float)(M_PI / c.rc_ang);
+  P.inv_rc_rad = (float)(1.0 / c.rc_rad);
+  P.inv_rc_ang = (float)(1.0 / c.rc_ang);
   for (int k = 0; k < NSR; k++) P.shf_r[k] = (float)(c.shift_rad0 + k * (c.rc_rad - c.shift_rad0) / NSR);
   for (int m = 0; m < NSA; m++) P.shf_a[m] = (float)(c.shift_ang0 + m * (c.rc_ang - c.shift_ang0) / NSA);
   for (int s = 0; s < NSZ; s++) {

@@ -61,6 +61,7 @@ struct AevParams {
   float rc_rad, rc_ang;
   float eta_r, eta_a, zeta;
   float pi_rc_rad, pi_rc_ang;   // pi / rc
+  float inv_rc_rad, inv_rc_ang; // 1 / rc
   float shf_r[NSR];
   float shf_a[NSA];
   float cos_z[NSZ], sin_z[NSZ]; // cos / sin of the section centres
@@ -74,6 +75,8 @@ struct MolGrid {
   int dx, dy, dz;         // cells per axis
   int cell_base;          // unused (first cells come from the scanned per-structure counts)
   int pbc;
+  float iLx, iLy, iLz;    // 1 / box edge (0 when not periodic)
+  float tau;              // float32 error band of the neighbour predicate for every pair of the structure
 };
 
 // ---------------------------------------------------------------------------------------- handles

@@ -238,6 +238,22 @@ __global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid 
         if (d[a] < 1) d[a] = 1;
       }
       g.dx = d[0]; g.dy = d[1]; g.dz = d[2];
+      // error band of the float32 predicate, from the largest magnitude S any pair of this structure can
+      // present (coordinates, and image offsets |n L| <= 2 max|x| + L/2): twice the bound on the float32
+      // error of d2 near R^2, 2 sqrt(3) e R + 3 e^2 + 4 u R^2 with e = 4 u S
+      {
+        double mabs = 0.0;
+        for (int a = 0; a < 3; a++) mabs = fmax(mabs, fmax(fabs((double)red[a][0]), fabs((double)red[3 + a][0])));
+        double Lmax = g.pbc ? fmax(fmax((double)g.Lx, (double)g.Ly), (double)g.Lz) : 0.0;
+        double S = g.pbc ? 2.0 * mabs + 0.5 * Lmax + Lmax : mabs;
+        const double u = 5.9604644775390625e-8;
+        double e = 4.0 * u * S;
+        double tau = 2.0 * (3.4641016151377544 * e * R * 1.01 + 3.0 * e * e + 4.0 * u * R * R) + 1e-30;
+        g.tau = (float)(tau * (1.0 + 1e-6));
+        g.iLx = g.pbc ? (float)(1.0 / (double)g.Lx) : 0.f;
+        g.iLy = g.pbc ? (float)(1.0 / (double)g.Ly) : 0.f;
+        g.iLz = g.pbc ? (float)(1.0 / (double)g.Lz) : 0.f;
+      }
       g.ix = ext[0] > 0 ? (float)(d[0] / ext[0]) : 0.f;
       g.iy = ext[1] > 0 ? (float)(d[1] / ext[1]) : 0.f;
       g.iz = ext[2] > 0 ? (float)(d[2] / ext[2]) : 0.f;
@@ -317,28 +333,24 @@ struct PredConst {
 // d2 < R^2 with the float64 semantics of the interface, via a float32 test outside a proven band.
 // The float32 separation carries an absolute per-component error e <= 4u S (u = 2^-24, S the largest
 // magnitude among the coordinates and the image offset); near the threshold the squared distance then
-// errs by at most 2 sqrt(3) e R + 3 e^2 + 4 u R^2.  Twice that bound is the band re-tested in float64.
+// errs by at most 2 sqrt(3) e R + 3 e^2 + 4 u R^2.  Twice that bound, with S the largest magnitude over
+// the whole structure (MolGrid::tau), is the band re-tested in float64.  The image n = -rint(dx / L)
+// is formed with 1/L: for a pair within R < L/2, dx/L is far from a half-integer, so n is the same.
 __device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, const PredConst &pc, char4 &sh) {
   float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
   float nx = 0.f, ny = 0.f, nz = 0.f;
   if (g.pbc) {
-    nx = -rintf(dx / g.Lx);
-    ny = -rintf(dy / g.Ly);
-    nz = -rintf(dz / g.Lz);
+    nx = -rintf(dx * g.iLx);
+    ny = -rintf(dy * g.iLy);
+    nz = -rintf(dz * g.iLz);
     dx = fmaf(nx, g.Lx, dx);
     dy = fmaf(ny, g.Ly, dy);
     dz = fmaf(nz, g.Lz, dz);
   }
   sh = make_char4((signed char)nx, (signed char)ny, (signed char)nz, 0);
   float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  float S = fmaxf(fmaxf(fmaxf(fabsf(pi.x), fabsf(pi.y)), fmaxf(fabsf(pi.z), fabsf(pj.x))),
-                  fmaxf(fmaxf(fabsf(pj.y), fabsf(pj.z)),
-                        fmaxf(fabsf(nx * g.Lx), fmaxf(fabsf(ny * g.Ly), fabsf(nz * g.Lz)))));
-  const float u = 5.9604645e-8f;
-  float e = 4.f * u * S;
-  float tau = 2.f * (3.4641016f * e * pc.Rf * 1.01f + 3.f * e * e + 4.f * u * pc.R2f) + 1e-30f;
-  if (d2 < pc.R2f - tau) return true;
-  if (d2 > pc.R2f + tau) return false;
+  if (d2 < pc.R2f - g.tau) return true;
+  if (d2 > pc.R2f + g.tau) return false;
   // exact float64 predicate, rounded to nearest without contraction
   double rx = __dsub_rn((double)pj.x, (double)pi.x);
   double ry = __dsub_rn((double)pj.y, (double)pi.y);
@@ -366,58 +378,6 @@ __device__ __forceinline__ int stencil(int c, int d, int pbc, int *out) {
   return n;
 }
 
-template <bool FILL>
-__global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
-                                               const int32_t *atom_mol, const int32_t *cell_of,
-                                               const int32_t *cell_start, const int32_t *cell_atoms,
-                                               PredConst pc, int32_t *counts, const int32_t *row_ptr,
-                                               int32_t *nbr, char4 *shift, int64_t cap, const int32_t *meta) {
-  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
-  int lane = threadIdx.x & 31;
-  unsigned lt = (1u << lane) - 1u;
-  int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  const int n_binned = cell_start[meta[META_CELLS]];   // atoms that belong to a structure
-  for (int w = wg; w < n_binned; w += nw) {
-    int i = cell_atoms[w];   // atoms in cell order: neighbouring warps share neighbour cells
-    int m = atom_mol[i];
-    MolGrid g = grid[m];
-    int base = mol_base[m];
-    int cl = cell_of[i] - base;
-    int cx = cl % g.dx, cy = (cl / g.dx) % g.dy, cz = cl / (g.dx * g.dy);
-    int ox[3], oy[3], oz[3];
-    int nox = stencil(cx, g.dx, g.pbc, ox), noy = stencil(cy, g.dy, g.pbc, oy), noz = stencil(cz, g.dz, g.pbc, oz);
-    float4 pi = pos[i];
-    int count = 0;
-    int64_t out = FILL ? (int64_t)row_ptr[i] : 0;
-    for (int a = 0; a < noz; a++)
-      for (int b = 0; b < noy; b++)
-        for (int q = 0; q < nox; q++) {
-          int c = base + (oz[a] * g.dy + oy[b]) * g.dx + ox[q];
-          int s0 = cell_start[c], s1 = cell_start[c + 1];
-          for (int k0 = s0; k0 < s1; k0 += 32) {
-            int k = k0 + lane;
-            bool in = false;
-            int j = -1;
-            char4 sh = make_char4(0, 0, 0, 0);
-            if (k < s1) {
-              j = cell_atoms[k];
-              if (j != i) in = pair_in(pi, pos[j], g, pc, sh);
-            }
-            unsigned mask = __ballot_sync(FULL, in);
-            if (FILL && in) {
-              int64_t idx = out + count + __popc(mask & lt);
-              if (idx < cap) {
-                nbr[idx] = j;
-                shift[idx] = sh;
-              }
-            }
-            count += __popc(mask);
-          }
-        }
-    if (!FILL && lane == 0) counts[i] = count;
-  }
-}
-
 // One traversal of atom i's stencil (warp-wide).  Entries are written at base + position while below
 // limit; returns the number of neighbours (all of them, written or not).
 __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid *grid, const int32_t *mol_base,
@@ -436,10 +396,14 @@ __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid
   const float4 pi = pos[i];
   int count = 0;
   for (int a = 0; a < noz; a++)
-    for (int b = 0; b < noy; b++)
-      for (int q = 0; q < nox; q++) {
-        const int c = mb + (oz[a] * g.dy + oy[b]) * g.dx + ox[q];
-        const int s0 = cell_start[c], s1 = cell_start[c + 1];
+    for (int b = 0; b < noy; b++) {
+      const int rowc = mb + (oz[a] * g.dy + oy[b]) * g.dx;
+      // x-neighbour cells with consecutive indices hold consecutive atoms: one range per run
+      for (int q = 0; q < nox;) {
+        const int x0 = ox[q];
+        int x1 = x0;
+        for (q++; q < nox && ox[q] == x1 + 1; q++) x1 = ox[q];
+        const int s0 = cell_start[rowc + x0], s1 = cell_start[rowc + x1 + 1];
         for (int k0 = s0; k0 < s1; k0 += 32) {
           const int k = k0 + lane;
           bool in = false;
@@ -460,7 +424,29 @@ __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid
           count += __popc(mask);
         }
       }
+    }
   return count;
+}
+
+// Two-traversal form (the allocation-free entry point): COUNT writes each atom's count, FILL writes the
+// entries at the CSR row pointers.
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
+                                               const int32_t *atom_mol, const int32_t *cell_of,
+                                               const int32_t *cell_start, const int32_t *cell_atoms,
+                                               PredConst pc, int32_t *counts, const int32_t *row_ptr,
+                                               int32_t *nbr, char4 *shift, int64_t cap, const int32_t *meta) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_binned = cell_start[meta[META_CELLS]];   // atoms that belong to a structure
+  for (int w = wg; w < n_binned; w += nw) {
+    const int i = cell_atoms[w];   // atoms in cell order: neighbouring warps share neighbour cells
+    const int64_t out = FILL ? (int64_t)row_ptr[i] : 0;
+    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, nbr, shift,
+                                out, FILL ? cap : 0);
+    if (!FILL && lane == 0) counts[i] = count;
+  }
 }
 
 constexpr int PAIR_STRIDE = 128;   // staged entries per atom; longer rows are traversed again at compaction
