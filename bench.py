@@ -99,9 +99,48 @@ def recorded_traffic(kernel: str, digest: str):
     return None
 
 
+class _NvmlLib:
+    """The driver's NVML through ctypes (read-only queries: SM clock, its maximum, event reasons, power)."""
+
+    def __init__(self, torch_index: int):
+        import ctypes
+        self.c = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(torch_index).uuid)
+        except Exception:
+            pass
+        ok = False
+        if uuid:
+            key = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            ok = lib.nvmlDeviceGetHandleByUUID(key.encode(), ctypes.byref(h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(torch_index, ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle for the device")
+        self.lib, self.h = lib, h
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        m = ctypes.c_uint()
+        self.max_mhz = float(m.value) if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(m)) == 0 else None
+
+    def sample(self):
+        c = self.c
+        mhz, pw, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(mhz)) != 0:
+            return None
+        self.reasons_fn(self.h, c.byref(rs))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, c.byref(pw))
+        return float(mhz.value), int(rs.value), pw.value / 1000.0
+
+
 class ClockSampler:
-    """SM clocks and throttle reasons sampled during the timed region: NVML from a background thread every
-    2 ms (the timed regions are tens of milliseconds), nvidia-smi at 200 ms if NVML is unavailable."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML (the driver library through
+    ctypes) from a background thread every 1 ms (the timed regions are milliseconds long), nvidia-smi at
+    200 ms if NVML cannot be opened."""
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40, "sw_power_cap": 0x4}
 
     def __init__(self, index: int):
@@ -110,31 +149,30 @@ class ClockSampler:
         self.max_mhz = None
         self._stop = None
         self.proc = None
+        self.mode = None
 
-    def _nvml_loop(self, pynvml, h):
-        get = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            getattr(pynvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
-        self._reasons = get
+    def _nvml_loop(self, nv):
         while not self._stop.is_set():
             try:
-                mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                reasons = self._reasons(h)
-                power = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
-                self.rows.append((mhz, reasons, power))
+                r = nv.sample()
+                if r:
+                    self.rows.append(r)
             except Exception:
                 pass
-            self._stop.wait(0.002)
+            self._stop.wait(0.001)
 
     def __enter__(self):
         import threading
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            nv = _NvmlLib(self.index)
+            self.max_mhz = nv.max_mhz
+            r = nv.sample()          # one sample at the start of the region
+            if r:
+                self.rows.append(r)
             self._stop = threading.Event()
-            self.thread = threading.Thread(target=self._nvml_loop, args=(pynvml, h), daemon=True)
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv,), daemon=True)
             self.thread.start()
+            self._nv = nv
             self.mode = "nvml"
         except Exception:
             self.mode = "nvidia-smi"
@@ -153,6 +191,12 @@ class ClockSampler:
         if self.mode == "nvml":
             self._stop.set()
             self.thread.join(timeout=2)
+            try:
+                r = self._nv.sample()     # and one at its end
+                if r:
+                    self.rows.append(r)
+            except Exception:
+                pass
             return
         self.out = ""
         if self.proc:
@@ -347,32 +391,41 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1):
 
 
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
-    """K timed steps of one form: per-step CUDA events (L2 flushed outside them), per-kernel events."""
-    stream = torch.cuda.current_stream()
+    """K timed steps of one form, each a replay of the step's CUDA graph (list rebuild + energies +
+    forces + virials) on its own stream, CUDA events around every replay (L2 flushed outside them);
+    then the same steps launched eagerly with per-kernel events for the kernel table."""
+    g = fnn.Graph(ctx, ds, nl, form, virial=True, rebuild=True)
+    stream = g.stream
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.launch()
+        fnn.check(ctx, f"warm-up {form}", stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = fnn.launch_count(ctx)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                g.launch()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        launches = fnn.launch_count(ctx) - launches0
+        fnn.check(ctx, f"timed steps {form}", stream=stream)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        E.copy_(g.E)
+        F.copy_(g.F)
+        Wv.copy_(g.W)
+    torch.cuda.synchronize()
+    g.close()
 
+    # per-kernel times: the same steps eagerly, an event pair around every launch (outside the timing above)
     def step():
         fnn.build_neighbors(ctx, ds, nl)
         fnn.energy_forces(ctx, ds, nl, form, out=(E, F, Wv))
 
-    for _ in range(warmup):
-        step()
-    fnn.check(ctx, f"warm-up {form}")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    launches0 = fnn.launch_count(ctx)
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    launches = fnn.launch_count(ctx) - launches0
-    fnn.check(ctx, f"timed steps {form}")
-    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-    # per-kernel times: the same steps again with an event pair around every launch (outside the timing above)
     fnn.profile_read(ctx)
     fnn.profile_enable(ctx, True)
     for k in range(steps):
@@ -475,7 +528,7 @@ def main():
     for form in forms:
         ms, prof, launches, clocks = time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, args.steps,
                                                args.warmup, barrier)
-        fnn.energy_forces(ctx, ds, nl, form, out=(E, F, Wv))
+        fnn.energy_forces(ctx, ds, nl, form, out=(E, F, Wv))   # the reported errors: an eager evaluation
         fnn.check(ctx, form)
         results[form] = dict(ms=max_over_ranks(ms), prof=prof, launches=launches, clocks=clocks,
                              E=E.cpu().numpy().copy(), F=F.cpu().numpy().copy())

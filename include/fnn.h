@@ -209,6 +209,24 @@ typedef struct {
 fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
                            const float *dLdF, const fnn_grads *g, void *stream);
 
+/*
+ * One step as a CUDA graph: fnn_build_neighbors (when rebuild != 0) then fnn_energy_forces, recorded on
+ * stream (not the legacy default stream) after one eager step that sizes every buffer (and
+ * calibrates the FP8 form), then instantiated.  The system's device arrays, the list and the outputs
+ * are bound by address: a replay reads their contents at replay time (new positions in the same
+ * buffer are fine; a different atom count or structure layout needs a new graph).  A replay cannot
+ * grow a list: an overflow posts FNN_E_CAPACITY (read with fnn_sync); reserve and recreate.  The
+ * eager step's device status is returned (and cleared) by create.  Synchronous.
+ */
+typedef struct fnn_graph fnn_graph;
+fnn_status fnn_graph_create(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, fnn_precision prec, double *E,
+                            float *F, double *virial, int32_t rebuild, void *stream, fnn_graph **graph);
+/* Replay on stream (asynchronous). */
+fnn_status fnn_graph_launch(fnn_graph *graph, void *stream);
+/* Kernel launches one replay performs. */
+fnn_status fnn_graph_kernels(const fnn_graph *graph, int64_t *kernels);
+fnn_status fnn_graph_destroy(fnn_graph *graph);
+
 /* Synchronise the stream, return and clear the sticky device status; *info
  * (optional) receives its detail (entries needed for FNN_E_CAPACITY, the
  * offending atom for FNN_E_SPECIES, ...). */

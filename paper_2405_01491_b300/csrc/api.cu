@@ -430,3 +430,92 @@ extern "C" fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info) {
   if (info) *info = h.info;
   return (fnn_status)h.code;
 }
+
+// ------------------------------------------------------------------------------------- CUDA graphs
+struct fnn_graph {
+  fnn_ctx *ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;   // kernel launches one replay performs
+};
+
+extern "C" fnn_status fnn_graph_create(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, fnn_precision prec,
+                                       double *E, float *F, double *virial, int32_t rebuild, void *stream,
+                                       fnn_graph **out) {
+  if (!ctx || !sys || !nl || !E || !F || !out) return FNN_E_INVALID;
+  if (!stream) {
+    ctx->last_error = "graph capture needs a stream other than the legacy default stream";
+    return FNN_E_INVALID;
+  }
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  fnn_status st;
+  // one eager step first: every buffer, calibration and kernel attribute is in place before capture
+  if (rebuild && (st = fnn_build_neighbors(ctx, sys, nl, stream))) return st;
+  if (!rebuild && (!nl->built || nl->n_atoms != sys->n_atoms || nl->n_mol != sys->n_mol)) {
+    ctx->last_error = "neighbour list was not built for this system";
+    return FNN_E_STATE;
+  }
+  if ((st = fnn_energy_forces(ctx, sys, nl, prec, E, F, virial, stream))) return st;
+  int64_t info = 0;
+  if ((st = fnn_sync(ctx, stream, &info))) {
+    ctx->last_error = "the eager step before capture posted a device status";
+    return st;
+  }
+  const long long l0 = ctx->prof.launches;
+  const bool prof = ctx->prof.on;
+  ctx->prof.on = false;   // no per-kernel events inside the graph
+  FNN_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  st = FNN_OK;
+  if (rebuild) st = fnn_build_neighbors(ctx, sys, nl, stream);
+  if (!st) st = fnn_energy_forces(ctx, sys, nl, prec, E, F, virial, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &g);
+  ctx->prof.on = prof;
+  const long long kernels = ctx->prof.launches - l0;
+  ctx->prof.launches = l0;   // capture launches nothing
+  if (st || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!st) {
+      ctx->last_error = std::string("stream capture failed: ") + cudaGetErrorString(ec);
+      st = FNN_E_CUDA;
+    }
+    return st;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    ctx->last_error = "cudaGraphInstantiate failed";
+    return FNN_E_CUDA;
+  }
+  fnn_graph *G = new fnn_graph();
+  G->ctx = ctx;
+  G->graph = g;
+  G->exec = exec;
+  G->kernels = kernels;
+  *out = G;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_graph_launch(fnn_graph *g, void *stream) {
+  if (!g) return FNN_E_INVALID;
+  FNN_CUDA_TRY(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  g->ctx->prof.launches += g->kernels;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_graph_kernels(const fnn_graph *g, int64_t *kernels) {
+  if (!g || !kernels) return FNN_E_INVALID;
+  *kernels = g->kernels;
+  return FNN_OK;
+}
+
+extern "C" fnn_status fnn_graph_destroy(fnn_graph *g) {
+  if (!g) return FNN_E_INVALID;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return FNN_OK;
+}

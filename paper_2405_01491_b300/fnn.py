@@ -100,6 +100,10 @@ def _load():
         "fnn_aev_jvp": (I32, [P, P, P, P, P, P]),
         "fnn_param_grads": (I32, [P, P, P, P, P, P, P]),
         "fnn_calibrate_fp8": (I32, [P, P, P, P]),
+        "fnn_graph_create": (I32, [P, P, P, I32, P, P, P, I32, P, P]),
+        "fnn_graph_launch": (I32, [P, P]),
+        "fnn_graph_kernels": (I32, [P, P]),
+        "fnn_graph_destroy": (I32, [P]),
         "fnn_energy_forces": (I32, [P, P, P, I32, P, P, P, P]),
         "fnn_energy_forces_host": (I32, [P, I32, I32, P, P, P, P, P, I32, P, P, P, P]),
         "fnn_sync": (I32, [P, P, P]),
@@ -462,6 +466,45 @@ def md_run(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision:
                               int(n_steps), float(dt_fs), int(rebuild_every), _ptr(E_hist), _ptr(F), _stream(stream)),
                "fnn_md_run")
     return E_hist, F
+
+
+class Graph:
+    """fnn_graph_*: one step (list rebuild when rebuild, then energies and forces) captured as a CUDA graph
+    on a non-default stream; replays read the system's buffers at replay time."""
+
+    def __init__(self, ctx: Context, system: DeviceSystem, nl: NeighborList, precision: str = "fp32x3",
+                 virial: bool = True, rebuild: bool = True, stream=None):
+        import torch
+        self.ctx, self.system, self.nl = ctx, system, nl
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.E = torch.empty(system.n_mol, dtype=torch.float64, device="cuda")
+        self.F = torch.empty((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+        self.W = torch.empty((system.n_mol, 3, 3), dtype=torch.float64, device="cuda") if virial else None
+        self._cs = system.c()
+        h = ctypes.c_void_p()
+        self.h = None
+        code = lib.fnn_graph_create(ctx.h, ctypes.byref(self._cs), nl.h, PRECISION[precision], _ptr(self.E),
+                                    _ptr(self.F), _ptr(self.W), int(bool(rebuild)),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        ctx._check(code, "fnn_graph_create")
+        self.h = h
+        k = ctypes.c_int64(0)
+        lib.fnn_graph_kernels(self.h, ctypes.byref(k))
+        self.kernels = k.value
+
+    def launch(self):
+        self.ctx._check(lib.fnn_graph_launch(self.h, ctypes.c_void_p(self.stream.cuda_stream)), "fnn_graph_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fnn_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
