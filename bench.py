@@ -390,6 +390,39 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1):
             "note": "forward (E, F) + loss + parameter gradients; the optimizer update is not timed"}
 
 
+def md_bench(fnn, torch, synth, n_steps: int = 1000, M: int = 8):
+    """The periodic water box (216 H2O, 648 atoms) under NVE velocity Verlet: n_steps force evaluations
+    at 0.5 fs, 8-member ensemble, FP32X3 networks, list skin 1 A rebuilt every 10 steps, Maxwell-Boltzmann
+    velocities at 300 K; fnn_md_run on a side stream (10-step blocks as CUDA-graph replays)."""
+    s = synth.water216()
+    ctx = fnn.Context(M, skin=1.0)
+    fnn.load_weights(ctx, synth.xavier_weights(M))
+    ds = fnn.DeviceSystem.from_structures(s)
+    vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+    vel[:, :3] = torch.from_numpy(synth.maxwell_boltzmann(s.Z, 300.0, seed=2))
+    vel = vel.cuda()
+    nl = fnn.NeighborList(ctx)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        fnn.md_run(ctx, ds, vel.clone(), nl, "fp32x3", 20, 0.5, 10, stream=stream)   # warm-up (sizes, graphs)
+        fnn.check(ctx, "md warm-up", stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = fnn.launch_count(ctx)
+        a.record(stream)
+        E, F = fnn.md_run(ctx, ds, vel, nl, "fp32x3", n_steps, 0.5, 10, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fnn.check(ctx, "md", stream=stream)
+    ms = a.elapsed_time(b)
+    E = E.cpu().numpy()[:, 0]
+    return {"workload": "water216: 216 rigid H2O (648 atoms), 18.64 A periodic cube, seed 2", "members": M,
+            "precision": "fp32x3", "steps": n_steps, "dt_fs": 0.5, "rebuild_every": 10, "skin_A": 1.0,
+            "ms_total": ms, "ms_per_step": ms / n_steps, "atom_evals_per_s": s.n_atoms * n_steps / (ms * 1e-3),
+            "gpu_launches_per_step": (fnn.launch_count(ctx) - l0) / n_steps,
+            "energy_first_last": [float(E[0]), float(E[-1])]}
+
+
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
     """K timed steps of one form, each a replay of the step's CUDA graph (list rebuild + energies +
     forces + virials) on its own stream, CUDA events around every replay (L2 flushed outside them);
@@ -476,6 +509,7 @@ def main():
                     help="form whose throughput is the headline value")
     ap.add_argument("--forms", default="fp32x3,fp32,bf16,fp8", help="forms timed and reported (comma separated)")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-md", action="store_true", help="skip the water-box MD measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -553,6 +587,9 @@ def main():
     serve = None
     if world == 1 and not args.no_serve:
         serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds)
+    md = None
+    if world == 1 and not args.no_md:
+        md = md_bench(fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
         train = train_bench(fnn, torch, synth, args.steps, max(3, args.warmup))
@@ -590,6 +627,8 @@ def main():
         line["serve"] = serve
     if train is not None:
         line["train"] = train
+    if md is not None:
+        line["md"] = md
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

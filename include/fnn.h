@@ -240,7 +240,9 @@ fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
  * A/fs^2).  pos, vel: device [N][4] (w unused), updated in place (pos replaces sys->pos); the list is
  * rebuilt before evaluations 0, rebuild_every, 2 rebuild_every, ... (use a context skin of at least
  * the largest displacement between rebuilds).  E_hist: device [n_steps][n_mol] float64, or NULL.
- * F: device [N][3], the forces of the last evaluation.  Asynchronous.
+ * F: device [N][3], the forces of the last evaluation.  The step index lives on the device, so on a
+ * stream other than the legacy default stream every whole block of rebuild_every steps after the
+ * first runs as a replay of one CUDA graph.  Asynchronous.
  */
 fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl, fnn_precision prec,
                       int32_t n_steps, double dt_fs, int32_t rebuild_every, double *E_hist, float *F, void *stream);

@@ -107,6 +107,30 @@ fnn_status launch_advance_steps(fnn_ctx *ctx, int n_mol, int32_t *mol_step, cuda
   return check_launch(ctx, "advance_steps");
 }
 
+// One MD step on the device: [list rebuild] -> energies and forces -> energy history row -> velocity
+// Verlet update -> step counter.  The step index lives on the device (mol_step), so a sequence of steps
+// can be captured once as a CUDA graph and replayed.
+static fnn_status md_step(fnn_ctx *ctx, fnn_system *v, float *pos, float *vel, fnn_nlist *nl, fnn_precision prec,
+                          bool rebuild, int32_t n_steps, double dt_fs, double *E, double *E_hist, float *F,
+                          int32_t *mol_step, int32_t *mol_nsteps, cudaStream_t s) {
+  fnn_status st;
+  if (rebuild && (st = fnn_build_neighbors(ctx, v, nl, s))) return st;
+  if ((st = fnn_energy_forces(ctx, v, nl, prec, E, F, nullptr, s))) return st;
+  if (E_hist && (st = launch_record_energy(ctx, v->n_mol, E, mol_step, mol_nsteps, nullptr, E_hist, 0, v->n_mol, s)))
+    return st;
+  if ((st = launch_vv(ctx, nl, v->n_atoms, reinterpret_cast<float4 *>(pos), reinterpret_cast<float4 *>(vel), F,
+                      mol_step, mol_nsteps, nullptr, 0, n_steps, dt_fs, s)))
+    return st;
+  return launch_advance_steps(ctx, v->n_mol, mol_step, s);
+}
+
+__global__ void k_md_init(int n_mol, int32_t n_steps, int32_t *mol_step, int32_t *mol_nsteps) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_mol; m += gridDim.x * blockDim.x) {
+    mol_step[m] = 0;
+    mol_nsteps[m] = n_steps;
+  }
+}
+
 }  // namespace fnn
 
 using namespace fnn;
@@ -120,19 +144,59 @@ extern "C" fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos
   cudaStream_t s = (cudaStream_t)stream;
   fnn_system v = *sys;
   v.pos = pos;
+  const int nm = v.n_mol > 0 ? v.n_mol : 1;
+  // scratch: energies of the current step, per-structure step counters
+  char *scratch = nullptr;
+  const size_t bytes = (size_t)nm * (sizeof(double) + 2 * sizeof(int32_t)) + 64;
+  FNN_CUDA_TRY(ctx, cudaMallocAsync((void **)&scratch, bytes, s));
+  double *E = reinterpret_cast<double *>(scratch);
+  int32_t *mol_step = reinterpret_cast<int32_t *>(scratch + (size_t)nm * sizeof(double));
+  int32_t *mol_nsteps = mol_step + nm;
   fnn_status st = FNN_OK;
-  double *E = nullptr;
-  if (!E_hist) {
-    FNN_CUDA_TRY(ctx, cudaMallocAsync(&E, (size_t)(v.n_mol > 0 ? v.n_mol : 1) * sizeof(double), s));
+  {
+    FNN_KERNEL(ctx, "md_init", s);
+    k_md_init<<<(nm + 255) / 256, 256, 0, s>>>(nm, n_steps, mol_step, mol_nsteps);
   }
-  for (int k = 0; k < n_steps; k++) {
-    if (k % rebuild_every == 0 && (st = fnn_build_neighbors(ctx, &v, nl, stream))) break;
-    double *Ek = E_hist ? E_hist + (size_t)k * v.n_mol : E;
-    if ((st = fnn_energy_forces(ctx, &v, nl, prec, Ek, F, nullptr, stream))) break;
-    if ((st = launch_vv(ctx, nl, v.n_atoms, reinterpret_cast<float4 *>(pos), reinterpret_cast<float4 *>(vel), F,
-                        nullptr, nullptr, nullptr, k, n_steps, dt_fs, s)))
-      break;
+  const int R = rebuild_every;
+  int k = 0;
+  // the first block eagerly (sizes every buffer, calibrates the FP8 form)
+  for (; k < n_steps && k < R && !st; k++)
+    st = md_step(ctx, &v, pos, vel, nl, prec, k % R == 0, n_steps, dt_fs, E, E_hist, F, mol_step, mol_nsteps, s);
+  // whole blocks of R steps (one rebuild each) as a CUDA graph, when the stream can be captured
+  if (!st && s && n_steps - k >= 2 * R) {
+    const long long l0 = ctx->prof.launches;
+    const bool prof = ctx->prof.on;
+    ctx->prof.on = false;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      fnn_status cs = FNN_OK;
+      for (int j = 0; j < R && !cs; j++)
+        cs = md_step(ctx, &v, pos, vel, nl, prec, j == 0, n_steps, dt_fs, E, E_hist, F, mol_step, mol_nsteps, s);
+      const cudaError_t ec = cudaStreamEndCapture(s, &g);
+      if (cs || ec != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+    }
+    cudaGetLastError();
+    ctx->prof.on = prof;
+    const long long per_block = ctx->prof.launches - l0;
+    ctx->prof.launches = l0;
+    if (exec) {
+      for (; n_steps - k >= R; k += R) {
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+          cudaGetLastError();
+          ctx->last_error = "cudaGraphLaunch failed";
+          st = FNN_E_CUDA;
+          break;
+        }
+        ctx->prof.launches += per_block;
+      }
+      cudaGraphExecDestroy(exec);
+    }
+    if (g) cudaGraphDestroy(g);
   }
-  if (E) cudaFreeAsync(E, s);
+  // the rest eagerly (also every step when the stream cannot be captured)
+  for (; k < n_steps && !st; k++)
+    st = md_step(ctx, &v, pos, vel, nl, prec, k % R == 0, n_steps, dt_fs, E, E_hist, F, mol_step, mol_nsteps, s);
+  cudaFreeAsync(scratch, s);
   return st;
 }

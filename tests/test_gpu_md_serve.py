@@ -29,7 +29,8 @@ def _velocities(s, seed):
     return synth.maxwell_boltzmann(s.Z, 300.0, seed=seed)
 
 
-def _md_gpu(fnn, s, v0, M, precision, n_steps, dt, skin=1.0, rebuild=10):
+def _md_gpu(fnn, s, v0, M, precision, n_steps, dt, skin=1.0, rebuild=10, side_stream=False):
+    """fnn_md_run; on a side stream whole blocks of `rebuild` steps run as replays of one CUDA graph."""
     import torch
     ctx = fnn.Context(M, skin=skin)
     fnn.load_weights(ctx, weights(M))
@@ -38,18 +39,23 @@ def _md_gpu(fnn, s, v0, M, precision, n_steps, dt, skin=1.0, rebuild=10):
     vel[:, :3] = torch.from_numpy(v0)
     vel = vel.cuda()
     nl = fnn.NeighborList(ctx)
-    E, F = fnn.md_run(ctx, ds, vel, nl, precision, n_steps, dt, rebuild)
-    fnn.check(ctx, "md_run")
+    stream = torch.cuda.Stream() if side_stream else None
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+        E, F = fnn.md_run(ctx, ds, vel, nl, precision, n_steps, dt, rebuild, stream=stream)
+    fnn.check(ctx, "md_run", stream=stream)
     return E.cpu().numpy(), ds.pos[:, :3].cpu().numpy(), vel[:, :3].cpu().numpy(), F.cpu().numpy()
 
 
-@pytest.mark.parametrize("name,M,precision,skin,rebuild", [("gas24", 1, "fp32", 0.0, 1), ("gas24", 2, "fp32x3", 1.0, 5),
-                                                           ("water216", 1, "fp32x3", 1.0, 10)])
-def test_md_matches_oracle_velocity_verlet(fnn, name, M, precision, skin, rebuild):
+@pytest.mark.parametrize("name,M,precision,skin,rebuild,graph", [("gas24", 1, "fp32", 0.0, 1, False),
+                                                                 ("gas24", 2, "fp32x3", 1.0, 5, True),
+                                                                 ("water216", 1, "fp32x3", 1.0, 10, False),
+                                                                 ("water216", 2, "fp32x3", 1.0, 3, True)])
+def test_md_matches_oracle_velocity_verlet(fnn, name, M, precision, skin, rebuild, graph):
     s = structure(name)
     v0 = _velocities(s, 3)
     n, dt = 20, 0.5
-    E, x, v, F = _md_gpu(fnn, s, v0, M, precision, n, dt, skin, rebuild)
+    E, x, v, F = _md_gpu(fnn, s, v0, M, precision, n, dt, skin, rebuild, side_stream=graph)
     Er, xr, vr, Fr = oracle.velocity_verlet(s, weights(M), v0, n, dt)
     assert np.abs(E - Er).max() / s.n_atoms <= E_TOL_PER_ATOM
     assert np.abs(x - xr).max() <= 1e-4
