@@ -305,7 +305,8 @@ def serve_bench(fnn, torch, synth, duration_s=2.0, rate_hz=2000.0, pool_n=128, b
            "rate_hz": rate_hz, "members": 1, "precision": "bf16", "max_batch_atoms": st["max_batch_atoms"],
            "batch_steps": st["batch_steps"], "mean_atoms": float(np.mean([pool[k].n_atoms for _, k in stream])),
            "pool": f"{pool_n} structures, n = round(exp(U(ln 8, ln 20000))), periodic above 500 atoms, seed 5",
-           "budget_bytes": budget, "status": st["status"]}
+           "budget_bytes": budget, "status": st["status"], "scheduler_host_ms": st["host_ms"],
+           "scheduler_step_ms": st["step_ms"]}
     # batch-of-one FP32 form: the first requests of the same stream, each alone
     ctx1 = fnn.Context(1, skin=1.0)
     fnn.load_weights(ctx1, w1)

@@ -283,6 +283,8 @@ typedef struct {
   int64_t max_batch_atoms;
   int64_t pending;          /* requests waiting for admission */
   double bytes_per_atom;    /* the admission estimate */
+  double host_ms;           /* scheduler time spent retiring and re-laying out the batch */
+  double step_ms;           /* scheduler time spent in batch steps (GPU work, waited for) */
 } fnn_serve_counters;
 
 fnn_status fnn_serve_create(fnn_server **srv, fnn_ctx *ctx, size_t hbm_budget_bytes, fnn_precision prec,

@@ -10,6 +10,7 @@
 // rejected at submission.  A structure's result does not depend on what else is in the batch:
 // structures never interact (section II.A batch index), and each keeps its own list-rebuild schedule
 // relative to the skin.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -62,6 +63,13 @@ struct Slot {           // a structure in the device batch
   int step = 0;         // evaluations done
   int since_build = 0;  // evaluations since its list was last rebuilt
   int64_t hist_off = 0; // first entry of its energy history
+};
+
+// one copy of a structure's atoms (or history) from a source array into the new layout
+struct Seg {
+  int64_t src, dst;   // first element in the source and destination
+  int32_t n;          // elements
+  int32_t from;       // 0: the current batch arrays, 1: the host staging of admitted requests
 };
 
 template <typename T>
@@ -118,8 +126,23 @@ struct fnn_server {
   double *hist = nullptr;        // energy histories of the current layout
   double *hist_buf[2] = {nullptr, nullptr};
   size_t cap_hist[2] = {0, 0};
-  // pinned staging for the host copies
-  std::vector<float> host_tmp;
+  // relayout: device staging of admitted requests, segment tables, packed results (device and pinned host)
+  int32_t *sZ = nullptr;
+  float4 *spos = nullptr, *svel = nullptr;
+  size_t cap_sZ = 0, cap_spos = 0, cap_svel = 0;
+  Seg *d_seg = nullptr, *h_seg = nullptr;
+  size_t cap_seg = 0, cap_hseg = 0;
+  int32_t *h_sZ = nullptr;
+  float *h_spos = nullptr, *h_svel = nullptr;
+  size_t cap_hsZ = 0, cap_hspos = 0, cap_hsvel = 0;
+  int64_t *h_mol = nullptr;
+  size_t cap_hmol = 0;
+  float4 *r_pos = nullptr, *r_vel = nullptr, *h_rpos = nullptr, *h_rvel = nullptr;
+  float *r_F = nullptr, *h_rF = nullptr;
+  double *r_hist = nullptr, *h_rhist = nullptr;
+  size_t cap_rpos = 0, cap_rvel = 0, cap_rF = 0, cap_rhist = 0, cap_hrpos = 0, cap_hrvel = 0, cap_hrF = 0,
+         cap_hrhist = 0;
+  double host_ms = 0, step_ms = 0;   // worker time in layout changes and in batch steps
 };
 
 static double estimate_bytes_per_atom(const fnn_ctx *ctx, fnn_precision prec) {
@@ -131,89 +154,244 @@ static double estimate_bytes_per_atom(const fnn_ctx *ctx, fnn_precision prec) {
   return (ws32 + act) * 1.2 + list + state;
 }
 
-static fnn_status serve_step(fnn_server *S);
+// relayout of the batch: block per segment; Z, positions and velocities move together
+__global__ void k_relayout(const Seg *seg, int nseg, const int32_t *Z0, const float4 *p0, const float4 *v0,
+                           const int32_t *Z1, const float4 *p1, const float4 *v1, int32_t *Z, float4 *pos,
+                           float4 *vel) {
+  for (int k = blockIdx.x; k < nseg; k += gridDim.x) {
+    const Seg g = seg[k];
+    const int32_t *Zs = g.from ? Z1 : Z0;
+    const float4 *ps = g.from ? p1 : p0, *vs = g.from ? v1 : v0;
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+      Z[g.dst + i] = Zs[g.src + i];
+      pos[g.dst + i] = ps[g.src + i];
+      vel[g.dst + i] = vs[g.src + i];
+    }
+  }
+}
 
+// energy histories (doubles) into the new layout
+__global__ void k_gather_hist(const Seg *seg, int nseg, const double *src, double *dst) {
+  for (int k = blockIdx.x; k < nseg; k += gridDim.x) {
+    const Seg g = seg[k];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) dst[g.dst + i] = src[g.src + i];
+  }
+}
+
+// finished structures packed for one copy to the host: positions, velocities (float4), forces (3 floats)
+__global__ void k_pack_results(const Seg *seg, int nseg, const float4 *pos, const float4 *vel, const float *F,
+                               float4 *opos, float4 *ovel, float *oF) {
+  for (int k = blockIdx.x; k < nseg; k += gridDim.x) {
+    const Seg g = seg[k];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+      opos[g.dst + i] = pos[g.src + i];
+      ovel[g.dst + i] = vel[g.src + i];
+    }
+    for (int i = threadIdx.x; i < 3 * g.n; i += blockDim.x) oF[3 * g.dst + i] = F[3 * g.src + i];
+  }
+}
+
+template <typename T>
+static bool grow_host(T **p, size_t *cap, size_t need) {
+  if (need <= *cap && *p) return true;
+  size_t n = need + need / 2 + 64;
+  T *q = nullptr;
+  if (cudaHostAlloc((void **)&q, n * sizeof(T), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (*p) cudaFreeHost(*p);
+  *p = q;
+  *cap = n;
+  return true;
+}
+
+// Results of the structures that finished at the last step: packed on the device, copied to pinned
+// host memory (asynchronous; read after the next stream synchronisation by finish_retire).
+static fnn_status start_retire(fnn_server *S, const std::vector<Slot> &fin) {
+  cudaStream_t s = S->stream;
+  size_t atoms = 0, hist = 0;
+  std::vector<Seg> seg, hseg;
+  for (auto &sl : fin) {
+    seg.push_back(Seg{sl.offset, (int64_t)atoms, sl.req.n, 0});
+    hseg.push_back(Seg{sl.hist_off, (int64_t)hist, sl.req.n_steps, 0});
+    atoms += sl.req.n;
+    hist += sl.req.n_steps;
+  }
+  const size_t nseg = seg.size();
+  if (!grow(&S->r_pos, &S->cap_rpos, atoms + 1) || !grow(&S->r_vel, &S->cap_rvel, atoms + 1) ||
+      !grow(&S->r_F, &S->cap_rF, 3 * atoms + 3) || !grow(&S->r_hist, &S->cap_rhist, hist + 1) ||
+      !grow(&S->d_seg, &S->cap_seg, 2 * nseg + 2) ||
+      !grow_host(&S->h_rpos, &S->cap_hrpos, atoms + 1) || !grow_host(&S->h_rvel, &S->cap_hrvel, atoms + 1) ||
+      !grow_host(&S->h_rF, &S->cap_hrF, 3 * atoms + 3) || !grow_host(&S->h_rhist, &S->cap_hrhist, hist + 1) ||
+      !grow_host(&S->h_seg, &S->cap_hseg, 2 * nseg + 2))
+    return FNN_E_OOM;
+  memcpy(S->h_seg, seg.data(), nseg * sizeof(Seg));
+  memcpy(S->h_seg + nseg, hseg.data(), nseg * sizeof(Seg));
+  cudaMemcpyAsync(S->d_seg, S->h_seg, 2 * nseg * sizeof(Seg), cudaMemcpyHostToDevice, s);
+  const int blocks = (int)(nseg < 4096 ? nseg : 4096);
+  k_pack_results<<<blocks, 128, 0, s>>>(S->d_seg, (int)nseg, S->pos[S->cur], S->vel[S->cur], S->F, S->r_pos,
+                                         S->r_vel, S->r_F);
+  k_gather_hist<<<blocks, 128, 0, s>>>(S->d_seg + nseg, (int)nseg, S->hist, S->r_hist);
+  cudaMemcpyAsync(S->h_rpos, S->r_pos, atoms * sizeof(float4), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(S->h_rvel, S->r_vel, atoms * sizeof(float4), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(S->h_rF, S->r_F, 3 * atoms * sizeof(float), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(S->h_rhist, S->r_hist, hist * sizeof(double), cudaMemcpyDeviceToHost, s);
+  // the segment table is reused by the relayout below: the stream orders the two
+  cudaStreamSynchronize(s);
+  return cudaGetLastError() == cudaSuccess ? FNN_OK : FNN_E_CUDA;
+}
+
+static void finish_retire(fnn_server *S, std::vector<Slot> &fin) {
+  size_t atoms = 0, hist = 0;
+  const auto now = Clock::now();
+  std::vector<std::pair<uint64_t, Out>> outs;
+  outs.reserve(fin.size());
+  for (auto &sl : fin) {
+    Out o;
+    const int n = sl.req.n;
+    o.pos.resize(3 * (size_t)n);
+    o.vel.resize(3 * (size_t)n);
+    o.F.assign(S->h_rF + 3 * atoms, S->h_rF + 3 * (atoms + n));
+    o.E.assign(S->h_rhist + hist, S->h_rhist + hist + sl.req.n_steps);
+    for (int i = 0; i < n; i++) {
+      const float4 p = S->h_rpos[atoms + i], v = S->h_rvel[atoms + i];
+      o.pos[3 * i] = p.x; o.pos[3 * i + 1] = p.y; o.pos[3 * i + 2] = p.z;
+      o.vel[3 * i] = v.x; o.vel[3 * i + 1] = v.y; o.vel[3 * i + 2] = v.z;
+    }
+    o.latency_ms = std::chrono::duration<double, std::milli>(now - sl.req.t_submit).count();
+    o.queue_ms = std::chrono::duration<double, std::milli>(sl.req.t_admit - sl.req.t_submit).count();
+    o.n_steps_done = sl.step;
+    atoms += n;
+    hist += sl.req.n_steps;
+    outs.emplace_back(sl.req.ticket, std::move(o));
+  }
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    for (auto &po : outs) S->done[po.first] = std::move(po.second);
+  }
+  S->cv_done.notify_all();
+}
+
+// New layout: survivors (moved on the device), then admitted requests (from pinned host staging), all
+// with one segment table and one relayout kernel; per-structure arrays from one pinned block.
 static void repack(fnn_server *S, std::vector<Slot> &keep, std::vector<Req> &incoming, fnn_status *err) {
-  // new layout: survivors (copied on the device), then new structures (copied from the host)
-  size_t total = 0;
+  size_t total = 0, in_atoms = 0;
   for (auto &k : keep) total += k.req.n;
-  for (auto &r : incoming) total += r.n;
+  for (auto &r : incoming) in_atoms += r.n;
+  total += in_atoms;
   const int nxt = 1 - S->cur;
+  cudaStream_t s = S->stream;
+  const size_t nm = keep.size() + incoming.size();
   if (!grow(&S->Z[nxt], &S->cap_Z[nxt], total) || !grow(&S->pos[nxt], &S->cap_pos[nxt], total) ||
-      !grow(&S->vel[nxt], &S->cap_vel[nxt], total)) {
+      !grow(&S->vel[nxt], &S->cap_vel[nxt], total) || !grow(&S->sZ, &S->cap_sZ, in_atoms + 1) ||
+      !grow(&S->spos, &S->cap_spos, in_atoms + 1) || !grow(&S->svel, &S->cap_svel, in_atoms + 1) ||
+      !grow_host(&S->h_sZ, &S->cap_hsZ, in_atoms + 1) || !grow_host(&S->h_spos, &S->cap_hspos, 4 * in_atoms + 4) ||
+      !grow_host(&S->h_svel, &S->cap_hsvel, 4 * in_atoms + 4) || !grow(&S->d_seg, &S->cap_seg, 2 * nm + 2) ||
+      !grow_host(&S->h_seg, &S->cap_hseg, 2 * nm + 2)) {
     *err = FNN_E_OOM;
     return;
   }
-  cudaStream_t s = S->stream;
-  size_t off = 0;
+  // admitted requests into the pinned staging, one copy each way
+  size_t ia = 0;
+  for (auto &r : incoming) {
+    memcpy(S->h_sZ + ia, r.Z.data(), r.n * sizeof(int32_t));
+    memcpy(S->h_spos + 4 * ia, r.pos4.data(), 4 * (size_t)r.n * sizeof(float));
+    memcpy(S->h_svel + 4 * ia, r.vel4.data(), 4 * (size_t)r.n * sizeof(float));
+    ia += r.n;
+    // the structure lives on the device from here on: drop the host copy of its atoms
+    std::vector<int32_t>().swap(r.Z);
+    std::vector<float>().swap(r.pos4);
+    std::vector<float>().swap(r.vel4);
+  }
+  if (in_atoms) {
+    cudaMemcpyAsync(S->sZ, S->h_sZ, in_atoms * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(S->spos, S->h_spos, in_atoms * sizeof(float4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(S->svel, S->h_svel, in_atoms * sizeof(float4), cudaMemcpyHostToDevice, s);
+  }
+  size_t off = 0, ioff = 0;
   std::vector<Slot> next;
-  for (auto &k : keep) {
-    cudaMemcpyAsync(S->Z[nxt] + off, S->Z[S->cur] + k.offset, k.req.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(S->pos[nxt] + off, S->pos[S->cur] + k.offset, k.req.n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(S->vel[nxt] + off, S->vel[S->cur] + k.offset, k.req.n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-    Slot sl = k;
+  next.reserve(nm);
+  Seg *seg = S->h_seg;
+  std::vector<int> keep_step(keep.size());
+  std::vector<int64_t> keep_hist(keep.size());
+  for (size_t m = 0; m < keep.size(); m++) {
+    Slot &k = keep[m];
+    seg[next.size()] = Seg{k.offset, (int64_t)off, k.req.n, 0};
+    keep_step[m] = k.step;
+    keep_hist[m] = k.hist_off;
+    Slot sl = std::move(k);
     sl.offset = (int)off;
-    next.push_back(sl);
-    off += k.req.n;
+    off += sl.req.n;
+    next.push_back(std::move(sl));
   }
   for (auto &r : incoming) {
-    cudaMemcpyAsync(S->Z[nxt] + off, r.Z.data(), r.n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(S->pos[nxt] + off, r.pos4.data(), r.n * sizeof(float4), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(S->vel[nxt] + off, r.vel4.data(), r.n * sizeof(float4), cudaMemcpyHostToDevice, s);
+    seg[next.size()] = Seg{(int64_t)ioff, (int64_t)off, r.n, 1};
     Slot sl;
     sl.req = std::move(r);
     sl.offset = (int)off;
     sl.req.t_admit = Clock::now();
+    ioff += sl.req.n;
+    off += sl.req.n;
     next.push_back(std::move(sl));
-    off += next.back().req.n;
   }
-  // per-structure arrays
-  const size_t nm = next.size();
+  // histories move with their structures into the other buffer of the pair
+  int64_t hist_total = 0;
+  size_t nh = 0;
+  Seg *hseg = seg + nm;
+  for (size_t m = 0; m < nm; m++) {
+    if (m < keep.size() && keep_step[m] > 0) hseg[nh++] = Seg{keep_hist[m], hist_total, keep_step[m], 0};
+    next[m].hist_off = hist_total;
+    hist_total += next[m].req.n_steps;
+  }
+  const int hb = (S->hist == S->hist_buf[0]) ? 1 : 0;
   if (!grow(&S->mol_offsets, &S->cap_mol, nm + 1) || !grow(&S->mol_step, &S->cap_mol2, nm) ||
       !grow(&S->mol_nsteps, &S->cap_mol3, nm) || !grow(&S->cell, &S->cap_mol4, nm * 9) ||
       !grow(&S->pbc, &S->cap_mol5, nm) || !grow(&S->E, &S->cap_mol6, nm) || !grow(&S->hist_off, &S->cap_mol7, nm) ||
-      !grow(&S->mol_dt, &S->cap_mol8, nm) || !grow(&S->F, &S->cap_F, 3 * total + 3)) {
+      !grow(&S->mol_dt, &S->cap_mol8, nm) || !grow(&S->F, &S->cap_F, 3 * total + 3) ||
+      !grow(&S->hist_buf[hb], &S->cap_hist[hb], (size_t)hist_total + 1) ||
+      !grow_host(&S->h_mol, &S->cap_hmol, nm * 64 + 64)) {
     *err = FNN_E_OOM;
     return;
   }
-  std::vector<int32_t> mo(nm + 1), st(nm), ns(nm);
-  std::vector<float> ce(nm * 9);
-  std::vector<uint8_t> pb(nm);
-  std::vector<int64_t> ho(nm);
-  std::vector<float> dts(nm);
-  int64_t hist_total = 0;
+  cudaMemcpyAsync(S->d_seg, seg, (nm + nh) * sizeof(Seg), cudaMemcpyHostToDevice, s);
+  if (nm) {
+    const int blocks = (int)(nm < 4096 ? nm : 4096);
+    k_relayout<<<blocks, 128, 0, s>>>(S->d_seg, (int)nm, S->Z[S->cur], S->pos[S->cur], S->vel[S->cur], S->sZ, S->spos,
+                                      S->svel, S->Z[nxt], S->pos[nxt], S->vel[nxt]);
+  }
+  double *new_hist = S->hist_buf[hb];
+  if (nh) {
+    const int blocks = (int)(nh < 4096 ? nh : 4096);
+    k_gather_hist<<<blocks, 128, 0, s>>>(S->d_seg + nm, (int)nh, S->hist, new_hist);
+  }
+  // per-structure arrays from one pinned block
+  char *hm = reinterpret_cast<char *>(S->h_mol);
+  int32_t *mo = reinterpret_cast<int32_t *>(hm);
+  int32_t *st = mo + (nm + 1);
+  int32_t *ns = st + nm;
+  float *ce = reinterpret_cast<float *>(ns + nm);
+  float *dts = ce + 9 * nm;
+  int64_t *ho = reinterpret_cast<int64_t *>(hm + (((char *)(dts + nm) - hm + 7) & ~(size_t)7));
+  uint8_t *pb = reinterpret_cast<uint8_t *>(ho + nm);
   for (size_t m = 0; m < nm; m++) {
     mo[m] = next[m].offset;
     st[m] = next[m].step;
     ns[m] = next[m].req.n_steps;
     memcpy(&ce[9 * m], next[m].req.cell, 9 * sizeof(float));
-    pb[m] = next[m].req.pbc;
     dts[m] = (float)next[m].req.dt;
-    ho[m] = hist_total;
-    hist_total += next[m].req.n_steps;
+    ho[m] = next[m].hist_off;
+    pb[m] = next[m].req.pbc;
   }
   mo[nm] = (int32_t)total;
-  // histories move with their structures into the other buffer of the pair (grow-only, no frees here)
-  double *old_hist = S->hist;
-  const int hb = (S->hist == S->hist_buf[0]) ? 1 : 0;
-  if (!grow(&S->hist_buf[hb], &S->cap_hist[hb], (size_t)hist_total + 1)) {
-    *err = FNN_E_OOM;
-    return;
-  }
-  double *new_hist = S->hist_buf[hb];
-  for (size_t m = 0; m < keep.size(); m++)
-    if (keep[m].step > 0)
-      cudaMemcpyAsync(new_hist + ho[m], old_hist + keep[m].hist_off, keep[m].step * sizeof(double),
-                      cudaMemcpyDeviceToDevice, s);
-  for (size_t m = 0; m < nm; m++) next[m].hist_off = ho[m];
-  cudaMemcpyAsync(S->mol_offsets, mo.data(), (nm + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->mol_step, st.data(), nm * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->mol_nsteps, ns.data(), nm * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->cell, ce.data(), nm * 9 * sizeof(float), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->pbc, pb.data(), nm, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->hist_off, ho.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(S->mol_dt, dts.data(), nm * sizeof(float), cudaMemcpyHostToDevice, s);
-  cudaStreamSynchronize(s);   // host vectors above must outlive their copies
+  cudaMemcpyAsync(S->mol_offsets, mo, (nm + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->mol_step, st, nm * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->mol_nsteps, ns, nm * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->cell, ce, nm * 9 * sizeof(float), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->mol_dt, dts, nm * sizeof(float), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->hist_off, ho, nm * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->pbc, pb, nm, cudaMemcpyHostToDevice, s);
+  // the pinned blocks are rewritten only after the next stream synchronisation (end of the batch step)
   S->hist = new_hist;
   S->cur = nxt;
   S->active = std::move(next);
@@ -232,6 +410,12 @@ static fnn_status serve_step(fnn_server *S) {
   for (auto &sl : S->active)
     if (sl.since_build == 0 || sl.since_build >= S->rebuild_every) rebuild = true;
   fnn_status st;
+  // the list and (through its padded row count) every network workspace grow geometrically with the
+  // batch, so a batch that keeps growing does not reallocate gigabytes at every step
+  if (sys.n_atoms > S->nl->atom_cap || nm > S->nl->mol_cap) {
+    const int32_t na = 2 * sys.n_atoms, nmol = 2 * nm;
+    if ((st = fnn_nlist_reserve(S->nl, na, nmol, (int64_t)160 * na + 1024))) return st;
+  }
   if (rebuild) {
     // a list larger than its capacity is regrown and rebuilt before any force is computed
     for (int attempt = 0; attempt < 2; attempt++) {
@@ -261,83 +445,70 @@ static fnn_status serve_step(fnn_server *S) {
   return FNN_OK;
 }
 
-static void retire(fnn_server *S, std::vector<Slot> &finished) {
-  cudaStream_t s = S->stream;
-  for (auto &sl : finished) {
+static void fail_all(fnn_server *S, fnn_status err) {
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->fatal = err;
+  for (auto &sl : S->active) {
     Out o;
-    const int n = sl.req.n;
-    std::vector<float4> p4(n), v4(n);
-    o.F.resize(3 * (size_t)n);
-    o.E.resize(sl.req.n_steps);
-    cudaMemcpyAsync(p4.data(), S->pos[S->cur] + sl.offset, n * sizeof(float4), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(v4.data(), S->vel[S->cur] + sl.offset, n * sizeof(float4), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(o.F.data(), S->F + 3 * (size_t)sl.offset, 3 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
-    if (sl.req.n_steps > 0)
-      cudaMemcpyAsync(o.E.data(), S->hist + sl.hist_off, sl.req.n_steps * sizeof(double), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    o.pos.resize(3 * (size_t)n);
-    o.vel.resize(3 * (size_t)n);
-    for (int i = 0; i < n; i++) {
-      o.pos[3 * i] = p4[i].x; o.pos[3 * i + 1] = p4[i].y; o.pos[3 * i + 2] = p4[i].z;
-      o.vel[3 * i] = v4[i].x; o.vel[3 * i + 1] = v4[i].y; o.vel[3 * i + 2] = v4[i].z;
-    }
-    const auto now = Clock::now();
-    o.latency_ms = std::chrono::duration<double, std::milli>(now - sl.req.t_submit).count();
-    o.queue_ms = std::chrono::duration<double, std::milli>(sl.req.t_admit - sl.req.t_submit).count();
-    o.n_steps_done = sl.step;
-    std::lock_guard<std::mutex> lock(S->mu);
+    o.status = err;
     S->done[sl.req.ticket] = std::move(o);
   }
+  S->active.clear();
   S->cv_done.notify_all();
 }
 
 static void worker_main(fnn_server *S) {
   cudaSetDevice(S->ctx->device);
+  std::vector<Slot> fin;   // finished at the last batch step, results not yet taken
   for (;;) {
     std::vector<Req> incoming;
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      S->cv.wait(lock, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
-      if (S->stop && S->active.empty() && S->pending.empty()) break;
+      S->cv.wait(lock, [&] { return S->stop || !S->pending.empty() || !S->active.empty() || !fin.empty(); });
+      if (S->stop && S->active.empty() && S->pending.empty() && fin.empty()) break;
       // admit in arrival order while the batch fits the budget
       double in_use = 0;
-      for (auto &sl : S->active) in_use += sl.req.n * S->bytes_per_atom;
+      for (auto &sl : S->active)
+        if (sl.step < sl.req.n_steps) in_use += sl.req.n * S->bytes_per_atom;
       while (!S->pending.empty() && in_use + S->pending.front().n * S->bytes_per_atom <= (double)S->budget) {
         in_use += S->pending.front().n * S->bytes_per_atom;
         incoming.push_back(std::move(S->pending.front()));
         S->pending.pop_front();
       }
+      S->admitted += (long long)incoming.size();
     }
+    const auto t0 = Clock::now();
     // structures with nothing to evaluate finish at once
-    std::vector<Slot> finished;
     for (auto it = incoming.begin(); it != incoming.end();) {
       if (it->n_steps <= 0) {
-        Slot sl;
-        sl.req = std::move(*it);
-        sl.req.t_admit = Clock::now();
-        finished.push_back(std::move(sl));
+        Out o;
+        o.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - it->t_submit).count();
+        {
+          std::lock_guard<std::mutex> lock(S->mu);
+          S->done[it->ticket] = std::move(o);
+        }
+        S->cv_done.notify_all();
         it = incoming.erase(it);
       } else {
         ++it;
       }
     }
-    if (!finished.empty()) {
-      std::vector<Slot> none;
-      for (auto &sl : finished) {
-        std::lock_guard<std::mutex> lock(S->mu);
-        Out o;
-        o.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t_submit).count();
-        S->done[sl.req.ticket] = std::move(o);
-      }
-      S->cv_done.notify_all();
-    }
     fnn_status err = FNN_OK;
-    if (!incoming.empty()) {
-      std::vector<Slot> keep = S->active;
-      repack(S, keep, incoming, &err);
-      std::lock_guard<std::mutex> lock(S->mu);
-      S->admitted += (long long)incoming.size();
+    std::vector<Slot> keep;
+    const bool changed = !incoming.empty() ||
+                         std::any_of(S->active.begin(), S->active.end(),
+                                     [](const Slot &sl) { return sl.step >= sl.req.n_steps; });
+    if (changed) {
+      for (auto &sl : S->active) (sl.step >= sl.req.n_steps ? fin : keep).push_back(std::move(sl));
+      S->active.clear();
     }
+    if (!fin.empty()) err = start_retire(S, fin);
+    if (!fin.empty() && err == FNN_OK) {
+      finish_retire(S, fin);
+      fin.clear();
+    }
+    if (err == FNN_OK && changed) repack(S, keep, incoming, &err);
+    const auto t1 = Clock::now();
     if (err == FNN_OK && !S->active.empty()) {
       err = serve_step(S);
       if (err == FNN_OK) {
@@ -349,25 +520,19 @@ static void worker_main(fnn_server *S) {
       S->atom_evals += (long long)S->batch_atoms;
       if ((long long)S->batch_atoms > S->max_batch_atoms) S->max_batch_atoms = (long long)S->batch_atoms;
     }
-    if (err != FNN_OK) {
+    const auto t2 = Clock::now();
+    {
       std::lock_guard<std::mutex> lock(S->mu);
-      S->fatal = err;
-      for (auto &sl : S->active) {
-        Out o;
-        o.status = err;
-        S->done[sl.req.ticket] = std::move(o);
-      }
-      S->active.clear();
-      S->cv_done.notify_all();
-      continue;
+      S->host_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+      S->step_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
     }
-    // retire finished structures; the survivors are repacked at the next admission or now
-    std::vector<Slot> fin, keep;
-    for (auto &sl : S->active) (sl.step >= sl.req.n_steps ? fin : keep).push_back(sl);
-    if (!fin.empty()) {
-      retire(S, fin);
-      std::vector<Req> none;
-      repack(S, keep, none, &err);
+    if (err != FNN_OK) {
+      // every structure still waiting for its result fails (tickets survive a move of their slot)
+      if (S->active.empty())
+        for (auto &sl : keep) S->active.push_back(std::move(sl));
+      for (auto &sl : fin) S->active.push_back(std::move(sl));
+      fin.clear();
+      fail_all(S, err);
     }
   }
 }
@@ -465,6 +630,8 @@ extern "C" fnn_status fnn_serve_stats(fnn_server *S, fnn_serve_counters *st) {
   st->max_batch_atoms = S->max_batch_atoms;
   st->pending = (int64_t)S->pending.size();
   st->bytes_per_atom = S->bytes_per_atom;
+  st->host_ms = S->host_ms;
+  st->step_ms = S->step_ms;
   return S->fatal;
 }
 
@@ -483,9 +650,13 @@ extern "C" fnn_status fnn_serve_destroy(fnn_server *S) {
     if (S->vel[b]) cudaFree(S->vel[b]);
   }
   void *ptrs[] = {S->F, S->mol_offsets, S->mol_step, S->mol_nsteps, S->cell, S->pbc, S->E, S->hist_off,
-                  S->hist_buf[0], S->hist_buf[1], S->mol_dt};
+                  S->hist_buf[0], S->hist_buf[1], S->mol_dt, S->sZ, S->spos, S->svel, S->d_seg,
+                  S->r_pos, S->r_vel, S->r_F, S->r_hist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  void *hptrs[] = {S->h_seg, S->h_sZ, S->h_spos, S->h_svel, S->h_mol, S->h_rpos, S->h_rvel, S->h_rF, S->h_rhist};
+  for (void *p : hptrs)
+    if (p) cudaFreeHost(p);
   if (S->nl) fnn_nlist_destroy(S->nl);
   cudaStreamDestroy(S->stream);
   delete S;

@@ -71,7 +71,8 @@ class CResult(ctypes.Structure):
 
 class CServeCounters(ctypes.Structure):
     _fields_ = [("atom_evals", ctypes.c_int64), ("batch_steps", ctypes.c_int64), ("admitted", ctypes.c_int64),
-                ("max_batch_atoms", ctypes.c_int64), ("pending", ctypes.c_int64), ("bytes_per_atom", ctypes.c_double)]
+                ("max_batch_atoms", ctypes.c_int64), ("pending", ctypes.c_int64), ("bytes_per_atom", ctypes.c_double),
+                ("host_ms", ctypes.c_double), ("step_ms", ctypes.c_double)]
 
 
 class CSystem(ctypes.Structure):
