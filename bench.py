@@ -335,7 +335,7 @@ def serve_bench(fnn, torch, synth, duration_s=2.0, rate_hz=2000.0, pool_n=128, b
     return out
 
 
-def train_bench(fnn, torch, synth, steps, warmup, M=1):
+def train_bench(fnn, torch, synth, steps, warmup, M=1, precision="bf16"):
     """One training step of the 4096-molecule ragged batch (8..64 atoms each): energies and forces through
     the autograd function, the loss 0.99 mean (F - F*)^2 + 0.01 mean ((E - E*)/n)^2, and its parameter
     gradients (fnn_param_grads) by backward.  Device-resident inputs; CUDA events around each step."""
@@ -358,7 +358,7 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1):
         fnn.build_neighbors(ctx, ds, nl)
         for p in params:
             p.grad = None
-        E, F = fnn.energy_forces_autograd(ctx, ds, nl, params)
+        E, F = fnn.energy_forces_autograd(ctx, ds, nl, params, precision=precision)
         L = 0.99 * torch.mean((F - Ft) ** 2) + 0.01 * torch.mean(((E - Et) / n) ** 2)
         L.backward()
         return L
@@ -385,7 +385,7 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1):
     total = sum(v[0] for v in prof.values())
     top = sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]
     return {"workload": f"ragged batch: 4096 molecules, 8-64 atoms, {s.n_atoms} atoms (gas phase)",
-            "members": M, "precision": "fp32", "ms_per_step": ms, "atoms_per_s": s.n_atoms / (ms * 1e-3),
+            "members": M, "precision": precision, "ms_per_step": ms, "atoms_per_s": s.n_atoms / (ms * 1e-3),
             "loss": float(L.detach()), "gpu_launches_per_step": launches / steps,
             "kernel_share": {k: round(v[0] / total, 3) for k, v in top},
             "note": "forward (E, F) + loss + parameter gradients; the optimizer update is not timed"}
@@ -593,7 +593,8 @@ def main():
         md = md_bench(fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
-        train = train_bench(fnn, torch, synth, args.steps, max(3, args.warmup))
+        train = {p: train_bench(fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
+                 for p in ("bf16", "fp32")}
 
     head = results[args.precision]
     kernels, roof = kernel_table(head["prof"], args.steps, s.n_atoms, nnz, M, args.precision, pk)

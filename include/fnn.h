@@ -203,11 +203,13 @@ typedef struct {
  * order) at the current parameters:
  *   dL/dtheta = dL/dE . dE/dtheta - d/dtheta <J v, dE/dAEV>,  v = dL/dF,  J = dAEV/dx,
  * the second term by a forward-mode tangent of the networks along J v (fnn_aev_jvp) and one reverse
- * sweep over the primal and tangent activations.  FP32 arithmetic; the list must be built for sys.
- * Adds into g (zero it first).  Asynchronous on stream.
+ * sweep over the primal and tangent activations.  prec: FNN_FP32 (SIMT FP32 throughout) or FNN_BF16
+ * (every product on the tensor cores with bf16 operands and FP32 accumulation, the weight gradients
+ * as products over each element's rows); others give FNN_E_INVALID.  The list must be built for
+ * sys.  Adds into g (zero it first).  Asynchronous on stream.
  */
-fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
-                           const float *dLdF, const fnn_grads *g, void *stream);
+fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec,
+                           const double *dLdE, const float *dLdF, const fnn_grads *g, void *stream);
 
 /*
  * One step as a CUDA graph: fnn_build_neighbors (when rebuild != 0) then fnn_energy_forces, recorded on

@@ -264,6 +264,8 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
 void free_tc(fnn_ctx *ctx);
 fnn_status fp8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, cudaStream_t s);
 void free_train(fnn_ctx *ctx);
+fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
+                          const float *dLdF, const fnn_grads *g, cudaStream_t s);
 fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, cudaStream_t s);
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
                               int ntile, double *E, cudaStream_t s);

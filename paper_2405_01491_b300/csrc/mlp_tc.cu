@@ -20,11 +20,14 @@
 
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "tc_gemm.cuh"
 
 namespace fnn {
+
+void free_train_tc(void *p);
 
 namespace {
 
@@ -87,6 +90,7 @@ struct TcState {
   size_t rows = 0;
   Half h[2];   // [0] hi, [1] lo
   F8 f8;
+  void *train = nullptr;   // BF16 training buffers (tc_param_grads)
 };
 
 TcState *state(fnn_ctx *ctx) {
@@ -132,6 +136,7 @@ void free_tc(fnn_ctx *ctx) {
   if (t->f8.wscale) cudaFree(t->f8.wscale);
   if (t->f8.abuf) cudaFree(t->f8.abuf);
   if (t->f8.amax) cudaFree(t->f8.amax);
+  free_train_tc(t->train);
   delete t;
   ctx->w.tc = nullptr;
 }
@@ -546,6 +551,379 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
   st = split ? run_layers<true>(ctx, t, nl, s) : run_layers<false>(ctx, t, nl, s);
   if (st) return st;
   return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, s);
+}
+
+
+// ============================================================================================ training
+// Parameter gradients of the loss with BF16 networks on the tensor cores (the FP32 form of this
+// computation, with the derivation, is in train.cu).  Activations and gradient streams are bf16 in
+// HBM; every product accumulates in FP32:
+//   forward   h_l = CELU(h_{l-1} W_l^T + b_l)                           (EPI_BIAS_CELU)
+//   tangent   hd_l = CELU'(h_l) (hd_{l-1} W_l^T), hd_0 = J dL/dF         (EPI_DCELU, aux h_l)
+//   reverse   raw gb_{l-1} = gbz_l W_l, g_{l-1} = gz_l W_l               (EPI_PLAIN)
+//             gbz = CELU'(h) gb, gz = CELU'(h) g + (CELU''/CELU')(h) hd gb   (k_act_reverse_bf16)
+//   weights   dW_l += gbz_l^T hd_{l-1} + gz_l^T h_{l-1}: K runs over each element's rows, with both
+//             factors stored row-contiguous ([member][feature][row], k_transpose) (MODE_WG, EPI_ATOMIC)
+
+namespace {
+
+// [rows][member stride ms, F features] (float or bf16) -> bf16 [member][F][R] (and, for float input, a
+// bf16 row-major copy); 64 x 64 tiles through shared memory, 16-byte loads and stores on both sides
+// (rows a multiple of 64, F and the strides multiples of 8)
+template <typename InT>
+__global__ void __launch_bounds__(256) k_transpose_bf16(int rows, int F, const InT *in, long long ld, long long ms,
+                                                        __nv_bfloat16 *outT, long long R, __nv_bfloat16 *out_rm,
+                                                        long long ld_out) {
+  __shared__ __nv_bfloat16 tile[64][72];   // [row][feature], rows padded to 144 bytes
+  const int f0 = blockIdx.x * 64, r0 = blockIdx.y * 64, m = blockIdx.z;
+  constexpr int V = 16 / (int)sizeof(InT);   // elements per 16-byte load
+  // load: 64 rows x 64 features
+  for (int k = threadIdx.x; k < 64 * (64 / V); k += 256) {
+    const int rr = k / (64 / V), fv = (k % (64 / V)) * V;
+    const int r = r0 + rr, f = f0 + fv;
+    alignas(16) __nv_bfloat16 b[V];
+    if (r < rows && f < F) {
+      const InT *src = in + (size_t)r * ld + m * ms + f;
+      if constexpr (std::is_same<InT, float>::value) {
+        const float4 x = *reinterpret_cast<const float4 *>(src);
+        b[0] = __float2bfloat16(x.x); b[1] = __float2bfloat16(x.y);
+        b[2] = __float2bfloat16(x.z); b[3] = __float2bfloat16(x.w);
+        if (out_rm) *reinterpret_cast<uint2 *>(out_rm + (size_t)r * ld_out + m * ms + f) = *reinterpret_cast<uint2 *>(b);
+      } else {
+        *reinterpret_cast<uint4 *>(b) = *reinterpret_cast<const uint4 *>(src);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; j++) b[j] = __float2bfloat16(0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < V; j++) tile[rr][fv + j] = b[j];
+  }
+  __syncthreads();
+  // store: 64 features x 64 rows, eight rows per 16-byte store
+  for (int k = threadIdx.x; k < 64 * 8; k += 256) {
+    const int ff = k / 8, rv = (k % 8) * 8;
+    const int f = f0 + ff, r = r0 + rv;
+    if (f >= F || r >= rows) continue;
+    alignas(16) __nv_bfloat16 b[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) b[j] = tile[rv + j][ff];
+    *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f) * R + r) = *reinterpret_cast<const uint4 *>(b);
+  }
+}
+
+__device__ __forceinline__ float dcelu_hb(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
+__device__ __forceinline__ float ratio_hb(float h) { return h > 0.f ? 0.f : CELU_INV_ALPHA; }
+
+// output layer: gbz3 = CELU'(h3) (-(1/M) w4), gz3 = CELU'(h3) ((1/M) dL/dE w4) + ratio(h3) hd3 gb3;
+// dw4 += (1/M) dL/dE h3 - (1/M) hd3, db4 += (1/M) dL/dE, db3 += gz3 (sums per tile, one atomic each)
+__global__ void k_out_reverse_bf16(int M, const int32_t *tile_elem, const int32_t *inv, const int32_t *atom_mol,
+                                   const double *dLdE, const float *w4, const __nv_bfloat16 *h3,
+                                   const __nv_bfloat16 *hd3, __nv_bfloat16 *gbz3, __nv_bfloat16 *gz3, float *dw4,
+                                   float *db4, float *db3) {
+  const int tile = blockIdx.x, m = blockIdx.y, n = threadIdx.x;   // blockDim.x = H3
+  const int e = tile_elem[tile];
+  if (e < 0) return;
+  const float w = w4[((size_t)m * NE + e) * H3 + n];
+  const float c = 1.f / (float)M;
+  float acc_w = 0.f, acc_b = 0.f, acc_b3 = 0.f;
+  for (int rr = 0; rr < ROW_TILE; rr++) {
+    const size_t r = (size_t)tile * ROW_TILE + rr;
+    const int i = inv[r];
+    const size_t o = r * (size_t)M * H3 + (size_t)m * H3 + n;
+    const int mol = i < 0 ? -1 : atom_mol[i];
+    if (mol < 0) {
+      gbz3[o] = __float2bfloat16(0.f);
+      gz3[o] = __float2bfloat16(0.f);
+      continue;
+    }
+    const float cE = (float)dLdE[mol] * c;
+    const float h = __bfloat162float(h3[o]), hd = __bfloat162float(hd3[o]);
+    const float s1 = dcelu_hb(h);
+    const float gb = -c * w, g = cE * w;
+    const float gz = s1 * g + ratio_hb(h) * hd * gb;
+    gbz3[o] = __float2bfloat16(s1 * gb);
+    gz3[o] = __float2bfloat16(gz);
+    acc_w += cE * h - c * hd;
+    acc_b += cE;
+    acc_b3 += gz;
+  }
+  atomicAdd(&dw4[((size_t)m * NE + e) * H3 + n], acc_w);
+  atomicAdd(&db3[((size_t)m * NE + e) * H3 + n], acc_b3);
+  if (n == 0) atomicAdd(&db4[(size_t)m * NE + e], acc_b);
+}
+
+// hidden layer: (raw gb, g) -> gbz = CELU'(h) gb, gz = CELU'(h) g + ratio(h) hd gb; db += gz per tile
+__global__ void k_act_reverse_bf16(int M, int F, const int32_t *tile_elem, const __nv_bfloat16 *h,
+                                   const __nv_bfloat16 *hd, const __nv_bfloat16 *gb, const __nv_bfloat16 *g,
+                                   __nv_bfloat16 *gbz, __nv_bfloat16 *gz, float *db) {
+  const int tile = blockIdx.x, m = blockIdx.y;
+  const int e = tile_elem[tile];
+  if (e < 0) return;
+  for (int n = threadIdx.x; n < F; n += blockDim.x) {
+    float acc = 0.f;
+    for (int rr = 0; rr < ROW_TILE; rr++) {
+      const size_t o = ((size_t)tile * ROW_TILE + rr) * (size_t)M * F + (size_t)m * F + n;
+      const float hv = __bfloat162float(h[o]), b = __bfloat162float(gb[o]);
+      const float s1 = dcelu_hb(hv);
+      const float z = s1 * __bfloat162float(g[o]) + ratio_hb(hv) * __bfloat162float(hd[o]) * b;
+      gbz[o] = __float2bfloat16(s1 * b);
+      gz[o] = __float2bfloat16(z);
+      acc += z;
+    }
+    atomicAdd(&db[((size_t)m * NE + e) * F + n], acc);
+  }
+}
+
+struct TrainTc {
+  size_t rows = 0;
+  int M = 0;
+  void *buf = nullptr;
+  float *t32 = nullptr;                       // AEV tangent, float [R][1008]
+  __nv_bfloat16 *t = nullptr, *h3 = nullptr, *hd1 = nullptr, *hd2 = nullptr, *hd3 = nullptr;
+  __nv_bfloat16 *gbz3 = nullptr, *gz3 = nullptr, *gb2 = nullptr, *g2 = nullptr, *gbz2 = nullptr, *gz2 = nullptr;
+  __nv_bfloat16 *gb1 = nullptr, *g1 = nullptr, *gbz1 = nullptr, *gz1 = nullptr;
+  // row-contiguous transposes [member][feature][R]
+  __nv_bfloat16 *aevT = nullptr, *tT = nullptr, *h1T = nullptr, *hd1T = nullptr, *h2T = nullptr, *hd2T = nullptr;
+  __nv_bfloat16 *gbz3T = nullptr, *gz3T = nullptr, *gbz2T = nullptr, *gz2T = nullptr, *gbz1T = nullptr,
+                *gz1T = nullptr;
+  // operand maps (128-byte rows), epilogue piece maps, transposed operand maps
+  CUtensorMap mT, mHD1, mHD2, mGBZ3, mGZ3, mGBZ2, mGZ2;
+  CUtensorMap eH3, eHD1, eHD2, eHD3, eGB2, eG2, eGB1, eG1;
+  CUtensorMap tGBZ3, tGZ3, tGBZ2, tGZ2, tGBZ1, tGZ1, tHD2, tH2, tHD1, tH1, tT_, tAev;
+};
+
+}  // namespace
+
+void free_train_tc(void *p) {
+  TrainTc *T = static_cast<TrainTc *>(p);
+  if (!T) return;
+  if (T->buf) cudaFree(T->buf);
+  delete T;
+}
+
+static fnn_status train_tc_workspace(fnn_ctx *ctx, TcState *ts, size_t rows) {
+  if (!ts->train) ts->train = new TrainTc();
+  TrainTc &T = *static_cast<TrainTc *>(ts->train);
+  const int M = ts->M;
+  if (T.buf && rows <= T.rows && T.M == M) return FNN_OK;
+  if (T.buf) cudaFree(T.buf);
+  T.buf = nullptr;
+  rows = (rows + rows / 8 + 127) / 128 * 128;
+  const size_t R = rows;
+  const size_t n16 = R * (NAEV + (size_t)M * (H3 + H1 + H2 + H3 + 2 * H3 + 4 * H2 + 4 * H1)) +
+                     R * (2 * (size_t)NAEV + (size_t)M * (4 * H1 + 4 * H2 + 2 * H3));
+  const size_t bytes = R * NAEV * sizeof(float) + n16 * sizeof(__nv_bfloat16) + 4096;
+  if (cudaMalloc(&T.buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "cudaMalloc failed for the bf16 training workspace";
+    return FNN_E_OOM;
+  }
+  T.t32 = static_cast<float *>(T.buf);
+  __nv_bfloat16 *p = reinterpret_cast<__nv_bfloat16 *>(T.t32 + R * NAEV);
+  auto take = [&](size_t n) {
+    __nv_bfloat16 *q = p;
+    p += n;
+    return q;
+  };
+  T.t = take(R * NAEV);
+  T.h3 = take(R * M * H3);
+  T.hd1 = take(R * M * H1);
+  T.hd2 = take(R * M * H2);
+  T.hd3 = take(R * M * H3);
+  T.gbz3 = take(R * M * H3);
+  T.gz3 = take(R * M * H3);
+  T.gb2 = take(R * M * H2);
+  T.g2 = take(R * M * H2);
+  T.gbz2 = take(R * M * H2);
+  T.gz2 = take(R * M * H2);
+  T.gb1 = take(R * M * H1);
+  T.g1 = take(R * M * H1);
+  T.gbz1 = take(R * M * H1);
+  T.gz1 = take(R * M * H1);
+  T.aevT = take(R * NAEV);
+  T.tT = take(R * NAEV);
+  T.h1T = take(R * M * H1);
+  T.hd1T = take(R * M * H1);
+  T.gbz1T = take(R * M * H1);
+  T.gz1T = take(R * M * H1);
+  T.h2T = take(R * M * H2);
+  T.hd2T = take(R * M * H2);
+  T.gbz2T = take(R * M * H2);
+  T.gz2T = take(R * M * H2);
+  T.gbz3T = take(R * M * H3);
+  T.gz3T = take(R * M * H3);
+  const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE, S128 = CU_TENSOR_MAP_SWIZZLE_128B;
+  auto op = [&](CUtensorMap *mp, void *b, uint64_t F) {   // row-major operand, member in the middle
+    return encode3d(mp, b, F, M, R, F * 2, (uint64_t)M * F * 2, 64, 1, 128, BF, S128);
+  };
+  auto ep = [&](CUtensorMap *mp, void *b, uint64_t F) {   // epilogue pieces
+    return encode3d(mp, b, F, M, R, F * 2, (uint64_t)M * F * 2, 16, 1, 32, BF, NS);
+  };
+  auto tr = [&](CUtensorMap *mp, void *b, uint64_t F, uint64_t mem, uint32_t box_f) {   // [member][F][R]
+    return encode3d(mp, b, R, F, mem, R * 2, F * R * 2, 64, box_f, 1, BF, S128);
+  };
+  bool ok = encode3d(&T.mT, T.t, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 128, BF, S128) && op(&T.mHD1, T.hd1, H1) &&
+            op(&T.mHD2, T.hd2, H2) && op(&T.mGBZ3, T.gbz3, H3) && op(&T.mGZ3, T.gz3, H3) && op(&T.mGBZ2, T.gbz2, H2) &&
+            op(&T.mGZ2, T.gz2, H2) && ep(&T.eH3, T.h3, H3) && ep(&T.eHD1, T.hd1, H1) && ep(&T.eHD2, T.hd2, H2) &&
+            ep(&T.eHD3, T.hd3, H3) && ep(&T.eGB2, T.gb2, H2) && ep(&T.eG2, T.g2, H2) && ep(&T.eGB1, T.gb1, H1) &&
+            ep(&T.eG1, T.g1, H1) && tr(&T.tGBZ3, T.gbz3T, H3, M, 128) && tr(&T.tGZ3, T.gz3T, H3, M, 128) &&
+            tr(&T.tGBZ2, T.gbz2T, H2, M, 128) && tr(&T.tGZ2, T.gz2T, H2, M, 128) && tr(&T.tGBZ1, T.gbz1T, H1, M, 128) &&
+            tr(&T.tGZ1, T.gz1T, H1, M, 128) && tr(&T.tHD2, T.hd2T, H2, M, 192) && tr(&T.tH2, T.h2T, H2, M, 192) &&
+            tr(&T.tHD1, T.hd1T, H1, M, 256) && tr(&T.tH1, T.h1T, H1, M, 256) && tr(&T.tT_, T.tT, NAEV, 1, 256) &&
+            tr(&T.tAev, T.aevT, NAEV, 1, 256);
+  if (!ok) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the training maps";
+    return FNN_E_CUDA;
+  }
+  T.rows = rows;
+  T.M = M;
+  return FNN_OK;
+}
+
+template <typename InT>
+static fnn_status transpose(fnn_ctx *ctx, int rows, int F, int M, const InT *in, long long ld, long long ms,
+                            __nv_bfloat16 *outT, long long R, __nv_bfloat16 *out_rm, cudaStream_t s) {
+  dim3 grid((F + 63) / 64, (rows + 63) / 64, M);
+  FNN_KERNEL(ctx, "tr_transpose", s);
+  k_transpose_bf16<InT><<<grid, 256, 0, s>>>(rows, F, in, ld, ms, outT, R, out_rm, ld);
+  return check_launch(ctx, "tr_transpose");
+}
+
+fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
+                          const float *dLdF, const fnn_grads *g, cudaStream_t s) {
+  TcState *ts = state(ctx);
+  if (!ts->wbuf || ts->M != ctx->w.M) {
+    ctx->last_error = "bf16 weights missing";
+    return FNN_E_STATE;
+  }
+  fnn_status st;
+  if ((st = ensure_workspace(ctx, nl->pad_cap)) || (st = tc_workspace(ctx, nl->pad_cap, 1)) ||
+      (st = train_tc_workspace(ctx, ts, nl->pad_cap)))
+    return st;
+  TrainTc &T = *static_cast<TrainTc *>(ts->train);
+  const Half &H = ts->h[0];
+  const DeviceWeights &w = ctx->w;
+  const int M = w.M;
+  const long long R = (long long)T.rows;
+  const int rows = nl->pad_cap;
+  const unsigned tiles = (unsigned)(rows / ROW_TILE);
+  constexpr int B16 = tc::MODE_BF16;
+  // AEV (bf16) and its tangent along dL/dF (float -> bf16 row-major and transposed)
+  if ((st = launch_aev_forward_bf16(ctx, sys, nl, H.aev, nullptr, nl->inv, s))) return st;
+  if ((st = launch_aev_tangent(ctx, sys, nl, dLdF, T.t32, nl->inv, s))) return st;
+  if ((st = transpose<float>(ctx, rows, NAEV, 1, T.t32, NAEV, 0, T.tT, R, T.t, s))) return st;
+  if ((st = transpose<__nv_bfloat16>(ctx, rows, NAEV, 1, H.aev, NAEV, 0, T.aevT, R, nullptr, s))) return st;
+  tc::Args a{};
+  a.tile_elem = nl->tile_elem;
+  a.st = ctx->status;
+  a.M = M;
+  // ---- forward h1, h2, h3
+  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0; a.o_xm = 0; a.o_y = 2;
+  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
+  if ((st = launch<256, tc::EPI_BIAS_CELU, B16>(ctx, "tr16_l1_fwd",
+                                                {&H.mAev, &H.mW1, &H.mAev, &H.mW1, &H.eH1, &H.eH1, &H.eH1, &H.eH1}, a,
+                                                dim3(M, tiles, 1), s)))
+    return st;
+  a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1; a.o_y = 1;
+  a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
+  if ((st = launch<192, tc::EPI_BIAS_CELU, B16>(ctx, "tr16_l2_fwd",
+                                                {&H.mH1, &H.mW2, &H.mH1, &H.mW2, &H.eH2, &H.eH2, &H.eH2, &H.eH2}, a,
+                                                dim3(1, tiles, M), s)))
+    return st;
+  a.K = H2; a.N = H3;
+  a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
+  if ((st = launch<160, tc::EPI_BIAS_CELU, B16>(ctx, "tr16_l3_fwd",
+                                                {&H.mH2, &H.mW3, &H.mH2, &H.mW3, &T.eH3, &T.eH3, &T.eH3, &T.eH3}, a,
+                                                dim3(1, tiles, M), s)))
+    return st;
+  // ---- tangents hd1, hd2, hd3
+  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0; a.o_y = 2; a.x_y = 2;
+  if ((st = launch<256, tc::EPI_DCELU, B16>(ctx, "tr16_l1_tan",
+                                            {&T.mT, &H.mW1, &T.mT, &H.mW1, &T.eHD1, &T.eHD1, &H.eH1, &H.eH1}, a,
+                                            dim3(M, tiles, 1), s)))
+    return st;
+  a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1; a.o_y = 1; a.x_y = 1;
+  if ((st = launch<192, tc::EPI_DCELU, B16>(ctx, "tr16_l2_tan",
+                                            {&T.mHD1, &H.mW2, &T.mHD1, &H.mW2, &T.eHD2, &T.eHD2, &H.eH2, &H.eH2}, a,
+                                            dim3(1, tiles, M), s)))
+    return st;
+  a.K = H2; a.N = H3;
+  if ((st = launch<160, tc::EPI_DCELU, B16>(ctx, "tr16_l3_tan",
+                                            {&T.mHD2, &H.mW3, &T.mHD2, &H.mW3, &T.eHD3, &T.eHD3, &T.eH3, &T.eH3}, a,
+                                            dim3(1, tiles, M), s)))
+    return st;
+  // ---- output layer reverse (+ dw4, db4, db3)
+  {
+    FNN_KERNEL(ctx, "tr16_out_rev", s);
+    k_out_reverse_bf16<<<dim3(tiles, M), H3, 0, s>>>(M, nl->tile_elem, nl->inv, nl->atom_mol, dLdE, w.w4, T.h3,
+                                                      T.hd3, T.gbz3, T.gz3, g->w4, g->b4, g->b3);
+  }
+  // ---- layer 3 reverse: raw gb2 = gbz3 W3, g2 = gz3 W3, then the activation reverse at layer 2
+  a.K = H3; a.N = H2; a.a_by_member = 1; a.b_by_member = 1; a.o_y = 1;
+  if ((st = launch<192, tc::EPI_PLAIN, B16>(ctx, "tr16_l3_rev",
+                                            {&T.mGBZ3, &H.mW3T, &T.mGBZ3, &H.mW3T, &T.eGB2, &T.eGB2, &T.eGB2, &T.eGB2},
+                                            a, dim3(1, tiles, M), s)))
+    return st;
+  if ((st = launch<192, tc::EPI_PLAIN, B16>(ctx, "tr16_l3_rev",
+                                            {&T.mGZ3, &H.mW3T, &T.mGZ3, &H.mW3T, &T.eG2, &T.eG2, &T.eG2, &T.eG2}, a,
+                                            dim3(1, tiles, M), s)))
+    return st;
+  {
+    FNN_KERNEL(ctx, "tr16_act_rev", s);
+    k_act_reverse_bf16<<<dim3(tiles, M), H2, 0, s>>>(M, H2, nl->tile_elem, H.h2, T.hd2, T.gb2, T.g2, T.gbz2, T.gz2,
+                                                      g->b2);
+  }
+  // ---- layer 2 reverse
+  a.K = H2; a.N = H1;
+  if ((st = launch<256, tc::EPI_PLAIN, B16>(ctx, "tr16_l2_rev",
+                                            {&T.mGBZ2, &H.mW2T, &T.mGBZ2, &H.mW2T, &T.eGB1, &T.eGB1, &T.eGB1, &T.eGB1},
+                                            a, dim3(1, tiles, M), s)))
+    return st;
+  if ((st = launch<256, tc::EPI_PLAIN, B16>(ctx, "tr16_l2_rev",
+                                            {&T.mGZ2, &H.mW2T, &T.mGZ2, &H.mW2T, &T.eG1, &T.eG1, &T.eG1, &T.eG1}, a,
+                                            dim3(1, tiles, M), s)))
+    return st;
+  {
+    FNN_KERNEL(ctx, "tr16_act_rev", s);
+    k_act_reverse_bf16<<<dim3(tiles, M), H1, 0, s>>>(M, H1, nl->tile_elem, H.h1, T.hd1, T.gb1, T.g1, T.gbz1, T.gz1,
+                                                      g->b1);
+  }
+  // ---- row-contiguous transposes of the weight-gradient factors
+  struct TJ {
+    const __nv_bfloat16 *in;
+    int F;
+    __nv_bfloat16 *out;
+  } jobs[] = {{H.h1, H1, T.h1T},     {T.hd1, H1, T.hd1T},   {H.h2, H2, T.h2T},     {T.hd2, H2, T.hd2T},
+              {T.gbz3, H3, T.gbz3T}, {T.gz3, H3, T.gz3T},   {T.gbz2, H2, T.gbz2T}, {T.gz2, H2, T.gz2T},
+              {T.gbz1, H1, T.gbz1T}, {T.gz1, H1, T.gz1T}};
+  for (const TJ &j : jobs)
+    if ((st = transpose<__nv_bfloat16>(ctx, rows, j.F, M, j.in, (long long)M * j.F, j.F, j.out, R, nullptr, s)))
+      return st;
+  // ---- weight gradients: dW_l += gbz_l^T hd_{l-1} + gz_l^T h_{l-1} over each element's rows
+  tc::Args wg{};
+  wg.st = ctx->status;
+  wg.M = M;
+  wg.seg = nl->meta + META_SEG;
+  wg.kchunk = 4096;
+  wg.n_chunks = (rows + wg.kchunk - 1) / wg.kchunk;
+  constexpr int WG = tc::MODE_WG;
+  wg.K = 0;
+  wg.dW = g->W3; wg.O = H3; wg.I = H2; wg.N = H2;
+  if ((st = launch<192, tc::EPI_ATOMIC, WG>(ctx, "tr16_l3_wgrad",
+                                            {&T.tGBZ3, &T.tHD2, &T.tGZ3, &T.tH2, &T.tGBZ3, &T.tGBZ3, &T.tGBZ3, &T.tGBZ3},
+                                            wg, dim3(1, (H3 + 127) / 128, wg.n_chunks * M * NE), s)))
+    return st;
+  wg.dW = g->W2; wg.O = H2; wg.I = H1; wg.N = H1;
+  if ((st = launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l2_wgrad",
+                                            {&T.tGBZ2, &T.tHD1, &T.tGZ2, &T.tH1, &T.tGBZ2, &T.tGBZ2, &T.tGBZ2, &T.tGBZ2},
+                                            wg, dim3(1, (H2 + 127) / 128, wg.n_chunks * M * NE), s)))
+    return st;
+  wg.dW = g->W1; wg.O = H1; wg.I = NAEV; wg.N = NAEV; wg.b_shared = 1;
+  return launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l1_wgrad",
+                                         {&T.tGBZ1, &T.tT_, &T.tGZ1, &T.tAev, &T.tGBZ1, &T.tGBZ1, &T.tGBZ1, &T.tGBZ1},
+                                         wg, dim3((NAEV + 255) / 256, (H1 + 127) / 128, wg.n_chunks * M * NE), s);
 }
 
 }  // namespace fnn

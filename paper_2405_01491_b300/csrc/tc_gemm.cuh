@@ -31,9 +31,10 @@ constexpr int EPI_WARPS = 16;   // four per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 2000000000LL;  // clock64 cycles (about a second) before a wait gives up
 
-enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_F32 = 3 };
-// operand forms: bf16; the three-term bf16 split of an fp32 product; fp8 e4m3 with per-tensor scales
-enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_F8 = 2 };
+enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_F32 = 3, EPI_PLAIN = 4, EPI_ATOMIC = 5 };
+// operand forms: bf16; the three-term bf16 split of an fp32 product; fp8 e4m3 with per-tensor scales;
+// bf16 weight gradients (A and B are row-contiguous transposes, K runs over an element's rows)
+enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_F8 = 2, MODE_WG = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -190,6 +191,14 @@ struct Args {
   float a_scale, out_inv, aux_scale;
   const float *b_scale;
   int b_scale_by;
+  // weight gradients (MODE_WG, EPI_ATOMIC): tile t -> (i tile, o tile, row chunk, group g = 7 m + e);
+  // K = rows seg[e] + chunk * kchunk .. (at most kchunk, within the element's segment), both terms
+  // (A, B) then (A_lo, B_lo); the fp32 tile is added atomically into dW[g][O][I]
+  const int32_t *seg;
+  int kchunk, n_chunks;
+  int b_shared;               // B has one member for all (its z coordinate is 0)
+  float *dW;
+  int O, I;
 };
 
 // Shared memory of one CTA: the operand ring (1024-byte aligned for the 128-byte swizzle), then each
@@ -197,7 +206,7 @@ struct Args {
 // barriers.  The ring is as deep as the space allows (at most 6).
 template <int NT, int EPI, int MODE>
 struct Smem {
-  static constexpr int OB = EPI == EPI_F32 ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
+  static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   static constexpr int OBYTES = OB ? EPI_WARPS * 2 * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
@@ -233,13 +242,28 @@ __device__ __forceinline__ bool epi_any(bool pred) {
   return r != 0;
 }
 
-// tile t of the flattened grid -> (n tile, row tile, member); false when the row tile is padding
-__device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &rt, int &m, int &e) {
+// tile t of the flattened grid -> (n tile, row tile, member); false when the row tile is padding.
+// MODE_WG: (i tile, o tile, chunk, group): rt = o tile, m = member, e = element, r0 / nrows = its rows.
+template <int MODE>
+__device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &rt, int &m, int &e, int &r0,
+                                            int &nrows) {
   nt = t % p.n_ntiles;
   int rest = t / p.n_ntiles;
   rt = rest % p.n_rowtiles;
-  m = rest / p.n_rowtiles;
+  rest /= p.n_rowtiles;
+  if (MODE == MODE_WG) {
+    const int chunk = rest % p.n_chunks, g = rest / p.n_chunks;
+    m = g / NE;
+    e = g - m * NE;
+    const int s0 = p.seg[e], s1 = p.seg[e + 1];
+    r0 = s0 + chunk * p.kchunk;
+    nrows = min(p.kchunk, s1 - r0);
+    return nrows > 0;
+  }
+  m = rest;
   e = p.tile_elem[rt];
+  r0 = 0;
+  nrows = 0;
   return e >= 0;
 }
 
@@ -264,8 +288,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkb_seg = (p.K + BK - 1) / BK;
-  const int nkb = SPLIT ? 3 * nkb_seg : nkb_seg;
+  constexpr bool WG = MODE == MODE_WG;
+  const int nkb_fixed = SPLIT ? 3 * ((p.K + BK - 1) / BK) : (p.K + BK - 1) / BK;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
   volatile int *abort_flag = &S.abort_flag;
 
@@ -296,10 +320,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {  // ---- TMA producer: one continuous stage ring across this CTA's tiles
       long long g = 0, issued = 0;
       for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
-        int nt, rt, m, e;
-        if (!tile_coords(p, t, nt, rt, m, e)) continue;
+        int nt, rt, m, e, r0, nrows;
+        if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
         const int a_mid = p.a_by_member ? m : 0;
         const int b_grp = p.b_by_member ? m * NE + e : e;
+        const int nkb_seg = WG ? (nrows + BK - 1) / BK : (p.K + BK - 1) / BK;
+        const int nkb = WG ? 2 * nkb_seg : nkb_fixed;
         for (int kb = 0; kb < nkb; kb++, g++) {
           const int s = (int)(g % STAGES);
           if (g >= STAGES && !mbar_wait(&S.empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
@@ -307,9 +333,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BKB));
-          const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
-          tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
-          tma_load_3d(S.B[s], seg == 1 ? &tmB_lo : &tmB, &S.full[s], kk * BK, nt * NT, b_grp);
+          if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
+            const int term = kb / nkb_seg, x = r0 + (kb - term * nkb_seg) * BK;
+            tma_load_3d(S.A[s], term ? &tmA_lo : &tmA, &S.full[s], x, rt * BM, m);
+            tma_load_3d(S.B[s], term ? &tmB_lo : &tmB, &S.full[s], x, nt * NT, p.b_shared ? 0 : m);
+          } else {
+            const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
+            tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
+            tma_load_3d(S.B[s], seg == 1 ? &tmB_lo : &tmB, &S.full[s], kk * BK, nt * NT, b_grp);
+          }
           issued = g + 1;
         }
       }
@@ -323,8 +355,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long g = 0;
       int cnt = 0;
       for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
-        int nt, rt, m, e;
-        if (!tile_coords(p, t, nt, rt, m, e)) continue;
+        int nt, rt, m, e, r0, nrows;
+        if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
+        const int nkb = WG ? 2 * ((nrows + BK - 1) / BK) : nkb_fixed;
         const int a = cnt & 1;
         if (cnt >= 2 && !mbar_wait(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
           *abort_flag = 1;
@@ -368,21 +401,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned aux_out = 0;                   // lane 0: buffers with an aux load not yet consumed
     long long gk = 0;                       // pieces drained by this warp (buffer gk & 1)
     int cnt = 0;
+    int nt_cur = 0;                         // n tile of the tile being drained (aux y coordinate, x_y == 2)
     // lane 0: aux piece (columns col.. col + 15 of tile (rt, m)) into buffer b
     auto load_aux = [&](int b, int col, int rt, int m) {
       uint8_t *ob = wb + (size_t)b * SM::OB * SM::WBUF;
       mbar_expect_tx(&S.aux_bar[ew][b], (uint32_t)(SPLIT ? 2 * PB : PB));
-      const int y = p.x_y == 1 ? m : 0;
+      const int y = p.x_y == 1 ? m : p.x_y == 2 ? nt_cur : 0;
       tma_load_3d(ob, &tmX, &S.aux_bar[ew][b], col, y, rt * BM + q * 32);
       if (SPLIT) tma_load_3d(ob + SM::WBUF, &tmX_lo, &S.aux_bar[ew][b], col, y, rt * BM + q * 32);
       aux_out |= 1u << b;
     };
     for (int t = blockIdx.x; t < T; t += gridDim.x) {
-      int nt, rt, m, e;
-      if (!tile_coords(p, t, nt, rt, m, e)) continue;
+      int nt, rt, m, e, r0, nrows;
+      if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
       const int a = cnt & 1;
       const int n0 = nt * NT;
       const int ncols = min(NT, p.N - n0);
+      nt_cur = nt;
       // the first aux piece of the tile travels while its MMAs run
       if (EPI == EPI_DCELU && lane == 0 && 16 * part < ncols) {
         if (gk >= 2) bulk_wait_read1();
@@ -408,6 +443,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         float v[16];
         tmem_ld16(tbase + c, v);
         if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
+        if (EPI == EPI_ATOMIC) {   // weight-gradient tile: row o of dW, columns n0 + c ..
+          const int o = rt * BM + r;
+          if (o < p.O) {
+            float4 *dst = reinterpret_cast<float4 *>(p.dW + ((size_t)(m * NE + e) * p.O + o) * p.I + n0 + c);
+#pragma unroll
+            for (int j = 0; j < 4; j++) atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+          }
+          continue;
+        }
         if (EPI == EPI_F32) {
           float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
 #pragma unroll
@@ -434,7 +478,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 16; j++) v[j] *= sc;
         float f[16];
-        if (EPI == EPI_BIAS_CELU) {
+        if (EPI == EPI_PLAIN) {
+#pragma unroll
+          for (int j = 0; j < 16; j++) f[j] = v[j];
+        } else if (EPI == EPI_BIAS_CELU) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4) {
             const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c + j));

@@ -207,8 +207,8 @@ void free_train(fnn_ctx *ctx) {
 
 using namespace fnn;
 
-extern "C" fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
-                                      const float *dLdF, const fnn_grads *g, void *stream) {
+extern "C" fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec,
+                                      const double *dLdE, const float *dLdF, const fnn_grads *g, void *stream) {
   if (!ctx || !sys || !nl || !dLdE || !dLdF || !g || !g->W1 || !g->b1 || !g->W2 || !g->b2 || !g->W3 || !g->b3 ||
       !g->w4 || !g->b4)
     return FNN_E_INVALID;
@@ -221,6 +221,11 @@ extern "C" fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const
     return FNN_E_STATE;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == FNN_BF16) return tc_param_grads(ctx, sys, nl, dLdE, dLdF, g, s);
+  if (prec != FNN_FP32) {
+    ctx->last_error = "parameter gradients are built for the FP32 and BF16 forms";
+    return FNN_E_INVALID;
+  }
   if (!ctx->train) ctx->train = new TrainWs();
   TrainWs &T = *reinterpret_cast<TrainWs *>(ctx->train);
   fnn_status st;

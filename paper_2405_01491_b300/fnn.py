@@ -99,7 +99,7 @@ def _load():
         "fnn_nlist_export": (I32, [P, P, P, P, I64, P]),
         "fnn_aev": (I32, [P, P, P, P, P]),
         "fnn_aev_jvp": (I32, [P, P, P, P, P, P]),
-        "fnn_param_grads": (I32, [P, P, P, P, P, P, P]),
+        "fnn_param_grads": (I32, [P, P, P, I32, P, P, P, P]),
         "fnn_calibrate_fp8": (I32, [P, P, P, P]),
         "fnn_graph_create": (I32, [P, P, P, I32, P, P, P, I32, P, P]),
         "fnn_graph_launch": (I32, [P, P]),
@@ -315,9 +315,10 @@ def aev_jvp(ctx: Context, system: DeviceSystem, nl: NeighborList, V, out=None, s
 
 
 def param_grads(ctx: Context, system: DeviceSystem, nl: NeighborList, dLdE, dLdF, grads: dict | None = None,
-                stream=None) -> dict:
+                stream=None, precision: str = "fp32") -> dict:
     """fnn_param_grads: ADDS dL/dtheta into grads (float32 device tensors shaped like the weights; zeros
-    when None) for the loss gradients dL/dE [n_mol] float64 and dL/dF [N,3] float32; returns grads."""
+    when None) for the loss gradients dL/dE [n_mol] float64 and dL/dF [N,3] float32; returns grads.
+    precision "fp32" (SIMT) or "bf16" (tensor cores)."""
     import torch
     if grads is None:
         grads = {k: torch.zeros(v, dtype=torch.float32, device="cuda")
@@ -326,8 +327,8 @@ def param_grads(ctx: Context, system: DeviceSystem, nl: NeighborList, dLdE, dLdF
     dLdF = dLdF.to(torch.float32).contiguous()
     cg = CGrads(*(grads[k].data_ptr() for k in PARAM_NAMES))
     cs = system.c()
-    ctx._check(lib.fnn_param_grads(ctx.h, ctypes.byref(cs), nl.h, _ptr(dLdE), _ptr(dLdF), ctypes.byref(cg),
-                                   _stream(stream)), "fnn_param_grads")
+    ctx._check(lib.fnn_param_grads(ctx.h, ctypes.byref(cs), nl.h, PRECISION[precision], _ptr(dLdE), _ptr(dLdF),
+                                   ctypes.byref(cg), _stream(stream)), "fnn_param_grads")
     return grads
 
 
@@ -343,10 +344,10 @@ def _function():
 
     class EnergyForces(torch.autograd.Function):
         @staticmethod
-        def forward(fctx, ctx, system, nl, *params):
+        def forward(fctx, ctx, system, nl, precision, *params):
             _load_params(ctx, params)
-            E, F, _ = energy_forces(ctx, system, nl, "fp32", virial=False)
-            fctx.ctx, fctx.system, fctx.nl = ctx, system, nl
+            E, F, _ = energy_forces(ctx, system, nl, precision, virial=False)
+            fctx.ctx, fctx.system, fctx.nl, fctx.precision = ctx, system, nl, precision
             fctx.stamp = ctx.param_stamp
             return E, F
 
@@ -360,8 +361,8 @@ def _function():
                 gE = torch.zeros(system.n_mol, dtype=torch.float64, device="cuda")
             if gF is None:
                 gF = torch.zeros((system.n_atoms, 3), dtype=torch.float32, device="cuda")
-            g = param_grads(ctx, system, fctx.nl, gE, gF)
-            return (None, None, None) + tuple(g[k] for k in PARAM_NAMES)
+            g = param_grads(ctx, system, fctx.nl, gE, gF, precision=fctx.precision)
+            return (None, None, None, None) + tuple(g[k] for k in PARAM_NAMES)
 
     _FUNCTION = EnergyForces
     return _FUNCTION
@@ -377,11 +378,12 @@ def _load_params(ctx: Context, params):
     ctx.param_stamp = stamp
 
 
-def energy_forces_autograd(ctx: Context, system: DeviceSystem, nl: NeighborList, params):
+def energy_forces_autograd(ctx: Context, system: DeviceSystem, nl: NeighborList, params, precision: str = "fp32"):
     """(E [n_mol] float64, F [N,3] float32) as differentiable functions of params (the eight weight
     tensors in PARAM_NAMES order, float32): a loss built from E and F back-propagates into the
-    parameters through fnn_param_grads (section IV).  FP32 networks."""
-    return _function().apply(ctx, system, nl, *params)
+    parameters through fnn_param_grads (section IV).  precision "fp32" or "bf16" (networks on the
+    tensor cores for both the forward evaluation and the gradients)."""
+    return _function().apply(ctx, system, nl, precision, *params)
 
 
 def calibrate_fp8(ctx: Context, system: DeviceSystem, nl: NeighborList, stream=None):
