@@ -56,9 +56,14 @@ struct NbrStage {
   float adfc[ANG_CAP];           // its derivative (adjoint)
 };
 constexpr int GSTRIDE = 36;      // padded row of one element pair's 32 angular slots (distinct banks per pair)
+constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
 struct FwdStage {
   NbrStage nb;
-  float stage[32][13];           // per-triplet factors: 4 section powers, 8 Gaussians x switches, pair index
+  // per-triplet factors of one batch, triplet innermost so a consumer lane reads four at once:
+  // 4 section powers, 8 Gaussians x switches, and the element-pair block (-1 past the end)
+  alignas(16) float sf[NSZ][SROW];
+  alignas(16) float sg[NSA][SROW];
+  alignas(16) int sp[SROW];
   float acc[NPAIR * 32];         // angular accumulators of the atom
 };
 struct AdjStage {
@@ -281,27 +286,50 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
 #pragma unroll
           for (int s = 0; s < NSZ; s++) {
             const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
-            W.stage[lane][s] = exp2f_fast(P.zeta * __log2f(base_s));
+            W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
           }
           const float rbar = 0.5f * (d1.w + d2.w);
           const float fcc = 2.f * S.afc[ja] * S.afc[ka];
 #pragma unroll
           for (int m = 0; m < NSA; m++) {
             const float dr = rbar - P.shf_a[m];
-            W.stage[lane][4 + m] = __expf(-P.eta_a * dr * dr) * fcc;
+            W.sg[m][lane] = __expf(-P.eta_a * dr * dr) * fcc;
           }
-          W.stage[lane][12] = __int_as_float(pair_of(S.ae[ja], S.ae[ka]));   // e_j <= e_k: sorted list
+          W.sp[lane] = pair_of(S.ae[ja], S.ae[ka]);   // e_j <= e_k: sorted list
+        } else {
+#pragma unroll
+          for (int s = 0; s < NSZ; s++) W.sf[s][lane] = 0.f;
+#pragma unroll
+          for (int m = 0; m < NSA; m++) W.sg[m][lane] = 0.f;
+          W.sp[lane] = -1;
         }
         __syncwarp();
         const int nt = min(32, T - base);
-        for (int q = 0; q < nt; q++) {
-          const int p = __float_as_int(W.stage[q][12]);
-          if (p != run_p) {
-            if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
-            racc = 0.f;
-            run_p = p;
+        const float *fr = W.sf[s_my], *gr = W.sg[m_my];
+        // four triplets per step; four of the running element pair are four FMAs
+        for (int q = 0; q < nt; q += 4) {
+          const int4 pq = *reinterpret_cast<const int4 *>(&W.sp[q]);
+          const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
+          const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
+          if ((pq.x == run_p) & (pq.y == run_p) & (pq.z == run_p) & (pq.w == run_p)) {
+            racc = fmaf(fv.x, gv.x, racc);
+            racc = fmaf(fv.y, gv.y, racc);
+            racc = fmaf(fv.z, gv.z, racc);
+            racc = fmaf(fv.w, gv.w, racc);
+          } else {
+            const int pv[4] = {pq.x, pq.y, pq.z, pq.w};
+            const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, ga[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+              if (pv[u] < 0) break;   // past the last triplet
+              if (pv[u] != run_p) {
+                if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+                racc = 0.f;
+                run_p = pv[u];
+              }
+              racc = fmaf(fa[u], ga[u], racc);
+            }
           }
-          racc += W.stage[q][s_my] * W.stage[q][4 + m_my];
         }
         __syncwarp();
       }
