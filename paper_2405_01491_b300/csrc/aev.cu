@@ -69,8 +69,6 @@ struct FwdStage {
 struct AdjStage {
   NbrStage nb;
   float gacc[RAD_CAP][3];        // dE/dd per radial entry
-  float grad[NRAD];              // radial part of the incoming dE/dAEV row
-  float gang[NPAIR * GSTRIDE];   // angular part, one padded row per element pair
 };
 
 struct StageArgs {
@@ -357,7 +355,9 @@ struct AevAdjArgs {
   DevStatus *st;
 };
 
-__global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
+// The dE/dAEV row is read through the L1 cache where it is used (4 KB per atom, re-read by the warp's
+// lanes): staging it in shared memory would cap the number of resident warps.
+__global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_adjoint(AevAdjArgs A) {
   __shared__ AdjStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   AdjStage &W = smem[wl];
@@ -375,8 +375,6 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
     int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
     if (!stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st)) continue;
     const float *G = A.gaev + (size_t)row * NAEV;
-    for (int c = lane; c < NRAD; c += 32) W.grad[c] = G[c];
-    for (int p = 0; p < NPAIR; p++) W.gang[p * GSTRIDE + lane] = G[NRAD + p * 32 + lane];
     __syncwarp();
     // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
     int nrad = off_r[NE];
@@ -391,7 +389,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
       for (int k = 0; k < NSR; k++) {
         float dr = r - P.shf_r[k];
         float gk = __expf(-P.eta_r * dr * dr);
-        dEdr += W.grad[e * NSR + k] * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
+        dEdr += __ldg(G + e * NSR + k) * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
       }
       float f = dEdr * rcp_fast(r);
       W.gacc[t][0] = f * d.x;
@@ -412,7 +410,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
           tri_index(t, n, diag, ka);   // diagonal diag + 1 has as many pairs as row diag of the triangle
           const int ja = ka - diag - 1;
           const int p = pair_of(S.ae[ja], S.ae[ka]);
-          const float *Gp = &W.gang[p * GSTRIDE];
+          const float *Gp = G + NRAD + p * 32;
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
           const float r1 = d1.w, r2 = d2.w;
@@ -436,7 +434,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_adjoint(AevAdjArgs A) {
             const float dr = rbar - P.shf_a[m];
             const float gm = __expf(-P.eta_a * dr * dr);
             const float dgm = -2.f * P.eta_a * dr * gm;
-            const float4 g4 = *reinterpret_cast<const float4 *>(Gp + m * NSZ);
+            const float4 g4 = __ldg(reinterpret_cast<const float4 *>(Gp + m * NSZ));
             H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
             Hd[0] += g4.x * dgm; Hd[1] += g4.y * dgm; Hd[2] += g4.z * dgm; Hd[3] += g4.w * dgm;
           }
