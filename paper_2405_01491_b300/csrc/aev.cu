@@ -44,21 +44,24 @@ __device__ __forceinline__ float sqrt_fast(float x) {
   return y;
 }
 
-// per-warp staging of one centre atom's neighbours, bucketed by element
-struct NbrStage {
+// per-warp staging of one centre atom's neighbours, bucketed by element; the neighbour indices and the
+// switch derivatives only where the kernel differentiates (FULL)
+template <bool FULL>
+struct NbrStageT {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
   float rfc[RAD_CAP];            // radial switch fc(r; rc_rad)
-  int rj[RAD_CAP];               // neighbour atom
+  int rj[FULL ? RAD_CAP : 1];    // neighbour atom
   unsigned char re[RAD_CAP];     // neighbour element
   unsigned char aidx[ANG_CAP];   // angular entry -> radial entry
   unsigned char ae[ANG_CAP];     // angular entry element
   float afc[ANG_CAP];            // angular switch fc(r; rc_ang)
-  float adfc[ANG_CAP];           // its derivative (adjoint)
+  float adfc[FULL ? ANG_CAP : 1];  // its derivative
 };
+using NbrStage = NbrStageT<true>;
 constexpr int GSTRIDE = 36;      // padded row of one element pair's 32 angular slots (distinct banks per pair)
 constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
 struct FwdStage {
-  NbrStage nb;
+  NbrStageT<false> nb;
   // per-triplet factors of one batch, triplet innermost so a consumer lane reads four at once:
   // 4 section powers, 8 Gaussians x switches, and the element-pair block (-1 past the end)
   alignas(16) float sf[NSZ][SROW];
@@ -84,7 +87,8 @@ struct StageArgs {
 // Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
 // FNN_E_CAPACITY) when a list overflows.  On return cnt_*/off_* hold per-element counts and
 // segment starts (warp-uniform).
-__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStage &S, int cnt_r[NE],
+template <bool FULL>
+__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStageT<FULL> &S, int cnt_r[NE],
                                 int off_r[NE + 1], int cnt_a[NE], int off_a[NE + 1], bool want_dfc,
                                 DevStatus *st) {
   int lane = threadIdx.x & 31;
@@ -164,14 +168,14 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
     if (pr >= 0) {
       S.rd[pr] = make_float4(dx, dy, dz, r);
       S.rfc[pr] = 0.5f * cospif(r * P.inv_rc_rad) + 0.5f;
-      S.rj[pr] = j;
+      if constexpr (FULL) S.rj[pr] = j;
       S.re[pr] = (unsigned char)e;
     }
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
       S.ae[pa] = (unsigned char)e;
       S.afc[pa] = 0.5f * cospif(r * P.inv_rc_ang) + 0.5f;
-      if (want_dfc) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
+      if constexpr (FULL) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
     }
   }
   __syncwarp();
@@ -222,11 +226,11 @@ __device__ __forceinline__ void store_lo(__nv_bfloat16 *lo, size_t c, float v) {
 }
 
 template <typename OutT>
-__global__ void __launch_bounds__(AEV_WARPS * 32) k_aev_forward(AevFwdArgs A) {
+__global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A) {
   __shared__ FwdStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   FwdStage &W = smem[wl];
-  NbrStage &S = W.nb;
+  NbrStageT<false> &S = W.nb;
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
