@@ -76,10 +76,25 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
     return None
 
 
-def source_digest() -> str:
-    h = hashlib.sha256()
+KERNEL_SOURCES = [  # kernel-name prefix -> the files that define it (with the shared internal header)
+    (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "mlp_tc.cu")),
+    (("f32_", "atom_energy", "energy_reduce"), ("mlp_simt.cu",)),
+    (("aev_",), ("aev.cu",)),
+    (("pairs_", "scan_", "mol_setup", "check_", "bin", "scatter", "sort_cells", "elem_"), ("nlist.cu",)),
+]
+
+
+def source_digest(kernel: str | None = None) -> str:
+    """Digest of the sources a kernel is built from (all of csrc when kernel is None or unknown)."""
     d = os.path.join(ROOT, "paper_2405_01491_b300", "csrc")
-    for f in sorted(os.listdir(d)):
+    files = sorted(os.listdir(d))
+    if kernel:
+        for prefixes, srcs in KERNEL_SOURCES:
+            if kernel.startswith(prefixes):
+                files = ["fnn_internal.cuh", *srcs]
+                break
+    h = hashlib.sha256()
+    for f in files:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -598,7 +613,7 @@ def main():
 
     head = results[args.precision]
     kernels, roof = kernel_table(head["prof"], args.steps, s.n_atoms, nnz, M, args.precision, pk)
-    roof["traffic"] = recorded_traffic(roof["kernel"], source_digest())
+    roof["traffic"] = recorded_traffic(roof["kernel"], source_digest(roof["kernel"]))
     form_report = {}
     for form, r in results.items():
         ks, rf = kernel_table(r["prof"], args.steps, s.n_atoms, nnz, M, form, pk)
