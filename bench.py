@@ -80,7 +80,8 @@ KERNEL_SOURCES = [  # kernel-name prefix -> the files that define it (with the s
     (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "mlp_tc.cu")),
     (("f32_", "atom_energy", "energy_reduce"), ("mlp_simt.cu",)),
     (("aev_",), ("aev.cu",)),
-    (("pairs_", "scan_", "mol_setup", "check_", "bin", "scatter", "sort_cells", "elem_"), ("nlist.cu",)),
+    (("pairs_", "scan_", "mol_setup", "atom_setup", "mol_grid", "check_", "bin", "scatter", "sort_cells", "elem_"),
+     ("nlist.cu",)),
 ]
 
 

@@ -178,6 +178,7 @@ struct fnn_nlist {
   char4 *stage_shift = nullptr; // [N][128]
   // per structure
   fnn::MolGrid *grid = nullptr; // [n_mol]
+  float *bbox = nullptr;        // [n_mol][6] bounding box (min xyz, max xyz)
   int32_t *mol_cells = nullptr; // [n_mol + 1]
   // per cell
   int32_t *cell_count = nullptr;// [cells + 1]

@@ -3,7 +3,9 @@
 //
 // Pipeline (one stream, no host synchronisation):
 //   k_check_cover   offsets start at 0, end at N, never decrease
-//   k_mol_setup     per structure: validate species / cell, bounding box, cell-grid geometry
+//   k_atom_setup    per atom: structure (binary search of the offsets), species, bounding boxes
+//   k_mol_grid      per structure: validate cell, cell-grid geometry, predicate band
+//                   (the allocation-free entry point keeps k_mol_setup: a block per structure)
 //   scan            structure cell counts -> first global cell of each structure
 //   k_bin           per atom: cell index, histogram (atomics)
 //   scan            cell counts -> cell starts (counting sort)
@@ -97,11 +99,40 @@ __global__ void k_scan_add(int32_t *data, int64_t n, const int32_t *tile_sums) {
     if (base + k < n) data[base + k] += add;
 }
 
+// one block for a short array: chunks of SCAN_TILE with a running carry
+__global__ void k_scan_small(int32_t *data, int64_t n, int32_t *total_dev) {
+  int carry = 0;
+  for (int64_t c = 0; c < n; c += SCAN_TILE) {
+    const int64_t base = c + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+      v[k] = base + k < n ? data[base + k] : 0;
+      sum += v[k];
+    }
+    int tot;
+    int ex = block_excl_scan<SCAN_NT>(sum, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+      if (base + k < n) data[base + k] = ex;
+      ex += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+}
+
 int64_t scan_tmp_needed(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
                           int64_t tmp_len, cudaStream_t s) {
   if (n <= 0) return FNN_OK;
+  if (n <= 2 * SCAN_TILE) {   // one launch for short arrays (structure and small cell counts)
+    FNN_KERNEL(ctx, "scan_small", s);
+    k_scan_small<<<1, SCAN_NT, 0, s>>>(data, n, total_dev);
+    return check_launch(ctx, "exclusive_scan");
+  }
   int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nt > tmp_len) {
     ctx->last_error = "scan scratch too small";
@@ -124,13 +155,173 @@ fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total
 
 // ------------------------------------------------------------------------------------- structures
 // offsets must start at 0, end at N and never decrease: otherwise some atom has no structure
-__global__ void k_check_cover(fnn_system sys, DevStatus *st) {
+// (also resets the per-structure bounding boxes, when given, to empty)
+__global__ void k_check_cover(fnn_system sys, DevStatus *st, float *bbox) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= sys.n_mol; m += gridDim.x * blockDim.x) {
     int a = sys.mol_offsets[m];
     bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
     if (m == sys.n_mol) ok = ok && a == sys.n_atoms;
     if (!ok) post_status(st, FNN_E_INVALID, m);
+    if (bbox && m < sys.n_mol)
+      for (int a3 = 0; a3 < 3; a3++) {
+        bbox[6 * (size_t)m + a3] = __int_as_float(0x7f800000);        // +inf
+        bbox[6 * (size_t)m + 3 + a3] = __int_as_float((int)0xff800000);   // -inf
+      }
   }
+}
+
+// float min / max through integer atomics (valid for finite values and the +-inf initial bounds)
+__device__ __forceinline__ void atomic_fmin(float *a, float v) {
+  if (v >= 0.f)
+    atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
+  else
+    atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_fmax(float *a, float v) {
+  if (v >= 0.f)
+    atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+  else
+    atomicMin(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+
+// Per atom, all structures at once: its structure (binary search of the offsets), element, checks, and
+// the structure's bounding box (a warp whose atoms share one structure reduces before its atomics).
+__global__ void k_atom_setup(fnn_system sys, int32_t *atom_mol, uint8_t *elem, float *bbox, DevStatus *st) {
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  const int lane = threadIdx.x & 31;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < sys.n_atoms; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    int m = -1;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < sys.n_atoms) {
+      int lo = 0, hi = sys.n_mol;   // last m with offsets[m] <= i
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys.mol_offsets[mid] <= i) lo = mid; else hi = mid;
+      }
+      if (sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
+      if (m >= 0) {
+        atom_mol[i] = m;
+        int e = element_of(sys.Z[i]);
+        if (e < 0) {
+          post_status(st, FNN_E_SPECIES, i);
+          e = 0;
+        }
+        elem[i] = (uint8_t)e;
+        p = pos[i];
+        if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) post_status(st, FNN_E_NONFINITE, i);
+      }
+    }
+    const int m0 = __shfl_sync(FULL, m, 0);
+    if (__all_sync(FULL, m == m0)) {
+      if (m0 < 0) continue;
+      float v[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          v[a] = fminf(v[a], __shfl_xor_sync(FULL, v[a], o));
+          v[3 + a] = fmaxf(v[3 + a], __shfl_xor_sync(FULL, v[3 + a], o));
+        }
+      if (lane == 0)
+        for (int a = 0; a < 3; a++) {
+          atomic_fmin(&bbox[6 * (size_t)m0 + a], v[a]);
+          atomic_fmax(&bbox[6 * (size_t)m0 + 3 + a], v[3 + a]);
+        }
+    } else if (m >= 0) {
+      atomic_fmin(&bbox[6 * (size_t)m], p.x);
+      atomic_fmin(&bbox[6 * (size_t)m + 1], p.y);
+      atomic_fmin(&bbox[6 * (size_t)m + 2], p.z);
+      atomic_fmax(&bbox[6 * (size_t)m + 3], p.x);
+      atomic_fmax(&bbox[6 * (size_t)m + 4], p.y);
+      atomic_fmax(&bbox[6 * (size_t)m + 5], p.z);
+    }
+  }
+}
+
+__device__ MolGrid make_grid(const fnn_system &sys, int m, int n, int pbc, float bb[6], double R, DevStatus *st,
+                             int *cells);
+
+// Per structure: offsets check, then the grid from its bounding box
+__global__ void k_mol_grid(fnn_system sys, const float *bbox, MolGrid *grid, int32_t *mol_cells, double R,
+                           DevStatus *st) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < sys.n_mol; m += gridDim.x * blockDim.x) {
+    const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    if (a0 < 0 || a1 < a0 || a1 > sys.n_atoms) {
+      post_status(st, FNN_E_INVALID, m);
+      grid[m] = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
+      mol_cells[m] = 1;
+      continue;
+    }
+    const int pbc = sys.pbc ? (sys.pbc[m] != 0) : 0;
+    float bb[6];
+    for (int a = 0; a < 6; a++) bb[a] = bbox[6 * (size_t)m + a];
+    int cells;
+    grid[m] = make_grid(sys, m, a1 - a0, pbc, bb, R, st, &cells);
+    mol_cells[m] = cells;
+  }
+}
+
+// Cell grid, image data and predicate band of structure m with n atoms and bounding box bb (min xyz, max
+// xyz); posts FNN_E_CELL for a cell the minimum image cannot serve.
+__device__ MolGrid make_grid(const fnn_system &sys, int m, int n, int pbc, float bb[6], double R, DevStatus *st,
+                             int *cells) {
+  MolGrid g{};
+  double edge = R * (1.0 + 1e-4);   // cells at least this wide: fp32 binning error stays far below the margin
+  double ext[3];
+  g.pbc = pbc;
+  if (pbc) {
+    const float *c = sys.cell + 9 * (size_t)m;
+    bool ortho = c[1] == 0.f && c[2] == 0.f && c[3] == 0.f && c[5] == 0.f && c[6] == 0.f && c[7] == 0.f;
+    g.Lx = c[0]; g.Ly = c[4]; g.Lz = c[8];
+    if (!ortho || !((double)g.Lx > 2 * R) || !((double)g.Ly > 2 * R) || !((double)g.Lz > 2 * R)) {
+      post_status(st, FNN_E_CELL, m);
+      g.pbc = 0;  // keep the traversal well-defined; the result is flagged invalid
+      g.Lx = g.Ly = g.Lz = 0.f;
+    }
+    ext[0] = g.Lx; ext[1] = g.Ly; ext[2] = g.Lz;
+    g.ox = g.oy = g.oz = 0.f;
+  }
+  if (!g.pbc) {
+    if (n == 0) {
+      for (int a = 0; a < 6; a++) bb[a] = 0.f;
+    }
+    g.ox = bb[0]; g.oy = bb[1]; g.oz = bb[2];
+    for (int a = 0; a < 3; a++) ext[a] = (double)bb[3 + a] - (double)bb[a];
+  }
+  int d[3];
+  for (int a = 0; a < 3; a++) {
+    double q = ext[a] / edge;
+    d[a] = (q >= 1.0 && q < 1e6) ? (int)floor(q) : 1;
+  }
+  long long limit = n > 0 ? 2LL * n : 1;
+  while ((long long)d[0] * d[1] * d[2] > limit) {
+    int a = (d[0] >= d[1] && d[0] >= d[2]) ? 0 : (d[1] >= d[2] ? 1 : 2);
+    d[a] = d[a] * 3 / 4;
+    if (d[a] < 1) d[a] = 1;
+  }
+  g.dx = d[0]; g.dy = d[1]; g.dz = d[2];
+  // error band of the float32 predicate, from the largest magnitude S any pair of this structure can
+  // present (coordinates, and image offsets |n L| <= 2 max|x| + L/2): twice the bound on the float32
+  // error of d2 near R^2, 2 sqrt(3) e R + 3 e^2 + 4 u R^2 with e = 4 u S
+  {
+    double mabs = 0.0;
+    for (int a = 0; a < 3; a++) mabs = fmax(mabs, fmax(fabs((double)bb[a]), fabs((double)bb[3 + a])));
+    double Lmax = g.pbc ? fmax(fmax((double)g.Lx, (double)g.Ly), (double)g.Lz) : 0.0;
+    double S = g.pbc ? 2.0 * mabs + 0.5 * Lmax + Lmax : mabs;
+    const double u = 5.9604644775390625e-8;
+    double e = 4.0 * u * S;
+    double tau = 2.0 * (3.4641016151377544 * e * R * 1.01 + 3.0 * e * e + 4.0 * u * R * R) + 1e-30;
+    g.tau = (float)(tau * (1.0 + 1e-6));
+    g.iLx = g.pbc ? (float)(1.0 / (double)g.Lx) : 0.f;
+    g.iLy = g.pbc ? (float)(1.0 / (double)g.Ly) : 0.f;
+    g.iLz = g.pbc ? (float)(1.0 / (double)g.Lz) : 0.f;
+  }
+  g.ix = ext[0] > 0 ? (float)(d[0] / ext[0]) : 0.f;
+  g.iy = ext[1] > 0 ? (float)(d[1] / ext[1]) : 0.f;
+  g.iz = ext[2] > 0 ? (float)(d[2] / ext[2]) : 0.f;
+  *cells = d[0] * d[1] * d[2];
+  return g;
 }
 
 constexpr int SETUP_NT = 512;
@@ -201,64 +392,12 @@ __global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid 
           red[a][0] = fminf(red[a][0], red[a][k]);
           red[3 + a][0] = fmaxf(red[3 + a][0], red[3 + a][k]);
         }
-      MolGrid g{};
-      int n = a1 - a0;
-      double edge = R * (1.0 + 1e-4);   // cells at least this wide: fp32 binning error stays far below the margin
-      double ext[3];
-      g.pbc = pbc;
-      if (pbc) {
-        const float *c = sys.cell + 9 * (size_t)m;
-        bool ortho = c[1] == 0.f && c[2] == 0.f && c[3] == 0.f && c[5] == 0.f && c[6] == 0.f && c[7] == 0.f;
-        g.Lx = c[0]; g.Ly = c[4]; g.Lz = c[8];
-        if (!ortho || !((double)g.Lx > 2 * R) || !((double)g.Ly > 2 * R) || !((double)g.Lz > 2 * R)) {
-          post_status(st, FNN_E_CELL, m);
-          g.pbc = 0;  // keep the traversal well-defined; the result is flagged invalid
-          g.Lx = g.Ly = g.Lz = 0.f;
-        }
-        ext[0] = g.Lx; ext[1] = g.Ly; ext[2] = g.Lz;
-        g.ox = g.oy = g.oz = 0.f;
-      }
-      if (!g.pbc) {
-        if (n == 0) {
-          red[0][0] = red[1][0] = red[2][0] = 0.f;
-          red[3][0] = red[4][0] = red[5][0] = 0.f;
-        }
-        g.ox = red[0][0]; g.oy = red[1][0]; g.oz = red[2][0];
-        for (int a = 0; a < 3; a++) ext[a] = (double)red[3 + a][0] - (double)red[a][0];
-      }
-      int d[3];
-      for (int a = 0; a < 3; a++) {
-        double q = ext[a] / edge;
-        d[a] = (q >= 1.0 && q < 1e6) ? (int)floor(q) : 1;
-      }
-      long long limit = n > 0 ? 2LL * n : 1;
-      while ((long long)d[0] * d[1] * d[2] > limit) {
-        int a = (d[0] >= d[1] && d[0] >= d[2]) ? 0 : (d[1] >= d[2] ? 1 : 2);
-        d[a] = d[a] * 3 / 4;
-        if (d[a] < 1) d[a] = 1;
-      }
-      g.dx = d[0]; g.dy = d[1]; g.dz = d[2];
-      // error band of the float32 predicate, from the largest magnitude S any pair of this structure can
-      // present (coordinates, and image offsets |n L| <= 2 max|x| + L/2): twice the bound on the float32
-      // error of d2 near R^2, 2 sqrt(3) e R + 3 e^2 + 4 u R^2 with e = 4 u S
-      {
-        double mabs = 0.0;
-        for (int a = 0; a < 3; a++) mabs = fmax(mabs, fmax(fabs((double)red[a][0]), fabs((double)red[3 + a][0])));
-        double Lmax = g.pbc ? fmax(fmax((double)g.Lx, (double)g.Ly), (double)g.Lz) : 0.0;
-        double S = g.pbc ? 2.0 * mabs + 0.5 * Lmax + Lmax : mabs;
-        const double u = 5.9604644775390625e-8;
-        double e = 4.0 * u * S;
-        double tau = 2.0 * (3.4641016151377544 * e * R * 1.01 + 3.0 * e * e + 4.0 * u * R * R) + 1e-30;
-        g.tau = (float)(tau * (1.0 + 1e-6));
-        g.iLx = g.pbc ? (float)(1.0 / (double)g.Lx) : 0.f;
-        g.iLy = g.pbc ? (float)(1.0 / (double)g.Ly) : 0.f;
-        g.iLz = g.pbc ? (float)(1.0 / (double)g.Lz) : 0.f;
-      }
-      g.ix = ext[0] > 0 ? (float)(d[0] / ext[0]) : 0.f;
-      g.iy = ext[1] > 0 ? (float)(d[1] / ext[1]) : 0.f;
-      g.iz = ext[2] > 0 ? (float)(d[2] / ext[2]) : 0.f;
+      float bb[6];
+      for (int a = 0; a < 6; a++) bb[a] = red[a][0];
+      int cells;
+      const MolGrid g = make_grid(sys, m, a1 - a0, pbc, bb, R, st, &cells);
       grid[m] = g;
-      mol_cells[m] = d[0] * d[1] * d[2];
+      mol_cells[m] = cells;
     }
     __syncthreads();
   }
@@ -612,7 +751,9 @@ static fnn_status reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t
   }
   if (n_mol > nl->mol_cap || !nl->grid) {
     int32_t nm = n_mol > nl->mol_cap ? n_mol : nl->mol_cap;
-    if ((st = grow(ctx, &nl->grid, nm)) || (st = grow(ctx, &nl->mol_cells, (size_t)nm + 1))) return st;
+    if ((st = grow(ctx, &nl->grid, nm)) || (st = grow(ctx, &nl->mol_cells, (size_t)nm + 1)) ||
+        (st = grow(ctx, &nl->bbox, (size_t)6 * nm)))
+      return st;
     nl->mol_cap = nm;
   }
   int32_t cells = 2 * nl->atom_cap + nl->mol_cap + 1;
@@ -666,7 +807,7 @@ extern "C" fnn_status fnn_nlist_destroy(fnn_nlist *nl) {
   void *ptrs[] = {nl->row_ptr, nl->nbr, nl->shift, nl->atom_mol, nl->elem, nl->cell_of, nl->cell_tmp,
                   nl->cell_atoms, nl->counts, nl->grid, nl->mol_cells, nl->cell_count, nl->cell_start,
                   nl->perm, nl->inv, nl->tile_elem, nl->blk_count, nl->meta, nl->scan_tmp, nl->stage_nbr,
-                  nl->stage_shift};
+                  nl->stage_shift, nl->bbox};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete nl;
@@ -725,13 +866,17 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   int cover_blocks = (NM + 256) / 256 < 256 ? (NM + 256) / 256 : 256;
   {
     FNN_KERNEL(ctx, "check_cover", s);
-    k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status);
+    k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status, nl->bbox);
   }
-  int setup_blocks = NM < 4 * ctx->num_sms ? NM : 4 * ctx->num_sms;
+  if (N > 0) {
+    int ab = (N + 255) / 256;
+    if (ab > 8 * ctx->num_sms) ab = 8 * ctx->num_sms;
+    FNN_KERNEL(ctx, "atom_setup", s);
+    k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, ctx->status);
+  }
   {
-    FNN_KERNEL(ctx, "mol_setup", s);
-    k_mol_setup<<<setup_blocks, SETUP_NT, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->elem, R,
-                                                  ctx->status);
+    FNN_KERNEL(ctx, "mol_grid", s);
+    k_mol_grid<<<(NM + 127) / 128, 128, 0, s>>>(*sys, nl->bbox, nl->grid, nl->mol_cells, R, ctx->status);
   }
   if ((st = exclusive_scan(ctx, nl->mol_cells, NM + 1, nl->meta + META_CELLS, nl->scan_tmp, nl->scan_tmp_len, s)))
     return st;
@@ -944,7 +1089,7 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     FNN_STATIC_TRY(cudaMemsetAsync(S->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
     FNN_STATIC_TRY(cudaMemsetAsync(S->elem, 0, (size_t)N, s));
   }
-  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status);
+  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status, nullptr);
   k_mol_setup<<<NM, SETUP_NT, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->elem, R, &S->status);
   FNN_STATIC_TRY(scan_in_place(S->mol_cells, NM + 1, S->meta + META_CELLS, S->scan_tmp, s));
   FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
