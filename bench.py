@@ -115,6 +115,45 @@ def recorded_traffic(kernel: str, digest: str):
     return None
 
 
+class Ranks:
+    """Replicas on one node, one process per GPU (torchrun sets RANK / WORLD_SIZE / MASTER_*): a barrier
+    and the max over ranks.  A single process when WORLD_SIZE is unset.  backend "nccl" on GPUs, "gloo"
+    for the CPU tests of this logic."""
+
+    def __init__(self, backend: str = "nccl", device: str = "cuda"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        if self.dist:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_per_rank: float, seconds_per_rank: float, ranks: Ranks) -> float:
+    """Units of every rank over the slowest rank's time (weak scaling: each rank holds its own replica)."""
+    return ranks.world * units_per_rank / ranks.max(seconds_per_rank)
+
+
 class _NvmlLib:
     """The driver's NVML through ctypes (read-only queries: SM clock, its maximum, event reasons, power)."""
 
@@ -247,7 +286,7 @@ def oracle_full(M: int = 8, min_seconds: float = 10.0, max_reps: int = 3):
     s = synth.mix23558()
     w = synth.xavier_weights(M)
     times, res = [], None
-    while len(times) < max_reps and sum(times) < min_seconds:
+    while not times or (len(times) < max_reps and sum(times) < min_seconds):
         t = time.perf_counter()
         res = oracle.energy_forces(s, w)
         times.append(time.perf_counter() - t)
@@ -257,6 +296,14 @@ def oracle_full(M: int = 8, min_seconds: float = 10.0, max_reps: int = 3):
              "sample": f"{len(times)} full energy+force evaluation(s) of the same 23,558-atom box, M={M}, float64 "
                        f"(all-pairs neighbour search), {dt:.1f} s each"}
     return entry, res
+
+
+def arm_config(precision: str, list_entries, world: int = 1) -> dict:
+    """The workload description both arms print."""
+    return {"workload": WORKLOAD, "n_atoms": 23558, "members": 8, "precision": precision,
+            "precision_note": PRECISION_NOTE.get(precision, ""), "list_entries": list_entries,
+            "parallelism": f"replicas x{world}",
+            "l2": "flushed before every timed step (256 MB write outside the step's CUDA events)"}
 
 
 def run_reference(args):
@@ -274,7 +321,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "config": arm_config("float64 oracle (all-pairs neighbour search), host cores", None),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": entry["cores"], "kind": "oracle",
                              "sample": "each step: one float64 energy+force evaluation of the whole 23,558-atom box"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -405,6 +452,45 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1, precision="bf16"):
             "loss": float(L.detach()), "gpu_launches_per_step": launches / steps,
             "kernel_share": {k: round(v[0] / total, 3) for k, v in top},
             "note": "forward (E, F) + loss + parameter gradients; the optimizer update is not timed"}
+
+
+def latency_bench(fnn, torch, synth, reps: int = 200):
+    """The 24-atom gas-phase cluster, one member: microseconds per energy+force evaluation (list rebuild
+    included) as CUDA-graph replays back to back and as eager calls, for the FP32 and FP32X3 forms."""
+    s = synth.gas24()
+    out = {"workload": "gas24: 24-atom gas-phase cluster (10 H, 8 C, 3 N, 3 O), 6 A cube, seed 1", "members": 1}
+    ctx = fnn.Context(1)
+    fnn.load_weights(ctx, synth.xavier_weights(1))
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    for form in ("fp32", "fp32x3"):
+        g = fnn.Graph(ctx, ds, nl, form)
+        st = g.stream
+        with torch.cuda.stream(st):
+            for _ in range(10):
+                g.launch()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                g.launch()
+            b.record(st)
+            torch.cuda.synchronize()
+            graph_us = 1e3 * a.elapsed_time(b) / reps
+            for _ in range(10):
+                fnn.build_neighbors(ctx, ds, nl, stream=st)
+                fnn.energy_forces(ctx, ds, nl, form, out=(g.E, g.F, g.W), stream=st)
+            a.record(st)
+            for _ in range(reps):
+                fnn.build_neighbors(ctx, ds, nl, stream=st)
+                fnn.energy_forces(ctx, ds, nl, form, out=(g.E, g.F, g.W), stream=st)
+            b.record(st)
+            torch.cuda.synchronize()
+            eager_us = 1e3 * a.elapsed_time(b) / reps
+        fnn.check(ctx, "latency", stream=st)
+        out[form] = {"graph_us_per_eval": graph_us, "eager_us_per_eval": eager_us, "kernels_per_eval": g.kernels}
+        g.close()
+    return out
 
 
 def md_bench(fnn, torch, synth, n_steps: int = 1000, M: int = 8):
@@ -538,24 +624,10 @@ def main():
     import torch
     from paper_2405_01491_b300 import fnn, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks("nccl", "cuda")
+    world, rank = ranks.world, ranks.rank
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     M = 8
     s = synth.mix23558()
@@ -604,9 +676,10 @@ def main():
     serve = None
     if world == 1 and not args.no_serve:
         serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds)
-    md = None
+    md = latency = None
     if world == 1 and not args.no_md:
         md = md_bench(fnn, torch, synth)
+        latency = latency_bench(fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
         train = {p: train_bench(fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
@@ -631,10 +704,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp32x3": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "members": M, "precision": args.precision,
-                       "precision_note": PRECISION_NOTE.get(args.precision, ""),
-                       "list_entries": nnz, "parallelism": f"replicas x{world}",
-                       "l2": "flushed before every timed step (256 MB write outside the step's CUDA events)"},
+            "config": arm_config(args.precision, nnz, world),
             "roofline": roof, "gpu_launches": int(head["launches"]),
             "e2e": {"value": world * s.n_atoms / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -647,10 +717,11 @@ def main():
         line["train"] = train
     if md is not None:
         line["md"] = md
+    if latency is not None:
+        line["latency"] = latency
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
