@@ -172,7 +172,9 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   void *hp[] = {h.Z, h.mol_offsets, h.pos, h.cell, h.pbc, h.pos3, h.E, h.virial, h.F};
   for (void *p : hp)
     if (p) cudaFree(p);
+  if (h.graph) fnn_graph_destroy(h.graph);
   if (h.nl) fnn_nlist_destroy(h.nl);
+  if (h.own) cudaStreamDestroy(h.own);
   if (ctx->status) cudaFree(ctx->status);
   for (auto &r : ctx->prof.recs) {
     cudaEventDestroy(r.a);
@@ -330,10 +332,17 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
                                              fnn_precision prec, double *E, float *F, double *virial, void *stream) {
   if (!ctx || N < 0 || NM < 1 || !mol_offsets || (N > 0 && (!Z || !pos)) || !E || !F || (pbc && !cell))
     return FNN_E_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
   auto &h = ctx->host;
+  if (!stream && !h.own) FNN_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&h.own, cudaStreamNonBlocking));
+  if (!stream) stream = h.own;   // synchronous either way; a stream of its own can be captured
+  cudaStream_t s = (cudaStream_t)stream;
   fnn_status st;
   if (N > h.n_atoms || NM > h.n_mol) {
+    if (h.graph) {   // bound to the buffers about to be replaced
+      fnn_graph_destroy(h.graph);
+      h.graph = nullptr;
+      h.gkey = h.last_key = -1;
+    }
     int32_t na = N > h.n_atoms ? N : h.n_atoms, nm = NM > h.n_mol ? NM : h.n_mol;
     if ((st = dalloc(ctx, &h.Z, na)) || (st = dalloc(ctx, &h.pos, (size_t)na * 4)) ||
         (st = dalloc(ctx, &h.pos3, (size_t)na * 3)) || (st = dalloc(ctx, &h.F, (size_t)na * 3)) ||
@@ -358,8 +367,31 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(h.pbc, pbc, (size_t)NM, cudaMemcpyHostToDevice, s));
   }
   fnn_system sys{N, NM, h.mol_offsets, h.Z, h.pos, pbc ? h.cell : nullptr, pbc ? h.pbc : nullptr};
-  if ((st = fnn_build_neighbors(ctx, &sys, h.nl, stream))) return st;
-  if ((st = fnn_energy_forces(ctx, &sys, h.nl, prec, h.E, h.F, virial ? h.virial : nullptr, stream))) return st;
+  // a call repeating the previous one's shape replays the device part as a CUDA graph (created on the
+  // second such call, whose own evaluation is the graph's eager step)
+  const long long key = ((((long long)N * 2 + (pbc != nullptr)) * 2 + (virial != nullptr)) * 8 + (long long)prec) *
+                            (1LL << 20) + NM;
+  bool done = false;
+  if (h.graph && key == h.gkey) {
+    if ((st = fnn_graph_launch(h.graph, stream))) return st;
+    done = true;
+  } else if (key == h.last_key && stream != nullptr) {
+    if (h.graph) fnn_graph_destroy(h.graph);
+    h.graph = nullptr;
+    if (fnn_graph_create(ctx, &sys, h.nl, prec, h.E, h.F, virial ? h.virial : nullptr, 1, stream, &h.graph) ==
+        FNN_OK) {
+      h.gkey = key;
+      done = true;
+    } else {
+      h.graph = nullptr;
+      h.gkey = -1;
+    }
+  }
+  h.last_key = key;
+  if (!done) {
+    if ((st = fnn_build_neighbors(ctx, &sys, h.nl, stream))) return st;
+    if ((st = fnn_energy_forces(ctx, &sys, h.nl, prec, h.E, h.F, virial ? h.virial : nullptr, stream))) return st;
+  }
   FNN_CUDA_TRY(ctx, cudaMemcpyAsync(E, h.E, (size_t)NM * sizeof(double), cudaMemcpyDeviceToHost, s));
   FNN_CUDA_TRY(ctx, cudaMemcpyAsync(F, h.F, (size_t)N * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (virial)
@@ -368,6 +400,11 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
   st = fnn_sync(ctx, stream, &info);
   if (st == FNN_E_CAPACITY && info > 0) {
     // the list outgrew its capacity: grow it and evaluate again (once)
+    if (h.graph) {
+      fnn_graph_destroy(h.graph);
+      h.graph = nullptr;
+    }
+    h.gkey = h.last_key = -1;
     if ((st = fnn_nlist_reserve(h.nl, N, NM, info + info / 4))) return st;
     return fnn_energy_forces_host(ctx, N, NM, mol_offsets, Z, pos, cell, pbc, prec, E, F, virial, stream);
   }

@@ -151,6 +151,9 @@ struct fnn_ctx {
     double *E = nullptr, *virial = nullptr;
     float *F = nullptr;
     fnn_nlist *nl = nullptr;
+    cudaStream_t own = nullptr;        // the entry point's stream when the caller gives none
+    fnn_graph *graph = nullptr;        // the device part of the last repeated call, replayed
+    long long gkey = -1, last_key = -1;
   } host;
 };
 

@@ -98,3 +98,20 @@ def test_graph_without_rebuild_and_stream_rules(fnn):
     # the legacy default stream cannot be captured
     with pytest.raises(fnn.FnnError):
         fnn.Graph(ctx, ds, nl, "fp32x3", stream=torch.cuda.default_stream())
+
+
+def test_host_entry_point_replays_repeated_calls(fnn):
+    """fnn_energy_forces_host replays a graph from the second call of the same shape on: results equal
+    the first (eager) call's, and follow new positions."""
+    s = structure("box300")
+    ctx = fnn.Context(2)
+    fnn.load_weights(ctx, weights(2))
+    outs = [fnn.energy_forces_host(ctx, s, "fp32x3") for _ in range(4)]
+    for E, F, W in outs[1:]:
+        np.testing.assert_array_equal(E, outs[0][0])
+        np.testing.assert_allclose(F, outs[0][1], rtol=0, atol=1e-5)
+    moved = type(s)(s.Z, (s.pos + np.float32(0.03)).astype(np.float32), s.mol_offsets, s.cell, s.pbc)
+    E2, F2, _ = fnn.energy_forces_host(ctx, moved, "fp32x3")
+    r = oracle.energy_forces(moved, weights(2))
+    assert np.abs(E2 - r.energy).max() / s.n_atoms <= 1e-4
+    assert np.abs(F2 - r.forces).max() <= 1e-3
