@@ -123,6 +123,8 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // at most one committed store group still reading its shared-memory source
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// no committed store group still reading its source
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // every committed store group complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // make this thread's shared-memory writes visible to the async proxy (TMA)
@@ -208,7 +210,10 @@ template <int NT, int EPI, int MODE>
 struct Smem {
   static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
-  static constexpr int OBYTES = OB ? EPI_WARPS * 2 * OB * WBUF : 1024;
+  // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
+  // the space more (the split first layer: a fourth operand stage)
+  static constexpr int NBUF = (MODE == MODE_SPLIT && NT == 256 && EPI != EPI_DCELU) ? 1 : 2;
+  static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int FIT = (SMEM_LIMIT - FIXED) / (BM * BKB + NT * BKB);
   static constexpr int STAGES = FIT > 6 ? 6 : FIT;
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int r = q * 32 + lane;
     const int ew = warp - 2;                // epilogue warp index
     constexpr int PB = F8 ? 16 * 32 : 32 * 32;   // bytes of one 32 x 16 piece
-    uint8_t *wb = S.O + (size_t)ew * 2 * SM::OB * SM::WBUF;   // this warp's two buffers
+    uint8_t *wb = S.O + (size_t)ew * SM::NBUF * SM::OB * SM::WBUF;   // this warp's buffers
     uint32_t aux_phase[2] = {0u, 0u};
     unsigned aux_out = 0;                   // lane 0: buffers with an aux load not yet consumed
     long long gk = 0;                       // pieces drained by this warp (buffer gk & 1)
@@ -460,7 +465,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                                              v[j + 2] * sc * p.scale, v[j + 3] * sc * p.scale);
           continue;
         }
-        const int b = (int)(gk & 1);
+        const int b = SM::NBUF == 2 ? (int)(gk & 1) : 0;
         uint8_t *ob = wb + (size_t)b * SM::OB * SM::WBUF;
         if (EPI == EPI_DCELU) {
           const bool got = mbar_wait(&S.aux_bar[ew][b], aux_phase[b]);
@@ -471,7 +476,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
         } else {
-          if (lane == 0 && gk >= 2) bulk_wait_read1();
+          if (lane == 0 && SM::NBUF == 2 && gk >= 2) bulk_wait_read1();
+          if (lane == 0 && SM::NBUF == 1 && gk >= 1) bulk_wait_read0();
           __syncwarp();
         }
         if (F8)
