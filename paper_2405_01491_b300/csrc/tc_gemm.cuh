@@ -212,7 +212,7 @@ struct Smem {
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
   // the space more (the split first layer: a fourth operand stage)
-  static constexpr int NBUF = (MODE == MODE_SPLIT && NT == 256 && EPI != EPI_DCELU) ? 1 : 2;
+  static constexpr int NBUF = (MODE == MODE_SPLIT && EPI != EPI_DCELU) ? 1 : 2;
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int FIT = (SMEM_LIMIT - FIXED) / (BM * BKB + NT * BKB);
