@@ -78,9 +78,9 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
 
 KERNEL_SOURCES = [  # kernel-name prefix -> the files that define it (with the shared internal header)
     (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "mlp_tc.cu")),
-    (("f32_", "atom_energy", "energy_reduce"), ("mlp_simt.cu",)),
+    (("f32_", "energy_reduce"), ("mlp_simt.cu",)),
     (("aev_",), ("aev.cu",)),
-    (("pairs_", "scan_", "mol_setup", "atom_setup", "mol_grid", "check_", "bin", "scatter", "sort_cells", "elem_"),
+    (("pairs_", "scan", "mol_setup", "atom_setup", "mol_grid", "check_", "bin", "scatter", "sort_cells", "elem_"),
      ("nlist.cu",)),
 ]
 

@@ -65,11 +65,12 @@ fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows) {
       (st = dalloc(ctx, &ws.h2, rows * M * H2)) || (st = dalloc(ctx, &ws.g3, rows * M * H3)) ||
       (st = dalloc(ctx, &ws.g2, rows * M * H2)) || (st = dalloc(ctx, &ws.g1, rows * M * H1)) ||
       (st = dalloc(ctx, &ws.gaev, rows * NAEV)) || (st = dalloc(ctx, &ws.ypart, rows * M * 4)) ||
-      (st = dalloc(ctx, &ws.e_atom, rows))) {
+      (st = dalloc(ctx, &ws.e_part, rows)) || (st = dalloc(ctx, &ws.e_ticket, rows))) {
     ws.rows = 0;
     return st;
   }
   cudaMemset(ws.ypart, 0, rows * M * 4 * sizeof(float));
+  cudaMemset(ws.e_ticket, 0, rows * sizeof(unsigned));
   ws.rows = rows;
   ws.M = M;
   return FNN_OK;
@@ -88,7 +89,8 @@ static void free_workspace(Workspace &ws) {
   float *ptrs[] = {ws.aev, ws.h1, ws.h2, ws.g3, ws.g2, ws.g1, ws.gaev, ws.ypart};
   for (float *p : ptrs)
     if (p) cudaFree(p);
-  if (ws.e_atom) cudaFree(ws.e_atom);
+  if (ws.e_part) cudaFree(ws.e_part);
+  if (ws.e_ticket) cudaFree(ws.e_ticket);
   void *tc = ws.tc;
   size_t tr = ws.tc_rows;
   ws = Workspace();

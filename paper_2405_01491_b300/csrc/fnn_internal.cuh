@@ -108,7 +108,8 @@ struct Workspace {
   float *g1 = nullptr;      // [rows][M*256]
   float *gaev = nullptr;    // [rows][1008]
   float *ypart = nullptr;   // [rows][M][4]
-  double *e_atom = nullptr; // [rows] member-averaged atomic energies (atom order)
+  double *e_part = nullptr; // [rows] slice sums of the structure energies
+  unsigned *e_ticket = nullptr;  // [rows] slices finished per structure (zero between launches)
   void *tc = nullptr;       // tensor-core buffers (mlp_tc.cu)
   size_t tc_rows = 0;
 };
@@ -250,7 +251,7 @@ struct KScope {
 
 // exclusive scan of n int32 values in place; total written to *total_dev (device) when non-null
 fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
-                          int64_t tmp_len, cudaStream_t s);
+                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev = nullptr);
 int64_t scan_tmp_needed(int64_t n);
 
 // kernels' host launchers (defined in their .cu files)

@@ -207,34 +207,41 @@ fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStre
 }
 
 // ---------------------------------------------------------------------------- energy reduction
-// e_i = (1/M) sum_m (y partials + b4) per atom (wide, row order), then E_mol = sum over the structure's
-// contiguous atoms in float64, one block per structure, fixed order (section II.E).
-__global__ void k_atom_energy(int n_rows, const int32_t *meta, const int32_t *inv, const uint8_t *elem,
-                              const float *ypart, const float *b4, int M, int ntile, double *e_atom) {
-  int rows = min(n_rows, meta[META_NPAD]);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-    int i = inv[r];
-    if (i < 0) continue;
-    int e = elem[i];
-    float y = 0.f;
-    for (int m = 0; m < M; m++) {
-      const float *yp = ypart + ((size_t)r * M + m) * 4;
-      float ym = b4[m * NE + e];
-      for (int t = 0; t < ntile; t++) ym += yp[t];
-      y += ym;
-    }
-    e_atom[i] = (double)y / (double)M;
+// e_i = (1/M) sum_m (b4 + y partials of atom i's row), then E_mol = sum of e_i over the structure's
+// contiguous atoms in float64 (section II.E) in a fixed order: slice y of gridDim.y sums its atoms in
+// a fixed tree; with more than one slice the last slice block of a structure to finish adds the slice
+// sums (lane-strided, then a fixed shuffle tree) and rearms the structure's ticket for the next launch.
+__device__ __forceinline__ double atom_energy(int i, const int32_t *perm, const uint8_t *elem, const float *ypart,
+                                              const float *b4, int M, int ntile) {
+  const int row = perm[i], e = elem[i];
+  const float4 *yp = reinterpret_cast<const float4 *>(ypart) + (size_t)row * M;
+  float v = 0.f;
+#pragma unroll 4
+  for (int m = 0; m < M; m++) {
+    const float4 q = __ldg(yp + m);
+    float ym = b4[m * NE + e];
+    ym += q.x;
+    if (ntile > 1) ym += q.y;
+    if (ntile > 2) ym += q.z;
+    if (ntile > 3) ym += q.w;
+    v += ym;
   }
+  return (double)v / (double)M;
 }
 
-__global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, const double *e_atom, double *E,
-                         DevStatus *st) {
+__global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, const int32_t *perm,
+                         const uint8_t *elem, const float *ypart, const float *b4, int M, int ntile, double *part,
+                         unsigned *ticket, double *E, DevStatus *st) {
   __shared__ double red[32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int S = gridDim.y, y = blockIdx.y;
   for (int mol = blockIdx.x; mol < n_mol; mol += gridDim.x) {
-    int a0 = max(mol_offsets[mol], 0), a1 = min(mol_offsets[mol + 1], n_atoms);
+    const int a0 = max(mol_offsets[mol], 0), a1 = min(mol_offsets[mol + 1], n_atoms);
+    const int per = (max(a1 - a0, 0) + S - 1) / S;
+    const int s0 = a0 + y * per, s1 = min(a1, s0 + per);
     double acc = 0.0;
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc += e_atom[i];
+    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) acc += atom_energy(i, perm, elem, ypart, b4, M, ntile);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[w] = acc;
@@ -242,8 +249,29 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int q = 0; q < nwarp; q++) t += red[q];
-      E[mol] = t;
-      if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+      if (S == 1) {
+        E[mol] = t;
+        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+        last = 0;
+      } else {
+        part[(size_t)mol * S + y] = t;
+        __threadfence();
+        last = atomicAdd(&ticket[mol], 1u) == (unsigned)(S - 1);
+      }
+    }
+    __syncthreads();
+    if (last && w == 0) {
+      __threadfence();
+      const volatile double *pv = part + (size_t)mol * S;
+      double t = 0.0;
+      for (int q = lane; q < S; q += 32) t += pv[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        E[mol] = t;
+        ticket[mol] = 0u;
+        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+      }
     }
     __syncthreads();
   }
@@ -251,17 +279,18 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
 
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
                               int ntile, double *E, cudaStream_t s) {
-  {
-    int rows = nl->pad_cap;
-    int blocks = (rows + 255) / 256;
-    FNN_KERNEL(ctx, "atom_energy", s);
-    k_atom_energy<<<blocks, 256, 0, s>>>(rows, nl->meta, nl->inv, nl->elem, ypart, ctx->w.b4, ctx->w.M, ntile,
-                                         ctx->ws.e_atom);
-  }
-  int blocks = sys->n_mol < 8 * ctx->num_sms ? sys->n_mol : 8 * ctx->num_sms;
-  int threads = sys->n_atoms / (sys->n_mol > 0 ? sys->n_mol : 1) > 512 ? 1024 : 128;
+  const int NM = sys->n_mol;
+  if (NM <= 0) return FNN_OK;
+  // slices of about 256 atoms for large structures (a thread per atom or two, spread over SMs)
+  const long long avg = sys->n_atoms / NM;
+  int S = (int)((avg + 255) / 256);
+  if (S < 1) S = 1;
+  if (S > 256) S = 256;
+  while (S > 1 && (size_t)NM * S > ctx->ws.rows) S--;
+  const int blocks = NM < 8 * ctx->num_sms ? NM : 8 * ctx->num_sms;
   FNN_KERNEL(ctx, "energy_reduce", s);
-  k_energy<<<blocks, threads, 0, s>>>(sys->n_mol, sys->n_atoms, sys->mol_offsets, ctx->ws.e_atom, E, ctx->status);
+  k_energy<<<dim3(blocks, S), 128, 0, s>>>(NM, sys->n_atoms, sys->mol_offsets, nl->perm, nl->elem, ypart, ctx->w.b4,
+                                           ctx->w.M, ntile, ctx->ws.e_part, ctx->ws.e_ticket, E, ctx->status);
   return check_launch(ctx, "energy_reduce");
 }
 

@@ -123,33 +123,101 @@ __global__ void k_scan_small(int32_t *data, int64_t n, int32_t *total_dev) {
   if (threadIdx.x == 0 && total_dev) *total_dev = carry;
 }
 
-int64_t scan_tmp_needed(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+// Single-pass scan of long arrays (decoupled look-back, Merrill and Garland 2016).  Blocks take tiles
+// in the order they start (a ticket), so every tile a block waits on belongs to a block that is
+// already running.  Each tile publishes one 64-bit word per tile: flag (1 = its own sum, 2 = sum of
+// everything up to and including it) << 32 | value.  The scratch holds the ticket, a pad word and the
+// tile words, and must be zero at launch.  n_dev, when given, bounds the scanned length at run time to
+// min(n_max, *n_dev + 1) (a count known only on the device); blocks past it return at once.
+constexpr long long LOOKBACK_LIMIT = 2000000000LL;   // clock64 cycles (about a second) per wait
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(int32_t *data, int64_t n_max, const int32_t *n_dev,
+                                                              int32_t *total_dev, int32_t *scratch, DevStatus *st) {
+  __shared__ int tile_s, prefix_s;
+  unsigned *ticket = reinterpret_cast<unsigned *>(scratch);
+  unsigned long long *word = reinterpret_cast<unsigned long long *>(scratch + 2);
+  if (threadIdx.x == 0) tile_s = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int t = tile_s;
+  const int64_t n = n_dev ? min(n_max, (int64_t)*n_dev + 1) : n_max;
+  const int64_t base0 = (int64_t)t * SCAN_TILE;
+  if (base0 >= n) return;   // uniform over the block
+  const int64_t base = base0 + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = base + k < n ? data[base + k] : 0;
+    sum += v[k];
+  }
+  int agg;
+  int ex = block_excl_scan<SCAN_NT>(sum, &agg);
+  if (threadIdx.x < 32) {   // warp 0: publish, look back, publish the inclusive prefix
+    const int lane = threadIdx.x;
+    int prefix = 0;
+    if (t > 0) {
+      if (lane == 0) atomicExch(&word[t], (1ull << 32) | (unsigned)agg);
+      int j = t - 1;   // nearest predecessor not yet accounted for
+      bool done = false;
+      while (!done) {
+        const int idx = j - lane;
+        unsigned long long w = 2ull << 32;   // before tile 0: an inclusive zero
+        if (idx >= 0) {
+          volatile unsigned long long *pw = word + idx;
+          w = *pw;
+          if ((w >> 32) == 0) {
+            const long long t0 = clock64();
+            while (((w = *pw) >> 32) == 0)
+              if (clock64() - t0 > LOOKBACK_LIMIT) {
+                post_status(st, FNN_E_TIMEOUT, t);
+                w = 2ull << 32;
+                break;
+              }
+          }
+        }
+        const unsigned incl = __ballot_sync(FULL, (w >> 32) == 2);
+        const int stop = incl ? __ffs(incl) - 1 : 31;   // lanes 0..stop contribute
+        int val = lane <= stop ? (int)(unsigned)(w & 0xffffffffull) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(FULL, val, o);
+        prefix += val;
+        done = incl != 0;
+        j -= 32;
+      }
+    }
+    if (lane == 0) {
+      atomicExch(&word[t], (2ull << 32) | (unsigned)(prefix + agg));
+      prefix_s = prefix;
+      if (total_dev && base0 + SCAN_TILE >= n) *total_dev = prefix + agg;
+    }
+  }
+  __syncthreads();
+  ex += prefix_s;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) data[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+int64_t scan_tmp_needed(int64_t n) { return 2 * ((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
 
 fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
-                          int64_t tmp_len, cudaStream_t s) {
+                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev) {
   if (n <= 0) return FNN_OK;
-  if (n <= 2 * SCAN_TILE) {   // one launch for short arrays (structure and small cell counts)
+  if (n <= 2 * SCAN_TILE && !n_dev) {   // one block for short arrays (structure and small cell counts)
     FNN_KERNEL(ctx, "scan_small", s);
     k_scan_small<<<1, SCAN_NT, 0, s>>>(data, n, total_dev);
     return check_launch(ctx, "exclusive_scan");
   }
-  int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
-  if (nt > tmp_len) {
+  const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (2 * nt + 2 > tmp_len) {
     ctx->last_error = "scan scratch too small";
     return FNN_E_INVALID;
   }
-  {
-    FNN_KERNEL(ctx, "scan_tiles", s);
-    k_scan_tiles<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
-  }
-  {
-    FNN_KERNEL(ctx, "scan_top", s);
-    k_scan_top<<<1, SCAN_NT, 0, s>>>(tmp, nt, total_dev);
-  }
-  {
-    FNN_KERNEL(ctx, "scan_add", s);
-    k_scan_add<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, tmp);
-  }
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(tmp, 0, (size_t)(2 * nt + 2) * sizeof(int32_t), s));
+  FNN_KERNEL(ctx, "scan", s);
+  k_scan_single_pass<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, n_dev, total_dev, tmp, ctx->status);
   return check_launch(ctx, "exclusive_scan");
 }
 
@@ -892,7 +960,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     }
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->cell_start, nl->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
-    if ((st = exclusive_scan(ctx, nl->cell_start, cells_bound + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
+    if ((st = exclusive_scan(ctx, nl->cell_start, cells_bound + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s,
+                             nl->meta + META_CELLS)))
       return st;
     FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
     {
