@@ -65,10 +65,10 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
         return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
-    m = re.match(r"(f32|bf16|fp8|x3)_(l[123])_(fwd|bwd)", name)
-    if m:
+    m = re.match(r"(f32|bf16|fp8|x3)_(l[123])_(fwd|bwd|pair)", name)
+    if m:   # "_pair": the fused third layer, forward and backward products
         flops = 2.0 * gemm[m.group(2)] * M * n_atoms * (3 if m.group(1) == "x3" else 1)
-        return ("alu" if m.group(1) == "f32" else "tensor"), flops, "FLOP"
+        return ("alu" if m.group(1) == "f32" else "tensor"), flops * (2 if m.group(3) == "pair" else 1), "FLOP"
     if name in ("pairs_count", "pairs_fill", "pairs_stage"):
         return "hbm", n_atoms * 16 + (nnz * 8 if name != "pairs_count" else 0), "B"
     if name == "pairs_compact":     # staged entries read, list entries written

@@ -5,10 +5,13 @@
 //   L2  h2 = CELU(h1_m W2^T + b2)                NT = 192 per member
 //   L3  g3 = (1/M) w4 CELU'(z3), y_m = h3 . w4   NT = 160 per member (whole row in one tile)
 //   L3' g2 = (g3_m W3) * CELU'(z2)               NT = 192
+//   (bf16 and split forms: L3 and L3' are one kernel, tc_fused.cuh, with g3 kept in TMEM)
 //   L2' g1 = (g2_m W2) * CELU'(z1)               NT = 256
 //   L1' dE/dAEV = g1 W1cat                       NT = 256, N = 1008, K = M*256, fp32 out
 // Activations between layers are bf16 in HBM; operands reach shared memory by TMA (3-D tensor maps
-// whose middle coordinate selects the member, so each member's K range ends in zero fill).
+// whose middle coordinate selects the member, so each member's K range ends in zero fill).  The split
+// (FP32X3) products stage hi and lo of both operands per K chunk and issue hi*hi + hi*lo + lo*hi from
+// one stage, so each operand tile crosses L2 once per tile instead of twice.
 //
 // FP8 form: the same six products with e4m3 operands (tcgen05 kind::f8f6f4) and per-layer scaling.
 // Each weight block (member, element, layer) carries the scale amax / 448 (W1^T one per element, as
@@ -23,6 +26,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "tc_fused.cuh"
 #include "tc_gemm.cuh"
 
 namespace fnn {
@@ -104,7 +108,26 @@ struct Maps {
   const CUtensorMap *A, *B, *A_lo, *B_lo, *O, *O_lo, *X, *X_lo;
 };
 
-template <int NT, int EPI, int MODE>
+// fused third layer (tc_fused.cuh): persistent over the (row tile, member) grid
+template <int MODE>
+fnn_status launch_l3_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *const maps[10], tc::L3Args a,
+                          cudaStream_t s) {
+  const long long T = (long long)a.n_rowtiles * a.n_members;
+  if (T == 0) return FNN_OK;
+  dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
+  static bool attr_set = false;
+  const size_t sm = tc::l3_smem_bytes<MODE>();
+  if (!attr_set) {
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_l3_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  FNN_KERNEL(ctx, name, s);
+  tc::k_l3_pair<MODE><<<grid, tc::THREADS, sm, s>>>(*maps[0], *maps[1], *maps[2], *maps[3], *maps[4], *maps[5],
+                                                    *maps[6], *maps[7], *maps[8], *maps[9], a);
+  return check_launch(ctx, name);
+}
+
+template <int NT, int EPI, int MODE, bool QUAD = false>
 fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles, cudaStream_t s) {
   // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
   a.n_ntiles = (int)tiles.x;
@@ -113,16 +136,25 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, di
   const long long T = (long long)tiles.x * tiles.y * tiles.z;
   dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
   static bool attr_set = false;
-  const size_t sm = tc::smem_bytes<NT, EPI, MODE>();
+  const size_t sm = tc::smem_bytes<NT, EPI, MODE, QUAD>();
   if (!attr_set) {
-    FNN_CUDA_TRY(ctx,
-                 cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE, QUAD>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI, MODE><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
+  tc::k_umma<NT, EPI, MODE, QUAD><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
                                                           *mp.X_lo, a);
   return check_launch(ctx, name);
+}
+
+// the split with four-tile stages (hi and lo of both operands per K chunk) where quad is set
+template <int NT, int EPI, int MODE>
+fnn_status launch_q(bool quad, fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles,
+                    cudaStream_t s) {
+  if constexpr (MODE == tc::MODE_SPLIT)
+    if (quad) return launch<NT, EPI, MODE, true>(ctx, name, mp, a, tiles, s);
+  return launch<NT, EPI, MODE, false>(ctx, name, mp, a, tiles, s);
 }
 
 }  // namespace
@@ -405,7 +437,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   const int M = w.M;
   const unsigned tiles = (unsigned)(nl->pad_cap / ROW_TILE);
   const char *nm[6] = {SPLIT ? "x3_l1_fwd" : "bf16_l1_fwd", SPLIT ? "x3_l2_fwd" : "bf16_l2_fwd",
-                       SPLIT ? "x3_l3_fwd" : "bf16_l3_fwd", SPLIT ? "x3_l3_bwd" : "bf16_l3_bwd",
+                       nullptr, nullptr,
                        SPLIT ? "x3_l2_bwd" : "bf16_l2_bwd", SPLIT ? "x3_l1_bwd" : "bf16_l1_bwd"};
   fnn_status st;
   tc::Args a{};
@@ -416,38 +448,34 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
   a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(
+  if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true,
            ctx, nm[0], {&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1}, a, dim3(M, tiles, 1), s)))
     return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
   a.o_xm = 0; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
-  if ((st = launch<192, tc::EPI_BIAS_CELU, MODE>(
+  if ((st = launch_q<192, tc::EPI_BIAS_CELU, MODE>(true,
            ctx, nm[1], {&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2}, a, dim3(1, tiles, M), s)))
     return st;
-  // L3 + output layer
-  a.K = H2; a.N = H3;
-  a.bias = w.b3; a.bias_estride = H3; a.bias_mstride = (long long)NE * H3;
-  a.w4 = w.w4; a.w4_estride = H3; a.w4_mstride = (long long)NE * H3;
-  a.ypart = ctx->ws.ypart; a.scale = 1.f / (float)M;
-  if ((st = launch<160, tc::EPI_L3, MODE>(
-           ctx, nm[2], {&H.mH2, &H.mW3, &L.mH2, &L.mW3, &H.eG3, &L.eG3, &H.eG3, &L.eG3}, a, dim3(1, tiles, M), s)))
-    return st;
-  // L3 backward: g2 = (g3 W3) CELU'(h2)
-  a.K = H3; a.N = H2; a.x_y = 1;
-  if ((st = launch<192, tc::EPI_DCELU, MODE>(
-           ctx, nm[3], {&H.mG3, &H.mW3T, &L.mG3, &L.mW3T, &H.eG2, &L.eG2, &H.eH2, &L.eH2}, a, dim3(1, tiles, M), s)))
-    return st;
+  // L3 + output layer and the L3 backward g2 = (g3 W3) CELU'(h2) in one kernel (g3 stays in TMEM)
+  {
+    tc::L3Args l{};
+    l.n_rowtiles = (int)tiles; l.n_members = M; l.tile_elem = nl->tile_elem;
+    l.b3 = w.b3; l.w4 = w.w4; l.ypart = ctx->ws.ypart; l.M = M; l.scale = 1.f / (float)M; l.st = ctx->status;
+    const CUtensorMap *maps[10] = {&H.mH2, &L.mH2, &H.mW3, &L.mW3, &H.mW3T, &L.mW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
+    if ((st = launch_l3_pair<MODE>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
+  }
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
-  a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0;
+  a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;
+  // (two aux buffers per warp keep its CELU' rows in flight; four-tile stages would leave room for one)
   if ((st = launch<256, tc::EPI_DCELU, MODE>(
            ctx, nm[4], {&H.mG2, &H.mW2T, &L.mG2, &L.mW2T, &H.eG1, &L.eG1, &H.eH1, &L.eH1}, a, dim3(1, tiles, M), s)))
     return st;
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
-  return launch<256, tc::EPI_F32, MODE>(ctx, nm[5],
+  return launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
                                         {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1}, a,
                                         dim3((NAEV + 255) / 256, tiles, 1), s);
 }

@@ -206,28 +206,29 @@ struct Args {
 // Shared memory of one CTA: the operand ring (1024-byte aligned for the 128-byte swizzle), then each
 // epilogue warp's two output buffers (32 rows x 16 columns; hi and lo halves for the split), then the
 // barriers.  The ring is as deep as the space allows (at most 6).
-template <int NT, int EPI, int MODE>
+template <int NT, int EPI, int MODE, bool QUAD = false>
 struct Smem {
   static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
   // the space more (the split first layer: a fourth operand stage)
-  static constexpr int NBUF = (MODE == MODE_SPLIT && EPI != EPI_DCELU) ? 1 : 2;
+  static constexpr int NBUF = (MODE == MODE_SPLIT && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
-  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (BM * BKB + NT * BKB);
+  static constexpr int AQ = QUAD ? 2 : 1;   // operand tiles per stage and side (hi, lo)
+  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (AQ * (BM * BKB + NT * BKB));
   static constexpr int STAGES = FIT > 6 ? 6 : FIT;
-  uint8_t A[STAGES][BM * BKB];
-  uint8_t B[STAGES][NT * BKB];
+  uint8_t A[STAGES][AQ * BM * BKB];
+  uint8_t B[STAGES][AQ * NT * BKB];
   uint8_t O[OBYTES];
   uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin, aux_bar[EPI_WARPS][2];
   uint32_t tmem_base;
   int abort_flag;
 };
 
-template <int NT, int EPI, int MODE>
+template <int NT, int EPI, int MODE, bool QUAD = false>
 constexpr size_t smem_bytes() {
-  return sizeof(Smem<NT, EPI, MODE>) + 1024;
+  return sizeof(Smem<NT, EPI, MODE, QUAD>) + 1024;
 }
 
 __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
@@ -278,14 +279,15 @@ __device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &
 // barrier): it converts them into one of its two shared-memory buffers and its lane 0 stores the
 // piece with TMA while the warp fills the other buffer.  EPI_DCELU's aux piece is loaded by TMA into
 // the buffer ahead of use and overwritten in place by the result.
-template <int NT, int EPI, int MODE>
+template <int NT, int EPI, int MODE, bool QUAD = false>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
            const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo,
            const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
-  using SM = Smem<NT, EPI, MODE>;
+  static_assert(!QUAD || MODE == MODE_SPLIT, "four-tile stages are a form of the split");
+  using SM = Smem<NT, EPI, MODE, QUAD>;
   static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
   constexpr bool SPLIT = MODE == MODE_SPLIT, F8 = MODE == MODE_F8;
   constexpr int STAGES = SM::STAGES;
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool WG = MODE == MODE_WG;
-  const int nkb_fixed = SPLIT ? 3 * ((p.K + BK - 1) / BK) : (p.K + BK - 1) / BK;
+  const int nkb_fixed = (SPLIT && !QUAD) ? 3 * ((p.K + BK - 1) / BK) : (p.K + BK - 1) / BK;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
   volatile int *abort_flag = &S.abort_flag;
 
@@ -337,8 +339,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&S.full[s], (uint32_t)((BM + NT) * BKB));
-          if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
+          mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + NT) * BKB));
+          if (QUAD) {   // hi and lo of both operands for one K chunk
+            tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
+            tma_load_3d(S.A[s] + BM * BKB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
+            tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, nt * NT, b_grp);
+            tma_load_3d(S.B[s] + NT * BKB, &tmB_lo, &S.full[s], kb * BK, nt * NT, b_grp);
+          } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
             const int term = kb / nkb_seg, x = r0 + (kb - term * nkb_seg) * BK;
             tma_load_3d(S.A[s], term ? &tmA_lo : &tmA, &S.full[s], x, rt * BM, m);
             tma_load_3d(S.B[s], term ? &tmB_lo : &tmB, &S.full[s], x, nt * NT, p.b_shared ? 0 : m);
@@ -380,7 +387,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
           for (int k = 0; k < BKB / 32; k++) {
-            if (F8)
+            if (QUAD) {   // hi hi + hi lo + lo hi of this K step
+              const uint64_t ah = sdesc_sw128(a0 + 32 * k), al = sdesc_sw128(a0 + BM * BKB + 32 * k);
+              const uint64_t bh = sdesc_sw128(b0 + 32 * k), bl = sdesc_sw128(b0 + NT * BKB + 32 * k);
+              mma_bf16(d, ah, bh, idesc, (kb | k) != 0);
+              mma_bf16(d, ah, bl, idesc, 1u);
+              mma_bf16(d, al, bh, idesc, 1u);
+            } else if (F8)
               mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
             else
               mma_bf16(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
@@ -425,8 +438,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       nt_cur = nt;
       // the first aux piece of the tile travels while its MMAs run
       if (EPI == EPI_DCELU && lane == 0 && 16 * part < ncols) {
-        if (gk >= 2) bulk_wait_read1();
-        load_aux((int)(gk & 1), 16 * part, rt, m);
+        if (SM::NBUF == 2 && gk >= 2) bulk_wait_read1();
+        if (SM::NBUF == 1 && gk >= 1) bulk_wait_read0();
+        load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, 16 * part, rt, m);
       }
       bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
@@ -568,8 +582,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (SPLIT) tma_store_3d(&tmO_lo, ob + SM::WBUF, x, oy, rt * BM + q * 32);
           bulk_commit();
           if (EPI == EPI_DCELU && c + 64 < ncols) {   // this warp's next aux piece into the other buffer
-            bulk_wait_read1();
-            load_aux(b ^ 1, c + 64, rt, m);
+            if (SM::NBUF == 2) {
+              bulk_wait_read1();
+              load_aux(b ^ 1, c + 64, rt, m);
+            } else {   // one buffer: once this store has read it
+              bulk_wait_read0();
+              load_aux(0, c + 64, rt, m);
+            }
           }
         }
         gk++;
