@@ -6,11 +6,11 @@
 //
 // Forward, radial: for each element segment, lane (h, k) = (lane / 16, lane % 16) sums shift k
 // over every other neighbour; one shuffle joins the halves; 16 lanes write 64 contiguous bytes.
-// Forward, angular: all unordered pairs j < k of the element-sorted angular list in batches of 32.
-// Each lane evaluates one triplet (4 section powers, 8 radial Gaussians times the switch product)
-// into a shared staging row; then lane (m, s) = (lane / 4, lane % 4) sums pow_s(t) * gauss_m(t)
-// over the batch, keeping runs of equal element pair in a register and flushing them to a per-warp
-// accumulator of the 896 angular slots, stored with coalesced writes at the end.
+// Forward, angular: all unordered pairs j < k of the element-sorted angular list in batches of 32,
+// enumerated block by block in slot order (element pair (a, b), a <= b).  Each lane evaluates one
+// triplet (4 section powers, 8 radial Gaussians times the switch product) into a shared staging
+// row; then lane (m, s) = (lane / 4, lane % 4) sums pow_s(t) * gauss_m(t) over the batch into a
+// register that is stored (coalesced, 32 slots per pair) when the pair's block ends.
 // Adjoint: same staging and enumeration; per triplet the lane reads its pair's 32 gradient slots
 // from a padded shared row, chains the partials to dE/dd per neighbour in shared memory, then the
 // warp scatters them to the forces (F_j -= g, F_i += g) and the virial -d (x) g.
@@ -67,7 +67,9 @@ struct FwdStage {
   alignas(16) float sf[NSZ][SROW];
   alignas(16) float sg[NSA][SROW];
   alignas(16) int sp[SROW];
-  float acc[NPAIR * 32];         // angular accumulators of the atom
+  // element-pair blocks of the atom's triplets, in slot order: {triplets, j0 | k0 << 8 | (a == b) << 16,
+  // count of element b, count of element a} with j0, k0 the angular-list starts of elements a and b
+  int4 blk[NPAIR];
 };
 struct AdjStage {
   NbrStage nb;
@@ -266,21 +268,60 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
         }
       }
     }
-    // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch.
-    // The producer lane evaluates one triplet; lane (m, s) then sums pow_s * gauss_m over the batch,
-    // holding a run of equal element pair in a register and flushing it to the pair's accumulator.
+    // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch,
+    // enumerated block by block in slot order (element pair (a, b), a <= b; within a block j-major), so
+    // a pair's 32 slots are complete when its block ends.  The producer lane evaluates one triplet;
+    // lane (m, s) then sums pow_s * gauss_m over the batch into a register, which goes straight to
+    // the output row when the block ends (slots of absent pairs are written as zeros).
     {
       const int s_my = lane & 3, m_my = lane >> 2;
-      for (int c = lane; c < NPAIR * 32; c += 32) W.acc[c] = 0.f;
+      if (lane < NPAIR) {
+        int a = 0;
+        while (a + 1 < NE && pair_of(a + 1, a + 1) <= lane) a++;
+        const int b = a + (lane - pair_of(a, a));
+        int oa = 0, ob = 0, na = 0, nb = 0;
+#pragma unroll
+        for (int q = 0; q < NE; q++) {
+          if (q == a) { oa = off_a[q]; na = cnt_a[q]; }
+          if (q == b) { ob = off_a[q]; nb = cnt_a[q]; }
+        }
+        W.blk[lane] = make_int4(a == b ? na * (na - 1) / 2 : na * nb, oa | (ob << 8) | ((a == b) << 16), nb, na);
+      }
+      __syncwarp();
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
-      int run_p = -1;
+      int run_p = -1;          // pair block being summed (warp-uniform); every block before it is written
       float racc = 0.f;
+      auto put = [&](int pp, float v) {
+        store_out<OutT>(out + NRAD + pp * 32 + lane, v, A.out_inv);
+        store_lo(lo, NRAD + pp * 32 + lane, v);
+      };
+      int cp = 0, cu = 0;      // block and offset of the batch's first triplet (warp-uniform)
       for (int base = 0; base < T; base += 32) {
-        const int t = base + lane;
-        if (t < T) {
+        int u = cu + lane, pb = cp;
+        int4 bk = W.blk[pb];
+        while (u >= bk.x) {
+          u -= bk.x;
+          if (++pb >= NPAIR) break;
+          bk = W.blk[pb];
+        }
+        cp = __shfl_sync(FULL, pb, 31);
+        cu = __shfl_sync(FULL, u, 31) + 1;
+        if (pb < NPAIR) {
+          const int j0 = bk.y & 0xff;
           int ja, ka;
-          tri_index(t, n, ja, ka);
+          if (bk.y >> 16) {   // both from element a: the u-th pair of its segment
+            int jj, kk;
+            tri_index(u, bk.w, jj, kk);
+            ja = j0 + jj;
+            ka = j0 + kk;
+          } else {            // j from element a, k from element b
+            int jj = (int)((float)u * rcp_fast((float)bk.z));
+            if (jj * bk.z > u) jj--;
+            else if ((jj + 1) * bk.z <= u) jj++;
+            ja = j0 + jj;
+            ka = ((bk.y >> 8) & 0xff) + (u - jj * bk.z);
+          }
           const float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
           const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(d1.w * d2.w);
           const float c95 = 0.95f * c;
@@ -297,7 +338,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
             const float dr = rbar - P.shf_a[m];
             W.sg[m][lane] = __expf(-P.eta_a * dr * dr) * fcc;
           }
-          W.sp[lane] = pair_of(S.ae[ja], S.ae[ka]);   // e_j <= e_k: sorted list
+          W.sp[lane] = pb;
         } else {
 #pragma unroll
           for (int s = 0; s < NSZ; s++) W.sf[s][lane] = 0.f;
@@ -308,7 +349,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
         __syncwarp();
         const int nt = min(32, T - base);
         const float *fr = W.sf[s_my], *gr = W.sg[m_my];
-        // four triplets per step; four of the running element pair are four FMAs
+        // four triplets per step; four of the running block are four FMAs
         for (int q = 0; q < nt; q += 4) {
           const int4 pq = *reinterpret_cast<const int4 *>(&W.sp[q]);
           const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
@@ -322,25 +363,22 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
             const int pv[4] = {pq.x, pq.y, pq.z, pq.w};
             const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, ga[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-              if (pv[u] < 0) break;   // past the last triplet
-              if (pv[u] != run_p) {
-                if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
+            for (int uu = 0; uu < 4; uu++) {
+              if (pv[uu] < 0) break;   // past the last triplet
+              if (pv[uu] != run_p) {   // block run_p is complete; blocks between are empty
+                if (run_p >= 0) put(run_p, racc);
+                for (int pp = run_p + 1; pp < pv[uu]; pp++) put(pp, 0.f);
                 racc = 0.f;
-                run_p = pv[u];
+                run_p = pv[uu];
               }
-              racc = fmaf(fa[u], ga[u], racc);
+              racc = fmaf(fa[uu], ga[uu], racc);
             }
           }
         }
         __syncwarp();
       }
-      if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
-      __syncwarp();
-      for (int c = lane; c < NPAIR * 32; c += 32) {
-        store_out<OutT>(out + NRAD + c, W.acc[c], A.out_inv);
-        store_lo(lo, NRAD + c, W.acc[c]);
-      }
+      if (run_p >= 0) put(run_p, racc);
+      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f);
     }
     __syncwarp();
   }
