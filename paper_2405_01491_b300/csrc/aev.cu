@@ -23,6 +23,7 @@ namespace fnn {
 
 static constexpr unsigned FULL = 0xffffffffu;
 constexpr int AEV_WARPS = 4;
+constexpr int AEV_FWD_BLOCKS = 8, AEV_ADJ_BLOCKS = 6;   // resident blocks per SM (register budgets 64 and 85)
 
 // 2^x on the special-function unit (ex2.approx.ftz: about 2 ulp; arguments here are <= 0)
 __device__ __forceinline__ float exp2f_fast(float x) {
@@ -228,7 +229,7 @@ __device__ __forceinline__ void store_lo(__nv_bfloat16 *lo, size_t c, float v) {
 }
 
 template <typename OutT>
-__global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A) {
+__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(AevFwdArgs A) {
   __shared__ FwdStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   FwdStage &W = smem[wl];
@@ -307,6 +308,9 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
         }
         cp = __shfl_sync(FULL, pb, 31);
         cu = __shfl_sync(FULL, u, 31) + 1;
+        // triplets that open a new block (against the previous lane; lane 0 against the running block)
+        const int pprev = __shfl_up_sync(FULL, pb, 1);
+        const unsigned starts = __ballot_sync(FULL, pb < NPAIR && pb != (lane == 0 ? run_p : pprev));
         if (pb < NPAIR) {
           const int j0 = bk.y & 0xff;
           int ja, ka;
@@ -349,27 +353,28 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_forward(AevFwdArgs A)
         __syncwarp();
         const int nt = min(32, T - base);
         const float *fr = W.sf[s_my], *gr = W.sg[m_my];
-        // four triplets per step; four of the running block are four FMAs
+        // four triplets per step: within the running block four FMAs; where a block opens, the block
+        // before it is complete (and any between them empty)
         for (int q = 0; q < nt; q += 4) {
-          const int4 pq = *reinterpret_cast<const int4 *>(&W.sp[q]);
           const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
           const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
-          if ((pq.x == run_p) & (pq.y == run_p) & (pq.z == run_p) & (pq.w == run_p)) {
+          const unsigned st4 = (starts >> q) & 0xfu;
+          if (st4 == 0u) {
             racc = fmaf(fv.x, gv.x, racc);
             racc = fmaf(fv.y, gv.y, racc);
             racc = fmaf(fv.z, gv.z, racc);
             racc = fmaf(fv.w, gv.w, racc);
           } else {
-            const int pv[4] = {pq.x, pq.y, pq.z, pq.w};
             const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, ga[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
             for (int uu = 0; uu < 4; uu++) {
-              if (pv[uu] < 0) break;   // past the last triplet
-              if (pv[uu] != run_p) {   // block run_p is complete; blocks between are empty
+              if (q + uu >= nt) break;
+              if ((st4 >> uu) & 1u) {
+                const int pn = W.sp[q + uu];
                 if (run_p >= 0) put(run_p, racc);
-                for (int pp = run_p + 1; pp < pv[uu]; pp++) put(pp, 0.f);
+                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f);
                 racc = 0.f;
-                run_p = pv[uu];
+                run_p = pn;
               }
               racc = fmaf(fa[uu], ga[uu], racc);
             }
@@ -399,7 +404,7 @@ struct AevAdjArgs {
 
 // The dE/dAEV row is read through the L1 cache where it is used (4 KB per atom, re-read by the warp's
 // lanes): staging it in shared memory would cap the number of resident warps.
-__global__ void __launch_bounds__(AEV_WARPS * 32, 6) k_aev_adjoint(AevAdjArgs A) {
+__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
   __shared__ AdjStage smem[AEV_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   AdjStage &W = smem[wl];
@@ -702,9 +707,10 @@ static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
   return s;
 }
 
-static int aev_grid(fnn_ctx *ctx, int64_t rows) {
+// one wave of resident blocks (per_sm per SM, the kernel's launch bound) walking the rows
+static int aev_grid(fnn_ctx *ctx, int64_t rows, int per_sm) {
   int64_t need = (rows + AEV_WARPS - 1) / AEV_WARPS;
-  int64_t cap = (int64_t)ctx->num_sms * 12;
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
   if (need > cap) need = cap;
   return need < 1 ? 1 : (int)need;
 }
@@ -725,7 +731,7 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_forward", s);
-    k_aev_forward<float><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<float><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward");
 }
@@ -746,7 +752,7 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, out_lo ? "aev_forward_x3" : "aev_forward_bf16", s);
-    k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_bf16");
 }
@@ -767,7 +773,7 @@ fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_forward_fp8", s);
-    k_aev_forward<__nv_fp8_e4m3><<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<__nv_fp8_e4m3><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_fp8");
 }
@@ -788,7 +794,7 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_adjoint", s);
-    k_aev_adjoint<<<aev_grid(ctx, rows), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_adjoint<<<aev_grid(ctx, rows, AEV_ADJ_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_adjoint");
 }
@@ -808,7 +814,7 @@ fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_tangent", s);
-    k_aev_tangent<<<2 * aev_grid(ctx, rows), TAN_WARPS * 32, 0, s>>>(a);
+    k_aev_tangent<<<2 * aev_grid(ctx, rows, 12), TAN_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_tangent");
 }
