@@ -23,7 +23,7 @@ namespace fnn {
 
 static constexpr unsigned FULL = 0xffffffffu;
 constexpr int AEV_WARPS = 4;
-constexpr int AEV_FWD_BLOCKS = 8, AEV_ADJ_BLOCKS = 6;   // resident blocks per SM (register budgets 64 and 85)
+constexpr int AEV_FWD_BLOCKS = 8, AEV_ADJ_BLOCKS = 8;   // resident blocks per SM (64 registers)
 
 // 2^x on the special-function unit (ex2.approx.ftz: about 2 ulp; arguments here are <= 0)
 __device__ __forceinline__ float exp2f_fast(float x) {
@@ -75,6 +75,7 @@ struct FwdStage {
 struct AdjStage {
   NbrStage nb;
   float gacc[RAD_CAP][3];        // dE/dd per radial entry
+  double vacc[9];                // virial of the current structure (lane 0), flushed when it changes
 };
 
 struct StageArgs {
@@ -412,9 +413,9 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
-  double vacc[9];
-#pragma unroll
-  for (int q = 0; q < 9; q++) vacc[q] = 0.0;
+  double *vacc = W.vacc;
+  if (lane == 0)
+    for (int q = 0; q < 9; q++) vacc[q] = 0.0;
   int cur_mol = -1;
   for (int row = wg; row < nrows; row += nw) {
     int i = A.inv ? A.inv[row] : row;
