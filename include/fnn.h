@@ -136,6 +136,9 @@ fnn_status fnn_nlist_reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int6
  * float64, so the set is bit-exact with that predicate.  Cell lists: counting
  * sort of atoms into cells of edge >= R, then a warp per atom scans the 27
  * surrounding cells (ballot + popc compaction, prefix-sum row offsets).
+ * Row order: a row of at most 128 entries is sorted by neighbour element
+ * (H, C, N, O, F, S, Cl), stable within an element; a longer row is in cell
+ * traversal order.  Either order is deterministic.
  * Also records the species-sorted atom order used by fnn_energy_forces.
  * Asynchronous on stream; overflow posts FNN_E_CAPACITY (info = entries needed).
  */

@@ -80,6 +80,7 @@ struct AdjStage {
 
 struct StageArgs {
   int64_t cap;            // list capacity: entries at or beyond it were never written
+  int sorted_upto;        // rows of at most this many entries are sorted by neighbour element
   const float4 *pos;
   const int32_t *row_ptr, *nbr;
   const char4 *shift;
@@ -90,7 +91,8 @@ struct StageArgs {
 
 // Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
 // FNN_E_CAPACITY) when a list overflows.  On return cnt_*/off_* hold per-element counts and
-// segment starts (warp-uniform).
+// segment starts (warp-uniform).  A row sorted by neighbour element (see PAIR_STRIDE) is staged in one
+// pass, its radial and angular subsets in list order; any other row in two (count, then scatter).
 template <bool FULL>
 __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStageT<FULL> &S, int cnt_r[NE],
                                 int off_r[NE + 1], int cnt_a[NE], int off_a[NE + 1], bool want_dfc,
@@ -103,25 +105,78 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   MolGrid g = A.grid[mol];
   float Lx = g.pbc ? g.Lx : 0.f, Ly = g.pbc ? g.Ly : 0.f, Lz = g.pbc ? g.Lz : 0.f;
   int k0 = (int)min((int64_t)A.row_ptr[i], A.cap), k1 = (int)min((int64_t)A.row_ptr[i + 1], A.cap);
-#pragma unroll
-  for (int q = 0; q < NE; q++) cnt_r[q] = cnt_a[q] = 0;
-  // pass 1: counts per element
-  for (int kb = k0; kb < k1; kb += 32) {
-    int k = kb + lane;
-    bool vr = false, va = false;
-    int e = 0;
+  // list entry k (< k1) of this lane: separation, distance, element and the two cutoff tests
+  auto entry = [&](int k, int &j, float &dx, float &dy, float &dz, float &r, int &e, bool &vr, bool &va) {
+    vr = va = false;
+    e = 0;
+    j = 0;
+    dx = dy = dz = r = 0.f;
     if (k < k1) {
-      int j = A.nbr[k];
+      j = A.nbr[k];
       char4 sh = A.shift[k];
       float4 pj = A.pos[j];
-      float dx = (pj.x - pi.x) + (float)sh.x * Lx;
-      float dy = (pj.y - pi.y) + (float)sh.y * Ly;
-      float dz = (pj.z - pi.z) + (float)sh.z * Lz;
-      float r = sqrtf(dx * dx + dy * dy + dz * dz);
+      dx = (pj.x - pi.x) + (float)sh.x * Lx;
+      dy = (pj.y - pi.y) + (float)sh.y * Ly;
+      dz = (pj.z - pi.z) + (float)sh.z * Lz;
+      r = sqrtf(dx * dx + dy * dy + dz * dz);
       vr = r < P.rc_rad;
       va = r < P.rc_ang;
       e = A.elem[j];
     }
+  };
+  auto put = [&](int pr, int pa, int j, float dx, float dy, float dz, float r, int e) {
+    if (pr >= 0) {
+      S.rd[pr] = make_float4(dx, dy, dz, r);
+      S.rfc[pr] = 0.5f * cospif(r * P.inv_rc_rad) + 0.5f;
+      if constexpr (FULL) S.rj[pr] = j;
+      S.re[pr] = (unsigned char)e;
+    }
+    if (pa >= 0) {
+      S.aidx[pa] = (unsigned char)pr;
+      S.ae[pa] = (unsigned char)e;
+      S.afc[pa] = 0.5f * cospif(r * P.inv_rc_ang) + 0.5f;
+      if constexpr (FULL) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < NE; q++) cnt_r[q] = cnt_a[q] = 0;
+  if (k1 - k0 <= A.sorted_upto) {   // one pass: the subsets of a sorted row are sorted
+    int nr = 0, na = 0;
+    for (int kb = k0; kb < k1; kb += 32) {
+      int j, e;
+      float dx, dy, dz, r;
+      bool vr, va;
+      entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
+      const unsigned mr = __ballot_sync(FULL, vr), ma = __ballot_sync(FULL, va);
+#pragma unroll
+      for (int q = 0; q < NE; q++) {
+        cnt_r[q] += __popc(__ballot_sync(FULL, vr && e == q));
+        cnt_a[q] += __popc(__ballot_sync(FULL, va && e == q));
+      }
+      const int pr = nr + __popc(mr & lt), pa = na + __popc(ma & lt);
+      if (vr && pr < RAD_CAP) put(pr, va && pa < ANG_CAP ? pa : -1, j, dx, dy, dz, r, e);
+      nr += __popc(mr);
+      na += __popc(ma);
+    }
+    off_r[0] = off_a[0] = 0;
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      off_r[q + 1] = off_r[q] + cnt_r[q];
+      off_a[q + 1] = off_a[q] + cnt_a[q];
+    }
+    if (nr > RAD_CAP || na > ANG_CAP) {
+      if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
+      return false;
+    }
+    __syncwarp();
+    return true;
+  }
+  // pass 1: counts per element
+  for (int kb = k0; kb < k1; kb += 32) {
+    int j, e;
+    float dx, dy, dz, r;
+    bool vr, va;
+    entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
 #pragma unroll
     for (int q = 0; q < NE; q++) {
       cnt_r[q] += __popc(__ballot_sync(FULL, vr && e == q));
@@ -143,22 +198,10 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   for (int q = 0; q < NE; q++) run_r[q] = run_a[q] = 0;
   // pass 2: scatter into element segments (stable within an element)
   for (int kb = k0; kb < k1; kb += 32) {
-    int k = kb + lane;
-    bool vr = false, va = false;
-    int e = 0, j = 0;
-    float dx = 0, dy = 0, dz = 0, r = 0;
-    if (k < k1) {
-      j = A.nbr[k];
-      char4 sh = A.shift[k];
-      float4 pj = A.pos[j];
-      dx = (pj.x - pi.x) + (float)sh.x * Lx;
-      dy = (pj.y - pi.y) + (float)sh.y * Ly;
-      dz = (pj.z - pi.z) + (float)sh.z * Lz;
-      r = sqrtf(dx * dx + dy * dy + dz * dz);
-      vr = r < P.rc_rad;
-      va = r < P.rc_ang;
-      e = A.elem[j];
-    }
+    int j, e;
+    float dx, dy, dz, r;
+    bool vr, va;
+    entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
     int pr = -1, pa = -1;
 #pragma unroll
     for (int q = 0; q < NE; q++) {
@@ -169,18 +212,7 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
       run_r[q] += __popc(mr);
       run_a[q] += __popc(ma);
     }
-    if (pr >= 0) {
-      S.rd[pr] = make_float4(dx, dy, dz, r);
-      S.rfc[pr] = 0.5f * cospif(r * P.inv_rc_rad) + 0.5f;
-      if constexpr (FULL) S.rj[pr] = j;
-      S.re[pr] = (unsigned char)e;
-    }
-    if (pa >= 0) {
-      S.aidx[pa] = (unsigned char)pr;
-      S.ae[pa] = (unsigned char)e;
-      S.afc[pa] = 0.5f * cospif(r * P.inv_rc_ang) + 0.5f;
-      if constexpr (FULL) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
-    }
+    if (pr >= 0) put(pr, pa, j, dx, dy, dz, r, e);
   }
   __syncwarp();
   return true;
@@ -698,6 +730,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
 static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
   StageArgs s;
   s.cap = nl->capacity;
+  s.sorted_upto = PAIR_STRIDE;
   s.pos = reinterpret_cast<const float4 *>(sys->pos);
   s.row_ptr = nl->row_ptr;
   s.nbr = nl->nbr;

@@ -23,6 +23,9 @@ constexpr int NAEV = NRAD + NPAIR * NSA * NSZ;  // 1008
 constexpr int H1 = 256, H2 = 192, H3 = 160; // hidden widths
 constexpr int MAXM = 8;                     // ensemble members
 constexpr int ROW_TILE = 128;               // species segments are padded to this many rows
+// neighbour rows of at most PAIR_STRIDE entries (every row of a usual density) are stored sorted by
+// neighbour element, stable within an element; longer rows are in traversal order
+constexpr int PAIR_STRIDE = 128;
 constexpr int RAD_CAP = 160;                // neighbours within rc_rad handled per atom
 constexpr int ANG_CAP = 64;                 // neighbours within rc_ang handled per atom
 constexpr float CELU_ALPHA = 0.1f;

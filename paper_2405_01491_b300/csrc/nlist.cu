@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
   }
 }
 
-constexpr int PAIR_STRIDE = 128;   // staged entries per atom; longer rows are traversed again at compaction
+// PAIR_STRIDE (fnn_internal.cuh): staged entries per atom; longer rows are traversed again at compaction
 
 // pass 1: every atom's neighbours into its own PAIR_STRIDE-entry slot of the staging buffer, and its count
 __global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
@@ -677,16 +677,18 @@ __global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGr
   }
 }
 
-// pass 2: staged rows copied to their CSR place (row_ptr from the scan of the counts); a row longer than
-// the slot is found again by a second traversal writing straight into the list
+// pass 2: staged rows copied to their CSR place (row_ptr from the scan of the counts), sorted by
+// neighbour element (a stable counting sort: ballots count, then place, each element's entries); a row
+// longer than the slot is found again by a second traversal writing straight into the list
 __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
                                                        const int32_t *atom_mol, const int32_t *cell_of,
                                                        const int32_t *cell_start, const int32_t *cell_atoms,
                                                        PredConst pc, const int32_t *row_ptr, const int32_t *tnbr,
-                                                       const char4 *tshift, int32_t *nbr, char4 *shift, int64_t cap,
-                                                       const int32_t *meta) {
+                                                       const char4 *tshift, const uint8_t *elem, int32_t *nbr,
+                                                       char4 *shift, int64_t cap, const int32_t *meta) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n_binned = cell_start[meta[META_CELLS]];
   for (int w = wg; w < n_binned; w += nw) {
@@ -695,13 +697,100 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
     const int n = row_ptr[i + 1] - row_ptr[i];
     if (n <= PAIR_STRIDE) {
       const int64_t src = (int64_t)i * PAIR_STRIDE;
-      for (int k = lane; k < n; k += 32)
-        if (dst + k < cap) {
-          nbr[dst + k] = tnbr[src + k];
-          shift[dst + k] = tshift[src + k];
+      int off[NE];
+#pragma unroll
+      for (int q = 0; q < NE; q++) off[q] = 0;
+      for (int kb = 0; kb < n; kb += 32) {
+        const int k = kb + lane;
+        const int e = k < n ? (int)elem[tnbr[src + k]] : -1;
+#pragma unroll
+        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, e == q));
+      }
+      int run = 0;   // counts -> starts
+#pragma unroll
+      for (int q = 0; q < NE; q++) {
+        const int c = off[q];
+        off[q] = run;
+        run += c;
+      }
+      for (int kb = 0; kb < n; kb += 32) {
+        const int k = kb + lane;
+        int j = 0, e = -1, at = 0;
+        char4 sh = make_char4(0, 0, 0, 0);
+        if (k < n) {
+          j = tnbr[src + k];
+          sh = tshift[src + k];
+          e = elem[j];
         }
+#pragma unroll
+        for (int q = 0; q < NE; q++) {
+          const unsigned mq = __ballot_sync(FULL, e == q);
+          if (e == q) at = off[q] + __popc(mq & lt);
+          off[q] += __popc(mq);
+        }
+        if (k < n && dst + at < cap) {
+          nbr[dst + at] = j;
+          shift[dst + at] = sh;
+        }
+      }
     } else {
       pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, nbr, shift, dst, cap);
+    }
+  }
+}
+
+// rows of at most PAIR_STRIDE entries sorted by neighbour element in place (stable), as the staged
+// compaction leaves them: the whole row is read into registers before any entry is written back
+__global__ void __launch_bounds__(256) k_sort_rows(int n_atoms, const int32_t *row_ptr, const uint8_t *elem,
+                                                   int32_t *nbr, char4 *shift, int64_t cap) {
+  constexpr int NCH = PAIR_STRIDE / 32;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = wg; i < n_atoms; i += nw) {
+    const int64_t b0 = row_ptr[i];
+    const int n = row_ptr[i + 1] - row_ptr[i];
+    if (n > PAIR_STRIDE || b0 + n > cap) continue;   // long rows stay in traversal order
+    int jv[NCH], ev[NCH];
+    char4 sv[NCH];
+    int off[NE];
+#pragma unroll
+    for (int q = 0; q < NE; q++) off[q] = 0;
+#pragma unroll
+    for (int c = 0; c < NCH; c++) {
+      const int k = 32 * c + lane;
+      jv[c] = 0;
+      ev[c] = -1;
+      sv[c] = make_char4(0, 0, 0, 0);
+      if (k < n) {
+        jv[c] = nbr[b0 + k];
+        sv[c] = shift[b0 + k];
+        ev[c] = elem[jv[c]];
+      }
+#pragma unroll
+      for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, ev[c] == q));
+    }
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      const int cq = off[q];
+      off[q] = run;
+      run += cq;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < NCH; c++) {
+      int at = 0;
+#pragma unroll
+      for (int q = 0; q < NE; q++) {
+        const unsigned mq = __ballot_sync(FULL, ev[c] == q);
+        if (ev[c] == q) at = off[q] + __popc(mq & lt);
+        off[q] += __popc(mq);
+      }
+      if (ev[c] >= 0) {
+        nbr[b0 + at] = jv[c];
+        shift[b0 + at] = sv[c];
+      }
     }
   }
 }
@@ -994,8 +1083,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     {
       FNN_KERNEL(ctx, "pairs_compact", s);
       k_pairs_compact<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                         nl->cell_atoms, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift, nl->nbr,
-                                         nl->shift, nl->capacity, nl->meta);
+                                         nl->cell_atoms, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift, nl->elem,
+                                         nl->nbr, nl->shift, nl->capacity, nl->meta);
     }
   }
   // species-sorted, 128-row padded order for the networks
@@ -1182,6 +1271,7 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     k_pairs<true><<<pb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_start,
                                      S->cell_atoms, pc, nullptr, row_ptr, nbr, reinterpret_cast<char4 *>(shift4), cap,
                                      S->meta);
+    k_sort_rows<<<pb, 256, 0, s>>>(N, row_ptr, S->elem, nbr, reinterpret_cast<char4 *>(shift4), cap);
   }
   FNN_STATIC_TRY(cudaGetLastError());
   int32_t total = 0;
