@@ -313,7 +313,7 @@ fnn_status fnn_serve_destroy(fnn_server *srv);
  * Builds the same directed list as fnn_build_neighbors (same predicate, same
  * kernels) for at most FNN_STATIC_MAX_ATOMS atoms in at most FNN_STATIC_MAX_MOL
  * structures, with list radius R, and needs no context.  All scratch lives in
- * one array of about 0.3 MB compiled into the library, which every GPU that
+ * one array of about 0.4 MB compiled into the library, which every GPU that
  * loads the library keeps until the process exits; the call itself allocates
  * nothing.
  *   sys      device system, as for fnn_build_neighbors.

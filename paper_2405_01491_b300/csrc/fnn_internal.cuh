@@ -180,6 +180,7 @@ struct fnn_nlist {
   int32_t *cell_of = nullptr;   // [N]
   int32_t *cell_tmp = nullptr;  // [N]
   int32_t *cell_atoms = nullptr;// [N]
+  float4 *cell_pos = nullptr;   // [N] positions in cell_atoms order
   int32_t *counts = nullptr;    // [N + 1]
   int32_t *stage_nbr = nullptr; // [N][128] first pass of the pair search, one slot per atom
   char4 *stage_shift = nullptr; // [N][128]

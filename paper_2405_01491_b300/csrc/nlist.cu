@@ -513,9 +513,10 @@ __global__ void k_scatter(int n, const int32_t *cell_of, const int32_t *cell_sta
   }
 }
 
-// one warp per cell: order the cell's atoms by index (rank sort), so traversal order is deterministic
+// one warp per cell: order the cell's atoms by index (rank sort), so traversal order is deterministic;
+// their positions are copied in the same order, so the pair search reads candidates contiguously
 __global__ void k_sort_cells(const int32_t *meta, const int32_t *cell_start, const int32_t *cell_tmp,
-                             int32_t *cell_atoms) {
+                             const float4 *pos, int32_t *cell_atoms, float4 *cell_pos) {
   int lane = threadIdx.x & 31;
   int ncell = meta[META_CELLS];
   int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -526,6 +527,7 @@ __global__ void k_sort_cells(const int32_t *meta, const int32_t *cell_start, con
       int rank = 0;
       for (int b = s0; b < s1; b++) rank += cell_tmp[b] < v;
       cell_atoms[s0 + rank] = v;
+      cell_pos[s0 + rank] = pos[v];
     }
   }
 }
@@ -589,7 +591,8 @@ __device__ __forceinline__ int stencil(int c, int d, int pbc, int *out) {
 // limit; returns the number of neighbours (all of them, written or not).
 __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid *grid, const int32_t *mol_base,
                                          const int32_t *atom_mol, const int32_t *cell_of,
-                                         const int32_t *cell_start, const int32_t *cell_atoms, const PredConst &pc,
+                                         const int32_t *cell_start, const int32_t *cell_atoms,
+                                         const float4 *cell_pos, const PredConst &pc,
                                          int32_t *nbr, char4 *shift, int64_t base, int64_t limit) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -617,8 +620,9 @@ __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid
           int j = -1;
           char4 sh = make_char4(0, 0, 0, 0);
           if (k < s1) {
+            const float4 pj = cell_pos[k];
             j = cell_atoms[k];
-            if (j != i) in = pair_in(pi, pos[j], g, pc, sh);
+            in = pair_in(pi, pj, g, pc, sh) && j != i;
           }
           const unsigned mask = __ballot_sync(FULL, in);
           if (in) {
@@ -641,7 +645,8 @@ template <bool FILL>
 __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
                                                const int32_t *atom_mol, const int32_t *cell_of,
                                                const int32_t *cell_start, const int32_t *cell_atoms,
-                                               PredConst pc, int32_t *counts, const int32_t *row_ptr,
+                                               const float4 *cell_pos, PredConst pc, int32_t *counts,
+                                               const int32_t *row_ptr,
                                                int32_t *nbr, char4 *shift, int64_t cap, const int32_t *meta) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31;
@@ -650,7 +655,7 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
   for (int w = wg; w < n_binned; w += nw) {
     const int i = cell_atoms[w];   // atoms in cell order: neighbouring warps share neighbour cells
     const int64_t out = FILL ? (int64_t)row_ptr[i] : 0;
-    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, nbr, shift,
+    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc, nbr, shift,
                                 out, FILL ? cap : 0);
     if (!FILL && lane == 0) counts[i] = count;
   }
@@ -662,7 +667,8 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
 __global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
                                                      const int32_t *atom_mol, const int32_t *cell_of,
                                                      const int32_t *cell_start, const int32_t *cell_atoms,
-                                                     PredConst pc, int32_t *counts, int32_t *tnbr, char4 *tshift,
+                                                     const float4 *cell_pos, PredConst pc, int32_t *counts,
+                                                     int32_t *tnbr, char4 *tshift,
                                                      const int32_t *meta) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31;
@@ -671,7 +677,7 @@ __global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGr
   for (int w = wg; w < n_binned; w += nw) {
     const int i = cell_atoms[w];   // cell order: neighbouring warps share neighbour cells
     const int64_t base = (int64_t)i * PAIR_STRIDE;
-    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, tnbr, tshift,
+    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc, tnbr, tshift,
                                 base, base + PAIR_STRIDE);
     if (lane == 0) counts[i] = count;
   }
@@ -683,7 +689,8 @@ __global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGr
 __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
                                                        const int32_t *atom_mol, const int32_t *cell_of,
                                                        const int32_t *cell_start, const int32_t *cell_atoms,
-                                                       PredConst pc, const int32_t *row_ptr, const int32_t *tnbr,
+                                                       const float4 *cell_pos, PredConst pc, const int32_t *row_ptr,
+                                                       const int32_t *tnbr,
                                                        const char4 *tshift, const uint8_t *elem, int32_t *nbr,
                                                        char4 *shift, int64_t cap, const int32_t *meta) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
@@ -734,7 +741,7 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
         }
       }
     } else {
-      pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, pc, nbr, shift, dst, cap);
+      pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc, nbr, shift, dst, cap);
     }
   }
 }
@@ -893,6 +900,7 @@ static fnn_status reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t
     if ((st = grow(ctx, &nl->row_ptr, (size_t)na + 1)) || (st = grow(ctx, &nl->atom_mol, na)) ||
         (st = grow(ctx, &nl->elem, na)) || (st = grow(ctx, &nl->cell_of, na)) ||
         (st = grow(ctx, &nl->cell_tmp, na)) || (st = grow(ctx, &nl->cell_atoms, na)) ||
+        (st = grow(ctx, &nl->cell_pos, na)) ||
         (st = grow(ctx, &nl->counts, (size_t)na + 1)) || (st = grow(ctx, &nl->perm, na)))
       return st;
     int32_t pad = (na + ROW_TILE - 1) / ROW_TILE * ROW_TILE + NE * ROW_TILE;
@@ -964,7 +972,7 @@ extern "C" fnn_status fnn_nlist_destroy(fnn_nlist *nl) {
   void *ptrs[] = {nl->row_ptr, nl->nbr, nl->shift, nl->atom_mol, nl->elem, nl->cell_of, nl->cell_tmp,
                   nl->cell_atoms, nl->counts, nl->grid, nl->mol_cells, nl->cell_count, nl->cell_start,
                   nl->perm, nl->inv, nl->tile_elem, nl->blk_count, nl->meta, nl->scan_tmp, nl->stage_nbr,
-                  nl->stage_shift, nl->bbox};
+                  nl->stage_shift, nl->bbox, nl->cell_pos};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete nl;
@@ -1061,7 +1069,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     if (wb > 16 * ctx->num_sms) wb = 16 * ctx->num_sms;
     {
       FNN_KERNEL(ctx, "sort_cells", s);
-      k_sort_cells<<<wb, 256, 0, s>>>(nl->meta, nl->cell_start, nl->cell_tmp, nl->cell_atoms);
+      k_sort_cells<<<wb, 256, 0, s>>>(nl->meta, nl->cell_start, nl->cell_tmp,
+                                      reinterpret_cast<const float4 *>(sys->pos), nl->cell_atoms, nl->cell_pos);
     }
 
     PredConst pc{R * R, (float)(R * R), (float)R};
@@ -1070,7 +1079,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     {
       FNN_KERNEL(ctx, "pairs_stage", s);
       k_pairs_stage<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                       nl->cell_atoms, pc, nl->counts, nl->stage_nbr, nl->stage_shift, nl->meta);
+                                       nl->cell_atoms, nl->cell_pos, pc, nl->counts, nl->stage_nbr, nl->stage_shift,
+                                       nl->meta);
     }
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->row_ptr, nl->counts, ((size_t)N + 1) * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
@@ -1083,7 +1093,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     {
       FNN_KERNEL(ctx, "pairs_compact", s);
       k_pairs_compact<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
-                                         nl->cell_atoms, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift, nl->elem,
+                                         nl->cell_atoms, nl->cell_pos, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift,
+                                         nl->elem,
                                          nl->nbr, nl->shift, nl->capacity, nl->meta);
     }
   }
@@ -1174,6 +1185,7 @@ struct StaticScratch {
   int32_t cell_of[NS_MAX_ATOMS];
   int32_t cell_tmp[NS_MAX_ATOMS];
   int32_t cell_atoms[NS_MAX_ATOMS];
+  float4 cell_pos[NS_MAX_ATOMS];
   int32_t cell_count[NS_MAX_CELLS + 1];
   int32_t cell_start[NS_MAX_CELLS + 1];
   uint8_t elem[NS_MAX_ATOMS];
@@ -1260,17 +1272,17 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     FNN_STATIC_TRY(scan_in_place(S->cell_start, cells_bound + 1, nullptr, S->scan_tmp, s));
     FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
     k_scatter<<<nb, 256, 0, s>>>(N, S->cell_of, S->cell_start, S->cell_count, S->cell_tmp);
-    k_sort_cells<<<(int)((cells_bound * 32 + 255) / 256), 256, 0, s>>>(S->meta, S->cell_start, S->cell_tmp,
-                                                                       S->cell_atoms);
+    k_sort_cells<<<(int)((cells_bound * 32 + 255) / 256), 256, 0, s>>>(
+        S->meta, S->cell_start, S->cell_tmp, reinterpret_cast<const float4 *>(sys->pos), S->cell_atoms, S->cell_pos);
     PredConst pc{R * R, (float)(R * R), (float)R};
     const int pb = (N * 32 + 255) / 256;
     k_pairs<false><<<pb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_start,
-                                      S->cell_atoms, pc, row_ptr, nullptr, nullptr, nullptr, 0, S->meta);
+                                      S->cell_atoms, S->cell_pos, pc, row_ptr, nullptr, nullptr, nullptr, 0, S->meta);
     FNN_STATIC_TRY(scan_in_place(row_ptr, (int64_t)N + 1, nullptr, S->scan_tmp, s));
     k_check_capacity<<<1, 1, 0, s>>>(row_ptr, N, cap, S->meta, &S->status);
     k_pairs<true><<<pb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_start,
-                                     S->cell_atoms, pc, nullptr, row_ptr, nbr, reinterpret_cast<char4 *>(shift4), cap,
-                                     S->meta);
+                                     S->cell_atoms, S->cell_pos, pc, nullptr, row_ptr, nbr,
+                                     reinterpret_cast<char4 *>(shift4), cap, S->meta);
     k_sort_rows<<<pb, 256, 0, s>>>(N, row_ptr, S->elem, nbr, reinterpret_cast<char4 *>(shift4), cap);
   }
   FNN_STATIC_TRY(cudaGetLastError());
