@@ -69,6 +69,8 @@ struct Half {
   __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
   CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;   // operand maps (128-byte rows, swizzled)
   CUtensorMap eH1, eH2, eG3, eG2, eG1;         // epilogue maps: 32-row x 16-column pieces, unswizzled
+  // 64-byte-row (64-byte swizzle) operand maps (the split first-layer input gradient)
+  CUtensorMap qW1T, qG1;
 };
 
 // e4m3 operands of the FP8 form and their scales
@@ -127,7 +129,7 @@ fnn_status launch_l3_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *con
   return check_launch(ctx, name);
 }
 
-template <int NT, int EPI, int MODE, bool QUAD = false>
+template <int NT, int EPI, int MODE, bool QUAD = false, int KB = tc::BKB>
 fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles, cudaStream_t s) {
   // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
   a.n_ntiles = (int)tiles.x;
@@ -136,24 +138,27 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, di
   const long long T = (long long)tiles.x * tiles.y * tiles.z;
   dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
   static bool attr_set = false;
-  const size_t sm = tc::smem_bytes<NT, EPI, MODE, QUAD>();
+  const size_t sm = tc::smem_bytes<NT, EPI, MODE, QUAD, KB>();
   if (!attr_set) {
-    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE, QUAD>,
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma<NT, EPI, MODE, QUAD, KB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI, MODE, QUAD><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
+  tc::k_umma<NT, EPI, MODE, QUAD, KB><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
                                                           *mp.X_lo, a);
   return check_launch(ctx, name);
 }
 
 // the split with four-tile stages (hi and lo of both operands per K chunk) where quad is set
+// (and, where mp64 is given, 64-byte operand rows: twice the stages for the same bytes in flight)
 template <int NT, int EPI, int MODE>
-fnn_status launch_q(bool quad, fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles,
-                    cudaStream_t s) {
-  if constexpr (MODE == tc::MODE_SPLIT)
+fnn_status launch_q(bool quad, fnn_ctx *ctx, const char *name, const Maps &mp, const Maps *mp64, tc::Args a,
+                    dim3 tiles, cudaStream_t s) {
+  if constexpr (MODE == tc::MODE_SPLIT) {
+    if (quad && mp64) return launch<NT, EPI, MODE, true, 64>(ctx, name, *mp64, a, tiles, s);
     if (quad) return launch<NT, EPI, MODE, true>(ctx, name, mp, a, tiles, s);
+  }
   return launch<NT, EPI, MODE, false>(ctx, name, mp, a, tiles, s);
 }
 
@@ -282,6 +287,10 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
         encode3d(&H.mW2T, H.W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, H1, 1) &&
         encode3d(&H.mW3, H.W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 64, H3, 1) &&
         encode3d(&H.mW3T, H.W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 64, H2, 1);
+    const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapSwizzle S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    ok = ok && encode3d(&H.qW1T, H.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2,
+                        32, 256, 1, BF, S64);
     if (!ok) {
       ctx->last_error = "cuTensorMapEncodeTiled failed for the weight maps";
       return FNN_E_CUDA;
@@ -323,7 +332,9 @@ static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
               encode3d(&H.mG2, H.g2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 128) &&
               encode3d(&H.mG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 128);
     const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE;
+    const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE, S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    ok = ok && encode3d(&H.qG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 32, 1, 128,
+                        BF, S64);
     ok = ok && encode3d(&H.eH1, H.h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 16, 1, 32, BF, NS) &&
          encode3d(&H.eH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 16, 1, 32, BF, NS) &&
          encode3d(&H.eG3, H.g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 16, 1, 32, BF, NS) &&
@@ -449,14 +460,16 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
   if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true,
-           ctx, nm[0], {&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1}, a, dim3(M, tiles, 1), s)))
+           ctx, nm[0], {&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1}, nullptr, a,
+           dim3(M, tiles, 1), s)))
     return st;
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
   a.o_xm = 0; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
   if ((st = launch_q<192, tc::EPI_BIAS_CELU, MODE>(true,
-           ctx, nm[1], {&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2}, a, dim3(1, tiles, M), s)))
+           ctx, nm[1], {&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2}, nullptr, a,
+           dim3(1, tiles, M), s)))
     return st;
   // L3 + output layer and the L3 backward g2 = (g3 W3) CELU'(h2) in one kernel (g3 stays in TMEM)
   {
@@ -475,9 +488,13 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
+  // (split: 64-byte rows, four stages instead of two; measured faster here, slower for the forward first
+  // layer and for the bf16 form)
+  const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1};
   return launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
-                                        {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1}, a,
-                                        dim3((NAEV + 255) / 256, tiles, 1), s);
+                                        {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1},
+                                        SPLIT ? &q6 : nullptr,
+                                        a, dim3((NAEV + 255) / 256, tiles, 1), s);
 }
 
 // The six products with e4m3 operands; scales as described at the top of this file.

@@ -154,6 +154,21 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
+// the same for 64-byte rows with the 64-byte swizzle: 8-row groups 512 B apart, swizzle mode 4
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+// descriptor of a K-major operand whose rows are KB bytes (128 or 64), swizzled to match
+template <int KB>
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  static_assert(KB == 128 || KB == 64, "row width");
+  return KB == 128 ? sdesc_sw128(saddr) : sdesc_sw64(saddr);
+}
 
 // Instruction descriptor, kind::f16: fp32 accumulator [4,6) = 1, A and B bf16 [7,10) = [10,13) = 1,
 // both K-major (bits 15, 16 = 0), N >> 3 at [17,23), M >> 4 at [24,29).
@@ -206,7 +221,7 @@ struct Args {
 // Shared memory of one CTA: the operand ring (1024-byte aligned for the 128-byte swizzle), then each
 // epilogue warp's two output buffers (32 rows x 16 columns; hi and lo halves for the split), then the
 // barriers.  The ring is as deep as the space allows (at most 6).
-template <int NT, int EPI, int MODE, bool QUAD = false>
+template <int NT, int EPI, int MODE, bool QUAD = false, int KB = BKB>
 struct Smem {
   static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
@@ -216,19 +231,19 @@ struct Smem {
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int AQ = QUAD ? 2 : 1;   // operand tiles per stage and side (hi, lo)
-  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (AQ * (BM * BKB + NT * BKB));
+  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (AQ * (BM * KB + NT * KB));
   static constexpr int STAGES = FIT > 6 ? 6 : FIT;
-  uint8_t A[STAGES][AQ * BM * BKB];
-  uint8_t B[STAGES][AQ * NT * BKB];
+  uint8_t A[STAGES][AQ * BM * KB];
+  uint8_t B[STAGES][AQ * NT * KB];
   uint8_t O[OBYTES];
   uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin, aux_bar[EPI_WARPS][2];
   uint32_t tmem_base;
   int abort_flag;
 };
 
-template <int NT, int EPI, int MODE, bool QUAD = false>
+template <int NT, int EPI, int MODE, bool QUAD = false, int KB = BKB>
 constexpr size_t smem_bytes() {
-  return sizeof(Smem<NT, EPI, MODE, QUAD>) + 1024;
+  return sizeof(Smem<NT, EPI, MODE, QUAD, KB>) + 1024;
 }
 
 __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
@@ -279,7 +294,7 @@ __device__ __forceinline__ bool tile_coords(const Args &p, int t, int &nt, int &
 // barrier): it converts them into one of its two shared-memory buffers and its lane 0 stores the
 // piece with TMA while the warp fills the other buffer.  EPI_DCELU's aux piece is loaded by TMA into
 // the buffer ahead of use and overwritten in place by the result.
-template <int NT, int EPI, int MODE, bool QUAD = false>
+template <int NT, int EPI, int MODE, bool QUAD = false, int KB = BKB>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
@@ -287,11 +302,12 @@ __global__ void __launch_bounds__(THREADS, 1)
            const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
   static_assert(!QUAD || MODE == MODE_SPLIT, "four-tile stages are a form of the split");
-  using SM = Smem<NT, EPI, MODE, QUAD>;
+  static_assert(KB == BKB || QUAD, "64-byte rows only with four-tile stages");
+  using SM = Smem<NT, EPI, MODE, QUAD, KB>;
   static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
   constexpr bool SPLIT = MODE == MODE_SPLIT, F8 = MODE == MODE_F8;
   constexpr int STAGES = SM::STAGES;
-  constexpr int BK = F8 ? BKB : BKB / 2;   // K elements per stage
+  constexpr int BK = F8 ? KB : KB / 2;   // K elements per stage
   extern __shared__ uint8_t smem_raw[];
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -339,12 +355,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + NT) * BKB));
+          mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + NT) * KB));
           if (QUAD) {   // hi and lo of both operands for one K chunk
             tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
-            tma_load_3d(S.A[s] + BM * BKB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
+            tma_load_3d(S.A[s] + BM * KB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
             tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, nt * NT, b_grp);
-            tma_load_3d(S.B[s] + NT * BKB, &tmB_lo, &S.full[s], kb * BK, nt * NT, b_grp);
+            tma_load_3d(S.B[s] + NT * KB, &tmB_lo, &S.full[s], kb * BK, nt * NT, b_grp);
           } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
             const int term = kb / nkb_seg, x = r0 + (kb - term * nkb_seg) * BK;
             tma_load_3d(S.A[s], term ? &tmA_lo : &tmA, &S.full[s], x, rt * BM, m);
@@ -386,17 +402,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           fence_after();
           const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
-          for (int k = 0; k < BKB / 32; k++) {
+          for (int k = 0; k < KB / 32; k++) {
             if (QUAD) {   // hi hi + hi lo + lo hi of this K step
-              const uint64_t ah = sdesc_sw128(a0 + 32 * k), al = sdesc_sw128(a0 + BM * BKB + 32 * k);
-              const uint64_t bh = sdesc_sw128(b0 + 32 * k), bl = sdesc_sw128(b0 + NT * BKB + 32 * k);
+              const uint64_t ah = sdesc<KB>(a0 + 32 * k), al = sdesc<KB>(a0 + BM * KB + 32 * k);
+              const uint64_t bh = sdesc<KB>(b0 + 32 * k), bl = sdesc<KB>(b0 + NT * KB + 32 * k);
               mma_bf16(d, ah, bh, idesc, (kb | k) != 0);
               mma_bf16(d, ah, bl, idesc, 1u);
               mma_bf16(d, al, bh, idesc, 1u);
             } else if (F8)
               mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
             else
-              mma_bf16(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+              mma_bf16(d, sdesc<KB>(a0 + 32 * k), sdesc<KB>(b0 + 32 * k), idesc, (kb | k) != 0);
           }
           mma_commit(&S.empty[s]);
         }
