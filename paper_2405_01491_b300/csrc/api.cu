@@ -159,9 +159,29 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
     return FNN_E_OOM;
   }
   cudaMemset(ctx->status, 0, sizeof(DevStatus));
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    fnn_destroy(ctx);
+    return FNN_E_CUDA;
+  }
   *out = ctx;
   return FNN_OK;
 }
+
+namespace fnn {
+fnn_status side_fork(fnn_ctx *ctx, cudaStream_t s) {
+  FNN_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, s));
+  FNN_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  return FNN_OK;
+}
+fnn_status side_join(fnn_ctx *ctx, cudaStream_t s) {
+  FNN_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+  FNN_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+  return FNN_OK;
+}
+}  // namespace fnn
 
 extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   if (!ctx) return FNN_E_INVALID;
@@ -177,6 +197,9 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   if (h.graph) fnn_graph_destroy(h.graph);
   if (h.nl) fnn_nlist_destroy(h.nl);
   if (h.own) cudaStreamDestroy(h.own);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->status) cudaFree(ctx->status);
   for (auto &r : ctx->prof.recs) {
     cudaEventDestroy(r.a);

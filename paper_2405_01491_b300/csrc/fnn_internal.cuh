@@ -144,6 +144,10 @@ struct fnn_ctx {
   bool has_weights = false;
   fnn::Workspace ws;
   void *train = nullptr;                // training-gradient buffers (train.cu)
+  // a second stream for independent work inside one call (fork: side waits for the caller's stream;
+  // join: the caller's stream waits for side), so captured graphs get parallel branches
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string last_error;
   // host-call staging (fnn_energy_forces_host)
   struct HostStage {
@@ -257,6 +261,10 @@ struct KScope {
 fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
                           int64_t tmp_len, cudaStream_t s, const int32_t *n_dev = nullptr);
 int64_t scan_tmp_needed(int64_t n);
+// work enqueued on ctx->side between side_fork(s) and side_join(s) runs after what s held at the fork
+// and before what s gets after the join
+fnn_status side_fork(fnn_ctx *ctx, cudaStream_t s);
+fnn_status side_join(fnn_ctx *ctx, cudaStream_t s);
 
 // kernels' host launchers (defined in their .cu files)
 fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *out,

@@ -440,8 +440,11 @@ static fnn_status f8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nl
 
 namespace {
 
+// The six products (the third layer's two fused); the structure energies are reduced on the side
+// stream as soon as the output layer is done, overlapping the backward products.
 template <bool SPLIT>
-fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_t s) {
+fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn_nlist *nl, double *E,
+                      cudaStream_t s) {
   constexpr int MODE = SPLIT ? tc::MODE_SPLIT : tc::MODE_BF16;
   const DeviceWeights &w = ctx->w;
   const Half &H = t->h[0], &L = t->h[SPLIT ? 1 : 0];
@@ -479,6 +482,8 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
     const CUtensorMap *maps[10] = {&H.mH2, &L.mH2, &H.mW3, &L.mW3, &H.mW3T, &L.mW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
     if ((st = launch_l3_pair<MODE>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
   }
+  if ((st = side_fork(ctx, s)) || (st = energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, ctx->side)))
+    return st;
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
   a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;
   // (two aux buffers per warp keep its CELU' rows in flight; four-tile stages would leave room for one)
@@ -491,10 +496,11 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStream_
   // (split: 64-byte rows, four stages instead of two; measured faster here, slower for the forward first
   // layer and for the bf16 form)
   const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1};
-  return launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
-                                        {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1},
-                                        SPLIT ? &q6 : nullptr,
-                                        a, dim3((NAEV + 255) / 256, tiles, 1), s);
+  if ((st = launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
+                                             {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1},
+                                             SPLIT ? &q6 : nullptr, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
+    return st;
+  return side_join(ctx, s);
 }
 
 // The six products with e4m3 operands; scales as described at the top of this file.
@@ -593,9 +599,7 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
   }
   if ((st = tc_workspace(ctx, nl->pad_cap, split ? 2 : 1))) return st;
   if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->h[0].aev, split ? t->h[1].aev : nullptr, nl->inv, s))) return st;
-  st = split ? run_layers<true>(ctx, t, nl, s) : run_layers<false>(ctx, t, nl, s);
-  if (st) return st;
-  return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, s);
+  return split ? run_layers<true>(ctx, t, sys, nl, E, s) : run_layers<false>(ctx, t, sys, nl, E, s);
 }
 
 

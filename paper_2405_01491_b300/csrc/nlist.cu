@@ -1039,6 +1039,26 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     FNN_KERNEL(ctx, "atom_setup", s);
     k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, ctx->status);
   }
+  // species-sorted, 128-row padded order for the networks: needs only the elements, so it runs on the
+  // side stream while the cells and pairs are built
+  if ((st = side_fork(ctx, s))) return st;
+  {
+    cudaStream_t ss = ctx->side;
+    int nblk = (N + ELEM_NT - 1) / ELEM_NT;
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->inv, 0xff, (size_t)nl->pad_cap * sizeof(int32_t), ss));
+    if (nblk > 0) {
+      FNN_KERNEL(ctx, "elem_count", ss);
+      k_elem_count<<<nblk, ELEM_NT, 0, ss>>>(N, nl->elem, nl->blk_count);
+    }
+    {
+      FNN_KERNEL(ctx, "elem_scan", ss);
+      k_elem_scan<<<1, SCAN_NT, 0, ss>>>(nblk, nl->blk_count, nl->meta, nl->tile_elem, nl->pad_cap / ROW_TILE);
+    }
+    if (nblk > 0) {
+      FNN_KERNEL(ctx, "elem_scatter", ss);
+      k_elem_scatter<<<nblk, ELEM_NT, 0, ss>>>(N, nl->elem, nl->blk_count, nl->meta, nl->perm, nl->inv);
+    }
+  }
   {
     FNN_KERNEL(ctx, "mol_grid", s);
     k_mol_grid<<<(NM + 127) / 128, 128, 0, s>>>(*sys, nl->bbox, nl->grid, nl->mol_cells, R, ctx->status);
@@ -1098,21 +1118,7 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
                                          nl->nbr, nl->shift, nl->capacity, nl->meta);
     }
   }
-  // species-sorted, 128-row padded order for the networks
-  int nblk = (N + ELEM_NT - 1) / ELEM_NT;
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->inv, 0xff, (size_t)nl->pad_cap * sizeof(int32_t), s));
-  if (nblk > 0) {
-    FNN_KERNEL(ctx, "elem_count", s);
-    k_elem_count<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count);
-  }
-  {
-    FNN_KERNEL(ctx, "elem_scan", s);
-    k_elem_scan<<<1, SCAN_NT, 0, s>>>(nblk, nl->blk_count, nl->meta, nl->tile_elem, nl->pad_cap / ROW_TILE);
-  }
-  if (nblk > 0) {
-    FNN_KERNEL(ctx, "elem_scatter", s);
-    k_elem_scatter<<<nblk, ELEM_NT, 0, s>>>(N, nl->elem, nl->blk_count, nl->meta, nl->perm, nl->inv);
-  }
+  if ((st = side_join(ctx, s))) return st;
   return check_launch(ctx, "fnn_build_neighbors");
 }
 

@@ -32,6 +32,10 @@ def structure(name: str):
         "box300": lambda: synth.mix_box(300, (300 / 0.1) ** (1 / 3), seed=31),
         "box1500": lambda: synth.mix_box(1500, (1500 / 0.1) ** (1 / 3), seed=32,
                                          fractions=synth.MIX7),
+        # three periodic boxes in one batch: structures large enough that each one's float64 energy is
+        # summed in several slices, with more than one such structure at once
+        "boxes3": lambda: synth.concat([synth.mix_box(n, (n / 0.1) ** (1 / 3), seed=33 + k, fractions=synth.MIX7)
+                                        for k, n in enumerate((700, 2600, 1500))], "boxes3"),
     }[name]()
 
 

@@ -152,6 +152,34 @@ def test_energy_forces_fp32_parity(fnn, name, M, skin, precision):
 
 
 @pytest.mark.parametrize("precision", FP32_FORMS)
+def test_energy_forces_several_large_structures(fnn, precision):
+    """A batch of three periodic boxes (700, 2600 and 1500 atoms): each structure's energy is a float64 sum
+    over several slices of atoms, finished by whichever slice ends last, for all three at once."""
+    s = structure("boxes3")
+    _, _, _, E, F, W = _energy_case(fnn, s, 2, precision=precision)
+    r = oracle.energy_forces(s, weights(2))
+    _compare(s, r, E, F, W)
+
+
+def test_neighbor_rows_sorted_by_element(fnn):
+    """Rows of at most 128 entries come out sorted by neighbour element, stable within an element
+    (the order the AEV kernels stage in one pass); the set is the oracle's."""
+    for name, skin in (("box1500", 1.0), ("batch64", 0.0), ("mix23558", 0.0)):
+        s = structure(name)
+        _, _, nl, got = gpu_list(fnn, s, skin)
+        assert as_set(*got) == as_set(*oracle.neighbors(s, 5.1 + skin))
+        row_ptr, nbr, _ = fnn.nlist_export(nl, s.n_atoms)
+        Z = np.asarray(s.Z)
+        elem_of = {1: 0, 6: 1, 7: 2, 8: 3, 9: 4, 16: 5, 17: 6}
+        e = np.array([elem_of[int(z)] for z in Z])[nbr]
+        lens = np.diff(row_ptr)
+        assert lens.max() <= 128, lens.max()
+        for i in range(s.n_atoms):
+            ei = e[row_ptr[i]:row_ptr[i + 1]]
+            assert np.all(np.diff(ei) >= 0), (name, i, ei)
+
+
+@pytest.mark.parametrize("precision", FP32_FORMS)
 def test_energy_forces_fp32_full_size(fnn, precision):
     """The 23,558-atom periodic box with the 8-member ensemble, in the launch configuration the benchmark times."""
     s = structure("mix23558")
