@@ -110,6 +110,19 @@ struct Maps {
   const CUtensorMap *A, *B, *A_lo, *B_lo, *O, *O_lo, *X, *X_lo;
 };
 
+// zero the output tiles a tail-split EPI_F32 launch of grid G will add into (tail_sched): one block per tile
+__global__ void k_zero_tail(tc::Args p, int G, int nkb, int NT) {
+  const tc::TailSched ts = tc::tail_sched(p, G, nkb);
+  if ((int)blockIdx.x >= ts.R) return;
+  const int t = ts.W * G + (int)blockIdx.x;
+  const int nt = t % p.n_ntiles, rest = t / p.n_ntiles, rt = rest % ts.nv, m = rest / ts.nv;
+  const int c0 = nt * NT, nc = min(NT, p.N - c0);
+  for (int k = threadIdx.x; k < tc::BM * nc; k += blockDim.x) {
+    const int r = k / nc, c = k - r * nc;
+    p.out[((long long)rt * tc::BM + r) * p.ldo + m * p.o_mstride + c0 + c] = 0.f;
+  }
+}
+
 // fused third layer (tc_fused.cuh): persistent over the (row tile, member) grid
 template <int MODE>
 fnn_status launch_l3_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *const maps[10], tc::L3Args a,
@@ -482,17 +495,31 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
     const CUtensorMap *maps[10] = {&H.mH2, &L.mH2, &H.mW3, &L.mW3, &H.mW3T, &L.mW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
     if ((st = launch_l3_pair<MODE>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
   }
+  // side stream: the structure energies, and zeros for the first-layer input gradient's tail tiles
+  tc::Args az{};
+  az.n_ntiles = (NAEV + 255) / 256; az.n_rowtiles = (int)tiles; az.n_members = 1;
+  az.N = NAEV; az.out = ctx->ws.gaev; az.ldo = NAEV; az.o_mstride = 0;
+  az.tail_split = 1; az.meta = nl->meta; az.tile_elem = nl->tile_elem;
+  const int G1 = az.n_ntiles * az.n_rowtiles < ctx->num_sms ? az.n_ntiles * az.n_rowtiles : ctx->num_sms;
+  const int nkb1 = SPLIT ? (M * H1 + 31) / 32 : (M * H1 + 63) / 64;   // K chunks: 64-byte rows (split), 128 (bf16)
   if ((st = side_fork(ctx, s)) || (st = energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, ctx->side)))
     return st;
+  {
+    FNN_KERNEL(ctx, "zero_tail", ctx->side);
+    k_zero_tail<<<G1, 256, 0, ctx->side>>>(az, G1, nkb1, 256);
+  }
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
   a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;
   // (two aux buffers per warp keep its CELU' rows in flight; four-tile stages would leave room for one)
   if ((st = launch<256, tc::EPI_DCELU, MODE>(
            ctx, nm[4], {&H.mG2, &H.mW2T, &L.mG2, &L.mW2T, &H.eG1, &L.eG1, &H.eH1, &L.eH1}, a, dim3(1, tiles, M), s)))
     return st;
-  // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint
+  if ((st = side_join(ctx, s))) return st;
+  // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint; the partial last wave is
+  // split along K and added atomically into the tiles zeroed above
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
+  a.tail_split = 1; a.meta = nl->meta;
   // (split: 64-byte rows, four stages instead of two; measured faster here, slower for the forward first
   // layer and for the bf16 form)
   const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1};
@@ -500,7 +527,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
                                              {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1},
                                              SPLIT ? &q6 : nullptr, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
     return st;
-  return side_join(ctx, s);
+  return FNN_OK;
 }
 
 // The six products with e4m3 operands; scales as described at the top of this file.

@@ -216,7 +216,28 @@ struct Args {
   int b_shared;               // B has one member for all (its z coordinate is 0)
   float *dW;
   int O, I;
+  // EPI_F32 only: the tiles of the final partial wave are split along K over all CTAs and their parts
+  // added atomically into the output, which the caller zeroes first (tail_sched gives the tiles)
+  int tail_split;
+  const int32_t *meta;         // META_NPAD bounds the valid row tiles when tail_split is set
 };
+
+// Persistent schedule of a tail-split launch over the valid tiles (row tiles below META_NPAD), grid G:
+// CTA c takes tiles c, c + G, ... for the W whole waves; the R tiles of the partial wave are cut into
+// S parts of their nkb K chunks, part c % S of tile W G + c / S going to CTA c < R S.  Valid tile t is
+// n tile t % n_ntiles, row tile (t / n_ntiles) % nv, member t / (n_ntiles nv).
+struct TailSched {
+  int nv, W, R, S;
+};
+__device__ __forceinline__ TailSched tail_sched(const Args &p, int G, int nkb) {
+  TailSched s;
+  s.nv = min(p.meta[META_NPAD] / BM, p.n_rowtiles);
+  const int Tv = p.n_ntiles * s.nv * p.n_members;
+  s.W = Tv / G;
+  s.R = Tv - s.W * G;
+  s.S = s.R ? min(G / s.R, nkb) : 0;
+  return s;
+}
 
 // Shared memory of one CTA: the operand ring (1024-byte aligned for the 128-byte swizzle), then each
 // epilogue warp's two output buffers (32 rows x 16 columns; hi and lo halves for the split), then the
@@ -315,6 +336,45 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nkb_fixed = (SPLIT && !QUAD) ? 3 * ((p.K + BK - 1) / BK) : (p.K + BK - 1) / BK;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
   volatile int *abort_flag = &S.abort_flag;
+  // the work items of this CTA, in the same order for all three roles: tiles with their K chunk range
+  // [kb0, kb1) (all of K but for tail parts) and whether the fp32 tile is added atomically
+  const bool TS = EPI == EPI_F32 && p.tail_split;
+  TailSched ts{0, 0, 0, 0};
+  if (TS) ts = tail_sched(p, (int)gridDim.x, nkb_fixed);
+  struct Item {
+    int nt, rt, m, e, r0, nrows, kb0, kb1;
+    bool atomic;
+  };
+  // 0: no more items, 1: skip (padding tile), 2: item
+  auto item = [&](int it, Item &w) -> int {
+    w.kb0 = 0;
+    w.kb1 = -1;   // the tile's own count (nkb_fixed, or the WG chunk's)
+    w.atomic = false;
+    w.r0 = w.nrows = 0;
+    if (!TS) {
+      const int t = (int)blockIdx.x + it * (int)gridDim.x;
+      if (t >= T) return 0;
+      return tile_coords<MODE>(p, t, w.nt, w.rt, w.m, w.e, w.r0, w.nrows) ? 2 : 1;
+    }
+    int t;
+    if (it < ts.W) {
+      t = (int)blockIdx.x + it * (int)gridDim.x;
+    } else if (it == ts.W && (int)blockIdx.x < ts.R * ts.S) {
+      const int part = (int)blockIdx.x % ts.S;
+      t = ts.W * (int)gridDim.x + (int)blockIdx.x / ts.S;
+      w.kb0 = part * nkb_fixed / ts.S;
+      w.kb1 = (part + 1) * nkb_fixed / ts.S;
+      w.atomic = true;
+    } else {
+      return 0;
+    }
+    w.nt = t % p.n_ntiles;
+    const int rest = t / p.n_ntiles;
+    w.rt = rest % ts.nv;
+    w.m = rest / ts.nv;
+    w.e = p.tile_elem[w.rt];
+    return w.e >= 0 ? 2 : 1;
+  };
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -342,14 +402,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer: one continuous stage ring across this CTA's tiles
       long long g = 0, issued = 0;
-      for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
-        int nt, rt, m, e, r0, nrows;
-        if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
+      for (int it = 0; !*abort_flag; it++) {
+        Item w;
+        const int got = item(it, w);
+        if (got == 0) break;
+        if (got == 1) continue;
+        const int nt = w.nt, rt = w.rt, m = w.m, e = w.e, r0 = w.r0, nrows = w.nrows;
         const int a_mid = p.a_by_member ? m : 0;
         const int b_grp = p.b_by_member ? m * NE + e : e;
         const int nkb_seg = WG ? (nrows + BK - 1) / BK : (p.K + BK - 1) / BK;
-        const int nkb = WG ? 2 * nkb_seg : nkb_fixed;
-        for (int kb = 0; kb < nkb; kb++, g++) {
+        const int nkb = w.kb1 >= 0 ? w.kb1 : (WG ? 2 * nkb_seg : nkb_fixed);
+        for (int kb = w.kb0; kb < nkb; kb++, g++) {
           const int s = (int)(g % STAGES);
           if (g >= STAGES && !mbar_wait(&S.empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
             *abort_flag = 1;
@@ -382,10 +445,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t idesc = F8 ? idesc_e4m3(BM, NT) : idesc_bf16(BM, NT);
       long long g = 0;
       int cnt = 0;
-      for (int t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
-        int nt, rt, m, e, r0, nrows;
-        if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
-        const int nkb = WG ? 2 * ((nrows + BK - 1) / BK) : nkb_fixed;
+      for (int it = 0; !*abort_flag; it++) {
+        Item w;
+        const int got = item(it, w);
+        if (got == 0) break;
+        if (got == 1) continue;
+        const int kb0 = w.kb0;
+        const int nkb = w.kb1 >= 0 ? w.kb1 : (WG ? 2 * ((w.nrows + BK - 1) / BK) : nkb_fixed);
         const int a = cnt & 1;
         if (cnt >= 2 && !mbar_wait(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
           *abort_flag = 1;
@@ -393,7 +459,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(a * TMEM_COLS);
-        for (int kb = 0; kb < nkb; kb++, g++) {
+        for (int kb = kb0; kb < nkb; kb++, g++) {
+          const uint32_t acc0 = kb != kb0 ? 1u : 0u;   // the item's first K step starts the accumulator
           const int s = (int)(g % STAGES);
           if (!mbar_wait(&S.full[s], (uint32_t)((g / STAGES) & 1))) {
             *abort_flag = 1;
@@ -403,16 +470,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
           for (int k = 0; k < KB / 32; k++) {
+            const uint32_t acc = (acc0 | (uint32_t)k) != 0 ? 1u : 0u;
             if (QUAD) {   // hi hi + hi lo + lo hi of this K step
               const uint64_t ah = sdesc<KB>(a0 + 32 * k), al = sdesc<KB>(a0 + BM * KB + 32 * k);
               const uint64_t bh = sdesc<KB>(b0 + 32 * k), bl = sdesc<KB>(b0 + NT * KB + 32 * k);
-              mma_bf16(d, ah, bh, idesc, (kb | k) != 0);
+              mma_bf16(d, ah, bh, idesc, acc);
               mma_bf16(d, ah, bl, idesc, 1u);
               mma_bf16(d, al, bh, idesc, 1u);
             } else if (F8)
-              mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, (kb | k) != 0);
+              mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, acc);
             else
-              mma_bf16(d, sdesc<KB>(a0 + 32 * k), sdesc<KB>(b0 + 32 * k), idesc, (kb | k) != 0);
+              mma_bf16(d, sdesc<KB>(a0 + 32 * k), sdesc<KB>(b0 + 32 * k), idesc, acc);
           }
           mma_commit(&S.empty[s]);
         }
@@ -445,9 +513,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (SPLIT) tma_load_3d(ob + SM::WBUF, &tmX_lo, &S.aux_bar[ew][b], col, y, rt * BM + q * 32);
       aux_out |= 1u << b;
     };
-    for (int t = blockIdx.x; t < T; t += gridDim.x) {
-      int nt, rt, m, e, r0, nrows;
-      if (!tile_coords<MODE>(p, t, nt, rt, m, e, r0, nrows)) continue;
+    for (int it = 0;; it++) {
+      Item w;
+      const int got = item(it, w);
+      if (got == 0) break;
+      if (got == 1) continue;
+      const int nt = w.nt, rt = w.rt, m = w.m, e = w.e;
       const int a = cnt & 1;
       const int n0 = nt * NT;
       const int ncols = min(NT, p.N - n0);
@@ -490,9 +561,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (EPI == EPI_F32) {
           float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4 *>(o + j) = make_float4(v[j] * sc * p.scale, v[j + 1] * sc * p.scale,
-                                                             v[j + 2] * sc * p.scale, v[j + 3] * sc * p.scale);
+          for (int j = 0; j < 16; j += 4) {
+            const float4 f4 = make_float4(v[j] * sc * p.scale, v[j + 1] * sc * p.scale, v[j + 2] * sc * p.scale,
+                                          v[j + 3] * sc * p.scale);
+            if (w.atomic)
+              atomicAdd(reinterpret_cast<float4 *>(o + j), f4);
+            else
+              *reinterpret_cast<float4 *>(o + j) = f4;
+          }
           continue;
         }
         const int b = SM::NBUF == 2 ? (int)(gk & 1) : 0;
