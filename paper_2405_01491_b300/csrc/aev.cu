@@ -477,18 +477,29 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
       W.gacc[t][2] = f * d.z;
     }
     __syncwarp();
-    // ---- angular: one triplet per lane, enumerated by diagonals (k - j = 1, 2, ...) so that the 32
-    // lanes of a batch mostly hold distinct j and distinct k and their shared-memory atomics on
-    // dE/dd rarely collide (row-major order would send a whole batch to the same row j)
+    // ---- angular: one triplet per lane, enumerated by cyclic diagonals: diagonal d (1 <= d <= (n-1)/2)
+    // holds the n pairs {j, (j + d) mod n}, and for even n the last one (d = n/2) the n/2 pairs with
+    // j < n/2, so every pair appears once and within one diagonal the lanes hold distinct j and
+    // distinct k; a batch of 32 spans at most 32/n + 2 diagonals, so an entry's shared-memory atomics on
+    // dE/dd collide at most that often (the short diagonals of a triangle order would pile up to n of
+    // them onto the first entries)
     {
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
       for (int base = 0; base < T; base += 32) {
         const int t = base + lane;
         if (t < T) {
-          int diag, ka;
-          tri_index(t, n, diag, ka);   // diagonal diag + 1 has as many pairs as row diag of the triangle
-          const int ja = ka - diag - 1;
+          const int D = (n - 1) >> 1;   // diagonals of n pairs
+          int d, jc;
+          if (t < D * n) {
+            d = t / n + 1;
+            jc = t - (d - 1) * n;
+          } else {                      // even n: d = n / 2, j < n / 2
+            d = n >> 1;
+            jc = t - D * n;
+          }
+          const int kc = jc + d < n ? jc + d : jc + d - n;
+          const int ja = min(jc, kc), ka = max(jc, kc);   // list order: e(ja) <= e(ka)
           const int p = pair_of(S.ae[ja], S.ae[ka]);
           const float *Gp = G + NRAD + p * 32;
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
@@ -534,12 +545,18 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
           const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
           const float a1 = (dEdr1 - dEdc * c * ir1) * ir1, b1 = dEdc * inv12;
           const float a2 = (dEdr2 - dEdc * c * ir2) * ir2;
-          atomicAdd(&W.gacc[rj1][0], a1 * d1.x + b1 * d2.x);
-          atomicAdd(&W.gacc[rj1][1], a1 * d1.y + b1 * d2.y);
-          atomicAdd(&W.gacc[rj1][2], a1 * d1.z + b1 * d2.z);
-          atomicAdd(&W.gacc[rj2][0], a2 * d2.x + b1 * d1.x);
-          atomicAdd(&W.gacc[rj2][1], a2 * d2.y + b1 * d1.y);
-          atomicAdd(&W.gacc[rj2][2], a2 * d2.z + b1 * d1.z);
+          // entry ja gets g1, entry ka gets g2; the atomics go by the cyclic roles (jc, then kc), which are
+          // distinct within a diagonal
+          const float g1x = a1 * d1.x + b1 * d2.x, g1y = a1 * d1.y + b1 * d2.y, g1z = a1 * d1.z + b1 * d2.z;
+          const float g2x = a2 * d2.x + b1 * d1.x, g2y = a2 * d2.y + b1 * d1.y, g2z = a2 * d2.z + b1 * d1.z;
+          const bool jfirst = jc == ja;
+          const int rjc = jfirst ? rj1 : rj2, rkc = jfirst ? rj2 : rj1;
+          atomicAdd(&W.gacc[rjc][0], jfirst ? g1x : g2x);
+          atomicAdd(&W.gacc[rjc][1], jfirst ? g1y : g2y);
+          atomicAdd(&W.gacc[rjc][2], jfirst ? g1z : g2z);
+          atomicAdd(&W.gacc[rkc][0], jfirst ? g2x : g1x);
+          atomicAdd(&W.gacc[rkc][1], jfirst ? g2y : g1y);
+          atomicAdd(&W.gacc[rkc][2], jfirst ? g2z : g1z);
         }
       }
     }
