@@ -50,16 +50,22 @@ __device__ __forceinline__ float sqrt_fast(float x) {
 template <bool FULL>
 struct NbrStageT {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
-  float rfc[RAD_CAP];            // radial switch fc(r; rc_rad)
   int rj[FULL ? RAD_CAP : 1];    // neighbour atom
-  unsigned char re[RAD_CAP];     // neighbour element
+  // radial switch fc(r; rc_rad) and element per radial entry; once the radial terms are done the adjoint
+  // reuses the space for the triplets' dE/dd per angular entry
+  union {
+    struct {
+      float rfc[RAD_CAP];
+      unsigned char re[RAD_CAP];
+    };
+    float aacc[ANG_CAP][3];
+  };
   unsigned char aidx[ANG_CAP];   // angular entry -> radial entry
   unsigned char ae[ANG_CAP];     // angular entry element
   float afc[ANG_CAP];            // angular switch fc(r; rc_ang)
   float adfc[FULL ? ANG_CAP : 1];  // its derivative
 };
 using NbrStage = NbrStageT<true>;
-constexpr int GSTRIDE = 36;      // padded row of one element pair's 32 angular slots (distinct banks per pair)
 constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
 struct FwdStage {
   NbrStageT<false> nb;
@@ -486,6 +492,8 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
     {
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
+      for (int c = lane; c < 3 * n; c += 32) (&S.aacc[0][0])[c] = 0.f;   // the radial terms are done
+      __syncwarp();
       for (int base = 0; base < T; base += 32) {
         const int t = base + lane;
         if (t < T) {
@@ -545,19 +553,25 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
           const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
           const float a1 = (dEdr1 - dEdc * c * ir1) * ir1, b1 = dEdc * inv12;
           const float a2 = (dEdr2 - dEdc * c * ir2) * ir2;
-          // entry ja gets g1, entry ka gets g2; the atomics go by the cyclic roles (jc, then kc), which are
-          // distinct within a diagonal
+          // entry ja gets g1, entry ka gets g2; the atomics go by the cyclic roles (jc, then kc), distinct
+          // within a diagonal, into rows by angular index (distinct banks for up to 32 entries)
           const float g1x = a1 * d1.x + b1 * d2.x, g1y = a1 * d1.y + b1 * d2.y, g1z = a1 * d1.z + b1 * d2.z;
           const float g2x = a2 * d2.x + b1 * d1.x, g2y = a2 * d2.y + b1 * d1.y, g2z = a2 * d2.z + b1 * d1.z;
           const bool jfirst = jc == ja;
-          const int rjc = jfirst ? rj1 : rj2, rkc = jfirst ? rj2 : rj1;
-          atomicAdd(&W.gacc[rjc][0], jfirst ? g1x : g2x);
-          atomicAdd(&W.gacc[rjc][1], jfirst ? g1y : g2y);
-          atomicAdd(&W.gacc[rjc][2], jfirst ? g1z : g2z);
-          atomicAdd(&W.gacc[rkc][0], jfirst ? g2x : g1x);
-          atomicAdd(&W.gacc[rkc][1], jfirst ? g2y : g1y);
-          atomicAdd(&W.gacc[rkc][2], jfirst ? g2z : g1z);
+          atomicAdd(&S.aacc[jc][0], jfirst ? g1x : g2x);
+          atomicAdd(&S.aacc[jc][1], jfirst ? g1y : g2y);
+          atomicAdd(&S.aacc[jc][2], jfirst ? g1z : g2z);
+          atomicAdd(&S.aacc[kc][0], jfirst ? g2x : g1x);
+          atomicAdd(&S.aacc[kc][1], jfirst ? g2y : g1y);
+          atomicAdd(&S.aacc[kc][2], jfirst ? g2z : g1z);
         }
+      }
+      __syncwarp();
+      for (int t = lane; t < n; t += 32) {   // distinct angular entries are distinct radial entries
+        const int rj = S.aidx[t];
+        W.gacc[rj][0] += S.aacc[t][0];
+        W.gacc[rj][1] += S.aacc[t][1];
+        W.gacc[rj][2] += S.aacc[t][2];
       }
     }
     __syncwarp();
