@@ -258,8 +258,9 @@ struct KScope {
 #define FNN_KERNEL(ctx, name, s) ::fnn::KScope FNN_CAT(kscope_, __LINE__)(ctx, name, s)
 
 // exclusive scan of n int32 values in place; total written to *total_dev (device) when non-null
-fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
-                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev = nullptr);
+fnn_status exclusive_scan(fnn_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev, int32_t *tmp,
+                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev = nullptr, int32_t *out2 = nullptr,
+                          int64_t cap = -1, bool zeroed = false);
 int64_t scan_tmp_needed(int64_t n);
 // work enqueued on ctx->side between side_fork(s) and side_join(s) runs after what s held at the fork
 // and before what s gets after the join

@@ -99,8 +99,9 @@ __global__ void k_scan_add(int32_t *data, int64_t n, const int32_t *tile_sums) {
     if (base + k < n) data[base + k] += add;
 }
 
-// one block for a short array: chunks of SCAN_TILE with a running carry
-__global__ void k_scan_small(int32_t *data, int64_t n, int32_t *total_dev) {
+// one block for a short array: chunks of SCAN_TILE with a running carry (see exclusive_scan for the arguments)
+__global__ void k_scan_small(const int32_t *in, int32_t *out, int32_t *out2, int64_t n, int32_t *total_dev,
+                             int64_t cap, DevStatus *st) {
   int carry = 0;
   for (int64_t c = 0; c < n; c += SCAN_TILE) {
     const int64_t base = c + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -108,19 +109,25 @@ __global__ void k_scan_small(int32_t *data, int64_t n, int32_t *total_dev) {
     int sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-      v[k] = base + k < n ? data[base + k] : 0;
+      v[k] = base + k < n ? in[base + k] : 0;
       sum += v[k];
     }
     int tot;
     int ex = block_excl_scan<SCAN_NT>(sum, &tot) + carry;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-      if (base + k < n) data[base + k] = ex;
+      if (base + k < n) {
+        out[base + k] = ex;
+        if (out2) out2[base + k] = ex;
+      }
       ex += v[k];
     }
     carry += tot;
   }
-  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+  if (threadIdx.x == 0) {
+    if (total_dev) *total_dev = carry;
+    if (cap >= 0 && carry > cap) post_status(st, FNN_E_CAPACITY, carry);
+  }
 }
 
 // Single-pass scan of long arrays (decoupled look-back, Merrill and Garland 2016).  Blocks take tiles
@@ -131,8 +138,10 @@ __global__ void k_scan_small(int32_t *data, int64_t n, int32_t *total_dev) {
 // min(n_max, *n_dev + 1) (a count known only on the device); blocks past it return at once.
 constexpr long long LOOKBACK_LIMIT = 2000000000LL;   // clock64 cycles (about a second) per wait
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(int32_t *data, int64_t n_max, const int32_t *n_dev,
-                                                              int32_t *total_dev, int32_t *scratch, DevStatus *st) {
+__global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(const int32_t *in, int32_t *out, int32_t *out2,
+                                                              int64_t n_max, const int32_t *n_dev,
+                                                              int32_t *total_dev, int64_t cap, int32_t *scratch,
+                                                              DevStatus *st) {
   __shared__ int tile_s, prefix_s;
   unsigned *ticket = reinterpret_cast<unsigned *>(scratch);
   unsigned long long *word = reinterpret_cast<unsigned long long *>(scratch + 2);
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(int32_t *data, int
   int sum = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; k++) {
-    v[k] = base + k < n ? data[base + k] : 0;
+    v[k] = base + k < n ? in[base + k] : 0;
     sum += v[k];
   }
   int agg;
@@ -188,26 +197,37 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(int32_t *data, int
     if (lane == 0) {
       atomicExch(&word[t], (2ull << 32) | (unsigned)(prefix + agg));
       prefix_s = prefix;
-      if (total_dev && base0 + SCAN_TILE >= n) *total_dev = prefix + agg;
+      if (base0 + SCAN_TILE >= n) {   // the last tile
+        if (total_dev) *total_dev = prefix + agg;
+        if (cap >= 0 && prefix + agg > cap) post_status(st, FNN_E_CAPACITY, prefix + agg);
+      }
     }
   }
   __syncthreads();
   ex += prefix_s;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; k++) {
-    if (base + k < n) data[base + k] = ex;
+    if (base + k < n) {
+      out[base + k] = ex;
+      if (out2) out2[base + k] = ex;
+    }
     ex += v[k];
   }
 }
 
 int64_t scan_tmp_needed(int64_t n) { return 2 * ((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
 
-fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total_dev, int32_t *tmp,
-                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev) {
+// out[k] = in[0] + ... + in[k-1] for k < n (in and out may be the same array; so may out2, a second copy),
+// the total to *total_dev, and FNN_E_CAPACITY posted when the total exceeds cap (cap >= 0).  n_dev, when
+// given, bounds n at run time to min(n, *n_dev + 1).  tmp (tmp_len int32) is the single-pass scratch; with
+// zeroed set the caller has cleared it since its last use (no memset node).
+fnn_status exclusive_scan(fnn_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev, int32_t *tmp,
+                          int64_t tmp_len, cudaStream_t s, const int32_t *n_dev, int32_t *out2, int64_t cap,
+                          bool zeroed) {
   if (n <= 0) return FNN_OK;
   if (n <= 2 * SCAN_TILE && !n_dev) {   // one block for short arrays (structure and small cell counts)
     FNN_KERNEL(ctx, "scan_small", s);
-    k_scan_small<<<1, SCAN_NT, 0, s>>>(data, n, total_dev);
+    k_scan_small<<<1, SCAN_NT, 0, s>>>(in, out, out2, n, total_dev, cap, ctx->status);
     return check_launch(ctx, "exclusive_scan");
   }
   const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -215,17 +235,25 @@ fnn_status exclusive_scan(fnn_ctx *ctx, int32_t *data, int64_t n, int32_t *total
     ctx->last_error = "scan scratch too small";
     return FNN_E_INVALID;
   }
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(tmp, 0, (size_t)(2 * nt + 2) * sizeof(int32_t), s));
+  if (!zeroed) FNN_CUDA_TRY(ctx, cudaMemsetAsync(tmp, 0, (size_t)(2 * nt + 2) * sizeof(int32_t), s));
   FNN_KERNEL(ctx, "scan", s);
-  k_scan_single_pass<<<(unsigned)nt, SCAN_NT, 0, s>>>(data, n, n_dev, total_dev, tmp, ctx->status);
+  k_scan_single_pass<<<(unsigned)nt, SCAN_NT, 0, s>>>(in, out, out2, n, n_dev, total_dev, cap, tmp, ctx->status);
   return check_launch(ctx, "exclusive_scan");
 }
 
 // ------------------------------------------------------------------------------------- structures
 // offsets must start at 0, end at N and never decrease: otherwise some atom has no structure
 // (also resets the per-structure bounding boxes, when given, to empty)
-__global__ void k_check_cover(fnn_system sys, DevStatus *st, float *bbox) {
+// (the build's first kernel also clears, when given, meta, the structure cell counts and the scan scratch)
+__global__ void k_check_cover(fnn_system sys, DevStatus *st, float *bbox, int32_t *meta, int32_t *mol_cells,
+                              int32_t *scratch, int64_t n_scratch) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ng = (int64_t)gridDim.x * blockDim.x;
+  if (meta)
+    for (int64_t k = g; k < META_LEN; k += ng) meta[k] = 0;
+  if (scratch)
+    for (int64_t k = g; k < n_scratch; k += ng) scratch[k] = 0;
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= sys.n_mol; m += gridDim.x * blockDim.x) {
+    if (mol_cells) mol_cells[m] = 0;
     int a = sys.mol_offsets[m];
     bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
     if (m == sys.n_mol) ok = ok && a == sys.n_atoms;
@@ -254,21 +282,28 @@ __device__ __forceinline__ void atomic_fmax(float *a, float v) {
 
 // Per atom, all structures at once: its structure (binary search of the offsets), element, checks, and
 // the structure's bounding box (a warp whose atoms share one structure reduces before its atomics).
-__global__ void k_atom_setup(fnn_system sys, int32_t *atom_mol, uint8_t *elem, float *bbox, DevStatus *st) {
+// (also writes atom_mol = -1 and element 0 for an atom outside every structure, and zeroes counts [N+1])
+__global__ void k_atom_setup(fnn_system sys, int32_t *atom_mol, uint8_t *elem, float *bbox, int32_t *counts,
+                             DevStatus *st) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31;
+  if (counts && blockIdx.x == 0 && threadIdx.x == 0) counts[sys.n_atoms] = 0;
   for (int i0 = blockIdx.x * blockDim.x; i0 < sys.n_atoms; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + threadIdx.x;
     int m = -1;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < sys.n_atoms) {
+      if (counts) counts[i] = 0;
       int lo = 0, hi = sys.n_mol;   // last m with offsets[m] <= i
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (sys.mol_offsets[mid] <= i) lo = mid; else hi = mid;
       }
       if (sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
-      if (m >= 0) {
+      if (m < 0) {
+        atom_mol[i] = -1;
+        elem[i] = 0;
+      } else {
         atom_mol[i] = m;
         int e = element_of(sys.Z[i]);
         if (e < 0) {
@@ -503,13 +538,12 @@ __global__ void k_bin(fnn_system sys, const MolGrid *grid, const int32_t *mol_ba
   }
 }
 
-__global__ void k_scatter(int n, const int32_t *cell_of, const int32_t *cell_start, int32_t *cursor,
-                          int32_t *cell_tmp) {
+// cursor[c] starts at cell c's first slot (a copy of the cell starts)
+__global__ void k_scatter(int n, const int32_t *cell_of, int32_t *cursor, int32_t *cell_tmp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int c = cell_of[i];
     if (c < 0) continue;
-    int k = atomicAdd(&cursor[c], 1);
-    cell_tmp[cell_start[c] + k] = i;
+    cell_tmp[atomicAdd(&cursor[c], 1)] = i;
   }
 }
 
@@ -932,6 +966,7 @@ static fnn_status reserve(fnn_nlist *nl, int32_t n_atoms, int32_t n_mol, int64_t
   int64_t t3 = scan_tmp_needed((int64_t)nl->mol_cap + 1);
   if (t2 > need_tmp) need_tmp = t2;
   if (t3 > need_tmp) need_tmp = t3;
+  need_tmp *= 3;   // one region each for the structure, cell and row scans of a build
   if (need_tmp > nl->scan_tmp_len) {
     if ((st = grow(ctx, &nl->scan_tmp, need_tmp))) return st;
     nl->scan_tmp_len = need_tmp;
@@ -1020,27 +1055,28 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   nl->stream = s;
   nl->built = true;
 
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->meta, 0, META_LEN * sizeof(int32_t), s));
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->row_ptr, 0, ((size_t)N + 1) * sizeof(int32_t), s));
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->counts, 0, ((size_t)N + 1) * sizeof(int32_t), s));
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->mol_cells, 0, ((size_t)NM + 1) * sizeof(int32_t), s));
-  if (N > 0) {
-    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
-    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->elem, 0, (size_t)N, s));
-  }
+  // cells are bounded by 2N + n_mol + 1 by construction (k_mol_grid caps each structure at max(1, 2n));
+  // the structure, cell and row scans each have their own third of the scratch, all cleared by the first
+  // kernel
+  const int64_t cells_bound = 2LL * N + NM + 1;
+  const int64_t third = nl->scan_tmp_len / 3;
+  int32_t *tmp_mol = nl->scan_tmp, *tmp_cells = nl->scan_tmp + third, *tmp_rows = nl->scan_tmp + 2 * third;
   int cover_blocks = (NM + 256) / 256 < 256 ? (NM + 256) / 256 : 256;
   {
     FNN_KERNEL(ctx, "check_cover", s);
-    k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status, nl->bbox);
+    k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status, nl->bbox, nl->meta, nl->mol_cells, nl->scan_tmp,
+                                               3 * third);
   }
   if (N > 0) {
     int ab = (N + 255) / 256;
     if (ab > 8 * ctx->num_sms) ab = 8 * ctx->num_sms;
     FNN_KERNEL(ctx, "atom_setup", s);
-    k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, ctx->status);
+    k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, nl->counts, ctx->status);
+  } else {
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->counts, 0, sizeof(int32_t), s));
   }
-  // species-sorted, 128-row padded order for the networks: needs only the elements, so it runs on the
-  // side stream while the cells and pairs are built
+  // species-sorted order for the networks: needs only the elements, so it runs on the side stream while
+  // the cells and pairs are built
   if ((st = side_fork(ctx, s))) return st;
   {
     cudaStream_t ss = ctx->side;
@@ -1063,27 +1099,23 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     FNN_KERNEL(ctx, "mol_grid", s);
     k_mol_grid<<<(NM + 127) / 128, 128, 0, s>>>(*sys, nl->bbox, nl->grid, nl->mol_cells, R, ctx->status);
   }
-  if ((st = exclusive_scan(ctx, nl->mol_cells, NM + 1, nl->meta + META_CELLS, nl->scan_tmp, nl->scan_tmp_len, s)))
+  if ((st = exclusive_scan(ctx, nl->mol_cells, nl->mol_cells, NM + 1, nl->meta + META_CELLS, tmp_mol, third, s,
+                           nullptr, nullptr, -1, true)))
     return st;
-  // cells are bounded by 2N + n_mol + 1 by construction (k_mol_setup caps each structure at max(1, 2n))
-  int64_t cells_bound = 2LL * N + NM + 1;
   FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_start, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
   if (N > 0) {
     int tb = 256, nb = (N + tb - 1) / tb;
     {
       FNN_KERNEL(ctx, "bin", s);
       k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count);
     }
-    FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->cell_start, nl->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
-                                      cudaMemcpyDeviceToDevice, s));
-    if ((st = exclusive_scan(ctx, nl->cell_start, cells_bound + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s,
-                             nl->meta + META_CELLS)))
+    // cell starts (over the cells that exist), and the same starts back into the counts as the scatter's cursors
+    if ((st = exclusive_scan(ctx, nl->cell_count, nl->cell_start, cells_bound + 1, nullptr, tmp_cells, third, s,
+                             nl->meta + META_CELLS, nl->cell_count, -1, true)))
       return st;
-    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
     {
       FNN_KERNEL(ctx, "scatter", s);
-      k_scatter<<<nb, tb, 0, s>>>(N, nl->cell_of, nl->cell_start, nl->cell_count, nl->cell_tmp);
+      k_scatter<<<nb, tb, 0, s>>>(N, nl->cell_of, nl->cell_count, nl->cell_tmp);
     }
     int wb = (int)((cells_bound * 32 + 255) / 256);
     if (wb > 16 * ctx->num_sms) wb = 16 * ctx->num_sms;
@@ -1102,21 +1134,18 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
                                        nl->cell_atoms, nl->cell_pos, pc, nl->counts, nl->stage_nbr, nl->stage_shift,
                                        nl->meta);
     }
-    FNN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->row_ptr, nl->counts, ((size_t)N + 1) * sizeof(int32_t),
-                                      cudaMemcpyDeviceToDevice, s));
-    if ((st = exclusive_scan(ctx, nl->row_ptr, (int64_t)N + 1, nullptr, nl->scan_tmp, nl->scan_tmp_len, s)))
+    // row pointers; the total is the entry count (FNN_E_CAPACITY beyond the list's capacity)
+    if ((st = exclusive_scan(ctx, nl->counts, nl->row_ptr, (int64_t)N + 1, nl->meta + META_NNZ, tmp_rows, third, s,
+                             nullptr, nullptr, nl->capacity, true)))
       return st;
-    {
-      FNN_KERNEL(ctx, "check_capacity", s);
-      k_check_capacity<<<1, 1, 0, s>>>(nl->row_ptr, N, nl->capacity, nl->meta, ctx->status);
-    }
     {
       FNN_KERNEL(ctx, "pairs_compact", s);
       k_pairs_compact<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
                                          nl->cell_atoms, nl->cell_pos, pc, nl->row_ptr, nl->stage_nbr, nl->stage_shift,
-                                         nl->elem,
-                                         nl->nbr, nl->shift, nl->capacity, nl->meta);
+                                         nl->elem, nl->nbr, nl->shift, nl->capacity, nl->meta);
     }
+  } else {
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->row_ptr, 0, sizeof(int32_t), s));
   }
   if ((st = side_join(ctx, s))) return st;
   return check_launch(ctx, "fnn_build_neighbors");
@@ -1265,7 +1294,7 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     FNN_STATIC_TRY(cudaMemsetAsync(S->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
     FNN_STATIC_TRY(cudaMemsetAsync(S->elem, 0, (size_t)N, s));
   }
-  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status, nullptr);
+  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status, nullptr, nullptr, nullptr, nullptr, 0);
   k_mol_setup<<<NM, SETUP_NT, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->elem, R, &S->status);
   FNN_STATIC_TRY(scan_in_place(S->mol_cells, NM + 1, S->meta + META_CELLS, S->scan_tmp, s));
   FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
@@ -1276,8 +1305,9 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     FNN_STATIC_TRY(cudaMemcpyAsync(S->cell_start, S->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
                                    cudaMemcpyDeviceToDevice, s));
     FNN_STATIC_TRY(scan_in_place(S->cell_start, cells_bound + 1, nullptr, S->scan_tmp, s));
-    FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
-    k_scatter<<<nb, 256, 0, s>>>(N, S->cell_of, S->cell_start, S->cell_count, S->cell_tmp);
+    FNN_STATIC_TRY(cudaMemcpyAsync(S->cell_count, S->cell_start, ((size_t)cells_bound + 1) * sizeof(int32_t),
+                                   cudaMemcpyDeviceToDevice, s));
+    k_scatter<<<nb, 256, 0, s>>>(N, S->cell_of, S->cell_count, S->cell_tmp);
     k_sort_cells<<<(int)((cells_bound * 32 + 255) / 256), 256, 0, s>>>(
         S->meta, S->cell_start, S->cell_tmp, reinterpret_cast<const float4 *>(sys->pos), S->cell_atoms, S->cell_pos);
     PredConst pc{R * R, (float)(R * R), (float)R};
