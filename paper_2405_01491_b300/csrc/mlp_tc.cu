@@ -71,6 +71,8 @@ struct Half {
   CUtensorMap eH1, eH2, eG3, eG2, eG1;         // epilogue maps: 32-row x 16-column pieces, unswizzled
   // 64-byte-row (64-byte swizzle) operand maps (the split first-layer input gradient)
   CUtensorMap qW1T, qG1;
+  // weights with 64-row boxes: the column strips of a product's partial last wave
+  CUtensorMap sW1, sW2, sW2T;
 };
 
 // e4m3 operands of the FP8 form and their scales
@@ -108,6 +110,7 @@ TcState *state(fnn_ctx *ctx) {
 // repeat any valid map).
 struct Maps {
   const CUtensorMap *A, *B, *A_lo, *B_lo, *O, *O_lo, *X, *X_lo;
+  const CUtensorMap *Bs = nullptr, *Bs_lo = nullptr;   // B with strip-high boxes (tail column strips)
 };
 
 // zero the output tiles a tail-split EPI_F32 launch of grid G will add into (tail_sched): one block per tile
@@ -158,8 +161,9 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, di
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_umma<NT, EPI, MODE, QUAD, KB><<<grid, tc::THREADS, sm, s>>>(*mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X,
-                                                          *mp.X_lo, a);
+  tc::k_umma<NT, EPI, MODE, QUAD, KB><<<grid, tc::THREADS, sm, s>>>(
+      *mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X, *mp.X_lo, mp.Bs ? *mp.Bs : *mp.B,
+      mp.Bs_lo ? *mp.Bs_lo : *mp.B_lo, a);
   return check_launch(ctx, name);
 }
 
@@ -303,7 +307,10 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
     const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const CUtensorMapSwizzle S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     ok = ok && encode3d(&H.qW1T, H.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2,
-                        32, 256, 1, BF, S64);
+                        32, 256, 1, BF, S64) &&
+         encode3d(&H.sW1, H.W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 64, 1) &&
+         encode3d(&H.sW2, H.W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, 64, 1) &&
+         encode3d(&H.sW2T, H.W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, 64, 1);
     if (!ok) {
       ctx->last_error = "cuTensorMapEncodeTiled failed for the weight maps";
       return FNN_E_CUDA;
@@ -471,22 +478,28 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
   a.M = M;
+  // the partial last wave of the bias + CELU and CELU' products is cut into 64-column strips
+  a.tail_nsplit = 1; a.nsub_w = 64; a.meta = nl->meta;
   // L1: all members at once; the n tile is the member
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
   a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true,
-           ctx, nm[0], {&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1}, nullptr, a,
-           dim3(M, tiles, 1), s)))
-    return st;
+  {
+    Maps m1{&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1};
+    m1.Bs = &H.sW1; m1.Bs_lo = &L.sW1;
+    if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true, ctx, nm[0], m1, nullptr, a, dim3(M, tiles, 1), s)))
+      return st;
+  }
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
   a.o_xm = 0; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
-  if ((st = launch_q<192, tc::EPI_BIAS_CELU, MODE>(true,
-           ctx, nm[1], {&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2}, nullptr, a,
-           dim3(1, tiles, M), s)))
-    return st;
+  {
+    Maps m2{&H.mH1, &H.mW2, &L.mH1, &L.mW2, &H.eH2, &L.eH2, &H.eH2, &L.eH2};
+    m2.Bs = &H.sW2; m2.Bs_lo = &L.sW2;
+    if ((st = launch_q<192, tc::EPI_BIAS_CELU, MODE>(true, ctx, nm[1], m2, nullptr, a, dim3(1, tiles, M), s)))
+      return st;
+  }
   // L3 + output layer and the L3 backward g2 = (g3 W3) CELU'(h2) in one kernel (g3 stays in TMEM)
   {
     tc::L3Args l{};
@@ -511,9 +524,12 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
   a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;
   // (two aux buffers per warp keep its CELU' rows in flight; four-tile stages would leave room for one)
-  if ((st = launch<256, tc::EPI_DCELU, MODE>(
-           ctx, nm[4], {&H.mG2, &H.mW2T, &L.mG2, &L.mW2T, &H.eG1, &L.eG1, &H.eH1, &L.eH1}, a, dim3(1, tiles, M), s)))
-    return st;
+  {
+    Maps m4{&H.mG2, &H.mW2T, &L.mG2, &L.mW2T, &H.eG1, &L.eG1, &H.eH1, &L.eH1};
+    m4.Bs = &H.sW2T; m4.Bs_lo = &L.sW2T;
+    if ((st = launch<256, tc::EPI_DCELU, MODE>(ctx, nm[4], m4, a, dim3(1, tiles, M), s))) return st;
+  }
+  a.tail_nsplit = 0;
   if ((st = side_join(ctx, s))) return st;
   // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint; the partial last wave is
   // split along K and added atomically into the tiles zeroed above

@@ -219,7 +219,10 @@ struct Args {
   // EPI_F32 only: the tiles of the final partial wave are split along K over all CTAs and their parts
   // added atomically into the output, which the caller zeroes first (tail_sched gives the tiles)
   int tail_split;
-  const int32_t *meta;         // META_NPAD bounds the valid row tiles when tail_split is set
+  const int32_t *meta;         // META_NPAD bounds the valid row tiles when tail_split or tail_nsplit is set
+  // other epilogues: the partial wave's tiles are cut into NT / nsub_w column strips (when there are CTAs
+  // for all of them), B read through the map with nsub_w-row boxes
+  int tail_nsplit, nsub_w;
 };
 
 // Persistent schedule of a tail-split launch over the valid tiles (row tiles below META_NPAD), grid G:
@@ -236,6 +239,17 @@ __device__ __forceinline__ TailSched tail_sched(const Args &p, int G, int nkb) {
   s.W = Tv / G;
   s.R = Tv - s.W * G;
   s.S = s.R ? min(G / s.R, nkb) : 0;
+  return s;
+}
+// the same waves, the R partial-wave tiles cut into S = NT / nsub_w column strips when R S <= G (else S = 1)
+__device__ __forceinline__ TailSched tail_sched_n(const Args &p, int G, int NTc) {
+  TailSched s;
+  s.nv = min(p.meta[META_NPAD] / BM, p.n_rowtiles);
+  const int Tv = p.n_ntiles * s.nv * p.n_members;
+  s.W = Tv / G;
+  s.R = Tv - s.W * G;
+  const int S = NTc / p.nsub_w;
+  s.S = s.R * S <= G ? S : 1;
   return s;
 }
 
@@ -320,7 +334,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
            const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
            const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo,
-           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo, Args p) {
+           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo,
+           const __grid_constant__ CUtensorMap tmBs, const __grid_constant__ CUtensorMap tmBs_lo, Args p) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "UMMA N for M = 128");
   static_assert(!QUAD || MODE == MODE_SPLIT, "four-tile stages are a form of the split");
   static_assert(KB == BKB || QUAD, "64-byte rows only with four-tile stages");
@@ -339,11 +354,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   // the work items of this CTA, in the same order for all three roles: tiles with their K chunk range
   // [kb0, kb1) (all of K but for tail parts) and whether the fp32 tile is added atomically
   const bool TS = EPI == EPI_F32 && p.tail_split;
+  const bool TN = EPI != EPI_F32 && EPI != EPI_ATOMIC && EPI != EPI_L3 && !WG && p.tail_nsplit;
   TailSched ts{0, 0, 0, 0};
   if (TS) ts = tail_sched(p, (int)gridDim.x, nkb_fixed);
+  if (TN) ts = tail_sched_n(p, (int)gridDim.x, NT);
   struct Item {
     int nt, rt, m, e, r0, nrows, kb0, kb1;
     bool atomic;
+    int c0, cw;   // the item's columns of its tile: [c0, c0 + cw)
   };
   // 0: no more items, 1: skip (padding tile), 2: item
   auto item = [&](int it, Item &w) -> int {
@@ -351,7 +369,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     w.kb1 = -1;   // the tile's own count (nkb_fixed, or the WG chunk's)
     w.atomic = false;
     w.r0 = w.nrows = 0;
-    if (!TS) {
+    w.c0 = 0;
+    w.cw = NT;
+    if (!TS && !TN) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
       if (t >= T) return 0;
       return tile_coords<MODE>(p, t, w.nt, w.rt, w.m, w.e, w.r0, w.nrows) ? 2 : 1;
@@ -362,9 +382,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (it == ts.W && (int)blockIdx.x < ts.R * ts.S) {
       const int part = (int)blockIdx.x % ts.S;
       t = ts.W * (int)gridDim.x + (int)blockIdx.x / ts.S;
-      w.kb0 = part * nkb_fixed / ts.S;
-      w.kb1 = (part + 1) * nkb_fixed / ts.S;
-      w.atomic = true;
+      if (TS) {   // a K range, added atomically
+        w.kb0 = part * nkb_fixed / ts.S;
+        w.kb1 = (part + 1) * nkb_fixed / ts.S;
+        w.atomic = true;
+      } else if (ts.S > 1) {   // a column strip
+        w.c0 = part * p.nsub_w;
+        w.cw = p.nsub_w;
+      }
     } else {
       return 0;
     }
@@ -418,12 +443,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + NT) * KB));
+          const bool strip = w.cw < NT;   // B rows nt NT + c0 .. + cw through the strip maps
+          const CUtensorMap *mb = strip ? &tmBs : &tmB, *mb_lo = strip ? &tmBs_lo : &tmB_lo;
+          const int by = nt * NT + w.c0;
+          mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + w.cw) * KB));
           if (QUAD) {   // hi and lo of both operands for one K chunk
             tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
             tma_load_3d(S.A[s] + BM * KB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
-            tma_load_3d(S.B[s], &tmB, &S.full[s], kb * BK, nt * NT, b_grp);
-            tma_load_3d(S.B[s] + NT * KB, &tmB_lo, &S.full[s], kb * BK, nt * NT, b_grp);
+            tma_load_3d(S.B[s], mb, &S.full[s], kb * BK, by, b_grp);
+            tma_load_3d(S.B[s] + NT * KB, mb_lo, &S.full[s], kb * BK, by, b_grp);
           } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
             const int term = kb / nkb_seg, x = r0 + (kb - term * nkb_seg) * BK;
             tma_load_3d(S.A[s], term ? &tmA_lo : &tmA, &S.full[s], x, rt * BM, m);
@@ -431,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           } else {
             const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
             tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
-            tma_load_3d(S.B[s], seg == 1 ? &tmB_lo : &tmB, &S.full[s], kk * BK, nt * NT, b_grp);
+            tma_load_3d(S.B[s], seg == 1 ? mb_lo : mb, &S.full[s], kk * BK, by, b_grp);
           }
           issued = g + 1;
         }
@@ -452,6 +480,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (got == 1) continue;
         const int kb0 = w.kb0;
         const int nkb = w.kb1 >= 0 ? w.kb1 : (WG ? 2 * ((w.nrows + BK - 1) / BK) : nkb_fixed);
+        const uint32_t id = w.cw == NT ? idesc : (F8 ? idesc_e4m3(BM, w.cw) : idesc_bf16(BM, w.cw));
         const int a = cnt & 1;
         if (cnt >= 2 && !mbar_wait(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
           *abort_flag = 1;
@@ -474,13 +503,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (QUAD) {   // hi hi + hi lo + lo hi of this K step
               const uint64_t ah = sdesc<KB>(a0 + 32 * k), al = sdesc<KB>(a0 + BM * KB + 32 * k);
               const uint64_t bh = sdesc<KB>(b0 + 32 * k), bl = sdesc<KB>(b0 + NT * KB + 32 * k);
-              mma_bf16(d, ah, bh, idesc, acc);
-              mma_bf16(d, ah, bl, idesc, 1u);
-              mma_bf16(d, al, bh, idesc, 1u);
+              mma_bf16(d, ah, bh, id, acc);
+              mma_bf16(d, ah, bl, id, 1u);
+              mma_bf16(d, al, bh, id, 1u);
             } else if (F8)
-              mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, acc);
+              mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), id, acc);
             else
-              mma_bf16(d, sdesc<KB>(a0 + 32 * k), sdesc<KB>(b0 + 32 * k), idesc, acc);
+              mma_bf16(d, sdesc<KB>(a0 + 32 * k), sdesc<KB>(b0 + 32 * k), id, acc);
           }
           mma_commit(&S.empty[s]);
         }
@@ -524,10 +553,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int ncols = min(NT, p.N - n0);
       nt_cur = nt;
       // the first aux piece of the tile travels while its MMAs run
-      if (EPI == EPI_DCELU && lane == 0 && 16 * part < ncols) {
+      const int cend = min(ncols, w.c0 + w.cw);   // the item's columns (tile coordinates)
+      if (EPI == EPI_DCELU && lane == 0 && w.c0 + 16 * part < cend) {
         if (SM::NBUF == 2 && gk >= 2) bulk_wait_read1();
         if (SM::NBUF == 1 && gk >= 1) bulk_wait_read0();
-        load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, 16 * part, rt, m);
+        load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, w.c0 + 16 * part, rt, m);
       }
       bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
@@ -545,9 +575,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int oy = p.o_y == 1 ? m : p.o_y == 2 ? nt : 0;
       bool abort_now = false;
 #pragma unroll 1
-      for (int c = 16 * part; c < NT; c += 64) {
+      for (int c = w.c0 + 16 * part; c < w.c0 + w.cw; c += 64) {
         float v[16];
-        tmem_ld16(tbase + c, v);
+        tmem_ld16(tbase + (c - w.c0), v);
         if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
         if (EPI == EPI_ATOMIC) {   // weight-gradient tile: row o of dW, columns n0 + c ..
           const int o = rt * BM + r;
@@ -673,7 +703,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_store_3d(&tmO, ob, x, oy, rt * BM + q * 32);
           if (SPLIT) tma_store_3d(&tmO_lo, ob + SM::WBUF, x, oy, rt * BM + q * 32);
           bulk_commit();
-          if (EPI == EPI_DCELU && c + 64 < ncols) {   // this warp's next aux piece into the other buffer
+          if (EPI == EPI_DCELU && c + 64 < cend) {   // this warp's next aux piece into the other buffer
             if (SM::NBUF == 2) {
               bulk_wait_read1();
               load_aux(b ^ 1, c + 64, rt, m);
