@@ -666,42 +666,45 @@ template <typename InT>
 __global__ void __launch_bounds__(256) k_transpose_bf16(int rows, int F, const InT *in, long long ld, long long ms,
                                                         __nv_bfloat16 *outT, long long R, __nv_bfloat16 *out_rm,
                                                         long long ld_out) {
-  __shared__ __nv_bfloat16 tile[64][72];   // [row][feature], rows padded to 144 bytes
+  __shared__ alignas(16) __nv_bfloat16 tile[64][72];   // [row][feature], rows padded to 144 bytes
   const int f0 = blockIdx.x * 64, r0 = blockIdx.y * 64, m = blockIdx.z;
-  constexpr int V = 16 / (int)sizeof(InT);   // elements per 16-byte load
-  // load: 64 rows x 64 features
-  for (int k = threadIdx.x; k < 64 * (64 / V); k += 256) {
-    const int rr = k / (64 / V), fv = (k % (64 / V)) * V;
+  // load: 64 rows x 8 vectors of 8 features, each one 16-byte shared store
+  for (int k = threadIdx.x; k < 64 * 8; k += 256) {
+    const int rr = k >> 3, fv = (k & 7) * 8;
     const int r = r0 + rr, f = f0 + fv;
-    alignas(16) __nv_bfloat16 b[V];
+    alignas(16) __nv_bfloat16 b[8];
     if (r < rows && f < F) {
       const InT *src = in + (size_t)r * ld + m * ms + f;
       if constexpr (std::is_same<InT, float>::value) {
-        const float4 x = *reinterpret_cast<const float4 *>(src);
+        const float4 x = *reinterpret_cast<const float4 *>(src), y = *reinterpret_cast<const float4 *>(src + 4);
         b[0] = __float2bfloat16(x.x); b[1] = __float2bfloat16(x.y);
         b[2] = __float2bfloat16(x.z); b[3] = __float2bfloat16(x.w);
-        if (out_rm) *reinterpret_cast<uint2 *>(out_rm + (size_t)r * ld_out + m * ms + f) = *reinterpret_cast<uint2 *>(b);
+        b[4] = __float2bfloat16(y.x); b[5] = __float2bfloat16(y.y);
+        b[6] = __float2bfloat16(y.z); b[7] = __float2bfloat16(y.w);
+        if (out_rm) *reinterpret_cast<uint4 *>(out_rm + (size_t)r * ld_out + m * ms + f) = *reinterpret_cast<uint4 *>(b);
       } else {
         *reinterpret_cast<uint4 *>(b) = *reinterpret_cast<const uint4 *>(src);
       }
     } else {
-#pragma unroll
-      for (int j = 0; j < V; j++) b[j] = __float2bfloat16(0.f);
+      *reinterpret_cast<uint4 *>(b) = make_uint4(0u, 0u, 0u, 0u);
     }
-#pragma unroll
-    for (int j = 0; j < V; j++) tile[rr][fv + j] = b[j];
+    *reinterpret_cast<uint4 *>(&tile[rr][fv]) = *reinterpret_cast<const uint4 *>(b);
   }
   __syncthreads();
-  // store: 64 features x 64 rows, eight rows per 16-byte store
-  for (int k = threadIdx.x; k < 64 * 8; k += 256) {
-    const int ff = k / 8, rv = (k % 8) * 8;
-    const int f = f0 + ff, r = r0 + rv;
-    if (f >= F || r >= rows) continue;
-    alignas(16) __nv_bfloat16 b[8];
+  // store: thread (feature pair h, rows rv .. rv + 7) reads eight bf16-pair words (lanes h = 0 .. 31 of a
+  // warp hit distinct banks), splits them into the two features' eight rows, and writes 16 bytes each
+  const int h = threadIdx.x & 31, rv = (threadIdx.x >> 5) * 8;
+  const int f = f0 + 2 * h, r = r0 + rv;
+  if (r >= rows || f >= F) return;
+  uint32_t wd[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) b[j] = tile[rv + j][ff];
-    *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f) * R + r) = *reinterpret_cast<const uint4 *>(b);
-  }
+  for (int j = 0; j < 8; j++) wd[j] = *reinterpret_cast<const uint32_t *>(&tile[rv + j][2 * h]);
+  const uint4 even = make_uint4(__byte_perm(wd[0], wd[1], 0x5410), __byte_perm(wd[2], wd[3], 0x5410),
+                                __byte_perm(wd[4], wd[5], 0x5410), __byte_perm(wd[6], wd[7], 0x5410));
+  const uint4 odd = make_uint4(__byte_perm(wd[0], wd[1], 0x7632), __byte_perm(wd[2], wd[3], 0x7632),
+                               __byte_perm(wd[4], wd[5], 0x7632), __byte_perm(wd[6], wd[7], 0x7632));
+  *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f) * R + r) = even;
+  if (f + 1 < F) *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f + 1) * R + r) = odd;
 }
 
 __device__ __forceinline__ float dcelu_hb(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
