@@ -639,7 +639,7 @@ struct AevTanArgs {
   StageArgs sa;
   AevParams P;
   const float *V;         // [N][3] displacement field
-  float *out;             // [rows][1008]
+  void *out;              // [rows][1008], float or bf16
   const int32_t *inv;     // padded row -> atom; NULL = rows are atoms
   const int32_t *meta;
   int n_atoms;
@@ -648,6 +648,7 @@ struct AevTanArgs {
 
 constexpr int TAN_WARPS = 2;   // 15 KB of staging per warp: two warps keep the block under 48 KB
 
+template <typename OutT>
 __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
   __shared__ TanStage smem[TAN_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -657,12 +658,12 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   int wg = blockIdx.x * TAN_WARPS + wl, nw = gridDim.x * TAN_WARPS;
   for (int row = wg; row < nrows; row += nw) {
-    float *out = A.out + (size_t)row * NAEV;
+    OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
     int i = A.inv ? A.inv[row] : row;
     int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
     bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st);
     if (!ok) {
-      for (int c = lane; c < NAEV; c += 32) out[c] = 0.f;
+      for (int c = lane; c < NAEV; c += 32) store_out<OutT>(out + c, 0.f, 1.f);
       __syncwarp();
       continue;
     }
@@ -691,7 +692,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
           acc += __expf(-P.eta_r * dr * dr) * (-2.f * P.eta_r * dr * ft.x + ft.y);
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
-        if (lane < 16) out[q * NSR + k] = 0.25f * acc;
+        if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc, 1.f);
       }
     }
     // ---- angular
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
       }
       if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
       __syncwarp();
-      for (int c = lane; c < NPAIR * 32; c += 32) out[NRAD + c] = W.acc[c];
+      for (int c = lane; c < NPAIR * 32; c += 32) store_out<OutT>(out + NRAD + c, W.acc[c], 1.f);
     }
     __syncwarp();
   }
@@ -864,8 +865,9 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   return check_launch(ctx, "aev_adjoint");
 }
 
-fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
-                              const int32_t *inv, cudaStream_t s) {
+template <typename OutT>
+static fnn_status tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, OutT *out,
+                          const int32_t *inv, cudaStream_t s) {
   AevTanArgs a;
   a.sa = stage_args(sys, nl);
   a.P = ctx->aev;
@@ -879,9 +881,18 @@ fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_tangent", s);
-    k_aev_tangent<<<2 * aev_grid(ctx, rows, 12), TAN_WARPS * 32, 0, s>>>(a);
+    k_aev_tangent<OutT><<<2 * aev_grid(ctx, rows, 12), TAN_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_tangent");
+}
+
+fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
+                              const int32_t *inv, cudaStream_t s) {
+  return tangent<float>(ctx, sys, nl, V, out, inv, s);
+}
+fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
+                                   __nv_bfloat16 *out, const int32_t *inv, cudaStream_t s) {
+  return tangent<__nv_bfloat16>(ctx, sys, nl, V, out, inv, s);
 }
 
 }  // namespace fnn

@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/fnn.h is).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -274,6 +275,8 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
                               const int32_t *inv, float *F, double *virial, cudaStream_t s);
 fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
                               const int32_t *inv, cudaStream_t s);
+fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
+                                   __nv_bfloat16 *out, const int32_t *inv, cudaStream_t s);
 fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s);
 fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
                      cudaStream_t s);

@@ -69,10 +69,12 @@ struct Half {
   __nv_bfloat16 *aev = nullptr, *h1 = nullptr, *h2 = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
   CUtensorMap mAev, mH1, mH2, mG3, mG2, mG1;   // operand maps (128-byte rows, swizzled)
   CUtensorMap eH1, eH2, eG3, eG2, eG1;         // epilogue maps: 32-row x 16-column pieces, unswizzled
-  // 64-byte-row (64-byte swizzle) operand maps (the split first-layer input gradient)
-  CUtensorMap qW1T, qG1;
+  // 64-byte-row (64-byte swizzle) operand maps (the split first-layer input gradient, the fused third layer)
+  CUtensorMap qW1T, qG1, qW3, qW3T, qH2;
   // weights with 64-row boxes: the column strips of a product's partial last wave
   CUtensorMap sW1, sW2, sW2T;
+  // 64 rows x 64 features (MN-major operands of the weight gradients)
+  CUtensorMap wAev, wH1, wH2;
 };
 
 // e4m3 operands of the FP8 form and their scales
@@ -127,20 +129,20 @@ __global__ void k_zero_tail(tc::Args p, int G, int nkb, int NT) {
 }
 
 // fused third layer (tc_fused.cuh): persistent over the (row tile, member) grid
-template <int MODE>
+template <int MODE, int KB>
 fnn_status launch_l3_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *const maps[10], tc::L3Args a,
                           cudaStream_t s) {
   const long long T = (long long)a.n_rowtiles * a.n_members;
   if (T == 0) return FNN_OK;
   dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
   static bool attr_set = false;
-  const size_t sm = tc::l3_smem_bytes<MODE>();
+  const size_t sm = tc::l3_smem_bytes<MODE, KB>();
   if (!attr_set) {
-    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_l3_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_l3_pair<MODE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set = true;
   }
   FNN_KERNEL(ctx, name, s);
-  tc::k_l3_pair<MODE><<<grid, tc::THREADS, sm, s>>>(*maps[0], *maps[1], *maps[2], *maps[3], *maps[4], *maps[5],
+  tc::k_l3_pair<MODE, KB><<<grid, tc::THREADS, sm, s>>>(*maps[0], *maps[1], *maps[2], *maps[3], *maps[4], *maps[5],
                                                     *maps[6], *maps[7], *maps[8], *maps[9], a);
   return check_launch(ctx, name);
 }
@@ -308,6 +310,8 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
     const CUtensorMapSwizzle S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     ok = ok && encode3d(&H.qW1T, H.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2,
                         32, 256, 1, BF, S64) &&
+         encode3d(&H.qW3, H.W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 32, H3, 1, BF, S64) &&
+         encode3d(&H.qW3T, H.W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 32, H2, 1, BF, S64) &&
          encode3d(&H.sW1, H.W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 64, 1) &&
          encode3d(&H.sW2, H.W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, 64, 1) &&
          encode3d(&H.sW2T, H.W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, 64, 1);
@@ -354,7 +358,11 @@ static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
     const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE, S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     ok = ok && encode3d(&H.qG1, H.g1, (uint64_t)M * H1, 1, R, (uint64_t)M * H1 * 2, (uint64_t)M * H1 * 2, 32, 1, 128,
-                        BF, S64);
+                        BF, S64) &&
+         encode3d(&H.qH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 32, 1, 128, BF, S64) &&
+         encode3d(&H.wAev, H.aev, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 64) &&
+         encode3d(&H.wH1, H.h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 64, 1, 64) &&
+         encode3d(&H.wH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 64, 1, 64);
     ok = ok && encode3d(&H.eH1, H.h1, H1, M, R, H1 * 2, (uint64_t)M * H1 * 2, 16, 1, 32, BF, NS) &&
          encode3d(&H.eH2, H.h2, H2, M, R, H2 * 2, (uint64_t)M * H2 * 2, 16, 1, 32, BF, NS) &&
          encode3d(&H.eG3, H.g3, H3, M, R, H3 * 2, (uint64_t)M * H3 * 2, 16, 1, 32, BF, NS) &&
@@ -505,8 +513,9 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
     tc::L3Args l{};
     l.n_rowtiles = (int)tiles; l.n_members = M; l.tile_elem = nl->tile_elem;
     l.b3 = w.b3; l.w4 = w.w4; l.ypart = ctx->ws.ypart; l.M = M; l.scale = 1.f / (float)M; l.st = ctx->status;
-    const CUtensorMap *maps[10] = {&H.mH2, &L.mH2, &H.mW3, &L.mW3, &H.mW3T, &L.mW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
-    if ((st = launch_l3_pair<MODE>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
+    // (64-byte operand rows: twice the ring stages for the same bytes in flight)
+    const CUtensorMap *maps[10] = {&H.qH2, &L.qH2, &H.qW3, &L.qW3, &H.qW3T, &L.qW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
+    if ((st = launch_l3_pair<MODE, 64>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
   }
   // side stream: the structure energies, and zeros for the first-layer input gradient's tail tiles
   tc::Args az{};
@@ -654,58 +663,10 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
 //   tangent   hd_l = CELU'(h_l) (hd_{l-1} W_l^T), hd_0 = J dL/dF         (EPI_DCELU, aux h_l)
 //   reverse   raw gb_{l-1} = gbz_l W_l, g_{l-1} = gz_l W_l               (EPI_PLAIN)
 //             gbz = CELU'(h) gb, gz = CELU'(h) g + (CELU''/CELU')(h) hd gb   (k_act_reverse_bf16)
-//   weights   dW_l += gbz_l^T hd_{l-1} + gz_l^T h_{l-1}: K runs over each element's rows, with both
-//             factors stored row-contiguous ([member][feature][row], k_transpose) (MODE_WG, EPI_ATOMIC)
+//   weights   dW_l += gbz_l^T hd_{l-1} + gz_l^T h_{l-1}: K runs over each element's rows; both factors are
+//             read in place as MN-major operands (64 rows x 64 features per box) (MODE_WG, EPI_ATOMIC)
 
 namespace {
-
-// [rows][member stride ms, F features] (float or bf16) -> bf16 [member][F][R] (and, for float input, a
-// bf16 row-major copy); 64 x 64 tiles through shared memory, 16-byte loads and stores on both sides
-// (rows a multiple of 64, F and the strides multiples of 8)
-template <typename InT>
-__global__ void __launch_bounds__(256) k_transpose_bf16(int rows, int F, const InT *in, long long ld, long long ms,
-                                                        __nv_bfloat16 *outT, long long R, __nv_bfloat16 *out_rm,
-                                                        long long ld_out) {
-  __shared__ alignas(16) __nv_bfloat16 tile[64][72];   // [row][feature], rows padded to 144 bytes
-  const int f0 = blockIdx.x * 64, r0 = blockIdx.y * 64, m = blockIdx.z;
-  // load: 64 rows x 8 vectors of 8 features, each one 16-byte shared store
-  for (int k = threadIdx.x; k < 64 * 8; k += 256) {
-    const int rr = k >> 3, fv = (k & 7) * 8;
-    const int r = r0 + rr, f = f0 + fv;
-    alignas(16) __nv_bfloat16 b[8];
-    if (r < rows && f < F) {
-      const InT *src = in + (size_t)r * ld + m * ms + f;
-      if constexpr (std::is_same<InT, float>::value) {
-        const float4 x = *reinterpret_cast<const float4 *>(src), y = *reinterpret_cast<const float4 *>(src + 4);
-        b[0] = __float2bfloat16(x.x); b[1] = __float2bfloat16(x.y);
-        b[2] = __float2bfloat16(x.z); b[3] = __float2bfloat16(x.w);
-        b[4] = __float2bfloat16(y.x); b[5] = __float2bfloat16(y.y);
-        b[6] = __float2bfloat16(y.z); b[7] = __float2bfloat16(y.w);
-        if (out_rm) *reinterpret_cast<uint4 *>(out_rm + (size_t)r * ld_out + m * ms + f) = *reinterpret_cast<uint4 *>(b);
-      } else {
-        *reinterpret_cast<uint4 *>(b) = *reinterpret_cast<const uint4 *>(src);
-      }
-    } else {
-      *reinterpret_cast<uint4 *>(b) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    *reinterpret_cast<uint4 *>(&tile[rr][fv]) = *reinterpret_cast<const uint4 *>(b);
-  }
-  __syncthreads();
-  // store: thread (feature pair h, rows rv .. rv + 7) reads eight bf16-pair words (lanes h = 0 .. 31 of a
-  // warp hit distinct banks), splits them into the two features' eight rows, and writes 16 bytes each
-  const int h = threadIdx.x & 31, rv = (threadIdx.x >> 5) * 8;
-  const int f = f0 + 2 * h, r = r0 + rv;
-  if (r >= rows || f >= F) return;
-  uint32_t wd[8];
-#pragma unroll
-  for (int j = 0; j < 8; j++) wd[j] = *reinterpret_cast<const uint32_t *>(&tile[rv + j][2 * h]);
-  const uint4 even = make_uint4(__byte_perm(wd[0], wd[1], 0x5410), __byte_perm(wd[2], wd[3], 0x5410),
-                                __byte_perm(wd[4], wd[5], 0x5410), __byte_perm(wd[6], wd[7], 0x5410));
-  const uint4 odd = make_uint4(__byte_perm(wd[0], wd[1], 0x7632), __byte_perm(wd[2], wd[3], 0x7632),
-                               __byte_perm(wd[4], wd[5], 0x7632), __byte_perm(wd[6], wd[7], 0x7632));
-  *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f) * R + r) = even;
-  if (f + 1 < F) *reinterpret_cast<uint4 *>(outT + ((size_t)m * F + f + 1) * R + r) = odd;
-}
 
 __device__ __forceinline__ float dcelu_hb(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
 __device__ __forceinline__ float ratio_hb(float h) { return h > 0.f ? 0.f : CELU_INV_ALPHA; }
@@ -774,18 +735,13 @@ struct TrainTc {
   size_t rows = 0;
   int M = 0;
   void *buf = nullptr;
-  float *t32 = nullptr;                       // AEV tangent, float [R][1008]
-  __nv_bfloat16 *t = nullptr, *h3 = nullptr, *hd1 = nullptr, *hd2 = nullptr, *hd3 = nullptr;
+  __nv_bfloat16 *t = nullptr, *h3 = nullptr, *hd1 = nullptr, *hd2 = nullptr, *hd3 = nullptr;   // t: AEV tangent
   __nv_bfloat16 *gbz3 = nullptr, *gz3 = nullptr, *gb2 = nullptr, *g2 = nullptr, *gbz2 = nullptr, *gz2 = nullptr;
   __nv_bfloat16 *gb1 = nullptr, *g1 = nullptr, *gbz1 = nullptr, *gz1 = nullptr;
-  // row-contiguous transposes [member][feature][R]
-  __nv_bfloat16 *aevT = nullptr, *tT = nullptr, *h1T = nullptr, *hd1T = nullptr, *h2T = nullptr, *hd2T = nullptr;
-  __nv_bfloat16 *gbz3T = nullptr, *gz3T = nullptr, *gbz2T = nullptr, *gz2T = nullptr, *gbz1T = nullptr,
-                *gz1T = nullptr;
-  // operand maps (128-byte rows), epilogue piece maps, transposed operand maps
+  // operand maps (128-byte rows), epilogue piece maps, MN-major weight-gradient operand maps
   CUtensorMap mT, mHD1, mHD2, mGBZ3, mGZ3, mGBZ2, mGZ2;
   CUtensorMap eH3, eHD1, eHD2, eHD3, eGB2, eG2, eGB1, eG1;
-  CUtensorMap tGBZ3, tGZ3, tGBZ2, tGZ2, tGBZ1, tGZ1, tHD2, tH2, tHD1, tH1, tT_, tAev;
+  CUtensorMap wGBZ3, wGZ3, wGBZ2, wGZ2, wGBZ1, wGZ1, wHD2, wHD1, wT;
 };
 
 }  // namespace
@@ -806,16 +762,14 @@ static fnn_status train_tc_workspace(fnn_ctx *ctx, TcState *ts, size_t rows) {
   T.buf = nullptr;
   rows = (rows + rows / 8 + 127) / 128 * 128;
   const size_t R = rows;
-  const size_t n16 = R * (NAEV + (size_t)M * (H3 + H1 + H2 + H3 + 2 * H3 + 4 * H2 + 4 * H1)) +
-                     R * (2 * (size_t)NAEV + (size_t)M * (4 * H1 + 4 * H2 + 2 * H3));
-  const size_t bytes = R * NAEV * sizeof(float) + n16 * sizeof(__nv_bfloat16) + 4096;
+  const size_t n16 = R * (NAEV + (size_t)M * (H3 + H1 + H2 + H3 + 2 * H3 + 4 * H2 + 4 * H1));
+  const size_t bytes = n16 * sizeof(__nv_bfloat16) + 4096;
   if (cudaMalloc(&T.buf, bytes) != cudaSuccess) {
     cudaGetLastError();
     ctx->last_error = "cudaMalloc failed for the bf16 training workspace";
     return FNN_E_OOM;
   }
-  T.t32 = static_cast<float *>(T.buf);
-  __nv_bfloat16 *p = reinterpret_cast<__nv_bfloat16 *>(T.t32 + R * NAEV);
+  __nv_bfloat16 *p = static_cast<__nv_bfloat16 *>(T.buf);
   auto take = [&](size_t n) {
     __nv_bfloat16 *q = p;
     p += n;
@@ -836,18 +790,6 @@ static fnn_status train_tc_workspace(fnn_ctx *ctx, TcState *ts, size_t rows) {
   T.g1 = take(R * M * H1);
   T.gbz1 = take(R * M * H1);
   T.gz1 = take(R * M * H1);
-  T.aevT = take(R * NAEV);
-  T.tT = take(R * NAEV);
-  T.h1T = take(R * M * H1);
-  T.hd1T = take(R * M * H1);
-  T.gbz1T = take(R * M * H1);
-  T.gz1T = take(R * M * H1);
-  T.h2T = take(R * M * H2);
-  T.hd2T = take(R * M * H2);
-  T.gbz2T = take(R * M * H2);
-  T.gz2T = take(R * M * H2);
-  T.gbz3T = take(R * M * H3);
-  T.gz3T = take(R * M * H3);
   const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle NS = CU_TENSOR_MAP_SWIZZLE_NONE, S128 = CU_TENSOR_MAP_SWIZZLE_128B;
   auto op = [&](CUtensorMap *mp, void *b, uint64_t F) {   // row-major operand, member in the middle
@@ -856,18 +798,16 @@ static fnn_status train_tc_workspace(fnn_ctx *ctx, TcState *ts, size_t rows) {
   auto ep = [&](CUtensorMap *mp, void *b, uint64_t F) {   // epilogue pieces
     return encode3d(mp, b, F, M, R, F * 2, (uint64_t)M * F * 2, 16, 1, 32, BF, NS);
   };
-  auto tr = [&](CUtensorMap *mp, void *b, uint64_t F, uint64_t mem, uint32_t box_f) {   // [member][F][R]
-    return encode3d(mp, b, R, F, mem, R * 2, F * R * 2, 64, box_f, 1, BF, S128);
+  auto wn = [&](CUtensorMap *mp, void *b, uint64_t F) {   // MN-major boxes: 64 features x 64 rows
+    return encode3d(mp, b, F, M, R, F * 2, (uint64_t)M * F * 2, 64, 1, 64, BF, S128);
   };
   bool ok = encode3d(&T.mT, T.t, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 128, BF, S128) && op(&T.mHD1, T.hd1, H1) &&
             op(&T.mHD2, T.hd2, H2) && op(&T.mGBZ3, T.gbz3, H3) && op(&T.mGZ3, T.gz3, H3) && op(&T.mGBZ2, T.gbz2, H2) &&
             op(&T.mGZ2, T.gz2, H2) && ep(&T.eH3, T.h3, H3) && ep(&T.eHD1, T.hd1, H1) && ep(&T.eHD2, T.hd2, H2) &&
             ep(&T.eHD3, T.hd3, H3) && ep(&T.eGB2, T.gb2, H2) && ep(&T.eG2, T.g2, H2) && ep(&T.eGB1, T.gb1, H1) &&
-            ep(&T.eG1, T.g1, H1) && tr(&T.tGBZ3, T.gbz3T, H3, M, 128) && tr(&T.tGZ3, T.gz3T, H3, M, 128) &&
-            tr(&T.tGBZ2, T.gbz2T, H2, M, 128) && tr(&T.tGZ2, T.gz2T, H2, M, 128) && tr(&T.tGBZ1, T.gbz1T, H1, M, 128) &&
-            tr(&T.tGZ1, T.gz1T, H1, M, 128) && tr(&T.tHD2, T.hd2T, H2, M, 192) && tr(&T.tH2, T.h2T, H2, M, 192) &&
-            tr(&T.tHD1, T.hd1T, H1, M, 256) && tr(&T.tH1, T.h1T, H1, M, 256) && tr(&T.tT_, T.tT, NAEV, 1, 256) &&
-            tr(&T.tAev, T.aevT, NAEV, 1, 256);
+            ep(&T.eG1, T.g1, H1) && wn(&T.wGBZ3, T.gbz3, H3) && wn(&T.wGZ3, T.gz3, H3) && wn(&T.wGBZ2, T.gbz2, H2) &&
+            wn(&T.wGZ2, T.gz2, H2) && wn(&T.wGBZ1, T.gbz1, H1) && wn(&T.wGZ1, T.gz1, H1) && wn(&T.wHD2, T.hd2, H2) &&
+            wn(&T.wHD1, T.hd1, H1) && encode3d(&T.wT, T.t, NAEV, 1, R, NAEV * 2, NAEV * 2, 64, 1, 64, BF, S128);
   if (!ok) {
     ctx->last_error = "cuTensorMapEncodeTiled failed for the training maps";
     return FNN_E_CUDA;
@@ -875,15 +815,6 @@ static fnn_status train_tc_workspace(fnn_ctx *ctx, TcState *ts, size_t rows) {
   T.rows = rows;
   T.M = M;
   return FNN_OK;
-}
-
-template <typename InT>
-static fnn_status transpose(fnn_ctx *ctx, int rows, int F, int M, const InT *in, long long ld, long long ms,
-                            __nv_bfloat16 *outT, long long R, __nv_bfloat16 *out_rm, cudaStream_t s) {
-  dim3 grid((F + 63) / 64, (rows + 63) / 64, M);
-  FNN_KERNEL(ctx, "tr_transpose", s);
-  k_transpose_bf16<InT><<<grid, 256, 0, s>>>(rows, F, in, ld, ms, outT, R, out_rm, ld);
-  return check_launch(ctx, "tr_transpose");
 }
 
 fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const double *dLdE,
@@ -901,15 +832,12 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   const Half &H = ts->h[0];
   const DeviceWeights &w = ctx->w;
   const int M = w.M;
-  const long long R = (long long)T.rows;
   const int rows = nl->pad_cap;
   const unsigned tiles = (unsigned)(rows / ROW_TILE);
   constexpr int B16 = tc::MODE_BF16;
-  // AEV (bf16) and its tangent along dL/dF (float -> bf16 row-major and transposed)
+  // AEV and its tangent along dL/dF (bf16)
   if ((st = launch_aev_forward_bf16(ctx, sys, nl, H.aev, nullptr, nl->inv, s))) return st;
-  if ((st = launch_aev_tangent(ctx, sys, nl, dLdF, T.t32, nl->inv, s))) return st;
-  if ((st = transpose<float>(ctx, rows, NAEV, 1, T.t32, NAEV, 0, T.tT, R, T.t, s))) return st;
-  if ((st = transpose<__nv_bfloat16>(ctx, rows, NAEV, 1, H.aev, NAEV, 0, T.aevT, R, nullptr, s))) return st;
+  if ((st = launch_aev_tangent_bf16(ctx, sys, nl, dLdF, T.t, nl->inv, s))) return st;
   tc::Args a{};
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
@@ -985,17 +913,6 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
     k_act_reverse_bf16<<<dim3(tiles, M), H1, 0, s>>>(M, H1, nl->tile_elem, H.h1, T.hd1, T.gb1, T.g1, T.gbz1, T.gz1,
                                                       g->b1);
   }
-  // ---- row-contiguous transposes of the weight-gradient factors
-  struct TJ {
-    const __nv_bfloat16 *in;
-    int F;
-    __nv_bfloat16 *out;
-  } jobs[] = {{H.h1, H1, T.h1T},     {T.hd1, H1, T.hd1T},   {H.h2, H2, T.h2T},     {T.hd2, H2, T.hd2T},
-              {T.gbz3, H3, T.gbz3T}, {T.gz3, H3, T.gz3T},   {T.gbz2, H2, T.gbz2T}, {T.gz2, H2, T.gz2T},
-              {T.gbz1, H1, T.gbz1T}, {T.gz1, H1, T.gz1T}};
-  for (const TJ &j : jobs)
-    if ((st = transpose<__nv_bfloat16>(ctx, rows, j.F, M, j.in, (long long)M * j.F, j.F, j.out, R, nullptr, s)))
-      return st;
   // ---- weight gradients: dW_l += gbz_l^T hd_{l-1} + gz_l^T h_{l-1} over each element's rows
   tc::Args wg{};
   wg.st = ctx->status;
@@ -1007,17 +924,17 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   wg.K = 0;
   wg.dW = g->W3; wg.O = H3; wg.I = H2; wg.N = H2;
   if ((st = launch<192, tc::EPI_ATOMIC, WG>(ctx, "tr16_l3_wgrad",
-                                            {&T.tGBZ3, &T.tHD2, &T.tGZ3, &T.tH2, &T.tGBZ3, &T.tGBZ3, &T.tGBZ3, &T.tGBZ3},
+                                            {&T.wGBZ3, &T.wHD2, &T.wGZ3, &H.wH2, &T.wGBZ3, &T.wGBZ3, &T.wGBZ3, &T.wGBZ3},
                                             wg, dim3(1, (H3 + 127) / 128, wg.n_chunks * M * NE), s)))
     return st;
   wg.dW = g->W2; wg.O = H2; wg.I = H1; wg.N = H1;
   if ((st = launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l2_wgrad",
-                                            {&T.tGBZ2, &T.tHD1, &T.tGZ2, &T.tH1, &T.tGBZ2, &T.tGBZ2, &T.tGBZ2, &T.tGBZ2},
+                                            {&T.wGBZ2, &T.wHD1, &T.wGZ2, &H.wH1, &T.wGBZ2, &T.wGBZ2, &T.wGBZ2, &T.wGBZ2},
                                             wg, dim3(1, (H2 + 127) / 128, wg.n_chunks * M * NE), s)))
     return st;
   wg.dW = g->W1; wg.O = H1; wg.I = NAEV; wg.N = NAEV; wg.b_shared = 1;
   return launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l1_wgrad",
-                                         {&T.tGBZ1, &T.tT_, &T.tGZ1, &T.tAev, &T.tGBZ1, &T.tGBZ1, &T.tGBZ1, &T.tGBZ1},
+                                         {&T.wGBZ1, &T.wT, &T.wGZ1, &H.wAev, &T.wGBZ1, &T.wGBZ1, &T.wGBZ1, &T.wGBZ1},
                                          wg, dim3((NAEV + 255) / 256, (H1 + 127) / 128, wg.n_chunks * M * NE), s);
 }
 

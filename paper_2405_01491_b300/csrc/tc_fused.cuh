@@ -59,7 +59,7 @@ constexpr int L3_N1 = H3, L3_N2 = H2, L3_K1 = H2, L3_K2 = H3;
 constexpr int L3_ZCOLS = 160, L3_GCOL = 320;
 constexpr int L3_PIECES = 3;   // E2 pieces per epilogue warp: columns 16 part + {0, 64, 128} of 192
 
-template <int MODE>
+template <int MODE, int KB>
 struct L3Smem {
   static constexpr bool SPLIT = MODE == MODE_SPLIT;
   static constexpr int OB = SPLIT ? 2 : 1;      // halves per output buffer
@@ -70,10 +70,11 @@ struct L3Smem {
   static constexpr int BROWS = L3_N2 > L3_N1 ? L3_N2 : L3_N1;
   static constexpr int FIXED = OBYTES + 2048;
   // a split stage holds hi and lo of both operands for one K chunk (three products per K step)
-  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (OB * (BM * BKB + BROWS * BKB));
-  static constexpr int STAGES = FIT > 6 ? 6 : FIT;
-  uint8_t A[STAGES][OB * BM * BKB];
-  uint8_t B[STAGES][OB * BROWS * BKB];
+  static constexpr int FIT = (SMEM_LIMIT - FIXED) / (OB * (BM * KB + BROWS * KB));
+  static constexpr int CAP = 6 * (BKB / KB);
+  static constexpr int STAGES = FIT > CAP ? CAP : FIT;
+  uint8_t A[STAGES][OB * BM * KB];
+  uint8_t B[STAGES][OB * BROWS * KB];
   uint8_t O[OBYTES];
   uint64_t full[STAGES], empty[STAGES];
   uint64_t z_full[2], a_full[2], g_full, g_empty, fin, aux_bar[EPI_WARPS][NAUX];
@@ -81,9 +82,9 @@ struct L3Smem {
   int abort_flag;
 };
 
-template <int MODE>
+template <int MODE, int KB>
 constexpr size_t l3_smem_bytes() {
-  return sizeof(L3Smem<MODE>) + 1024;
+  return sizeof(L3Smem<MODE, KB>) + 1024;
 }
 
 // tile t -> (row tile, member, element); false for padding tiles
@@ -94,7 +95,7 @@ __device__ __forceinline__ bool l3_tile(const L3Args &p, int t, int &rt, int &m,
   return e >= 0;
 }
 
-template <int MODE>
+template <int MODE, int KB>
 __global__ void __launch_bounds__(THREADS, 1)
     k_l3_pair(const __grid_constant__ CUtensorMap tmH2, const __grid_constant__ CUtensorMap tmH2_lo,
               const __grid_constant__ CUtensorMap tmW3, const __grid_constant__ CUtensorMap tmW3_lo,
@@ -102,12 +103,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX_lo,
               const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo, L3Args p) {
   static_assert(MODE == MODE_SPLIT || MODE == MODE_BF16, "bf16 operands");
-  using SM = L3Smem<MODE>;
+  static_assert(KB == 128 || KB == 64, "operand row width");
+  using SM = L3Smem<MODE, KB>;
   static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
   constexpr bool SPLIT = MODE == MODE_SPLIT;
   constexpr int STAGES = SM::STAGES;
-  constexpr int BK = BKB / 2;                              // bf16 K elements per stage
-  constexpr int NK1 = (L3_K1 + BK - 1) / BK, NK2 = (L3_K2 + BK - 1) / BK;   // 3, 3
+  constexpr int BK = KB / 2;                               // bf16 K elements per stage
+  constexpr int NK1 = (L3_K1 + BK - 1) / BK, NK2 = (L3_K2 + BK - 1) / BK;   // 3, 3 (128-byte rows) or 6, 5
   extern __shared__ uint8_t smem_raw[];
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -166,17 +168,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               break;
             }
             if (phase == 0) {   // h2 and W3 (hi, and lo for the split)
-              mbar_expect_tx(&S.full[s], (uint32_t)(SM::OB * (BM + L3_N1) * BKB));
+              mbar_expect_tx(&S.full[s], (uint32_t)(SM::OB * (BM + L3_N1) * KB));
               tma_load_3d(S.A[s], &tmH2, &S.full[s], kk * BK, tm, trt * BM);
               tma_load_3d(S.B[s], &tmW3, &S.full[s], kk * BK, 0, tm * NE + te);
               if (SPLIT) {
-                tma_load_3d(S.A[s] + BM * BKB, &tmH2_lo, &S.full[s], kk * BK, tm, trt * BM);
-                tma_load_3d(S.B[s] + L3_N1 * BKB, &tmW3_lo, &S.full[s], kk * BK, 0, tm * NE + te);
+                tma_load_3d(S.A[s] + BM * KB, &tmH2_lo, &S.full[s], kk * BK, tm, trt * BM);
+                tma_load_3d(S.B[s] + L3_N1 * KB, &tmW3_lo, &S.full[s], kk * BK, 0, tm * NE + te);
               }
             } else {            // W3^T (hi, lo)
-              mbar_expect_tx(&S.full[s], (uint32_t)(SM::OB * L3_N2 * BKB));
+              mbar_expect_tx(&S.full[s], (uint32_t)(SM::OB * L3_N2 * KB));
               tma_load_3d(S.B[s], &tmW3T, &S.full[s], kk * BK, 0, tm * NE + te);
-              if (SPLIT) tma_load_3d(S.B[s] + L3_N2 * BKB, &tmW3T_lo, &S.full[s], kk * BK, 0, tm * NE + te);
+              if (SPLIT) tma_load_3d(S.B[s] + L3_N2 * KB, &tmW3T_lo, &S.full[s], kk * BK, 0, tm * NE + te);
             }
             issued = g + 1;
           }
@@ -217,12 +219,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_after();
             const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
-            for (int q = 0; q < BKB / 32; q++) {
-              const uint64_t ah = sdesc_sw128(a0 + 32 * q), bh = sdesc_sw128(b0 + 32 * q);
+            for (int q = 0; q < KB / 32; q++) {
+              const uint64_t ah = sdesc<KB>(a0 + 32 * q), bh = sdesc<KB>(b0 + 32 * q);
               mma_bf16(z, ah, bh, id1, (kb | q) != 0);
               if (SPLIT) {   // + hi lo + lo hi
-                mma_bf16(z, ah, sdesc_sw128(b0 + L3_N1 * BKB + 32 * q), id1, 1u);
-                mma_bf16(z, sdesc_sw128(a0 + BM * BKB + 32 * q), bh, id1, 1u);
+                mma_bf16(z, ah, sdesc<KB>(b0 + L3_N1 * KB + 32 * q), id1, 1u);
+                mma_bf16(z, sdesc<KB>(a0 + BM * KB + 32 * q), bh, id1, 1u);
               }
             }
             mma_commit(&S.empty[s]);
@@ -250,14 +252,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_after();
             const uint32_t b0 = smem_u32(S.B[s]);
 #pragma unroll
-            for (int q = 0; q < BKB / 32; q++) {
+            for (int q = 0; q < KB / 32; q++) {
               const int kblk = kk * (BK / 16) + q;   // 16-element K block of g3
               if (16 * kblk >= L3_K2) continue;
               const uint32_t ah = za + (uint32_t)(16 * kblk);
-              const uint64_t bh = sdesc_sw128(b0 + 32 * q);
+              const uint64_t bh = sdesc<KB>(b0 + 32 * q);
               mma_bf16_ts(gacc, ah, bh, id2, first ? 0u : 1u);
               if (SPLIT) {   // + hi lo + lo hi
-                mma_bf16_ts(gacc, ah, sdesc_sw128(b0 + L3_N2 * BKB + 32 * q), id2, 1u);
+                mma_bf16_ts(gacc, ah, sdesc<KB>(b0 + L3_N2 * KB + 32 * q), id2, 1u);
                 mma_bf16_ts(gacc, ah + 8u, bh, id2, 1u);
               }
               first = false;

@@ -33,7 +33,7 @@ constexpr long long WAIT_LIMIT = 2000000000LL;  // clock64 cycles (about a secon
 
 enum { EPI_BIAS_CELU = 0, EPI_L3 = 1, EPI_DCELU = 2, EPI_F32 = 3, EPI_PLAIN = 4, EPI_ATOMIC = 5 };
 // operand forms: bf16; the three-term bf16 split of an fp32 product; fp8 e4m3 with per-tensor scales;
-// bf16 weight gradients (A and B are row-contiguous transposes, K runs over an element's rows)
+// bf16 weight gradients (K runs over an element's rows; A and B are read feature-contiguous, MN-major)
 enum { MODE_BF16 = 0, MODE_SPLIT = 1, MODE_F8 = 2, MODE_WG = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -163,6 +163,16 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   d |= (uint64_t)4 << 61;
   return d;
 }
+// MN-major operand, 128-byte swizzle: atoms of 8 K rows x 64 MN elements (128 bytes per K row, 1024 B);
+// 8-K-row groups 1024 B apart (stride byte offset), 64-element MN blocks lbo bytes apart (leading byte offset)
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 // descriptor of a K-major operand whose rows are KB bytes (128 or 64), swizzled to match
 template <int KB>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -175,6 +185,8 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// the same with both operands MN-major (transpose bits 15 and 16)
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) { return idesc_bf16(M, N) | (1u << 15) | (1u << 16); }
 // kind::f8f6f4: fp32 accumulator, A and B format E4M3 (code 0 in [7,10) and [10,13)), both K-major
 __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -348,6 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool WG = MODE == MODE_WG;
+  static_assert(!WG || (NT % 64 == 0 && KB == BKB), "MN-major operands: 64-feature boxes of 64 rows");
   const int nkb_fixed = (SPLIT && !QUAD) ? 3 * ((p.K + BK - 1) / BK) : (p.K + BK - 1) / BK;
   const int T = p.n_ntiles * p.n_rowtiles * p.n_members;
   volatile int *abort_flag = &S.abort_flag;
@@ -452,10 +465,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             tma_load_3d(S.A[s] + BM * KB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
             tma_load_3d(S.B[s], mb, &S.full[s], kb * BK, by, b_grp);
             tma_load_3d(S.B[s] + NT * KB, mb_lo, &S.full[s], kb * BK, by, b_grp);
-          } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo); x runs over rows, y over features
-            const int term = kb / nkb_seg, x = r0 + (kb - term * nkb_seg) * BK;
-            tma_load_3d(S.A[s], term ? &tmA_lo : &tmA, &S.full[s], x, rt * BM, m);
-            tma_load_3d(S.B[s], term ? &tmB_lo : &tmB, &S.full[s], x, nt * NT, p.b_shared ? 0 : m);
+          } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo): BK rows x 64 features per box
+            const int term = kb / nkb_seg, y = r0 + (kb - term * nkb_seg) * BK;
+            const CUtensorMap *ma = term ? &tmA_lo : &tmA, *mbw = term ? &tmB_lo : &tmB;
+#pragma unroll
+            for (int j = 0; j < BM / 64; j++) tma_load_3d(S.A[s] + j * BK * 128, ma, &S.full[s], rt * BM + 64 * j, m, y);
+#pragma unroll
+            for (int j = 0; j < NT / 64; j++)
+              tma_load_3d(S.B[s] + j * BK * 128, mbw, &S.full[s], nt * NT + 64 * j, p.b_shared ? 0 : m, y);
           } else {
             const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
             tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
@@ -470,7 +487,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t idesc = F8 ? idesc_e4m3(BM, NT) : idesc_bf16(BM, NT);
+      const uint32_t idesc = F8 ? idesc_e4m3(BM, NT) : (WG ? idesc_bf16_mn(BM, NT) : idesc_bf16(BM, NT));
       long long g = 0;
       int cnt = 0;
       for (int it = 0; !*abort_flag; it++) {
@@ -506,6 +523,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               mma_bf16(d, ah, bh, id, acc);
               mma_bf16(d, ah, bl, id, 1u);
               mma_bf16(d, al, bh, id, 1u);
+            } else if (WG) {   // 16 K rows of 128 bytes per step
+              mma_bf16(d, sdesc_mn_sw128(a0 + 2048 * k, BK * 128), sdesc_mn_sw128(b0 + 2048 * k, BK * 128), id, acc);
             } else if (F8)
               mma_f8(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), id, acc);
             else
