@@ -450,6 +450,7 @@ def train_bench(fnn, torch, synth, steps, warmup, M=1, precision="bf16"):
     return {"workload": f"ragged batch: 4096 molecules, 8-64 atoms, {s.n_atoms} atoms (gas phase)",
             "members": M, "precision": precision, "ms_per_step": ms, "atoms_per_s": s.n_atoms / (ms * 1e-3),
             "loss": float(L.detach()), "gpu_launches_per_step": launches / steps,
+            "kernel_ms_per_step": total / steps,
             "kernel_share": {k: round(v[0] / total, 3) for k, v in top},
             "note": "forward (E, F) + loss + parameter gradients; the optimizer update is not timed"}
 

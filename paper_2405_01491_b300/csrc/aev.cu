@@ -239,6 +239,64 @@ __device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
 // slot block of the element pair (a, b), a <= b, in row-major upper-triangle order
 __device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
+// The element-pair blocks of an atom's triplets in slot order, one int4 per block (lanes 0 .. NPAIR - 1
+// write theirs): {triplets, j0 | k0 << 8 | (a == b) << 16, count of element b, count of element a} with j0,
+// k0 the angular-list starts of elements a and b
+__device__ __forceinline__ void fill_blocks(int4 *blk, const int off_a[NE + 1], const int cnt_a[NE]) {
+  const int lane = threadIdx.x & 31;
+  if (lane < NPAIR) {
+    int a = 0;
+    while (a + 1 < NE && pair_of(a + 1, a + 1) <= lane) a++;
+    const int b = a + (lane - pair_of(a, a));
+    int oa = 0, ob = 0, na = 0, nb = 0;
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      if (q == a) { oa = off_a[q]; na = cnt_a[q]; }
+      if (q == b) { ob = off_a[q]; nb = cnt_a[q]; }
+    }
+    blk[lane] = make_int4(a == b ? na * (na - 1) / 2 : na * nb, oa | (ob << 8) | ((a == b) << 16), nb, na);
+  }
+  __syncwarp();
+}
+
+// This lane's triplet of the next batch of 32 in block order (block by block in slot order, j-major
+// within a block): its block pb (NPAIR past the end) and angular entries ja < ka.  (cp, cu) is the
+// warp-uniform cursor (block, offset) of the batch's first triplet and advances by 32.  Returns the
+// lanes whose triplet opens a block, against the previous lane (lane 0 against the running block run_p).
+__device__ __forceinline__ unsigned next_batch(const int4 *blk, int &cp, int &cu, int run_p, int &pb, int &ja,
+                                               int &ka) {
+  const int lane = threadIdx.x & 31;
+  int u = cu + lane;
+  pb = cp;
+  int4 bk = blk[pb];
+  while (u >= bk.x) {
+    u -= bk.x;
+    if (++pb >= NPAIR) break;
+    bk = blk[pb];
+  }
+  cp = __shfl_sync(FULL, pb, 31);
+  cu = __shfl_sync(FULL, u, 31) + 1;
+  const int pprev = __shfl_up_sync(FULL, pb, 1);
+  const unsigned starts = __ballot_sync(FULL, pb < NPAIR && pb != (lane == 0 ? run_p : pprev));
+  ja = ka = 0;
+  if (pb < NPAIR) {
+    const int j0 = bk.y & 0xff;
+    if (bk.y >> 16) {   // both from element a: the u-th pair of its segment
+      int jj, kk;
+      tri_index(u, bk.w, jj, kk);
+      ja = j0 + jj;
+      ka = j0 + kk;
+    } else {            // j from element a, k from element b
+      int jj = (int)((float)u * rcp_fast((float)bk.z));
+      if (jj * bk.z > u) jj--;
+      else if ((jj + 1) * bk.z <= u) jj++;
+      ja = j0 + jj;
+      ka = ((bk.y >> 8) & 0xff) + (u - jj * bk.z);
+    }
+  }
+  return starts;
+}
+
 template <typename OutT>
 __device__ __forceinline__ void store_out(OutT *p, float v, float inv);
 template <>
@@ -315,19 +373,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
     // the output row when the block ends (slots of absent pairs are written as zeros).
     {
       const int s_my = lane & 3, m_my = lane >> 2;
-      if (lane < NPAIR) {
-        int a = 0;
-        while (a + 1 < NE && pair_of(a + 1, a + 1) <= lane) a++;
-        const int b = a + (lane - pair_of(a, a));
-        int oa = 0, ob = 0, na = 0, nb = 0;
-#pragma unroll
-        for (int q = 0; q < NE; q++) {
-          if (q == a) { oa = off_a[q]; na = cnt_a[q]; }
-          if (q == b) { ob = off_a[q]; nb = cnt_a[q]; }
-        }
-        W.blk[lane] = make_int4(a == b ? na * (na - 1) / 2 : na * nb, oa | (ob << 8) | ((a == b) << 16), nb, na);
-      }
-      __syncwarp();
+      fill_blocks(W.blk, off_a, cnt_a);
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
       int run_p = -1;          // pair block being summed (warp-uniform); every block before it is written
@@ -338,33 +384,9 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
       };
       int cp = 0, cu = 0;      // block and offset of the batch's first triplet (warp-uniform)
       for (int base = 0; base < T; base += 32) {
-        int u = cu + lane, pb = cp;
-        int4 bk = W.blk[pb];
-        while (u >= bk.x) {
-          u -= bk.x;
-          if (++pb >= NPAIR) break;
-          bk = W.blk[pb];
-        }
-        cp = __shfl_sync(FULL, pb, 31);
-        cu = __shfl_sync(FULL, u, 31) + 1;
-        // triplets that open a new block (against the previous lane; lane 0 against the running block)
-        const int pprev = __shfl_up_sync(FULL, pb, 1);
-        const unsigned starts = __ballot_sync(FULL, pb < NPAIR && pb != (lane == 0 ? run_p : pprev));
+        int pb, ja, ka;
+        const unsigned starts = next_batch(W.blk, cp, cu, run_p, pb, ja, ka);
         if (pb < NPAIR) {
-          const int j0 = bk.y & 0xff;
-          int ja, ka;
-          if (bk.y >> 16) {   // both from element a: the u-th pair of its segment
-            int jj, kk;
-            tri_index(u, bk.w, jj, kk);
-            ja = j0 + jj;
-            ka = j0 + kk;
-          } else {            // j from element a, k from element b
-            int jj = (int)((float)u * rcp_fast((float)bk.z));
-            if (jj * bk.z > u) jj--;
-            else if ((jj + 1) * bk.z <= u) jj++;
-            ja = j0 + jj;
-            ka = ((bk.y >> 8) & 0xff) + (u - jj * bk.z);
-          }
           const float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
           const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(d1.w * d2.w);
           const float c95 = 0.95f * c;
@@ -626,13 +648,24 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
 // t = (dAEV/dx) . V: the directional derivative of every AEV entry along a displacement field V.
 // Radial: d/dt [T_k(r)] = T_k'(r) rdot, rdot = d.(v_j - v_i) / r.  Angular: with c = cos theta,
 // cdot = (d2.vd1 + d1.vd2) / (r1 r2) - c (r1dot / r1 + r2dot / r2),
-// d/dt [2 f_s g_m C] = fdot_s (2 g_m C) + f_s (2 (gdot_m C + g_m Cdot)); same enumeration as the forward.
+// d/dt [2 f_s g_m C] = fdot_s (2 g_m C) + f_s (2 (gdot_m C + g_m Cdot)).  Same staging and block-order
+// enumeration as the forward: the producer lane stages one triplet's f_s, fdot_s, 2 g_m C and
+// 2 (gdot_m C + g_m Cdot); lane (m, s) sums the two products over the batch into a register that goes
+// to the output row when the pair's block ends.
 struct TanStage {
   NbrStage nb;
   float4 rv[RAD_CAP];            // v_j - v_i, rdot
-  float2 rt[RAD_CAP];            // fc(r) rdot, fc'(r) rdot   (radial switch)
-  float stage[32][25];           // f_s, fdot_s, 2 g_m C, 2 (gdot_m C + g_m Cdot), pair index
-  float acc[NPAIR * 32];
+  union {
+    float2 rt[RAD_CAP];          // fc(r) rdot, fc'(r) rdot   (radial switch: the radial terms only)
+    struct {                     // one batch of triplets, triplet innermost
+      alignas(16) float sf[NSZ][SROW];
+      alignas(16) float sfd[NSZ][SROW];
+      alignas(16) float sg[NSA][SROW];
+      alignas(16) float sgd[NSA][SROW];
+      alignas(16) int sp[SROW];
+    } b;
+  };
+  int4 blk[NPAIR];
 };
 
 struct AevTanArgs {
@@ -646,10 +679,10 @@ struct AevTanArgs {
   DevStatus *st;
 };
 
-constexpr int TAN_WARPS = 2;   // 15 KB of staging per warp: two warps keep the block under 48 KB
+constexpr int TAN_WARPS = 4, TAN_BLOCKS = 5;   // 11 KB of staging per warp
 
 template <typename OutT>
-__global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
+__global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevTanArgs A) {
   __shared__ TanStage smem[TAN_WARPS];
   int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   TanStage &W = smem[wl];
@@ -695,19 +728,21 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
         if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc, 1.f);
       }
     }
+    __syncwarp();   // the batch rows below reuse the radial staging
     // ---- angular
     {
       const int s_my = lane & 3, m_my = lane >> 2;
-      for (int c = lane; c < NPAIR * 32; c += 32) W.acc[c] = 0.f;
+      fill_blocks(W.blk, off_a, cnt_a);
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
       int run_p = -1;
       float racc = 0.f;
+      auto put = [&](int pp, float v) { store_out<OutT>(out + NRAD + pp * 32 + lane, v, 1.f); };
+      int cp = 0, cu = 0;
       for (int base = 0; base < T; base += 32) {
-        const int t = base + lane;
-        if (t < T) {
-          int ja, ka;
-          tri_index(t, n, ja, ka);
+        int pb, ja, ka;
+        const unsigned starts = next_batch(W.blk, cp, cu, run_p, pb, ja, ka);
+        if (pb < NPAIR) {
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
           const float r1 = d1.w, r2 = d2.w, ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
@@ -721,8 +756,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
           for (int sidx = 0; sidx < NSZ; sidx++) {
             const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[sidx] + s95 * P.sin_z[sidx]);
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
-            W.stage[lane][sidx] = f;
-            W.stage[lane][4 + sidx] =
+            W.b.sf[sidx][lane] = f;
+            W.b.sfd[sidx][lane] =
                 P.zeta * f * rcp_fast(base_s) * 0.5f * (0.95f * P.cos_z[sidx] + ds95 * P.sin_z[sidx]) * cdot;
           }
           const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
@@ -733,27 +768,52 @@ __global__ void __launch_bounds__(TAN_WARPS * 32) k_aev_tangent(AevTanArgs A) {
             const float dr = rbar - P.shf_a[m];
             const float g = __expf(-P.eta_a * dr * dr);
             const float gdot = -2.f * P.eta_a * dr * g * rbdot;
-            W.stage[lane][8 + m] = 2.f * g * C;
-            W.stage[lane][16 + m] = 2.f * (gdot * C + g * Cdot);
+            W.b.sg[m][lane] = 2.f * g * C;
+            W.b.sgd[m][lane] = 2.f * (gdot * C + g * Cdot);
           }
-          W.stage[lane][24] = __int_as_float(pair_of(S.ae[ja], S.ae[ka]));
+          W.b.sp[lane] = pb;
+        } else {
+#pragma unroll
+          for (int sidx = 0; sidx < NSZ; sidx++) W.b.sf[sidx][lane] = W.b.sfd[sidx][lane] = 0.f;
+#pragma unroll
+          for (int m = 0; m < NSA; m++) W.b.sg[m][lane] = W.b.sgd[m][lane] = 0.f;
+          W.b.sp[lane] = -1;
         }
         __syncwarp();
         const int nt = min(32, T - base);
-        for (int q = 0; q < nt; q++) {
-          const int p = __float_as_int(W.stage[q][24]);
-          if (p != run_p) {
-            if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
-            racc = 0.f;
-            run_p = p;
+        const float *fr = W.b.sf[s_my], *fdr = W.b.sfd[s_my], *gr = W.b.sg[m_my], *gdr = W.b.sgd[m_my];
+        for (int q = 0; q < nt; q += 4) {
+          const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
+          const float4 fdv = *reinterpret_cast<const float4 *>(fdr + q);
+          const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
+          const float4 gdv = *reinterpret_cast<const float4 *>(gdr + q);
+          const unsigned st4 = (starts >> q) & 0xfu;
+          if (st4 == 0u) {
+            racc = fmaf(fdv.x, gv.x, fmaf(fv.x, gdv.x, racc));
+            racc = fmaf(fdv.y, gv.y, fmaf(fv.y, gdv.y, racc));
+            racc = fmaf(fdv.z, gv.z, fmaf(fv.z, gdv.z, racc));
+            racc = fmaf(fdv.w, gv.w, fmaf(fv.w, gdv.w, racc));
+          } else {
+            const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, fda[4] = {fdv.x, fdv.y, fdv.z, fdv.w};
+            const float ga[4] = {gv.x, gv.y, gv.z, gv.w}, gda[4] = {gdv.x, gdv.y, gdv.z, gdv.w};
+#pragma unroll
+            for (int uu = 0; uu < 4; uu++) {
+              if (q + uu >= nt) break;
+              if ((st4 >> uu) & 1u) {
+                const int pn = W.b.sp[q + uu];
+                if (run_p >= 0) put(run_p, racc);
+                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f);
+                racc = 0.f;
+                run_p = pn;
+              }
+              racc = fmaf(fda[uu], ga[uu], fmaf(fa[uu], gda[uu], racc));
+            }
           }
-          racc += W.stage[q][4 + s_my] * W.stage[q][8 + m_my] + W.stage[q][s_my] * W.stage[q][16 + m_my];
         }
         __syncwarp();
       }
-      if (run_p >= 0) W.acc[run_p * 32 + lane] += racc;
-      __syncwarp();
-      for (int c = lane; c < NPAIR * 32; c += 32) store_out<OutT>(out + NRAD + c, W.acc[c], 1.f);
+      if (run_p >= 0) put(run_p, racc);
+      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f);
     }
     __syncwarp();
   }
@@ -881,7 +941,7 @@ static fnn_status tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_tangent", s);
-    k_aev_tangent<OutT><<<2 * aev_grid(ctx, rows, 12), TAN_WARPS * 32, 0, s>>>(a);
+    k_aev_tangent<OutT><<<aev_grid(ctx, rows, TAN_BLOCKS), TAN_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_tangent");
 }
