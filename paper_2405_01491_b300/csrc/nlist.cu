@@ -10,8 +10,8 @@
 //   k_bin           per atom: cell index, histogram (atomics)
 //   scan            cell counts -> cell starts (counting sort)
 //   k_scatter       atoms into cells; k_sort_cells orders each cell by atom index (determinism)
-//   k_pairs_stage   warp per atom: 27-cell stencil, predicate, ballot + popc compaction into the
-//                   atom's 128-entry staging slot, and its count
+//   k_pairs_stage   block per cell: its 27-cell stencil staged in shared memory, a warp per centre atom:
+//                   predicate, ballot + popc compaction into the atom's 128-entry staging slot, its count
 //   scan            counts -> CSR row pointers
 //   k_pairs_compact staged rows copied into the CSR list (rows longer than the slot: traversed again)
 //   (the allocation-free entry point keeps the two-traversal form: k_pairs<COUNT>, scan, k_pairs<FILL>)
@@ -697,23 +697,97 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
 
 // PAIR_STRIDE (fnn_internal.cuh): staged entries per atom; longer rows are traversed again at compaction
 
-// pass 1: every atom's neighbours into its own PAIR_STRIDE-entry slot of the staging buffer, and its count
-__global__ void __launch_bounds__(256) k_pairs_stage(fnn_system sys, const MolGrid *grid, const int32_t *mol_base,
-                                                     const int32_t *atom_mol, const int32_t *cell_of,
-                                                     const int32_t *cell_start, const int32_t *cell_atoms,
-                                                     const float4 *cell_pos, PredConst pc, int32_t *counts,
-                                                     int32_t *tnbr, char4 *tshift,
-                                                     const int32_t *meta) {
+// pass 1, a block per cell: the cell's stencil candidates (positions and atoms, in the traversal order of
+// pairs_row) are staged in shared memory once and tested by each warp against its centre atoms of the
+// cell, so every centre's row comes out exactly as pairs_row writes it: into the atom's own
+// PAIR_STRIDE-entry slot of the staging buffer, with its count.  A cell whose stencil holds more than
+// CELL_CAND candidates is traversed per centre from global memory instead.
+constexpr int CELL_WARPS = 4, CELL_CAND = 1024;
+
+__global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys, const MolGrid *grid,
+                                                                 const int32_t *mol_base, const int32_t *atom_mol,
+                                                                 const int32_t *cell_of, const int32_t *cell_start,
+                                                                 const int32_t *cell_atoms, const float4 *cell_pos,
+                                                                 PredConst pc, int32_t *counts, int32_t *tnbr,
+                                                                 char4 *tshift, const int32_t *meta) {
+  __shared__ float4 cpos[CELL_CAND];
+  __shared__ int32_t cidx[CELL_CAND];
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
-  const int lane = threadIdx.x & 31;
-  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  const int n_binned = cell_start[meta[META_CELLS]];
-  for (int w = wg; w < n_binned; w += nw) {
-    const int i = cell_atoms[w];   // cell order: neighbouring warps share neighbour cells
-    const int64_t base = (int64_t)i * PAIR_STRIDE;
-    const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc, tnbr, tshift,
-                                base, base + PAIR_STRIDE);
-    if (lane == 0) counts[i] = count;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int n_cells = meta[META_CELLS];
+  for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    const int a0 = cell_start[c], a1 = cell_start[c + 1];
+    if (a0 == a1) continue;   // empty cell (uniform over the block)
+    const int m = atom_mol[cell_atoms[a0]];
+    const MolGrid g = grid[m];
+    const int mb = mol_base[m];
+    const int cl = c - mb;
+    const int cx = cl % g.dx, cy = (cl / g.dx) % g.dy, cz = cl / (g.dx * g.dy);
+    int ox[3], oy[3], oz[3];
+    const int nox = stencil(cx, g.dx, g.pbc, ox), noy = stencil(cy, g.dy, g.pbc, oy), noz = stencil(cz, g.dz, g.pbc, oz);
+    // the stencil's runs of consecutive cells, in pairs_row's order: f(first candidate, run length)
+    auto runs = [&](auto &&f) {
+      for (int a = 0; a < noz; a++)
+        for (int b = 0; b < noy; b++) {
+          const int rowc = mb + (oz[a] * g.dy + oy[b]) * g.dx;
+          for (int q = 0; q < nox;) {
+            const int x0 = ox[q];
+            int x1 = x0;
+            for (q++; q < nox && ox[q] == x1 + 1; q++) x1 = ox[q];
+            const int s0 = cell_start[rowc + x0];
+            f(s0, cell_start[rowc + x1 + 1] - s0);
+          }
+        }
+    };
+    int total = 0;
+    runs([&](int, int len) { total += len; });
+    if (total <= CELL_CAND) {
+      __syncthreads();   // the previous cell's candidates are no longer read
+      int off = 0;
+      runs([&](int s0, int len) {
+        for (int k = threadIdx.x; k < len; k += CELL_WARPS * 32) {
+          cpos[off + k] = cell_pos[s0 + k];
+          cidx[off + k] = cell_atoms[s0 + k];
+        }
+        off += len;
+      });
+      __syncthreads();
+      for (int w = a0 + warp; w < a1; w += CELL_WARPS) {
+        const int i = cell_atoms[w];
+        const float4 pi = pos[i];
+        const int64_t base = (int64_t)i * PAIR_STRIDE;
+        int count = 0;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+          const int k = k0 + lane;
+          bool in = false;
+          int j = -1;
+          char4 sh = make_char4(0, 0, 0, 0);
+          if (k < total) {
+            j = cidx[k];
+            in = pair_in(pi, cpos[k], g, pc, sh) && j != i;
+          }
+          const unsigned mask = __ballot_sync(FULL, in);
+          if (in) {
+            const int at = count + __popc(mask & lt);
+            if (at < PAIR_STRIDE) {
+              tnbr[base + at] = j;
+              tshift[base + at] = sh;
+            }
+          }
+          count += __popc(mask);
+        }
+        if (lane == 0) counts[i] = count;
+      }
+    } else {
+      for (int w = a0 + warp; w < a1; w += CELL_WARPS) {
+        const int i = cell_atoms[w];
+        const int64_t base = (int64_t)i * PAIR_STRIDE;
+        const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc,
+                                    tnbr, tshift, base, base + PAIR_STRIDE);
+        if (lane == 0) counts[i] = count;
+      }
+    }
   }
 }
 
@@ -1128,9 +1202,10 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     PredConst pc{R * R, (float)(R * R), (float)R};
     int pb = (int)(((int64_t)N * 32 + 255) / 256);
     if (pb > 32 * ctx->num_sms) pb = 32 * ctx->num_sms;
+    const int cb = (int)(cells_bound < 8 * (int64_t)ctx->num_sms ? cells_bound : 8 * (int64_t)ctx->num_sms);
     {
       FNN_KERNEL(ctx, "pairs_stage", s);
-      k_pairs_stage<<<pb, 256, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
+      k_pairs_stage<<<cb > 0 ? cb : 1, CELL_WARPS * 32, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_start,
                                        nl->cell_atoms, nl->cell_pos, pc, nl->counts, nl->stage_nbr, nl->stage_shift,
                                        nl->meta);
     }
