@@ -414,6 +414,19 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
         __syncwarp();
         const int nt = min(32, T - base);
         const float *fr = W.sf[s_my], *gr = W.sg[m_my];
+        if (starts == 0u && nt == 32) {   // the whole batch continues the running block
+#pragma unroll
+          for (int q = 0; q < 32; q += 4) {
+            const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
+            const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
+            racc = fmaf(fv.x, gv.x, racc);
+            racc = fmaf(fv.y, gv.y, racc);
+            racc = fmaf(fv.z, gv.z, racc);
+            racc = fmaf(fv.w, gv.w, racc);
+          }
+          __syncwarp();
+          continue;
+        }
         // four triplets per step: within the running block four FMAs; where a block opens, the block
         // before it is complete (and any between them empty)
         for (int q = 0; q < nt; q += 4) {

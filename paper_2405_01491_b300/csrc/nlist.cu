@@ -579,9 +579,11 @@ struct PredConst {
 // errs by at most 2 sqrt(3) e R + 3 e^2 + 4 u R^2.  Twice that bound, with S the largest magnitude over
 // the whole structure (MolGrid::tau), is the band re-tested in float64.  The image n = -rint(dx / L)
 // is formed with 1/L: for a pair within R < L/2, dx/L is far from a half-integer, so n is the same.
-__device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, const PredConst &pc, char4 &sh) {
+// (the image shift n of a pair is returned as floats; make_shift packs it where the pair is kept)
+__device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, const PredConst &pc, float &nx,
+                                        float &ny, float &nz) {
   float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-  float nx = 0.f, ny = 0.f, nz = 0.f;
+  nx = ny = nz = 0.f;
   if (g.pbc) {
     nx = -rintf(dx * g.iLx);
     ny = -rintf(dy * g.iLy);
@@ -590,7 +592,6 @@ __device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, 
     dy = fmaf(ny, g.Ly, dy);
     dz = fmaf(nz, g.Lz, dz);
   }
-  sh = make_char4((signed char)nx, (signed char)ny, (signed char)nz, 0);
   float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   if (d2 < pc.R2f - g.tau) return true;
   if (d2 > pc.R2f + g.tau) return false;
@@ -603,6 +604,9 @@ __device__ __forceinline__ bool pair_in(float4 pi, float4 pj, const MolGrid &g, 
   double ez = __dadd_rn(rz, __dmul_rn((double)nz, (double)g.Lz));
   double D2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
   return D2 < pc.R2d;
+}
+__device__ __forceinline__ char4 make_shift(float nx, float ny, float nz) {
+  return make_char4((signed char)nx, (signed char)ny, (signed char)nz, 0);
 }
 
 __device__ __forceinline__ int stencil(int c, int d, int pbc, int *out) {
@@ -652,18 +656,18 @@ __device__ __forceinline__ int pairs_row(int i, const float4 *pos, const MolGrid
           const int k = k0 + lane;
           bool in = false;
           int j = -1;
-          char4 sh = make_char4(0, 0, 0, 0);
+          float nx, ny, nz;
           if (k < s1) {
             const float4 pj = cell_pos[k];
             j = cell_atoms[k];
-            in = pair_in(pi, pj, g, pc, sh) && j != i;
+            in = pair_in(pi, pj, g, pc, nx, ny, nz) && j != i;
           }
           const unsigned mask = __ballot_sync(FULL, in);
           if (in) {
             const int64_t idx = base + count + __popc(mask & lt);
             if (idx < limit) {
               nbr[idx] = j;
-              shift[idx] = sh;
+              shift[idx] = make_shift(nx, ny, nz);
             }
           }
           count += __popc(mask);
@@ -762,17 +766,17 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
           const int k = k0 + lane;
           bool in = false;
           int j = -1;
-          char4 sh = make_char4(0, 0, 0, 0);
+          float nx, ny, nz;
           if (k < total) {
             j = cidx[k];
-            in = pair_in(pi, cpos[k], g, pc, sh) && j != i;
+            in = pair_in(pi, cpos[k], g, pc, nx, ny, nz) && j != i;
           }
           const unsigned mask = __ballot_sync(FULL, in);
           if (in) {
             const int at = count + __popc(mask & lt);
             if (at < PAIR_STRIDE) {
               tnbr[base + at] = j;
-              tshift[base + at] = sh;
+              tshift[base + at] = make_shift(nx, ny, nz);
             }
           }
           count += __popc(mask);
