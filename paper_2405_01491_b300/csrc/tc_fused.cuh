@@ -41,6 +41,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16]) 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 2^x on the special-function unit (ex2.approx.ftz, arguments <= 0 here); exp(x) = 2^(x log2 e)
+constexpr float LOG2E = 1.4426950408889634f;
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -339,9 +347,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int u = 0; u < 2; u++) {
               const float z = v[2 * jj + u] + __shfl_sync(0xffffffffu, pre[i], 2 * jj + u);
               const float w = __shfl_sync(0xffffffffu, pre[i], 16 + 2 * jj + u);
-              const float ez = __expf(fminf(z, 0.f) * CELU_INV_ALPHA);
-              ysum += (z > 0.f ? z : CELU_ALPHA * (ez - 1.f)) * w;
-              g[u] = p.scale * w * (z > 0.f ? 1.f : ez);
+              const float ez = exp2_approx(fminf(z, 0.f) * (CELU_INV_ALPHA * LOG2E));   // exp(min(z, 0) / alpha)
+              const bool pos = z > 0.f;
+              ysum = fmaf(pos ? z : fmaf(CELU_ALPHA, ez, -CELU_ALPHA), w, ysum);
+              g[u] = (p.scale * w) * (pos ? 1.f : ez);
             }
             const __nv_bfloat162 hi = __floats2bfloat162_rn(g[0], g[1]);
             const float2 hf = __bfloat1622float2(hi);
