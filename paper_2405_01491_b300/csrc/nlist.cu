@@ -701,7 +701,8 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
 
 // PAIR_STRIDE (fnn_internal.cuh): staged entries per atom; longer rows are traversed again at compaction
 
-// pass 1, a block per cell: the cell's stencil candidates (positions and atoms, in the traversal order of
+// pass 1, a block per cell (or per slice of a cell's centres when there are fewer cells than blocks): the
+// cell's stencil candidates (positions and atoms, in the traversal order of
 // pairs_row) are staged in shared memory once and tested by each warp against its centre atoms of the
 // cell, so every centre's row comes out exactly as pairs_row writes it: into the atom's own
 // PAIR_STRIDE-entry slot of the staging buffer, with its count.  A cell whose stencil holds more than
@@ -720,9 +721,12 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int n_cells = meta[META_CELLS];
-  for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+  // with fewer cells than blocks, S blocks share a cell, block slice sl taking its centres sl, sl + S, ...
+  const int S = n_cells > 0 ? max(1, min(8, (int)gridDim.x / n_cells)) : 1;
+  for (int t = blockIdx.x; t < n_cells * S; t += gridDim.x) {
+    const int c = t / S, sl = t - c * S;
     const int a0 = cell_start[c], a1 = cell_start[c + 1];
-    if (a0 == a1) continue;   // empty cell (uniform over the block)
+    if (a0 + sl * CELL_WARPS >= a1) continue;   // no centres for this slice (uniform over the block)
     const int m = atom_mol[cell_atoms[a0]];
     const MolGrid g = grid[m];
     const int mb = mol_base[m];
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
         off += len;
       });
       __syncthreads();
-      for (int w = a0 + warp; w < a1; w += CELL_WARPS) {
+      for (int w = a0 + sl * CELL_WARPS + warp; w < a1; w += S * CELL_WARPS) {
         const int i = cell_atoms[w];
         const float4 pi = pos[i];
         const int64_t base = (int64_t)i * PAIR_STRIDE;
@@ -784,7 +788,7 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
         if (lane == 0) counts[i] = count;
       }
     } else {
-      for (int w = a0 + warp; w < a1; w += CELL_WARPS) {
+      for (int w = a0 + sl * CELL_WARPS + warp; w < a1; w += S * CELL_WARPS) {
         const int i = cell_atoms[w];
         const int64_t base = (int64_t)i * PAIR_STRIDE;
         const int count = pairs_row(i, pos, grid, mol_base, atom_mol, cell_of, cell_start, cell_atoms, cell_pos, pc,
