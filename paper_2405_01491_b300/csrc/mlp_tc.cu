@@ -513,6 +513,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
     tc::L3Args l{};
     l.n_rowtiles = (int)tiles; l.n_members = M; l.tile_elem = nl->tile_elem;
     l.b3 = w.b3; l.w4 = w.w4; l.ypart = ctx->ws.ypart; l.M = M; l.scale = 1.f / (float)M; l.st = ctx->status;
+    l.reverse = 1;   // the second-layer forward wrote the last tiles last
     // (64-byte operand rows: twice the ring stages for the same bytes in flight)
     const CUtensorMap *maps[10] = {&H.qH2, &L.qH2, &H.qW3, &L.qW3, &H.qW3T, &L.qW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
     if ((st = launch_l3_pair<MODE, 64>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;

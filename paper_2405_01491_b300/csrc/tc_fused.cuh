@@ -61,6 +61,7 @@ struct L3Args {
   int M;
   float scale;                 // 1/M
   DevStatus *st;
+  int reverse;                 // tiles last to first: h2's most recently written tiles (still in L2) first
 };
 
 constexpr int L3_N1 = H3, L3_N2 = H2, L3_K1 = H2, L3_K2 = H3;
@@ -97,6 +98,7 @@ constexpr size_t l3_smem_bytes() {
 
 // tile t -> (row tile, member, element); false for padding tiles
 __device__ __forceinline__ bool l3_tile(const L3Args &p, int t, int &rt, int &m, int &e) {
+  if (p.reverse) t = p.n_rowtiles * p.n_members - 1 - t;
   rt = t % p.n_rowtiles;
   m = t / p.n_rowtiles;
   e = p.tile_elem[rt];
