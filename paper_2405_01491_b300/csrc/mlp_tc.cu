@@ -116,15 +116,20 @@ struct Maps {
 };
 
 // zero the output tiles a tail-split EPI_F32 launch of grid G will add into (tail_sched): one block per tile
-__global__ void k_zero_tail(tc::Args p, int G, int nkb, int NT) {
+// ZT_PARTS blocks of 64 threads per tile, each clearing BM / ZT_PARTS rows with 16-byte stores (the
+// output's columns and row stride are multiples of four floats)
+constexpr int ZT_PARTS = 8;
+__global__ void __launch_bounds__(64) k_zero_tail(tc::Args p, int G, int nkb, int NT) {
   const tc::TailSched ts = tc::tail_sched(p, G, nkb);
-  if ((int)blockIdx.x >= ts.R) return;
-  const int t = ts.W * G + (int)blockIdx.x;
+  const int tile = (int)blockIdx.x / ZT_PARTS, part = (int)blockIdx.x % ZT_PARTS;
+  if (tile >= ts.R) return;
+  const int t = ts.W * G + tile;
   const int nt = t % p.n_ntiles, rest = t / p.n_ntiles, rt = rest % ts.nv, m = rest / ts.nv;
-  const int c0 = nt * NT, nc = min(NT, p.N - c0);
-  for (int k = threadIdx.x; k < tc::BM * nc; k += blockDim.x) {
-    const int r = k / nc, c = k - r * nc;
-    p.out[((long long)rt * tc::BM + r) * p.ldo + m * p.o_mstride + c0 + c] = 0.f;
+  const int c0 = nt * NT, n4 = min(NT, p.N - c0) / 4;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int rr = 0; rr < tc::BM / ZT_PARTS; rr++) {
+    float *row = p.out + ((long long)rt * tc::BM + part * (tc::BM / ZT_PARTS) + rr) * p.ldo + m * p.o_mstride + c0;
+    for (int c4 = threadIdx.x; c4 < n4; c4 += 64) reinterpret_cast<float4 *>(row)[c4] = z;
   }
 }
 
@@ -529,7 +534,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
     return st;
   {
     FNN_KERNEL(ctx, "zero_tail", ctx->side);
-    k_zero_tail<<<G1, 256, 0, ctx->side>>>(az, G1, nkb1, 256);
+    k_zero_tail<<<G1 * ZT_PARTS, 64, 0, ctx->side>>>(az, G1, nkb1, 256);
   }
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
   a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;

@@ -32,6 +32,9 @@ def structure(name: str):
         "box300": lambda: synth.mix_box(300, (300 / 0.1) ** (1 / 3), seed=31),
         "box1500": lambda: synth.mix_box(1500, (1500 / 0.1) ** (1 / 3), seed=32,
                                          fractions=synth.MIX7),
+        # a 20 A periodic box (3 cells per axis: every cell's stencil is the whole box, 1100 candidates,
+        # more than the pair search stages in shared memory, so its per-centre traversal runs)
+        "box1100": lambda: synth.mix_box(1100, 20.0, seed=36, fractions=synth.MIX7),
         # three periodic boxes in one batch: structures large enough that each one's float64 energy is
         # summed in several slices, with more than one such structure at once
         "boxes3": lambda: synth.concat([synth.mix_box(n, (n / 0.1) ** (1 / 3), seed=33 + k, fractions=synth.MIX7)

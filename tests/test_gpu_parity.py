@@ -40,7 +40,7 @@ def as_set(ei, ej, es):
 
 
 @pytest.mark.parametrize("name,skin", [("gas24", 0.0), ("water216", 1.0), ("box300", 0.0), ("box1500", 1.0),
-                                       ("batch64", 0.0), ("mix23558", 0.0), ("mix23558", 1.0)])
+                                       ("box1100", 0.0), ("batch64", 0.0), ("mix23558", 0.0), ("mix23558", 1.0)])
 def test_neighbor_list_bit_exact(fnn, name, skin):
     s = structure(name)
     _, _, _, got = gpu_list(fnn, s, skin)
@@ -143,7 +143,7 @@ FP32_FORMS = ["fp32", "fp32x3"]   # SIMT FFMA, and the three-term bf16 split on 
 
 @pytest.mark.parametrize("precision", FP32_FORMS)
 @pytest.mark.parametrize("name,M,skin", [("gas24", 1, 0.0), ("water216", 8, 1.0), ("box1500", 2, 0.0),
-                                         ("batch64", 1, 0.5)])
+                                         ("box1100", 1, 0.0), ("batch64", 1, 0.5)])
 def test_energy_forces_fp32_parity(fnn, name, M, skin, precision):
     s = structure(name)
     _, _, _, E, F, W = _energy_case(fnn, s, M, skin, precision=precision)
