@@ -686,6 +686,7 @@ struct AevTanArgs {
   AevParams P;
   const float *V;         // [N][3] displacement field
   void *out;              // [rows][1008], float or bf16
+  __nv_bfloat16 *out_fwd; // the AEV rows themselves (bf16), or NULL: the same sums as k_aev_forward's, in its order
   const int32_t *inv;     // padded row -> atom; NULL = rows are atoms
   const int32_t *meta;
   int n_atoms;
@@ -708,8 +709,12 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
     int i = A.inv ? A.inv[row] : row;
     int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
     bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st);
+    __nv_bfloat16 *fout = A.out_fwd ? A.out_fwd + (size_t)row * NAEV : nullptr;
     if (!ok) {
-      for (int c = lane; c < NAEV; c += 32) store_out<OutT>(out + c, 0.f, 1.f);
+      for (int c = lane; c < NAEV; c += 32) {
+        store_out<OutT>(out + c, 0.f, 1.f);
+        if (fout) fout[c] = __float2bfloat16(0.f);
+      }
       __syncwarp();
       continue;
     }
@@ -731,14 +736,20 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       float Rk = P.shf_r[k];
 #pragma unroll 1
       for (int q = 0; q < NE; q++) {
-        float acc = 0.f;
+        float acc = 0.f, accf = 0.f;
         for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
           const float dr = S.rd[t].w - Rk;
           const float2 ft = W.rt[t];
-          acc += __expf(-P.eta_r * dr * dr) * (-2.f * P.eta_r * dr * ft.x + ft.y);
+          const float gk = __expf(-P.eta_r * dr * dr);
+          acc += gk * (-2.f * P.eta_r * dr * ft.x + ft.y);
+          accf += gk * S.rfc[t];
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
-        if (lane < 16) store_out<OutT>(out + q * NSR + k, 0.25f * acc, 1.f);
+        accf += __shfl_xor_sync(FULL, accf, 16);
+        if (lane < 16) {
+          store_out<OutT>(out + q * NSR + k, 0.25f * acc, 1.f);
+          if (fout) fout[q * NSR + k] = __float2bfloat16(0.25f * accf);
+        }
       }
     }
     __syncwarp();   // the batch rows below reuse the radial staging
@@ -749,8 +760,11 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       const int n = off_a[NE];
       const int T = n * (n - 1) / 2;
       int run_p = -1;
-      float racc = 0.f;
-      auto put = [&](int pp, float v) { store_out<OutT>(out + NRAD + pp * 32 + lane, v, 1.f); };
+      float racc = 0.f, raccf = 0.f;   // tangent and (fout) forward sums of the running block
+      auto put = [&](int pp, float v, float vf) {
+        store_out<OutT>(out + NRAD + pp * 32 + lane, v, 1.f);
+        if (fout) fout[NRAD + pp * 32 + lane] = __float2bfloat16(vf);
+      };
       int cp = 0, cu = 0;
       for (int base = 0; base < T; base += 32) {
         int pb, ja, ka;
@@ -759,7 +773,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
           const float r1 = d1.w, r2 = d2.w, ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
-          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
+          // cos theta formed as the forward kernel forms it, so that the AEV rows of this pass equal its rows
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(r1 * r2);
           const float cdot = (d2.x * v1.x + d2.y * v1.y + d2.z * v1.z + d1.x * v2.x + d1.y * v2.y + d1.z * v2.z) * inv12 -
                              c * (v1.w * ir1 + v2.w * ir2);
           const float c95 = 0.95f * c;
@@ -806,6 +821,10 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
             racc = fmaf(fdv.y, gv.y, fmaf(fv.y, gdv.y, racc));
             racc = fmaf(fdv.z, gv.z, fmaf(fv.z, gdv.z, racc));
             racc = fmaf(fdv.w, gv.w, fmaf(fv.w, gdv.w, racc));
+            raccf = fmaf(fv.x, gv.x, raccf);
+            raccf = fmaf(fv.y, gv.y, raccf);
+            raccf = fmaf(fv.z, gv.z, raccf);
+            raccf = fmaf(fv.w, gv.w, raccf);
           } else {
             const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, fda[4] = {fdv.x, fdv.y, fdv.z, fdv.w};
             const float ga[4] = {gv.x, gv.y, gv.z, gv.w}, gda[4] = {gdv.x, gdv.y, gdv.z, gdv.w};
@@ -814,19 +833,20 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
               if (q + uu >= nt) break;
               if ((st4 >> uu) & 1u) {
                 const int pn = W.b.sp[q + uu];
-                if (run_p >= 0) put(run_p, racc);
-                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f);
-                racc = 0.f;
+                if (run_p >= 0) put(run_p, racc, raccf);
+                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f, 0.f);
+                racc = raccf = 0.f;
                 run_p = pn;
               }
               racc = fmaf(fda[uu], ga[uu], fmaf(fa[uu], gda[uu], racc));
+              raccf = fmaf(fa[uu], ga[uu], raccf);
             }
           }
         }
         __syncwarp();
       }
-      if (run_p >= 0) put(run_p, racc);
-      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f);
+      if (run_p >= 0) put(run_p, racc, raccf);
+      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f, 0.f);
     }
     __syncwarp();
   }
@@ -940,12 +960,13 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
 
 template <typename OutT>
 static fnn_status tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, OutT *out,
-                          const int32_t *inv, cudaStream_t s) {
+                          __nv_bfloat16 *out_fwd, const int32_t *inv, cudaStream_t s) {
   AevTanArgs a;
   a.sa = stage_args(sys, nl);
   a.P = ctx->aev;
   a.V = V;
   a.out = out;
+  a.out_fwd = out_fwd;
   a.inv = inv;
   a.meta = nl->meta;
   a.n_atoms = sys->n_atoms;
@@ -961,11 +982,11 @@ static fnn_status tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
 
 fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
                               const int32_t *inv, cudaStream_t s) {
-  return tangent<float>(ctx, sys, nl, V, out, inv, s);
+  return tangent<float>(ctx, sys, nl, V, out, nullptr, inv, s);
 }
 fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
-                                   __nv_bfloat16 *out, const int32_t *inv, cudaStream_t s) {
-  return tangent<__nv_bfloat16>(ctx, sys, nl, V, out, inv, s);
+                                   __nv_bfloat16 *out, __nv_bfloat16 *out_fwd, const int32_t *inv, cudaStream_t s) {
+  return tangent<__nv_bfloat16>(ctx, sys, nl, V, out, out_fwd, inv, s);
 }
 
 }  // namespace fnn

@@ -275,8 +275,9 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
                               const int32_t *inv, float *F, double *virial, cudaStream_t s);
 fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *out,
                               const int32_t *inv, cudaStream_t s);
+// bf16 tangent rows, and (out_fwd != NULL) the bf16 AEV rows of the same pass, equal to launch_aev_forward_bf16's
 fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
-                                   __nv_bfloat16 *out, const int32_t *inv, cudaStream_t s);
+                                   __nv_bfloat16 *out, __nv_bfloat16 *out_fwd, const int32_t *inv, cudaStream_t s);
 fnn_status mlp_fp32_forward_backward(fnn_ctx *ctx, const fnn_nlist *nl, cudaStream_t s);
 fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
                      cudaStream_t s);

@@ -841,9 +841,8 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   const int rows = nl->pad_cap;
   const unsigned tiles = (unsigned)(rows / ROW_TILE);
   constexpr int B16 = tc::MODE_BF16;
-  // AEV and its tangent along dL/dF (bf16)
-  if ((st = launch_aev_forward_bf16(ctx, sys, nl, H.aev, nullptr, nl->inv, s))) return st;
-  if ((st = launch_aev_tangent_bf16(ctx, sys, nl, dLdF, T.t, nl->inv, s))) return st;
+  // AEV and its tangent along dL/dF (bf16), in one pass over the triplets
+  if ((st = launch_aev_tangent_bf16(ctx, sys, nl, dLdF, T.t, H.aev, nl->inv, s))) return st;
   tc::Args a{};
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
