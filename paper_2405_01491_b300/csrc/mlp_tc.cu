@@ -678,62 +678,118 @@ __device__ __forceinline__ float dcelu_hb(float h) { return h > 0.f ? 1.f : 1.f 
 __device__ __forceinline__ float ratio_hb(float h) { return h > 0.f ? 0.f : CELU_INV_ALPHA; }
 
 // output layer: gbz3 = CELU'(h3) (-(1/M) w4), gz3 = CELU'(h3) ((1/M) dL/dE w4) + ratio(h3) hd3 gb3;
-// dw4 += (1/M) dL/dE h3 - (1/M) hd3, db4 += (1/M) dL/dE, db3 += gz3 (sums per tile, one atomic each)
-__global__ void k_out_reverse_bf16(int M, const int32_t *tile_elem, const int32_t *inv, const int32_t *atom_mol,
-                                   const double *dLdE, const float *w4, const __nv_bfloat16 *h3,
-                                   const __nv_bfloat16 *hd3, __nv_bfloat16 *gbz3, __nv_bfloat16 *gz3, float *dw4,
-                                   float *db4, float *db3) {
-  const int tile = blockIdx.x, m = blockIdx.y, n = threadIdx.x;   // blockDim.x = H3
-  const int e = tile_elem[tile];
-  if (e < 0) return;
-  const float w = w4[((size_t)m * NE + e) * H3 + n];
-  const float c = 1.f / (float)M;
-  float acc_w = 0.f, acc_b = 0.f, acc_b3 = 0.f;
-  for (int rr = 0; rr < ROW_TILE; rr++) {
-    const size_t r = (size_t)tile * ROW_TILE + rr;
-    const int i = inv[r];
-    const size_t o = r * (size_t)M * H3 + (size_t)m * H3 + n;
-    const int mol = i < 0 ? -1 : atom_mol[i];
-    if (mol < 0) {
-      gbz3[o] = __float2bfloat16(0.f);
-      gz3[o] = __float2bfloat16(0.f);
-      continue;
-    }
-    const float cE = (float)dLdE[mol] * c;
-    const float h = __bfloat162float(h3[o]), hd = __bfloat162float(hd3[o]);
-    const float s1 = dcelu_hb(h);
-    const float gb = -c * w, g = cE * w;
-    const float gz = s1 * g + ratio_hb(h) * hd * gb;
-    gbz3[o] = __float2bfloat16(s1 * gb);
-    gz3[o] = __float2bfloat16(gz);
-    acc_w += cE * h - c * hd;
-    acc_b += cE;
-    acc_b3 += gz;
-  }
-  atomicAdd(&dw4[((size_t)m * NE + e) * H3 + n], acc_w);
-  atomicAdd(&db3[((size_t)m * NE + e) * H3 + n], acc_b3);
-  if (n == 0) atomicAdd(&db4[(size_t)m * NE + e], acc_b);
-}
-
-// hidden layer: (raw gb, g) -> gbz = CELU'(h) gb, gz = CELU'(h) g + ratio(h) hd gb; db += gz per tile
-__global__ void k_act_reverse_bf16(int M, int F, const int32_t *tile_elem, const __nv_bfloat16 *h,
-                                   const __nv_bfloat16 *hd, const __nv_bfloat16 *gb, const __nv_bfloat16 *g,
-                                   __nv_bfloat16 *gbz, __nv_bfloat16 *gz, float *db) {
+// dw4 += (1/M) dL/dE h3 - (1/M) hd3, db4 += (1/M) dL/dE, db3 += gz3 (sums per tile, one atomic each).
+// blockDim = H3: thread (feature group fg of 8, row lane rl of 8) moves 16 bytes per array and row
+__global__ void __launch_bounds__(H3) k_out_reverse_bf16(int M, const int32_t *tile_elem, const int32_t *inv,
+                                                         const int32_t *atom_mol, const double *dLdE, const float *w4,
+                                                         const __nv_bfloat16 *h3, const __nv_bfloat16 *hd3,
+                                                         __nv_bfloat16 *gbz3, __nv_bfloat16 *gz3, float *dw4,
+                                                         float *db4, float *db3) {
+  __shared__ float red_w[8][H3], red_b3[8][H3];
+  __shared__ float red_b[8];
+  constexpr int G8 = H3 / 8;
   const int tile = blockIdx.x, m = blockIdx.y;
   const int e = tile_elem[tile];
   if (e < 0) return;
-  for (int n = threadIdx.x; n < F; n += blockDim.x) {
-    float acc = 0.f;
-    for (int rr = 0; rr < ROW_TILE; rr++) {
-      const size_t o = ((size_t)tile * ROW_TILE + rr) * (size_t)M * F + (size_t)m * F + n;
-      const float hv = __bfloat162float(h[o]), b = __bfloat162float(gb[o]);
-      const float s1 = dcelu_hb(hv);
-      const float z = s1 * __bfloat162float(g[o]) + ratio_hb(hv) * __bfloat162float(hd[o]) * b;
-      gbz[o] = __float2bfloat16(s1 * b);
-      gz[o] = __float2bfloat16(z);
-      acc += z;
+  const int fg = threadIdx.x % G8, rl = threadIdx.x / G8;
+  const float c = 1.f / (float)M;
+  float w[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) w[j] = w4[((size_t)m * NE + e) * H3 + 8 * fg + j];
+  float acc_w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, acc_b3[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float acc_b = 0.f;
+  for (int rr = rl; rr < ROW_TILE; rr += 8) {
+    const size_t r = (size_t)tile * ROW_TILE + rr;
+    const int i = inv[r];
+    const size_t o = r * (size_t)M * H3 + (size_t)m * H3 + 8 * fg;
+    const int mol = i < 0 ? -1 : atom_mol[i];
+    alignas(16) __nv_bfloat16 hv[8], hdv[8], ob[8], oz[8];
+    if (mol < 0) {
+      *reinterpret_cast<uint4 *>(gbz3 + o) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(gz3 + o) = make_uint4(0u, 0u, 0u, 0u);
+      continue;
     }
-    atomicAdd(&db[((size_t)m * NE + e) * F + n], acc);
+    const float cE = (float)dLdE[mol] * c;
+    *reinterpret_cast<uint4 *>(hv) = *reinterpret_cast<const uint4 *>(h3 + o);
+    *reinterpret_cast<uint4 *>(hdv) = *reinterpret_cast<const uint4 *>(hd3 + o);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const float h = __bfloat162float(hv[j]), hd = __bfloat162float(hdv[j]);
+      const float s1 = dcelu_hb(h);
+      const float gb = -c * w[j], g = cE * w[j];
+      const float gz = s1 * g + ratio_hb(h) * hd * gb;
+      ob[j] = __float2bfloat16(s1 * gb);
+      oz[j] = __float2bfloat16(gz);
+      acc_w[j] += cE * h - c * hd;
+      acc_b3[j] += gz;
+    }
+    *reinterpret_cast<uint4 *>(gbz3 + o) = *reinterpret_cast<const uint4 *>(ob);
+    *reinterpret_cast<uint4 *>(gz3 + o) = *reinterpret_cast<const uint4 *>(oz);
+    acc_b += cE;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    red_w[rl][8 * fg + j] = acc_w[j];
+    red_b3[rl][8 * fg + j] = acc_b3[j];
+  }
+  if (fg == 0) red_b[rl] = acc_b;
+  __syncthreads();
+  const int n = threadIdx.x;
+  float tw = 0.f, tb3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    tw += red_w[q][n];
+    tb3 += red_b3[q][n];
+  }
+  atomicAdd(&dw4[((size_t)m * NE + e) * H3 + n], tw);
+  atomicAdd(&db3[((size_t)m * NE + e) * H3 + n], tb3);
+  if (n == 0) {
+    float tb = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) tb += red_b[q];
+    atomicAdd(&db4[(size_t)m * NE + e], tb);
+  }
+}
+
+// hidden layer: (raw gb, g) -> gbz = CELU'(h) gb, gz = CELU'(h) g + ratio(h) hd gb; db += gz per tile.
+// blockDim = F: thread (feature group fg of 8, row lane rl of 8) moves 16 bytes per array and row
+__global__ void __launch_bounds__(256) k_act_reverse_bf16(int M, int F, const int32_t *tile_elem,
+                                                          const __nv_bfloat16 *h, const __nv_bfloat16 *hd,
+                                                          const __nv_bfloat16 *gb, const __nv_bfloat16 *g,
+                                                          __nv_bfloat16 *gbz, __nv_bfloat16 *gz, float *db) {
+  __shared__ float red[8][256];
+  const int tile = blockIdx.x, m = blockIdx.y;
+  const int e = tile_elem[tile];
+  if (e < 0) return;
+  const int G8 = F / 8, fg = threadIdx.x % G8, rl = threadIdx.x / G8;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int rr = rl; rr < ROW_TILE; rr += 8) {
+    const size_t o = ((size_t)tile * ROW_TILE + rr) * (size_t)M * F + (size_t)m * F + 8 * fg;
+    alignas(16) __nv_bfloat16 hv[8], hdv[8], gbv[8], gv[8], ob[8], oz[8];
+    *reinterpret_cast<uint4 *>(hv) = *reinterpret_cast<const uint4 *>(h + o);
+    *reinterpret_cast<uint4 *>(hdv) = *reinterpret_cast<const uint4 *>(hd + o);
+    *reinterpret_cast<uint4 *>(gbv) = *reinterpret_cast<const uint4 *>(gb + o);
+    *reinterpret_cast<uint4 *>(gv) = *reinterpret_cast<const uint4 *>(g + o);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const float x = __bfloat162float(hv[j]), b = __bfloat162float(gbv[j]);
+      const float s1 = dcelu_hb(x);
+      const float z = s1 * __bfloat162float(gv[j]) + ratio_hb(x) * __bfloat162float(hdv[j]) * b;
+      ob[j] = __float2bfloat16(s1 * b);
+      oz[j] = __float2bfloat16(z);
+      acc[j] += z;
+    }
+    *reinterpret_cast<uint4 *>(gbz + o) = *reinterpret_cast<const uint4 *>(ob);
+    *reinterpret_cast<uint4 *>(gz + o) = *reinterpret_cast<const uint4 *>(oz);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j++) red[rl][8 * fg + j] = acc[j];
+  __syncthreads();
+  if ((int)threadIdx.x < F) {
+    float t = 0.f;
+#pragma unroll
+    for (int r = 0; r < 8; r++) t += red[r][threadIdx.x];
+    atomicAdd(&db[((size_t)m * NE + e) * F + threadIdx.x], t);
   }
 }
 
@@ -923,7 +979,7 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   wg.st = ctx->status;
   wg.M = M;
   wg.seg = nl->meta + META_SEG;
-  wg.kchunk = 4096;
+  wg.kchunk = 1024;   // rows per work item: about four waves on 148 SMs for the 148,565-row batch (4096: two)
   wg.n_chunks = (rows + wg.kchunk - 1) / wg.kchunk;
   constexpr int WG = tc::MODE_WG;
   wg.K = 0;
