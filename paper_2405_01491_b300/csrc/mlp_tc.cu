@@ -100,12 +100,28 @@ struct TcState {
   size_t rows = 0;
   Half h[2];   // [0] hi, [1] lo
   F8 f8;
+  // fp32 dE/dAEV [rows][1008] as the input-gradient product's output map (32-row x 8-column boxes)
+  CUtensorMap mGaev;
+  const float *gaev_for = nullptr;
+  size_t gaev_rows = 0;
   void *train = nullptr;   // BF16 training buffers (tc_param_grads)
 };
 
 TcState *state(fnn_ctx *ctx) {
   if (!ctx->w.tc) ctx->w.tc = new TcState();
   return static_cast<TcState *>(ctx->w.tc);
+}
+
+// the output map of ws.gaev, re-encoded when the workspace moved
+static const CUtensorMap *gaev_map(fnn_ctx *ctx, TcState *t) {
+  if (t->gaev_for != ctx->ws.gaev || t->gaev_rows != ctx->ws.rows) {
+    if (!encode3d(&t->mGaev, ctx->ws.gaev, NAEV, 1, ctx->ws.rows, NAEV * 4, NAEV * 4, 8, 1, 32,
+                  CU_TENSOR_MAP_DATA_TYPE_FLOAT32, CU_TENSOR_MAP_SWIZZLE_NONE))
+      return nullptr;
+    t->gaev_for = ctx->ws.gaev;
+    t->gaev_rows = ctx->ws.rows;
+  }
+  return &t->mGaev;
 }
 
 // Operand, output and aux tensor maps of one product (lo = the split's low halves; unused ones may
@@ -553,9 +569,14 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   a.tail_split = 1; a.meta = nl->meta;
   // (split: 64-byte rows, four stages instead of two; measured faster here, slower for the forward first
   // layer and for the bf16 form)
-  const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1};
+  const CUtensorMap *og = gaev_map(ctx, t);
+  if (!og) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the dE/dAEV map";
+    return FNN_E_CUDA;
+  }
+  const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, og, og, &H.mG1, &L.mG1};
   if ((st = launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
-                                             {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, &H.mG1, &L.mG1, &H.mG1, &L.mG1},
+                                             {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, og, og, &H.mG1, &L.mG1},
                                              SPLIT ? &q6 : nullptr, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
     return st;
   return FNN_OK;
@@ -622,9 +643,13 @@ fnn_status run_layers_f8(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStre
   a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
   a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
   a.a_scale = f.act[5]; a.b_scale = f.wscale + 1 * MNE; a.b_scale_by = 0;
-  return launch<256, tc::EPI_F32, MODE>(ctx, "fp8_l1_bwd",
-                                        {&f.mG1, &f.mW1T, &f.mG1, &f.mW1T, &f.mG1, &f.mG1, &f.mG1, &f.mG1}, a,
-                                        dim3((NAEV + 255) / 256, tiles, 1), s);
+  const CUtensorMap *og = gaev_map(ctx, t);
+  if (!og) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the dE/dAEV map";
+    return FNN_E_CUDA;
+  }
+  return launch<256, tc::EPI_F32, MODE>(ctx, "fp8_l1_bwd", {&f.mG1, &f.mW1T, &f.mG1, &f.mW1T, og, og, &f.mG1, &f.mG1},
+                                        a, dim3((NAEV + 255) / 256, tiles, 1), s);
 }
 
 }  // namespace

@@ -200,7 +200,8 @@ struct Args {
   int a_by_member;             // A's middle coordinate = member (else 0)
   int b_by_member;             // B's group coordinate = member * 7 + element (else element)
   const int32_t *tile_elem;    // element of each 128-row tile (-1: skip)
-  // EPI_F32: fp32 output written directly, [rows][ldo] with member stride o_mstride
+  // EPI_F32: fp32 output [rows][ldo] (o_mstride 0): stored through the output map (box 8 x 1 x 32, fp32),
+  // and by vector atomics at `out` for the K parts of a tail-split launch
   float *out;
   long long ldo, o_mstride;
   // every other epilogue stores 32-row x 16-column pieces through the output tensor map (box 16 x 1 x 32):
@@ -270,11 +271,12 @@ __device__ __forceinline__ TailSched tail_sched_n(const Args &p, int G, int NTc)
 // barriers.  The ring is as deep as the space allows (at most 6).
 template <int NT, int EPI, int MODE, bool QUAD = false, int KB = BKB>
 struct Smem {
-  static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 0 : (MODE == MODE_SPLIT ? 2 : 1);   // halves per buffer
+  // halves per buffer (an fp32 piece of 32 rows x 8 columns fills one)
+  static constexpr int OB = EPI == EPI_ATOMIC ? 0 : EPI == EPI_F32 ? 1 : (MODE == MODE_SPLIT ? 2 : 1);
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
   // the space more (the split first layer: a fourth operand stage)
-  static constexpr int NBUF = (MODE == MODE_SPLIT && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
+  static constexpr int NBUF = (MODE == MODE_SPLIT && EPI != EPI_F32 && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int AQ = QUAD ? 2 : 1;   // operand tiles per stage and side (hi, lo)
@@ -608,15 +610,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           continue;
         }
         if (EPI == EPI_F32) {
-          float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
+          const float k = sc * p.scale;
+          if (w.atomic) {   // a K part of a tail tile: added into the tile zeroed beforehand
+            float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            const float4 f4 = make_float4(v[j] * sc * p.scale, v[j + 1] * sc * p.scale, v[j + 2] * sc * p.scale,
-                                          v[j + 3] * sc * p.scale);
-            if (w.atomic)
-              atomicAdd(reinterpret_cast<float4 *>(o + j), f4);
-            else
-              *reinterpret_cast<float4 *>(o + j) = f4;
+            for (int j = 0; j < 16; j += 4)
+              atomicAdd(reinterpret_cast<float4 *>(o + j), make_float4(v[j] * k, v[j + 1] * k, v[j + 2] * k, v[j + 3] * k));
+          } else {          // two 32-row x 8-column pieces through this warp's two buffers, stored by TMA
+#pragma unroll
+            for (int hh = 0; hh < 2; hh++) {
+              uint8_t *ob = wb + (size_t)(gk & 1) * SM::WBUF;
+              if (lane == 0 && gk >= 2) bulk_wait_read1();   // the store that last read this buffer
+              __syncwarp();
+              float4 *d4 = reinterpret_cast<float4 *>(ob + lane * 32);
+              d4[0] = make_float4(v[8 * hh] * k, v[8 * hh + 1] * k, v[8 * hh + 2] * k, v[8 * hh + 3] * k);
+              d4[1] = make_float4(v[8 * hh + 4] * k, v[8 * hh + 5] * k, v[8 * hh + 6] * k, v[8 * hh + 7] * k);
+              fence_proxy_async();
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_3d(&tmO, ob, n0 + c + 8 * hh, 0, rt * BM + q * 32);
+                bulk_commit();
+              }
+              gk++;
+            }
           }
           continue;
         }
