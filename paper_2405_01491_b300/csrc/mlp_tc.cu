@@ -1008,19 +1008,26 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   wg.n_chunks = (rows + wg.kchunk - 1) / wg.kchunk;
   constexpr int WG = tc::MODE_WG;
   wg.K = 0;
-  wg.dW = g->W3; wg.O = H3; wg.I = H2; wg.N = H2;
-  if ((st = launch<192, tc::EPI_ATOMIC, WG>(ctx, "tr16_l3_wgrad",
-                                            {&T.wGBZ3, &T.wHD2, &T.wGZ3, &H.wH2, &T.wGBZ3, &T.wGBZ3, &T.wGBZ3, &T.wGBZ3},
+  // dW[m][e] (O x I, fp32) as the reduce-add target of each product: boxes of 32 rows x 8 columns
+  CUtensorMap d3, d2, d1;
+  auto dmap = [&](CUtensorMap *mp, float *dW, uint64_t O, uint64_t I) {
+    return encode3d(mp, dW, I, O, (uint64_t)M * NE, I * 4, O * I * 4, 8, 32, 1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    CU_TENSOR_MAP_SWIZZLE_NONE);
+  };
+  if (!dmap(&d3, g->W3, H3, H2) || !dmap(&d2, g->W2, H2, H1) || !dmap(&d1, g->W1, H1, NAEV)) {
+    ctx->last_error = "cuTensorMapEncodeTiled failed for the weight-gradient maps";
+    return FNN_E_CUDA;
+  }
+  wg.N = H2; wg.O = H3;
+  if ((st = launch<192, tc::EPI_ATOMIC, WG>(ctx, "tr16_l3_wgrad", {&T.wGBZ3, &T.wHD2, &T.wGZ3, &H.wH2, &d3, &d3, &d3, &d3},
                                             wg, dim3(1, (H3 + 127) / 128, wg.n_chunks * M * NE), s)))
     return st;
-  wg.dW = g->W2; wg.O = H2; wg.I = H1; wg.N = H1;
-  if ((st = launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l2_wgrad",
-                                            {&T.wGBZ2, &T.wHD1, &T.wGZ2, &H.wH1, &T.wGBZ2, &T.wGBZ2, &T.wGBZ2, &T.wGBZ2},
+  wg.N = H1; wg.O = H2;
+  if ((st = launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l2_wgrad", {&T.wGBZ2, &T.wHD1, &T.wGZ2, &H.wH1, &d2, &d2, &d2, &d2},
                                             wg, dim3(1, (H2 + 127) / 128, wg.n_chunks * M * NE), s)))
     return st;
-  wg.dW = g->W1; wg.O = H1; wg.I = NAEV; wg.N = NAEV; wg.b_shared = 1;
-  return launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l1_wgrad",
-                                         {&T.wGBZ1, &T.wT, &T.wGZ1, &H.wAev, &T.wGBZ1, &T.wGBZ1, &T.wGBZ1, &T.wGBZ1},
+  wg.N = NAEV; wg.O = H1; wg.b_shared = 1;
+  return launch<256, tc::EPI_ATOMIC, WG>(ctx, "tr16_l1_wgrad", {&T.wGBZ1, &T.wT, &T.wGZ1, &H.wAev, &d1, &d1, &d1, &d1},
                                          wg, dim3((NAEV + 255) / 256, (H1 + 127) / 128, wg.n_chunks * M * NE), s);
 }
 

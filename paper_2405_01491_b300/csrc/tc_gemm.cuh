@@ -120,6 +120,13 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void 
                "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
                : "memory");
 }
+// tile [smem] added into the tensor (bulk group; fp32 add by the map's element type)
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2) {
+  asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   (uint64_t)map),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // at most one committed store group still reading its shared-memory source
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
@@ -223,12 +230,12 @@ struct Args {
   int b_scale_by;
   // weight gradients (MODE_WG, EPI_ATOMIC): tile t -> (i tile, o tile, row chunk, group g = 7 m + e);
   // K = rows seg[e] + chunk * kchunk .. (at most kchunk, within the element's segment), both terms
-  // (A, B) then (A_lo, B_lo); the fp32 tile is added atomically into dW[g][O][I]
+  // (A, B) then (A_lo, B_lo); the fp32 tile is added into dW[g][O][I] by TMA reduce-add through the
+  // output map (dims I, O, g; box 8 x 32 x 1)
   const int32_t *seg;
   int kchunk, n_chunks;
   int b_shared;               // B has one member for all (its z coordinate is 0)
-  float *dW;
-  int O, I;
+  int O;                      // rows of dW (a 32-row piece starting at or beyond O is skipped)
   // EPI_F32 only: the tiles of the final partial wave are split along K over all CTAs and their parts
   // added atomically into the output, which the caller zeroes first (tail_sched gives the tiles)
   int tail_split;
@@ -272,11 +279,12 @@ __device__ __forceinline__ TailSched tail_sched_n(const Args &p, int G, int NTc)
 template <int NT, int EPI, int MODE, bool QUAD = false, int KB = BKB>
 struct Smem {
   // halves per buffer (an fp32 piece of 32 rows x 8 columns fills one)
-  static constexpr int OB = EPI == EPI_ATOMIC ? 0 : EPI == EPI_F32 ? 1 : (MODE == MODE_SPLIT ? 2 : 1);
+  static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 1 : (MODE == MODE_SPLIT ? 2 : 1);
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
   // the space more (the split first layer: a fourth operand stage)
-  static constexpr int NBUF = (MODE == MODE_SPLIT && EPI != EPI_F32 && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
+  static constexpr int NBUF =
+      (MODE == MODE_SPLIT && EPI != EPI_F32 && EPI != EPI_ATOMIC && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int AQ = QUAD ? 2 : 1;   // operand tiles per stage and side (hi, lo)
@@ -600,40 +608,39 @@ __global__ void __launch_bounds__(THREADS, 1)
         float v[16];
         tmem_ld16(tbase + (c - w.c0), v);
         if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
-        if (EPI == EPI_ATOMIC) {   // weight-gradient tile: row o of dW, columns n0 + c ..
-          const int o = rt * BM + r;
-          if (o < p.O) {
-            float4 *dst = reinterpret_cast<float4 *>(p.dW + ((size_t)(m * NE + e) * p.O + o) * p.I + n0 + c);
+        if (EPI == EPI_ATOMIC && rt * BM + q * 32 >= p.O) continue;   // rows beyond dW (warp-uniform)
+        if (EPI == EPI_ATOMIC || (EPI == EPI_F32 && !w.atomic)) {
+          // 32-row x 8-column fp32 pieces through this warp's two buffers, by TMA: the weight-gradient tile
+          // (rows o of dW[m][e], beyond O clipped by the map) added into dW, the input gradient stored
+          const float k = EPI == EPI_F32 ? sc * p.scale : 1.f;
 #pragma unroll
-            for (int j = 0; j < 4; j++) atomicAdd(dst + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+          for (int hh = 0; hh < 2; hh++) {
+            uint8_t *ob = wb + (size_t)(gk & 1) * SM::WBUF;
+            if (lane == 0 && gk >= 2) bulk_wait_read1();   // the operation that last read this buffer
+            __syncwarp();
+            float4 *d4 = reinterpret_cast<float4 *>(ob + lane * 32);
+            d4[0] = make_float4(v[8 * hh] * k, v[8 * hh + 1] * k, v[8 * hh + 2] * k, v[8 * hh + 3] * k);
+            d4[1] = make_float4(v[8 * hh + 4] * k, v[8 * hh + 5] * k, v[8 * hh + 6] * k, v[8 * hh + 7] * k);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+              if (EPI == EPI_ATOMIC)
+                tma_reduce_add_3d(&tmO, ob, n0 + c + 8 * hh, rt * BM + q * 32, m * NE + e);
+              else
+                tma_store_3d(&tmO, ob, n0 + c + 8 * hh, 0, rt * BM + q * 32);
+              bulk_commit();
+            }
+            gk++;
           }
           continue;
         }
         if (EPI == EPI_F32) {
+          // (the stored pieces are handled above) a K part of a tail tile: added into the tile zeroed beforehand
           const float k = sc * p.scale;
-          if (w.atomic) {   // a K part of a tail tile: added into the tile zeroed beforehand
-            float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
+          float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
 #pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              atomicAdd(reinterpret_cast<float4 *>(o + j), make_float4(v[j] * k, v[j + 1] * k, v[j + 2] * k, v[j + 3] * k));
-          } else {          // two 32-row x 8-column pieces through this warp's two buffers, stored by TMA
-#pragma unroll
-            for (int hh = 0; hh < 2; hh++) {
-              uint8_t *ob = wb + (size_t)(gk & 1) * SM::WBUF;
-              if (lane == 0 && gk >= 2) bulk_wait_read1();   // the store that last read this buffer
-              __syncwarp();
-              float4 *d4 = reinterpret_cast<float4 *>(ob + lane * 32);
-              d4[0] = make_float4(v[8 * hh] * k, v[8 * hh + 1] * k, v[8 * hh + 2] * k, v[8 * hh + 3] * k);
-              d4[1] = make_float4(v[8 * hh + 4] * k, v[8 * hh + 5] * k, v[8 * hh + 6] * k, v[8 * hh + 7] * k);
-              fence_proxy_async();
-              __syncwarp();
-              if (lane == 0) {
-                tma_store_3d(&tmO, ob, n0 + c + 8 * hh, 0, rt * BM + q * 32);
-                bulk_commit();
-              }
-              gk++;
-            }
-          }
+          for (int j = 0; j < 16; j += 4)
+            atomicAdd(reinterpret_cast<float4 *>(o + j), make_float4(v[j] * k, v[j + 1] * k, v[j + 2] * k, v[j + 3] * k));
           continue;
         }
         const int b = SM::NBUF == 2 ? (int)(gk & 1) : 0;
