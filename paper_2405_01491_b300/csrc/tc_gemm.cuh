@@ -207,8 +207,8 @@ struct Args {
   int a_by_member;             // A's middle coordinate = member (else 0)
   int b_by_member;             // B's group coordinate = member * 7 + element (else element)
   const int32_t *tile_elem;    // element of each 128-row tile (-1: skip)
-  // EPI_F32: fp32 output [rows][ldo] (o_mstride 0): stored through the output map (box 8 x 1 x 32, fp32),
-  // and by vector atomics at `out` for the K parts of a tail-split launch
+  // EPI_F32: fp32 output [rows][ldo] (o_mstride 0) through the output map (box 8 x 1 x 32, fp32): stored, or
+  // for the K parts of a tail-split launch added by TMA reduce-add into tiles zeroed at `out` beforehand
   float *out;
   long long ldo, o_mstride;
   // every other epilogue stores 32-row x 16-column pieces through the output tensor map (box 16 x 1 x 32):
@@ -609,9 +609,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_ld16(tbase + (c - w.c0), v);
         if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
         if (EPI == EPI_ATOMIC && rt * BM + q * 32 >= p.O) continue;   // rows beyond dW (warp-uniform)
-        if (EPI == EPI_ATOMIC || (EPI == EPI_F32 && !w.atomic)) {
+        if (EPI == EPI_ATOMIC || EPI == EPI_F32) {
           // 32-row x 8-column fp32 pieces through this warp's two buffers, by TMA: the weight-gradient tile
-          // (rows o of dW[m][e], beyond O clipped by the map) added into dW, the input gradient stored
+          // (rows o of dW[m][e]) added into dW; the input gradient stored, or for a K part of a tail tile
+          // added into the tile zeroed beforehand
           const float k = EPI == EPI_F32 ? sc * p.scale : 1.f;
 #pragma unroll
           for (int hh = 0; hh < 2; hh++) {
@@ -626,21 +627,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (lane == 0) {
               if (EPI == EPI_ATOMIC)
                 tma_reduce_add_3d(&tmO, ob, n0 + c + 8 * hh, rt * BM + q * 32, m * NE + e);
+              else if (w.atomic)
+                tma_reduce_add_3d(&tmO, ob, n0 + c + 8 * hh, 0, rt * BM + q * 32);
               else
                 tma_store_3d(&tmO, ob, n0 + c + 8 * hh, 0, rt * BM + q * 32);
               bulk_commit();
             }
             gk++;
           }
-          continue;
-        }
-        if (EPI == EPI_F32) {
-          // (the stored pieces are handled above) a K part of a tail tile: added into the tile zeroed beforehand
-          const float k = sc * p.scale;
-          float *o = p.out + row * p.ldo + m * p.o_mstride + n0 + c;
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            atomicAdd(reinterpret_cast<float4 *>(o + j), make_float4(v[j] * k, v[j + 1] * k, v[j + 2] * k, v[j + 3] * k));
           continue;
         }
         const int b = SM::NBUF == 2 ? (int)(gk & 1) : 0;
