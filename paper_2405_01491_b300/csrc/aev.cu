@@ -224,18 +224,6 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   return true;
 }
 
-// (j, k) of the t-th unordered pair j < k among n items, row-major upper triangle
-__device__ __forceinline__ void tri_index(int t, int n, int &j, int &k) {
-  float b = 2.f * n - 1.f;
-  int jj = (int)floorf(0.5f * (b - sqrt_fast(fmaxf(b * b - 8.f * t, 0.f))));   // a guess, corrected below
-  jj = max(0, min(jj, n - 2));
-  // start of row j is j (2n - j - 1) / 2
-  while (jj > 0 && jj * (2 * n - jj - 1) / 2 > t) jj--;
-  while ((jj + 1) * (2 * n - jj - 2) / 2 <= t) jj++;
-  j = jj;
-  k = t - jj * (2 * n - jj - 1) / 2 + jj + 1;
-}
-
 // slot block of the element pair (a, b), a <= b, in row-major upper-triangle order
 __device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
@@ -259,8 +247,10 @@ __device__ __forceinline__ void fill_blocks(int4 *blk, const int off_a[NE + 1], 
   __syncwarp();
 }
 
-// This lane's triplet of the next batch of 32 in block order (block by block in slot order, j-major
-// within a block): its block pb (NPAIR past the end) and angular entries ja < ka.  (cp, cu) is the
+// This lane's triplet of the next batch of 32 in block order (block by block in slot order): its block
+// pb (NPAIR past the end) and angular entries ja, ka.  Within a block of one element (n entries) the
+// pairs run along cyclic diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds
+// n/2 pairs); within a block of two elements, j-major.  (cp, cu) is the
 // warp-uniform cursor (block, offset) of the batch's first triplet and advances by 32.  Returns the
 // lanes whose triplet opens a block, against the previous lane (lane 0 against the running block run_p).
 __device__ __forceinline__ unsigned next_batch(const int4 *blk, int &cp, int &cu, int run_p, int &pb, int &ja,
@@ -282,10 +272,20 @@ __device__ __forceinline__ unsigned next_batch(const int4 *blk, int &cp, int &cu
   if (pb < NPAIR) {
     const int j0 = bk.y & 0xff;
     if (bk.y >> 16) {   // both from element a: the u-th pair of its segment
-      int jj, kk;
-      tri_index(u, bk.w, jj, kk);
-      ja = j0 + jj;
-      ka = j0 + kk;
+      const int n = bk.w, D = (n - 1) >> 1;
+      int d, jc;
+      if (u < D * n) {
+        d = (int)((float)u * rcp_fast((float)n));   // u / n, corrected below
+        if (d * n > u) d--;
+        else if ((d + 1) * n <= u) d++;
+        jc = u - d * n;
+        d++;
+      } else {
+        d = n >> 1;
+        jc = u - D * n;
+      }
+      ja = j0 + jc;
+      ka = j0 + (jc + d < n ? jc + d : jc + d - n);
     } else {            // j from element a, k from element b
       int jj = (int)((float)u * rcp_fast((float)bk.z));
       if (jj * bk.z > u) jj--;
@@ -393,15 +393,16 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
           const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
 #pragma unroll
           for (int s = 0; s < NSZ; s++) {
-            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+            const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
             W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
           }
           const float rbar = 0.5f * (d1.w + d2.w);
-          const float fcc = 2.f * S.afc[ja] * S.afc[ka];
+          // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
+          const float lf = __log2f(2.f * S.afc[ja] * S.afc[ka]);
 #pragma unroll
           for (int m = 0; m < NSA; m++) {
             const float dr = rbar - P.shf_a[m];
-            W.sg[m][lane] = __expf(-P.eta_a * dr * dr) * fcc;
+            W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
           }
           W.sp[lane] = pb;
         } else {
@@ -686,7 +687,8 @@ struct AevTanArgs {
   AevParams P;
   const float *V;         // [N][3] displacement field
   void *out;              // [rows][1008], float or bf16
-  __nv_bfloat16 *out_fwd; // the AEV rows themselves (bf16), or NULL: the same sums as k_aev_forward's, in its order
+  __nv_bfloat16 *out_fwd; // the AEV rows themselves (bf16), or NULL: k_aev_forward's sums in its order (its
+                          // Gaussians there as exp(-eta dr^2) times the switch product)
   const int32_t *inv;     // padded row -> atom; NULL = rows are atoms
   const int32_t *meta;
   int n_atoms;
@@ -773,7 +775,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
           const float r1 = d1.w, r2 = d2.w, ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
-          // cos theta formed as the forward kernel forms it, so that the AEV rows of this pass equal its rows
+          // cos theta formed as the forward kernel forms it
           const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(r1 * r2);
           const float cdot = (d2.x * v1.x + d2.y * v1.y + d2.z * v1.z + d1.x * v2.x + d1.y * v2.y + d1.z * v2.z) * inv12 -
                              c * (v1.w * ir1 + v2.w * ir2);
@@ -782,7 +784,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float ds95 = -0.9025f * c * rcp_fast(s95);
 #pragma unroll
           for (int sidx = 0; sidx < NSZ; sidx++) {
-            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[sidx] + s95 * P.sin_z[sidx]);
+            const float base_s = fmaf(s95, P.hsin_z[sidx], fmaf(c95, P.hcos_z[sidx], 0.5f));
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
             W.b.sf[sidx][lane] = f;
             W.b.sfd[sidx][lane] =

@@ -152,7 +152,10 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
     double th = M_PI / 8.0 + s * M_PI / 4.0;
     P.cos_z[s] = (float)cos(th);
     P.sin_z[s] = (float)sin(th);
+    P.hcos_z[s] = (float)(0.5 * cos(th));
+    P.hsin_z[s] = (float)(0.5 * sin(th));
   }
+  P.eta_a_l2 = (float)(-c.eta_ang / M_LN2);
   if (cudaMalloc(&ctx->status, sizeof(DevStatus)) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;

@@ -69,6 +69,8 @@ struct AevParams {
   float shf_r[NSR];
   float shf_a[NSA];
   float cos_z[NSZ], sin_z[NSZ]; // cos / sin of the section centres
+  float hcos_z[NSZ], hsin_z[NSZ];   // the same halved
+  float eta_a_l2;               // -eta_a log2(e): the angular Gaussian as a power of two
 };
 
 // per-structure cell-list geometry
