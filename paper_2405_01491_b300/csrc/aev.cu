@@ -557,21 +557,23 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
           float fs[NSZ], dfs[NSZ];
 #pragma unroll
           for (int s = 0; s < NSZ; s++) {
-            const float base_s = 0.5f + 0.5f * (c95 * P.cos_z[s] + s95 * P.sin_z[s]);
+            const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
             fs[s] = f;
-            dfs[s] = P.zeta * f * rcp_fast(base_s) * 0.5f * (0.95f * P.cos_z[s] + ds95 * P.sin_z[s]);
+            // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
+            dfs[s] = P.zeta * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[s], P.qcos_z[s]);
           }
           const float rbar = 0.5f * (r1 + r2);
+          // H_s = sum_m G[m][s] g_m and Hd_s = sum_m G[m][s] dr_m g_m (times -2 eta below: d g_m / d rbar)
           float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
 #pragma unroll
           for (int m = 0; m < NSA; m++) {
             const float dr = rbar - P.shf_a[m];
-            const float gm = __expf(-P.eta_a * dr * dr);
-            const float dgm = -2.f * P.eta_a * dr * gm;
+            const float gm = exp2f_fast(dr * dr * P.eta_a_l2);
+            const float tm = dr * gm;
             const float4 g4 = __ldg(reinterpret_cast<const float4 *>(Gp + m * NSZ));
             H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
-            Hd[0] += g4.x * dgm; Hd[1] += g4.y * dgm; Hd[2] += g4.z * dgm; Hd[3] += g4.w * dgm;
+            Hd[0] += g4.x * tm; Hd[1] += g4.y * tm; Hd[2] += g4.z * tm; Hd[3] += g4.w * tm;
           }
           const float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
           const float C = f1 * f2;
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
             sHd += fs[s] * Hd[s];
           }
           const float dEdc = 2.f * C * sdH;
-          const float dEdrbar = 2.f * C * sHd;
+          const float dEdrbar = -4.f * P.eta_a * C * sHd;
           const float dEdC = 2.f * sH;
           const float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
           const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;

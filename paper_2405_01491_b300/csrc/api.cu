@@ -154,6 +154,7 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
     P.sin_z[s] = (float)sin(th);
     P.hcos_z[s] = (float)(0.5 * cos(th));
     P.hsin_z[s] = (float)(0.5 * sin(th));
+    P.qcos_z[s] = (float)(0.475 * cos(th));
   }
   P.eta_a_l2 = (float)(-c.eta_ang / M_LN2);
   if (cudaMalloc(&ctx->status, sizeof(DevStatus)) != cudaSuccess) {

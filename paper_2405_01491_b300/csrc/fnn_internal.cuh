@@ -70,6 +70,7 @@ struct AevParams {
   float shf_a[NSA];
   float cos_z[NSZ], sin_z[NSZ]; // cos / sin of the section centres
   float hcos_z[NSZ], hsin_z[NSZ];   // the same halved
+  float qcos_z[NSZ];            // 0.475 cos: the cos term of d(base)/dc in the adjoint
   float eta_a_l2;               // -eta_a log2(e): the angular Gaussian as a power of two
 };
 
