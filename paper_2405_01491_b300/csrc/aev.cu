@@ -784,24 +784,26 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float c95 = 0.95f * c;
           const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
           const float ds95 = -0.9025f * c * rcp_fast(s95);
+          const float zc = P.zeta * cdot;
 #pragma unroll
           for (int sidx = 0; sidx < NSZ; sidx++) {
             const float base_s = fmaf(s95, P.hsin_z[sidx], fmaf(c95, P.hcos_z[sidx], 0.5f));
             const float f = exp2f_fast(P.zeta * __log2f(base_s));
             W.b.sf[sidx][lane] = f;
-            W.b.sfd[sidx][lane] =
-                P.zeta * f * rcp_fast(base_s) * 0.5f * (0.95f * P.cos_z[sidx] + ds95 * P.sin_z[sidx]) * cdot;
+            // fdot = zeta f / base * 0.5 (0.95 cos + ds95 sin) * cdot
+            W.b.sfd[sidx][lane] = zc * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[sidx], P.qcos_z[sidx]);
           }
           const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
           const float f1 = S.afc[ja], f2 = S.afc[ka];
           const float C = f1 * f2, Cdot = S.adfc[ja] * v1.w * f2 + f1 * S.adfc[ka] * v2.w;
+          // 2 g C and 2 (gdot C + g Cdot) = g (dr (-4 eta rbdot C) + 2 Cdot), gdot = -2 eta dr g rbdot
+          const float C2 = 2.f * C, a2 = -4.f * P.eta_a * rbdot * C, c2 = 2.f * Cdot;
 #pragma unroll
           for (int m = 0; m < NSA; m++) {
             const float dr = rbar - P.shf_a[m];
-            const float g = __expf(-P.eta_a * dr * dr);
-            const float gdot = -2.f * P.eta_a * dr * g * rbdot;
-            W.b.sg[m][lane] = 2.f * g * C;
-            W.b.sgd[m][lane] = 2.f * (gdot * C + g * Cdot);
+            const float g = exp2f_fast(dr * dr * P.eta_a_l2);
+            W.b.sg[m][lane] = g * C2;
+            W.b.sgd[m][lane] = g * fmaf(dr, a2, c2);
           }
           W.b.sp[lane] = pb;
         } else {
