@@ -59,6 +59,7 @@ fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows) {
   Workspace &ws = ctx->ws;
   const int M = ctx->w.M;
   if (rows <= ws.rows && M == ws.M) return FNN_OK;
+  ctx->gen++;
   rows = rows + rows / 8;  // headroom against small growth
   fnn_status st;
   if ((st = dalloc(ctx, &ws.aev, rows * NAEV)) || (st = dalloc(ctx, &ws.h1, rows * M * H1)) ||
@@ -201,6 +202,7 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   if (h.graph) fnn_graph_destroy(h.graph);
   if (h.nl) fnn_nlist_destroy(h.nl);
   if (h.own) cudaStreamDestroy(h.own);
+  if (h.status) cudaFreeHost(h.status);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -265,6 +267,7 @@ static fnn_status load_weights_host(fnn_ctx *ctx, const fnn_weights *hw) {
 
 extern "C" fnn_status fnn_load_weights(fnn_ctx *ctx, const char *path, const fnn_weights *host) {
   if (!ctx || (!path) == (!host)) return FNN_E_INVALID;
+  ctx->gen++;
   if (host) return load_weights_host(ctx, host);
   FILE *f = fopen(path, "rb");
   if (!f) {
@@ -382,6 +385,12 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
     h.n_mol = nm;
   }
   if (!h.nl && (st = fnn_nlist_create(ctx, &h.nl, 0))) return st;
+  if (!h.status) FNN_CUDA_TRY(ctx, cudaMallocHost(&h.status, sizeof(DevStatus)));
+  if (h.graph && h.ggen != ctx->gen) {   // a buffer the recorded step references was reallocated since
+    fnn_graph_destroy(h.graph);
+    h.graph = nullptr;
+    h.gkey = -1;
+  }
   FNN_CUDA_TRY(ctx, cudaMemcpyAsync(h.mol_offsets, mol_offsets, ((size_t)NM + 1) * sizeof(int32_t),
                                     cudaMemcpyHostToDevice, s));
   if (N > 0) {
@@ -410,6 +419,7 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
     if (fnn_graph_create(ctx, &sys, h.nl, prec, h.E, h.F, virial ? h.virial : nullptr, 1, stream, &h.graph) ==
         FNN_OK) {
       h.gkey = key;
+      h.ggen = ctx->gen;
       done = true;
     } else {
       h.graph = nullptr;
@@ -425,8 +435,12 @@ extern "C" fnn_status fnn_energy_forces_host(fnn_ctx *ctx, int32_t N, int32_t NM
   FNN_CUDA_TRY(ctx, cudaMemcpyAsync(F, h.F, (size_t)N * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (virial)
     FNN_CUDA_TRY(ctx, cudaMemcpyAsync(virial, h.virial, (size_t)NM * 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  int64_t info = 0;
-  st = fnn_sync(ctx, stream, &info);
+  // the device status read back and cleared in stream order: one wait for the whole call
+  FNN_CUDA_TRY(ctx, cudaMemcpyAsync(h.status, ctx->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s));
+  FNN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  const int64_t info = h.status->info;
+  st = (fnn_status)h.status->code;
   if (st == FNN_E_CAPACITY && info > 0) {
     // the list outgrew its capacity: grow it and evaluate again (once)
     if (h.graph) {

@@ -153,6 +153,8 @@ struct fnn_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string last_error;
+  // bumped whenever a device buffer that a recorded graph may reference is (re)allocated
+  long long gen = 0;
   // host-call staging (fnn_energy_forces_host)
   struct HostStage {
     int32_t n_atoms = -1, n_mol = -1;
@@ -166,6 +168,8 @@ struct fnn_ctx {
     cudaStream_t own = nullptr;        // the entry point's stream when the caller gives none
     fnn_graph *graph = nullptr;        // the device part of the last repeated call, replayed
     long long gkey = -1, last_key = -1;
+    fnn::DevStatus *status = nullptr;  // pinned: the device status read back in the call's own stream order
+    long long ggen = -1;               // ctx->gen when graph was recorded
   } host;
 };
 

@@ -349,6 +349,7 @@ static fnn_status tc_workspace(fnn_ctx *ctx, size_t rows, int halves) {
   const int M = t->M;
   const bool have = t->abuf && rows <= t->rows && (halves == 1 || t->h[1].aev);
   if (have) return FNN_OK;
+  ctx->gen++;
   rows = rows + rows / 8;
   if (t->abuf) cudaFree(t->abuf);
   t->abuf = nullptr;
@@ -407,6 +408,7 @@ static fnn_status f8_workspace(fnn_ctx *ctx, size_t rows) {
   F8 &f = t->f8;
   const int M = t->M;
   if (f.abuf && rows <= f.rows) return FNN_OK;
+  ctx->gen++;
   rows = rows + rows / 8;
   if (f.abuf) cudaFree(f.abuf);
   f.abuf = nullptr;

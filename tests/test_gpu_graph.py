@@ -115,3 +115,25 @@ def test_host_entry_point_replays_repeated_calls(fnn):
     r = oracle.energy_forces(moved, weights(2))
     assert np.abs(E2 - r.energy).max() / s.n_atoms <= 1e-4
     assert np.abs(F2 - r.forces).max() <= 1e-3
+
+
+def test_host_entry_point_after_weight_reload(fnn):
+    """The entry point's recorded graph is dropped when the context's buffers are reallocated: after a
+    weight reload the next call evaluates the new networks (a fresh context and the oracle agree)."""
+    s = structure("box300")
+    ctx = fnn.Context(2)
+    fnn.load_weights(ctx, weights(2))
+    for _ in range(4):   # the second call records the graph, the later ones replay it
+        fnn.energy_forces_host(ctx, s, "fp32x3")
+    from paper_2405_01491_b300 import synth
+    w2 = synth.xavier_weights(2, seed=9)
+    fnn.load_weights(ctx, w2)
+    E, F, _ = fnn.energy_forces_host(ctx, s, "fp32x3")
+    fresh = fnn.Context(2)
+    fnn.load_weights(fresh, w2)
+    Ef, Ff, _ = fnn.energy_forces_host(fresh, s, "fp32x3")
+    np.testing.assert_array_equal(E, Ef)
+    np.testing.assert_allclose(F, Ff, rtol=0, atol=1e-5)
+    r = oracle.energy_forces(s, w2)
+    assert np.abs(E - r.energy).max() / s.n_atoms <= 1e-4
+    assert np.abs(F - r.forces).max() <= 1e-3
