@@ -226,7 +226,9 @@ fnn_status fnn_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist 
 typedef struct fnn_graph fnn_graph;
 fnn_status fnn_graph_create(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, fnn_precision prec, double *E,
                             float *F, double *virial, int32_t rebuild, void *stream, fnn_graph **graph);
-/* Replay on stream (asynchronous). */
+/* Replay on stream (asynchronous).  FNN_E_STATE (nothing launched) once the context has reallocated a
+ * buffer the graph references since it was recorded: weights reloaded, or a larger system evaluated
+ * on the context; record a new graph then. */
 fnn_status fnn_graph_launch(fnn_graph *graph, void *stream);
 /* Kernel launches one replay performs. */
 fnn_status fnn_graph_kernels(const fnn_graph *graph, int64_t *kernels);

@@ -517,6 +517,7 @@ struct fnn_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;   // kernel launches one replay performs
+  long long gen = 0;       // ctx->gen at recording: its buffers are the ones the graph references
 };
 
 extern "C" fnn_status fnn_graph_create(fnn_ctx *ctx, const fnn_system *sys, fnn_nlist *nl, fnn_precision prec,
@@ -575,12 +576,18 @@ extern "C" fnn_status fnn_graph_create(fnn_ctx *ctx, const fnn_system *sys, fnn_
   G->graph = g;
   G->exec = exec;
   G->kernels = kernels;
+  G->gen = ctx->gen;
   *out = G;
   return FNN_OK;
 }
 
 extern "C" fnn_status fnn_graph_launch(fnn_graph *g, void *stream) {
   if (!g) return FNN_E_INVALID;
+  if (g->gen != g->ctx->gen) {
+    g->ctx->last_error = "the context reallocated buffers this graph references (weights reloaded or a larger "
+                         "system evaluated): record the graph again";
+    return FNN_E_STATE;
+  }
   FNN_CUDA_TRY(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
   g->ctx->prof.launches += g->kernels;
   return FNN_OK;

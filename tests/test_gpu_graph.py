@@ -137,3 +137,24 @@ def test_host_entry_point_after_weight_reload(fnn):
     r = oracle.energy_forces(s, w2)
     assert np.abs(E - r.energy).max() / s.n_atoms <= 1e-4
     assert np.abs(F - r.forces).max() <= 1e-3
+
+
+def test_graph_refuses_replay_after_reallocation(fnn):
+    """A recorded graph references the context's buffers: after a weight reload its launch returns
+    FNN_E_STATE (nothing runs) and a newly recorded graph evaluates the new networks."""
+    s, ctx, ds, nl = _setup(fnn, "water216", 2)
+    g = fnn.Graph(ctx, ds, nl, "fp32x3")
+    g.launch()
+    fnn.check(ctx, stream=g.stream)
+    from paper_2405_01491_b300 import synth
+    w2 = synth.xavier_weights(2, seed=11)
+    fnn.load_weights(ctx, w2)
+    with pytest.raises(fnn.FnnError):
+        g.launch()
+    g.close()
+    g2 = fnn.Graph(ctx, ds, nl, "fp32x3")
+    g2.launch()
+    fnn.check(ctx, stream=g2.stream)
+    r = oracle.energy_forces(s, w2)
+    assert np.abs(g2.E.cpu().numpy() - r.energy).max() / s.n_atoms <= 1e-4
+    g2.close()
