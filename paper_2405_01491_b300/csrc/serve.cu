@@ -81,7 +81,10 @@ bool grow(T **p, size_t *cap, size_t need) {
     cudaGetLastError();
     return false;
   }
-  if (*p) cudaFree(*p);
+  if (*p) {
+    cudaDeviceSynchronize();   // queued work (a result copy on the side stream) may still read the old buffer
+    cudaFree(*p);
+  }
   *p = q;
   *cap = n;
   return true;
@@ -142,6 +145,11 @@ struct fnn_server {
   double *r_hist = nullptr, *h_rhist = nullptr;
   size_t cap_rpos = 0, cap_rvel = 0, cap_rF = 0, cap_rhist = 0, cap_hrpos = 0, cap_hrvel = 0, cap_hrF = 0,
          cap_hrhist = 0;
+  // results leave on a side stream while the next batch step runs; their segment table has its own buffers
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_pack = nullptr, ev_ret = nullptr;
+  Seg *d_rseg = nullptr, *h_rseg = nullptr;
+  size_t cap_rseg = 0, cap_hrseg = 0;
   double host_ms = 0, step_ms = 0;   // worker time in layout changes and in batch steps
 };
 
@@ -206,8 +214,9 @@ static bool grow_host(T **p, size_t *cap, size_t need) {
   return true;
 }
 
-// Results of the structures that finished at the last step: packed on the device, copied to pinned
-// host memory (asynchronous; read after the next stream synchronisation by finish_retire).
+// Results of the structures that finished at the last step: packed on the device (batch stream), copied
+// to pinned host memory on the side stream, so that the relayout and the next batch step need not wait
+// for the host link; finish_retire waits for the copies (ev_ret) while that step runs.
 static fnn_status start_retire(fnn_server *S, const std::vector<Slot> &fin) {
   cudaStream_t s = S->stream;
   size_t atoms = 0, hist = 0;
@@ -221,28 +230,34 @@ static fnn_status start_retire(fnn_server *S, const std::vector<Slot> &fin) {
   const size_t nseg = seg.size();
   if (!grow(&S->r_pos, &S->cap_rpos, atoms + 1) || !grow(&S->r_vel, &S->cap_rvel, atoms + 1) ||
       !grow(&S->r_F, &S->cap_rF, 3 * atoms + 3) || !grow(&S->r_hist, &S->cap_rhist, hist + 1) ||
-      !grow(&S->d_seg, &S->cap_seg, 2 * nseg + 2) ||
+      !grow(&S->d_rseg, &S->cap_rseg, 2 * nseg + 2) ||
       !grow_host(&S->h_rpos, &S->cap_hrpos, atoms + 1) || !grow_host(&S->h_rvel, &S->cap_hrvel, atoms + 1) ||
       !grow_host(&S->h_rF, &S->cap_hrF, 3 * atoms + 3) || !grow_host(&S->h_rhist, &S->cap_hrhist, hist + 1) ||
-      !grow_host(&S->h_seg, &S->cap_hseg, 2 * nseg + 2))
+      !grow_host(&S->h_rseg, &S->cap_hrseg, 2 * nseg + 2))
     return FNN_E_OOM;
-  memcpy(S->h_seg, seg.data(), nseg * sizeof(Seg));
-  memcpy(S->h_seg + nseg, hseg.data(), nseg * sizeof(Seg));
-  cudaMemcpyAsync(S->d_seg, S->h_seg, 2 * nseg * sizeof(Seg), cudaMemcpyHostToDevice, s);
+  memcpy(S->h_rseg, seg.data(), nseg * sizeof(Seg));
+  memcpy(S->h_rseg + nseg, hseg.data(), nseg * sizeof(Seg));
+  cudaMemcpyAsync(S->d_rseg, S->h_rseg, 2 * nseg * sizeof(Seg), cudaMemcpyHostToDevice, s);
   const int blocks = (int)(nseg < 4096 ? nseg : 4096);
-  k_pack_results<<<blocks, 128, 0, s>>>(S->d_seg, (int)nseg, S->pos[S->cur], S->vel[S->cur], S->F, S->r_pos,
+  k_pack_results<<<blocks, 128, 0, s>>>(S->d_rseg, (int)nseg, S->pos[S->cur], S->vel[S->cur], S->F, S->r_pos,
                                          S->r_vel, S->r_F);
-  k_gather_hist<<<blocks, 128, 0, s>>>(S->d_seg + nseg, (int)nseg, S->hist, S->r_hist);
-  cudaMemcpyAsync(S->h_rpos, S->r_pos, atoms * sizeof(float4), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(S->h_rvel, S->r_vel, atoms * sizeof(float4), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(S->h_rF, S->r_F, 3 * atoms * sizeof(float), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(S->h_rhist, S->r_hist, hist * sizeof(double), cudaMemcpyDeviceToHost, s);
-  // the segment table is reused by the relayout below: the stream orders the two
-  cudaStreamSynchronize(s);
+  k_gather_hist<<<blocks, 128, 0, s>>>(S->d_rseg + nseg, (int)nseg, S->hist, S->r_hist);
+  cudaEventRecord(S->ev_pack, s);
+  cudaStreamWaitEvent(S->cstream, S->ev_pack, 0);
+  cudaMemcpyAsync(S->h_rpos, S->r_pos, atoms * sizeof(float4), cudaMemcpyDeviceToHost, S->cstream);
+  cudaMemcpyAsync(S->h_rvel, S->r_vel, atoms * sizeof(float4), cudaMemcpyDeviceToHost, S->cstream);
+  cudaMemcpyAsync(S->h_rF, S->r_F, 3 * atoms * sizeof(float), cudaMemcpyDeviceToHost, S->cstream);
+  cudaMemcpyAsync(S->h_rhist, S->r_hist, hist * sizeof(double), cudaMemcpyDeviceToHost, S->cstream);
+  cudaEventRecord(S->ev_ret, S->cstream);
   return cudaGetLastError() == cudaSuccess ? FNN_OK : FNN_E_CUDA;
 }
 
-static void finish_retire(fnn_server *S, std::vector<Slot> &fin) {
+// Waits for the result copies of start_retire, then hands each finished structure its output.
+static fnn_status finish_retire(fnn_server *S, std::vector<Slot> &fin) {
+  if (cudaEventSynchronize(S->ev_ret) != cudaSuccess) {
+    cudaGetLastError();
+    return FNN_E_CUDA;
+  }
   size_t atoms = 0, hist = 0;
   const auto now = Clock::now();
   std::vector<std::pair<uint64_t, Out>> outs;
@@ -271,6 +286,7 @@ static void finish_retire(fnn_server *S, std::vector<Slot> &fin) {
     for (auto &po : outs) S->done[po.first] = std::move(po.second);
   }
   S->cv_done.notify_all();
+  return FNN_OK;
 }
 
 // New layout: survivors (moved on the device), then admitted requests (from pinned host staging), all
@@ -503,14 +519,18 @@ static void worker_main(fnn_server *S) {
       S->active.clear();
     }
     if (!fin.empty()) err = start_retire(S, fin);
-    if (!fin.empty() && err == FNN_OK) {
-      finish_retire(S, fin);
-      fin.clear();
-    }
+    const bool retiring = !fin.empty() && err == FNN_OK;
     if (err == FNN_OK && changed) repack(S, keep, incoming, &err);
     const auto t1 = Clock::now();
-    if (err == FNN_OK && !S->active.empty()) {
-      err = serve_step(S);
+    // the finished structures' results are handed out while the batch step runs on the device
+    const bool stepping = err == FNN_OK && !S->active.empty();
+    if (stepping) err = serve_step(S);
+    if (retiring) {
+      const fnn_status rs = finish_retire(S, fin);
+      if (rs == FNN_OK) fin.clear();
+      else if (err == FNN_OK) err = rs;
+    }
+    if (stepping) {
       if (err == FNN_OK) {
         int64_t info = 0;
         err = fnn_sync(S->ctx, S->stream, &info);
@@ -553,8 +573,21 @@ extern "C" fnn_status fnn_serve_create(fnn_server **out, fnn_ctx *ctx, size_t hb
     delete S;
     return FNN_E_CUDA;
   }
+  if (cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_pack, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_ret, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (S->ev_pack) cudaEventDestroy(S->ev_pack);
+    if (S->cstream) cudaStreamDestroy(S->cstream);
+    cudaStreamDestroy(S->stream);
+    delete S;
+    return FNN_E_CUDA;
+  }
   fnn_status st = fnn_nlist_create(ctx, &S->nl, 0);
   if (st) {
+    cudaEventDestroy(S->ev_pack);
+    cudaEventDestroy(S->ev_ret);
+    cudaStreamDestroy(S->cstream);
     cudaStreamDestroy(S->stream);
     delete S;
     return st;
@@ -644,6 +677,7 @@ extern "C" fnn_status fnn_serve_destroy(fnn_server *S) {
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
   cudaStreamSynchronize(S->stream);
+  cudaStreamSynchronize(S->cstream);
   for (int b = 0; b < 2; b++) {
     if (S->Z[b]) cudaFree(S->Z[b]);
     if (S->pos[b]) cudaFree(S->pos[b]);
@@ -651,13 +685,16 @@ extern "C" fnn_status fnn_serve_destroy(fnn_server *S) {
   }
   void *ptrs[] = {S->F, S->mol_offsets, S->mol_step, S->mol_nsteps, S->cell, S->pbc, S->E, S->hist_off,
                   S->hist_buf[0], S->hist_buf[1], S->mol_dt, S->sZ, S->spos, S->svel, S->d_seg,
-                  S->r_pos, S->r_vel, S->r_F, S->r_hist};
+                  S->d_rseg, S->r_pos, S->r_vel, S->r_F, S->r_hist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  void *hptrs[] = {S->h_seg, S->h_sZ, S->h_spos, S->h_svel, S->h_mol, S->h_rpos, S->h_rvel, S->h_rF, S->h_rhist};
+  void *hptrs[] = {S->h_seg, S->h_rseg, S->h_sZ, S->h_spos, S->h_svel, S->h_mol, S->h_rpos, S->h_rvel, S->h_rF, S->h_rhist};
   for (void *p : hptrs)
     if (p) cudaFreeHost(p);
   if (S->nl) fnn_nlist_destroy(S->nl);
+  cudaEventDestroy(S->ev_pack);
+  cudaEventDestroy(S->ev_ret);
+  cudaStreamDestroy(S->cstream);
   cudaStreamDestroy(S->stream);
   delete S;
   return FNN_OK;
