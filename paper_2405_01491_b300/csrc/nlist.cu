@@ -609,6 +609,20 @@ __device__ __forceinline__ char4 make_shift(float nx, float ny, float nz) {
   return make_char4((signed char)nx, (signed char)ny, (signed char)nz, 0);
 }
 
+// entry k of the list stencil() writes, and its length, without the array
+__device__ __forceinline__ int stencil_n(int c, int d, int pbc) {
+  if (pbc) return d < 3 ? d : 3;
+  return 1 + (c > 0) + (c + 1 < d);
+}
+__device__ __forceinline__ int stencil_at(int c, int d, int pbc, int k) {
+  if (pbc) {
+    if (d < 3) return k;   // {0} or {0, 1}
+    const int v = c - 1 + k;
+    return v < 0 ? v + d : (v >= d ? v - d : v);
+  }
+  return (c > 0 ? c - 1 : c) + k;
+}
+
 __device__ __forceinline__ int stencil(int c, int d, int pbc, int *out) {
   if (pbc) {
     if (d == 1) { out[0] = 0; return 1; }
@@ -709,7 +723,7 @@ __global__ void __launch_bounds__(256) k_pairs(fnn_system sys, const MolGrid *gr
 // CELL_CAND candidates is traversed per centre from global memory instead.
 constexpr int CELL_WARPS = 4, CELL_CAND = 1024;
 
-__global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys, const MolGrid *grid,
+__global__ void __launch_bounds__(CELL_WARPS * 32, 8) k_pairs_stage(fnn_system sys, const MolGrid *grid,
                                                                  const int32_t *mol_base, const int32_t *atom_mol,
                                                                  const int32_t *cell_of, const int32_t *cell_start,
                                                                  const int32_t *cell_atoms, const float4 *cell_pos,
@@ -717,6 +731,7 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
                                                                  char4 *tshift, const int32_t *meta) {
   __shared__ float4 cpos[CELL_CAND];
   __shared__ int32_t cidx[CELL_CAND];
+  __shared__ int32_t run_s0[27], run_off[28], run_total;   // at most 9 stencil rows of at most 3 runs
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -732,34 +747,100 @@ __global__ void __launch_bounds__(CELL_WARPS * 32) k_pairs_stage(fnn_system sys,
     const int mb = mol_base[m];
     const int cl = c - mb;
     const int cx = cl % g.dx, cy = (cl / g.dx) % g.dy, cz = cl / (g.dx * g.dy);
-    int ox[3], oy[3], oz[3];
-    const int nox = stencil(cx, g.dx, g.pbc, ox), noy = stencil(cy, g.dy, g.pbc, oy), noz = stencil(cz, g.dz, g.pbc, oz);
-    // the stencil's runs of consecutive cells, in pairs_row's order: f(first candidate, run length)
-    auto runs = [&](auto &&f) {
-      for (int a = 0; a < noz; a++)
-        for (int b = 0; b < noy; b++) {
-          const int rowc = mb + (oz[a] * g.dy + oy[b]) * g.dx;
-          for (int q = 0; q < nox;) {
-            const int x0 = ox[q];
-            int x1 = x0;
-            for (q++; q < nox && ox[q] == x1 + 1; q++) x1 = ox[q];
-            const int s0 = cell_start[rowc + x0];
-            f(s0, cell_start[rowc + x1 + 1] - s0);
+    const int noy = stencil_n(cy, g.dy, g.pbc), noz = stencil_n(cz, g.dz, g.pbc);
+    // x-neighbour cells with consecutive indices hold consecutive atoms: the (at most three) runs of the
+    // x stencil, grouped as pairs_row groups them
+    const int nox = stencil_n(cx, g.dx, g.pbc);
+    const int x0 = stencil_at(cx, g.dx, g.pbc, 0), x1 = stencil_at(cx, g.dx, g.pbc, 1),
+              x2 = stencil_at(cx, g.dx, g.pbc, 2);
+    int ra0 = x0, ra1 = x0, rb0 = 0, rb1 = -1, rc0 = 0, rc1 = -1, nxr = 1;
+    if (nox > 1) {
+      if (x1 == ra1 + 1) ra1 = x1;
+      else { rb0 = rb1 = x1; nxr = 2; }
+    }
+    if (nox > 2) {
+      if (nxr == 1) {
+        if (x2 == ra1 + 1) ra1 = x2;
+        else { rb0 = rb1 = x2; nxr = 2; }
+      } else {
+        if (x2 == rb1 + 1) rb1 = x2;
+        else { rc0 = rc1 = x2; nxr = 3; }
+      }
+    }
+    __syncthreads();   // the previous cell's candidates and run table are no longer read
+    if (warp == 0) {
+      // lane t: stencil row t (z-major, as pairs_row walks it), its runs' ranges loaded side by side;
+      // the table holds each run's first candidate and its offset in the traversal order
+      const int nrow = noz * noy;
+      int s0 = 0, s1 = 0, s2 = 0, l0 = 0, l1 = 0, l2 = 0;
+      if (lane < nrow) {
+        const int a = lane / noy, b = lane - a * noy;
+        const int rowc = mb + (stencil_at(cz, g.dz, g.pbc, a) * g.dy + stencil_at(cy, g.dy, g.pbc, b)) * g.dx;
+        s0 = cell_start[rowc + ra0];
+        l0 = cell_start[rowc + ra1 + 1] - s0;
+        if (nxr > 1) {
+          s1 = cell_start[rowc + rb0];
+          l1 = cell_start[rowc + rb1 + 1] - s1;
+        }
+        if (nxr > 2) {
+          s2 = cell_start[rowc + rc0];
+          l2 = cell_start[rowc + rc1 + 1] - s2;
+        }
+      }
+      const int mine = l0 + l1 + l2;
+      int inc = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += v;
+      }
+      const int ex = inc - mine;
+      if (lane < nrow) {
+        const int r = lane * nxr;
+        run_s0[r] = s0;
+        run_off[r] = ex;
+        if (nxr > 1) {
+          run_s0[r + 1] = s1;
+          run_off[r + 1] = ex + l0;
+        }
+        if (nxr > 2) {
+          run_s0[r + 2] = s2;
+          run_off[r + 2] = ex + l0 + l1;
+        }
+      }
+      if (lane == 31) {
+        run_off[nrow * nxr] = inc;
+        run_total = inc;
+      }
+    }
+    __syncthreads();
+    const int total = run_total;
+    if (total <= CELL_CAND) {
+      // candidates in traversal order: each thread finds the run of its slots in the table (its slots
+      // ascend, so the search only moves forward) and has two loads in flight before it stores
+      int r = 0;
+      for (int h = 0; h < total; h += 2 * CELL_WARPS * 32) {
+        float4 v[2];
+        int id[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int k = h + threadIdx.x + u * CELL_WARPS * 32;
+          if (k < total) {
+            while (run_off[r + 1] <= k) r++;
+            const int src = run_s0[r] + (k - run_off[r]);
+            v[u] = cell_pos[src];
+            id[u] = cell_atoms[src];
           }
         }
-    };
-    int total = 0;
-    runs([&](int, int len) { total += len; });
-    if (total <= CELL_CAND) {
-      __syncthreads();   // the previous cell's candidates are no longer read
-      int off = 0;
-      runs([&](int s0, int len) {
-        for (int k = threadIdx.x; k < len; k += CELL_WARPS * 32) {
-          cpos[off + k] = cell_pos[s0 + k];
-          cidx[off + k] = cell_atoms[s0 + k];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int k = h + threadIdx.x + u * CELL_WARPS * 32;
+          if (k < total) {
+            cpos[k] = v[u];
+            cidx[k] = id[u];
+          }
         }
-        off += len;
-      });
+      }
       __syncthreads();
       for (int w = a0 + sl * CELL_WARPS + warp; w < a1; w += S * CELL_WARPS) {
         const int i = cell_atoms[w];
