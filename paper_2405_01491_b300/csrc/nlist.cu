@@ -900,15 +900,32 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
     const int64_t dst = row_ptr[i];
     const int n = row_ptr[i + 1] - row_ptr[i];
     if (n <= PAIR_STRIDE) {
+      // the whole staged row in registers (all its loads in flight together), then a stable counting
+      // sort by neighbour element: ballots count each element's entries, then place them
+      constexpr int NCH = PAIR_STRIDE / 32;
       const int64_t src = (int64_t)i * PAIR_STRIDE;
+      int jv[NCH], ev[NCH];
+      char4 sv[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        const int k = 32 * c + lane;
+        jv[c] = 0;
+        sv[c] = make_char4(0, 0, 0, 0);
+        if (k < n) {
+          jv[c] = tnbr[src + k];
+          sv[c] = tshift[src + k];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; c++) ev[c] = 32 * c + lane < n ? (int)elem[jv[c]] : -1;
       int off[NE];
 #pragma unroll
       for (int q = 0; q < NE; q++) off[q] = 0;
-      for (int kb = 0; kb < n; kb += 32) {
-        const int k = kb + lane;
-        const int e = k < n ? (int)elem[tnbr[src + k]] : -1;
 #pragma unroll
-        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, e == q));
+      for (int c = 0; c < NCH; c++) {
+        if (32 * c >= n) break;   // uniform over the warp
+#pragma unroll
+        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, ev[c] == q));
       }
       int run = 0;   // counts -> starts
 #pragma unroll
@@ -917,24 +934,19 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
         off[q] = run;
         run += c;
       }
-      for (int kb = 0; kb < n; kb += 32) {
-        const int k = kb + lane;
-        int j = 0, e = -1, at = 0;
-        char4 sh = make_char4(0, 0, 0, 0);
-        if (k < n) {
-          j = tnbr[src + k];
-          sh = tshift[src + k];
-          e = elem[j];
-        }
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        if (32 * c >= n) break;
+        int at = 0;
 #pragma unroll
         for (int q = 0; q < NE; q++) {
-          const unsigned mq = __ballot_sync(FULL, e == q);
-          if (e == q) at = off[q] + __popc(mq & lt);
+          const unsigned mq = __ballot_sync(FULL, ev[c] == q);
+          if (ev[c] == q) at = off[q] + __popc(mq & lt);
           off[q] += __popc(mq);
         }
-        if (k < n && dst + at < cap) {
-          nbr[dst + at] = j;
-          shift[dst + at] = sh;
+        if (32 * c + lane < n && dst + at < cap) {
+          nbr[dst + at] = jv[c];
+          shift[dst + at] = sv[c];
         }
       }
     } else {
