@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(CELL_WARPS * 32, 8) k_pairs_stage(fnn_system s
       __syncthreads();
       for (int w = a0 + sl * CELL_WARPS + warp; w < a1; w += S * CELL_WARPS) {
         const int i = cell_atoms[w];
-        const float4 pi = pos[i];
+        const float4 pi = cell_pos[w];   // pos[i], copied in cell order: no wait on i
         const int64_t base = (int64_t)i * PAIR_STRIDE;
         int count = 0;
         for (int k0 = 0; k0 < total; k0 += 32) {
