@@ -55,24 +55,27 @@ def peaks():
 
 
 def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
-    """Algorithmic work of one launch of a kernel: (bound, amount, unit) or None."""
+    """Algorithmic work of one launch of a kernel: (bound, amount, unit, executed) or None.  For the network
+    products the amount is the method's own work, one FP32 product of 2 in out FLOP per row and member;
+    `executed` is what the tensor pipe runs (three bf16 products for the FP32X3 split), else None."""
     if name == "aev_forward":       # positions once, list entries (index + shift), the AEV row written
-        return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B"
+        return "hbm", n_atoms * (16 + 4032) + nnz * 8, "B", None
     if name in ("aev_forward_bf16", "aev_forward_x3"):  # bf16 AEV row (x3: hi and lo rows)
-        return "hbm", n_atoms * (16 + (4032 if name.endswith("x3") else 2016)) + nnz * 8, "B"
+        return "hbm", n_atoms * (16 + (4032 if name.endswith("x3") else 2016)) + nnz * 8, "B", None
     if name == "aev_forward_fp8":   # e4m3 AEV row
-        return "hbm", n_atoms * (16 + 1008) + nnz * 8, "B"
+        return "hbm", n_atoms * (16 + 1008) + nnz * 8, "B", None
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
-        return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B"
+        return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B", None
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
     m = re.match(r"(f32|bf16|fp8|x3)_(l[123])_(fwd|bwd|pair)", name)
     if m:   # "_pair": the fused third layer, forward and backward products
-        flops = 2.0 * gemm[m.group(2)] * M * n_atoms * (3 if m.group(1) == "x3" else 1)
-        return ("alu" if m.group(1) == "f32" else "tensor"), flops * (2 if m.group(3) == "pair" else 1), "FLOP"
+        flops = 2.0 * gemm[m.group(2)] * M * n_atoms * (2 if m.group(3) == "pair" else 1)
+        return (("alu" if m.group(1) == "f32" else "tensor"), flops, "FLOP",
+                3 * flops if m.group(1) == "x3" else None)
     if name in ("pairs_count", "pairs_fill", "pairs_stage"):
-        return "hbm", n_atoms * 16 + (nnz * 8 if name != "pairs_count" else 0), "B"
+        return "hbm", n_atoms * 16 + (nnz * 8 if name != "pairs_count" else 0), "B", None
     if name == "pairs_compact":     # staged entries read, list entries written
-        return "hbm", nnz * 16, "B"
+        return "hbm", nnz * 16, "B", None
     return None
 
 
@@ -577,21 +580,26 @@ def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, bar
 
 
 def kernel_table(prof, steps, n_atoms, nnz, M, form, pk):
+    """Per kernel: time per launch, share, and the roofline of its algorithmic work.  Kernel times are
+    CUDA events around single launches inside a millisecond-long step, so tensor-bound kernels are held
+    against the measured burst bf16 rate (fp8: twice it, the nominal ratio)."""
     ffma_peak = N_SM * FFMA_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
-    tensor_peak = pk["bf16_tflops_sustained"] * (2 if form == "fp8" else 1)
+    tensor_peak = pk["bf16_tflops"] * (2 if form == "fp8" else 1)
     kernels = {}
     total = sum(v[0] for v in prof.values())
     for name, (tot_ms, n) in prof.items():
         entry = {"ms_per_launch": tot_ms / n, "launches_per_step": n / steps, "share": tot_ms / total if total else None}
         wk = kernel_work(name, n_atoms, nnz, M)
         if wk:
-            bound, amount, u = wk
+            bound, amount, u, executed = wk
             t = tot_ms / n * 1e-3
             if u == "B":
                 entry.update(bound=bound, achieved=amount / t / 1e9, unit="GB/s", peak=pk["hbm_gbs"])
             else:
                 entry.update(bound=bound, achieved=amount / t / 1e12, unit="TFLOP/s",
                              peak=ffma_peak if bound == "alu" else tensor_peak)
+                if executed:   # the split products the tensor pipe runs, as a fraction of the same peak
+                    entry["executed_frac"] = executed / t / 1e12 / entry["peak"]
             entry["frac"] = entry["achieved"] / entry["peak"]
         kernels[name] = entry
     dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: prof[k][0])
@@ -600,7 +608,12 @@ def kernel_table(prof, steps, n_atoms, nnz, M, form, pk):
             "frac": d["frac"],
             "peak_src": (f"FP32 FFMA: {N_SM} SMs x {FFMA_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz"
                          if d["bound"] == "alu" else
-                         f"{pk['src']} {'HBM copy' if d['bound'] == 'hbm' else 'bf16 sustained'}")}
+                         f"{pk['src']} {'HBM copy' if d['bound'] == 'hbm' else 'bf16 burst'}"),
+            "work": ("algorithmic: one FP32 product per layer (2 in out FLOP per row and member); the FP32X3 "
+                     "split runs three bf16 products, reported as executed_frac" if d["unit"] == "TFLOP/s"
+                     else "algorithmic bytes per launch")}
+    if "executed_frac" in d:
+        roof["executed_frac"] = d["executed_frac"]
     return kernels, roof
 
 

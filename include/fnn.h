@@ -57,7 +57,7 @@ typedef enum {
   FNN_E_CAPACITY = -4,  /* neighbour list larger than its capacity; info = entries needed */
   FNN_E_OOM = -5,       /* device allocation failed */
   FNN_E_TIMEOUT = -6,   /* a bounded device wait gave up */
-  FNN_E_NONFINITE = -7, /* non-finite coordinate or energy */
+  FNN_E_NONFINITE = -7, /* non-finite coordinate (info = atom) or energy (info = -(structure + 1)) */
   FNN_E_CUDA = -8,      /* a CUDA runtime call failed; see fnn_last_error */
   FNN_E_STATE = -9      /* call out of order (e.g. no weights loaded) */
 } fnn_status;
@@ -292,11 +292,17 @@ typedef struct {
   double bytes_per_atom;    /* the admission estimate */
   double host_ms;           /* scheduler time spent retiring and re-laying out the batch */
   double step_ms;           /* scheduler time spent in batch steps (GPU work, waited for) */
+  int64_t failed;           /* requests failed alone by their own structure's device-detected error */
 } fnn_serve_counters;
 
 fnn_status fnn_serve_create(fnn_server **srv, fnn_ctx *ctx, size_t hbm_budget_bytes, fnn_precision prec,
                             int32_t rebuild_every);
-/* Copies the request; never blocks on the GPU.  FNN_E_OOM when the structure alone exceeds the budget. */
+/* Copies the request; never blocks on the GPU.  Rejected at once, before it can reach the shared batch:
+ * FNN_E_OOM when the structure alone exceeds the budget, FNN_E_SPECIES for an atomic number outside the
+ * table, FNN_E_NONFINITE for a non-finite position or velocity, FNN_E_CELL for a cell that is not
+ * orthorhombic or has an edge <= 2 (rc_rad + skin), FNN_E_INVALID for n_steps < 0.  A structure whose own
+ * atoms raise a device-detected error later (a non-finite coordinate or energy, an atom beyond the AEV
+ * neighbour limits) leaves the batch and its ticket's poll returns that error; the other requests go on. */
 fnn_status fnn_serve_submit(fnn_server *srv, const fnn_request *req, uint64_t *ticket);
 /* FNN_OK and the result (copied into the caller's buffers) once the request is done; FNN_PENDING if it
  * is not done within timeout_us (0 = do not wait).  A ticket's result can be taken once. */
@@ -312,12 +318,13 @@ fnn_status fnn_serve_destroy(fnn_server *srv);
  * library -- for example code running inside a host framework that hands out
  * all device memory from its own pool, or a latency-sensitive loop in which
  * cudaMalloc/cudaFree would synchronise the device and stall other streams.
- * Builds the same directed list as fnn_build_neighbors (same predicate, same
- * kernels) for at most FNN_STATIC_MAX_ATOMS atoms in at most FNN_STATIC_MAX_MOL
- * structures, with list radius R, and needs no context.  All scratch lives in
- * one array of about 0.4 MB compiled into the library, which every GPU that
- * loads the library keeps until the process exits; the call itself allocates
- * nothing.
+ * Builds the same directed list as fnn_build_neighbors (the same predicate and
+ * cell traversal, in a two-pass count/fill form; rows of at most 128 entries
+ * sorted by neighbour element, longer rows in traversal order, as there) for at
+ * most FNN_STATIC_MAX_ATOMS atoms in at most FNN_STATIC_MAX_MOL structures, with
+ * list radius R, and needs no context.  All scratch lives in one array of
+ * 423,280 bytes compiled into the library, which every GPU that loads the
+ * library keeps until the process exits; the call itself allocates nothing.
  *   sys      device system, as for fnn_build_neighbors.
  *   row_ptr  device int32 [N+1] (caller-owned), CSR row offsets.
  *   nbr      device int32 [cap], neighbour indices.
@@ -326,12 +333,16 @@ fnn_status fnn_serve_destroy(fnn_server *srv);
  * Returns FNN_E_CAPACITY at once, touching nothing, when n_atoms or n_mol is
  * above the limit; FNN_E_CAPACITY after the build when nnz > cap (entries
  * beyond cap are not written); otherwise the device status (FNN_E_SPECIES,
- * FNN_E_CELL, ...).  Synchronises the stream before returning.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array per device: calls that overlap on
- * the GPU (several streams or threads at once) race and corrupt each other's
- * lists; each call clears the parts that must start at zero.
+ * FNN_E_CELL, FNN_E_INVALID for inconsistent offsets, ...); FNN_E_CUDA when a
+ * CUDA call fails, after waiting for the work the call had already queued.
+ * Synchronises the stream before returning, so it must not be called while
+ * the stream (or, in global capture mode, any stream) is being captured.
+ * The array's device address is looked up (cudaGetSymbolAddress, with the
+ * device current) by the first call in each CUDA context of a device, and
+ * again after that context is reset.  Every call shares the one array per
+ * device: calls that overlap on the GPU (several streams or threads at once)
+ * race and corrupt each other's lists; each call clears the parts that must
+ * start at zero.
  */
 #define FNN_STATIC_MAX_ATOMS 8192
 #define FNN_STATIC_MAX_MOL 256
@@ -348,6 +359,15 @@ fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R, int32_t *
 fnn_status fnn_profile_enable(fnn_ctx *ctx, int on);
 fnn_status fnn_profile_read(fnn_ctx *ctx, char *names, double *ms, int64_t *launches, int32_t cap, int32_t *count);
 fnn_status fnn_launch_count(const fnn_ctx *ctx, int64_t *n);
+
+/* Self-test of the device-side wait limits (no counterpart in the paper; failure detection).  Runs the
+ * neighbour build's single-pass prefix scan (decoupled look-back, whose every wait on a predecessor
+ * tile gives up after about a second of clock cycles and posts FNN_E_TIMEOUT) over a library-owned
+ * array of 3 x 2048 ones.  withhold != 0 makes the first tile never publish its sum, so the other
+ * tiles' waits run out: the next fnn_sync returns FNN_E_TIMEOUT, nothing reads the scan's result, and
+ * the context stays usable.  withhold == 0 checks the scan's result (FNN_E_INVALID if wrong).
+ * Asynchronous on stream. */
+fnn_status fnn_selftest_lookback(fnn_ctx *ctx, int32_t withhold, void *stream);
 
 /* Text of the last host-side error of this context (never NULL). */
 const char *fnn_last_error(const fnn_ctx *ctx);

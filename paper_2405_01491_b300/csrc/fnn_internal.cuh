@@ -215,7 +215,9 @@ struct fnn_nlist {
 
 namespace fnn {
 
-enum { META_CELLS = 0, META_NNZ = 1, META_NPAD = 2, META_SEG = 4 /* [8] segment starts */, META_LEN = 16 };
+// META_BAD: 1 when the structure offsets are inconsistent (written once per build by k_check_cover's first
+// block; every later setup kernel then treats all atoms as outside every structure)
+enum { META_CELLS = 0, META_NNZ = 1, META_NPAD = 2, META_BAD = 3, META_SEG = 4 /* [8] segment starts */, META_LEN = 16 };
 
 // ---------------------------------------------------------------------------------------- helpers
 #define FNN_CUDA_TRY(ctx, call)                                                        \

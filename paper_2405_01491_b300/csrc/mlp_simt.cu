@@ -251,7 +251,7 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
       for (int q = 0; q < nwarp; q++) t += red[q];
       if (S == 1) {
         E[mol] = t;
-        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, -(long long)(mol + 1));
         last = 0;
       } else {
         part[(size_t)mol * S + y] = t;
@@ -270,7 +270,7 @@ __global__ void k_energy(int n_mol, int n_atoms, const int32_t *mol_offsets, con
       if (lane == 0) {
         E[mol] = t;
         ticket[mol] = 0u;
-        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, mol);
+        if (!isfinite(t)) post_status(st, FNN_E_NONFINITE, -(long long)(mol + 1));
       }
     }
     __syncthreads();

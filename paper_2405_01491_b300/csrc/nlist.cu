@@ -141,7 +141,7 @@ constexpr long long LOOKBACK_LIMIT = 2000000000LL;   // clock64 cycles (about a 
 __global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(const int32_t *in, int32_t *out, int32_t *out2,
                                                               int64_t n_max, const int32_t *n_dev,
                                                               int32_t *total_dev, int64_t cap, int32_t *scratch,
-                                                              DevStatus *st) {
+                                                              DevStatus *st, int withhold_first = 0) {
   __shared__ int tile_s, prefix_s;
   unsigned *ticket = reinterpret_cast<unsigned *>(scratch);
   unsigned long long *word = reinterpret_cast<unsigned long long *>(scratch + 2);
@@ -195,7 +195,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_single_pass(const int32_t *in,
       }
     }
     if (lane == 0) {
-      atomicExch(&word[t], (2ull << 32) | (unsigned)(prefix + agg));
+      // (withhold_first: the self-test of the bounded wait; tile 0 never publishes, so its successors'
+      // waits run out)
+      if (!(withhold_first && t == 0)) atomicExch(&word[t], (2ull << 32) | (unsigned)(prefix + agg));
       prefix_s = prefix;
       if (base0 + SCAN_TILE >= n) {   // the last tile
         if (total_dev) *total_dev = prefix + agg;
@@ -241,23 +243,53 @@ fnn_status exclusive_scan(fnn_ctx *ctx, const int32_t *in, int32_t *out, int64_t
   return check_launch(ctx, "exclusive_scan");
 }
 
+// Self-test of the look-back's bounded wait (fnn_selftest_lookback): a scan of SELFTEST_TILES tiles of
+// ones in a library-owned buffer, optionally with tile 0's publication withheld.  Nothing reads the
+// result but k_selftest_check, which posts FNN_E_INVALID when a scan that was not withheld is wrong.
+constexpr int SELFTEST_TILES = 3;
+__global__ void k_selftest_fill(int32_t *data, int64_t n, int32_t *scratch, int64_t n_scratch) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    data[k] = 1;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_scratch;
+       k += (int64_t)gridDim.x * blockDim.x)
+    scratch[k] = 0;
+}
+__global__ void k_selftest_check(const int32_t *data, int64_t n, DevStatus *st) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    if (data[k] != (int32_t)k) post_status(st, FNN_E_INVALID, k);
+}
+
 // ------------------------------------------------------------------------------------- structures
-// offsets must start at 0, end at N and never decrease: otherwise some atom has no structure
-// (also resets the per-structure bounding boxes, when given, to empty)
-// (the build's first kernel also clears, when given, meta, the structure cell counts and the scan scratch)
+// offsets must start at 0, end at N and never decrease: otherwise some atom has no structure, or
+// structures overlap.  The verdict is global: the first block checks every offset and writes bad[0]
+// (0 or 1) once, so the later setup kernels can drop every structure of an inconsistent batch (per
+// structure checks alone would let overlapping structures claim more cells than the bound allows).
+// The other blocks reset the per-structure bounding boxes, when given, to empty, and clear, when given,
+// meta (except META_BAD), the structure cell counts and the scan scratch.
 __global__ void k_check_cover(fnn_system sys, DevStatus *st, float *bbox, int32_t *meta, int32_t *mol_cells,
-                              int32_t *scratch, int64_t n_scratch) {
+                              int32_t *scratch, int64_t n_scratch, int32_t *bad) {
+  if (blockIdx.x == 0) {
+    int any = 0;
+    for (int m = threadIdx.x; m <= sys.n_mol; m += blockDim.x) {
+      const int a = sys.mol_offsets[m];
+      bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
+      if (m == sys.n_mol) ok = ok && a == sys.n_atoms;
+      if (!ok) {
+        post_status(st, FNN_E_INVALID, m);
+        any = 1;
+      }
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) *bad = any;
+  }
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ng = (int64_t)gridDim.x * blockDim.x;
   if (meta)
-    for (int64_t k = g; k < META_LEN; k += ng) meta[k] = 0;
+    for (int64_t k = g; k < META_LEN; k += ng)
+      if (meta + k != bad) meta[k] = 0;
   if (scratch)
     for (int64_t k = g; k < n_scratch; k += ng) scratch[k] = 0;
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= sys.n_mol; m += gridDim.x * blockDim.x) {
     if (mol_cells) mol_cells[m] = 0;
-    int a = sys.mol_offsets[m];
-    bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
-    if (m == sys.n_mol) ok = ok && a == sys.n_atoms;
-    if (!ok) post_status(st, FNN_E_INVALID, m);
     if (bbox && m < sys.n_mol)
       for (int a3 = 0; a3 < 3; a3++) {
         bbox[6 * (size_t)m + a3] = __int_as_float(0x7f800000);        // +inf
@@ -284,9 +316,10 @@ __device__ __forceinline__ void atomic_fmax(float *a, float v) {
 // the structure's bounding box (a warp whose atoms share one structure reduces before its atomics).
 // (also writes atom_mol = -1 and element 0 for an atom outside every structure, and zeroes counts [N+1])
 __global__ void k_atom_setup(fnn_system sys, int32_t *atom_mol, uint8_t *elem, float *bbox, int32_t *counts,
-                             DevStatus *st) {
+                             DevStatus *st, const int32_t *bad) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   const int lane = threadIdx.x & 31;
+  const bool drop = *bad != 0;   // inconsistent offsets: no atom belongs to a structure
   if (counts && blockIdx.x == 0 && threadIdx.x == 0) counts[sys.n_atoms] = 0;
   for (int i0 = blockIdx.x * blockDim.x; i0 < sys.n_atoms; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + threadIdx.x;
@@ -299,7 +332,7 @@ __global__ void k_atom_setup(fnn_system sys, int32_t *atom_mol, uint8_t *elem, f
         const int mid = (lo + hi) >> 1;
         if (sys.mol_offsets[mid] <= i) lo = mid; else hi = mid;
       }
-      if (sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
+      if (!drop && sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
       if (m < 0) {
         atom_mol[i] = -1;
         elem[i] = 0;
@@ -347,10 +380,11 @@ __device__ MolGrid make_grid(const fnn_system &sys, int m, int n, int pbc, float
 
 // Per structure: offsets check, then the grid from its bounding box
 __global__ void k_mol_grid(fnn_system sys, const float *bbox, MolGrid *grid, int32_t *mol_cells, double R,
-                           DevStatus *st) {
+                           DevStatus *st, const int32_t *bad) {
+  const bool drop = *bad != 0;   // inconsistent offsets (posted by k_check_cover): every structure empty
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < sys.n_mol; m += gridDim.x * blockDim.x) {
     const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
-    if (a0 < 0 || a1 < a0 || a1 > sys.n_atoms) {
+    if (drop || a0 < 0 || a1 < a0 || a1 > sys.n_atoms) {
       post_status(st, FNN_E_INVALID, m);
       grid[m] = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
       mol_cells[m] = 1;
@@ -431,14 +465,14 @@ constexpr int SETUP_NT = 512;
 
 __global__ void __launch_bounds__(SETUP_NT) k_mol_setup(fnn_system sys, MolGrid *grid, int32_t *mol_cells,
                                                         int32_t *atom_mol, uint8_t *elem, double R,
-                                                        DevStatus *st) {
+                                                        DevStatus *st, const int32_t *bad) {
+  const bool drop = *bad != 0;   // inconsistent offsets (posted by k_check_cover): every structure empty
   __shared__ float red[6][SETUP_NT / 32];
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int m = blockIdx.x; m < sys.n_mol; m += gridDim.x) {
     int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
-    bool bad = (a0 < 0 || a1 < a0 || a1 > sys.n_atoms);
-    if (bad) {
+    if (drop || a0 < 0 || a1 < a0 || a1 > sys.n_atoms) {
       if (threadIdx.x == 0) {
         post_status(st, FNN_E_INVALID, m);
         grid[m] = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
@@ -519,7 +553,7 @@ __device__ __forceinline__ int axis_cell(float x, float o, float inv, float L, i
 }
 
 __global__ void k_bin(fnn_system sys, const MolGrid *grid, const int32_t *mol_base, const int32_t *atom_mol,
-                      int32_t *cell_of, int32_t *cell_count) {
+                      int32_t *cell_of, int32_t *cell_count, int64_t cells_bound) {
   const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sys.n_atoms; i += gridDim.x * blockDim.x) {
     int m = atom_mol[i];
@@ -533,6 +567,10 @@ __global__ void k_bin(fnn_system sys, const MolGrid *grid, const int32_t *mol_ba
     int cy = axis_cell(p.y, g.oy, g.iy, g.Ly, g.pbc, g.dy);
     int cz = axis_cell(p.z, g.oz, g.iz, g.Lz, g.pbc, g.dz);
     int c = mol_base[m] + (cz * g.dy + cy) * g.dx + cx;
+    if (c < 0 || c >= cells_bound) {   // unreachable with consistent offsets; never count outside the array
+      cell_of[i] = -1;
+      continue;
+    }
     cell_of[i] = c;
     atomicAdd(&cell_count[c], 1);
   }
@@ -1240,13 +1278,14 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   {
     FNN_KERNEL(ctx, "check_cover", s);
     k_check_cover<<<cover_blocks, 256, 0, s>>>(*sys, ctx->status, nl->bbox, nl->meta, nl->mol_cells, nl->scan_tmp,
-                                               3 * third);
+                                               3 * third, nl->meta + META_BAD);
   }
   if (N > 0) {
     int ab = (N + 255) / 256;
     if (ab > 8 * ctx->num_sms) ab = 8 * ctx->num_sms;
     FNN_KERNEL(ctx, "atom_setup", s);
-    k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, nl->counts, ctx->status);
+    k_atom_setup<<<ab, 256, 0, s>>>(*sys, nl->atom_mol, nl->elem, nl->bbox, nl->counts, ctx->status,
+                                    nl->meta + META_BAD);
   } else {
     FNN_CUDA_TRY(ctx, cudaMemsetAsync(nl->counts, 0, sizeof(int32_t), s));
   }
@@ -1272,7 +1311,8 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   }
   {
     FNN_KERNEL(ctx, "mol_grid", s);
-    k_mol_grid<<<(NM + 127) / 128, 128, 0, s>>>(*sys, nl->bbox, nl->grid, nl->mol_cells, R, ctx->status);
+    k_mol_grid<<<(NM + 127) / 128, 128, 0, s>>>(*sys, nl->bbox, nl->grid, nl->mol_cells, R, ctx->status,
+                                                nl->meta + META_BAD);
   }
   if ((st = exclusive_scan(ctx, nl->mol_cells, nl->mol_cells, NM + 1, nl->meta + META_CELLS, tmp_mol, third, s,
                            nullptr, nullptr, -1, true)))
@@ -1282,7 +1322,7 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
     int tb = 256, nb = (N + tb - 1) / tb;
     {
       FNN_KERNEL(ctx, "bin", s);
-      k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count);
+      k_bin<<<nb, tb, 0, s>>>(*sys, nl->grid, nl->mol_cells, nl->atom_mol, nl->cell_of, nl->cell_count, cells_bound);
     }
     // cell starts (over the cells that exist), and the same starts back into the counts as the scatter's cursors
     if ((st = exclusive_scan(ctx, nl->cell_count, nl->cell_start, cells_bound + 1, nullptr, tmp_cells, third, s,
@@ -1330,6 +1370,30 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   return check_launch(ctx, "fnn_build_neighbors");
 }
 
+extern "C" fnn_status fnn_selftest_lookback(fnn_ctx *ctx, int32_t withhold, void *stream) {
+  if (!ctx) return FNN_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = (int64_t)SELFTEST_TILES * SCAN_TILE, ns = 2 * SELFTEST_TILES + 2;
+  int32_t *buf = nullptr;
+  FNN_CUDA_TRY(ctx, cudaMallocAsync((void **)&buf, (size_t)(n + ns) * sizeof(int32_t), s));
+  int32_t *tmp = buf + n;   // 8-byte aligned: n is a multiple of SCAN_TILE
+  {
+    FNN_KERNEL(ctx, "selftest_fill", s);
+    k_selftest_fill<<<8, 256, 0, s>>>(buf, n, tmp, ns);
+  }
+  {
+    FNN_KERNEL(ctx, "scan", s);
+    k_scan_single_pass<<<SELFTEST_TILES, SCAN_NT, 0, s>>>(buf, buf, nullptr, n, nullptr, nullptr, -1, tmp,
+                                                          ctx->status, withhold != 0);
+  }
+  if (!withhold) {
+    FNN_KERNEL(ctx, "selftest_check", s);
+    k_selftest_check<<<8, 256, 0, s>>>(buf, n, ctx->status);
+  }
+  FNN_CUDA_TRY(ctx, cudaFreeAsync(buf, s));
+  return check_launch(ctx, "fnn_selftest_lookback");
+}
+
 extern "C" fnn_status fnn_nlist_nnz(fnn_nlist *nl, int64_t *nnz) {
   if (!nl || !nnz) return FNN_E_INVALID;
   if (!nl->built) {
@@ -1375,10 +1439,12 @@ extern "C" fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t 
 }
 
 // ------------------------------------------------------------------ allocation-free list build
-// fnn_build_neighbors_static: the same kernels as fnn_build_neighbors, with every scratch array
-// (structure grids, cell counts and starts, per-atom cell data, scan partials, status) carved from
-// one file-scope device array instead of library allocations.  For callers that may not allocate
-// device memory; sizes are capped at FNN_STATIC_MAX_ATOMS atoms and FNN_STATIC_MAX_MOL structures.
+// fnn_build_neighbors_static: the predicate and cell traversal of fnn_build_neighbors in a two-pass
+// count/fill form (k_pairs<false>, scan, k_pairs<true>, then k_sort_rows orders rows of at most
+// PAIR_STRIDE entries by neighbour element, as k_pairs_compact does), with every scratch array (structure
+// grids, cell counts and starts, per-atom cell data, scan partials, status) carved from one file-scope
+// device array instead of library allocations.  For callers that may not allocate device memory; sizes
+// are capped at FNN_STATIC_MAX_ATOMS atoms and FNN_STATIC_MAX_MOL structures.
 #include <mutex>
 
 namespace fnn {
@@ -1404,28 +1470,67 @@ struct StaticScratch {
   int32_t cell_start[NS_MAX_CELLS + 1];
   uint8_t elem[NS_MAX_ATOMS];
 };
+// the size the header states (423,280 bytes with 8192 atoms and 256 structures)
+static_assert(sizeof(StaticScratch) == 423280, "fnn.h states the static scratch size");
 
-// The scratch every call shares (about 0.3 MB on every device that loads the library).
+// The scratch every call shares (423,280 bytes on every device that loads the library).
 static __device__ __align__(256) unsigned char g_nl_scratch[sizeof(StaticScratch)];
 
 constexpr int NS_MAX_DEVICES = 64;
 std::mutex g_nl_scratch_mu;
-StaticScratch *g_nl_scratch_dev[NS_MAX_DEVICES] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;   // driver id of the context the address belongs to (0: none yet)
+  StaticScratch *ptr = nullptr;
+};
+ScratchAddr g_nl_scratch_dev[NS_MAX_DEVICES];
 
-// Device address of the scratch on the current device; looked up once per device.
+// Unique id of the current thread's CUDA context (0 when the driver cannot say).  Ids are never reused
+// within a process, so an address looked up in a context that was since destroyed (cudaDeviceReset) is
+// never taken for the new context's.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrentFn)(void **);
+  typedef int (*GetIdFn)(void *, unsigned long long *);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+    cudaGetLastError();
+  });
+  void *c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == 0 && c && get_id(c, &id) == 0) return id;
+  return 0;
+}
+
+// Device address of the scratch in the current device's context: looked up with cudaGetSymbolAddress
+// once per context (a device's first call, and its first call after a context reset), with the device
+// current.  When the context id is unavailable the address is looked up on every call.
 cudaError_t static_scratch(StaticScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NS_MAX_DEVICES) return cudaErrorInvalidDevice;
+  if ((e = cudaSetDevice(dev)) != cudaSuccess) return e;   // makes the device's primary context current
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_nl_scratch_mu);
-  if (!g_nl_scratch_dev[dev]) {
+  ScratchAddr &a = g_nl_scratch_dev[dev];
+  if (id == 0 || a.ctx_id != id || !a.ptr) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_nl_scratch);
     if (e != cudaSuccess) return e;
-    g_nl_scratch_dev[dev] = reinterpret_cast<StaticScratch *>(p);
+    a.ptr = reinterpret_cast<StaticScratch *>(p);
+    a.ctx_id = id;
   }
-  *out = g_nl_scratch_dev[dev];
+  *out = a.ptr;
   return cudaSuccess;
 }
 
@@ -1442,9 +1547,13 @@ cudaError_t scan_in_place(int32_t *data, int64_t n, int32_t *total_dev, int32_t 
 }  // namespace
 }  // namespace fnn
 
+// On a failed step, the work this call already queued is waited for (its error ignored) before the
+// error returns, so no kernel of the call still writes the caller's arrays or the shared scratch.
 #define FNN_STATIC_TRY(call)                 \
   do {                                       \
     if ((call) != cudaSuccess) {             \
+      cudaGetLastError();                    \
+      cudaStreamSynchronize(s);              \
       cudaGetLastError();                    \
       return FNN_E_CUDA;                     \
     }                                        \
@@ -1458,9 +1567,12 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     return FNN_E_INVALID;
   *nnz = 0;
   if (sys->n_atoms > NS_MAX_ATOMS || sys->n_mol > NS_MAX_MOL) return FNN_E_CAPACITY;  // beyond the static scratch
-  StaticScratch *S = nullptr;
-  FNN_STATIC_TRY(static_scratch(&S));
   cudaStream_t s = (cudaStream_t)stream;
+  StaticScratch *S = nullptr;
+  if (static_scratch(&S) != cudaSuccess) {   // nothing queued yet
+    cudaGetLastError();
+    return FNN_E_CUDA;
+  }
   const int N = sys->n_atoms, NM = sys->n_mol;
   const int64_t cells_bound = 2LL * N + NM + 1;
 
@@ -1473,14 +1585,15 @@ extern "C" fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R
     FNN_STATIC_TRY(cudaMemsetAsync(S->atom_mol, 0xff, (size_t)N * sizeof(int32_t), s));
     FNN_STATIC_TRY(cudaMemsetAsync(S->elem, 0, (size_t)N, s));
   }
-  k_check_cover<<<(NM + 256) / 256, 256, 0, s>>>(*sys, &S->status, nullptr, nullptr, nullptr, nullptr, 0);
-  k_mol_setup<<<NM, SETUP_NT, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->elem, R, &S->status);
+  k_check_cover<<<1, 256, 0, s>>>(*sys, &S->status, nullptr, nullptr, nullptr, nullptr, 0, S->meta + META_BAD);
+  k_mol_setup<<<NM, SETUP_NT, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->elem, R, &S->status,
+                                      S->meta + META_BAD);
   FNN_STATIC_TRY(scan_in_place(S->mol_cells, NM + 1, S->meta + META_CELLS, S->scan_tmp, s));
   FNN_STATIC_TRY(cudaMemsetAsync(S->cell_count, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
   FNN_STATIC_TRY(cudaMemsetAsync(S->cell_start, 0, ((size_t)cells_bound + 1) * sizeof(int32_t), s));
   if (N > 0) {
     const int nb = (N + 255) / 256;
-    k_bin<<<nb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_count);
+    k_bin<<<nb, 256, 0, s>>>(*sys, S->grid, S->mol_cells, S->atom_mol, S->cell_of, S->cell_count, cells_bound);
     FNN_STATIC_TRY(cudaMemcpyAsync(S->cell_start, S->cell_count, ((size_t)cells_bound + 1) * sizeof(int32_t),
                                    cudaMemcpyDeviceToDevice, s));
     FNN_STATIC_TRY(scan_in_place(S->cell_start, cells_bound + 1, nullptr, S->scan_tmp, s));

@@ -12,6 +12,7 @@
 // relative to the skin.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -63,6 +64,7 @@ struct Slot {           // a structure in the device batch
   int step = 0;         // evaluations done
   int since_build = 0;  // evaluations since its list was last rebuilt
   int64_t hist_off = 0; // first entry of its energy history
+  fnn_status failed = FNN_OK;   // a device-detected error of this structure alone: it leaves the batch
 };
 
 // one copy of a structure's atoms (or history) from a source array into the new layout
@@ -151,7 +153,30 @@ struct fnn_server {
   Seg *d_rseg = nullptr, *h_rseg = nullptr;
   size_t cap_rseg = 0, cap_hrseg = 0;
   double host_ms = 0, step_ms = 0;   // worker time in layout changes and in batch steps
+  long long failed = 0;              // requests that failed alone (their structure's own error)
+  std::vector<std::pair<fnn_status, int64_t>> faults;   // device errors of single structures in this step
 };
+
+// Index in S->active of the structure a device-detected error belongs to, or -1 when the error concerns
+// the whole batch: a non-finite coordinate (info = atom) or energy (info = -(structure + 1)), or an atom
+// beyond the AEV kernels' neighbour limits (FNN_E_CAPACITY, info = -(atom + 1)).
+static int fault_slot(const fnn_server *S, fnn_status code, int64_t info) {
+  int64_t atom = -1;
+  if (code == FNN_E_NONFINITE && info < 0) {
+    const int64_t m = -info - 1;
+    return m < (int64_t)S->active.size() ? (int)m : -1;
+  }
+  if (code == FNN_E_NONFINITE) atom = info;
+  else if (code == FNN_E_CAPACITY && info < 0) atom = -info - 1;
+  else return -1;
+  int lo = 0, hi = (int)S->active.size();   // last slot whose first atom is <= atom
+  if (hi == 0 || atom < S->active[0].offset) return -1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (S->active[mid].offset <= atom) lo = mid; else hi = mid;
+  }
+  return atom < S->active[lo].offset + S->active[lo].req.n ? lo : -1;
+}
 
 static double estimate_bytes_per_atom(const fnn_ctx *ctx, fnn_precision prec) {
   const double M = ctx->cfg.n_members;
@@ -442,6 +467,10 @@ static fnn_status serve_step(fnn_server *S) {
         if ((st = fnn_nlist_reserve(S->nl, sys.n_atoms, nm, info + info / 4))) return st;
         continue;
       }
+      if (st && fault_slot(S, st, info) >= 0) {   // one structure's own error: the others go on
+        S->faults.emplace_back(st, info);
+        st = FNN_OK;
+      }
       if (st) return st;
       break;
     }
@@ -512,11 +541,31 @@ static void worker_main(fnn_server *S) {
     fnn_status err = FNN_OK;
     std::vector<Slot> keep;
     const bool changed = !incoming.empty() ||
-                         std::any_of(S->active.begin(), S->active.end(),
-                                     [](const Slot &sl) { return sl.step >= sl.req.n_steps; });
+                         std::any_of(S->active.begin(), S->active.end(), [](const Slot &sl) {
+                           return sl.step >= sl.req.n_steps || sl.failed != FNN_OK;
+                         });
     if (changed) {
-      for (auto &sl : S->active) (sl.step >= sl.req.n_steps ? fin : keep).push_back(std::move(sl));
+      std::vector<std::pair<uint64_t, Out>> failed_out;
+      for (auto &sl : S->active) {
+        if (sl.failed != FNN_OK) {   // its own error: its ticket fails, nothing of it is copied back
+          Out o;
+          o.status = sl.failed;
+          o.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t_submit).count();
+          o.n_steps_done = sl.step;
+          failed_out.emplace_back(sl.req.ticket, std::move(o));
+          continue;
+        }
+        (sl.step >= sl.req.n_steps ? fin : keep).push_back(std::move(sl));
+      }
       S->active.clear();
+      if (!failed_out.empty()) {
+        {
+          std::lock_guard<std::mutex> lock(S->mu);
+          S->failed += (long long)failed_out.size();
+          for (auto &po : failed_out) S->done[po.first] = std::move(po.second);
+        }
+        S->cv_done.notify_all();
+      }
     }
     if (!fin.empty()) err = start_retire(S, fin);
     const bool retiring = !fin.empty() && err == FNN_OK;
@@ -534,7 +583,18 @@ static void worker_main(fnn_server *S) {
       if (err == FNN_OK) {
         int64_t info = 0;
         err = fnn_sync(S->ctx, S->stream, &info);
+        if (err != FNN_OK && fault_slot(S, err, info) >= 0) {
+          S->faults.emplace_back(err, info);
+          err = FNN_OK;
+        }
       }
+      // structures with their own error leave the batch at the next layout change; the step's results of
+      // every other structure stand (structures never interact)
+      for (auto &f : S->faults) {
+        const int k = fault_slot(S, f.first, f.second);
+        if (k >= 0 && S->active[k].failed == FNN_OK) S->active[k].failed = f.first;
+      }
+      S->faults.clear();
       std::lock_guard<std::mutex> lock(S->mu);
       S->batch_steps++;
       S->atom_evals += (long long)S->batch_atoms;
@@ -600,7 +660,20 @@ extern "C" fnn_status fnn_serve_create(fnn_server **out, fnn_ctx *ctx, size_t hb
 extern "C" fnn_status fnn_serve_submit(fnn_server *S, const fnn_request *q, uint64_t *ticket) {
   if (!S || !q || !ticket || q->n_atoms < 0 || (q->n_atoms > 0 && (!q->Z || !q->pos)) || !(q->dt_fs > 0))
     return FNN_E_INVALID;
+  if (q->n_steps < 0) return FNN_E_INVALID;
   if (q->n_atoms * S->bytes_per_atom > (double)S->budget) return FNN_E_OOM;   // alone it exceeds the budget
+  // what the device would reject for the whole batch is rejected here, for this request alone
+  for (int i = 0; i < q->n_atoms; i++) {
+    if (element_of(q->Z[i]) < 0) return FNN_E_SPECIES;
+    for (int a = 0; a < 3; a++)
+      if (!std::isfinite(q->pos[3 * i + a]) || (q->vel && !std::isfinite(q->vel[3 * i + a]))) return FNN_E_NONFINITE;
+  }
+  if (q->cell) {
+    const float *c = q->cell;
+    const double R = S->ctx->cfg.rc_rad + S->ctx->cfg.skin;
+    const bool ortho = c[1] == 0.f && c[2] == 0.f && c[3] == 0.f && c[5] == 0.f && c[6] == 0.f && c[7] == 0.f;
+    if (!ortho || !((double)c[0] > 2 * R) || !((double)c[4] > 2 * R) || !((double)c[8] > 2 * R)) return FNN_E_CELL;
+  }
   Req r;
   r.n = q->n_atoms;
   r.Z.assign(q->Z, q->Z + q->n_atoms);
@@ -665,6 +738,7 @@ extern "C" fnn_status fnn_serve_stats(fnn_server *S, fnn_serve_counters *st) {
   st->bytes_per_atom = S->bytes_per_atom;
   st->host_ms = S->host_ms;
   st->step_ms = S->step_ms;
+  st->failed = S->failed;
   return S->fatal;
 }
 

@@ -72,7 +72,7 @@ class CResult(ctypes.Structure):
 class CServeCounters(ctypes.Structure):
     _fields_ = [("atom_evals", ctypes.c_int64), ("batch_steps", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("max_batch_atoms", ctypes.c_int64), ("pending", ctypes.c_int64), ("bytes_per_atom", ctypes.c_double),
-                ("host_ms", ctypes.c_double), ("step_ms", ctypes.c_double)]
+                ("host_ms", ctypes.c_double), ("step_ms", ctypes.c_double), ("failed", ctypes.c_int64)]
 
 
 class CSystem(ctypes.Structure):
@@ -112,6 +112,7 @@ def _load():
         "fnn_profile_enable": (I32, [P, I32]),
         "fnn_profile_read": (I32, [P, P, P, P, I32, P]),
         "fnn_launch_count": (I32, [P, P]),
+        "fnn_selftest_lookback": (I32, [P, I32, P]),
         "fnn_build_neighbors_static": (I32, [P, ctypes.c_double, P, P, P, I64, P, P]),
         "fnn_md_run": (I32, [P, P, P, P, P, I32, I32, ctypes.c_double, I32, P, P, P]),
         "fnn_serve_create": (I32, [P, P, ctypes.c_size_t, I32, I32]),

@@ -39,8 +39,10 @@ def _reference_list(fnn, ds, skin):
 
 def test_static_entry_point_matches_allocating_one_twice_in_a_row():
     from paper_2405_01491_b300 import fnn
-    # a periodic box with a skin, then a ragged gas-phase batch: the second call must not see the first's data
-    for name, skin in (("box1500", 1.0), ("batch64", 0.0)):
+    # a periodic box with a skin, then a ragged gas-phase batch: the second call must not see the first's data;
+    # then a dense box at R = 6.5 A whose rows hold about 158 entries (beyond the 128 that are sorted by
+    # element: such rows keep the traversal order, on both entry points)
+    for name, skin in (("box1500", 1.0), ("batch64", 0.0), ("box1100", 1.4)):
         ds = fnn.DeviceSystem.from_structures(structure(name))
         R = 5.1 + skin
         row_ref, nbr_ref, sh_ref = _reference_list(fnn, ds, skin)
@@ -50,6 +52,8 @@ def test_static_entry_point_matches_allocating_one_twice_in_a_row():
         assert np.array_equal(row_ptr, row_ref)
         assert np.array_equal(nbr, nbr_ref)
         assert np.array_equal(sh, sh_ref)
+        if name == "box1100":
+            assert np.diff(row_ptr).max() > 128
 
 
 def test_static_entry_point_limits():
@@ -63,3 +67,19 @@ def test_static_entry_point_limits():
     big = synth.mix_box(9000, (9000 / 0.1) ** (1 / 3), seed=5)
     code, nnz, *_ = _static_list(fnn, fnn.DeviceSystem.from_structures(big), 5.1, cap=10)
     assert code == -4 and nnz == 0
+
+
+def test_static_entry_point_rejects_overlapping_offsets():
+    from paper_2405_01491_b300 import fnn, synth
+    s = structure("box300")
+    N = s.n_atoms
+    # consistent structure by structure, but [0, N) twice: every structure is dropped, nothing is listed
+    over = synth.Structures(s.Z, s.pos, np.array([0, N, 0, N], np.int32), np.repeat(s.cell, 3, 0),
+                            np.repeat(s.pbc, 3))
+    code, nnz, row_ptr, *_ = _static_list(fnn, fnn.DeviceSystem.from_structures(over), 5.1, cap=1000)
+    assert code == -1 and nnz == 0 and not row_ptr.any()
+    # and the next call on the shared scratch is clean again
+    ds = fnn.DeviceSystem.from_structures(s)
+    row_ref, nbr_ref, _ = _reference_list(fnn, ds, 0.0)
+    code, nnz, row_ptr, nbr, _ = _static_list(fnn, ds, 5.1, cap=len(nbr_ref))
+    assert code == 0 and np.array_equal(row_ptr, row_ref) and np.array_equal(nbr, nbr_ref)
