@@ -240,24 +240,63 @@ fnn_status fnn_graph_destroy(fnn_graph *graph);
 fnn_status fnn_sync(fnn_ctx *ctx, void *stream, int64_t *info);
 
 /*
- * NVE velocity Verlet on the device (the native engine's NVE integrator, section V.D):
- * n_steps force evaluations at x_0 .. x_{n-1}.  After evaluation k every atom does v += a dt/2
- * (completing step k) and, unless k is the last, v += a dt/2 and x += v dt (a = F/m, masses
- * H 1.008 C 12.011 N 14.007 O 15.999 F 18.998 S 32.06 Cl 35.45 amu, 1 kcal/mol/A/amu = 4.184e-4
- * A/fs^2).  pos, vel: device [N][4] (w unused), updated in place (pos replaces sys->pos); the list is
- * rebuilt before evaluations 0, rebuild_every, 2 rebuild_every, ... (use a context skin of at least
- * the largest displacement between rebuilds).  E_hist: device [n_steps][n_mol] float64, or NULL.
- * F: device [N][3], the forces of the last evaluation.  The step index lives on the device, so on a
- * stream other than the legacy default stream every whole block of rebuild_every steps after the
- * first runs as a replay of one CUDA graph.  Asynchronous.
+ * NVE velocity Verlet on the device: fnn_md_run_ex with FNN_MD_NVE, the skin guard on, no kinetic
+ * history and no counters (asynchronous).  The list is rebuilt before evaluations 0, rebuild_every, ...
+ * and early whenever an atom has moved more than skin/2 since the last rebuild.
  */
 fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl, fnn_precision prec,
                       int32_t n_steps, double dt_fs, int32_t rebuild_every, double *E_hist, float *F, void *stream);
 
 /*
+ * Device-resident molecular dynamics (the native engine of section V.D): n_steps force evaluations at
+ * x_0 .. x_{n-1} of the system whose positions are pos.  After evaluation k every atom does
+ *   k > 0:     v += a dt/2  (completes step k-1; K_hist[k] is the kinetic energy of this v)
+ *   k < n-1:   v += a dt/2, then
+ *              FNN_MD_NVE:      x += v dt                                         (velocity Verlet)
+ *              FNN_MD_LANGEVIN: x += v dt/2, v = c1 v + c2 sqrt(kB T/m) xi, x += v dt/2   (BAOAB)
+ * a = F/m (masses H 1.008 C 12.011 N 14.007 O 15.999 F 18.998 S 32.06 Cl 35.45 amu; 1 kcal/mol/A/amu
+ * = 4.184e-4 A/fs^2), c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2), kB = 0.0019872041 kcal/mol/K.  xi: for
+ * atom i at noise step t = step0 + k, the Philox-4x32-10 block of counter (i, t mod 2^32, t >> 32, 0)
+ * and key (seed mod 2^32, seed >> 32) gives words w0..w3, u_j = (floor(w_j / 256) + 1/2) / 2^24, and
+ * xi = (sqrt(-2 ln u0) cos 2 pi u1, sqrt(-2 ln u0) sin 2 pi u1, sqrt(-2 ln u2) cos 2 pi u3).
+ * Neighbour list: rebuilt before evaluation 0, whenever rebuild_every evaluations have passed since the
+ * last rebuild, and (skin_guard != 0) before any evaluation at which some atom lies more than skin/2
+ * from its position at the last rebuild (the context's skin; with skin 0 any motion rebuilds).  The
+ * decision is taken on the device; on a stream other than the legacy default stream, whole blocks of
+ * rebuild_every steps after the first run as replays of one CUDA graph whose rebuilds are conditional
+ * nodes.  pos, vel: device [N][4] (w unused), updated in place.  E_hist: device [n_steps][n_mol]
+ * float64 potential energies, or NULL.  K_hist: device [n_steps][n_mol] float64 kinetic energies (kcal/mol),
+ * or NULL.  F: device [N][3], the forces of the last evaluation.  counters: host, or NULL; when given the
+ * call synchronises the stream and fills it.  Otherwise asynchronous.
+ */
+typedef enum { FNN_MD_NVE = 0, FNN_MD_LANGEVIN = 1 } fnn_md_integrator;
+typedef struct {
+  int32_t n_steps;          /* force evaluations */
+  double dt_fs;             /* time step, fs */
+  int32_t rebuild_every;    /* the list is rebuilt at least every this many evaluations (>= 1) */
+  int32_t skin_guard;       /* 1: also rebuild early when an atom moved more than skin/2 */
+  int32_t integrator;       /* fnn_md_integrator */
+  double temperature_K;     /* Langevin bath temperature */
+  double friction_per_fs;   /* Langevin friction gamma (> 0), 1/fs */
+  uint64_t seed;            /* Langevin noise key */
+  uint64_t step0;           /* noise counter of evaluation 0 (continue a run with step0 + n_steps) */
+} fnn_md_options;
+typedef struct {
+  int32_t rebuilds;          /* list builds, the first included */
+  int32_t guard_rebuilds;    /* of them, forced early by the skin guard */
+  int32_t graph_blocks;      /* blocks of rebuild_every steps that ran as graph replays */
+  double max_displacement;   /* largest displacement from the last rebuild seen by a rebuild decision, A */
+} fnn_md_counters;
+fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl,
+                         fnn_precision prec, const fnn_md_options *opt, double *E_hist, double *K_hist, float *F,
+                         fnn_md_counters *counters, void *stream);
+
+/*
  * Continuous-batching MD service.  A scheduler thread keeps a ragged batch of
  * structures on the device and advances all of them one velocity-Verlet step per batch step (one
- * neighbour-list/AEV/network/adjoint pass over the whole batch); between batch steps it retires
+ * neighbour-list/AEV/network/adjoint pass over the whole batch; the shared list is rebuilt when the
+ * batch changes, every rebuild_every steps, and early when an atom of any structure has moved more
+ * than skin/2 since the last rebuild); between batch steps it retires
  * finished structures and admits queued requests, in arrival order, while the batch's estimated
  * device memory stays within hbm_budget_bytes.  A structure's results do not depend on the rest of
  * the batch.  The server uses ctx (weights, constants, skin) exclusively while it exists: make no
@@ -293,6 +332,8 @@ typedef struct {
   double host_ms;           /* scheduler time spent retiring and re-laying out the batch */
   double step_ms;           /* scheduler time spent in batch steps (GPU work, waited for) */
   int64_t failed;           /* requests failed alone by their own structure's device-detected error */
+  int64_t rebuilds;         /* batch neighbour-list builds */
+  int64_t guard_rebuilds;   /* of them, forced early by the skin guard (an atom moved more than skin/2) */
 } fnn_serve_counters;
 
 fnn_status fnn_serve_create(fnn_server **srv, fnn_ctx *ctx, size_t hbm_budget_bytes, fnn_precision prec,

@@ -406,3 +406,86 @@ def velocity_verlet(s, w, v0, n_steps: int, dt: float, params: Params = Params()
             v = v + 0.5 * dt * a
             x = x + dt * v
     return np.asarray(energies), x, v, F
+
+
+# ---------------------------------------------------------------------------------------------- Langevin
+KB_KCAL = 0.0019872041   # Boltzmann constant, kcal/mol/K
+
+
+def philox4x32_10(ctr: np.ndarray, key) -> np.ndarray:
+    """Philox-4x32-10, the counter-based generator of Salmon, Moraes, Dror and Shaw (SC 2011): ten rounds,
+    each forming the two 64-bit products of counter words 0 and 2 with the multipliers 0xD2511F53 and
+    0xCD9E8D57 and mixing their halves with words 1, 3 and the round key; the key advances between rounds
+    by the Weyl constants 0x9E3779B9 and 0xBB67AE85.  ctr: uint32 [n, 4]; key: two uint32 words."""
+    c = np.asarray(ctr, np.uint64).copy()
+    k0, k1 = np.uint64(int(key[0]) & 0xffffffff), np.uint64(int(key[1]) & 0xffffffff)
+    mask = np.uint64(0xffffffff)
+    for r in range(10):
+        if r:
+            k0 = (k0 + np.uint64(0x9E3779B9)) & mask
+            k1 = (k1 + np.uint64(0xBB67AE85)) & mask
+        p0 = c[:, 0] * np.uint64(0xD2511F53)
+        p1 = c[:, 2] * np.uint64(0xCD9E8D57)
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c = np.stack([hi1 ^ c[:, 1] ^ k0, lo1, hi0 ^ c[:, 3] ^ k1, lo0], axis=1)
+    return c.astype(np.uint32)
+
+
+def langevin_noise(n_atoms: int, t: int, seed: int) -> np.ndarray:
+    """Three standard normal numbers per atom for noise step t: the Philox block of counter
+    (atom, t mod 2^32, t >> 32, 0) and key (seed mod 2^32, seed >> 32), each word w turned into
+    u = (floor(w / 256) + 1/2) / 2^24 in (0, 1), then the Box-Muller transform of (u0, u1) and (u2, u3)
+    (the sine of the second pair unused).  Returns float64 [n_atoms, 3]."""
+    ctr = np.zeros((n_atoms, 4), np.uint64)
+    ctr[:, 0] = np.arange(n_atoms)
+    ctr[:, 1] = t & 0xffffffff
+    ctr[:, 2] = (t >> 32) & 0xffffffff
+    w = philox4x32_10(ctr, (seed & 0xffffffff, (seed >> 32) & 0xffffffff)).astype(np.float64)
+    u = (np.floor(w / 256.0) + 0.5) / 2.0 ** 24
+    r0 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r1 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    return np.stack([r0 * np.cos(2 * np.pi * u[:, 1]), r0 * np.sin(2 * np.pi * u[:, 1]),
+                     r1 * np.cos(2 * np.pi * u[:, 3])], axis=1)
+
+
+def kinetic_energies(s, v) -> np.ndarray:
+    """Per-structure kinetic energy sum_i m_i |v_i|^2 / 2 in kcal/mol (v in A/fs, masses in amu)."""
+    m = np.asarray([MASS[int(e)] for e in elements(s.Z)])
+    ke = 0.5 * m * np.sum(np.asarray(v, np.float64) ** 2, axis=1) / ACCEL
+    off = np.asarray(s.mol_offsets)
+    return np.array([ke[off[i]:off[i + 1]].sum() for i in range(len(off) - 1)])
+
+
+def langevin_baoab(s, w, v0, n_steps: int, dt: float, temperature: float, gamma: float, seed: int,
+                   step0: int = 0, params: Params = Params()):
+    """Langevin dynamics by the BAOAB splitting (Leimkuhler and Matthews 2013), the integrator of the paper's
+    native engine for Langevin runs (section V.D).  n_steps force evaluations at x_0 .. x_{n-1}; after
+    evaluation k: B (v += a dt/2, completing step k-1 when k > 0), then, unless k is the last: B, A
+    (x += v dt/2), O (v = c1 v + c2 sqrt(kB T / m) xi with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2), xi
+    from langevin_noise at noise step step0 + k), A.  gamma = 0 is velocity Verlet.
+    Returns (potential energies [n, n_mol], kinetic energies of v_k [n, n_mol], final x, final v, final F)."""
+    el = elements(s.Z)
+    m = np.asarray([MASS[int(e)] for e in el])[:, None]
+    x = np.asarray(s.pos, np.float64).copy()
+    v = np.asarray(v0, np.float64).copy()
+    c1 = np.exp(-gamma * dt)
+    c2 = np.sqrt(1.0 - c1 * c1)
+    sig = np.sqrt(KB_KCAL * temperature * ACCEL / m)
+    energies, kinetic = [], []
+    F = None
+    for k in range(n_steps):
+        st = type(s)(s.Z, x, s.mol_offsets, s.cell, s.pbc)
+        r = energy_forces(st, w, params)
+        energies.append(r.energy)
+        a = r.forces / m * ACCEL
+        if k > 0:
+            v = v + 0.5 * dt * a
+        kinetic.append(kinetic_energies(s, v))
+        F = r.forces
+        if k < n_steps - 1:
+            v = v + 0.5 * dt * a
+            x = x + 0.5 * dt * v
+            v = c1 * v + c2 * sig * langevin_noise(s.n_atoms, step0 + k, seed)
+            x = x + 0.5 * dt * v
+    return np.asarray(energies), np.asarray(kinetic), x, v, F

@@ -200,6 +200,7 @@ extern "C" fnn_status fnn_destroy(fnn_ctx *ctx) {
   for (void *p : hp)
     if (p) cudaFree(p);
   if (h.graph) fnn_graph_destroy(h.graph);
+  if (ctx->pinned_flag) cudaFreeHost(ctx->pinned_flag);
   if (h.nl) fnn_nlist_destroy(h.nl);
   if (h.own) cudaStreamDestroy(h.own);
   if (h.status) cudaFreeHost(h.status);

@@ -144,6 +144,7 @@ struct fnn_ctx {
   int device = 0;
   int num_sms = 148;
   fnn::DevStatus *status = nullptr;   // device
+  int32_t *pinned_flag = nullptr;      // 64 pinned host bytes: device scalars read between eager MD steps
   fnn::DeviceWeights w;
   bool has_weights = false;
   fnn::Workspace ws;
@@ -301,5 +302,35 @@ fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *n
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
                               int ntile, double *E, cudaStream_t s);
 fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows);
+
+// ------------------------------------------------------------------------------------------- MD (md.cu)
+// device state of one MD run: the rebuild schedule and the skin guard
+struct MdState {
+  int since_build;      // evaluations since the last rebuild
+  unsigned max_d2;      // largest |x - x_ref|^2 since the last rebuild (float bits, non-negative)
+  int rebuilds, guard_rebuilds;
+  unsigned max_seen;    // largest max_d2 any rebuild decision saw (float bits)
+  int need;             // the last decision
+};
+// one integrator update after an evaluation: NVE velocity Verlet, or BAOAB Langevin when gamma > 0
+struct MdUpdate {
+  const int32_t *mol_step = nullptr, *mol_nsteps = nullptr;   // per structure, or NULL: step / nsteps for all
+  const float *mol_dt = nullptr;                              // per structure, or NULL: dt for all
+  int step = 0, nsteps = 0;
+  double dt = 0.0;
+  double gamma = 0.0, temperature = 0.0;   // 1/fs, K
+  uint64_t seed = 0, step0 = 0;            // noise key and the counter of evaluation 0
+  const float4 *xref = nullptr;            // positions at the last rebuild (guard), or NULL
+  unsigned *max_d2 = nullptr;              // max |x - xref|^2 (float bits) accumulated by atomicMax, or NULL
+  double *K = nullptr;                     // kinetic energies K[k * K_stride + m] (kcal/mol), or NULL
+  int64_t K_stride = 0;
+};
+fnn_status launch_md_update(fnn_ctx *ctx, const fnn_nlist *nl, int n, float4 *pos, float4 *vel, const float *F,
+                            const MdUpdate &u, cudaStream_t s);
+fnn_status launch_record_energy(fnn_ctx *ctx, int n_mol, const double *E, const int32_t *mol_step,
+                                const int32_t *mol_nsteps, const int64_t *hist_off, double *hist, int step,
+                                int64_t stride, cudaStream_t s);
+fnn_status launch_advance_steps(fnn_ctx *ctx, int n_mol, int32_t *mol_step, MdState *st, cudaStream_t s);
+fnn_status launch_md_ref(fnn_ctx *ctx, int n, const float4 *pos, float4 *xref, cudaStream_t s);
 
 }  // namespace fnn

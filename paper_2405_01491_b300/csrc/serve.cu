@@ -23,16 +23,6 @@
 
 #include "fnn_internal.cuh"
 
-namespace fnn {
-fnn_status launch_vv(fnn_ctx *ctx, const fnn_nlist *nl, int n, float4 *pos, float4 *vel, const float *F,
-                     const int32_t *mol_step, const int32_t *mol_nsteps, const float *mol_dt, int step, int nsteps,
-                     double dt, cudaStream_t s);
-fnn_status launch_record_energy(fnn_ctx *ctx, int n_mol, const double *E, const int32_t *mol_step,
-                                const int32_t *mol_nsteps, const int64_t *hist_off, double *hist, int step,
-                                int64_t stride, cudaStream_t s);
-fnn_status launch_advance_steps(fnn_ctx *ctx, int n_mol, int32_t *mol_step, cudaStream_t s);
-}  // namespace fnn
-
 using namespace fnn;
 using Clock = std::chrono::steady_clock;
 
@@ -154,6 +144,13 @@ struct fnn_server {
   size_t cap_rseg = 0, cap_hrseg = 0;
   double host_ms = 0, step_ms = 0;   // worker time in layout changes and in batch steps
   long long failed = 0;              // requests that failed alone (their structure's own error)
+  // skin guard: positions at the last rebuild, the batch's largest squared displacement since (device
+  // word, and its pinned host copy read after each step)
+  float4 *xref = nullptr;
+  size_t cap_xref = 0;
+  unsigned *d_max_d2 = nullptr;
+  float *h_max_d2 = nullptr;
+  long long since_any_build = 0, rebuilds = 0, guard_rebuilds = 0;
   std::vector<std::pair<fnn_status, int64_t>> faults;   // device errors of single structures in this step
 };
 
@@ -447,10 +444,16 @@ static fnn_status serve_step(fnn_server *S) {
   const int nm = (int)S->active.size();
   fnn_system sys{(int32_t)S->batch_atoms, nm, S->mol_offsets, S->Z[S->cur], reinterpret_cast<float *>(S->pos[S->cur]),
                  S->cell, S->pbc};
-  bool rebuild = false;
+  bool rebuild = false, due = false;
   for (auto &sl : S->active)
-    if (sl.since_build == 0 || sl.since_build >= S->rebuild_every) rebuild = true;
+    if (sl.since_build == 0 || sl.since_build >= S->rebuild_every) due = true;
+  // skin guard: an atom of some structure moved more than skin/2 since the last rebuild (the largest
+  // displacement of the batch, read back with the previous step)
+  const double hs = 0.5 * ctx->cfg.skin;
+  const bool moved = S->since_any_build > 0 && (double)*S->h_max_d2 > hs * hs;
+  rebuild = due || moved;
   fnn_status st;
+  if (!grow(&S->xref, &S->cap_xref, S->batch_atoms + 1)) return FNN_E_OOM;
   // the list and (through its padded row count) every network workspace grow geometrically with the
   // batch, so a batch that keeps growing does not reallocate gigabytes at every step
   if (sys.n_atoms > S->nl->atom_cap || nm > S->nl->mol_cap) {
@@ -475,18 +478,30 @@ static fnn_status serve_step(fnn_server *S) {
       break;
     }
     for (auto &sl : S->active) sl.since_build = 0;
+    S->since_any_build = 0;
+    S->rebuilds++;
+    if (!due) S->guard_rebuilds++;
+    if ((st = launch_md_ref(ctx, sys.n_atoms, S->pos[S->cur], S->xref, S->stream))) return st;
+    FNN_CUDA_TRY(ctx, cudaMemsetAsync(S->d_max_d2, 0, sizeof(unsigned), S->stream));
   }
   if ((st = fnn_energy_forces(ctx, &sys, S->nl, S->prec, S->E, S->F, nullptr, S->stream))) return st;
   if ((st = launch_record_energy(ctx, nm, S->E, S->mol_step, S->mol_nsteps, S->hist_off, S->hist, 0, 0, S->stream)))
     return st;
-  if ((st = launch_vv(ctx, S->nl, (int)S->batch_atoms, S->pos[S->cur], S->vel[S->cur], S->F, S->mol_step,
-                      S->mol_nsteps, S->mol_dt, 0, 0, 0.0, S->stream)))
+  MdUpdate u;
+  u.mol_step = S->mol_step;
+  u.mol_nsteps = S->mol_nsteps;
+  u.mol_dt = S->mol_dt;
+  u.xref = S->xref;
+  u.max_d2 = S->d_max_d2;
+  if ((st = launch_md_update(ctx, S->nl, (int)S->batch_atoms, S->pos[S->cur], S->vel[S->cur], S->F, u, S->stream)))
     return st;
-  if ((st = launch_advance_steps(ctx, nm, S->mol_step, S->stream))) return st;
+  if ((st = launch_advance_steps(ctx, nm, S->mol_step, nullptr, S->stream))) return st;
+  FNN_CUDA_TRY(ctx, cudaMemcpyAsync(S->h_max_d2, S->d_max_d2, sizeof(unsigned), cudaMemcpyDeviceToHost, S->stream));
   for (auto &sl : S->active) {
     sl.step++;
     sl.since_build++;
   }
+  S->since_any_build++;
   return FNN_OK;
 }
 
@@ -644,6 +659,17 @@ extern "C" fnn_status fnn_serve_create(fnn_server **out, fnn_ctx *ctx, size_t hb
     return FNN_E_CUDA;
   }
   fnn_status st = fnn_nlist_create(ctx, &S->nl, 0);
+  if (!st && (cudaMalloc((void **)&S->d_max_d2, 256) != cudaSuccess ||
+              cudaHostAlloc((void **)&S->h_max_d2, 64, cudaHostAllocDefault) != cudaSuccess)) {
+    cudaGetLastError();
+    if (S->d_max_d2) cudaFree(S->d_max_d2);
+    fnn_nlist_destroy(S->nl);
+    st = FNN_E_OOM;
+  }
+  if (!st) {
+    *S->h_max_d2 = 0.f;
+    cudaMemset(S->d_max_d2, 0, 256);
+  }
   if (st) {
     cudaEventDestroy(S->ev_pack);
     cudaEventDestroy(S->ev_ret);
@@ -739,6 +765,8 @@ extern "C" fnn_status fnn_serve_stats(fnn_server *S, fnn_serve_counters *st) {
   st->host_ms = S->host_ms;
   st->step_ms = S->step_ms;
   st->failed = S->failed;
+  st->rebuilds = S->rebuilds;
+  st->guard_rebuilds = S->guard_rebuilds;
   return S->fatal;
 }
 
@@ -759,10 +787,11 @@ extern "C" fnn_status fnn_serve_destroy(fnn_server *S) {
   }
   void *ptrs[] = {S->F, S->mol_offsets, S->mol_step, S->mol_nsteps, S->cell, S->pbc, S->E, S->hist_off,
                   S->hist_buf[0], S->hist_buf[1], S->mol_dt, S->sZ, S->spos, S->svel, S->d_seg,
-                  S->d_rseg, S->r_pos, S->r_vel, S->r_F, S->r_hist};
+                  S->d_rseg, S->r_pos, S->r_vel, S->r_F, S->r_hist, S->xref, S->d_max_d2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  void *hptrs[] = {S->h_seg, S->h_rseg, S->h_sZ, S->h_spos, S->h_svel, S->h_mol, S->h_rpos, S->h_rvel, S->h_rF, S->h_rhist};
+  void *hptrs[] = {S->h_seg,  S->h_rseg, S->h_sZ,   S->h_spos,  S->h_svel,
+                   S->h_mol,  S->h_rpos, S->h_rvel, S->h_rF,    S->h_rhist, S->h_max_d2};
   for (void *p : hptrs)
     if (p) cudaFreeHost(p);
   if (S->nl) fnn_nlist_destroy(S->nl);

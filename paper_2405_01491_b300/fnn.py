@@ -72,7 +72,19 @@ class CResult(ctypes.Structure):
 class CServeCounters(ctypes.Structure):
     _fields_ = [("atom_evals", ctypes.c_int64), ("batch_steps", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("max_batch_atoms", ctypes.c_int64), ("pending", ctypes.c_int64), ("bytes_per_atom", ctypes.c_double),
-                ("host_ms", ctypes.c_double), ("step_ms", ctypes.c_double), ("failed", ctypes.c_int64)]
+                ("host_ms", ctypes.c_double), ("step_ms", ctypes.c_double), ("failed", ctypes.c_int64),
+                ("rebuilds", ctypes.c_int64), ("guard_rebuilds", ctypes.c_int64)]
+
+
+class CMdOptions(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int32), ("dt_fs", ctypes.c_double), ("rebuild_every", ctypes.c_int32),
+                ("skin_guard", ctypes.c_int32), ("integrator", ctypes.c_int32), ("temperature_K", ctypes.c_double),
+                ("friction_per_fs", ctypes.c_double), ("seed", ctypes.c_uint64), ("step0", ctypes.c_uint64)]
+
+
+class CMdCounters(ctypes.Structure):
+    _fields_ = [("rebuilds", ctypes.c_int32), ("guard_rebuilds", ctypes.c_int32), ("graph_blocks", ctypes.c_int32),
+                ("max_displacement", ctypes.c_double)]
 
 
 class CSystem(ctypes.Structure):
@@ -115,6 +127,7 @@ def _load():
         "fnn_selftest_lookback": (I32, [P, I32, P]),
         "fnn_build_neighbors_static": (I32, [P, ctypes.c_double, P, P, P, I64, P, P]),
         "fnn_md_run": (I32, [P, P, P, P, P, I32, I32, ctypes.c_double, I32, P, P, P]),
+        "fnn_md_run_ex": (I32, [P, P, P, P, P, I32, P, P, P, P, P, P]),
         "fnn_serve_create": (I32, [P, P, ctypes.c_size_t, I32, I32]),
         "fnn_serve_submit": (I32, [P, P, P]),
         "fnn_serve_poll": (I32, [P, ctypes.c_uint64, P, I64]),
@@ -470,6 +483,29 @@ def md_run(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision:
                               int(n_steps), float(dt_fs), int(rebuild_every), _ptr(E_hist), _ptr(F), _stream(stream)),
                "fnn_md_run")
     return E_hist, F
+
+
+def md_run_ex(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision: str, n_steps: int, dt_fs: float,
+              rebuild_every: int = 10, integrator: str = "nve", temperature_K: float = 300.0,
+              friction_per_fs: float = 0.0, seed: int = 0, step0: int = 0, skin_guard: bool = True,
+              kinetic: bool = False, counters: bool = False, stream=None):
+    """fnn_md_run_ex: NVE velocity Verlet or BAOAB Langevin on the device, rebuilds on schedule and by the
+    skin guard; system.pos and vel ([N,4] float32) advance in place.  Returns (E_hist [n_steps, n_mol],
+    K_hist [n_steps, n_mol] or None, F [N,3] of the last evaluation, counters dict or None)."""
+    import torch
+    E_hist = torch.empty((n_steps, system.n_mol), dtype=torch.float64, device="cuda")
+    K_hist = torch.empty((n_steps, system.n_mol), dtype=torch.float64, device="cuda") if kinetic else None
+    F = torch.empty((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+    o = CMdOptions(int(n_steps), float(dt_fs), int(rebuild_every), int(bool(skin_guard)),
+                   {"nve": 0, "langevin": 1}[integrator], float(temperature_K), float(friction_per_fs), int(seed),
+                   int(step0))
+    c = CMdCounters()
+    cs = system.c()
+    ctx._check(lib.fnn_md_run_ex(ctx.h, ctypes.byref(cs), _ptr(system.pos), _ptr(vel), nl.h, PRECISION[precision],
+                                 ctypes.byref(o), _ptr(E_hist), _ptr(K_hist) if kinetic else None, _ptr(F),
+                                 ctypes.byref(c) if counters else None, _stream(stream)), "fnn_md_run_ex")
+    cnt = {f: getattr(c, f) for f, _ in CMdCounters._fields_} if counters else None
+    return E_hist, K_hist, F, cnt
 
 
 class Graph:

@@ -136,3 +136,102 @@ def test_serving_admission_budget_and_poll(fnn):
     with pytest.raises(fnn.FnnError):
         srv.submit(big, None, 1, 0.5)
     srv.close()
+
+
+def _md_ex(fnn, s, v0, M, precision, n, dt, skin, rebuild, side_stream=True, **kw):
+    """fnn_md_run_ex with counters and the kinetic history; on a side stream blocks run as graph replays."""
+    import torch
+    ctx = fnn.Context(M, skin=skin)
+    fnn.load_weights(ctx, weights(M))
+    ds = fnn.DeviceSystem.from_structures(s)
+    vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+    vel[:, :3] = torch.from_numpy(np.asarray(v0, np.float32))
+    vel = vel.cuda()
+    nl = fnn.NeighborList(ctx)
+    stream = torch.cuda.Stream() if side_stream else None
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+        E, K, F, cnt = fnn.md_run_ex(ctx, ds, vel, nl, precision, n, dt, rebuild, kinetic=True, counters=True,
+                                     stream=stream, **kw)
+    fnn.check(ctx, "md_run_ex", stream=stream)
+    return (E.cpu().numpy(), K.cpu().numpy(), ds.pos[:, :3].cpu().numpy(), vel[:, :3].cpu().numpy(),
+            F.cpu().numpy(), cnt)
+
+
+@pytest.mark.parametrize("name,M,precision,rebuild,graph", [("gas24", 1, "fp32", 1, False),
+                                                            ("water216", 1, "fp32x3", 5, True)])
+def test_langevin_matches_oracle_baoab(fnn, name, M, precision, rebuild, graph):
+    s = structure(name)
+    v0 = _velocities(s, 4)
+    n, dt, T, gamma, seed = 20, 0.5, 300.0, 0.02, 0x5eed_0001_0002
+    E, K, x, v, F, cnt = _md_ex(fnn, s, v0, M, precision, n, dt, 1.0, rebuild, graph, integrator="langevin",
+                                temperature_K=T, friction_per_fs=gamma, seed=seed, step0=1000)
+    Er, Kr, xr, vr, Fr = oracle.langevin_baoab(s, weights(M), v0, n, dt, T, gamma, seed, step0=1000)
+    assert np.abs(E - Er).max() / s.n_atoms <= E_TOL_PER_ATOM
+    assert np.abs(K - Kr).max() / s.n_atoms <= E_TOL_PER_ATOM
+    assert np.abs(x - xr).max() <= 1e-4 and np.abs(v - vr).max() <= 1e-5
+    assert np.abs(F - Fr).max() <= 1e-3
+    assert cnt["graph_blocks"] == ((n - rebuild) // rebuild if graph else 0)
+    # friction and noise did act: the trajectory differs from velocity Verlet's
+    Ev, xv, _, _ = oracle.velocity_verlet(s, weights(M), v0, n, dt)
+    assert np.abs(xv - xr).max() > 1e-3
+
+
+def test_skin_guard_rebuilds_inside_graph_blocks_and_matches_oracle(fnn):
+    s = structure("water216")
+    v0 = _velocities(s, 6)
+    n, dt, skin, rebuild = 40, 1.5, 0.3, 10
+    E, K, x, v, F, cnt = _md_ex(fnn, s, v0, 1, "fp32x3", n, dt, skin, rebuild, True)
+    # atoms move ~0.05 A per step: the 0.15 A half-skin is crossed within every block of 10 steps
+    assert cnt["graph_blocks"] == 3 and cnt["guard_rebuilds"] > 3
+    assert cnt["rebuilds"] > n // rebuild + 3
+    Er, xr, vr, Fr = oracle.velocity_verlet(s, weights(1), v0, n, dt)
+    assert np.abs(E[:, 0] - Er[:, 0]).max() / s.n_atoms <= E_TOL_PER_ATOM
+    assert np.abs(x - xr).max() <= 1e-4 and np.abs(F - Fr).max() <= 1e-3
+    assert abs(K[-1, 0] - oracle.kinetic_energies(s, vr)[0]) / s.n_atoms <= E_TOL_PER_ATOM
+
+
+def test_serving_skin_guard_matches_oracle(fnn):
+    s = structure("gas24")
+    v0 = _velocities(s, 8)
+    n, dt = 24, 1.5
+    ctx = fnn.Context(1, skin=0.2)
+    fnn.load_weights(ctx, weights(1))
+    srv = fnn.Server(ctx, 8 << 30, "fp32x3", rebuild_every=10)
+    r = srv.poll(srv.submit(s, v0, n, dt), timeout_s=120)
+    st = srv.stats()
+    srv.close()
+    assert st["guard_rebuilds"] > 0
+    Er, xr, vr, Fr = oracle.velocity_verlet(s, weights(1), v0, n, dt)
+    assert np.abs(r["energies"] - Er[:, 0]).max() / s.n_atoms <= E_TOL_PER_ATOM
+    assert np.abs(r["pos"] - xr).max() <= 1e-4
+
+
+def test_water_box_1000_steps_matches_oracle_every_100_steps(fnn):
+    """The periodic water box under NVE for 1000 steps of 0.5 fs (8-member ensemble, FP32X3, skin 1 A, list
+    rebuilt every 10 steps and by the guard): run as ten continued runs of 100 steps, the oracle evaluated
+    at the GPU's positions after each (energy per atom within 1e-4, forces within 1e-3)."""
+    import torch
+    s = structure("water216")
+    M = 8
+    ctx = fnn.Context(M, skin=1.0)
+    fnn.load_weights(ctx, weights(M))
+    ds = fnn.DeviceSystem.from_structures(s)
+    vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+    vel[:, :3] = torch.from_numpy(_velocities(s, 2))
+    vel = vel.cuda()
+    nl = fnn.NeighborList(ctx)
+    stream = torch.cuda.Stream()
+    worst_e = worst_f = 0.0
+    for chunk in range(10):
+        with torch.cuda.stream(stream):
+            # 101 evaluations: the first repeats the previous chunk's last position (no drift after it)
+            E, K, F, cnt = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", 101, 0.5, 10, kinetic=True, counters=True,
+                                         stream=stream)
+        fnn.check(ctx, "md chunk", stream=stream)
+        st = synth.Structures(s.Z, ds.pos[:, :3].cpu().numpy(), s.mol_offsets, s.cell, s.pbc)
+        r = oracle.energy_forces(st, weights(M))
+        worst_e = max(worst_e, abs(float(E[-1, 0]) - r.energy[0]) / s.n_atoms)
+        worst_f = max(worst_f, float(np.abs(F.cpu().numpy() - r.forces).max()))
+        assert cnt["graph_blocks"] == 9
+    assert worst_e <= E_TOL_PER_ATOM and worst_f <= 1e-3
