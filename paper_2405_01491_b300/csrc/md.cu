@@ -351,9 +351,36 @@ fnn_status md_step_eager(MdRun &r, cudaStream_t s, int *rebuilds) {
   return md_after(r, s);
 }
 
+// Streams and events of the rebuild bodies' captures.  The neighbour build forks work to the context's
+// side stream; by the second captured step that stream has joined the outer capture (through the energy
+// call), so a body capture borrowing it would tie one stream to two capture sequences.  Each body is
+// therefore captured with its own origin stream, side stream and fork/join events, swapped into the
+// context for the duration of the body capture.
+struct BodyCapture {
+  cudaStream_t origin = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool ok() const { return origin && side && ev_fork && ev_join; }
+  void create() {
+    if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess) origin = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) side = nullptr;
+    if (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) ev_fork = nullptr;
+    if (cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) ev_join = nullptr;
+    cudaGetLastError();
+  }
+  void destroy() {
+    if (origin) cudaStreamDestroy(origin);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    origin = side = nullptr;
+    ev_fork = ev_join = nullptr;
+  }
+};
+
 // One step captured: the decision kernel sets a conditional handle; an IF node holds the rebuild (captured
-// into its body on a helper stream); the rest follows the node.  Returns launches of the rebuild body.
-fnn_status md_step_capture(MdRun &r, cudaStream_t s, cudaStream_t body_stream, long long *body_launches) {
+// into its body from the BodyCapture streams); the rest follows the node.  *body_launches receives the
+// kernel launches of the rebuild body.
+fnn_status md_step_capture(MdRun &r, cudaStream_t s, BodyCapture &bc, long long *body_launches) {
   fnn_ctx *ctx = r.ctx;
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
@@ -369,22 +396,38 @@ fnn_status md_step_capture(MdRun &r, cudaStream_t s, cudaStream_t body_stream, l
   fnn_status st;
   if ((st = md_decide(r, s, h, 1))) return st;
   FNN_CUDA_TRY(ctx, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive || !g) {
+    ctx->last_error = "md step capture: capture ended";
+    return FNN_E_CUDA;
+  }
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeIf;
   cp.conditional.size = 1;
-  cudaGraphNode_t node;
+  cudaGraphNode_t node = nullptr;
   FNN_CUDA_TRY(ctx, cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  if (!node || !cp.conditional.phGraph_out || !cp.conditional.phGraph_out[0]) {
+    ctx->last_error = "md step capture: conditional node without a body graph";
+    return FNN_E_CUDA;
+  }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   FNN_CUDA_TRY(ctx, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-  FNN_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0,
+  FNN_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(bc.origin, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal));
+  const cudaStream_t side = ctx->side;
+  const cudaEvent_t ef = ctx->ev_fork, ej = ctx->ev_join;
+  ctx->side = bc.side;
+  ctx->ev_fork = bc.ev_fork;
+  ctx->ev_join = bc.ev_join;
   const long long l0 = ctx->prof.launches;
-  fnn_status bs = md_rebuild(r, body_stream);
+  fnn_status bs = md_rebuild(r, bc.origin);
   *body_launches = ctx->prof.launches - l0;
+  ctx->side = side;
+  ctx->ev_fork = ef;
+  ctx->ev_join = ej;
   cudaGraph_t out = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(body_stream, &out);
+  const cudaError_t ec = cudaStreamEndCapture(bc.origin, &out);
   if (bs) return bs;
   if (ec != cudaSuccess) {
     ctx->last_error = std::string("md rebuild body capture: ") + cudaGetErrorString(ec);
@@ -466,21 +509,20 @@ extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *
     ctx->prof.on = false;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t bs = nullptr;
+    BodyCapture bc;
+    bc.create();
     long long body_total = 0;
-    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess &&
-        cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    if (bc.ok() && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       fnn_status cs = FNN_OK;
       for (int j = 0; j < B && !cs; j++) {
         long long bl = 0;
-        cs = md_step_capture(r, s, bs, &bl);
+        cs = md_step_capture(r, s, bc, &bl);
         body_total += bl;
       }
       const cudaError_t ec = cudaStreamEndCapture(s, &g);
       if (cs || ec != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
     }
     cudaGetLastError();
-    if (bs) cudaStreamDestroy(bs);
     nl->stream = s;   // the capture recorded the rebuild on the helper stream, which is gone
     ctx->prof.on = prof;
     const long long per_block = ctx->prof.launches - l0 - body_total;   // without the rebuild bodies
@@ -501,6 +543,7 @@ extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *
       cudaGraphExecDestroy(exec);
     }
     if (g) cudaGraphDestroy(g);
+    bc.destroy();   // after the replays: the graph's bodies were recorded from these streams
   }
   // the rest eagerly (also every step when the stream cannot be captured)
   for (; k < n_steps && !st; k++) st = md_step_eager(r, s, &eager_rebuilds);
