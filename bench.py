@@ -302,6 +302,79 @@ def oracle_full(M: int = 8, min_seconds: float = 10.0, max_reps: int = 3):
     return entry, res
 
 
+# The oracle timed per configuration in a child process (so its thread count can be pinned): every
+# workload of the measurement plan, each a bounded sample, reported in atom-evals/s.
+_PLAN_CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import oracle
+from paper_2405_01491_b300 import synth
+one_core = sys.argv[2] == "1"
+out = {}
+def timed(f, min_s=1.0):
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f(); n += 1
+        if time.perf_counter() - t0 >= min_s: return (time.perf_counter() - t0) / n, n
+s = synth.gas24(); w1 = synth.xavier_weights(1)
+dt, n = timed(lambda: oracle.energy_forces(s, w1))
+out["gas24"] = {"atom_evals_per_s": s.n_atoms / dt, "sample": f"{n} evaluations, M=1"}
+s = synth.water216(); w8 = synth.xavier_weights(8); v = synth.maxwell_boltzmann(s.Z, 300.0, seed=2)
+t0 = time.perf_counter(); oracle.velocity_verlet(s, w8, v, 20, 0.5); dt = (time.perf_counter() - t0) / 20
+out["water216"] = {"atom_evals_per_s": s.n_atoms / dt, "ms_per_step": 1e3 * dt,
+                   "s_per_1000_steps": 1e3 * dt, "sample": "20 velocity-Verlet steps, M=8, extrapolated to 1000"}
+if one_core:   # a 1/8-volume box of the same density and composition (2,944 atoms): per-atom cost
+    s = synth.mix_box(2944, 62.2 / 2, seed=3)
+    sample = "2,944-atom periodic box (31.1 A, same density and composition), M=8, per atom"
+else:
+    s = synth.mix23558(); sample = "the 23,558-atom box, M=8"
+t0 = time.perf_counter(); oracle.energy_forces(s, w8); dt = time.perf_counter() - t0
+out["mix23558"] = {"atom_evals_per_s": s.n_atoms / dt, "sample": sample}
+b = synth.ragged_batch(); sub = synth.concat([b.molecule(m) for m in range(256)]); E, F = synth.batch_targets(sub)
+t0 = time.perf_counter(); oracle.loss_and_weight_grads(sub, w1, E, F); dt = time.perf_counter() - t0
+out["batch4096"] = {"atom_evals_per_s": sub.n_atoms / dt, "sample": f"256-molecule subset ({sub.n_atoms} atoms): "
+                    "energies, forces, loss and weight gradients, M=1, per atom"}
+pool = synth.request_pool(12, seed=5); reqs = [p for p in pool if p.n_atoms <= 4000][:6]
+t0 = time.perf_counter()
+for p in reqs: oracle.velocity_verlet(p, w1, np.zeros((p.n_atoms, 3)), 10, 0.5)
+dt = time.perf_counter() - t0
+out["serve"] = {"atom_evals_per_s": 10 * sum(p.n_atoms for p in reqs) / dt,
+                "sample": f"the first {len(reqs)} pool requests of at most 4000 atoms "
+                          f"({sum(p.n_atoms for p in reqs)} atoms), 10 velocity-Verlet steps each, M=1"}
+print(json.dumps(out))
+"""
+
+
+def cpu_model() -> str:
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_plan(timeout_s: float = 240.0) -> dict:
+    """The oracle on every configuration of the measurement plan, on all host cores and on one core."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    res = {"cpu_model": cpu_model(), "cores_all": cores}
+    for label, one in (("all_cores", False), ("one_core", True)):
+        env = dict(os.environ)
+        if one:
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+                env[k] = "1"
+        try:
+            r = subprocess.run([sys.executable, "-c", _PLAN_CHILD, ROOT, "1" if one else "0"], env=env,
+                               capture_output=True, text=True, timeout=timeout_s)
+            res[label] = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else \
+                {"error": (r.stderr or "")[-300:]}
+        except Exception as e:   # a slow host: the plan is context, not the measurement
+            res[label] = {"error": str(e)[:300]}
+    return res
+
+
 def arm_config(precision: str, list_entries, world: int = 1) -> dict:
     """The workload description both arms print."""
     return {"workload": WORKLOAD, "n_atoms": 23558, "members": 8, "precision": precision,
@@ -333,72 +406,144 @@ def run_reference(args):
     return 0
 
 
-def serve_bench(fnn, torch, synth, duration_s=2.0, rate_hz=2000.0, pool_n=128, budget=120 << 30, n_steps=10,
-                dt=0.5, one_requests=64):
-    """Serving stream: Poisson arrivals of structures with log-uniform sizes 8..20000 atoms (periodic above 500),
-    each 10 velocity-Verlet steps, one ensemble member; BF16 served form with continuous batching under an HBM
-    budget, against the FP32-accurate form run batch-of-one (each request alone, sequentially)."""
+def _fifo_latencies(arrivals, services):
+    """Completion - arrival of a single first-in first-out server: c_k = max(a_k, c_{k-1}) + s_k."""
+    import numpy as np
+    c, out = 0.0, []
+    for a, sv in zip(arrivals, services):
+        c = max(a, c) + sv
+        out.append(c - a)
+    return np.array(out)
+
+
+def _served_stream(fnn, srv, pool, vels, stream, n_steps, dt):
+    """Submit an open-loop arrival stream (busy-waiting on each arrival time) while draining finished
+    tickets, then wait for the rest.  Returns (latencies ms, wall s)."""
+    import collections
+    import numpy as np
+    t0 = time.perf_counter()
+    outstanding = collections.deque()
+    lat = []
+    for t_arr, k in stream:
+        while time.perf_counter() - t0 < t_arr:
+            if outstanding:
+                r = srv.poll(outstanding[0], timeout_s=0.0, arrays=False)
+                if r is not None:
+                    lat.append(r["latency_ms"])
+                    outstanding.popleft()
+        outstanding.append(srv.submit(pool[k], vels[k], n_steps, dt))
+    while outstanding:
+        r = srv.poll(outstanding.popleft(), timeout_s=600, arrays=False)
+        lat.append(r["latency_ms"])
+    return np.array(lat), time.perf_counter() - t0
+
+
+def _batch_of_one(fnn, torch, pool, vels, stream, n_steps, dt, budget_s, w1):
+    """Each request alone on the GPU (FP32X3, fnn_md_run_ex), in arrival order: service time = host copy of the
+    request in, the 10 steps, the result copied out; latencies of a first-in first-out server over the same
+    arrivals follow from the measured service times.  Stops after budget_s seconds of service."""
+    import numpy as np
+    ctx = fnn.Context(1, skin=1.0)
+    fnn.load_weights(ctx, w1)
+    nl = fnn.NeighborList(ctx)
+    side = torch.cuda.Stream()
+    arr, svc, evals = [], [], 0
+    for idx, (t_arr, k) in enumerate(stream):
+        s = pool[k]
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        with torch.cuda.stream(side):
+            ds = fnn.DeviceSystem.from_structures(s)
+            vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+            vel[:, :3] = torch.from_numpy(vels[k])
+            vel = vel.cuda()
+            E, _, F, _ = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", n_steps, dt, 10, stream=side)
+            res = (E.cpu(), ds.pos.cpu(), vel.cpu(), F.cpu())
+        fnn.check(ctx, "batch-of-one", stream=side)
+        sv = time.perf_counter() - ta
+        if idx > 0:   # the first call carries one-time set-up
+            arr.append(t_arr)
+            svc.append(sv)
+            evals += s.n_atoms * n_steps
+        if sum(svc) >= budget_s:
+            break
+    del res
+    return np.array(arr), np.array(svc), evals
+
+
+def serve_bench(fnn, torch, synth, duration_s=60.0, rate_hz=2000.0, pool_n=4096, budget=120 << 30, n_steps=10,
+                dt=0.5, one_budget_s=20.0, matched_s=20.0):
+    """Serving stream: Poisson arrivals at rate_hz for duration_s of structures drawn from a pool of pool_n
+    (log-uniform sizes 8..20000 atoms, periodic above 500), each 10 velocity-Verlet steps, one ensemble member;
+    BF16 served form with continuous batching under an HBM budget.  Against it, the FP32-accurate form run
+    batch-of-one under the same arrivals (a first-in first-out queue in front of one request at a time), and
+    both forms at a matched load that batch-of-one sustains."""
     import numpy as np
     w1 = synth.xavier_weights(1)
-    pool = synth.request_pool(pool_n, seed=5)
+    workers = max(1, min(32, (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 4)))
+    t_pool = time.perf_counter()
+    pool = synth.request_pool(pool_n, seed=5, workers=workers)
     vels = [synth.maxwell_boltzmann(p.Z, 300.0, seed=k) for k, p in enumerate(pool)]
+    t_pool = time.perf_counter() - t_pool
     rng = np.random.Generator(np.random.PCG64([5, 2]))
-    stream, t = [], 0.0
-    while True:
-        t += rng.exponential(1.0 / rate_hz)
-        if t >= duration_s:
-            break
-        stream.append((t, int(rng.integers(pool_n))))
+
+    def poisson(rate, T):
+        out, t = [], 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t >= T:
+                return out
+            out.append((t, int(rng.integers(pool_n))))
+
+    stream = poisson(rate_hz, duration_s)
     ctx = fnn.Context(1, skin=1.0)
     fnn.load_weights(ctx, w1)
     srv = fnn.Server(ctx, budget, "bf16", rebuild_every=10)
     for k in range(4):                                   # warm-up (allocations, first launches)
-        srv.poll(srv.submit(pool[k], vels[k], n_steps, dt), timeout_s=300)
-    t0 = time.perf_counter()
-    tickets = []
-    for t_arr, k in stream:
-        while time.perf_counter() - t0 < t_arr:
-            pass
-        tickets.append((srv.submit(pool[k], vels[k], n_steps, dt), k))
-    res = [(srv.poll(tk, timeout_s=600), k) for tk, k in tickets]
-    wall = time.perf_counter() - t0
+        srv.poll(srv.submit(pool[k], vels[k], n_steps, dt), timeout_s=300, arrays=False)
+    st0 = srv.stats()
+    lat, wall = _served_stream(fnn, srv, pool, vels, stream, n_steps, dt)
     st = srv.stats()
-    srv.close()
-    lat = np.array([r["latency_ms"] for r, _ in res if r is not None])
     evals = sum(pool[k].n_atoms * n_steps for _, k in stream)
     out = {"requests": len(stream), "completed": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "atom_evals_per_s": evals / wall,
            "offered_atom_evals_per_s": evals / duration_s, "arrival_window_s": duration_s, "wall_s": wall,
            "rate_hz": rate_hz, "members": 1, "precision": "bf16", "max_batch_atoms": st["max_batch_atoms"],
-           "batch_steps": st["batch_steps"], "mean_atoms": float(np.mean([pool[k].n_atoms for _, k in stream])),
-           "pool": f"{pool_n} structures, n = round(exp(U(ln 8, ln 20000))), periodic above 500 atoms, seed 5",
-           "budget_bytes": budget, "status": st["status"], "scheduler_host_ms": st["host_ms"],
-           "scheduler_step_ms": st["step_ms"]}
-    # batch-of-one FP32 form: the first requests of the same stream, each alone
-    ctx1 = fnn.Context(1, skin=1.0)
-    fnn.load_weights(ctx1, w1)
-    one = []
-    evals1 = 0
-    t_all = 0.0
-    for _, k in stream[:one_requests]:
-        s = pool[k]
-        ds = fnn.DeviceSystem.from_structures(s)
-        vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
-        vel[:, :3] = torch.from_numpy(vels[k])
-        vel = vel.cuda()
-        nl = fnn.NeighborList(ctx1)
-        torch.cuda.synchronize()
-        ta = time.perf_counter()
-        fnn.md_run(ctx1, ds, vel, nl, "fp32x3", n_steps, dt, 10)
-        fnn.check(ctx1, "batch-of-one")
-        dt_req = time.perf_counter() - ta
-        one.append(1e3 * dt_req)
-        t_all += dt_req
-        evals1 += s.n_atoms * n_steps
-    one = np.array(one[1:] if len(one) > 1 else one)   # the first call carries one-time set-up
-    out["batch_of_one"] = {"precision": "fp32x3", "requests": len(one), "p50_ms": float(np.percentile(one, 50)),
-                           "p99_ms": float(np.percentile(one, 99)), "atom_evals_per_s": evals1 / t_all,
-                           "note": "each request alone on the GPU, no queueing, sequential"}
+           "batch_steps": st["batch_steps"] - st0["batch_steps"],
+           "mean_atoms": float(np.mean([pool[k].n_atoms for _, k in stream])),
+           "pool": f"{pool_n} structures, n = round(exp(U(ln 8, ln 20000))), periodic above 500 atoms, seed 5 "
+                   f"(built in {t_pool:.0f} s by {workers} processes)",
+           "budget_bytes": budget, "status": st["status"], "scheduler_host_ms": st["host_ms"] - st0["host_ms"],
+           "scheduler_step_ms": st["step_ms"] - st0["step_ms"], "rebuilds": st["rebuilds"] - st0["rebuilds"],
+           "guard_rebuilds": st["guard_rebuilds"] - st0["guard_rebuilds"]}
+    # batch-of-one FP32X3 under the same arrivals (the first one_budget_s seconds of service)
+    arr, svc, ev1 = _batch_of_one(fnn, torch, pool, vels, stream, n_steps, dt, one_budget_s, w1)
+    l1 = 1e3 * _fifo_latencies(arr, svc)
+    cap_hz = len(svc) / svc.sum()
+    out["batch_of_one"] = {
+        "precision": "fp32x3", "requests": int(len(svc)), "arrival_window_s": float(arr[-1]),
+        "p50_ms": float(np.percentile(l1, 50)), "p99_ms": float(np.percentile(l1, 99)),
+        "service_p50_ms": float(1e3 * np.percentile(svc, 50)), "saturation_rate_hz": cap_hz,
+        "saturation_atom_evals_per_s": ev1 / svc.sum(),
+        "note": "same arrivals, one request at a time (first in, first out; host copies in the service time); the "
+                f"offered {rate_hz:.0f} req/s exceeds what it completes ({cap_hz:.0f} req/s), so its queue grows "
+                "for as long as the stream lasts: latencies are over the first arrival_window_s seconds"}
+    # matched load: both forms at half of batch-of-one's saturation rate
+    r_m = 0.5 * cap_hz
+    mstream = poisson(r_m, matched_s)
+    lat_m, wall_m = _served_stream(fnn, srv, pool, vels, mstream, n_steps, dt)
+    arr_m, svc_m, ev_m = _batch_of_one(fnn, torch, pool, vels, mstream, n_steps, dt, 1e9, w1)
+    l1m = 1e3 * _fifo_latencies(arr_m, svc_m)
+    ev_served = sum(pool[k].n_atoms * n_steps for _, k in mstream)
+    out["matched_load"] = {"rate_hz": r_m, "arrival_window_s": matched_s, "requests": len(mstream),
+                           "served_bf16": {"p50_ms": float(np.percentile(lat_m, 50)),
+                                           "p99_ms": float(np.percentile(lat_m, 99)),
+                                           "atom_evals_per_s": ev_served / wall_m},
+                           "batch_of_one_fp32x3": {"p50_ms": float(np.percentile(l1m, 50)),
+                                                   "p99_ms": float(np.percentile(l1m, 99)),
+                                                   "atom_evals_per_s": ev_m / max(arr_m[-1] if len(arr_m) else 1,
+                                                                                 svc_m.sum())}}
+    srv.close()
     return out
 
 
@@ -498,37 +643,119 @@ def latency_bench(fnn, torch, synth, reps: int = 200):
     return out
 
 
-def md_bench(fnn, torch, synth, n_steps: int = 1000, M: int = 8):
-    """The periodic water box (216 H2O, 648 atoms) under NVE velocity Verlet: n_steps force evaluations
-    at 0.5 fs, 8-member ensemble, FP32X3 networks, list skin 1 A rebuilt every 10 steps, Maxwell-Boltzmann
-    velocities at 300 K; fnn_md_run on a side stream (10-step blocks as CUDA-graph replays)."""
+def md_bench(fnn, torch, synth, n_steps: int = 1000, M: int = 8, check: bool = True):
+    """The periodic water box (216 H2O, 648 atoms) under NVE velocity Verlet: n_steps force evaluations at
+    0.5 fs, 8-member ensemble, FP32X3 networks, list skin 1 A rebuilt every 10 steps and by the skin/2 guard,
+    Maxwell-Boltzmann velocities at 300 K; fnn_md_run_ex on a side stream (10-step blocks as CUDA-graph
+    replays with conditional rebuilds).  Then the same run in ten continued pieces of 100 steps, the oracle
+    evaluated at the GPU positions after each (energy per atom, forces)."""
+    import numpy as np
     s = synth.water216()
     ctx = fnn.Context(M, skin=1.0)
-    fnn.load_weights(ctx, synth.xavier_weights(M))
-    ds = fnn.DeviceSystem.from_structures(s)
-    vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
-    vel[:, :3] = torch.from_numpy(synth.maxwell_boltzmann(s.Z, 300.0, seed=2))
-    vel = vel.cuda()
+    w = synth.xavier_weights(M)
+    fnn.load_weights(ctx, w)
+    v0 = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+    v0[:, :3] = torch.from_numpy(synth.maxwell_boltzmann(s.Z, 300.0, seed=2))
     nl = fnn.NeighborList(ctx)
     stream = torch.cuda.Stream()
+
+    def fresh():
+        return fnn.DeviceSystem.from_structures(s), v0.clone().cuda()
+
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        fnn.md_run(ctx, ds, vel.clone(), nl, "fp32x3", 20, 0.5, 10, stream=stream)   # warm-up (sizes, graphs)
+        ds, vel = fresh()
+        fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", 20, 0.5, 10, stream=stream)   # warm-up (sizes, graphs)
         fnn.check(ctx, "md warm-up", stream=stream)
+        ds, vel = fresh()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = fnn.launch_count(ctx)
         a.record(stream)
-        E, F = fnn.md_run(ctx, ds, vel, nl, "fp32x3", n_steps, 0.5, 10, stream=stream)
+        E, K, F, cnt = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", n_steps, 0.5, 10, kinetic=True, stream=stream)
         b.record(stream)
         torch.cuda.synchronize()
         fnn.check(ctx, "md", stream=stream)
     ms = a.elapsed_time(b)
-    E = E.cpu().numpy()[:, 0]
-    return {"workload": "water216: 216 rigid H2O (648 atoms), 18.64 A periodic cube, seed 2", "members": M,
-            "precision": "fp32x3", "steps": n_steps, "dt_fs": 0.5, "rebuild_every": 10, "skin_A": 1.0,
-            "ms_total": ms, "ms_per_step": ms / n_steps, "atom_evals_per_s": s.n_atoms * n_steps / (ms * 1e-3),
-            "gpu_launches_per_step": (fnn.launch_count(ctx) - l0) / n_steps,
-            "energy_first_last": [float(E[0]), float(E[-1])]}
+    launches = fnn.launch_count(ctx) - l0
+    Ep, Kk = E.cpu().numpy()[:, 0], K.cpu().numpy()[:, 0]
+    Et = Ep + Kk
+    out = {"workload": "water216: 216 rigid H2O (648 atoms), 18.64 A periodic cube, seed 2", "members": M,
+           "precision": "fp32x3", "steps": n_steps, "dt_fs": 0.5, "rebuild_every": 10, "skin_A": 1.0,
+           "skin_guard": True, "ms_total": ms, "ms_per_step": ms / n_steps,
+           "atom_evals_per_s": s.n_atoms * n_steps / (ms * 1e-3), "gpu_launches_per_step": launches / n_steps,
+           "potential_first_last": [float(Ep[0]), float(Ep[-1])], "kinetic_first_last": [float(Kk[0]), float(Kk[-1])],
+           "total_first_last": [float(Et[0]), float(Et[-1])],
+           "total_drift_per_atom": float((Et[-1] - Et[0]) / s.n_atoms)}
+    if check:
+        import oracle
+        ds, vel = fresh()
+        worst_e = worst_f = 0.0
+        guard = rebuilds = 0
+        for chunk in range(n_steps // 100):
+            with torch.cuda.stream(stream):
+                Ec, _, Fc, c = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", 101, 0.5, 10, counters=True, stream=stream)
+            fnn.check(ctx, "md snapshot run", stream=stream)
+            guard += c["guard_rebuilds"]
+            rebuilds += c["rebuilds"]
+            st = synth.Structures(s.Z, ds.pos[:, :3].cpu().numpy(), s.mol_offsets, s.cell, s.pbc)
+            r = oracle.energy_forces(st, w)
+            worst_e = max(worst_e, abs(float(Ec[-1, 0]) - r.energy[0]) / s.n_atoms)
+            worst_f = max(worst_f, float(np.abs(Fc.cpu().numpy() - r.forces).max()))
+        out["oracle_snapshots"] = {"every_steps": 100, "count": n_steps // 100, "max_dE_per_atom": worst_e,
+                                   "max_dF": worst_f, "rebuilds": rebuilds, "guard_rebuilds": guard,
+                                   "note": "the run in ten continued pieces of 100 steps; the oracle evaluated at "
+                                           "the GPU positions after each"}
+    return out
+
+
+def drift_bench(fnn, torch, synth, forms=("fp32", "fp32x3", "bf16", "fp8"), n_steps=4000, dt=0.1, M=1):
+    """Energy conservation by precision form (section V.E: FP32 conserves the total energy in NVE, BF16 and
+    TF32 matmuls do not): the water box under NVE at 0.1 fs for n_steps, one member (the paper's ANI-2x
+    member 0), skin 1 A with the guard; total energy = potential + kinetic per step.  Reported per form: the
+    linear drift (kcal/mol per ps per atom), the spread about it and the largest excursion from the start
+    (kcal/mol per atom).  Then a Langevin (BAOAB) run at 300 K: its mean kinetic temperature."""
+    import numpy as np
+    s = synth.water216()
+    w = synth.xavier_weights(M)
+    v0 = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+    v0[:, :3] = torch.from_numpy(synth.maxwell_boltzmann(s.Z, 300.0, seed=2))
+    stream = torch.cuda.Stream()
+    out = {"workload": "water216, NVE velocity Verlet", "dt_fs": dt, "steps": n_steps, "members": M, "forms": {}}
+    t_ps = np.arange(n_steps) * dt * 1e-3
+    for form in forms:
+        ctx = fnn.Context(M, skin=1.0)
+        fnn.load_weights(ctx, w)
+        nl = fnn.NeighborList(ctx)
+        ds = fnn.DeviceSystem.from_structures(s)
+        vel = v0.clone().cuda()
+        with torch.cuda.stream(stream):
+            E, K, _, cnt = fnn.md_run_ex(ctx, ds, vel, nl, form, n_steps, dt, 10, kinetic=True, counters=True,
+                                         stream=stream)
+        fnn.check(ctx, f"drift {form}", stream=stream)
+        Et = (E.cpu().numpy()[:, 0] + K.cpu().numpy()[:, 0]) / s.n_atoms
+        slope, icpt = np.polyfit(t_ps, Et, 1)
+        out["forms"][form] = {"drift_per_atom_per_ps": float(slope), "spread_per_atom": float(np.std(Et - (slope * t_ps + icpt))),
+                              "max_excursion_per_atom": float(np.abs(Et - Et[0]).max()),
+                              "kinetic_per_atom_mean": float(K.cpu().numpy()[:, 0].mean() / s.n_atoms),
+                              "rebuilds": cnt["rebuilds"], "guard_rebuilds": cnt["guard_rebuilds"]}
+    ctx = fnn.Context(M, skin=1.0)
+    fnn.load_weights(ctx, w)
+    nl = fnn.NeighborList(ctx)
+    ds = fnn.DeviceSystem.from_structures(s)
+    vel = v0.clone().cuda()
+    n_l, dt_l, gamma = 4000, 0.5, 0.01
+    with torch.cuda.stream(stream):
+        E, K, _, cnt = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", n_l, dt_l, 10, integrator="langevin",
+                                     temperature_K=300.0, friction_per_fs=gamma, seed=2405, kinetic=True,
+                                     counters=True, stream=stream)
+    fnn.check(ctx, "langevin", stream=stream)
+    Kk = K.cpu().numpy()[:, 0]
+    kb = 0.0019872041
+    out["langevin"] = {"integrator": "BAOAB", "T_bath_K": 300.0, "friction_per_fs": gamma, "dt_fs": dt_l,
+                       "steps": n_l, "T_kinetic_mean_K_second_half": float(2 * Kk[n_l // 2:].mean() / (3 * s.n_atoms * kb)),
+                       "rebuilds": cnt["rebuilds"], "guard_rebuilds": cnt["guard_rebuilds"]}
+    return out
 
 
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
@@ -630,7 +857,10 @@ def main():
     ap.add_argument("--no-md", action="store_true", help="skip the water-box MD measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-pool", type=int, default=4096)
+    ap.add_argument("--no-drift", action="store_true", help="skip the energy-drift study")
+    ap.add_argument("--no-cpu-plan", action="store_true", help="skip the oracle timings of every configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -688,13 +918,18 @@ def main():
     base, ref = (None, None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, ref = oracle_full(M)
+    plan = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_cpu_plan:
+        plan = cpu_plan()
     serve = None
     if world == 1 and not args.no_serve:
-        serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds)
-    md = latency = None
+        serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds, pool_n=args.serve_pool)
+    md = latency = drift = None
     if world == 1 and not args.no_md:
         md = md_bench(fnn, torch, synth)
         latency = latency_bench(fnn, torch, synth)
+    if world == 1 and not args.no_drift:
+        drift = drift_bench(fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
         train = {p: train_bench(fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
@@ -726,6 +961,8 @@ def main():
             "clocks": head["clocks"], "forms": form_report, "kernels": kernels, "source_digest": source_digest()}
     if base is not None:
         line["cpu_baseline"] = base
+        if plan is not None:
+            line["cpu_baseline"]["plan"] = plan
     if serve is not None:
         line["serve"] = serve
     if train is not None:
@@ -734,6 +971,8 @@ def main():
         line["md"] = md
     if latency is not None:
         line["latency"] = latency
+    if drift is not None:
+        line["drift"] = drift
     if rank == 0:
         print(json.dumps(line), flush=True)
     ranks.close()

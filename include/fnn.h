@@ -83,7 +83,15 @@ typedef struct {
   double shift_ang0;  /* first angular radial shift, A (0.8); shifts shift_ang0 + m (rc_ang - shift_ang0) / 8 */
   double skin;        /* neighbour-list skin, A; list radius = rc_rad + skin (0 = exact list) */
   int32_t n_members;  /* ensemble size M, 1..8; the energy is the member average */
+  int32_t switch_kind;/* switching function of both cutoffs (section II.A), fnn_switch; 0 = cosine */
+  double switch_p;    /* exponent p of the polynomial envelope (> 0; 6 by default) */
 } fnn_config;
+
+/* Switching functions f(r) for r < rc (0 from rc on), d = r / rc (section II.A processing modules):
+ *   FNN_SWITCH_COSINE       cos(pi d) / 2 + 1/2                                   (ANI)
+ *   FNN_SWITCH_POLYNOMIAL   1 - (p+1)(p+2)/2 d^p + p(p+2) d^(p+1) - p(p+1)/2 d^(p+2)  (Gasteiger et al. 2020)
+ *   FNN_SWITCH_EXPONENTIAL  exp(-r^2 / ((rc - r)(rc + r)))                        (SpookyNet) */
+typedef enum { FNN_SWITCH_COSINE = 0, FNN_SWITCH_POLYNOMIAL = 1, FNN_SWITCH_EXPONENTIAL = 2 } fnn_switch;
 
 /* Network parameters, float32, host memory, row-major W[out][in]:
  * W1 [M][7][256][1008], b1 [M][7][256], W2 [M][7][192][256], b2 [M][7][192],
@@ -104,11 +112,12 @@ typedef struct {
   const uint8_t *pbc;         /* [n_mol] 1 = periodic, or NULL = none periodic */
 } fnn_system;
 
-/* Fill *cfg with the ANI-2x constants, skin 0 and M = 1. */
+/* Fill *cfg with the ANI-2x constants, skin 0, M = 1 and the cosine switch (p = 6). */
 void fnn_config_default(fnn_config *cfg);
 
 /* Create a context on the current CUDA device.  Returns FNN_E_INVALID for
- * out-of-range constants (cutoffs <= 0, rc_ang > rc_rad, M outside 1..8). */
+ * out-of-range constants (cutoffs <= 0, rc_ang > rc_rad, M outside 1..8, an unknown
+ * switch_kind, switch_p <= 0). */
 fnn_status fnn_create(fnn_ctx **ctx, const fnn_config *cfg);
 fnn_status fnn_destroy(fnn_ctx *ctx);
 
@@ -158,7 +167,8 @@ fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t *nbr, int8_
  * 1/4 exp(-eta_rad (r - R_k)^2) fc(r); angular slot 112 + p*32 + m*4 + s = sum
  * over unordered neighbour pairs {j,k} within rc_ang with element pair p of
  * 2 ((1 + cos(theta' - theta_s))/2)^zeta exp(-eta_ang ((r_ij + r_ik)/2 - A_m)^2)
- * fc(r_ij) fc(r_ik), theta' = acos(0.95 cos theta_ijk); fc(r) = cos(pi r/rc)/2 + 1/2.
+ * fc(r_ij) fc(r_ik), theta' = acos(0.95 cos theta_ijk); fc the context's switching function
+ * (cos(pi r/rc)/2 + 1/2 by default) with the cutoff of the term.
  * Asynchronous. */
 fnn_status fnn_aev(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *aev, void *stream);
 

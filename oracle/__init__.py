@@ -59,10 +59,16 @@ class Params:
     zeta: float = 14.1
     shf_r0: float = 0.8
     shf_a0: float = 0.8
+    switch: str = "cosine"   # switching function (section II.A): "cosine", "polynomial" or "exponential"
+    switch_p: float = 6.0    # exponent of the polynomial envelope
+
+
+SWITCH_KIND = {"cosine": 0, "polynomial": 1, "exponential": 2}
 
 
 class _CParams(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta", "shf_r0", "shf_a0")]
+    _fields_ = [(n, ctypes.c_double) for n in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta", "shf_r0", "shf_a0",
+                                               "sw_kind", "sw_p")]
 
 
 class _CGraph(ctypes.Structure):
@@ -99,6 +105,9 @@ def lib():
         _lib.oracle_aev.argtypes = [ctypes.c_void_p] * 3
         _lib.oracle_aev_vjp.argtypes = [ctypes.c_void_p] * 5
         _lib.oracle_aev_jvp.argtypes = [ctypes.c_void_p] * 4
+        _lib.oracle_switch.restype = None
+        _lib.oracle_switch.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p]
     return _lib
 
 
@@ -147,8 +156,19 @@ class Graph:
         Z, pos, mo, cell, pbc = self.arrays
         self.c = _CGraph(s.n_atoms, s.n_mol, _p(mo), _p(Z), _p(pos), _p(cell), _p(pbc),
                          self.ei.shape[0], _p(self.ei), _p(self.ej), _p(self.es))
-        self.cp = _CParams(*(getattr(params, f) for f in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta",
-                                                          "shf_r0", "shf_a0")))
+        self.cp = _c_params(params)
+
+
+def _c_params(params: Params) -> _CParams:
+    return _CParams(*(getattr(params, f) for f in ("rc_rad", "rc_ang", "eta_r", "eta_a", "zeta", "shf_r0", "shf_a0")),
+                    float(SWITCH_KIND[params.switch]), float(params.switch_p))
+
+
+def switch(r: float, rc: float, params: Params = Params()):
+    """The switching function of params at distance r for cutoff rc: (value, derivative)."""
+    f, df = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_switch(ctypes.byref(_c_params(params)), float(r), float(rc), ctypes.byref(f), ctypes.byref(df))
+    return f.value, df.value
 
 
 def _check(rc: int, what: str):

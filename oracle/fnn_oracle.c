@@ -51,6 +51,8 @@ typedef struct {
   double rc_rad, rc_ang;     /* cutoffs, A */
   double eta_r, eta_a, zeta; /* Gaussian widths and angular exponent */
   double shf_r0, shf_a0;     /* first radial / angular-radial shift, A */
+  double sw_kind;            /* switching function: 0 cosine, 1 polynomial envelope, 2 exponential */
+  double sw_p;               /* exponent p of the polynomial envelope */
 } oracle_params;
 
 static const double PI = 3.14159265358979323846;
@@ -69,9 +71,51 @@ static int pair_index(int a, int b) {
   return a * NE - a * (a - 1) / 2 + (b - a);
 }
 
-/* cosine switching function and its derivative (section II.A processing modules) */
-static double fcut(double r, double rc) { return r < rc ? 0.5 * cos(PI * r / rc) + 0.5 : 0.0; }
-static double dfcut(double r, double rc) { return r < rc ? -0.5 * PI / rc * sin(PI * r / rc) : 0.0; }
+/*
+ * Switching functions and their derivatives (section II.A processing modules: the cosine function of
+ * the ANI models, the polynomial envelope of Gasteiger et al. 2020 and the exponential function of
+ * SpookyNet), all 0 from the cutoff on:
+ *   cosine:       f = cos(pi r / rc) / 2 + 1/2
+ *   polynomial:   f = 1 - (p+1)(p+2)/2 d^p + p(p+2) d^(p+1) - p(p+1)/2 d^(p+2),  d = r / rc
+ *   exponential:  f = exp(-r^2 / ((rc - r)(rc + r)))
+ */
+static int g_sw_kind = 0;     /* set from the parameters at each entry point */
+static double g_sw_p = 6.0;
+static void set_switch(const void *params) {
+  const oracle_params *P = (const oracle_params *)params;
+  g_sw_kind = (int)P->sw_kind;
+  g_sw_p = P->sw_p;
+}
+static double fcut(double r, double rc) {
+  if (!(r < rc)) return 0.0;
+  if (g_sw_kind == 1) {
+    double p = g_sw_p, d = r / rc;
+    return 1.0 - 0.5 * (p + 1.0) * (p + 2.0) * pow(d, p) + p * (p + 2.0) * pow(d, p + 1.0) -
+           0.5 * p * (p + 1.0) * pow(d, p + 2.0);
+  }
+  if (g_sw_kind == 2) return exp(-r * r / ((rc - r) * (rc + r)));
+  return 0.5 * cos(PI * r / rc) + 0.5;
+}
+static double dfcut(double r, double rc) {
+  if (!(r < rc)) return 0.0;
+  if (g_sw_kind == 1) {
+    double p = g_sw_p, d = r / rc;
+    return (-0.5 * p * (p + 1.0) * (p + 2.0) * pow(d, p - 1.0) + p * (p + 1.0) * (p + 2.0) * pow(d, p) -
+            0.5 * p * (p + 1.0) * (p + 2.0) * pow(d, p + 1.0)) / rc;
+  }
+  if (g_sw_kind == 2) {
+    double q = (rc - r) * (rc + r);
+    return -exp(-r * r / q) * 2.0 * r * rc * rc / (q * q);
+  }
+  return -0.5 * PI / rc * sin(PI * r / rc);
+}
+
+/* the switching function of the given parameters at r (value and derivative), for the pins */
+void oracle_switch(const void *params, double r, double rc, double *f, double *df) {
+  set_switch(params);
+  *f = fcut(r, rc);
+  *df = dfcut(r, rc);
+}
 
 static int box_of(const double *cell, const uint8_t *pbc, int m, double L[3]) {
   if (!pbc || !pbc[m] || !cell) { L[0] = L[1] = L[2] = 0.0; return 0; }
@@ -251,6 +295,7 @@ static int angular_list(const oracle_graph *g, const oracle_params *P, const int
 
 /* Returns 0, or -2 when a species is outside the element table. */
 int oracle_aev(const oracle_graph *g, const oracle_params *P, double *aev) {
+  set_switch(P);
   int overflow = 0;
   for (int i = 0; i < g->n_atoms; i++) if (oracle_element(g->Z[i]) < 0) return -2;
   int32_t *am = make_atom_mol(g);
@@ -298,6 +343,7 @@ int oracle_aev(const oracle_graph *g, const oracle_params *P, double *aev) {
  * Per-edge gradients are formed per centre atom, then scattered serially.
  */
 int oracle_aev_vjp(const oracle_graph *g, const oracle_params *P, const double *G, double *grad, double *virial) {
+  set_switch(P);
   int overflow = 0;
   for (int i = 0; i < g->n_atoms; i++) if (oracle_element(g->Z[i]) < 0) return -2;
   int32_t *am = make_atom_mol(g);
@@ -374,6 +420,7 @@ int oracle_aev_vjp(const oracle_graph *g, const oracle_params *P, const double *
  * weight gradient: d/dtheta <T, dE/dAEV(theta)>.
  */
 int oracle_aev_jvp(const oracle_graph *g, const oracle_params *P, const double *V, double *T_out) {
+  set_switch(P);
   int overflow = 0;
   for (int i = 0; i < g->n_atoms; i++) if (oracle_element(g->Z[i]) < 0) return -2;
   int32_t *am = make_atom_mol(g);

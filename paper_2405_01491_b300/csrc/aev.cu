@@ -133,15 +133,15 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   auto put = [&](int pr, int pa, int j, float dx, float dy, float dz, float r, int e) {
     if (pr >= 0) {
       S.rd[pr] = make_float4(dx, dy, dz, r);
-      S.rfc[pr] = 0.5f * cospif(r * P.inv_rc_rad) + 0.5f;
+      S.rfc[pr] = switch_f(P, r, P.rc_rad, P.inv_rc_rad);
       if constexpr (FULL) S.rj[pr] = j;
       S.re[pr] = (unsigned char)e;
     }
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
       S.ae[pa] = (unsigned char)e;
-      S.afc[pa] = 0.5f * cospif(r * P.inv_rc_ang) + 0.5f;
-      if constexpr (FULL) S.adfc[pa] = -0.5f * P.pi_rc_ang * sinpif(r * P.inv_rc_ang);
+      S.afc[pa] = switch_f(P, r, P.rc_ang, P.inv_rc_ang);
+      if constexpr (FULL) S.adfc[pa] = switch_df(P, r, P.rc_ang, P.inv_rc_ang, P.pi_rc_ang);
     }
   };
 #pragma unroll
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
       float r = d.w;
       int e = S.re[t];
       float fc = S.rfc[t];
-      float dfc = -0.5f * P.pi_rc_rad * sinpif(r * P.inv_rc_rad);
+      float dfc = switch_df(P, r, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
       float dEdr = 0.f;
 #pragma unroll
       for (int k = 0; k < NSR; k++) {
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       const float vx = A.V[3 * (size_t)j] - vix, vy = A.V[3 * (size_t)j + 1] - viy, vz = A.V[3 * (size_t)j + 2] - viz;
       const float rdot = (d.x * vx + d.y * vy + d.z * vz) * rcp_fast(d.w);
       W.rv[t] = make_float4(vx, vy, vz, rdot);
-      const float dfc = -0.5f * P.pi_rc_rad * sinpif(d.w * P.inv_rc_rad);
+      const float dfc = switch_df(P, d.w, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
       W.rt[t] = make_float2(S.rfc[t] * rdot, dfc * rdot);
     }
     __syncwarp();

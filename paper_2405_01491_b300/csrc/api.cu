@@ -122,6 +122,8 @@ extern "C" void fnn_config_default(fnn_config *c) {
   c->shift_ang0 = 0.8;
   c->skin = 0.0;
   c->n_members = 1;
+  c->switch_kind = FNN_SWITCH_COSINE;
+  c->switch_p = 6.0;
 }
 
 extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
@@ -130,7 +132,8 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
   const fnn_config &c = *cfg;
   if (!(c.rc_rad > 0) || !(c.rc_ang > 0) || c.rc_ang > c.rc_rad || !(c.eta_rad >= 0) || !(c.eta_ang >= 0) ||
       !(c.zeta >= 0) || !(c.skin >= 0) || c.n_members < 1 || c.n_members > MAXM || !(c.shift_rad0 < c.rc_rad) ||
-      !(c.shift_ang0 < c.rc_ang))
+      !(c.shift_ang0 < c.rc_ang) || c.switch_kind < FNN_SWITCH_COSINE || c.switch_kind > FNN_SWITCH_EXPONENTIAL ||
+      !(c.switch_p > 0))
     return FNN_E_INVALID;
   fnn_ctx *ctx = new fnn_ctx();
   ctx->cfg = c;
@@ -158,6 +161,15 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
     P.qcos_z[s] = (float)(0.475 * cos(th));
   }
   P.eta_a_l2 = (float)(-c.eta_ang / M_LN2);
+  P.sw_kind = c.switch_kind;
+  {
+    const double p = c.switch_p;
+    P.sw_pm1 = (float)(p - 1.0);
+    P.sw_c0 = (float)(-0.5 * (p + 1.0) * (p + 2.0));
+    P.sw_c1 = (float)(p * (p + 2.0));
+    P.sw_c2 = (float)(-0.5 * p * (p + 1.0));
+    P.sw_k = (float)(0.5 * p * (p + 1.0) * (p + 2.0));
+  }
   if (cudaMalloc(&ctx->status, sizeof(DevStatus)) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;

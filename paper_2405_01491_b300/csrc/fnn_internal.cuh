@@ -72,7 +72,33 @@ struct AevParams {
   float hcos_z[NSZ], hsin_z[NSZ];   // the same halved
   float qcos_z[NSZ];            // 0.475 cos: the cos term of d(base)/dc in the adjoint
   float eta_a_l2;               // -eta_a log2(e): the angular Gaussian as a power of two
+  int sw_kind;                  // fnn_switch
+  float sw_pm1;                 // polynomial envelope: p - 1, and the coefficients of d^p, d^(p+1), d^(p+2)
+  float sw_c0, sw_c1, sw_c2;
+  float sw_k;                   // p (p+1) (p+2) / 2: f'(d) = -sw_k d^(p-1) (1 - d)^2
 };
+
+// The switching function and its derivative at r < rc (section II.A): cosine, polynomial envelope
+// (Gasteiger et al. 2020), exponential (SpookyNet); the kind is uniform over a launch.
+__device__ __forceinline__ float switch_f(const AevParams &P, float r, float rc, float inv_rc) {
+  if (P.sw_kind == FNN_SWITCH_POLYNOMIAL) {
+    const float d = r * inv_rc;
+    return 1.f + powf(d, P.sw_pm1) * d * (P.sw_c0 + d * (P.sw_c1 + d * P.sw_c2));
+  }
+  if (P.sw_kind == FNN_SWITCH_EXPONENTIAL) return expf(-r * r / ((rc - r) * (rc + r)));
+  return 0.5f * cospif(r * inv_rc) + 0.5f;
+}
+__device__ __forceinline__ float switch_df(const AevParams &P, float r, float rc, float inv_rc, float pi_rc) {
+  if (P.sw_kind == FNN_SWITCH_POLYNOMIAL) {
+    const float d = r * inv_rc, om = 1.f - d;
+    return -P.sw_k * powf(d, P.sw_pm1) * om * om * inv_rc;
+  }
+  if (P.sw_kind == FNN_SWITCH_EXPONENTIAL) {
+    const float q = (rc - r) * (rc + r);
+    return -expf(-r * r / q) * 2.f * r * rc * rc / (q * q);
+  }
+  return -0.5f * pi_rc * sinpif(r * inv_rc);
+}
 
 // per-structure cell-list geometry
 struct MolGrid {

@@ -37,7 +37,11 @@ class FnnError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("rc_rad", ctypes.c_double), ("rc_ang", ctypes.c_double), ("eta_rad", ctypes.c_double),
                 ("eta_ang", ctypes.c_double), ("zeta", ctypes.c_double), ("shift_rad0", ctypes.c_double),
-                ("shift_ang0", ctypes.c_double), ("skin", ctypes.c_double), ("n_members", ctypes.c_int32)]
+                ("shift_ang0", ctypes.c_double), ("skin", ctypes.c_double), ("n_members", ctypes.c_int32),
+                ("switch_kind", ctypes.c_int32), ("switch_p", ctypes.c_double)]
+
+
+SWITCH = {"cosine": 0, "polynomial": 1, "exponential": 2}
 
 
 class CWeights(ctypes.Structure):
@@ -162,6 +166,8 @@ class Context:
         lib.fnn_config_default(ctypes.byref(cfg))
         cfg.n_members = n_members
         cfg.skin = skin
+        if "switch" in overrides:   # by name: "cosine", "polynomial", "exponential"
+            cfg.switch_kind = SWITCH[overrides.pop("switch")]
         for k, v in overrides.items():
             setattr(cfg, k, v)
         self.cfg = cfg
@@ -574,17 +580,23 @@ class Server:
         self.n[t.value] = (s.n_atoms, int(n_steps))
         return t.value
 
-    def poll(self, ticket: int, timeout_s: float = 0.0):
-        """The result dict once done, else None (after waiting up to timeout_s)."""
+    def poll(self, ticket: int, timeout_s: float = 0.0, arrays: bool = True):
+        """The result dict once done, else None (after waiting up to timeout_s).  With arrays=False only the
+        timings and step count come back (nothing of the structure is copied)."""
         n, k = self.n[ticket]
-        out = {"energies": np.zeros(k), "pos": np.zeros((n, 3), np.float32), "vel": np.zeros((n, 3), np.float32),
-               "forces": np.zeros((n, 3), np.float32)}
-        r = CResult(out["energies"].ctypes.data, out["pos"].ctypes.data, out["vel"].ctypes.data,
-                    out["forces"].ctypes.data, 0.0, 0.0, 0)
+        if arrays:
+            out = {"energies": np.zeros(k), "pos": np.zeros((n, 3), np.float32),
+                   "vel": np.zeros((n, 3), np.float32), "forces": np.zeros((n, 3), np.float32)}
+            r = CResult(out["energies"].ctypes.data, out["pos"].ctypes.data, out["vel"].ctypes.data,
+                        out["forces"].ctypes.data, 0.0, 0.0, 0)
+        else:
+            out = {}
+            r = CResult(None, None, None, None, 0.0, 0.0, 0)
         code = lib.fnn_serve_poll(self.h, ticket, ctypes.byref(r), int(timeout_s * 1e6))
         if code == FNN_PENDING:
             return None
         if code != FNN_OK:
+            del self.n[ticket]
             raise FnnError(code, "fnn_serve_poll")
         del self.n[ticket]
         out.update(latency_ms=r.latency_ms, queue_ms=r.queue_ms, n_steps_done=r.n_steps_done)

@@ -309,13 +309,32 @@ def request_sizes(rng: np.random.Generator, n: int, lo: int = 8, hi: int = 20000
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))).astype(np.int64)
 
 
+def _pool_member(args) -> Structures:
+    seed, k, n, pbc_above = args
+    rng = np.random.Generator(np.random.PCG64([seed, 1, k]))
+    return random_molecule(rng, int(n), MIX7, periodic=bool(n > pbc_above), name=f"req{k}")
+
+
 def request_pool(n_pool: int = 4096, seed: int = 5, lo: int = 8, hi: int = 20000,
-                 pbc_above: int = 500) -> list[Structures]:
-    """Pool of request structures: log-uniform sizes, MIX7 composition, PBC above 500 atoms."""
+                 pbc_above: int = 500, workers: int = 1) -> list[Structures]:
+    """Pool of request structures: log-uniform sizes, MIX7 composition, PBC above 500 atoms.  Structure k is
+    drawn from its own stream (seed, 1, k), so the pool is the same whether it is built serially or by
+    `workers` spawned processes."""
     rng = np.random.Generator(np.random.PCG64([seed, 1]))
     sizes = request_sizes(rng, n_pool, lo, hi)
-    return [random_molecule(rng, int(s), MIX7, periodic=bool(s > pbc_above), name=f"req{k}")
-            for k, s in enumerate(sizes)]
+    jobs = [(seed, k, int(n), pbc_above) for k, n in enumerate(sizes)]
+    if workers <= 1:
+        return [_pool_member(j) for j in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    # largest first, so the long placements start early; results come back in pool order
+    order = sorted(range(len(jobs)), key=lambda k: -jobs[k][2])
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        built = list(ex.map(_pool_member, [jobs[k] for k in order], chunksize=8))
+    out = [None] * len(jobs)
+    for k, b in zip(order, built):
+        out[k] = b
+    return out
 
 
 def poisson_stream(pool: list[Structures], rate_hz: float = 2000.0, duration_s: float = 60.0,

@@ -16,7 +16,7 @@ import pytest
 import oracle
 from oracle import Params
 from paper_2405_01491_b300 import synth
-from conftest import structure
+from conftest import structure, weights
 
 ELEM = {1: 0, 6: 1, 7: 2, 8: 3, 9: 4, 16: 5, 17: 6}
 
@@ -228,3 +228,81 @@ def test_jvp_vjp_finite_differences(name):
                 out.append(np.sum(G * oracle.aev(st)))
             dEde = (out[0] - out[1]) / (2 * h)
             assert -dEde == pytest.approx(vir[0, a, a], rel=1e-6)
+
+
+# ------------------------------------------------------------------------ switching-function variants
+SWITCHES = ("cosine", "polynomial", "exponential")
+
+
+@pytest.mark.parametrize("p", [6.0, 4.0])
+def test_polynomial_envelope_is_fixed_by_its_boundary_conditions(p):
+    """The envelope 1 + a d^p + b d^(p+1) + c d^(p+2) with f(1) = f'(1) = f''(1) = 0: the three coefficients
+    from a linear solve of those conditions, compared with the oracle's switch everywhere on [0, 1)."""
+    A = np.array([[1.0, 1.0, 1.0], [p, p + 1, p + 2], [p * (p - 1), (p + 1) * p, (p + 2) * (p + 1)]])
+    a, b, c = np.linalg.solve(A, [-1.0, 0.0, 0.0])
+    P = oracle.Params(switch="polynomial", switch_p=p)
+    for d in np.linspace(0.0, 0.999, 37):
+        f, df = oracle.switch(d * 5.1, 5.1, P)
+        want = 1 + a * d ** p + b * d ** (p + 1) + c * d ** (p + 2)
+        dwant = (a * p * d ** (p - 1) + b * (p + 1) * d ** p + c * (p + 2) * d ** (p + 1)) / 5.1
+        assert abs(f - want) < 1e-13 and abs(df - dwant) < 1e-12
+    assert oracle.switch(5.1, 5.1, P) == (0.0, 0.0) and oracle.switch(6.0, 5.1, P) == (0.0, 0.0)
+
+
+def test_exponential_switch_special_values():
+    P = oracle.Params(switch="exponential")
+    rc = 3.5
+    assert oracle.switch(0.0, rc, P)[0] == 1.0
+    f, _ = oracle.switch(rc / np.sqrt(2.0), rc, P)          # r^2 = rc^2 - r^2: exactly exp(-1)
+    assert abs(f - np.exp(-1.0)) < 1e-15
+    assert oracle.switch(rc * 0.99, rc, P)[0] < 1e-20        # flat to every order at the cutoff
+
+
+@pytest.mark.parametrize("sw", SWITCHES)
+def test_switch_derivative_and_smoothness(sw):
+    P = oracle.Params(switch=sw)
+    rc, h = 5.1, 1e-6
+    for r in (0.3, 1.7, 2.9, 4.4, 5.0):
+        fp, fm = oracle.switch(r + h, rc, P)[0], oracle.switch(r - h, rc, P)[0]
+        assert abs((fp - fm) / (2 * h) - oracle.switch(r, rc, P)[1]) < 1e-8
+    # value and slope go to zero at the cutoff (and, for these two, the curvature)
+    f, df = oracle.switch(rc - 1e-5, rc, P)
+    assert f < 1e-8 and abs(df) < 1e-3
+    if sw != "cosine":
+        d1, d2 = oracle.switch(rc - 2e-3, rc, P)[1], oracle.switch(rc - 1e-3, rc, P)[1]
+        assert abs(d2 - d1) / 1e-3 < 1e-2
+
+
+@pytest.mark.parametrize("sw", SWITCHES[1:])
+def test_diatomic_radial_slot_with_switch(sw):
+    P = oracle.Params(switch=sw)
+    r = 2.37
+    s = synth.Structures(np.array([6, 8], np.int32), np.array([[0, 0, 0], [r, 0, 0]], np.float32),
+                         np.array([0, 2], np.int32), np.zeros((1, 9), np.float32), np.zeros(1, np.uint8))
+    A = oracle.aev(s, P)
+    r32 = float(np.float32(r))
+    f = oracle.switch(r32, 5.1, P)[0]
+    shifts = 0.8 + np.arange(16) * (5.1 - 0.8) / 16
+    # atom 0 (C) sees one O: element 3's radial block
+    np.testing.assert_allclose(A[0, 3 * 16:4 * 16], 0.25 * np.exp(-19.7 * (r32 - shifts) ** 2) * f, rtol=1e-12,
+                               atol=1e-300)
+    assert np.all(A[0, 112:] == 0.0)
+
+
+@pytest.mark.parametrize("sw", SWITCHES[1:])
+def test_forces_are_minus_energy_gradient_with_switch(sw):
+    P = oracle.Params(switch=sw)
+    s = structure("gas24")
+    w = weights(1)
+    r = oracle.energy_forces(s, w, P)
+    rng = np.random.default_rng(5)
+    h = 1e-4
+    for i in rng.choice(s.n_atoms, 4, replace=False):
+        for a in range(3):
+            xp = np.asarray(s.pos, np.float64).copy()
+            xm = xp.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            Ep = oracle.energy_forces(synth.Structures(s.Z, xp, s.mol_offsets, s.cell, s.pbc), w, P).energy[0]
+            Em = oracle.energy_forces(synth.Structures(s.Z, xm, s.mol_offsets, s.cell, s.pbc), w, P).energy[0]
+            assert abs(-(Ep - Em) / (2 * h) - r.forces[i, a]) < 1e-6 * max(1.0, abs(r.forces[i, a]))
