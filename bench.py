@@ -739,12 +739,13 @@ def drift_bench(fnn, torch, synth, forms=("fp32", "fp32x3", "bf16", "fp8"), n_st
                               "max_excursion_per_atom": float(np.abs(Et - Et[0]).max()),
                               "kinetic_per_atom_mean": float(K.cpu().numpy()[:, 0].mean() / s.n_atoms),
                               "rebuilds": cnt["rebuilds"], "guard_rebuilds": cnt["guard_rebuilds"]}
-    ctx = fnn.Context(M, skin=1.0)
-    fnn.load_weights(ctx, w)
+    M8 = 8   # the Langevin run uses the 8-member ensemble of the NVE water run (smoother random-weight surface)
+    ctx = fnn.Context(M8, skin=1.0)
+    fnn.load_weights(ctx, synth.xavier_weights(M8))
     nl = fnn.NeighborList(ctx)
     ds = fnn.DeviceSystem.from_structures(s)
     vel = v0.clone().cuda()
-    n_l, dt_l, gamma = 4000, 0.5, 0.01
+    n_l, dt_l, gamma = 1000, 0.5, 0.01
     with torch.cuda.stream(stream):
         E, K, _, cnt = fnn.md_run_ex(ctx, ds, vel, nl, "fp32x3", n_l, dt_l, 10, integrator="langevin",
                                      temperature_K=300.0, friction_per_fs=gamma, seed=2405, kinetic=True,
@@ -752,7 +753,7 @@ def drift_bench(fnn, torch, synth, forms=("fp32", "fp32x3", "bf16", "fp8"), n_st
     fnn.check(ctx, "langevin", stream=stream)
     Kk = K.cpu().numpy()[:, 0]
     kb = 0.0019872041
-    out["langevin"] = {"integrator": "BAOAB", "T_bath_K": 300.0, "friction_per_fs": gamma, "dt_fs": dt_l,
+    out["langevin"] = {"integrator": "BAOAB", "members": M8, "T_bath_K": 300.0, "friction_per_fs": gamma, "dt_fs": dt_l,
                        "steps": n_l, "T_kinetic_mean_K_second_half": float(2 * Kk[n_l // 2:].mean() / (3 * s.n_atoms * kb)),
                        "rebuilds": cnt["rebuilds"], "guard_rebuilds": cnt["guard_rebuilds"]}
     return out
@@ -844,6 +845,15 @@ def kernel_table(prof, steps, n_atoms, nnz, M, form, pk):
     return kernels, roof
 
 
+def section(name, fn, *a, **kw):
+    """An optional measurement: its result, or the error it raised (the JSON line is printed either way)."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:   # noqa: BLE001 - reported, not hidden
+        print(f"bench: section {name} failed: {e!r}", file=sys.stderr, flush=True)
+        return {"error": f"{type(e).__name__}: {e}"[:500]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -920,19 +930,19 @@ def main():
         base, ref = oracle_full(M)
     plan = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_cpu_plan:
-        plan = cpu_plan()
+        plan = section("cpu_plan", cpu_plan)
     serve = None
     if world == 1 and not args.no_serve:
-        serve = serve_bench(fnn, torch, synth, duration_s=args.serve_seconds, pool_n=args.serve_pool)
+        serve = section("serve", serve_bench, fnn, torch, synth, duration_s=args.serve_seconds, pool_n=args.serve_pool)
     md = latency = drift = None
     if world == 1 and not args.no_md:
-        md = md_bench(fnn, torch, synth)
-        latency = latency_bench(fnn, torch, synth)
+        md = section("md", md_bench, fnn, torch, synth)
+        latency = section("latency", latency_bench, fnn, torch, synth)
     if world == 1 and not args.no_drift:
-        drift = drift_bench(fnn, torch, synth)
+        drift = section("drift", drift_bench, fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
-        train = {p: train_bench(fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
+        train = {p: section(f"train_{p}", train_bench, fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
                  for p in ("bf16", "fp32")}
 
     head = results[args.precision]

@@ -302,6 +302,34 @@ fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *pos, float 
                          fnn_md_counters *counters, void *stream);
 
 /*
+ * Ring-polymer molecular dynamics (the NQE method of section V.D): P replicas (beads) of one structure, whose
+ * potential energies and forces come from one batched evaluation -- the beads are the P structures of the
+ * system `beads` (n_mol = P, each of n_atoms / P atoms, bead b's atom i at b n + i, identical species and
+ * cells; periodic beads use the minimum image each).  The free ring polymer, springs 1/2 m wP^2 |x_b - x_(b+1)|^2
+ * with wP = P kB T / hbar (hbar = 15.178736 kcal/mol fs), is propagated exactly in its normal modes
+ * q~_k = sum_j C_jk x_j (C: the real Fourier basis, 1/sqrt(P); sqrt(2/P) cos(2 pi j k / P) for 0 < k < P/2;
+ * (-1)^j / sqrt(P) for k = P/2; sqrt(2/P) sin(2 pi j k / P) above), mode k a harmonic oscillator of frequency
+ * 2 wP sin(k pi / P) (the centroid free).  After evaluation k: v += a dt/2 (completing step k-1; H_hist[k] =
+ * the ring-polymer Hamiltonian: bead kinetic + spring + potential energies), and unless k is the last:
+ * v += a dt/2 and the exact free-ring-polymer step for dt.  The list schedule and skin guard are those of
+ * fnn_md_run_ex (the guard on a bound of the displacement: 3 times its largest component squared).
+ * pos, vel: device [P n][4].  E_hist: device [n_steps][P] bead energies, or NULL.  H_hist: device [n_steps]
+ * float64, or NULL.  F: device [P n][3], the last evaluation's forces.  counters as for fnn_md_run_ex.
+ */
+#define FNN_RPMD_MAX_BEADS 32
+typedef struct {
+  int32_t n_beads;          /* P, 1..FNN_RPMD_MAX_BEADS */
+  int32_t n_steps;
+  double dt_fs;
+  double temperature_K;     /* sets the spring constant (> 0) */
+  int32_t rebuild_every;
+  int32_t skin_guard;
+} fnn_rpmd_options;
+fnn_status fnn_rpmd_run(fnn_ctx *ctx, const fnn_system *beads, float *pos, float *vel, fnn_nlist *nl,
+                        fnn_precision prec, const fnn_rpmd_options *opt, double *E_hist, double *H_hist, float *F,
+                        fnn_md_counters *counters, void *stream);
+
+/*
  * Continuous-batching MD service.  A scheduler thread keeps a ragged batch of
  * structures on the device and advances all of them one velocity-Verlet step per batch step (one
  * neighbour-list/AEV/network/adjoint pass over the whole batch; the shared list is rebuilt when the
@@ -399,6 +427,29 @@ fnn_status fnn_serve_destroy(fnn_server *srv);
 #define FNN_STATIC_MAX_MOL 256
 fnn_status fnn_build_neighbors_static(const fnn_system *sys, double R, int32_t *row_ptr, int32_t *nbr, int8_t *shift4,
                                       int64_t cap, int64_t *nnz, void *stream);
+
+/*
+ * CRATE angular resource of the first interaction layer (Appendix A, angular resources), over the
+ * neighbours within rc_ang of a list built for sys:
+ *   D_ij[c] = f~(r_ij) sum_a B~_a(r_ij) V[e(j)][a][c],   B~_a(r) = exp(-eta_ang (r - A_a)^2),
+ *   g_i[n][c] = sum over unordered neighbour pairs {j, k} of cos(n theta_jik) D_ij[c] D_ik[c],
+ * a < FNN_CRATE_NB radial functions on the angular shifts A_a = shift_ang0 + a (rc_ang - shift_ang0) / 8,
+ * n < FNN_CRATE_NT (the Fourier angular basis, cos(n theta) evaluated as a Chebyshev polynomial of
+ * cos theta), c < FNN_CRATE_DA channels, f~ the context's switching function at rc_ang, e(j) the element
+ * index (H C N O F S Cl = 0..6).  V [7][8][32] float32 (device): the product of the layer's neighbour
+ * embedding table (a row per element) and its trainable tensor W_ang, contracted over the embedding.
+ * g: device [N][4][32] float32, written.  At most 64 neighbours within rc_ang per atom (FNN_E_CAPACITY,
+ * info = -(atom + 1); that atom's row is zero).  Asynchronous.
+ */
+#define FNN_CRATE_NB 8
+#define FNN_CRATE_DA 32
+#define FNN_CRATE_NT 4
+fnn_status fnn_crate_angular(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V, float *g,
+                             void *stream);
+/* Vector-Jacobian product of fnn_crate_angular: with G = dL/dg [N][4][32] (device), grad_x [N][3] = dL/dx and
+ * (when grad_V != NULL) grad_V [7][8][32] = dL/dV, both device float32 and overwritten.  Asynchronous. */
+fnn_status fnn_crate_angular_vjp(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
+                                 const float *G, float *grad_x, float *grad_V, void *stream);
 
 /* Instrumentation (no counterpart in the paper; the tracing the benchmark reads).
  * fnn_profile_enable: while on, every kernel this context launches is bracketed

@@ -509,3 +509,146 @@ def langevin_baoab(s, w, v0, n_steps: int, dt: float, temperature: float, gamma:
             v = c1 * v + c2 * sig * langevin_noise(s.n_atoms, step0 + k, seed)
             x = x + 0.5 * dt * v
     return np.asarray(energies), np.asarray(kinetic), x, v, F
+
+
+# ------------------------------------------------------------------------- CRATE angular resource (App. A)
+CRATE_NB = 8       # triplet radial basis functions B~_a
+CRATE_DA = 32      # channels d_a of D_ij
+CRATE_NT = 4       # angular basis functions Theta_n = cos(n theta), n = 0..3
+
+
+def _switch_torch(r, rc, params: Params):
+    """The switching function of params (section II.A) in torch float64, for the autograd of the CRATE
+    resource; it is compared point by point with the C oracle's switch in the pins."""
+    import torch
+    inside = r < rc
+    rr = torch.where(inside, r, torch.zeros_like(r))
+    if params.switch == "polynomial":
+        p, d = params.switch_p, rr / rc
+        f = 1 - 0.5 * (p + 1) * (p + 2) * d ** p + p * (p + 2) * d ** (p + 1) - 0.5 * p * (p + 1) * d ** (p + 2)
+    elif params.switch == "exponential":
+        f = torch.exp(-rr * rr / ((rc - rr) * (rc + rr)))
+    else:
+        f = 0.5 * torch.cos(np.pi * rr / rc) + 0.5
+    return torch.where(inside, f, torch.zeros_like(f))
+
+
+def crate_triplets(ei: np.ndarray):
+    """Unordered pairs {p, q}, p < q, of the directed edges that share their centre atom (edges sorted by
+    centre): the triplets (i, j, k) of Appendix A's sum over {jk}."""
+    P, Q = [], []
+    starts = np.flatnonzero(np.r_[True, ei[1:] != ei[:-1]]) if len(ei) else np.zeros(0, np.int64)
+    ends = np.r_[starts[1:], len(ei)]
+    for a, b in zip(starts, ends):
+        p, q = np.triu_indices(b - a, 1)
+        P.append(p + a)
+        Q.append(q + a)
+    if not P:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    return np.concatenate(P).astype(np.int64), np.concatenate(Q).astype(np.int64)
+
+
+def crate_angular(s, V, params: Params = Params(), G=None):
+    """The angular resource of CRATE's first interaction layer (Appendix A, angular resources):
+        D_ij[c] = f~(r_ij) sum_a B~_a(r_ij) V[e(j), a, c],   B~_a(r) = exp(-eta_a (r - A_a)^2),
+        g_i[n, c] = sum_{j<k} Theta_n(theta_jik) D_ij[c] D_ik[c],   Theta_n = cos(n theta),
+    over neighbours within rc_ang (the triplet cutoff), A_a = shf_a0 + a (rc_ang - shf_a0) / 8, f~ the switch
+    at rc_ang.  The neighbour embedding depends on the neighbour's element only (layer 1), so the product of
+    the species table and the trainable tensor W_ang enters as one tensor V [7, 8, 32].  cos(n theta) is
+    evaluated as the Chebyshev polynomial T_n(cos theta) (equal for every theta, smooth at 0 and pi).
+    Returns g [N, 4, 32]; with G = dL/dg given, also (dL/dx [N, 3], dL/dV [7, 8, 32]) by float64 autograd."""
+    import torch
+    Z, pos, mo, cell, pbc = _sys_arrays(s)
+    ei, ej, es = neighbors(s, params.rc_ang)
+    x = torch.tensor(pos, dtype=torch.float64, requires_grad=G is not None)
+    Vt = torch.tensor(np.asarray(V, np.float64), requires_grad=G is not None)
+    mol = np.repeat(np.arange(s.n_mol), np.diff(mo))
+    L = np.zeros((s.n_atoms, 3))
+    for m in range(s.n_mol):
+        if pbc[m]:
+            L[mo[m]:mo[m + 1]] = cell[m, [0, 4, 8]]
+    sh = torch.tensor(es.astype(np.float64) * L[ei], dtype=torch.float64)
+    d = x[torch.from_numpy(ej.astype(np.int64))] - x[torch.from_numpy(ei.astype(np.int64))] + sh
+    r = torch.sqrt((d * d).sum(1))
+    shifts = torch.tensor(params.shf_a0 + np.arange(CRATE_NB) * (params.rc_ang - params.shf_a0) / CRATE_NB)
+    B = torch.exp(-params.eta_a * (r[:, None] - shifts[None, :]) ** 2)
+    el = torch.from_numpy(elements(Z)[ej].astype(np.int64))
+    D = _switch_torch(r, params.rc_ang, params)[:, None] * torch.einsum("pa,pac->pc", B, Vt[el])
+    p, q = crate_triplets(ei)
+    p, q = torch.from_numpy(p), torch.from_numpy(q)
+    c = (d[p] * d[q]).sum(1) / (r[p] * r[q])
+    T = torch.stack([torch.ones_like(c), c, 2 * c * c - 1, (4 * c * c - 3) * c], 1)
+    g = torch.zeros((s.n_atoms, CRATE_NT, CRATE_DA), dtype=torch.float64)
+    g = g.index_add(0, torch.from_numpy(ei.astype(np.int64))[p], T[:, :, None] * (D[p] * D[q])[:, None, :])
+    if G is None:
+        return g.detach().numpy()
+    gx, gV = torch.autograd.grad(g, (x, Vt), grad_outputs=torch.tensor(np.asarray(G, np.float64)),
+                                 allow_unused=True)
+    gx = torch.zeros_like(x) if gx is None else gx
+    gV = torch.zeros_like(Vt) if gV is None else gV
+    return g.detach().numpy(), gx.numpy(), gV.numpy()
+
+
+# -------------------------------------------------------------------------------- RPMD (section V.D)
+HBAR_KCAL_FS = 15.178736   # reduced Planck constant in kcal/mol fs (1.054571817e-34 J s, N_A, 4184 J/kcal)
+
+
+def rpmd_normal_modes(P: int):
+    """Orthogonal matrix C [bead j, mode k] of the free ring polymer (real Fourier basis): k = 0 the centroid
+    1/sqrt(P); 0 < k < P/2 sqrt(2/P) cos(2 pi j k / P); k = P/2 (-1)^j / sqrt(P); P/2 < k sqrt(2/P) sin(2 pi j k / P).
+    Returns C and the mode frequencies in units of omega_P: 2 sin(k pi / P)."""
+    j = np.arange(P)[:, None]
+    k = np.arange(P)[None, :]
+    C = np.where(k == 0, 1.0 / np.sqrt(P), 0.0)
+    C = C + np.where((k > 0) & (2 * k < P), np.sqrt(2.0 / P) * np.cos(2 * np.pi * j * k / P), 0.0)
+    C = C + np.where((2 * k == P), (-1.0) ** j / np.sqrt(P), 0.0)
+    C = C + np.where(2 * k > P, np.sqrt(2.0 / P) * np.sin(2 * np.pi * j * k / P), 0.0)
+    return C, 2.0 * np.sin(np.arange(P) * np.pi / P)
+
+
+def rpmd(s, w, P: int, x0, v0, n_steps: int, dt: float, temperature: float, params: Params = Params()):
+    """Ring-polymer molecular dynamics (Habershon et al. 2013; the paper's NQE method of section V.D): P replicas
+    (beads) of the structure s, bead b's positions x[b] and velocities v[b] ([P, N, 3]); the physical forces of
+    all beads from one batched evaluation (the beads as P structures of one batch), and the free ring polymer,
+    whose springs 1/2 m omega_P^2 |x_b - x_(b+1)|^2 (omega_P = P kB T / hbar) couple neighbouring beads, propagated
+    exactly in its normal modes.  After evaluation k: v += a dt/2 (completing step k-1 when k > 0; then the
+    Hamiltonian of the ring polymer at step k is recorded), and unless k is the last: v += a dt/2, then each mode
+    q~_k = sum_j C_jk x_j evolves for dt as a harmonic oscillator of frequency omega_P 2 sin(k pi / P) (the centroid
+    freely).  Returns (bead potential energies [n_steps, P], Hamiltonian [n_steps], x, v, F [P, N, 3])."""
+    el = elements(s.Z)
+    m = np.asarray([MASS[int(e)] for e in el])[None, :, None]
+    N = s.n_atoms
+    x = np.asarray(x0, np.float64).reshape(P, N, 3).copy()
+    v = np.asarray(v0, np.float64).reshape(P, N, 3).copy()
+    C, wk = rpmd_normal_modes(P)
+    wP = P * KB_KCAL * temperature / HBAR_KCAL_FS
+    om = wk * wP
+    batch = lambda xx: type(s)(np.tile(s.Z, P), xx.reshape(P * N, 3), np.arange(P + 1, dtype=np.int32) * N,
+                               np.repeat(np.asarray(s.cell, np.float64).reshape(1, 9), P, 0), np.repeat(s.pbc, P))
+    energies, hamilton = [], []
+    F = None
+    for k in range(n_steps):
+        r = energy_forces(batch(x), w, params)
+        energies.append(r.energy.copy())
+        F = r.forces.reshape(P, N, 3)
+        a = F / m * ACCEL
+        if k > 0:
+            v = v + 0.5 * dt * a
+        kin = 0.5 * np.sum(m * v * v) / ACCEL
+        spring = 0.5 * np.sum(m * (wP ** 2) * (x - np.roll(x, -1, axis=0)) ** 2) / ACCEL
+        hamilton.append(kin + spring + r.energy.sum())
+        if k < n_steps - 1:
+            v = v + 0.5 * dt * a
+            q = np.einsum("jk,jnc->knc", C, x)
+            p = np.einsum("jk,jnc->knc", C, v)
+            qn, pn = q.copy(), p.copy()
+            for kk in range(P):
+                if om[kk] == 0.0:
+                    qn[kk] = q[kk] + dt * p[kk]
+                else:
+                    cs, sn = np.cos(om[kk] * dt), np.sin(om[kk] * dt)
+                    qn[kk] = cs * q[kk] + sn / om[kk] * p[kk]
+                    pn[kk] = -om[kk] * sn * q[kk] + cs * p[kk]
+            x = np.einsum("jk,knc->jnc", C, qn)
+            v = np.einsum("jk,knc->jnc", C, pn)
+    return np.asarray(energies), np.asarray(hamilton), x, v, F

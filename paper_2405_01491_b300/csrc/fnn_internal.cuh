@@ -82,8 +82,10 @@ struct AevParams {
 // (Gasteiger et al. 2020), exponential (SpookyNet); the kind is uniform over a launch.
 __device__ __forceinline__ float switch_f(const AevParams &P, float r, float rc, float inv_rc) {
   if (P.sw_kind == FNN_SWITCH_POLYNOMIAL) {
+    // near the cutoff the terms cancel to O(float eps), which may fall just below zero: clamped, since the
+    // angular terms take the logarithm of switch products
     const float d = r * inv_rc;
-    return 1.f + powf(d, P.sw_pm1) * d * (P.sw_c0 + d * (P.sw_c1 + d * P.sw_c2));
+    return fminf(fmaxf(1.f + powf(d, P.sw_pm1) * d * (P.sw_c0 + d * (P.sw_c1 + d * P.sw_c2)), 0.f), 1.f);
   }
   if (P.sw_kind == FNN_SWITCH_EXPONENTIAL) return expf(-r * r / ((rc - r) * (rc + r)));
   return 0.5f * cospif(r * inv_rc) + 0.5f;

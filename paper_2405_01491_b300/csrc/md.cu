@@ -19,6 +19,7 @@
 // exactly when needed with no host round trip.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "fnn_internal.cuh"
 
@@ -28,6 +29,7 @@ namespace fnn {
 static const double MASS_AMU[NE] = {1.008, 12.011, 14.007, 15.999, 18.998, 32.06, 35.45};
 static constexpr double ACCEL = 4.184e-4;       // A/fs^2 per kcal/mol/A/amu (and A^2/fs^2 per kcal/mol/amu)
 static constexpr double KB_KCAL = 0.0019872041; // Boltzmann constant, kcal/mol/K
+static constexpr double HBAR_KCAL_FS = 15.178736; // reduced Planck constant, kcal/mol fs
 
 // ------------------------------------------------------------------------------------ Philox-4x32-10
 // Counter-based generator of Salmon, Moraes, Dror and Shaw (SC 2011): ten rounds of two 32x32->64 bit
@@ -199,6 +201,142 @@ fnn_status launch_md_update(fnn_ctx *ctx, const fnn_nlist *nl, int n, float4 *po
   return check_launch(ctx, "md_update");
 }
 
+// ------------------------------------------------------------------------------------------ RPMD
+// Ring-polymer MD (section V.D, NQE methods): the P beads of one ring polymer are the P structures of the
+// batch (bead b's atom i at b N + i), all at the same step.  One warp per (atom, Cartesian component),
+// lane = bead: the kicks, the ring-polymer Hamiltonian terms (kinetic + springs 1/2 m wP^2 |x_b - x_(b+1)|^2),
+// and the exact free-ring-polymer step in normal modes q~_k = sum_j C_jk x_j (transforms by shuffles).
+constexpr int RPMD_MAXP = 32;
+struct RpmdKArgs {
+  int N, P;
+  float4 *pos, *vel;
+  const float *F;
+  const uint8_t *elem;
+  const int32_t *mol_step;
+  int nsteps;
+  float dt;
+  float acc[NE];         // ACCEL / mass
+  float half_m[NE];      // mass / (2 ACCEL)
+  float half_m_wp2[NE];  // mass wP^2 / (2 ACCEL)
+  const float *C;        // [P][P] bead j, mode k
+  const float4 *prop;    // [P] per mode: cos(w dt), sin(w dt) / w (dt for w = 0), -w sin(w dt)
+  const double *E;       // [P] bead energies of this evaluation
+  double *H;             // [nsteps] ring-polymer Hamiltonian, or NULL
+  const float4 *xref;    // guard reference positions, or NULL
+  unsigned *max_d2;
+};
+
+__global__ void __launch_bounds__(256) k_rpmd_update(RpmdKArgs a) {
+  __shared__ float Cs[RPMD_MAXP * RPMD_MAXP];
+  __shared__ float4 ps[RPMD_MAXP];
+  __shared__ double hsum;
+  const unsigned FULL = 0xffffffffu;
+  const int P = a.P;
+  for (int q = threadIdx.x; q < P * P; q += blockDim.x) Cs[q] = a.C[q];
+  for (int q = threadIdx.x; q < P; q += blockDim.x) ps[q] = a.prop[q];
+  if (threadIdx.x == 0) hsum = 0.0;
+  __syncthreads();
+  const int k = a.mol_step[0];
+  const bool valid = k >= 0 && k < a.nsteps;
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < P;
+  const int nw = 3 * a.N;
+  float hacc = 0.f;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; valid && w < nw; w += (gridDim.x * blockDim.x) >> 5) {
+    const int i = w / 3, comp = w - 3 * i;
+    const int e = a.elem[i];
+    const size_t at = (size_t)(on ? lane : 0) * a.N + i;
+    float x = 0.f, v = 0.f, f = 0.f;
+    if (on) {
+      x = reinterpret_cast<const float *>(a.pos + at)[comp];
+      v = reinterpret_cast<const float *>(a.vel + at)[comp];
+      f = a.F[3 * at + comp];
+    }
+    const float h = 0.5f * a.dt * a.acc[e];
+    if (k > 0) v = fmaf(h, f, v);   // completes step k - 1
+    const float xn = __shfl_sync(FULL, x, on ? (lane + 1) % P : lane);
+    if (on) hacc += a.half_m[e] * v * v + a.half_m_wp2[e] * (x - xn) * (x - xn);
+    if (k < a.nsteps - 1) {
+      v = fmaf(h, f, v);
+      float qm = 0.f, pm = 0.f;   // lane m: normal mode m
+      for (int j = 0; j < P; j++) {
+        const float xj = __shfl_sync(FULL, x, j), vj = __shfl_sync(FULL, v, j);
+        const float c = on ? Cs[j * P + lane] : 0.f;
+        qm = fmaf(c, xj, qm);
+        pm = fmaf(c, vj, pm);
+      }
+      const float4 pr = on ? ps[lane] : make_float4(1.f, 0.f, 0.f, 0.f);
+      const float qn = fmaf(pr.x, qm, pr.y * pm), pn = fmaf(pr.z, qm, pr.x * pm);
+      float xb = 0.f, vb = 0.f;   // lane j: bead j again
+      for (int m = 0; m < P; m++) {
+        const float qq = __shfl_sync(FULL, qn, m), pp = __shfl_sync(FULL, pn, m);
+        const float c = on ? Cs[lane * P + m] : 0.f;
+        xb = fmaf(c, qq, xb);
+        vb = fmaf(c, pp, vb);
+      }
+      x = xb;
+      v = vb;
+      if (on) reinterpret_cast<float *>(a.pos + at)[comp] = x;
+      if (a.max_d2) {   // 3 d_c^2 bounds |d|^2 from above when it is the largest component's
+        float d = 0.f;
+        if (on) d = x - reinterpret_cast<const float *>(a.xref + at)[comp];
+        float d2 = 3.f * d * d;
+        if (!(d2 == d2)) d2 = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(FULL, d2, o));
+        if (lane == 0 && d2 > 0.f) atomicMax(a.max_d2, __float_as_uint(d2));
+      }
+    }
+    if (on) reinterpret_cast<float *>(a.vel + at)[comp] = v;
+  }
+  if (a.H && valid) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hacc += __shfl_xor_sync(FULL, hacc, o);
+    if (lane == 0 && hacc != 0.f) atomicAdd(&hsum, (double)hacc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = hsum;
+      if (blockIdx.x == 0)
+        for (int b = 0; b < P; b++) t += a.E[b];
+      atomicAdd(&a.H[k], t);
+    }
+  }
+}
+
+fnn_status launch_rpmd_update(fnn_ctx *ctx, const fnn_nlist *nl, int N, int P, float4 *pos, float4 *vel,
+                              const float *F, const int32_t *mol_step, int nsteps, double dt, double temperature,
+                              const float *C, const float4 *prop, const double *E, double *H, const float4 *xref,
+                              unsigned *max_d2, cudaStream_t s) {
+  if (N <= 0) return FNN_OK;
+  RpmdKArgs a{};
+  a.N = N;
+  a.P = P;
+  a.pos = pos;
+  a.vel = vel;
+  a.F = F;
+  a.elem = nl->elem;
+  a.mol_step = mol_step;
+  a.nsteps = nsteps;
+  a.dt = (float)dt;
+  const double wP = P * KB_KCAL * temperature / HBAR_KCAL_FS;
+  for (int e = 0; e < NE; e++) {
+    a.acc[e] = (float)(ACCEL / MASS_AMU[e]);
+    a.half_m[e] = (float)(0.5 * MASS_AMU[e] / ACCEL);
+    a.half_m_wp2[e] = (float)(0.5 * MASS_AMU[e] * wP * wP / ACCEL);
+  }
+  a.C = C;
+  a.prop = prop;
+  a.E = E;
+  a.H = H;
+  a.xref = xref;
+  a.max_d2 = max_d2;
+  int blocks = (int)((3LL * N * 32 + 255) / 256);
+  if (blocks > 8 * ctx->num_sms) blocks = 8 * ctx->num_sms;
+  FNN_KERNEL(ctx, "rpmd_update", s);
+  k_rpmd_update<<<blocks, 256, 0, s>>>(a);
+  return check_launch(ctx, "rpmd_update");
+}
+
 // copy E[m] of the evaluation just done into each structure's history at hist_off[m] + step[m]
 __global__ void k_record_energy(int n_mol, const double *E, const int32_t *mol_step, const int32_t *mol_nsteps,
                                 const int64_t *hist_off, double *hist, int step, int64_t stride) {
@@ -293,6 +431,12 @@ struct MdRun {
   float4 *xref;
   unsigned *max_d2;
   float half_skin2;
+  // ring-polymer MD (fnn_rpmd_run): beads, temperature, normal-mode matrix and propagators, Hamiltonian
+  int rp_P = 0;
+  double rp_T = 0.0;
+  const float *rp_C = nullptr;
+  const float4 *rp_prop = nullptr;
+  double *H_hist = nullptr;
 };
 
 // the rebuild itself: list, then the guard's reference positions
@@ -310,6 +454,13 @@ fnn_status md_after(MdRun &r, cudaStream_t s) {
   if (r.E_hist &&
       (st = launch_record_energy(ctx, r.v.n_mol, r.E, r.mol_step, r.mol_nsteps, nullptr, r.E_hist, 0, r.v.n_mol, s)))
     return st;
+  if (r.rp_P > 0) {
+    if ((st = launch_rpmd_update(ctx, r.nl, r.v.n_atoms / r.rp_P, r.rp_P, reinterpret_cast<float4 *>(r.pos),
+                                 reinterpret_cast<float4 *>(r.vel), r.F, r.mol_step, r.o.n_steps, r.o.dt_fs, r.rp_T,
+                                 r.rp_C, r.rp_prop, r.E, r.H_hist, r.xref, r.o.skin_guard ? r.max_d2 : nullptr, s)))
+      return st;
+    return launch_advance_steps(ctx, r.v.n_mol, r.mol_step, r.st, s);
+  }
   MdUpdate u;
   u.mol_step = r.mol_step;
   u.mol_nsteps = r.mol_nsteps;
@@ -441,14 +592,19 @@ fnn_status md_step_capture(MdRun &r, cudaStream_t s, BodyCapture &bc, long long 
 
 using namespace fnn;
 
-extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl,
-                                    fnn_precision prec, const fnn_md_options *opt, double *E_hist, double *K_hist,
-                                    float *F, fnn_md_counters *counters, void *stream) {
-  if (!ctx || !sys || !pos || !vel || !nl || !F || !opt || opt->n_steps < 0 || !(opt->dt_fs > 0) ||
-      opt->rebuild_every < 1 || ((uintptr_t)pos & 15) || ((uintptr_t)vel & 15) ||
-      (opt->integrator != FNN_MD_NVE && opt->integrator != FNN_MD_LANGEVIN) ||
-      (opt->integrator == FNN_MD_LANGEVIN && (!(opt->friction_per_fs > 0) || !(opt->temperature_K >= 0))))
-    return FNN_E_INVALID;
+namespace fnn {
+namespace {
+struct RpmdSetup {   // ring-polymer MD: beads and temperature, and where the histories go
+  int P = 0;
+  double T = 0.0;
+  double *H_hist = nullptr;
+};
+
+// The driver of fnn_md_run_ex and fnn_rpmd_run: scratch, the first block eagerly, whole blocks as replays of
+// one captured graph with conditional rebuilds, the rest eagerly, counters.
+fnn_status md_run_core(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl, fnn_precision prec,
+                       const fnn_md_options *opt, double *E_hist, double *K_hist, float *F, fnn_md_counters *counters,
+                       void *stream, const RpmdSetup &rp) {
   if (!ctx->pinned_flag) FNN_CUDA_TRY(ctx, cudaHostAlloc((void **)&ctx->pinned_flag, 64, cudaHostAllocDefault));
   cudaStream_t s = (cudaStream_t)stream;
   MdRun r{};
@@ -472,7 +628,8 @@ extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *
   const size_t off_step = ((size_t)nm * sizeof(double) + 255) & ~(size_t)255;
   const size_t off_state = (off_step + 2 * (size_t)nm * sizeof(int32_t) + 255) & ~(size_t)255;
   const size_t off_ref = (off_state + sizeof(MdState) + 255) & ~(size_t)255;
-  const size_t bytes = off_ref + (size_t)(N > 0 ? N : 1) * sizeof(float4);
+  const size_t off_rp = (off_ref + (size_t)(N > 0 ? N : 1) * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t bytes = off_rp + (size_t)rp.P * rp.P * sizeof(float) + (size_t)rp.P * sizeof(float4) + 16;
   FNN_CUDA_TRY(ctx, cudaMallocAsync((void **)&scratch, bytes, s));
   r.E = reinterpret_cast<double *>(scratch);
   r.mol_step = reinterpret_cast<int32_t *>(scratch + off_step);
@@ -481,6 +638,48 @@ extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *
   r.max_d2 = &r.st->max_d2;
   r.xref = reinterpret_cast<float4 *>(scratch + off_ref);
   fnn_status st = FNN_OK;
+  if (rp.P > 0) {
+    // normal modes of the free ring polymer (real Fourier basis) and their exact one-step propagators
+    const int P = rp.P;
+    std::vector<float> tab((size_t)P * P + 4 * (size_t)P);
+    const double wP = P * KB_KCAL * rp.T / HBAR_KCAL_FS, dt = opt->dt_fs;
+    for (int j = 0; j < P; j++)
+      for (int k = 0; k < P; k++) {
+        double c;
+        if (k == 0) c = 1.0 / sqrt((double)P);
+        else if (2 * k < P) c = sqrt(2.0 / P) * cos(2.0 * M_PI * j * k / P);
+        else if (2 * k == P) c = ((j & 1) ? -1.0 : 1.0) / sqrt((double)P);
+        else c = sqrt(2.0 / P) * sin(2.0 * M_PI * j * k / P);
+        tab[(size_t)j * P + k] = (float)c;
+      }
+    float *pr = tab.data() + (size_t)P * P;
+    for (int k = 0; k < P; k++) {
+      const double w = 2.0 * wP * sin(k * M_PI / P);
+      pr[4 * k] = (float)cos(w * dt);
+      pr[4 * k + 1] = (float)(w > 0 ? sin(w * dt) / w : dt);
+      pr[4 * k + 2] = (float)(-w * sin(w * dt));
+      pr[4 * k + 3] = 0.f;
+    }
+    r.rp_P = P;
+    r.rp_T = rp.T;
+    r.rp_C = reinterpret_cast<const float *>(scratch + off_rp);
+    r.rp_prop = reinterpret_cast<const float4 *>(scratch + off_rp + (((size_t)P * P * sizeof(float) + 15) & ~(size_t)15));
+    r.H_hist = rp.H_hist;
+    // pageable source: the copies complete before the calls return, so tab may go out of scope
+    cudaError_t e = cudaMemcpyAsync(const_cast<float *>(r.rp_C), tab.data(), (size_t)P * P * sizeof(float),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<float4 *>(r.rp_prop), pr, (size_t)P * sizeof(float4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && rp.H_hist && opt->n_steps > 0)
+      e = cudaMemsetAsync(rp.H_hist, 0, (size_t)opt->n_steps * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeAsync(scratch, s);
+      ctx->last_error = "ring-polymer tables";
+      return FNN_E_CUDA;
+    }
+  }
   if (K_hist && opt->n_steps > 0) {
     const cudaError_t e = cudaMemsetAsync(K_hist, 0, (size_t)opt->n_steps * nm * sizeof(double), s);
     if (e != cudaSuccess) {
@@ -571,6 +770,41 @@ extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *
   ctx->prof.launches += scheduled_rebuild_launches;
   cudaFreeAsync(scratch, s);
   return st;
+}
+
+}  // namespace
+}  // namespace fnn
+
+extern "C" fnn_status fnn_md_run_ex(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl,
+                                    fnn_precision prec, const fnn_md_options *opt, double *E_hist, double *K_hist,
+                                    float *F, fnn_md_counters *counters, void *stream) {
+  if (!ctx || !sys || !pos || !vel || !nl || !F || !opt || opt->n_steps < 0 || !(opt->dt_fs > 0) ||
+      opt->rebuild_every < 1 || ((uintptr_t)pos & 15) || ((uintptr_t)vel & 15) ||
+      (opt->integrator != FNN_MD_NVE && opt->integrator != FNN_MD_LANGEVIN) ||
+      (opt->integrator == FNN_MD_LANGEVIN && (!(opt->friction_per_fs > 0) || !(opt->temperature_K >= 0))))
+    return FNN_E_INVALID;
+  return md_run_core(ctx, sys, pos, vel, nl, prec, opt, E_hist, K_hist, F, counters, stream, RpmdSetup{});
+}
+
+extern "C" fnn_status fnn_rpmd_run(fnn_ctx *ctx, const fnn_system *beads, float *pos, float *vel, fnn_nlist *nl,
+                                   fnn_precision prec, const fnn_rpmd_options *opt, double *E_hist, double *H_hist,
+                                   float *F, fnn_md_counters *counters, void *stream) {
+  if (!ctx || !beads || !pos || !vel || !nl || !F || !opt || opt->n_beads < 1 || opt->n_beads > FNN_RPMD_MAX_BEADS ||
+      beads->n_mol != opt->n_beads || beads->n_atoms % opt->n_beads != 0 || opt->n_steps < 0 ||
+      !(opt->dt_fs > 0) || !(opt->temperature_K > 0) || opt->rebuild_every < 1 || ((uintptr_t)pos & 15) ||
+      ((uintptr_t)vel & 15))
+    return FNN_E_INVALID;
+  fnn_md_options o{};
+  o.n_steps = opt->n_steps;
+  o.dt_fs = opt->dt_fs;
+  o.rebuild_every = opt->rebuild_every;
+  o.skin_guard = opt->skin_guard;
+  o.integrator = FNN_MD_NVE;
+  RpmdSetup rp;
+  rp.P = opt->n_beads;
+  rp.T = opt->temperature_K;
+  rp.H_hist = H_hist;
+  return md_run_core(ctx, beads, pos, vel, nl, prec, &o, E_hist, nullptr, F, counters, stream, rp);
 }
 
 extern "C" fnn_status fnn_md_run(fnn_ctx *ctx, const fnn_system *sys, float *pos, float *vel, fnn_nlist *nl,

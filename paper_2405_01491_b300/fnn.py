@@ -91,6 +91,11 @@ class CMdCounters(ctypes.Structure):
                 ("max_displacement", ctypes.c_double)]
 
 
+class CRpmdOptions(ctypes.Structure):
+    _fields_ = [("n_beads", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("dt_fs", ctypes.c_double),
+                ("temperature_K", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("skin_guard", ctypes.c_int32)]
+
+
 class CSystem(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int32), ("n_mol", ctypes.c_int32), ("mol_offsets", ctypes.c_void_p),
                 ("Z", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("cell", ctypes.c_void_p), ("pbc", ctypes.c_void_p)]
@@ -129,9 +134,12 @@ def _load():
         "fnn_profile_read": (I32, [P, P, P, P, I32, P]),
         "fnn_launch_count": (I32, [P, P]),
         "fnn_selftest_lookback": (I32, [P, I32, P]),
+        "fnn_crate_angular": (I32, [P, P, P, P, P, P]),
+        "fnn_crate_angular_vjp": (I32, [P, P, P, P, P, P, P, P]),
         "fnn_build_neighbors_static": (I32, [P, ctypes.c_double, P, P, P, I64, P, P]),
         "fnn_md_run": (I32, [P, P, P, P, P, I32, I32, ctypes.c_double, I32, P, P, P]),
         "fnn_md_run_ex": (I32, [P, P, P, P, P, I32, P, P, P, P, P, P]),
+        "fnn_rpmd_run": (I32, [P, P, P, P, P, I32, P, P, P, P, P, P]),
         "fnn_serve_create": (I32, [P, P, ctypes.c_size_t, I32, I32]),
         "fnn_serve_submit": (I32, [P, P, P]),
         "fnn_serve_poll": (I32, [P, ctypes.c_uint64, P, I64]),
@@ -406,6 +414,29 @@ def energy_forces_autograd(ctx: Context, system: DeviceSystem, nl: NeighborList,
     return _function().apply(ctx, system, nl, precision, *params)
 
 
+def crate_angular(ctx: Context, system: DeviceSystem, nl: NeighborList, V, out=None, stream=None):
+    """fnn_crate_angular: the CRATE angular resource g [N, 4, 32] (float32, device) from V [7, 8, 32]."""
+    import torch
+    if out is None:
+        out = torch.empty((system.n_atoms, 4, 32), dtype=torch.float32, device="cuda")
+    cs = system.c()
+    ctx._check(lib.fnn_crate_angular(ctx.h, ctypes.byref(cs), nl.h, _ptr(V), _ptr(out), _stream(stream)),
+               "fnn_crate_angular")
+    return out
+
+
+def crate_angular_vjp(ctx: Context, system: DeviceSystem, nl: NeighborList, V, G, grad_V: bool = True,
+                      stream=None):
+    """fnn_crate_angular_vjp: (dL/dx [N, 3], dL/dV [7, 8, 32] or None) from G = dL/dg [N, 4, 32]."""
+    import torch
+    gx = torch.empty((system.n_atoms, 3), dtype=torch.float32, device="cuda")
+    gV = torch.empty((7, 8, 32), dtype=torch.float32, device="cuda") if grad_V else None
+    cs = system.c()
+    ctx._check(lib.fnn_crate_angular_vjp(ctx.h, ctypes.byref(cs), nl.h, _ptr(V), _ptr(G), _ptr(gx), _ptr(gV),
+                                         _stream(stream)), "fnn_crate_angular_vjp")
+    return gx, gV
+
+
 def calibrate_fp8(ctx: Context, system: DeviceSystem, nl: NeighborList, stream=None):
     """fnn_calibrate_fp8: per-layer activation scales of the FP8 form from an FP32 evaluation of system."""
     cs = system.c()
@@ -489,6 +520,37 @@ def md_run(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision:
                               int(n_steps), float(dt_fs), int(rebuild_every), _ptr(E_hist), _ptr(F), _stream(stream)),
                "fnn_md_run")
     return E_hist, F
+
+
+def bead_system(s, x, device="cuda"):
+    """The P beads of structure s at positions x [P, N, 3] as one batch of P structures (bead-major)."""
+    from . import synth
+    P, N = x.shape[0], s.n_atoms
+    b = synth.Structures(np.tile(np.asarray(s.Z, np.int32), P), np.asarray(x, np.float32).reshape(P * N, 3),
+                         np.arange(P + 1, dtype=np.int32) * N,
+                         np.repeat(np.asarray(s.cell, np.float32).reshape(1, 9), P, 0),
+                         np.repeat(np.asarray(s.pbc, np.uint8), P))
+    return DeviceSystem.from_structures(b, device)
+
+
+def rpmd_run(ctx: Context, beads: DeviceSystem, vel, nl: NeighborList, precision: str, n_beads: int, n_steps: int,
+             dt_fs: float, temperature_K: float = 300.0, rebuild_every: int = 10, skin_guard: bool = True,
+             counters: bool = False, stream=None):
+    """fnn_rpmd_run: ring-polymer MD of the beads (a batch of n_beads structures, bead-major); beads.pos and
+    vel ([P N, 4] float32) advance in place.  Returns (E_hist [n_steps, P], H_hist [n_steps], F, counters)."""
+    import torch
+    E_hist = torch.empty((n_steps, n_beads), dtype=torch.float64, device="cuda")
+    H_hist = torch.empty((n_steps,), dtype=torch.float64, device="cuda")
+    F = torch.empty((beads.n_atoms, 3), dtype=torch.float32, device="cuda")
+    o = CRpmdOptions(int(n_beads), int(n_steps), float(dt_fs), float(temperature_K), int(rebuild_every),
+                     int(bool(skin_guard)))
+    c = CMdCounters()
+    cs = beads.c()
+    ctx._check(lib.fnn_rpmd_run(ctx.h, ctypes.byref(cs), _ptr(beads.pos), _ptr(vel), nl.h, PRECISION[precision],
+                                ctypes.byref(o), _ptr(E_hist), _ptr(H_hist), _ptr(F),
+                                ctypes.byref(c) if counters else None, _stream(stream)), "fnn_rpmd_run")
+    cnt = {f: getattr(c, f) for f, _ in CMdCounters._fields_} if counters else None
+    return E_hist, H_hist, F, cnt
 
 
 def md_run_ex(ctx: Context, system: DeviceSystem, vel, nl: NeighborList, precision: str, n_steps: int, dt_fs: float,

@@ -235,3 +235,32 @@ def test_water_box_1000_steps_matches_oracle_every_100_steps(fnn):
         worst_f = max(worst_f, float(np.abs(F.cpu().numpy() - r.forces).max()))
         assert cnt["graph_blocks"] == 9
     assert worst_e <= E_TOL_PER_ATOM and worst_f <= 1e-3
+
+
+@pytest.mark.parametrize("name,P,n,rebuild,graph", [("gas24", 4, 8, 3, False), ("water216", 8, 20, 5, True)])
+def test_rpmd_matches_oracle(fnn, name, P, n, rebuild, graph):
+    import torch
+    s = structure(name)
+    rng = np.random.default_rng(12)
+    x0 = (np.asarray(s.pos, np.float64)[None] + 0.02 * rng.standard_normal((P, s.n_atoms, 3))).astype(np.float32)
+    v0 = np.stack([_velocities(s, 50 + b) for b in range(P)]).astype(np.float32)
+    ctx = fnn.Context(1, skin=1.0)
+    fnn.load_weights(ctx, weights(1))
+    ds = fnn.bead_system(s, x0)
+    vel = torch.zeros((P * s.n_atoms, 4), dtype=torch.float32)
+    vel[:, :3] = torch.from_numpy(v0.reshape(-1, 3))
+    vel = vel.cuda()
+    nl = fnn.NeighborList(ctx)
+    stream = torch.cuda.Stream() if graph else None
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+        E, H, F, cnt = fnn.rpmd_run(ctx, ds, vel, nl, "fp32x3", P, n, 0.5, 300.0, rebuild, counters=True,
+                                    stream=stream)
+    fnn.check(ctx, "rpmd", stream=stream)
+    Er, Hr, xr, vr, Fr = oracle.rpmd(s, weights(1), P, x0.astype(np.float64), v0.astype(np.float64), n, 0.5, 300.0)
+    assert np.abs(E.cpu().numpy() - Er).max() / s.n_atoms <= E_TOL_PER_ATOM
+    assert np.abs(H.cpu().numpy() - Hr).max() / (P * s.n_atoms) <= E_TOL_PER_ATOM
+    x = ds.pos[:, :3].cpu().numpy().reshape(P, s.n_atoms, 3)
+    assert np.abs(x - xr).max() <= 1e-4
+    assert np.abs(F.cpu().numpy().reshape(P, s.n_atoms, 3) - Fr).max() <= 1e-3
+    assert cnt["graph_blocks"] == ((n - rebuild) // rebuild if graph else 0)

@@ -60,3 +60,27 @@ def test_switch_variants_energy_forces(fnn, sw, name, M, precision):
     assert np.abs(F.cpu().numpy() - r.forces).max() <= F_TOL
     scale = max(1.0, np.abs(r.virial).max())
     assert np.abs(W.cpu().numpy().reshape(r.virial.shape) - r.virial).max() <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("name,skin,sw", [("gas24", 0.0, "cosine"), ("water216", 1.0, "cosine"),
+                                          ("batch64", 0.5, "polynomial"), ("box1500", 0.0, "exponential"),
+                                          ("box1100", 0.0, "cosine")])
+def test_crate_angular_and_vjp_parity(fnn, name, skin, sw):
+    import torch
+    s = structure(name)
+    P = oracle.Params(switch=sw)
+    rng = np.random.default_rng(11)
+    V = (rng.standard_normal((7, 8, 32)) / 4).astype(np.float32)
+    G = rng.standard_normal((s.n_atoms, 4, 32)).astype(np.float32)
+    ctx = fnn.Context(1, skin=skin, switch=sw)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    Vd, Gd = torch.from_numpy(V).cuda(), torch.from_numpy(G).cuda()
+    g = fnn.crate_angular(ctx, ds, nl, Vd).cpu().numpy()
+    gx, gV = fnn.crate_angular_vjp(ctx, ds, nl, Vd, Gd)
+    fnn.check(ctx)
+    gw, gxw, gVw = oracle.crate_angular(s, V, P, G=G)
+    assert np.abs(g - gw).max() <= 2e-5 * np.abs(gw).max() + 1e-6
+    assert np.abs(gx.cpu().numpy() - gxw).max() <= 1e-4 * np.abs(gxw).max() + 1e-5
+    assert np.abs(gV.cpu().numpy() - gVw).max() <= 1e-4 * np.abs(gVw).max() + 1e-5
