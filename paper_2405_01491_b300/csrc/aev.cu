@@ -325,15 +325,14 @@ __device__ __forceinline__ void store_lo(__nv_bfloat16 *lo, size_t c, float v) {
   if (lo) lo[c] = __float2bfloat16(v - __bfloat162float(__float2bfloat16(v)));
 }
 
+// One warp's share of the forward: rows wg, wg + nw, ..., staged in W (the kernel below, and the fused
+// small-system kernel, call it)
 template <typename OutT>
-__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(AevFwdArgs A) {
-  __shared__ FwdStage smem[AEV_WARPS];
-  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  FwdStage &W = smem[wl];
+__device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw) {
+  int lane = threadIdx.x & 31;
   NbrStageT<false> &S = W.nb;
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
-  int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
   for (int row = wg; row < nrows; row += nw) {
     OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
     __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
@@ -464,6 +463,13 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
   }
 }
 
+template <typename OutT>
+__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(AevFwdArgs A) {
+  __shared__ FwdStage smem[AEV_WARPS];
+  const int wl = threadIdx.x >> 5;
+  aev_forward_rows<OutT>(A, smem[wl], blockIdx.x * AEV_WARPS + wl, gridDim.x * AEV_WARPS);
+}
+
 // ------------------------------------------------------------------------------------- adjoint
 struct AevAdjArgs {
   StageArgs sa;
@@ -479,14 +485,12 @@ struct AevAdjArgs {
 
 // The dE/dAEV row is read through the L1 cache where it is used (4 KB per atom, re-read by the warp's
 // lanes): staging it in shared memory would cap the number of resident warps.
-__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
-  __shared__ AdjStage smem[AEV_WARPS];
-  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  AdjStage &W = smem[wl];
+// One warp's share of the adjoint: rows wg, wg + nw, ..., staged in W
+__device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &W, int wg, int nw) {
+  int lane = threadIdx.x & 31;
   NbrStage &S = W.nb;
   const AevParams &P = A.P;
   int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
-  int wg = blockIdx.x * AEV_WARPS + wl, nw = gridDim.x * AEV_WARPS;
   double *vacc = W.vacc;
   if (lane == 0)
     for (int q = 0; q < 9; q++) vacc[q] = 0.0;
@@ -658,6 +662,12 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
   }
   if (lane == 0 && A.virial && cur_mol >= 0)
     for (int q = 0; q < 9; q++) atomicAdd(&A.virial[9 * (size_t)cur_mol + q], vacc[q]);
+}
+
+__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
+  __shared__ AdjStage smem[AEV_WARPS];
+  const int wl = threadIdx.x >> 5;
+  aev_adjoint_rows(A, smem[wl], blockIdx.x * AEV_WARPS + wl, gridDim.x * AEV_WARPS);
 }
 
 // ------------------------------------------------------------------------------- tangent (JVP)
@@ -858,6 +868,278 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
   }
 }
 
+// ------------------------------------------------------------------------------ small systems
+// Energies, forces and virials of a small system (atoms x members at most SMALL_EVAL_ROWS) in one cooperative
+// launch: the AEV forward, the networks forward (members fused in the first layer) and backward to dE/dAEV in
+// FP32 FFMA, the AEV adjoint and the float64 energies, the stages separated by grid barriers.  A single
+// 128-row tensor-core tile would sit on one SM; here every dense layer is cut into tasks of (member, element,
+// up to 16 of its atoms, 32 output columns) spread over the grid, each reducing K across its 8 warps in a
+// fixed order, so the energies are deterministic.
+constexpr int SE_WARPS = 8, SE_RG = 16;
+constexpr long long SE_BARRIER_LIMIT = 2000000000LL;   // clock64 cycles (about a second) per barrier wait
+
+struct GridBar {
+  unsigned count, gen, abort, pad;
+};
+
+// Every block arrives; the last one releases the others by advancing the generation.  A wait that runs out
+// posts FNN_E_TIMEOUT and raises abort.  Returns false once aborted (every block then leaves).
+__device__ bool grid_barrier(GridBar *b, DevStatus *st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &b->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > SE_BARRIER_LIMIT) {
+          post_status(st, FNN_E_TIMEOUT, -2);
+          atomicExch(&b->abort, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile unsigned *)&b->abort == 0u;
+}
+
+struct SmallEvalArgs {
+  AevFwdArgs fa;
+  AevAdjArgs aa;
+  int N, NM, M;
+  const int32_t *mol_offsets;
+  const uint8_t *elem;
+  const int32_t *inv;      // species-sorted row -> atom (-1 padding)
+  const int32_t *meta;     // META_SEG
+  const float *W1T, *b1, *W2T, *b2, *W3T, *b3, *w4, *b4, *W3, *W2, *W1;
+  float *aev, *h1, *h2, *g3, *g2, *g1, *gaev;   // [N][...] in atom order
+  float *y;                // [N][M] per-member atom energies (stride 4 floats per member)
+  double *E;
+  float *F;
+  double *virial;
+  GridBar *bar;
+  DevStatus *st;
+};
+
+struct SmallDense {
+  float red[SE_WARPS][SE_RG][32];
+  int rows[SE_RG];
+  float ypart[SE_WARPS][SE_RG];
+};
+union SmallShared {
+  FwdStage fwd[SE_WARPS];
+  AdjStage adj[SE_WARPS];
+  SmallDense d;
+};
+
+// Task t of a layer over the element row groups: member, element, row group (atoms rows[0..R)), column chunk.
+struct SmallTask {
+  int m, e, R, chunk;
+};
+__device__ bool small_task(const SmallEvalArgs &A, const int *ecount, int t, int n_chunks, int members,
+                           SmallTask &k, int *rows) {
+  int per_m = 0;
+  for (int e = 0; e < NE; e++) per_m += (ecount[e] + SE_RG - 1) / SE_RG * n_chunks;
+  if (t >= per_m * members) return false;
+  k.m = t / per_m;
+  int u = t - k.m * per_m;
+  for (int e = 0; e < NE; e++) {
+    const int g = (ecount[e] + SE_RG - 1) / SE_RG;
+    if (u < g * n_chunks) {
+      const int rg = u / n_chunks;
+      k.e = e;
+      k.chunk = u - rg * n_chunks;
+      k.R = min(SE_RG, ecount[e] - rg * SE_RG);
+      const int base = A.meta[META_SEG + e] + rg * SE_RG;
+      if (threadIdx.x < SE_RG) rows[threadIdx.x] = threadIdx.x < k.R ? A.inv[base + threadIdx.x] : 0;
+      return true;
+    }
+    u -= g * n_chunks;
+  }
+  return false;
+}
+
+// acc[r] = sum over this warp's slice of k of A[rows[r]][a_off + k] * B[k][col] (K, a_off, lda multiples of 4)
+__device__ __forceinline__ void small_dot(const float *A, int lda, int a_off, const int *rows, int R, int K,
+                                          const float *B, int ldb, int col, bool colok, float acc[SE_RG]) {
+  const int warp = threadIdx.x >> 5;
+  const int ks = ((K + SE_WARPS - 1) / SE_WARPS + 3) & ~3;
+  const int k0 = warp * ks, k1 = min(K, k0 + ks);
+#pragma unroll
+  for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
+  for (int k = k0; k < k1; k += 4) {
+    float b[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) b[u] = colok ? __ldg(B + (size_t)(k + u) * ldb + col) : 0.f;
+#pragma unroll
+    for (int r = 0; r < SE_RG; r++) {
+      if (r < R) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(A + (size_t)rows[r] * lda + a_off + k));
+        acc[r] = fmaf(a.x, b[0], acc[r]);
+        acc[r] = fmaf(a.y, b[1], acc[r]);
+        acc[r] = fmaf(a.z, b[2], acc[r]);
+        acc[r] = fmaf(a.w, b[3], acc[r]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
+// CELU' from the activation h = CELU(z): 1 for z > 0, exp(z / alpha) = 1 + h / alpha otherwise
+__device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : fmaf(h, CELU_INV_ALPHA, 1.f); }
+
+// One dense layer over every (member, element row group, 32-column chunk) task of the grid.
+// kind 0: out = CELU(A B + bias); 1: out = (A B) * CELU'(aux); 2: out = A B
+__device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ecount, int kind, const float *Ab,
+                            int lda, int a_member_off, int K, const float *Bb, long long b_me_stride, int ldb,
+                            int ncol, const float *bias, long long bias_me_stride, const float *aux, int ldaux,
+                            int aux_member_off, float *out, int ldo, int o_member_off, int members) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_chunks = (ncol + 31) / 32;
+  for (int t = blockIdx.x;; t += gridDim.x) {
+    SmallTask k;
+    __syncthreads();
+    const bool ok = small_task(A, ecount, t, n_chunks, members, k, D.rows);
+    __syncthreads();
+    if (!ok) break;
+    const int col = k.chunk * 32 + lane;
+    const bool colok = col < ncol;
+    const float *B = Bb + (long long)(k.m * NE + k.e) * b_me_stride;
+    float acc[SE_RG];
+    small_dot(Ab, lda, k.m * a_member_off, D.rows, k.R, K, B, ldb, col, colok, acc);
+#pragma unroll
+    for (int r = 0; r < SE_RG; r++) D.red[warp][r][lane] = acc[r];
+    __syncthreads();
+    for (int q = threadIdx.x; q < k.R * 32; q += blockDim.x) {
+      const int r = q >> 5, l = q & 31, c = k.chunk * 32 + l;
+      if (c >= ncol) continue;
+      float z = 0.f;
+#pragma unroll
+      for (int w = 0; w < SE_WARPS; w++) z += D.red[w][r][l];   // fixed order
+      const int row = D.rows[r];
+      float v;
+      if (kind == 0) v = celu_f(z + bias[(long long)(k.m * NE + k.e) * bias_me_stride + c]);
+      else if (kind == 1) v = z * dcelu_h(aux[(size_t)row * ldaux + k.m * aux_member_off + c]);
+      else v = z;
+      out[(size_t)row * ldo + k.m * o_member_off + c] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A) {
+  extern __shared__ __align__(16) unsigned char small_eval_dyn[];
+  SmallShared &S = *reinterpret_cast<SmallShared *>(small_eval_dyn);
+  __shared__ int ecount[NE];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wg = blockIdx.x * SE_WARPS + warp, nw = gridDim.x * SE_WARPS;
+  const int M = A.M, N = A.N;
+  // element counts (every block, from the species segments' occupancy)
+  if (threadIdx.x < NE) ecount[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&ecount[A.elem[i]], 1);
+  // zero the accumulated outputs
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * N; q += gridDim.x * blockDim.x) A.F[q] = 0.f;
+  if (A.virial)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 9 * A.NM; q += gridDim.x * blockDim.x) A.virial[q] = 0.0;
+  // AEV rows (atom order)
+  aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw);
+  if (!grid_barrier(A.bar, A.st)) return;
+  SmallDense &D = S.d;
+  const int MH1 = M * H1;
+  // first layer, all members fused: h1 = CELU(aev W1^T + b1), [N][M 256]
+  small_layer(A, D, ecount, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0,
+              0, A.h1, MH1, 0, 1);
+  if (!grid_barrier(A.bar, A.st)) return;
+  // second layer per member: h2 = CELU(h1_m W2^T + b2), [N][M 192]
+  small_layer(A, D, ecount, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2,
+              M * H2, H2, M);
+  if (!grid_barrier(A.bar, A.st)) return;
+  // third layer per member, all 160 columns in one block (five warps, full K): h3, the output layer's dot
+  // product in a fixed order, and g3 = (1/M) w4 CELU'(z3)
+  {
+    for (int t = blockIdx.x;; t += gridDim.x) {
+      SmallTask k;
+      __syncthreads();
+      const bool ok = small_task(A, ecount, t, 1, M, k, D.rows);
+      __syncthreads();
+      if (!ok) break;
+      const long long me = (long long)(k.m * NE + k.e);
+      if (warp < H3 / 32) {
+        const int col = warp * 32 + lane;
+        float acc[SE_RG];
+#pragma unroll
+        for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
+        const float *B = A.W3T + me * H2 * H3;
+        for (int kk = 0; kk < H2; kk += 4) {
+          float b[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) b[u] = __ldg(B + (size_t)(kk + u) * H3 + col);
+#pragma unroll
+          for (int r = 0; r < SE_RG; r++)
+            if (r < k.R) {
+              const float4 a = __ldg(reinterpret_cast<const float4 *>(A.h2 + (size_t)D.rows[r] * (M * H2) + k.m * H2 + kk));
+              acc[r] = fmaf(a.x, b[0], fmaf(a.y, b[1], fmaf(a.z, b[2], fmaf(a.w, b[3], acc[r]))));
+            }
+        }
+        const float bb = A.b3[me * H3 + col], w = A.w4[me * H3 + col];
+#pragma unroll
+        for (int r = 0; r < SE_RG; r++) {
+          if (r < k.R) {
+            const float z = acc[r] + bb;
+            const float h = celu_f(z);
+            A.g3[(size_t)D.rows[r] * (M * H3) + k.m * H3 + col] = w * dcelu_h(h) / (float)M;
+            float p = w * h;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == 0) D.ypart[warp][r] = p;
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < k.R) {
+        float yv = A.b4[me];
+        for (int w = 0; w < H3 / 32; w++) yv += D.ypart[w][threadIdx.x];
+        A.y[((size_t)D.rows[threadIdx.x] * M + k.m) * 4] = yv;
+      }
+    }
+  }
+  if (!grid_barrier(A.bar, A.st)) return;
+  // third layer's input gradient: g2 = (g3 W3) * CELU'(h2)
+  small_layer(A, D, ecount, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2,
+              A.g2, M * H2, H2, M);
+  if (!grid_barrier(A.bar, A.st)) return;
+  // second layer's: g1 = (g2 W2) * CELU'(h1)
+  small_layer(A, D, ecount, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1,
+              A.g1, MH1, H1, M);
+  if (!grid_barrier(A.bar, A.st)) return;
+  // first layer's, summed over the members: dE/dAEV = g1 W1 (K = M 256 through the member-concatenated W1)
+  small_layer(A, D, ecount, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
+              A.gaev, NAEV, 0, 1);
+  if (!grid_barrier(A.bar, A.st)) return;
+  // forces and virials; energies in a fixed order (a thread per structure)
+  __syncthreads();
+  aev_adjoint_rows(A.aa, S.adj[warp], wg, nw);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < A.NM; m += gridDim.x * blockDim.x) {
+    const int a0 = max(A.mol_offsets[m], 0), a1 = min(A.mol_offsets[m + 1], N);
+    double e = 0.0;
+    for (int i = a0; i < a1; i++) {
+      double yi = 0.0;
+      for (int q = 0; q < M; q++) yi += (double)A.y[((size_t)i * M + q) * 4];
+      e += yi / (double)M;
+    }
+    A.E[m] = e;
+    if (!isfinite(e)) post_status(A.st, FNN_E_NONFINITE, -(long long)(m + 1));
+  }
+}
+
 static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
   StageArgs s;
   s.cap = nl->capacity;
@@ -993,6 +1275,99 @@ fnn_status launch_aev_tangent(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
 fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *V,
                                    __nv_bfloat16 *out, __nv_bfloat16 *out_fwd, const int32_t *inv, cudaStream_t s) {
   return tangent<__nv_bfloat16>(ctx, sys, nl, V, out, out_fwd, inv, s);
+}
+
+
+fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, float *F,
+                             double *virial, cudaStream_t s) {
+  const int N = sys->n_atoms, M = ctx->cfg.n_members;
+  if (!ctx->grid_bar) FNN_CUDA_TRY(ctx, cudaMalloc(&ctx->grid_bar, 256));
+  const size_t dyn = sizeof(SmallShared);
+  static bool attr_set = false;
+  static int per_sm = 0;
+  if (!attr_set) {
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(k_small_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_eval, SE_WARPS * 32, dyn));
+    attr_set = true;
+  }
+  if (per_sm < 1) {
+    ctx->last_error = "small-system kernel does not fit on an SM";
+    return FNN_E_CUDA;
+  }
+  Workspace &ws = ctx->ws;
+  const DeviceWeights &w = ctx->w;
+  SmallEvalArgs a{};
+  a.fa.sa = stage_args(sys, nl);
+  a.fa.P = ctx->aev;
+  a.fa.out = ws.aev;
+  a.fa.out_lo = nullptr;
+  a.fa.out_inv = 1.f;
+  a.fa.inv = nullptr;
+  a.fa.meta = nl->meta;
+  a.fa.n_atoms = N;
+  a.fa.st = ctx->status;
+  a.aa.sa = a.fa.sa;
+  a.aa.P = ctx->aev;
+  a.aa.gaev = ws.gaev;
+  a.aa.inv = nullptr;
+  a.aa.meta = nl->meta;
+  a.aa.n_atoms = N;
+  a.aa.F = F;
+  a.aa.virial = virial;
+  a.aa.st = ctx->status;
+  a.N = N;
+  a.NM = sys->n_mol;
+  a.M = M;
+  a.mol_offsets = sys->mol_offsets;
+  a.elem = nl->elem;
+  a.inv = nl->inv;
+  a.meta = nl->meta;
+  a.W1T = w.W1Tcat;
+  a.b1 = w.b1cat;
+  a.W2T = w.W2T;
+  a.b2 = w.b2;
+  a.W3T = w.W3T;
+  a.b3 = w.b3;
+  a.w4 = w.w4;
+  a.b4 = w.b4;
+  a.W3 = w.W3;
+  a.W2 = w.W2;
+  a.W1 = w.W1cat;
+  a.aev = ws.aev;
+  a.h1 = ws.h1;
+  a.h2 = ws.h2;
+  a.g3 = ws.g3;
+  a.g2 = ws.g2;
+  a.g1 = ws.g1;
+  a.gaev = ws.gaev;
+  a.y = ws.ypart;
+  a.E = E;
+  a.F = F;
+  a.virial = virial;
+  a.bar = reinterpret_cast<GridBar *>(ctx->grid_bar);
+  a.st = ctx->status;
+  // a grid no larger than the widest layer needs (and co-resident: a cooperative launch)
+  const int row_groups = (N + SE_RG - 1) / SE_RG + NE;
+  int grid = row_groups * (NAEV + 31) / 32;
+  const int cap = per_sm * ctx->num_sms < 128 ? per_sm * ctx->num_sms : 128;
+  if (grid > cap) grid = cap;
+  FNN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), s));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(SE_WARPS * 32);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  {
+    FNN_KERNEL(ctx, "small_eval", s);
+    FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_small_eval, a));
+  }
+  (void)M;
+  return check_launch(ctx, "small_eval");
 }
 
 }  // namespace fnn

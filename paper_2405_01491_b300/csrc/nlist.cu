@@ -993,6 +993,244 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
   }
 }
 
+// ------------------------------------------------------------------ small systems: the build in one block
+// At most SMALL_BUILD_ATOMS atoms in SMALL_BUILD_MOL structures: every stage of the build in one block of
+// 1024 threads -- the global offsets check, per-atom setup, per-structure images and predicate band
+// (make_grid), each atom's neighbours by brute force over its structure with the same predicate
+// (pair_in: the same set), row offsets by a block scan, rows of at most PAIR_STRIDE entries sorted by
+// neighbour element (stable; longer rows in atom order), and the species order of the networks.
+// One launch instead of the cell-list pipeline's thirteen, for systems whose cost is launch latency.
+constexpr int SMALL_NT = 1024;
+struct SmallBuildShared {
+  float bb[SMALL_BUILD_MOL][6];
+  MolGrid g[SMALL_BUILD_MOL];
+  int32_t am[SMALL_BUILD_ATOMS];
+  int32_t start[SMALL_BUILD_ATOMS + 1];
+  uint8_t el[SMALL_BUILD_ATOMS];
+  int32_t stage_j[SMALL_NT / 32][PAIR_STRIDE];
+  char4 stage_s[SMALL_NT / 32][PAIR_STRIDE];
+  int ecount[8], eseg[8];
+};
+static_assert(SMALL_BUILD_ATOMS <= SMALL_NT, "one atom per thread in the scans");
+
+__global__ void __launch_bounds__(SMALL_NT, 1)
+    k_small_build(fnn_system sys, double R, PredConst pc, int64_t cap, int32_t *atom_mol, uint8_t *elem,
+                  MolGrid *grid, int32_t *row_ptr, int32_t *nbr, char4 *shift, int32_t *perm, int32_t *inv,
+                  int32_t *tile_elem, int ntiles_cap, int pad_cap, int32_t *meta, DevStatus *st) {
+  extern __shared__ __align__(16) unsigned char small_build_dyn[];
+  SmallBuildShared &S = *reinterpret_cast<SmallBuildShared *>(small_build_dyn);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = SMALL_NT / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  const int N = sys.n_atoms, NM = sys.n_mol;
+  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  // offsets start at 0, end at N and never decrease; otherwise no atom belongs to a structure
+  int badl = 0;
+  for (int m = tid; m <= NM; m += SMALL_NT) {
+    const int a = sys.mol_offsets[m];
+    bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
+    if (m == NM) ok = ok && a == N;
+    if (!ok) {
+      post_status(st, FNN_E_INVALID, m);
+      badl = 1;
+    }
+  }
+  for (int m = tid; m < NM; m += SMALL_NT)
+    for (int a = 0; a < 3; a++) {
+      S.bb[m][a] = __int_as_float(0x7f800000);
+      S.bb[m][3 + a] = __int_as_float((int)0xff800000);
+    }
+  if (tid < 8) S.ecount[tid] = 0;
+  const bool bad = __syncthreads_or(badl) != 0;
+  // per atom: structure, element, checks, bounding boxes
+  for (int i = tid; i < N; i += SMALL_NT) {
+    int m = -1, e = 0;
+    if (!bad) {
+      int lo = 0, hi = NM;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys.mol_offsets[mid] <= i) lo = mid; else hi = mid;
+      }
+      if (sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
+    }
+    if (m >= 0) {
+      e = element_of(sys.Z[i]);
+      if (e < 0) {
+        post_status(st, FNN_E_SPECIES, i);
+        e = 0;
+      }
+      const float4 p = pos[i];
+      if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) post_status(st, FNN_E_NONFINITE, i);
+      atomic_fmin(&S.bb[m][0], p.x);
+      atomic_fmin(&S.bb[m][1], p.y);
+      atomic_fmin(&S.bb[m][2], p.z);
+      atomic_fmax(&S.bb[m][3], p.x);
+      atomic_fmax(&S.bb[m][4], p.y);
+      atomic_fmax(&S.bb[m][5], p.z);
+    }
+    S.am[i] = m;
+    S.el[i] = (uint8_t)e;
+    atom_mol[i] = m;
+    elem[i] = (uint8_t)e;
+    atomicAdd(&S.ecount[e], 1);
+  }
+  __syncthreads();
+  // per structure: images and the predicate band, exactly as the cell-list build takes them
+  for (int m = tid; m < NM; m += SMALL_NT) {
+    const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    MolGrid g = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
+    if (!bad && a0 >= 0 && a1 >= a0 && a1 <= N) {
+      const int pbc = sys.pbc ? (sys.pbc[m] != 0) : 0;
+      float bb[6];
+      for (int a = 0; a < 6; a++) bb[a] = S.bb[m][a];
+      int cells;
+      g = make_grid(sys, m, a1 - a0, pbc, bb, R, st, &cells);
+    }
+    S.g[m] = g;
+    grid[m] = g;
+  }
+  __syncthreads();
+  // pass 1: neighbour counts, a warp per atom over the atoms of its structure
+  for (int i = warp; i < N; i += nwarp) {
+    const int m = S.am[i];
+    int count = 0;
+    if (m >= 0) {
+      const MolGrid g = S.g[m];
+      const float4 pi = pos[i];
+      const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+      for (int j0 = a0; j0 < a1; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        float nx, ny, nz;
+        if (j < a1) in = pair_in(pi, pos[j], g, pc, nx, ny, nz) && j != i;
+        count += __popc(__ballot_sync(FULL, in));
+      }
+    }
+    if (lane == 0) S.start[i] = count;
+  }
+  __syncthreads();
+  // row offsets and the entry count
+  {
+    const int v = tid < N ? S.start[tid] : 0;
+    int tot;
+    const int ex = block_excl_scan<SMALL_NT>(v, &tot);
+    if (tid < N) {
+      S.start[tid] = ex;
+      row_ptr[tid] = ex;
+    }
+    if (tid == 0) {
+      S.start[N] = tot;
+      row_ptr[N] = tot;
+      meta[META_NNZ] = tot;
+      if ((int64_t)tot > cap) post_status(st, FNN_E_CAPACITY, tot);
+    }
+  }
+  __syncthreads();
+  // pass 2: the entries (none when the list is over capacity: the status says so)
+  const bool fill = (int64_t)S.start[N] <= cap;
+  for (int i = warp; fill && i < N; i += nwarp) {
+    const int m = S.am[i];
+    if (m < 0) continue;   // uniform over the warp
+    const MolGrid g = S.g[m];
+    const float4 pi = pos[i];
+    const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    const int64_t dst = S.start[i];
+    const int n = S.start[i + 1] - S.start[i];
+    const bool sortable = n <= PAIR_STRIDE;
+    int at = 0;
+    for (int j0 = a0; j0 < a1; j0 += 32) {
+      const int j = j0 + lane;
+      bool in = false;
+      float nx = 0.f, ny = 0.f, nz = 0.f;
+      if (j < a1) in = pair_in(pi, pos[j], g, pc, nx, ny, nz) && j != i;
+      const unsigned mask = __ballot_sync(FULL, in);
+      if (in) {
+        const int idx = at + __popc(mask & lt);
+        if (sortable) {
+          S.stage_j[warp][idx] = j;
+          S.stage_s[warp][idx] = make_shift(nx, ny, nz);
+        } else {
+          nbr[dst + idx] = j;
+          shift[dst + idx] = make_shift(nx, ny, nz);
+        }
+      }
+      at += __popc(mask);
+    }
+    __syncwarp();
+    if (sortable) {   // stable counting sort of the staged row by neighbour element
+      constexpr int NCH = PAIR_STRIDE / 32;
+      int jv[NCH], ev[NCH];
+      char4 sv[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        const int k = 32 * c + lane;
+        jv[c] = k < n ? S.stage_j[warp][k] : 0;
+        sv[c] = k < n ? S.stage_s[warp][k] : make_char4(0, 0, 0, 0);
+        ev[c] = k < n ? (int)S.el[jv[c]] : -1;
+      }
+      int off[NE];
+#pragma unroll
+      for (int q = 0; q < NE; q++) off[q] = 0;
+#pragma unroll
+      for (int c = 0; c < NCH; c++)
+#pragma unroll
+        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, ev[c] == q));
+      int run = 0;
+#pragma unroll
+      for (int q = 0; q < NE; q++) {
+        const int c = off[q];
+        off[q] = run;
+        run += c;
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        int w = 0;
+#pragma unroll
+        for (int q = 0; q < NE; q++) {
+          const unsigned mq = __ballot_sync(FULL, ev[c] == q);
+          if (ev[c] == q) w = off[q] + __popc(mq & lt);
+          off[q] += __popc(mq);
+        }
+        if (ev[c] >= 0) {
+          nbr[dst + w] = jv[c];
+          shift[dst + w] = sv[c];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // species order: element segments padded to ROW_TILE rows, atoms in index order within each
+  if (tid == 0) {
+    int s0 = 0;
+    for (int e = 0; e < NE; e++) {
+      S.eseg[e] = s0;
+      meta[META_SEG + e] = s0;
+      s0 += (S.ecount[e] + ROW_TILE - 1) / ROW_TILE * ROW_TILE;
+    }
+    S.eseg[NE] = s0;
+    meta[META_SEG + NE] = s0;
+    meta[META_NPAD] = s0;
+  }
+  for (int r = tid; r < pad_cap; r += SMALL_NT) inv[r] = -1;
+  __syncthreads();
+  for (int e = 0; e < NE; e++) {
+    const int flag = (tid < N && S.el[tid] == e) ? 1 : 0;
+    int tot;
+    const int rank = block_excl_scan<SMALL_NT>(flag, &tot);
+    if (flag) {
+      const int row = S.eseg[e] + rank;
+      perm[tid] = row;
+      inv[row] = tid;
+    }
+  }
+  for (int t = tid; t < ntiles_cap; t += SMALL_NT) {
+    const int r = t * ROW_TILE;
+    int e = -1;
+    for (int q = 0; q < NE; q++)
+      if (r >= S.eseg[q] && r < S.eseg[q + 1]) e = q;
+    tile_elem[t] = e;
+  }
+}
+
 // rows of at most PAIR_STRIDE entries sorted by neighbour element in place (stable), as the staged
 // compaction leaves them: the whole row is read into registers before any entry is written back
 __global__ void __launch_bounds__(256) k_sort_rows(int n_atoms, const int32_t *row_ptr, const uint8_t *elem,
@@ -1268,6 +1506,20 @@ extern "C" fnn_status fnn_build_neighbors(fnn_ctx *ctx, const fnn_system *sys, f
   nl->stream = s;
   nl->built = true;
 
+  if (N > 0 && N <= SMALL_BUILD_ATOMS && NM <= SMALL_BUILD_MOL) {   // one launch for small systems
+    const size_t dyn = sizeof(SmallBuildShared);
+    static bool attr_set = false;
+    if (!attr_set) {
+      FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(k_small_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      attr_set = true;
+    }
+    PredConst pc{R * R, (float)(R * R), (float)R};
+    FNN_KERNEL(ctx, "small_build", s);
+    k_small_build<<<1, SMALL_NT, dyn, s>>>(*sys, R, pc, nl->capacity, nl->atom_mol, nl->elem, nl->grid, nl->row_ptr,
+                                           nl->nbr, nl->shift, nl->perm, nl->inv, nl->tile_elem,
+                                           nl->pad_cap / ROW_TILE, nl->pad_cap, nl->meta, ctx->status);
+    return check_launch(ctx, "fnn_build_neighbors");
+  }
   // cells are bounded by 2N + n_mol + 1 by construction (k_mol_grid caps each structure at max(1, 2n));
   // the structure, cell and row scans each have their own third of the scratch, all cleared by the first
   // kernel

@@ -282,3 +282,42 @@ def test_fp8_and_fp32_forms_agree_on_the_full_box(fnn):
     rel = np.sqrt(np.mean((F8 - F32) ** 2) / np.mean(F32 ** 2))
     print(f"fp8 mix23558: |dE|/atom={abs(E8[0] - E32[0]) / s.n_atoms:.2e} rms rel F={rel:.2e}")
     assert abs(E8[0] - E32[0]) / s.n_atoms <= 0.16 and rel <= 0.48
+
+
+@pytest.mark.parametrize("M,precision", [(1, "fp32"), (1, "fp32x3"), (2, "fp32x3")])
+def test_small_system_path_matches_oracle(fnn, M, precision):
+    """Systems of at most 256 atoms (atoms x members at most 256) take the one-block list build and the single
+    cooperative evaluation kernel: the same list set and the oracle's energies, forces and virials."""
+    rng = np.random.default_rng(61)
+    parts = [structure("gas24"), synth.random_molecule(rng, 8), synth.random_molecule(rng, 40)]
+    if M == 1:
+        parts.append(synth.random_molecule(rng, 150, periodic=True))
+    s = synth.concat(parts, "small")
+    assert s.n_atoms * M <= 256
+    w = weights(M)
+    ctx = fnn.Context(M, skin=0.5)
+    fnn.load_weights(ctx, w)
+    ds = fnn.DeviceSystem.from_structures(s)
+    nl = fnn.NeighborList(ctx)
+    fnn.profile_read(ctx)
+    fnn.profile_enable(ctx, True)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    E, F, W = fnn.energy_forces(ctx, ds, nl, precision)
+    fnn.check(ctx)
+    fnn.profile_enable(ctx, False)
+    names = set(fnn.profile_read(ctx))
+    assert {"small_build", "small_eval"} <= names, names
+    row_ptr, nbr, shift = fnn.nlist_export(nl, s.n_atoms)
+    ei = np.repeat(np.arange(s.n_atoms), np.diff(row_ptr))
+    assert as_set(ei, nbr, shift) == as_set(*oracle.neighbors(s, 5.6))
+    # rows (all under 128 entries here) sorted by neighbour element
+    el = oracle.elements(s.Z)
+    for i in range(s.n_atoms):
+        e = el[nbr[row_ptr[i]:row_ptr[i + 1]]]
+        assert np.all(np.diff(e) >= 0)
+    r = oracle.energy_forces(s, w)
+    _compare(s, r, E.cpu().numpy(), F.cpu().numpy(), W.cpu().numpy())
+    # energies are deterministic: a second evaluation gives the same bits
+    E2, _, _ = fnn.energy_forces(ctx, ds, nl, precision)
+    fnn.check(ctx)
+    np.testing.assert_array_equal(E2.cpu().numpy(), E.cpu().numpy())
