@@ -887,8 +887,7 @@ struct GridBar {
 __device__ bool grid_barrier(GridBar *b, DevStatus *st) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = &b->gen;
-    const unsigned g = *vgen;
+    const unsigned g = *(volatile unsigned *)&b->gen;
     __threadfence();
     if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
       atomicExch(&b->count, 0u);
@@ -896,13 +895,15 @@ __device__ bool grid_barrier(GridBar *b, DevStatus *st) {
       atomicAdd(&b->gen, 1u);
     } else {
       const long long t0 = clock64();
-      while (*vgen == g) {
+      unsigned cur;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&b->gen) : "memory");
+        if (cur != g) break;
         if (clock64() - t0 > SE_BARRIER_LIMIT) {
           post_status(st, FNN_E_TIMEOUT, -2);
           atomicExch(&b->abort, 1u);
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -917,11 +918,11 @@ struct SmallEvalArgs {
   int N, NM, M;
   const int32_t *mol_offsets;
   const uint8_t *elem;
-  const int32_t *inv;      // species-sorted row -> atom (-1 padding)
+  const int32_t *perm;     // atom -> species-sorted row
   const int32_t *meta;     // META_SEG
   const float *W1T, *b1, *W2T, *b2, *W3T, *b3, *w4, *b4, *W3, *W2, *W1;
   float *aev, *h1, *h2, *g3, *g2, *g1, *gaev;   // [N][...] in atom order
-  float *y;                // [N][M] per-member atom energies (stride 4 floats per member)
+  float *ysl;              // [N][M][SE_YCH] output-layer partial sums per third-layer column chunk
   double *E;
   float *F;
   double *virial;
@@ -929,10 +930,17 @@ struct SmallEvalArgs {
   DevStatus *st;
 };
 
+constexpr int SE_KC = 1024;  // K staged at once (a longer K -- the first layer's input gradient above four
+                             // members -- in steps of SE_KC, each waited for)
+constexpr int SE_YCH = H3 / 32;   // third-layer column chunks: output-layer partial sums per row and member
 struct SmallDense {
+  float As[SE_RG][SE_KC];
+  float Bs[SE_KC][32];
   float red[SE_WARPS][SE_RG][32];
+  float tmp[SE_RG][33];
+  float ep_bias[32], ep_w4[32];   // the epilogue's bias and output-layer weights of the chunk
+  float ep_aux[SE_RG][32];        // and its CELU' operand rows
   int rows[SE_RG];
-  float ypart[SE_WARPS][SE_RG];
 };
 union SmallShared {
   FwdStage fwd[SE_WARPS];
@@ -944,8 +952,8 @@ union SmallShared {
 struct SmallTask {
   int m, e, R, chunk;
 };
-__device__ bool small_task(const SmallEvalArgs &A, const int *ecount, int t, int n_chunks, int members,
-                           SmallTask &k, int *rows) {
+__device__ bool small_task(const SmallEvalArgs &A, const int *ecount, const int *estart, const int *srow, int t,
+                           int n_chunks, int members, SmallTask &k, int *rows) {
   int per_m = 0;
   for (int e = 0; e < NE; e++) per_m += (ecount[e] + SE_RG - 1) / SE_RG * n_chunks;
   if (t >= per_m * members) return false;
@@ -958,8 +966,8 @@ __device__ bool small_task(const SmallEvalArgs &A, const int *ecount, int t, int
       k.e = e;
       k.chunk = u - rg * n_chunks;
       k.R = min(SE_RG, ecount[e] - rg * SE_RG);
-      const int base = A.meta[META_SEG + e] + rg * SE_RG;
-      if (threadIdx.x < SE_RG) rows[threadIdx.x] = threadIdx.x < k.R ? A.inv[base + threadIdx.x] : 0;
+      const int base = estart[e] + rg * SE_RG;
+      if (threadIdx.x < SE_RG) rows[threadIdx.x] = threadIdx.x < k.R ? srow[base + threadIdx.x] : 0;
       return true;
     }
     u -= g * n_chunks;
@@ -967,69 +975,127 @@ __device__ bool small_task(const SmallEvalArgs &A, const int *ecount, int t, int
   return false;
 }
 
-// acc[r] = sum over this warp's slice of k of A[rows[r]][a_off + k] * B[k][col] (K, a_off, lda multiples of 4)
-__device__ __forceinline__ void small_dot(const float *A, int lda, int a_off, const int *rows, int R, int K,
-                                          const float *B, int ldb, int col, bool colok, float acc[SE_RG]) {
-  const int warp = threadIdx.x >> 5;
-  const int ks = ((K + SE_WARPS - 1) / SE_WARPS + 3) & ~3;
-  const int k0 = warp * ks, k1 = min(K, k0 + ks);
-#pragma unroll
-  for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
-  for (int k = k0; k < k1; k += 4) {
-    float b[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) b[u] = colok ? __ldg(B + (size_t)(k + u) * ldb + col) : 0.f;
-#pragma unroll
-    for (int r = 0; r < SE_RG; r++) {
-      if (r < R) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(A + (size_t)rows[r] * lda + a_off + k));
-        acc[r] = fmaf(a.x, b[0], acc[r]);
-        acc[r] = fmaf(a.y, b[1], acc[r]);
-        acc[r] = fmaf(a.z, b[2], acc[r]);
-        acc[r] = fmaf(a.w, b[3], acc[r]);
-      }
-    }
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// copies of one K chunk [kc0, kc0 + kn) into buffer b: the rows' A values and the 32 columns of B (zeros past
+// ncol; every offset is a multiple of four floats, so each copy is 16 aligned bytes)
+__device__ __forceinline__ void small_stage(SmallDense &D, const float *A, int lda, int a_off, int R,
+                                            const float *B, int ldb, int c0, int ncol, int kc0, int kn) {
+  const int kq = kn / 4;
+  for (int q = threadIdx.x; q < R * kq; q += blockDim.x) {
+    const int r = q / kq, k4 = (q - r * kq) * 4;
+    cp16(&D.As[r][k4], A + (size_t)D.rows[r] * lda + a_off + kc0 + k4);
   }
+  for (int q = threadIdx.x; q < kn * 8; q += blockDim.x) {
+    const int k = q >> 3, c4 = (q & 7) * 4;
+    if (c0 + c4 < ncol) cp16(&D.Bs[k][c4], B + (size_t)(kc0 + k) * ldb + c0 + c4);
+    else *reinterpret_cast<float4 *>(&D.Bs[k][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  cp_commit();
 }
 
 __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
 // CELU' from the activation h = CELU(z): 1 for z > 0, exp(z / alpha) = 1 + h / alpha otherwise
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : fmaf(h, CELU_INV_ALPHA, 1.f); }
 
-// One dense layer over every (member, element row group, 32-column chunk) task of the grid.
-// kind 0: out = CELU(A B + bias); 1: out = (A B) * CELU'(aux); 2: out = A B
-__device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ecount, int kind, const float *Ab,
+// One dense layer over every (member, element row group, 32-column chunk) task of the grid; K in staged
+// chunks, each warp a slice of every chunk, the warps' partial sums added in a fixed order.
+// kind 0: out = CELU(A B + bias); 1: out = (A B) * CELU'(aux); 2: out = A B;
+// 3 (third layer): h = CELU(A B + bias), out = w4 CELU'(h) / M, and the output layer's sum of w4 h over the
+// chunk's columns into ysl[(row M + m) SE_YCH + chunk]
+__device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ecount, const int *estart,
+                            const int *srow, int kind, const float *Ab,
                             int lda, int a_member_off, int K, const float *Bb, long long b_me_stride, int ldb,
                             int ncol, const float *bias, long long bias_me_stride, const float *aux, int ldaux,
-                            int aux_member_off, float *out, int ldo, int o_member_off, int members) {
+                            int aux_member_off, float *out, int ldo, int o_member_off, int members, float *ysl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_chunks = (ncol + 31) / 32;
+  const int nkc = (K + SE_KC - 1) / SE_KC;
   for (int t = blockIdx.x;; t += gridDim.x) {
     SmallTask k;
     __syncthreads();
-    const bool ok = small_task(A, ecount, t, n_chunks, members, k, D.rows);
+    const bool ok = small_task(A, ecount, estart, srow, t, n_chunks, members, k, D.rows);
     __syncthreads();
     if (!ok) break;
-    const int col = k.chunk * 32 + lane;
-    const bool colok = col < ncol;
-    const float *B = Bb + (long long)(k.m * NE + k.e) * b_me_stride;
+    const int c0 = k.chunk * 32;
+    const long long me = (long long)(k.m * NE + k.e);
+    const float *B = Bb + me * b_me_stride;
+    const int a_off = k.m * a_member_off;
     float acc[SE_RG];
-    small_dot(Ab, lda, k.m * a_member_off, D.rows, k.R, K, B, ldb, col, colok, acc);
+#pragma unroll
+    for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
+    // the epilogue's operands travel with the first operand copies
+    if (threadIdx.x < 8) {
+      const int c4 = threadIdx.x * 4;
+      if (c0 + c4 < ncol) {
+        if (kind == 0 || kind == 3) cp16(&D.ep_bias[c4], bias + me * bias_me_stride + c0 + c4);
+        if (kind == 3) cp16(&D.ep_w4[c4], A.w4 + me * H3 + c0 + c4);
+      }
+    }
+    if (kind == 1)
+      for (int q = threadIdx.x; q < k.R * 8; q += blockDim.x) {
+        const int r = q >> 3, c4 = (q & 7) * 4;
+        if (c0 + c4 < ncol) cp16(&D.ep_aux[r][c4], aux + (size_t)D.rows[r] * ldaux + k.m * aux_member_off + c0 + c4);
+      }
+    for (int c = 0; c < nkc; c++) {
+      const int kc0 = c * SE_KC, kn = min(SE_KC, K - kc0);
+      small_stage(D, Ab, lda, a_off, k.R, B, ldb, c0, ncol, kc0, kn);
+      cp_wait0();
+      __syncthreads();
+      // warp w takes every SE_WARPS-th group of four k (interleaved: every warp busy for any kn)
+      for (int kk = 4 * warp; kk < kn; kk += 4 * SE_WARPS) {
+        const float b0 = D.Bs[kk][lane], b1 = D.Bs[kk + 1][lane], b2 = D.Bs[kk + 2][lane], b3 = D.Bs[kk + 3][lane];
+#pragma unroll
+        for (int r = 0; r < SE_RG; r++) {
+          if (r < k.R) {
+            const float4 a = *reinterpret_cast<const float4 *>(&D.As[r][kk]);
+            acc[r] = fmaf(a.x, b0, fmaf(a.y, b1, fmaf(a.z, b2, fmaf(a.w, b3, acc[r]))));
+          }
+        }
+      }
+      __syncthreads();   // before the buffers are staged again
+    }
 #pragma unroll
     for (int r = 0; r < SE_RG; r++) D.red[warp][r][lane] = acc[r];
     __syncthreads();
     for (int q = threadIdx.x; q < k.R * 32; q += blockDim.x) {
-      const int r = q >> 5, l = q & 31, c = k.chunk * 32 + l;
-      if (c >= ncol) continue;
+      const int r = q >> 5, l = q & 31, col = c0 + l;
       float z = 0.f;
 #pragma unroll
       for (int w = 0; w < SE_WARPS; w++) z += D.red[w][r][l];   // fixed order
       const int row = D.rows[r];
-      float v;
-      if (kind == 0) v = celu_f(z + bias[(long long)(k.m * NE + k.e) * bias_me_stride + c]);
-      else if (kind == 1) v = z * dcelu_h(aux[(size_t)row * ldaux + k.m * aux_member_off + c]);
-      else v = z;
-      out[(size_t)row * ldo + k.m * o_member_off + c] = v;
+      float yv = 0.f;
+      if (col < ncol) {
+        float v;
+        if (kind == 0) {
+          v = celu_f(z + D.ep_bias[l]);
+        } else if (kind == 1) {
+          v = z * dcelu_h(D.ep_aux[r][l]);
+        } else if (kind == 2) {
+          v = z;
+        } else {
+          const float h = celu_f(z + D.ep_bias[l]), w = D.ep_w4[l];
+          v = w * dcelu_h(h) / (float)A.M;
+          yv = w * h;
+        }
+        out[(size_t)row * ldo + k.m * o_member_off + col] = v;
+      }
+      if (kind == 3) D.tmp[r][l] = yv;
+    }
+    if (kind == 3) {
+      __syncthreads();
+      if (threadIdx.x < k.R) {
+        float ys = 0.f;
+        for (int l = 0; l < 32; l++) ys += D.tmp[threadIdx.x][l];   // fixed order
+        ysl[((size_t)D.rows[threadIdx.x] * A.M + k.m) * SE_YCH + k.chunk] = ys;
+      }
     }
   }
 }
@@ -1041,10 +1107,22 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wg = blockIdx.x * SE_WARPS + warp, nw = gridDim.x * SE_WARPS;
   const int M = A.M, N = A.N;
-  // element counts (every block, from the species segments' occupancy)
+  // element counts and the atoms in element order (every block; from the species order of the list)
+  __shared__ int estart[NE + 1];
+  __shared__ int srow[SMALL_BUILD_ATOMS];
   if (threadIdx.x < NE) ecount[threadIdx.x] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&ecount[A.elem[i]], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    estart[0] = 0;
+    for (int e = 0; e < NE; e++) estart[e + 1] = estart[e] + ecount[e];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int e = A.elem[i];
+    srow[estart[e] + A.perm[i] - A.meta[META_SEG + e]] = i;
+  }
   // zero the accumulated outputs
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * N; q += gridDim.x * blockDim.x) A.F[q] = 0.f;
   if (A.virial)
@@ -1055,86 +1133,50 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   SmallDense &D = S.d;
   const int MH1 = M * H1;
   // first layer, all members fused: h1 = CELU(aev W1^T + b1), [N][M 256]
-  small_layer(A, D, ecount, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0,
-              0, A.h1, MH1, 0, 1);
+  small_layer(A, D, ecount, estart, srow, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0,
+              0, A.h1, MH1, 0, 1, nullptr);
   if (!grid_barrier(A.bar, A.st)) return;
   // second layer per member: h2 = CELU(h1_m W2^T + b2), [N][M 192]
-  small_layer(A, D, ecount, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2,
-              M * H2, H2, M);
+  small_layer(A, D, ecount, estart, srow, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2,
+              M * H2, H2, M, nullptr);
   if (!grid_barrier(A.bar, A.st)) return;
-  // third layer per member, all 160 columns in one block (five warps, full K): h3, the output layer's dot
-  // product in a fixed order, and g3 = (1/M) w4 CELU'(z3)
-  {
-    for (int t = blockIdx.x;; t += gridDim.x) {
-      SmallTask k;
-      __syncthreads();
-      const bool ok = small_task(A, ecount, t, 1, M, k, D.rows);
-      __syncthreads();
-      if (!ok) break;
-      const long long me = (long long)(k.m * NE + k.e);
-      if (warp < H3 / 32) {
-        const int col = warp * 32 + lane;
-        float acc[SE_RG];
-#pragma unroll
-        for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
-        const float *B = A.W3T + me * H2 * H3;
-        for (int kk = 0; kk < H2; kk += 4) {
-          float b[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) b[u] = __ldg(B + (size_t)(kk + u) * H3 + col);
-#pragma unroll
-          for (int r = 0; r < SE_RG; r++)
-            if (r < k.R) {
-              const float4 a = __ldg(reinterpret_cast<const float4 *>(A.h2 + (size_t)D.rows[r] * (M * H2) + k.m * H2 + kk));
-              acc[r] = fmaf(a.x, b[0], fmaf(a.y, b[1], fmaf(a.z, b[2], fmaf(a.w, b[3], acc[r]))));
-            }
-        }
-        const float bb = A.b3[me * H3 + col], w = A.w4[me * H3 + col];
-#pragma unroll
-        for (int r = 0; r < SE_RG; r++) {
-          if (r < k.R) {
-            const float z = acc[r] + bb;
-            const float h = celu_f(z);
-            A.g3[(size_t)D.rows[r] * (M * H3) + k.m * H3 + col] = w * dcelu_h(h) / (float)M;
-            float p = w * h;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == 0) D.ypart[warp][r] = p;
-          }
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x < k.R) {
-        float yv = A.b4[me];
-        for (int w = 0; w < H3 / 32; w++) yv += D.ypart[w][threadIdx.x];
-        A.y[((size_t)D.rows[threadIdx.x] * M + k.m) * 4] = yv;
-      }
-    }
-  }
+  // third layer per member: h3 = CELU(h2_m W3^T + b3) -> g3 = (1/M) w4 CELU'(z3) and the output layer's
+  // partial sums per column chunk (fixed slots, added in a fixed order with the energies)
+  small_layer(A, D, ecount, estart, srow, 3, A.h2, M * H2, H2, H2, A.W3T, (long long)H2 * H3, H3, H3, A.b3, H3, nullptr, 0, 0, A.g3,
+              M * H3, H3, M, A.ysl);
   if (!grid_barrier(A.bar, A.st)) return;
   // third layer's input gradient: g2 = (g3 W3) * CELU'(h2)
-  small_layer(A, D, ecount, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2,
-              A.g2, M * H2, H2, M);
+  small_layer(A, D, ecount, estart, srow, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2,
+              A.g2, M * H2, H2, M, nullptr);
   if (!grid_barrier(A.bar, A.st)) return;
   // second layer's: g1 = (g2 W2) * CELU'(h1)
-  small_layer(A, D, ecount, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1,
-              A.g1, MH1, H1, M);
+  small_layer(A, D, ecount, estart, srow, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1,
+              A.g1, MH1, H1, M, nullptr);
   if (!grid_barrier(A.bar, A.st)) return;
   // first layer's, summed over the members: dE/dAEV = g1 W1 (K = M 256 through the member-concatenated W1)
-  small_layer(A, D, ecount, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
-              A.gaev, NAEV, 0, 1);
+  small_layer(A, D, ecount, estart, srow, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
+              A.gaev, NAEV, 0, 1, nullptr);
   if (!grid_barrier(A.bar, A.st)) return;
-  // forces and virials; energies in a fixed order (a thread per structure)
+  // forces and virials (a warp per atom, the first warps); the energies meanwhile on the last warps, a warp
+  // per structure: lanes over its atoms, then a shuffle tree (a fixed order)
   __syncthreads();
   aev_adjoint_rows(A.aa, S.adj[warp], wg, nw);
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < A.NM; m += gridDim.x * blockDim.x) {
+  for (int m = nw - 1 - wg; m < A.NM; m += nw) {
     const int a0 = max(A.mol_offsets[m], 0), a1 = min(A.mol_offsets[m + 1], N);
     double e = 0.0;
-    for (int i = a0; i < a1; i++) {
+    for (int i = a0 + lane; i < a1; i += 32) {
+      const int el = A.elem[i];
       double yi = 0.0;
-      for (int q = 0; q < M; q++) yi += (double)A.y[((size_t)i * M + q) * 4];
+      for (int q = 0; q < M; q++) {
+        float yq = A.b4[q * NE + el];
+        for (int c = 0; c < SE_YCH; c++) yq += A.ysl[((size_t)i * M + q) * SE_YCH + c];
+        yi += (double)yq;
+      }
       e += yi / (double)M;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane != 0) continue;
     A.E[m] = e;
     if (!isfinite(e)) post_status(A.st, FNN_E_NONFINITE, -(long long)(m + 1));
   }
@@ -1281,7 +1323,8 @@ fnn_status launch_aev_tangent_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
 fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, float *F,
                              double *virial, cudaStream_t s) {
   const int N = sys->n_atoms, M = ctx->cfg.n_members;
-  if (!ctx->grid_bar) FNN_CUDA_TRY(ctx, cudaMalloc(&ctx->grid_bar, 256));
+  // the barrier word, then the output-layer partial sums (atoms x members x chunks at most SMALL_EVAL_ROWS x 5)
+  if (!ctx->grid_bar) FNN_CUDA_TRY(ctx, cudaMalloc(&ctx->grid_bar, 256 + (size_t)SMALL_EVAL_ROWS * SE_YCH * sizeof(float)));
   const size_t dyn = sizeof(SmallShared);
   static bool attr_set = false;
   static int per_sm = 0;
@@ -1320,7 +1363,7 @@ fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlis
   a.M = M;
   a.mol_offsets = sys->mol_offsets;
   a.elem = nl->elem;
-  a.inv = nl->inv;
+  a.perm = nl->perm;
   a.meta = nl->meta;
   a.W1T = w.W1Tcat;
   a.b1 = w.b1cat;
@@ -1340,7 +1383,7 @@ fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlis
   a.g2 = ws.g2;
   a.g1 = ws.g1;
   a.gaev = ws.gaev;
-  a.y = ws.ypart;
+  a.ysl = reinterpret_cast<float *>(reinterpret_cast<char *>(ctx->grid_bar) + 256);
   a.E = E;
   a.F = F;
   a.virial = virial;
@@ -1349,7 +1392,7 @@ fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlis
   // a grid no larger than the widest layer needs (and co-resident: a cooperative launch)
   const int row_groups = (N + SE_RG - 1) / SE_RG + NE;
   int grid = row_groups * (NAEV + 31) / 32;
-  const int cap = per_sm * ctx->num_sms < 128 ? per_sm * ctx->num_sms : 128;
+  const int cap = per_sm * ctx->num_sms < 64 ? per_sm * ctx->num_sms : 64;   // fewer arrivals per barrier
   if (grid > cap) grid = cap;
   FNN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), s));
   cudaLaunchConfig_t cfg{};

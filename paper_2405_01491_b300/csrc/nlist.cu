@@ -1002,6 +1002,9 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
 // One launch instead of the cell-list pipeline's thirteen, for systems whose cost is launch latency.
 constexpr int SMALL_NT = 1024;
 struct SmallBuildShared {
+  float4 pos[SMALL_BUILD_ATOMS];
+  int32_t z[SMALL_BUILD_ATOMS];
+  int32_t off[SMALL_BUILD_MOL + 1];
   float bb[SMALL_BUILD_MOL][6];
   MolGrid g[SMALL_BUILD_MOL];
   int32_t am[SMALL_BUILD_ATOMS];
@@ -1010,6 +1013,7 @@ struct SmallBuildShared {
   int32_t stage_j[SMALL_NT / 32][PAIR_STRIDE];
   char4 stage_s[SMALL_NT / 32][PAIR_STRIDE];
   int ecount[8], eseg[8];
+  int wcnt[SMALL_NT / 32][8];
 };
 static_assert(SMALL_BUILD_ATOMS <= SMALL_NT, "one atom per thread in the scans");
 
@@ -1022,12 +1026,21 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = SMALL_NT / 32;
   const unsigned lt = (1u << lane) - 1u;
   const int N = sys.n_atoms, NM = sys.n_mol;
-  const float4 *pos = reinterpret_cast<const float4 *>(sys.pos);
+  // positions, atomic numbers and offsets read once into shared memory
+  const float4 *gpos = reinterpret_cast<const float4 *>(sys.pos);
+  for (int i = tid; i < N; i += SMALL_NT) {
+    S.pos[i] = gpos[i];
+    S.z[i] = sys.Z[i];
+  }
+  for (int m = tid; m <= NM; m += SMALL_NT) S.off[m] = sys.mol_offsets[m];
+  __syncthreads();
+  const float4 *pos = S.pos;
+  const int32_t *offs = S.off;
   // offsets start at 0, end at N and never decrease; otherwise no atom belongs to a structure
   int badl = 0;
   for (int m = tid; m <= NM; m += SMALL_NT) {
-    const int a = sys.mol_offsets[m];
-    bool ok = (m == 0) ? a == 0 : (a >= sys.mol_offsets[m - 1]);
+    const int a = offs[m];
+    bool ok = (m == 0) ? a == 0 : (a >= offs[m - 1]);
     if (m == NM) ok = ok && a == N;
     if (!ok) {
       post_status(st, FNN_E_INVALID, m);
@@ -1048,12 +1061,12 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
       int lo = 0, hi = NM;
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (sys.mol_offsets[mid] <= i) lo = mid; else hi = mid;
+        if (offs[mid] <= i) lo = mid; else hi = mid;
       }
-      if (sys.mol_offsets[lo] <= i && i < sys.mol_offsets[lo + 1]) m = lo;
+      if (offs[lo] <= i && i < offs[lo + 1]) m = lo;
     }
     if (m >= 0) {
-      e = element_of(sys.Z[i]);
+      e = element_of(S.z[i]);
       if (e < 0) {
         post_status(st, FNN_E_SPECIES, i);
         e = 0;
@@ -1076,7 +1089,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
   __syncthreads();
   // per structure: images and the predicate band, exactly as the cell-list build takes them
   for (int m = tid; m < NM; m += SMALL_NT) {
-    const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    const int a0 = offs[m], a1 = offs[m + 1];
     MolGrid g = MolGrid{0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 0};
     if (!bad && a0 >= 0 && a1 >= a0 && a1 <= N) {
       const int pbc = sys.pbc ? (sys.pbc[m] != 0) : 0;
@@ -1096,7 +1109,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
     if (m >= 0) {
       const MolGrid g = S.g[m];
       const float4 pi = pos[i];
-      const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+      const int a0 = offs[m], a1 = offs[m + 1];
       for (int j0 = a0; j0 < a1; j0 += 32) {
         const int j = j0 + lane;
         bool in = false;
@@ -1132,7 +1145,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
     if (m < 0) continue;   // uniform over the warp
     const MolGrid g = S.g[m];
     const float4 pi = pos[i];
-    const int a0 = sys.mol_offsets[m], a1 = sys.mol_offsets[m + 1];
+    const int a0 = offs[m], a1 = offs[m + 1];
     const int64_t dst = S.start[i];
     const int n = S.start[i + 1] - S.start[i];
     const bool sortable = n <= PAIR_STRIDE;
@@ -1212,12 +1225,19 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
   }
   for (int r = tid; r < pad_cap; r += SMALL_NT) inv[r] = -1;
   __syncthreads();
-  for (int e = 0; e < NE; e++) {
-    const int flag = (tid < N && S.el[tid] == e) ? 1 : 0;
-    int tot;
-    const int rank = block_excl_scan<SMALL_NT>(flag, &tot);
-    if (flag) {
-      const int row = S.eseg[e] + rank;
+  {   // rank among the atoms of the same element, in index order: ballots per warp, then the warps before
+    const int e_i = tid < N ? (int)S.el[tid] : NE;
+    int mine = 0;
+    for (int q = 0; q < NE; q++) {
+      const unsigned mq = __ballot_sync(FULL, e_i == q);
+      if (lane == 0) S.wcnt[warp][q] = __popc(mq);
+      if (e_i == q) mine = __popc(mq & lt);
+    }
+    __syncthreads();
+    if (tid < N) {
+      int before = 0;
+      for (int w = 0; w < warp; w++) before += S.wcnt[w][e_i];
+      const int row = S.eseg[e_i] + before + mine;
       perm[tid] = row;
       inv[row] = tid;
     }

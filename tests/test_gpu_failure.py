@@ -161,3 +161,28 @@ def test_serving_rejects_bad_requests_and_isolates_a_failing_structure(fnn):
         assert b is not None and b["n_steps_done"] == k
         assert np.abs(a["energies"] - b["energies"]).max() / p.n_atoms <= E_TOL_PER_ATOM
         assert np.abs(a["pos"] - b["pos"]).max() <= 1e-4
+
+
+def test_small_build_reports_bad_inputs(fnn):
+    """The one-block build of small systems (at most 256 atoms) makes the same checks as the cell-list build."""
+    s = structure("gas24")
+    ctx = fnn.Context(1)
+    nl = fnn.NeighborList(ctx)
+    pos = s.pos.copy()
+    pos[9, 2] = np.nan
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(synth.Structures(s.Z, pos, s.mol_offsets, s.cell,
+                                                                                 s.pbc)), nl)
+    assert fnn.sync(ctx) == (-7, 9)
+    Z = s.Z.copy()
+    Z[4] = 26
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(synth.Structures(Z, s.pos, s.mol_offsets, s.cell,
+                                                                                 s.pbc)), nl)
+    assert fnn.sync(ctx) == (-2, 4)
+    over = synth.Structures(s.Z, s.pos, np.array([0, 24, 0, 24], np.int32), np.zeros((3, 9), np.float32),
+                            np.zeros(3, np.uint8))
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(over), nl)
+    assert fnn.sync(ctx)[0] == -1 and fnn.nlist_nnz(nl) == 0
+    nl_small = fnn.NeighborList(ctx, capacity=50)
+    fnn.build_neighbors(ctx, fnn.DeviceSystem.from_structures(s), nl_small)
+    code, info = fnn.sync(ctx)
+    assert code == -4 and info == len(oracle.neighbors(s, 5.1)[0])
