@@ -759,6 +759,111 @@ def drift_bench(fnn, torch, synth, forms=("fp32", "fp32x3", "bf16", "fp8"), n_st
     return out
 
 
+def variants_bench(fnn, torch, synth, steps=10, warmup=3):
+    """The descriptor variants on the 23,558-atom box: the CRATE angular resource (Appendix A) and its
+    vector-Jacobian product (random V and dL/dg, seeded), and one energy + force step of the FP32X3 form with
+    each switching function (section II.A), M = 8; CUDA events around each call, L2 flushed before each."""
+    import numpy as np
+    pk = peaks()
+    s = synth.mix23558()
+    ds = fnn.DeviceSystem.from_structures(s)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    out = {"workload": "mix23558 (23,558 atoms, 62.2 A periodic box)"}
+    rng = np.random.default_rng(17)
+    V = torch.from_numpy((rng.standard_normal((7, 8, 32)) / 4).astype(np.float32)).cuda()
+    G = torch.from_numpy(rng.standard_normal((s.n_atoms, 4, 32)).astype(np.float32)).cuda()
+    ctx = fnn.Context(1)
+    nl = fnn.NeighborList(ctx)
+    fnn.build_neighbors(ctx, ds, nl, checked=True)
+    nnz = fnn.nlist_nnz(nl)
+    g = torch.empty((s.n_atoms, 4, 32), dtype=torch.float32, device="cuda")
+    ms_f = timed(lambda: fnn.crate_angular(ctx, ds, nl, V, out=g))
+    ms_v = timed(lambda: fnn.crate_angular_vjp(ctx, ds, nl, V, G))
+    fnn.check(ctx, "crate")
+    # algorithmic bytes: positions, the list (index + shift per entry), the resource row (and dL/dg, gradient)
+    b_f = s.n_atoms * (16 + 512) + nnz * 8
+    b_v = s.n_atoms * (16 + 512 + 12) + nnz * 8
+    out["crate_angular"] = {"ms": ms_f, "atoms_per_s": s.n_atoms / (ms_f * 1e-3),
+                            "achieved_gbs": b_f / (ms_f * 1e-3) / 1e9, "hbm_frac": b_f / (ms_f * 1e-3) / 1e9 / pk["hbm_gbs"]}
+    out["crate_angular_vjp"] = {"ms": ms_v, "atoms_per_s": s.n_atoms / (ms_v * 1e-3),
+                                "achieved_gbs": b_v / (ms_v * 1e-3) / 1e9,
+                                "hbm_frac": b_v / (ms_v * 1e-3) / 1e9 / pk["hbm_gbs"]}
+    w = synth.xavier_weights(8)
+    for sw in ("cosine", "polynomial", "exponential"):
+        c = fnn.Context(8, switch=sw)
+        fnn.load_weights(c, w)
+        n2 = fnn.NeighborList(c)
+        fnn.build_neighbors(c, ds, n2, checked=True)
+        E = torch.empty(s.n_mol, dtype=torch.float64, device="cuda")
+        F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+        Wv = torch.empty((s.n_mol, 3, 3), dtype=torch.float64, device="cuda")
+
+        def step():
+            fnn.build_neighbors(c, ds, n2)
+            fnn.energy_forces(c, ds, n2, "fp32x3", out=(E, F, Wv))
+        ms = timed(step)
+        fnn.check(c, f"switch {sw}")
+        out[f"step_fp32x3_{sw}"] = {"ms": ms, "atom_evals_per_s": s.n_atoms / (ms * 1e-3), "members": 8,
+                                    "note": "eager step (list + energies + forces + virials)"}
+    return out
+
+
+def rpmd_bench(fnn, torch, synth, P=32, n_steps=200, dt=0.25, T=300.0):
+    """Ring-polymer MD of the water box (section V.D): P beads of 648 atoms as one batch of P structures,
+    one member, FP32X3, skin 1 A rebuilt every 10 steps and by the guard; exact normal-mode free steps.
+    Reports bead-atom evaluations per second and the ring-polymer Hamiltonian's drift."""
+    import numpy as np
+    s = synth.water216()
+    rng = np.random.default_rng(7)
+    x0 = (np.asarray(s.pos, np.float64)[None] + 0.02 * rng.standard_normal((P, s.n_atoms, 3))).astype(np.float32)
+    v0 = np.stack([synth.maxwell_boltzmann(s.Z, T, seed=100 + b) for b in range(P)]).astype(np.float32)
+    ctx = fnn.Context(1, skin=1.0)
+    fnn.load_weights(ctx, synth.xavier_weights(1))
+    nl = fnn.NeighborList(ctx)
+    stream = torch.cuda.Stream()
+
+    def fresh():
+        ds = fnn.bead_system(s, x0)
+        vel = torch.zeros((P * s.n_atoms, 4), dtype=torch.float32)
+        vel[:, :3] = torch.from_numpy(v0.reshape(-1, 3))
+        return ds, vel.cuda()
+
+    with torch.cuda.stream(stream):
+        ds, vel = fresh()
+        fnn.rpmd_run(ctx, ds, vel, nl, "fp32x3", P, 20, dt, T, 10, stream=stream)   # warm-up (sizes, graphs)
+        fnn.check(ctx, "rpmd warm-up", stream=stream)
+        ds, vel = fresh()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        E, H, F, cnt = fnn.rpmd_run(ctx, ds, vel, nl, "fp32x3", P, n_steps, dt, T, 10, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fnn.check(ctx, "rpmd", stream=stream)
+    ms = a.elapsed_time(b)
+    Hh = H.cpu().numpy()
+    n = P * s.n_atoms
+    return {"workload": f"water216 ring polymer, {P} beads ({n} bead atoms per evaluation)", "members": 1,
+            "precision": "fp32x3", "beads": P, "steps": n_steps, "dt_fs": dt, "T_K": T, "ms_total": ms,
+            "ms_per_step": ms / n_steps, "bead_atom_evals_per_s": n * n_steps / (ms * 1e-3),
+            "hamiltonian_first_last": [float(Hh[0]), float(Hh[-1])],
+            "hamiltonian_drift_per_bead_atom": float((Hh[-1] - Hh[0]) / n)}
+
+
 def time_form(fnn, torch, ctx, ds, nl, E, F, Wv, flush, form, steps, warmup, barrier):
     """K timed steps of one form, each a replay of the step's CUDA graph (list rebuild + energies +
     forces + virials) on its own stream, CUDA events around every replay (L2 flushed outside them);
@@ -871,6 +976,10 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=4096)
     ap.add_argument("--no-drift", action="store_true", help="skip the energy-drift study")
     ap.add_argument("--no-cpu-plan", action="store_true", help="skip the oracle timings of every configuration")
+    ap.add_argument("--no-variants", action="store_true", help="skip the CRATE / switch measurements")
+    ap.add_argument("--no-rpmd", action="store_true", help="skip the ring-polymer measurement")
+    ap.add_argument("--only", default=None, choices=["variants", "rpmd", "md", "drift", "latency", "serve"],
+                    help="run one measurement section alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -878,6 +987,18 @@ def main():
     import numpy as np
     import torch
     from paper_2405_01491_b300 import fnn, synth
+
+    if args.only:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        fn = {"variants": lambda: variants_bench(fnn, torch, synth, args.steps, args.warmup),
+              "rpmd": lambda: rpmd_bench(fnn, torch, synth),
+              "md": lambda: md_bench(fnn, torch, synth, check=False),
+              "drift": lambda: drift_bench(fnn, torch, synth),
+              "latency": lambda: latency_bench(fnn, torch, synth),
+              "serve": lambda: serve_bench(fnn, torch, synth, duration_s=args.serve_seconds,
+                                           pool_n=args.serve_pool)}[args.only]
+        print(json.dumps({"section": args.only, "result": fn()}), flush=True)
+        return 0
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     ranks = Ranks("nccl", "cuda")
@@ -940,6 +1061,11 @@ def main():
         latency = section("latency", latency_bench, fnn, torch, synth)
     if world == 1 and not args.no_drift:
         drift = section("drift", drift_bench, fnn, torch, synth)
+    variants = rpmd = None
+    if world == 1 and not args.no_variants:
+        variants = section("variants", variants_bench, fnn, torch, synth)
+    if world == 1 and not args.no_rpmd:
+        rpmd = section("rpmd", rpmd_bench, fnn, torch, synth)
     train = None
     if world == 1 and not args.no_train:
         train = {p: section(f"train_{p}", train_bench, fnn, torch, synth, args.steps, max(3, args.warmup), precision=p)
@@ -983,6 +1109,10 @@ def main():
         line["latency"] = latency
     if drift is not None:
         line["drift"] = drift
+    if variants is not None:
+        line["variants"] = variants
+    if rpmd is not None:
+        line["rpmd"] = rpmd
     if rank == 0:
         print(json.dumps(line), flush=True)
     ranks.close()
