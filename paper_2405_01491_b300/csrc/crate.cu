@@ -18,7 +18,7 @@ static constexpr unsigned CFULL = 0xffffffffu;
 constexpr int CR_NB = FNN_CRATE_NB, CR_DA = FNN_CRATE_DA, CR_NT = FNN_CRATE_NT;
 static_assert(CR_DA == 32, "one channel per lane");
 constexpr int CR_CAP = ANG_CAP;           // neighbours within rc_ang per atom
-constexpr int CR_FWD_WARPS = 4, CR_VJP_WARPS = 2;
+constexpr int CR_FWD_WARPS = 4, CR_VJP_WARPS = 4;
 
 struct CrateNbr {   // one centre atom's neighbours within rc_ang, in list order
   float4 u[CR_CAP];      // unit vector to the neighbour, distance
@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(CR_FWD_WARPS * 32) k_crate_forward(CrateArgs A
 struct CrateVjpWarp {
   CrateNbr nb;
   float D[CR_CAP][CR_DA];
-  float dDdr[CR_CAP][CR_DA];
   float dD[CR_CAP][CR_DA];     // dL/dD per neighbour and channel
   float4 row[32];              // T1, T2, T3 of one row of pairs
   float4 drow[32];             // dT1/dc, dT2/dc, dT3/dc
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(CR_VJP_WARPS * 32) k_crate_vjp(CrateArgs A) {
   for (int i = blockIdx.x * CR_VJP_WARPS + warp; i < A.n_atoms; i += gridDim.x * CR_VJP_WARPS) {
     const int n = crate_stage(A, i, W.nb);
     if (n < 2) continue;   // uniform over the warp
-    crate_build_D(A, W.nb, n, Vs, W.D, W.dDdr);
+    crate_build_D(A, W.nb, n, Vs, W.D, nullptr);
     const float *Gi = A.G + (size_t)i * CR_NT * CR_DA + lane;
     const float G0 = Gi[0], G1 = Gi[CR_DA], G2 = Gi[2 * CR_DA], G3 = Gi[3 * CR_DA];
     for (int t = 0; t < n; t++) W.dD[t][lane] = 0.f;
@@ -261,7 +260,18 @@ __global__ void __launch_bounds__(CR_VJP_WARPS * 32) k_crate_vjp(CrateArgs A) {
     // per neighbour: dL/dr through D (summed over channels), and dL/dV
     for (int t = 0; t < n; t++) {
       const float dDt = W.dD[t][lane];
-      float s = dDt * W.dDdr[t][lane];
+      // dD/dr of this channel, recomputed: f~' sum_a B~_a V + f~ sum_a B~_a' V
+      const float r = W.nb.u[t].w;
+      const float *v = Vs + (int)W.nb.e[t] * CR_NB * CR_DA + lane;
+      float sb = 0.f, sbd = 0.f;
+#pragma unroll
+      for (int a = 0; a < CR_NB; a++) {
+        const float dr = r - A.P.shf_a[a];
+        const float bb = __expf(-A.P.eta_a * dr * dr);
+        sb = fmaf(bb, v[a * CR_DA], sb);
+        sbd = fmaf(-2.f * A.P.eta_a * dr * bb, v[a * CR_DA], sbd);
+      }
+      float s = dDt * (W.nb.df[t] * sb + W.nb.f[t] * sbd);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(CFULL, s, o);
       if (lane == 0) {
@@ -271,7 +281,7 @@ __global__ void __launch_bounds__(CR_VJP_WARPS * 32) k_crate_vjp(CrateArgs A) {
         W.gd[t][2] = fmaf(s, u.z, W.gd[t][2]);
       }
       if (A.gV) {
-        const float r = W.nb.u[t].w, ft = W.nb.f[t] * dDt;
+        const float ft = W.nb.f[t] * dDt;
         float *gv = gVs + (int)W.nb.e[t] * CR_NB * CR_DA + lane;
 #pragma unroll
         for (int a = 0; a < CR_NB; a++) {
