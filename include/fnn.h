@@ -162,7 +162,8 @@ fnn_status fnn_nlist_nnz(fnn_nlist *nl, int64_t *nnz);
 fnn_status fnn_nlist_export(fnn_nlist *nl, int32_t *row_ptr, int32_t *nbr, int8_t *shift, int64_t cap,
                             int64_t *nnz);
 
-/* AEVs [N][1008] float32 (device, caller-owned) from a list built for sys.
+/* AEVs [N][1008] float32 (device, caller-owned, 16-byte aligned: FNN_E_INVALID otherwise) from a list
+ * built for sys.
  * Radial slot e*16+k = sum over neighbours j of element e within rc_rad of
  * 1/4 exp(-eta_rad (r - R_k)^2) fc(r); angular slot 112 + p*32 + m*4 + s = sum
  * over unordered neighbour pairs {j,k} within rc_ang with element pair p of

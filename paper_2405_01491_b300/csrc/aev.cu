@@ -67,16 +67,27 @@ struct NbrStageT {
 };
 using NbrStage = NbrStageT<true>;
 constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
+
+// The forward's staging of one centre atom: only what its sums read, in the form they read it
+struct FwdNbr {
+  float2 rr[RAD_CAP];            // r, log2 fc(r; rc_rad) - 2   (element-sorted, r < rc_rad; the 1/4 prefactor)
+  float4 au[ANG_CAP];            // unit vector to the neighbour, r / 2   (element-sorted, r < rc_ang)
+  float la[ANG_CAP];             // log2 fc(r; rc_ang) + 1/2: la_j + la_k = log2(2 fc_j fc_k)
+};
 struct FwdStage {
-  NbrStageT<false> nb;
+  FwdNbr nb;
   // per-triplet factors of one batch, triplet innermost so a consumer lane reads four at once:
-  // 4 section powers, 8 Gaussians x switches, and the element-pair block (-1 past the end)
+  // 4 section powers and 8 Gaussians x switches
   alignas(16) float sf[NSZ][SROW];
   alignas(16) float sg[NSA][SROW];
-  alignas(16) int sp[SROW];
-  // element-pair blocks of the atom's triplets, in slot order: {triplets, j0 | k0 << 8 | (a == b) << 16,
-  // count of element b, count of element a} with j0, k0 the angular-list starts of elements a and b
-  int4 blk[NPAIR];
+  int sp[32];                    // slot block of a triplet that opens one
+  // the non-empty element-pair blocks of the atom's triplets in slot order, then one past the last:
+  // {first slot, j0 | k0 << 8 | (a == b) << 16, count of element b, count of element a} with j0, k0 the
+  // angular-list starts of elements a and b; {slots, 0, 0, 0} past the last (a block of t triplets takes
+  // t rounded up to a multiple of four slots)
+  int4 bt[NPAIR + 1];
+  float bi[NPAIR + 1];           // 1 / count of a (a == b) or of b: the divisor of the block's pair index
+  int bq[NPAIR + 1];             // slot block | triplets << 8
 };
 struct AdjStage {
   NbrStage nb;
@@ -224,6 +235,122 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   return true;
 }
 
+// the lanes of a chunk whose element is q, from the three bit planes of the lanes' elements
+__device__ __forceinline__ unsigned elem_lanes(int q, unsigned b0, unsigned b1, unsigned b2) {
+  return (q & 1 ? b0 : ~b0) & (q & 2 ? b1 : ~b1) & (q & 4 ? b2 : ~b2);
+}
+
+// Stage atom i's neighbours for the forward (FwdNbr); returns false when the atom has no structure, or
+// (after posting FNN_E_CAPACITY) when a list overflows.  The per-element counts are kept one element per
+// lane: on return lane q < NE holds the start of element q's radial (orr) and angular (oa) segment and its
+// angular count (ca); lane NE holds the totals in orr and oa.  A row sorted by neighbour element is staged
+// in one pass, any other in two (count, then scatter, stable within an element).
+__device__ bool stage_fwd(const StageArgs &A, const AevParams &P, int i, FwdNbr &S, int &orr, int &oa, int &ca,
+                          DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int mol = A.atom_mol[i];
+  if (mol < 0) return false;   // atom outside every structure (already posted)
+  const float4 pi = A.pos[i];
+  const MolGrid &g = A.grid[mol];
+  const int pbc = g.pbc;
+  const float Lx = pbc ? g.Lx : 0.f, Ly = pbc ? g.Ly : 0.f, Lz = pbc ? g.Lz : 0.f;
+  const int k0 = (int)min((int64_t)A.row_ptr[i], A.cap), k1 = (int)min((int64_t)A.row_ptr[i + 1], A.cap);
+  struct Ent {
+    float dx, dy, dz, r;
+    int e;
+    bool vr, va;
+  };
+  auto entry = [&](int k, Ent &t) {
+    t.vr = t.va = false;
+    t.e = 0;
+    t.dx = t.dy = t.dz = t.r = 0.f;
+    if (k < k1) {
+      const int j = A.nbr[k];
+      const char4 sh = A.shift[k];
+      const float4 pj = A.pos[j];
+      t.dx = (pj.x - pi.x) + (float)sh.x * Lx;
+      t.dy = (pj.y - pi.y) + (float)sh.y * Ly;
+      t.dz = (pj.z - pi.z) + (float)sh.z * Lz;
+      t.r = sqrt_fast(t.dx * t.dx + t.dy * t.dy + t.dz * t.dz);
+      t.vr = t.r < P.rc_rad;
+      t.va = t.r < P.rc_ang;
+      t.e = A.elem[j];
+    }
+  };
+  auto put = [&](int pr, int pa, const Ent &t) {
+    S.rr[pr] = make_float2(t.r, __log2f(switch_f(P, t.r, P.rc_rad, P.inv_rc_rad)) - 2.f);
+    if (pa >= 0) {
+      const float ir = rcp_fast(t.r);
+      S.au[pa] = make_float4(t.dx * ir, t.dy * ir, t.dz * ir, 0.5f * t.r);
+      S.la[pa] = __log2f(switch_f(P, t.r, P.rc_ang, P.inv_rc_ang)) + 0.5f;
+    }
+  };
+  const bool mine = lane < NE;   // lane q counts element q
+  int cr = 0;
+  ca = 0;
+  if (k1 - k0 <= A.sorted_upto) {   // one pass: the subsets of a sorted row are sorted
+    int nr = 0, na = 0;
+    for (int kb = k0; kb < k1; kb += 32) {
+      Ent t;
+      entry(kb + lane, t);
+      const unsigned mr = __ballot_sync(FULL, t.vr), ma = __ballot_sync(FULL, t.va);
+      const unsigned q = elem_lanes(lane, __ballot_sync(FULL, t.e & 1), __ballot_sync(FULL, t.e & 2),
+                                    __ballot_sync(FULL, t.e & 4));
+      cr += __popc(q & mr);
+      ca += __popc(q & ma);
+      const int pr = nr + __popc(mr & lt), pa = na + __popc(ma & lt);
+      if (t.vr && pr < RAD_CAP) put(pr, t.va && pa < ANG_CAP ? pa : -1, t);
+      nr += __popc(mr);
+      na += __popc(ma);
+    }
+  } else {   // pass 1: counts per element
+    for (int kb = k0; kb < k1; kb += 32) {
+      Ent t;
+      entry(kb + lane, t);
+      const unsigned mr = __ballot_sync(FULL, t.vr), ma = __ballot_sync(FULL, t.va);
+      const unsigned q = elem_lanes(lane, __ballot_sync(FULL, t.e & 1), __ballot_sync(FULL, t.e & 2),
+                                    __ballot_sync(FULL, t.e & 4));
+      cr += __popc(q & mr);
+      ca += __popc(q & ma);
+    }
+  }
+  if (!mine) cr = ca = 0;
+  // exclusive scan over lanes 0 .. NE of the counts; lane NE receives the totals
+  int ir = cr, ia = ca;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int vr = __shfl_up_sync(FULL, ir, o), va = __shfl_up_sync(FULL, ia, o);
+    if (lane >= o) {
+      ir += vr;
+      ia += va;
+    }
+  }
+  orr = ir - cr;
+  oa = ia - ca;
+  if (__shfl_sync(FULL, orr, NE) > RAD_CAP || __shfl_sync(FULL, oa, NE) > ANG_CAP) {
+    if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
+    return false;
+  }
+  if (k1 - k0 > A.sorted_upto) {   // pass 2: scatter into element segments (stable within an element)
+    int runr = orr, runa = oa;    // lane q: next free radial / angular slot of element q
+    for (int kb = k0; kb < k1; kb += 32) {
+      Ent t;
+      entry(kb + lane, t);
+      const unsigned mr = __ballot_sync(FULL, t.vr), ma = __ballot_sync(FULL, t.va);
+      const unsigned b0 = __ballot_sync(FULL, t.e & 1), b1 = __ballot_sync(FULL, t.e & 2),
+                     b2 = __ballot_sync(FULL, t.e & 4);
+      const unsigned same = elem_lanes(t.e, b0, b1, b2), q = elem_lanes(lane, b0, b1, b2);
+      const int br = __shfl_sync(FULL, runr, t.e), ba = __shfl_sync(FULL, runa, t.e);
+      if (t.vr) put(br + __popc(same & mr & lt), t.va ? ba + __popc(same & ma & lt) : -1, t);
+      runr += __popc(q & mr);
+      runa += __popc(q & ma);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
 // slot block of the element pair (a, b), a <= b, in row-major upper-triangle order
 __device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
@@ -325,139 +452,200 @@ __device__ __forceinline__ void store_lo(__nv_bfloat16 *lo, size_t c, float v) {
   if (lo) lo[c] = __float2bfloat16(v - __bfloat162float(__float2bfloat16(v)));
 }
 
+// zeros over n elements of type T from p (16-byte aligned; n * sizeof(T) a multiple of 16), by the warp
+template <typename T>
+__device__ __forceinline__ void zero_span(T *p, int n) {
+  const int lane = threadIdx.x & 31;
+  uint4 *q = reinterpret_cast<uint4 *>(p);
+  const int n16 = n * (int)sizeof(T) / 16;
+  for (int c = lane; c < n16; c += 32) q[c] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Slot base + lane of one batch (32 consecutive slots in block order; every block padded to a multiple of
+// four slots) for the lane: the table entry of its block (idx), its angular entries ja, ka, and whether it
+// opens its block; false for a padding slot (ja = ka = 0 then).  cur is the table entry holding the
+// batch's first slot (warp-uniform) and is advanced to the one holding its last; nblk the table's entries
+// before the one-past-the-last.  Within a block of one element (n entries) the pairs run along cyclic
+// diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds n/2 pairs); within a block
+// of two elements, j-major.
+__device__ __forceinline__ bool batch_triplet(const FwdStage &W, int base, int nblk, int &cur, int &idx, int &ja,
+                                              int &ka, bool &opens) {
+  const int lane = threadIdx.x & 31;
+  if (W.bt[cur + 1].x == base) cur++;   // a block opening at the batch's first slot
+  // the blocks opening inside the batch, as bits of the slot offsets (table entries one per lane)
+  unsigned bit = 0u;
+  if (lane <= nblk) {
+    const int o = W.bt[lane].x - base;
+    if (o > 0 && o < 32) bit = 1u << o;
+  }
+  const unsigned M = __reduce_or_sync(FULL, bit);
+  idx = cur + __popc(M & ((2u << lane) - 1u));
+  cur += __popc(M);
+  const int4 bk = W.bt[idx];
+  const int w = base + lane - bk.x;
+  const int cnt = W.bq[idx] >> 8;
+  opens = w == 0 && cnt > 0;
+  const bool diag = (bk.y >> 16) != 0;
+  const int n = bk.w, dv = diag ? n : bk.z, D = (n - 1) >> 1;
+  int q = (int)((float)w * W.bi[idx]);   // w / dv, corrected below
+  if (q * dv > w) q--;
+  else if ((q + 1) * dv <= w) q++;
+  const int r = w - q * dv;
+  const int j0 = bk.y & 0xff;
+  int jrel, krel;
+  if (diag) {
+    const bool tail = q >= D;   // even n: the last diagonal, d = n / 2
+    jrel = tail ? w - D * n : r;
+    const int k = jrel + (tail ? n >> 1 : q + 1);
+    krel = k < n ? k : k - n;
+  } else {
+    jrel = q;
+    krel = ((bk.y >> 8) & 0xff) - j0 + r;
+  }
+  const bool real = w < cnt;
+  ja = real ? j0 + jrel : 0;
+  ka = real ? j0 + krel : 0;
+  return real;
+}
+
 // One warp's share of the forward: rows wg, wg + nw, ..., staged in W (the kernel below, and the fused
 // small-system kernel, call it)
 template <typename OutT>
 __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw) {
-  int lane = threadIdx.x & 31;
-  NbrStageT<false> &S = W.nb;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const AevParams &P = A.P;
-  int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   for (int row = wg; row < nrows; row += nw) {
     OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
     __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
-    int i = A.inv ? A.inv[row] : row;
-    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
-    bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, false, A.st);
+    const int i = A.inv ? A.inv[row] : row;
+    int orr, oa, ca;
+    const bool ok = i >= 0 && stage_fwd(A.sa, P, i, W.nb, orr, oa, ca, A.st);
     if (!ok) {
-      for (int c = lane; c < NAEV; c += 32) {
-        store_out<OutT>(out + c, 0.f, A.out_inv);
-        store_lo(lo, c, 0.f);
-      }
+      zero_span(out, NAEV);
+      if (lo) zero_span(lo, NAEV);
       __syncwarp();
       continue;
     }
-    // ---- radial
+    // every slot of an element (pair) without neighbours stays zero
+    zero_span(out, NAEV);
+    if (lo) zero_span(lo, NAEV);
+    __syncwarp();   // orders the zeros before the lanes' own stores below
+    // ---- radial: lane (h, k) sums shift k over every other neighbour of each element segment
     {
-      int h = lane >> 4, k = lane & 15;
-      float Rk = P.shf_r[k];
+      const int h = lane >> 4, k = lane & 15;
+      const float Rk = P.shf_r[k], ce = P.eta_r_l2;
 #pragma unroll 1
       for (int q = 0; q < NE; q++) {
-        float acc = 0.f;
-        for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
-          float dr = S.rd[t].w - Rk;
-          acc += __expf(-P.eta_r * dr * dr) * S.rfc[t];
+        const int t0 = __shfl_sync(FULL, orr, q), t1 = __shfl_sync(FULL, orr, q + 1);
+        if (t0 == t1) continue;
+        int t = t0 + h;
+        float a0 = 0.f, a1 = 0.f;
+        for (; t + 6 < t1; t += 8) {
+          const float2 v0 = W.nb.rr[t], v1 = W.nb.rr[t + 2], v2 = W.nb.rr[t + 4], v3 = W.nb.rr[t + 6];
+          const float d0 = v0.x - Rk, d1 = v1.x - Rk, d2 = v2.x - Rk, d3 = v3.x - Rk;
+          a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
+          a1 += exp2f_fast(fmaf(d1 * d1, ce, v1.y));
+          a0 += exp2f_fast(fmaf(d2 * d2, ce, v2.y));
+          a1 += exp2f_fast(fmaf(d3 * d3, ce, v3.y));
         }
+        for (; t < t1; t += 2) {
+          const float2 v0 = W.nb.rr[t];
+          const float d0 = v0.x - Rk;
+          a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
+        }
+        float acc = a0 + a1;
         acc += __shfl_xor_sync(FULL, acc, 16);
         if (lane < 16) {
-          store_out<OutT>(out + q * NSR + k, 0.25f * acc, A.out_inv);
-          store_lo(lo, q * NSR + k, 0.25f * acc);
+          store_out<OutT>(out + q * NSR + k, acc, A.out_inv);
+          store_lo(lo, q * NSR + k, acc);
         }
       }
     }
     // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch,
-    // enumerated block by block in slot order (element pair (a, b), a <= b; within a block j-major), so
-    // a pair's 32 slots are complete when its block ends.  The producer lane evaluates one triplet;
-    // lane (m, s) then sums pow_s * gauss_m over the batch into a register, which goes straight to
-    // the output row when the block ends (slots of absent pairs are written as zeros).
+    // enumerated block by block in slot order (element pair (a, b), a <= b), so a pair's 32 slots are
+    // complete when its block ends.  The producer lane evaluates one triplet; lane (m, s) then sums
+    // pow_s * gauss_m over the batch in four chains, which go to the output row when the block ends.
     {
+      // the table of non-empty blocks: lane p < NPAIR evaluates block p = (a, b)
+      const int a = (lane >= 7) + (lane >= 13) + (lane >= 18) + (lane >= 22) + (lane >= 25) + (lane >= 27);
+      const int b = min(a + lane - pair_of(a, a), NE - 1);
+      const int na = __shfl_sync(FULL, ca, a), nb = __shfl_sync(FULL, ca, b);
+      const int ja0 = __shfl_sync(FULL, oa, a), kb0 = __shfl_sync(FULL, oa, b);
+      const int cnt = lane < NPAIR ? (a == b ? na * (na - 1) / 2 : na * nb) : 0;
+      const unsigned nonempty = __ballot_sync(FULL, cnt > 0);
+      int incl = (cnt + 3) & ~3;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int T = __shfl_sync(FULL, incl, 31);
+      if (cnt > 0) {
+        const int e = __popc(nonempty & lt);
+        W.bt[e] = make_int4(incl - ((cnt + 3) & ~3), ja0 | (kb0 << 8) | ((a == b) << 16), nb, na);
+        W.bi[e] = rcp_fast((float)(a == b ? na : nb));
+        W.bq[e] = lane | (cnt << 8);
+      }
+      const int nblk = __popc(nonempty);
+      if (lane == 0) {
+        W.bt[nblk] = make_int4(T, 0, 0, 0);
+        W.bq[nblk] = 0;
+        W.bi[nblk] = 0.f;
+      }
+      __syncwarp();
       const int s_my = lane & 3, m_my = lane >> 2;
-      fill_blocks(W.blk, off_a, cnt_a);
-      const int n = off_a[NE];
-      const int T = n * (n - 1) / 2;
-      int run_p = -1;          // pair block being summed (warp-uniform); every block before it is written
-      float racc = 0.f;
+      const float *fr = W.sf[s_my], *gr = W.sg[m_my];
+      int run_p = -1;          // slot block being summed (warp-uniform)
+      float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
       auto put = [&](int pp, float v) {
         store_out<OutT>(out + NRAD + pp * 32 + lane, v, A.out_inv);
         store_lo(lo, NRAD + pp * 32 + lane, v);
       };
-      int cp = 0, cu = 0;      // block and offset of the batch's first triplet (warp-uniform)
+      auto open = [&](int pn) {
+        if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
+        r0 = r1 = r2 = r3 = 0.f;
+        run_p = pn;
+      };
+      int cur = 0;
       for (int base = 0; base < T; base += 32) {
-        int pb, ja, ka;
-        const unsigned starts = next_batch(W.blk, cp, cu, run_p, pb, ja, ka);
-        if (pb < NPAIR) {
-          const float4 d1 = S.rd[S.aidx[ja]], d2 = S.rd[S.aidx[ka]];
-          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(d1.w * d2.w);
-          const float c95 = 0.95f * c;
-          const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+        // every lane evaluates a triplet; a padding slot's Gaussians are zero (its switch product -inf)
+        int idx, ja, ka;
+        bool opens;
+        const bool real = batch_triplet(W, base, nblk, cur, idx, ja, ka, opens);
+        const float4 u1 = W.nb.au[ja], u2 = W.nb.au[ka];
+        const float c95 = 0.95f * (u1.x * u2.x + u1.y * u2.y + u1.z * u2.z);
+        const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
 #pragma unroll
-          for (int s = 0; s < NSZ; s++) {
-            const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-            W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
-          }
-          const float rbar = 0.5f * (d1.w + d2.w);
-          // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
-          const float lf = __log2f(2.f * S.afc[ja] * S.afc[ka]);
-#pragma unroll
-          for (int m = 0; m < NSA; m++) {
-            const float dr = rbar - P.shf_a[m];
-            W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
-          }
-          W.sp[lane] = pb;
-        } else {
-#pragma unroll
-          for (int s = 0; s < NSZ; s++) W.sf[s][lane] = 0.f;
-#pragma unroll
-          for (int m = 0; m < NSA; m++) W.sg[m][lane] = 0.f;
-          W.sp[lane] = -1;
+        for (int s = 0; s < NSZ; s++) {
+          const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
+          W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
         }
+        // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
+        const float rbar = u1.w + u2.w, lf = real ? W.nb.la[ja] + W.nb.la[ka] : __int_as_float(0xff800000);
+#pragma unroll
+        for (int m = 0; m < NSA; m++) {
+          const float dr = rbar - P.shf_a[m];
+          W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
+        }
+        if (opens) W.sp[lane] = W.bq[idx] & 0xff;
+        // blocks open only at slots that are multiples of four
+        const unsigned starts = __ballot_sync(FULL, opens);
         __syncwarp();
-        const int nt = min(32, T - base);
-        const float *fr = W.sf[s_my], *gr = W.sg[m_my];
-        if (starts == 0u && nt == 32) {   // the whole batch continues the running block
 #pragma unroll
-          for (int q = 0; q < 32; q += 4) {
-            const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
-            const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
-            racc = fmaf(fv.x, gv.x, racc);
-            racc = fmaf(fv.y, gv.y, racc);
-            racc = fmaf(fv.z, gv.z, racc);
-            racc = fmaf(fv.w, gv.w, racc);
-          }
-          __syncwarp();
-          continue;
-        }
-        // four triplets per step: within the running block four FMAs; where a block opens, the block
-        // before it is complete (and any between them empty)
-        for (int q = 0; q < nt; q += 4) {
+        for (int q = 0; q < 32; q += 4) {
           const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
           const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
-          const unsigned st4 = (starts >> q) & 0xfu;
-          if (st4 == 0u) {
-            racc = fmaf(fv.x, gv.x, racc);
-            racc = fmaf(fv.y, gv.y, racc);
-            racc = fmaf(fv.z, gv.z, racc);
-            racc = fmaf(fv.w, gv.w, racc);
-          } else {
-            const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, ga[4] = {gv.x, gv.y, gv.z, gv.w};
-#pragma unroll
-            for (int uu = 0; uu < 4; uu++) {
-              if (q + uu >= nt) break;
-              if ((st4 >> uu) & 1u) {
-                const int pn = W.sp[q + uu];
-                if (run_p >= 0) put(run_p, racc);
-                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f);
-                racc = 0.f;
-                run_p = pn;
-              }
-              racc = fmaf(fa[uu], ga[uu], racc);
-            }
-          }
+          if ((starts >> q) & 1u) open(W.sp[q]);
+          r0 = fmaf(fv.x, gv.x, r0);
+          r1 = fmaf(fv.y, gv.y, r1);
+          r2 = fmaf(fv.z, gv.z, r2);
+          r3 = fmaf(fv.w, gv.w, r3);
         }
         __syncwarp();
       }
-      if (run_p >= 0) put(run_p, racc);
-      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f);
+      if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
     }
     __syncwarp();
   }

@@ -161,6 +161,7 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
     P.qcos_z[s] = (float)(0.475 * cos(th));
   }
   P.eta_a_l2 = (float)(-c.eta_ang / M_LN2);
+  P.eta_r_l2 = (float)(-c.eta_rad / M_LN2);
   P.sw_kind = c.switch_kind;
   {
     const double p = c.switch_p;
@@ -311,6 +312,10 @@ extern "C" fnn_status fnn_load_weights(fnn_ctx *ctx, const char *path, const fnn
 
 extern "C" fnn_status fnn_aev(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, float *aev, void *stream) {
   if (!ctx || !sys || !nl || !aev) return FNN_E_INVALID;
+  if ((uintptr_t)aev & 15) {
+    ctx->last_error = "aev must be 16-byte aligned";
+    return FNN_E_INVALID;
+  }
   if (!nl->built || nl->n_atoms != sys->n_atoms || nl->n_mol != sys->n_mol) {
     ctx->last_error = "neighbour list was not built for this system";
     return FNN_E_STATE;

@@ -76,6 +76,7 @@ struct AevParams {
   float hcos_z[NSZ], hsin_z[NSZ];   // the same halved
   float qcos_z[NSZ];            // 0.475 cos: the cos term of d(base)/dc in the adjoint
   float eta_a_l2;               // -eta_a log2(e): the angular Gaussian as a power of two
+  float eta_r_l2;               // -eta_r log2(e): the radial one
   int sw_kind;                  // fnn_switch
   float sw_pm1;                 // polynomial envelope: p - 1, and the coefficients of d^p, d^(p+1), d^(p+2)
   float sw_c0, sw_c1, sw_c2;
@@ -84,6 +85,15 @@ struct AevParams {
 
 // The switching function and its derivative at r < rc (section II.A): cosine, polynomial envelope
 // (Gasteiger et al. 2020), exponential (SpookyNet); the kind is uniform over a launch.
+// sin and cos of y = (pi / 2) min(x, 1 - x), 0 <= x <= 1, by their Taylor series to y^9 and y^8 (y <= pi / 4:
+// truncation below 2e-9 and 3e-8).  The cosine switch is cos^2(pi x / 2) = 1/2 cos(pi x) + 1/2 with
+// x = r / rc: c^2 for x <= 1/2, s^2 above (never negative, accurate to the last bits near the cutoff), and
+// its derivative -(pi / rc) s c.
+__device__ __forceinline__ void quarter_sincos(float x, float &s, float &c) {
+  const float y = 1.57079632679489662f * fminf(x, 1.f - x), z = y * y;
+  s = y * fmaf(z, fmaf(z, fmaf(z, fmaf(z, 2.75573192e-6f, -1.98412698e-4f), 8.33333333e-3f), -1.66666667e-1f), 1.f);
+  c = fmaf(z, fmaf(z, fmaf(z, fmaf(z, 2.48015873e-5f, -1.38888889e-3f), 4.16666667e-2f), -0.5f), 1.f);
+}
 __device__ __forceinline__ float switch_f(const AevParams &P, float r, float rc, float inv_rc) {
   if (P.sw_kind == FNN_SWITCH_POLYNOMIAL) {
     // near the cutoff the terms cancel to O(float eps), which may fall just below zero: clamped, since the
@@ -92,7 +102,10 @@ __device__ __forceinline__ float switch_f(const AevParams &P, float r, float rc,
     return fminf(fmaxf(1.f + powf(d, P.sw_pm1) * d * (P.sw_c0 + d * (P.sw_c1 + d * P.sw_c2)), 0.f), 1.f);
   }
   if (P.sw_kind == FNN_SWITCH_EXPONENTIAL) return expf(-r * r / ((rc - r) * (rc + r)));
-  return 0.5f * cospif(r * inv_rc) + 0.5f;
+  const float x = r * inv_rc;
+  float sn, cs;
+  quarter_sincos(x, sn, cs);
+  return x <= 0.5f ? cs * cs : sn * sn;
 }
 __device__ __forceinline__ float switch_df(const AevParams &P, float r, float rc, float inv_rc, float pi_rc) {
   if (P.sw_kind == FNN_SWITCH_POLYNOMIAL) {
@@ -103,7 +116,9 @@ __device__ __forceinline__ float switch_df(const AevParams &P, float r, float rc
     const float q = (rc - r) * (rc + r);
     return -expf(-r * r / q) * 2.f * r * rc * rc / (q * q);
   }
-  return -0.5f * pi_rc * sinpif(r * inv_rc);
+  float sn, cs;
+  quarter_sincos(r * inv_rc, sn, cs);
+  return -pi_rc * sn * cs;
 }
 
 // per-structure cell-list geometry
