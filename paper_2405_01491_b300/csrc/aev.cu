@@ -106,22 +106,29 @@ struct StageArgs {
   const MolGrid *grid;
 };
 
+// the lanes of a chunk whose element is q, from the three bit planes of the lanes' elements
+__device__ __forceinline__ unsigned elem_lanes(int q, unsigned b0, unsigned b1, unsigned b2) {
+  return (q & 1 ? b0 : ~b0) & (q & 2 ? b1 : ~b1) & (q & 4 ? b2 : ~b2);
+}
+
 // Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
-// FNN_E_CAPACITY) when a list overflows.  On return cnt_*/off_* hold per-element counts and
-// segment starts (warp-uniform).  A row sorted by neighbour element (see PAIR_STRIDE) is staged in one
-// pass, its radial and angular subsets in list order; any other row in two (count, then scatter).
+// FNN_E_CAPACITY) when a list overflows.  The per-element counts are kept one element per lane: on return
+// lane q < NE holds the start of element q's radial (orr) and angular (oa) segment and their counts (cr,
+// ca); lane NE holds the totals in orr and oa.  A row sorted by neighbour element (see PAIR_STRIDE) is
+// staged in one pass, its radial and angular subsets in list order; any other row in two (count, then
+// scatter, stable within an element).
 template <bool FULL>
-__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStageT<FULL> &S, int cnt_r[NE],
-                                int off_r[NE + 1], int cnt_a[NE], int off_a[NE + 1], bool want_dfc,
-                                DevStatus *st) {
-  int lane = threadIdx.x & 31;
-  unsigned lt = (1u << lane) - 1u;
-  int mol = A.atom_mol[i];
+__device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, NbrStageT<FULL> &S, int &orr,
+                                int &oa, int &cr, int &ca, DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int mol = A.atom_mol[i];
   if (mol < 0) return false;   // atom outside every structure (already posted)
-  float4 pi = A.pos[i];
-  MolGrid g = A.grid[mol];
-  float Lx = g.pbc ? g.Lx : 0.f, Ly = g.pbc ? g.Ly : 0.f, Lz = g.pbc ? g.Lz : 0.f;
-  int k0 = (int)min((int64_t)A.row_ptr[i], A.cap), k1 = (int)min((int64_t)A.row_ptr[i + 1], A.cap);
+  const float4 pi = A.pos[i];
+  const MolGrid &g = A.grid[mol];
+  const int pbc = g.pbc;
+  const float Lx = pbc ? g.Lx : 0.f, Ly = pbc ? g.Ly : 0.f, Lz = pbc ? g.Lz : 0.f;
+  const int k0 = (int)min((int64_t)A.row_ptr[i], A.cap), k1 = (int)min((int64_t)A.row_ptr[i + 1], A.cap);
   // list entry k (< k1) of this lane: separation, distance, element and the two cutoff tests
   auto entry = [&](int k, int &j, float &dx, float &dy, float &dz, float &r, int &e, bool &vr, bool &va) {
     vr = va = false;
@@ -130,24 +137,22 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
     dx = dy = dz = r = 0.f;
     if (k < k1) {
       j = A.nbr[k];
-      char4 sh = A.shift[k];
-      float4 pj = A.pos[j];
+      const char4 sh = A.shift[k];
+      const float4 pj = A.pos[j];
       dx = (pj.x - pi.x) + (float)sh.x * Lx;
       dy = (pj.y - pi.y) + (float)sh.y * Ly;
       dz = (pj.z - pi.z) + (float)sh.z * Lz;
-      r = sqrtf(dx * dx + dy * dy + dz * dz);
+      r = sqrt_fast(dx * dx + dy * dy + dz * dz);
       vr = r < P.rc_rad;
       va = r < P.rc_ang;
       e = A.elem[j];
     }
   };
   auto put = [&](int pr, int pa, int j, float dx, float dy, float dz, float r, int e) {
-    if (pr >= 0) {
-      S.rd[pr] = make_float4(dx, dy, dz, r);
-      S.rfc[pr] = switch_f(P, r, P.rc_rad, P.inv_rc_rad);
-      if constexpr (FULL) S.rj[pr] = j;
-      S.re[pr] = (unsigned char)e;
-    }
+    S.rd[pr] = make_float4(dx, dy, dz, r);
+    S.rfc[pr] = switch_f(P, r, P.rc_rad, P.inv_rc_rad);
+    if constexpr (FULL) S.rj[pr] = j;
+    S.re[pr] = (unsigned char)e;
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
       S.ae[pa] = (unsigned char)e;
@@ -155,89 +160,61 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
       if constexpr (FULL) S.adfc[pa] = switch_df(P, r, P.rc_ang, P.inv_rc_ang, P.pi_rc_ang);
     }
   };
+  const bool sorted = k1 - k0 <= A.sorted_upto;
+  cr = ca = 0;   // lane q < NE: entries of element q
+  int nr = 0, na = 0;
+  for (int kb = k0; kb < k1; kb += 32) {   // sorted rows: the only pass; others: counts
+    int j, e;
+    float dx, dy, dz, r;
+    bool vr, va;
+    entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
+    const unsigned mr = __ballot_sync(FULL, vr), ma = __ballot_sync(FULL, va);
+    const unsigned q = elem_lanes(lane, __ballot_sync(FULL, e & 1), __ballot_sync(FULL, e & 2),
+                                  __ballot_sync(FULL, e & 4));
+    cr += __popc(q & mr);
+    ca += __popc(q & ma);
+    if (sorted) {
+      const int pr = nr + __popc(mr & lt), pa = na + __popc(ma & lt);
+      if (vr && pr < RAD_CAP) put(pr, va && pa < ANG_CAP ? pa : -1, j, dx, dy, dz, r, e);
+      nr += __popc(mr);
+      na += __popc(ma);
+    }
+  }
+  if (lane >= NE) cr = ca = 0;
+  int ir = cr, ia = ca;   // inclusive scan over lanes 0 .. NE; lane NE ends with the totals
 #pragma unroll
-  for (int q = 0; q < NE; q++) cnt_r[q] = cnt_a[q] = 0;
-  if (k1 - k0 <= A.sorted_upto) {   // one pass: the subsets of a sorted row are sorted
-    int nr = 0, na = 0;
+  for (int o = 1; o < 8; o <<= 1) {
+    const int vr = __shfl_up_sync(FULL, ir, o), va = __shfl_up_sync(FULL, ia, o);
+    if (lane >= o) {
+      ir += vr;
+      ia += va;
+    }
+  }
+  orr = ir - cr;
+  oa = ia - ca;
+  if (__shfl_sync(FULL, orr, NE) > RAD_CAP || __shfl_sync(FULL, oa, NE) > ANG_CAP) {
+    if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
+    return false;
+  }
+  if (!sorted) {   // pass 2: scatter into element segments (stable within an element)
+    int runr = orr, runa = oa;    // lane q: next free radial / angular slot of element q
     for (int kb = k0; kb < k1; kb += 32) {
       int j, e;
       float dx, dy, dz, r;
       bool vr, va;
       entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
       const unsigned mr = __ballot_sync(FULL, vr), ma = __ballot_sync(FULL, va);
-#pragma unroll
-      for (int q = 0; q < NE; q++) {
-        cnt_r[q] += __popc(__ballot_sync(FULL, vr && e == q));
-        cnt_a[q] += __popc(__ballot_sync(FULL, va && e == q));
-      }
-      const int pr = nr + __popc(mr & lt), pa = na + __popc(ma & lt);
-      if (vr && pr < RAD_CAP) put(pr, va && pa < ANG_CAP ? pa : -1, j, dx, dy, dz, r, e);
-      nr += __popc(mr);
-      na += __popc(ma);
+      const unsigned b0 = __ballot_sync(FULL, e & 1), b1 = __ballot_sync(FULL, e & 2),
+                     b2 = __ballot_sync(FULL, e & 4);
+      const unsigned same = elem_lanes(e, b0, b1, b2), q = elem_lanes(lane, b0, b1, b2);
+      const int br = __shfl_sync(FULL, runr, e), ba = __shfl_sync(FULL, runa, e);
+      if (vr) put(br + __popc(same & mr & lt), va ? ba + __popc(same & ma & lt) : -1, j, dx, dy, dz, r, e);
+      runr += __popc(q & mr);
+      runa += __popc(q & ma);
     }
-    off_r[0] = off_a[0] = 0;
-#pragma unroll
-    for (int q = 0; q < NE; q++) {
-      off_r[q + 1] = off_r[q] + cnt_r[q];
-      off_a[q + 1] = off_a[q] + cnt_a[q];
-    }
-    if (nr > RAD_CAP || na > ANG_CAP) {
-      if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
-      return false;
-    }
-    __syncwarp();
-    return true;
-  }
-  // pass 1: counts per element
-  for (int kb = k0; kb < k1; kb += 32) {
-    int j, e;
-    float dx, dy, dz, r;
-    bool vr, va;
-    entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
-#pragma unroll
-    for (int q = 0; q < NE; q++) {
-      cnt_r[q] += __popc(__ballot_sync(FULL, vr && e == q));
-      cnt_a[q] += __popc(__ballot_sync(FULL, va && e == q));
-    }
-  }
-  off_r[0] = off_a[0] = 0;
-#pragma unroll
-  for (int q = 0; q < NE; q++) {
-    off_r[q + 1] = off_r[q] + cnt_r[q];
-    off_a[q + 1] = off_a[q] + cnt_a[q];
-  }
-  if (off_r[NE] > RAD_CAP || off_a[NE] > ANG_CAP) {
-    if (lane == 0) post_status(st, FNN_E_CAPACITY, -(long long)(i + 1));
-    return false;
-  }
-  int run_r[NE], run_a[NE];
-#pragma unroll
-  for (int q = 0; q < NE; q++) run_r[q] = run_a[q] = 0;
-  // pass 2: scatter into element segments (stable within an element)
-  for (int kb = k0; kb < k1; kb += 32) {
-    int j, e;
-    float dx, dy, dz, r;
-    bool vr, va;
-    entry(kb + lane, j, dx, dy, dz, r, e, vr, va);
-    int pr = -1, pa = -1;
-#pragma unroll
-    for (int q = 0; q < NE; q++) {
-      unsigned mr = __ballot_sync(FULL, vr && e == q);
-      unsigned ma = __ballot_sync(FULL, va && e == q);
-      if (vr && e == q) pr = off_r[q] + run_r[q] + __popc(mr & lt);
-      if (va && e == q) pa = off_a[q] + run_a[q] + __popc(ma & lt);
-      run_r[q] += __popc(mr);
-      run_a[q] += __popc(ma);
-    }
-    if (pr >= 0) put(pr, pa, j, dx, dy, dz, r, e);
   }
   __syncwarp();
   return true;
-}
-
-// the lanes of a chunk whose element is q, from the three bit planes of the lanes' elements
-__device__ __forceinline__ unsigned elem_lanes(int q, unsigned b0, unsigned b1, unsigned b2) {
-  return (q & 1 ? b0 : ~b0) & (q & 2 ? b1 : ~b1) & (q & 4 ? b2 : ~b2);
 }
 
 // Stage atom i's neighbours for the forward (FwdNbr); returns false when the atom has no structure, or
@@ -686,26 +663,33 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
   for (int row = wg; row < nrows; row += nw) {
     int i = A.inv ? A.inv[row] : row;
     if (i < 0) continue;
-    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
-    if (!stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st)) continue;
     const float *G = A.gaev + (size_t)row * NAEV;
+    int orr, oa, cr, ca;
+    if (!stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st)) continue;
     __syncwarp();
     // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
-    int nrad = off_r[NE];
+    const int nrad = __shfl_sync(FULL, orr, NE);
     for (int t = lane; t < nrad; t += 32) {
-      float4 d = S.rd[t];
-      float r = d.w;
-      int e = S.re[t];
-      float fc = S.rfc[t];
-      float dfc = switch_df(P, r, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
+      const float4 d = S.rd[t];
+      const float r = d.w;
+      const float4 *Ge = reinterpret_cast<const float4 *>(G + S.re[t] * NSR);
+      // 1/4 (g_k)' fc + 1/4 g_k fc' with g_k = exp(-eta (r - R_k)^2): g_k (fc' / 4 - eta dr_k fc / 2)
+      const float fc2 = -0.5f * P.eta_r * S.rfc[t];
+      const float dfc4 = 0.25f * switch_df(P, r, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
       float dEdr = 0.f;
+      auto term = [&](float Gk, int k) {
+        const float dr = r - P.shf_r[k];
+        dEdr = fmaf(Gk * exp2f_fast(dr * dr * P.eta_r_l2), fmaf(dr, fc2, dfc4), dEdr);
+      };
 #pragma unroll
-      for (int k = 0; k < NSR; k++) {
-        float dr = r - P.shf_r[k];
-        float gk = __expf(-P.eta_r * dr * dr);
-        dEdr += __ldg(G + e * NSR + k) * 0.25f * gk * (-2.f * P.eta_r * dr * fc + dfc);
+      for (int k4 = 0; k4 < NSR / 4; k4++) {
+        const float4 gv = __ldg(Ge + k4);
+        term(gv.x, 4 * k4);
+        term(gv.y, 4 * k4 + 1);
+        term(gv.z, 4 * k4 + 2);
+        term(gv.w, 4 * k4 + 3);
       }
-      float f = dEdr * rcp_fast(r);
+      const float f = dEdr * rcp_fast(r);
       W.gacc[t][0] = f * d.x;
       W.gacc[t][1] = f * d.y;
       W.gacc[t][2] = f * d.z;
@@ -718,18 +702,22 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     // dE/dd collide at most that often (the short diagonals of a triangle order would pile up to n of
     // them onto the first entries)
     {
-      const int n = off_a[NE];
+      const int n = __shfl_sync(FULL, oa, NE);
       const int T = n * (n - 1) / 2;
+      const int D = (n - 1) >> 1;      // diagonals of n pairs
+      const float inv_n = rcp_fast((float)n);
       for (int c = lane; c < 3 * n; c += 32) (&S.aacc[0][0])[c] = 0.f;   // the radial terms are done
       __syncwarp();
       for (int base = 0; base < T; base += 32) {
         const int t = base + lane;
         if (t < T) {
-          const int D = (n - 1) >> 1;   // diagonals of n pairs
           int d, jc;
           if (t < D * n) {
-            d = t / n + 1;
-            jc = t - (d - 1) * n;
+            d = (int)((float)t * inv_n);   // t / n, corrected below
+            if (d * n > t) d--;
+            else if ((d + 1) * n <= t) d++;
+            jc = t - d * n;
+            d++;
           } else {                      // even n: d = n / 2, j < n / 2
             d = n >> 1;
             jc = t - D * n;
@@ -909,8 +897,18 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
   for (int row = wg; row < nrows; row += nw) {
     OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
     int i = A.inv ? A.inv[row] : row;
-    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];
-    bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, cnt_r, off_r, cnt_a, off_a, true, A.st);
+    int orr, oa, cr, ca;
+    bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st);
+    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];   // the counts warp-uniform
+#pragma unroll
+    for (int q = 0; q < NE; q++) {
+      cnt_r[q] = __shfl_sync(FULL, cr, q);
+      cnt_a[q] = __shfl_sync(FULL, ca, q);
+      off_r[q] = __shfl_sync(FULL, orr, q);
+      off_a[q] = __shfl_sync(FULL, oa, q);
+    }
+    off_r[NE] = __shfl_sync(FULL, orr, NE);
+    off_a[NE] = __shfl_sync(FULL, oa, NE);
     __nv_bfloat16 *fout = A.out_fwd ? A.out_fwd + (size_t)row * NAEV : nullptr;
     if (!ok) {
       for (int c = lane; c < NAEV; c += 32) {
