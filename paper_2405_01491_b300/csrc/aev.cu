@@ -697,99 +697,156 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     __syncwarp();
     // ---- angular: one triplet per lane, enumerated by cyclic diagonals: diagonal d (1 <= d <= (n-1)/2)
     // holds the n pairs {j, (j + d) mod n}, and for even n the last one (d = n/2) the n/2 pairs with
-    // j < n/2, so every pair appears once and within one diagonal the lanes hold distinct j and
-    // distinct k; a batch of 32 spans at most 32/n + 2 diagonals, so an entry's shared-memory atomics on
-    // dE/dd collide at most that often (the short diagonals of a triangle order would pile up to n of
-    // them onto the first entries)
+    // j < n/2, so every pair appears once and within one diagonal the lanes hold distinct j and distinct k.
+    // Up to 32 entries, lane e owns entry e's dE/dd in registers: for each diagonal a batch spans, it takes
+    // its contribution as j from the lane of pair {e, e + d} and as k from the lane of pair {e - d, e}.
+    // Beyond 32 entries the contributions go to shared memory by atomics (a batch spans at most 32/n + 2
+    // diagonals, so an entry's atomics collide at most that often).
     {
       const int n = __shfl_sync(FULL, oa, NE);
       const int T = n * (n - 1) / 2;
       const int D = (n - 1) >> 1;      // diagonals of n pairs
       const float inv_n = rcp_fast((float)n);
-      for (int c = lane; c < 3 * n; c += 32) (&S.aacc[0][0])[c] = 0.f;   // the radial terms are done
-      __syncwarp();
+      // t / n for 0 <= t < 2016, n <= 64
+      auto div_n = [&](int t) {
+        int q = (int)((float)t * inv_n);
+        if (q * n > t) q--;
+        else if ((q + 1) * n <= t) q++;
+        return q;
+      };
+      const bool own = n <= 32;
+      float ax = 0.f, ay = 0.f, az = 0.f;   // lane e < n: entry e (own)
+      if (!own) {
+        for (int c = lane; c < 3 * n; c += 32) (&S.aacc[0][0])[c] = 0.f;   // the radial terms are done
+        __syncwarp();
+      }
       for (int base = 0; base < T; base += 32) {
-        const int t = base + lane;
-        if (t < T) {
-          int d, jc;
-          if (t < D * n) {
-            d = (int)((float)t * inv_n);   // t / n, corrected below
-            if (d * n > t) d--;
-            else if ((d + 1) * n <= t) d++;
-            jc = t - d * n;
-            d++;
-          } else {                      // even n: d = n / 2, j < n / 2
-            d = n >> 1;
-            jc = t - D * n;
-          }
-          const int kc = jc + d < n ? jc + d : jc + d - n;
-          const int ja = min(jc, kc), ka = max(jc, kc);   // list order: e(ja) <= e(ka)
-          const int p = pair_of(S.ae[ja], S.ae[ka]);
-          const float *Gp = G + NRAD + p * 32;
-          const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
-          const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
-          const float r1 = d1.w, r2 = d2.w;
-          const float ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
-          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
-          const float c95 = 0.95f * c;
-          const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
-          const float ds95 = -0.9025f * c * rcp_fast(s95);   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
-          float fs[NSZ], dfs[NSZ];
+        const int t = min(base + lane, T - 1);
+        int d, jc;
+        if (t < D * n) {
+          d = div_n(t);
+          jc = t - d * n;
+          d++;
+        } else {                        // even n: d = n / 2, j < n / 2
+          d = n >> 1;
+          jc = t - D * n;
+        }
+        const int kc = jc + d < n ? jc + d : jc + d - n;
+        const int ja = min(jc, kc), ka = max(jc, kc);   // list order: e(ja) <= e(ka)
+        const int p = pair_of(S.ae[ja], S.ae[ka]);
+        const float *Gp = G + NRAD + p * 32;
+        const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
+        const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
+        const float r1 = d1.w, r2 = d2.w;
+        const float ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
+        const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
+        const float c95 = 0.95f * c;
+        const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+        const float ds95 = -0.9025f * c * rcp_fast(s95);   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
+        float fs[NSZ], dfs[NSZ];
 #pragma unroll
-          for (int s = 0; s < NSZ; s++) {
-            const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-            const float f = exp2f_fast(P.zeta * __log2f(base_s));
-            fs[s] = f;
-            // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
-            dfs[s] = P.zeta * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[s], P.qcos_z[s]);
-          }
-          const float rbar = 0.5f * (r1 + r2);
-          // H_s = sum_m G[m][s] g_m and Hd_s = sum_m G[m][s] dr_m g_m (times -2 eta below: d g_m / d rbar)
-          float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
+        for (int s = 0; s < NSZ; s++) {
+          const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
+          const float f = exp2f_fast(P.zeta * __log2f(base_s));
+          fs[s] = f;
+          // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
+          dfs[s] = P.zeta * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[s], P.qcos_z[s]);
+        }
+        const float rbar = 0.5f * (r1 + r2);
+        // H_s = sum_m G[m][s] g_m and Hd_s = sum_m G[m][s] dr_m g_m (times -2 eta below: d g_m / d rbar)
+        float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
 #pragma unroll
-          for (int m = 0; m < NSA; m++) {
-            const float dr = rbar - P.shf_a[m];
-            const float gm = exp2f_fast(dr * dr * P.eta_a_l2);
-            const float tm = dr * gm;
-            const float4 g4 = __ldg(reinterpret_cast<const float4 *>(Gp + m * NSZ));
-            H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
-            Hd[0] += g4.x * tm; Hd[1] += g4.y * tm; Hd[2] += g4.z * tm; Hd[3] += g4.w * tm;
-          }
-          const float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
-          const float C = f1 * f2;
-          float sH = 0.f, sdH = 0.f, sHd = 0.f;
+        for (int m = 0; m < NSA; m++) {
+          const float dr = rbar - P.shf_a[m];
+          const float gm = exp2f_fast(dr * dr * P.eta_a_l2);
+          const float tm = dr * gm;
+          const float4 g4 = __ldg(reinterpret_cast<const float4 *>(Gp + m * NSZ));
+          H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
+          Hd[0] += g4.x * tm; Hd[1] += g4.y * tm; Hd[2] += g4.z * tm; Hd[3] += g4.w * tm;
+        }
+        const float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
+        // a lane past the last pair contributes nothing (its switch product taken as zero)
+        const float C = base + lane < T ? f1 * f2 : 0.f, Cs = base + lane < T ? 1.f : 0.f;
+        float sH = 0.f, sdH = 0.f, sHd = 0.f;
 #pragma unroll
-          for (int s = 0; s < NSZ; s++) {
-            sH += fs[s] * H[s];
-            sdH += dfs[s] * H[s];
-            sHd += fs[s] * Hd[s];
+        for (int s = 0; s < NSZ; s++) {
+          sH += fs[s] * H[s];
+          sdH += dfs[s] * H[s];
+          sHd += fs[s] * Hd[s];
+        }
+        const float dEdc = 2.f * C * sdH;
+        const float dEdrbar = -4.f * P.eta_a * C * sHd;
+        const float dEdC = 2.f * Cs * sH;
+        const float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
+        const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
+        const float a1 = (dEdr1 - dEdc * c * ir1) * ir1, b1 = dEdc * inv12;
+        const float a2 = (dEdr2 - dEdc * c * ir2) * ir2;
+        // entry ja gets g1, entry ka gets g2: by the cyclic roles, entry jc gets cj and entry kc gets ck
+        const float g1x = a1 * d1.x + b1 * d2.x, g1y = a1 * d1.y + b1 * d2.y, g1z = a1 * d1.z + b1 * d2.z;
+        const float g2x = a2 * d2.x + b1 * d1.x, g2y = a2 * d2.y + b1 * d1.y, g2z = a2 * d2.z + b1 * d1.z;
+        const bool jfirst = jc == ja;
+        const float cjx = jfirst ? g1x : g2x, cjy = jfirst ? g1y : g2y, cjz = jfirst ? g1z : g2z;
+        const float ckx = jfirst ? g2x : g1x, cky = jfirst ? g2y : g1y, ckz = jfirst ? g2z : g1z;
+        if (own) {
+          // the diagonals of this batch, segment by segment: lanes [la, lb) hold diagonal dd with j = s0 + (lane - la)
+          const int tend = min(base + 32, T);
+          for (int ts = base; ts < tend;) {   // warp-uniform
+            int dd, s0, tnext;
+            if (ts < D * n) {
+              const int q = div_n(ts);
+              dd = q + 1;
+              s0 = ts - q * n;
+              tnext = dd * n;
+            } else {
+              dd = n >> 1;
+              s0 = ts - D * n;
+              tnext = T;
+            }
+            const int la = ts - base, lb = min(tnext, tend) - base;
+            // as j: pair {e, e + dd}; as k: pair {e - dd, e} (no wrap on the last diagonal of even n)
+            int jk = lane - dd;
+            if (ts < D * n && jk < 0) jk += n;
+            const int lj = la + lane - s0, lk = la + jk - s0;
+            const bool vj = lane < n && lane >= s0 && lj < lb, vk = lane < n && jk >= s0 && lk < lb;
+            const int sj = vj ? lj : 0, sk = vk ? lk : 0;
+            const float xj = __shfl_sync(FULL, cjx, sj), yj = __shfl_sync(FULL, cjy, sj), zj = __shfl_sync(FULL, cjz, sj);
+            const float xk = __shfl_sync(FULL, ckx, sk), yk = __shfl_sync(FULL, cky, sk), zk = __shfl_sync(FULL, ckz, sk);
+            if (vj) {
+              ax += xj;
+              ay += yj;
+              az += zj;
+            }
+            if (vk) {
+              ax += xk;
+              ay += yk;
+              az += zk;
+            }
+            ts = lb + base;
           }
-          const float dEdc = 2.f * C * sdH;
-          const float dEdrbar = -4.f * P.eta_a * C * sHd;
-          const float dEdC = 2.f * sH;
-          const float dEdr1 = 0.5f * dEdrbar + dEdC * df1 * f2;
-          const float dEdr2 = 0.5f * dEdrbar + dEdC * f1 * df2;
-          const float a1 = (dEdr1 - dEdc * c * ir1) * ir1, b1 = dEdc * inv12;
-          const float a2 = (dEdr2 - dEdc * c * ir2) * ir2;
-          // entry ja gets g1, entry ka gets g2; the atomics go by the cyclic roles (jc, then kc), distinct
-          // within a diagonal, into rows by angular index (distinct banks for up to 32 entries)
-          const float g1x = a1 * d1.x + b1 * d2.x, g1y = a1 * d1.y + b1 * d2.y, g1z = a1 * d1.z + b1 * d2.z;
-          const float g2x = a2 * d2.x + b1 * d1.x, g2y = a2 * d2.y + b1 * d1.y, g2z = a2 * d2.z + b1 * d1.z;
-          const bool jfirst = jc == ja;
-          atomicAdd(&S.aacc[jc][0], jfirst ? g1x : g2x);
-          atomicAdd(&S.aacc[jc][1], jfirst ? g1y : g2y);
-          atomicAdd(&S.aacc[jc][2], jfirst ? g1z : g2z);
-          atomicAdd(&S.aacc[kc][0], jfirst ? g2x : g1x);
-          atomicAdd(&S.aacc[kc][1], jfirst ? g2y : g1y);
-          atomicAdd(&S.aacc[kc][2], jfirst ? g2z : g1z);
+        } else if (base + lane < T) {
+          atomicAdd(&S.aacc[jc][0], cjx);
+          atomicAdd(&S.aacc[jc][1], cjy);
+          atomicAdd(&S.aacc[jc][2], cjz);
+          atomicAdd(&S.aacc[kc][0], ckx);
+          atomicAdd(&S.aacc[kc][1], cky);
+          atomicAdd(&S.aacc[kc][2], ckz);
         }
       }
       __syncwarp();
-      for (int t = lane; t < n; t += 32) {   // distinct angular entries are distinct radial entries
-        const int rj = S.aidx[t];
-        W.gacc[rj][0] += S.aacc[t][0];
-        W.gacc[rj][1] += S.aacc[t][1];
-        W.gacc[rj][2] += S.aacc[t][2];
+      if (own) {
+        if (lane < n) {   // distinct angular entries are distinct radial entries
+          const int rj = S.aidx[lane];
+          W.gacc[rj][0] += ax;
+          W.gacc[rj][1] += ay;
+          W.gacc[rj][2] += az;
+        }
+      } else {
+        for (int t = lane; t < n; t += 32) {
+          const int rj = S.aidx[t];
+          W.gacc[rj][0] += S.aacc[t][0];
+          W.gacc[rj][1] += S.aacc[t][1];
+          W.gacc[rj][2] += S.aacc[t][2];
+        }
       }
     }
     __syncwarp();
