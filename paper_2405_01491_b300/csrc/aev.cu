@@ -45,25 +45,17 @@ __device__ __forceinline__ float sqrt_fast(float x) {
   return y;
 }
 
-// per-warp staging of one centre atom's neighbours, bucketed by element; the neighbour indices and the
-// switch derivatives only where the kernel differentiates (FULL)
+// per-warp staging of one centre atom's neighbours, bucketed by element, for the adjoint and the tangent
+// (the switch values of radial entries are recomputed from r where used)
 template <bool FULL>
 struct NbrStageT {
   float4 rd[RAD_CAP];            // dx, dy, dz, r   (element-sorted, r < rc_rad)
-  int rj[FULL ? RAD_CAP : 1];    // neighbour atom
-  // radial switch fc(r; rc_rad) and element per radial entry; once the radial terms are done the adjoint
-  // reuses the space for the triplets' dE/dd per angular entry
-  union {
-    struct {
-      float rfc[RAD_CAP];
-      unsigned char re[RAD_CAP];
-    };
-    float aacc[ANG_CAP][3];
-  };
+  int rj[RAD_CAP];               // neighbour atom
+  unsigned char re[RAD_CAP];     // element per radial entry
   unsigned char aidx[ANG_CAP];   // angular entry -> radial entry
   unsigned char ae[ANG_CAP];     // angular entry element
   float afc[ANG_CAP];            // angular switch fc(r; rc_ang)
-  float adfc[FULL ? ANG_CAP : 1];  // its derivative
+  float adfc[ANG_CAP];           // its derivative
 };
 using NbrStage = NbrStageT<true>;
 constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
@@ -150,14 +142,13 @@ __device__ bool stage_neighbors(const StageArgs &A, const AevParams &P, int i, N
   };
   auto put = [&](int pr, int pa, int j, float dx, float dy, float dz, float r, int e) {
     S.rd[pr] = make_float4(dx, dy, dz, r);
-    S.rfc[pr] = switch_f(P, r, P.rc_rad, P.inv_rc_rad);
-    if constexpr (FULL) S.rj[pr] = j;
+    S.rj[pr] = j;
     S.re[pr] = (unsigned char)e;
     if (pa >= 0) {
       S.aidx[pa] = (unsigned char)pr;
       S.ae[pa] = (unsigned char)e;
       S.afc[pa] = switch_f(P, r, P.rc_ang, P.inv_rc_ang);
-      if constexpr (FULL) S.adfc[pa] = switch_df(P, r, P.rc_ang, P.inv_rc_ang, P.pi_rc_ang);
+      S.adfc[pa] = switch_df(P, r, P.rc_ang, P.inv_rc_ang, P.pi_rc_ang);
     }
   };
   const bool sorted = k1 - k0 <= A.sorted_upto;
@@ -674,7 +665,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
       const float r = d.w;
       const float4 *Ge = reinterpret_cast<const float4 *>(G + S.re[t] * NSR);
       // 1/4 (g_k)' fc + 1/4 g_k fc' with g_k = exp(-eta (r - R_k)^2): g_k (fc' / 4 - eta dr_k fc / 2)
-      const float fc2 = -0.5f * P.eta_r * S.rfc[t];
+      const float fc2 = -0.5f * P.eta_r * switch_f(P, r, P.rc_rad, P.inv_rc_rad);
       const float dfc4 = 0.25f * switch_df(P, r, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
       float dEdr = 0.f;
       auto term = [&](float Gk, int k) {
@@ -716,10 +707,6 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
       };
       const bool own = n <= 32;
       float ax = 0.f, ay = 0.f, az = 0.f;   // lane e < n: entry e (own)
-      if (!own) {
-        for (int c = lane; c < 3 * n; c += 32) (&S.aacc[0][0])[c] = 0.f;   // the radial terms are done
-        __syncwarp();
-      }
       for (int base = 0; base < T; base += 32) {
         const int t = min(base + lane, T - 1);
         int d, jc;
@@ -824,29 +811,21 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
             ts = lb + base;
           }
         } else if (base + lane < T) {
-          atomicAdd(&S.aacc[jc][0], cjx);
-          atomicAdd(&S.aacc[jc][1], cjy);
-          atomicAdd(&S.aacc[jc][2], cjz);
-          atomicAdd(&S.aacc[kc][0], ckx);
-          atomicAdd(&S.aacc[kc][1], cky);
-          atomicAdd(&S.aacc[kc][2], ckz);
+          const int rjc = S.aidx[jc], rkc = S.aidx[kc];   // distinct angular entries, distinct radial entries
+          atomicAdd(&W.gacc[rjc][0], cjx);
+          atomicAdd(&W.gacc[rjc][1], cjy);
+          atomicAdd(&W.gacc[rjc][2], cjz);
+          atomicAdd(&W.gacc[rkc][0], ckx);
+          atomicAdd(&W.gacc[rkc][1], cky);
+          atomicAdd(&W.gacc[rkc][2], ckz);
         }
       }
       __syncwarp();
-      if (own) {
-        if (lane < n) {   // distinct angular entries are distinct radial entries
-          const int rj = S.aidx[lane];
-          W.gacc[rj][0] += ax;
-          W.gacc[rj][1] += ay;
-          W.gacc[rj][2] += az;
-        }
-      } else {
-        for (int t = lane; t < n; t += 32) {
-          const int rj = S.aidx[t];
-          W.gacc[rj][0] += S.aacc[t][0];
-          W.gacc[rj][1] += S.aacc[t][1];
-          W.gacc[rj][2] += S.aacc[t][2];
-        }
+      if (own && lane < n) {   // distinct angular entries are distinct radial entries
+        const int rj = S.aidx[lane];
+        W.gacc[rj][0] += ax;
+        W.gacc[rj][1] += ay;
+        W.gacc[rj][2] += az;
       }
     }
     __syncwarp();
@@ -984,7 +963,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       const float rdot = (d.x * vx + d.y * vy + d.z * vz) * rcp_fast(d.w);
       W.rv[t] = make_float4(vx, vy, vz, rdot);
       const float dfc = switch_df(P, d.w, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
-      W.rt[t] = make_float2(S.rfc[t] * rdot, dfc * rdot);
+      W.rt[t] = make_float2(switch_f(P, d.w, P.rc_rad, P.inv_rc_rad) * rdot, dfc * rdot);
     }
     __syncwarp();
     // ---- radial
@@ -999,7 +978,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float2 ft = W.rt[t];
           const float gk = __expf(-P.eta_r * dr * dr);
           acc += gk * (-2.f * P.eta_r * dr * ft.x + ft.y);
-          accf += gk * S.rfc[t];
+          accf += gk * switch_f(P, S.rd[t].w, P.rc_rad, P.inv_rc_rad);
         }
         acc += __shfl_xor_sync(FULL, acc, 16);
         accf += __shfl_xor_sync(FULL, accf, 16);
