@@ -22,8 +22,8 @@
 namespace fnn {
 
 static constexpr unsigned FULL = 0xffffffffu;
-constexpr int AEV_WARPS = 4;
-constexpr int AEV_FWD_BLOCKS = 8, AEV_ADJ_BLOCKS = 8;   // resident blocks per SM (64 registers)
+constexpr int AEV_WARPS = 4, ADJ_WARPS = 4;
+constexpr int AEV_FWD_BLOCKS = 8, AEV_ADJ_BLOCKS = 5;   // resident blocks per SM (shared memory)
 
 // 2^x on the special-function unit (ex2.approx.ftz: about 2 ulp; arguments here are <= 0)
 __device__ __forceinline__ float exp2f_fast(float x) {
@@ -44,6 +44,16 @@ __device__ __forceinline__ float sqrt_fast(float x) {
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// 16-byte copies global -> shared (cp.async, L2 only), their commit groups and waits
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // per-warp staging of one centre atom's neighbours, bucketed by element, for the adjoint and the tangent
 // (the switch values of radial entries are recomputed from r where used)
@@ -85,6 +95,7 @@ struct AdjStage {
   NbrStage nb;
   float gacc[RAD_CAP][3];        // dE/dd per radial entry
   double vacc[9];                // virial of the current structure (lane 0), flushed when it changes
+  alignas(16) float gs[NPAIR * 32];   // the angular part of the atom's dE/dAEV row
 };
 
 struct StageArgs {
@@ -657,6 +668,9 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     const float *G = A.gaev + (size_t)row * NAEV;
     int orr, oa, cr, ca;
     if (!stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st)) continue;
+    // the angular part of the dE/dAEV row into shared memory while the radial terms run
+    for (int c = lane; c < NPAIR * 8; c += 32) cp16(W.gs + 4 * c, G + NRAD + 4 * c);
+    cp_commit();
     __syncwarp();
     // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
     const int nrad = __shfl_sync(FULL, orr, NE);
@@ -707,6 +721,8 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
       };
       const bool own = n <= 32;
       float ax = 0.f, ay = 0.f, az = 0.f;   // lane e < n: entry e (own)
+      cp_wait0();
+      __syncwarp();
       for (int base = 0; base < T; base += 32) {
         const int t = min(base + lane, T - 1);
         int d, jc;
@@ -721,7 +737,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
         const int kc = jc + d < n ? jc + d : jc + d - n;
         const int ja = min(jc, kc), ka = max(jc, kc);   // list order: e(ja) <= e(ka)
         const int p = pair_of(S.ae[ja], S.ae[ka]);
-        const float *Gp = G + NRAD + p * 32;
+        const float *Gp = W.gs + p * 32;
         const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
         const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
         const float r1 = d1.w, r2 = d2.w;
@@ -747,7 +763,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
           const float dr = rbar - P.shf_a[m];
           const float gm = exp2f_fast(dr * dr * P.eta_a_l2);
           const float tm = dr * gm;
-          const float4 g4 = __ldg(reinterpret_cast<const float4 *>(Gp + m * NSZ));
+          const float4 g4 = *reinterpret_cast<const float4 *>(Gp + m * NSZ);
           H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
           Hd[0] += g4.x * tm; Hd[1] += g4.y * tm; Hd[2] += g4.z * tm; Hd[3] += g4.w * tm;
         }
@@ -876,10 +892,10 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     for (int q = 0; q < 9; q++) atomicAdd(&A.virial[9 * (size_t)cur_mol + q], vacc[q]);
 }
 
-__global__ void __launch_bounds__(AEV_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
-  __shared__ AdjStage smem[AEV_WARPS];
+__global__ void __launch_bounds__(ADJ_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
+  __shared__ AdjStage smem[ADJ_WARPS];
   const int wl = threadIdx.x >> 5;
-  aev_adjoint_rows(A, smem[wl], blockIdx.x * AEV_WARPS + wl, gridDim.x * AEV_WARPS);
+  aev_adjoint_rows(A, smem[wl], blockIdx.x * ADJ_WARPS + wl, gridDim.x * ADJ_WARPS);
 }
 
 // ------------------------------------------------------------------------------- tangent (JVP)
@@ -1197,14 +1213,6 @@ __device__ bool small_task(const SmallEvalArgs &A, const int *ecount, const int 
   return false;
 }
 
-__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-               "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // copies of one K chunk [kc0, kc0 + kn) into buffer b: the rows' A values and the 32 columns of B (zeros past
 // ncol; every offset is a multiple of four floats, so each copy is 16 aligned bytes)
@@ -1419,8 +1427,8 @@ static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
 }
 
 // one wave of resident blocks (per_sm per SM, the kernel's launch bound) walking the rows
-static int aev_grid(fnn_ctx *ctx, int64_t rows, int per_sm) {
-  int64_t need = (rows + AEV_WARPS - 1) / AEV_WARPS;
+static int aev_grid(fnn_ctx *ctx, int64_t rows, int per_sm, int warps = AEV_WARPS) {
+  int64_t need = (rows + warps - 1) / warps;
   int64_t cap = (int64_t)ctx->num_sms * per_sm;
   if (need > cap) need = cap;
   return need < 1 ? 1 : (int)need;
@@ -1505,7 +1513,7 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_adjoint", s);
-    k_aev_adjoint<<<aev_grid(ctx, rows, AEV_ADJ_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_adjoint<<<aev_grid(ctx, rows, AEV_ADJ_BLOCKS, ADJ_WARPS), ADJ_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_adjoint");
 }
