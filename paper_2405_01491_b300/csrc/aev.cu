@@ -70,6 +70,17 @@ struct NbrStageT {
 using NbrStage = NbrStageT<true>;
 constexpr int SROW = 36;         // padded staging row: rows s (or m) start 4 banks apart
 
+// The non-empty element-pair blocks of an atom's triplets in slot order, then one past the last:
+// bt = {first slot, j0 | k0 << 8 | (a == b) << 16, count of element b, count of element a} with j0, k0 the
+// angular-list starts of elements a and b, {slots, 0, 0, 0} past the last (a block of t triplets takes t
+// rounded up to a multiple of four slots); bi = 1 / count of a (a == b) or of b, the divisor of the block's
+// pair index; bq = slot block | t << 8
+struct BlockTable {
+  int4 bt[NPAIR + 1];
+  float bi[NPAIR + 1];
+  int bq[NPAIR + 1];
+};
+
 // The forward's staging of one centre atom: only what its sums read, in the form they read it
 struct FwdNbr {
   float2 rr[RAD_CAP];            // r, log2 fc(r; rc_rad) - 2   (element-sorted, r < rc_rad; the 1/4 prefactor)
@@ -83,13 +94,7 @@ struct FwdStage {
   alignas(16) float sf[NSZ][SROW];
   alignas(16) float sg[NSA][SROW];
   int sp[32];                    // slot block of a triplet that opens one
-  // the non-empty element-pair blocks of the atom's triplets in slot order, then one past the last:
-  // {first slot, j0 | k0 << 8 | (a == b) << 16, count of element b, count of element a} with j0, k0 the
-  // angular-list starts of elements a and b; {slots, 0, 0, 0} past the last (a block of t triplets takes
-  // t rounded up to a multiple of four slots)
-  int4 bt[NPAIR + 1];
-  float bi[NPAIR + 1];           // 1 / count of a (a == b) or of b: the divisor of the block's pair index
-  int bq[NPAIR + 1];             // slot block | triplets << 8
+  BlockTable tb;
 };
 struct AdjStage {
   NbrStage nb;
@@ -333,76 +338,6 @@ __device__ bool stage_fwd(const StageArgs &A, const AevParams &P, int i, FwdNbr 
 // slot block of the element pair (a, b), a <= b, in row-major upper-triangle order
 __device__ __forceinline__ int pair_of(int a, int b) { return a * NE - a * (a - 1) / 2 + (b - a); }
 
-// The element-pair blocks of an atom's triplets in slot order, one int4 per block (lanes 0 .. NPAIR - 1
-// write theirs): {triplets, j0 | k0 << 8 | (a == b) << 16, count of element b, count of element a} with j0,
-// k0 the angular-list starts of elements a and b
-__device__ __forceinline__ void fill_blocks(int4 *blk, const int off_a[NE + 1], const int cnt_a[NE]) {
-  const int lane = threadIdx.x & 31;
-  if (lane < NPAIR) {
-    int a = 0;
-    while (a + 1 < NE && pair_of(a + 1, a + 1) <= lane) a++;
-    const int b = a + (lane - pair_of(a, a));
-    int oa = 0, ob = 0, na = 0, nb = 0;
-#pragma unroll
-    for (int q = 0; q < NE; q++) {
-      if (q == a) { oa = off_a[q]; na = cnt_a[q]; }
-      if (q == b) { ob = off_a[q]; nb = cnt_a[q]; }
-    }
-    blk[lane] = make_int4(a == b ? na * (na - 1) / 2 : na * nb, oa | (ob << 8) | ((a == b) << 16), nb, na);
-  }
-  __syncwarp();
-}
-
-// This lane's triplet of the next batch of 32 in block order (block by block in slot order): its block
-// pb (NPAIR past the end) and angular entries ja, ka.  Within a block of one element (n entries) the
-// pairs run along cyclic diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds
-// n/2 pairs); within a block of two elements, j-major.  (cp, cu) is the
-// warp-uniform cursor (block, offset) of the batch's first triplet and advances by 32.  Returns the
-// lanes whose triplet opens a block, against the previous lane (lane 0 against the running block run_p).
-__device__ __forceinline__ unsigned next_batch(const int4 *blk, int &cp, int &cu, int run_p, int &pb, int &ja,
-                                               int &ka) {
-  const int lane = threadIdx.x & 31;
-  int u = cu + lane;
-  pb = cp;
-  int4 bk = blk[pb];
-  while (u >= bk.x) {
-    u -= bk.x;
-    if (++pb >= NPAIR) break;
-    bk = blk[pb];
-  }
-  cp = __shfl_sync(FULL, pb, 31);
-  cu = __shfl_sync(FULL, u, 31) + 1;
-  const int pprev = __shfl_up_sync(FULL, pb, 1);
-  const unsigned starts = __ballot_sync(FULL, pb < NPAIR && pb != (lane == 0 ? run_p : pprev));
-  ja = ka = 0;
-  if (pb < NPAIR) {
-    const int j0 = bk.y & 0xff;
-    if (bk.y >> 16) {   // both from element a: the u-th pair of its segment
-      const int n = bk.w, D = (n - 1) >> 1;
-      int d, jc;
-      if (u < D * n) {
-        d = (int)((float)u * rcp_fast((float)n));   // u / n, corrected below
-        if (d * n > u) d--;
-        else if ((d + 1) * n <= u) d++;
-        jc = u - d * n;
-        d++;
-      } else {
-        d = n >> 1;
-        jc = u - D * n;
-      }
-      ja = j0 + jc;
-      ka = j0 + (jc + d < n ? jc + d : jc + d - n);
-    } else {            // j from element a, k from element b
-      int jj = (int)((float)u * rcp_fast((float)bk.z));
-      if (jj * bk.z > u) jj--;
-      else if ((jj + 1) * bk.z <= u) jj++;
-      ja = j0 + jj;
-      ka = ((bk.y >> 8) & 0xff) + (u - jj * bk.z);
-    }
-  }
-  return starts;
-}
-
 template <typename OutT>
 __device__ __forceinline__ void store_out(OutT *p, float v, float inv);
 template <>
@@ -440,6 +375,41 @@ __device__ __forceinline__ void zero_span(T *p, int n) {
   for (int c = lane; c < n16; c += 32) q[c] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// The table of an atom's non-empty blocks from its per-element angular counts and starts (lane q < NE:
+// ca, oa); lane p < NPAIR evaluates block p = (a, b).  Returns the slots (a multiple of four per block) and
+// the number of blocks in nblk.
+__device__ __forceinline__ int build_blocks(BlockTable &W, int ca, int oa, int &nblk) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int a = (lane >= 7) + (lane >= 13) + (lane >= 18) + (lane >= 22) + (lane >= 25) + (lane >= 27);
+  const int b = min(a + lane - pair_of(a, a), NE - 1);
+  const int na = __shfl_sync(FULL, ca, a), nb = __shfl_sync(FULL, ca, b);
+  const int ja0 = __shfl_sync(FULL, oa, a), kb0 = __shfl_sync(FULL, oa, b);
+  const int cnt = lane < NPAIR ? (a == b ? na * (na - 1) / 2 : na * nb) : 0;
+  const unsigned nonempty = __ballot_sync(FULL, cnt > 0);
+  int incl = (cnt + 3) & ~3;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int T = __shfl_sync(FULL, incl, 31);
+  if (cnt > 0) {
+    const int e = __popc(nonempty & lt);
+    W.bt[e] = make_int4(incl - ((cnt + 3) & ~3), ja0 | (kb0 << 8) | ((a == b) << 16), nb, na);
+    W.bi[e] = rcp_fast((float)(a == b ? na : nb));
+    W.bq[e] = lane | (cnt << 8);
+  }
+  nblk = __popc(nonempty);
+  if (lane == 0) {
+    W.bt[nblk] = make_int4(T, 0, 0, 0);
+    W.bq[nblk] = 0;
+    W.bi[nblk] = 0.f;
+  }
+  __syncwarp();
+  return T;
+}
+
 // Slot base + lane of one batch (32 consecutive slots in block order; every block padded to a multiple of
 // four slots) for the lane: the table entry of its block (idx), its angular entries ja, ka, and whether it
 // opens its block; false for a padding slot (ja = ka = 0 then).  cur is the table entry holding the
@@ -447,7 +417,7 @@ __device__ __forceinline__ void zero_span(T *p, int n) {
 // before the one-past-the-last.  Within a block of one element (n entries) the pairs run along cyclic
 // diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds n/2 pairs); within a block
 // of two elements, j-major.
-__device__ __forceinline__ bool batch_triplet(const FwdStage &W, int base, int nblk, int &cur, int &idx, int &ja,
+__device__ __forceinline__ bool batch_triplet(const BlockTable &W, int base, int nblk, int &cur, int &idx, int &ja,
                                               int &ka, bool &opens) {
   const int lane = threadIdx.x & 31;
   if (W.bt[cur + 1].x == base) cur++;   // a block opening at the batch's first slot
@@ -492,7 +462,6 @@ __device__ __forceinline__ bool batch_triplet(const FwdStage &W, int base, int n
 template <typename OutT>
 __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw) {
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
   const AevParams &P = A.P;
   const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   for (int row = wg; row < nrows; row += nw) {
@@ -547,33 +516,8 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
     // complete when its block ends.  The producer lane evaluates one triplet; lane (m, s) then sums
     // pow_s * gauss_m over the batch in four chains, which go to the output row when the block ends.
     {
-      // the table of non-empty blocks: lane p < NPAIR evaluates block p = (a, b)
-      const int a = (lane >= 7) + (lane >= 13) + (lane >= 18) + (lane >= 22) + (lane >= 25) + (lane >= 27);
-      const int b = min(a + lane - pair_of(a, a), NE - 1);
-      const int na = __shfl_sync(FULL, ca, a), nb = __shfl_sync(FULL, ca, b);
-      const int ja0 = __shfl_sync(FULL, oa, a), kb0 = __shfl_sync(FULL, oa, b);
-      const int cnt = lane < NPAIR ? (a == b ? na * (na - 1) / 2 : na * nb) : 0;
-      const unsigned nonempty = __ballot_sync(FULL, cnt > 0);
-      int incl = (cnt + 3) & ~3;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int T = __shfl_sync(FULL, incl, 31);
-      if (cnt > 0) {
-        const int e = __popc(nonempty & lt);
-        W.bt[e] = make_int4(incl - ((cnt + 3) & ~3), ja0 | (kb0 << 8) | ((a == b) << 16), nb, na);
-        W.bi[e] = rcp_fast((float)(a == b ? na : nb));
-        W.bq[e] = lane | (cnt << 8);
-      }
-      const int nblk = __popc(nonempty);
-      if (lane == 0) {
-        W.bt[nblk] = make_int4(T, 0, 0, 0);
-        W.bq[nblk] = 0;
-        W.bi[nblk] = 0.f;
-      }
-      __syncwarp();
+      int nblk;
+      const int T = build_blocks(W.tb, ca, oa, nblk);
       const int s_my = lane & 3, m_my = lane >> 2;
       const float *fr = W.sf[s_my], *gr = W.sg[m_my];
       int run_p = -1;          // slot block being summed (warp-uniform)
@@ -592,7 +536,7 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
         // every lane evaluates a triplet; a padding slot's Gaussians are zero (its switch product -inf)
         int idx, ja, ka;
         bool opens;
-        const bool real = batch_triplet(W, base, nblk, cur, idx, ja, ka, opens);
+        const bool real = batch_triplet(W.tb, base, nblk, cur, idx, ja, ka, opens);
         const float4 u1 = W.nb.au[ja], u2 = W.nb.au[ka];
         const float c95 = 0.95f * (u1.x * u2.x + u1.y * u2.y + u1.z * u2.z);
         const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
@@ -608,7 +552,7 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
           const float dr = rbar - P.shf_a[m];
           W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
         }
-        if (opens) W.sp[lane] = W.bq[idx] & 0xff;
+        if (opens) W.sp[lane] = W.tb.bq[idx] & 0xff;
         // blocks open only at slots that are multiples of four
         const unsigned starts = __ballot_sync(FULL, opens);
         __syncwarp();
@@ -902,10 +846,10 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(
 // t = (dAEV/dx) . V: the directional derivative of every AEV entry along a displacement field V.
 // Radial: d/dt [T_k(r)] = T_k'(r) rdot, rdot = d.(v_j - v_i) / r.  Angular: with c = cos theta,
 // cdot = (d2.vd1 + d1.vd2) / (r1 r2) - c (r1dot / r1 + r2dot / r2),
-// d/dt [2 f_s g_m C] = fdot_s (2 g_m C) + f_s (2 (gdot_m C + g_m Cdot)).  Same staging and block-order
-// enumeration as the forward: the producer lane stages one triplet's f_s, fdot_s, 2 g_m C and
-// 2 (gdot_m C + g_m Cdot); lane (m, s) sums the two products over the batch into a register that goes
-// to the output row when the pair's block ends.
+// d/dt [2 f_s g_m C] = fdot_s (2 g_m C) + f_s (2 (gdot_m C + g_m Cdot)).  The forward's block table and
+// batches (blocks padded to four slots): the producer lane stages one triplet's f_s, fdot_s, 2 g_m C and
+// 2 (gdot_m C + g_m Cdot); lane (m, s) sums the two products over the batch in chains that go to the
+// output row when the pair's block ends.
 struct TanStage {
   NbrStage nb;
   float4 rv[RAD_CAP];            // v_j - v_i, rdot
@@ -916,10 +860,10 @@ struct TanStage {
       alignas(16) float sfd[NSZ][SROW];
       alignas(16) float sg[NSA][SROW];
       alignas(16) float sgd[NSA][SROW];
-      alignas(16) int sp[SROW];
+      int sp[32];                // slot block of a triplet that opens one
     } b;
   };
-  int4 blk[NPAIR];
+  BlockTable tb;
 };
 
 struct AevTanArgs {
@@ -951,16 +895,9 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
     int i = A.inv ? A.inv[row] : row;
     int orr, oa, cr, ca;
     bool ok = i >= 0 && stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st);
-    int cnt_r[NE], off_r[NE + 1], cnt_a[NE], off_a[NE + 1];   // the counts warp-uniform
+    int off_r[NE + 1];   // radial segment starts, warp-uniform
 #pragma unroll
-    for (int q = 0; q < NE; q++) {
-      cnt_r[q] = __shfl_sync(FULL, cr, q);
-      cnt_a[q] = __shfl_sync(FULL, ca, q);
-      off_r[q] = __shfl_sync(FULL, orr, q);
-      off_a[q] = __shfl_sync(FULL, oa, q);
-    }
-    off_r[NE] = __shfl_sync(FULL, orr, NE);
-    off_a[NE] = __shfl_sync(FULL, oa, NE);
+    for (int q = 0; q <= NE; q++) off_r[q] = __shfl_sync(FULL, orr, q);
     __nv_bfloat16 *fout = A.out_fwd ? A.out_fwd + (size_t)row * NAEV : nullptr;
     if (!ok) {
       for (int c = lane; c < NAEV; c += 32) {
@@ -1005,28 +942,39 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       }
     }
     __syncwarp();   // the batch rows below reuse the radial staging
-    // ---- angular
+    // ---- angular (the slots of element pairs without triplets are written as zeros up front)
+    for (int c = lane; c < NPAIR * 32; c += 32) {
+      store_out<OutT>(out + NRAD + c, 0.f, 1.f);
+      if (fout) fout[NRAD + c] = __float2bfloat16(0.f);
+    }
+    __syncwarp();
     {
       const int s_my = lane & 3, m_my = lane >> 2;
-      fill_blocks(W.blk, off_a, cnt_a);
-      const int n = off_a[NE];
-      const int T = n * (n - 1) / 2;
+      int nblk;
+      const int T = build_blocks(W.tb, ca, oa, nblk);
       int run_p = -1;
-      float racc = 0.f, raccf = 0.f;   // tangent and (fout) forward sums of the running block
-      auto put = [&](int pp, float v, float vf) {
-        store_out<OutT>(out + NRAD + pp * 32 + lane, v, 1.f);
-        if (fout) fout[NRAD + pp * 32 + lane] = __float2bfloat16(vf);
+      float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;      // tangent sums of the running block
+      float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;      // and (fout) its forward sums
+      auto open = [&](int pn) {
+        if (run_p >= 0) {
+          store_out<OutT>(out + NRAD + run_p * 32 + lane, (r0 + r1) + (r2 + r3), 1.f);
+          if (fout) fout[NRAD + run_p * 32 + lane] = __float2bfloat16((q0 + q1) + (q2 + q3));
+        }
+        r0 = r1 = r2 = r3 = q0 = q1 = q2 = q3 = 0.f;
+        run_p = pn;
       };
-      int cp = 0, cu = 0;
+      const float *fr = W.b.sf[s_my], *fdr = W.b.sfd[s_my], *gr = W.b.sg[m_my], *gdr = W.b.sgd[m_my];
+      int cur = 0;
       for (int base = 0; base < T; base += 32) {
-        int pb, ja, ka;
-        const unsigned starts = next_batch(W.blk, cp, cu, run_p, pb, ja, ka);
-        if (pb < NPAIR) {
+        // every lane evaluates a triplet; a padding slot's switch product and its rate are zero
+        int idx, ja, ka;
+        bool opens;
+        const bool real = batch_triplet(W.tb, base, nblk, cur, idx, ja, ka, opens);
+        {
           const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
           const float4 d1 = S.rd[rj1], d2 = S.rd[rj2], v1 = W.rv[rj1], v2 = W.rv[rj2];
           const float r1 = d1.w, r2 = d2.w, ir1 = rcp_fast(r1), ir2 = rcp_fast(r2), inv12 = ir1 * ir2;
-          // cos theta formed as the forward kernel forms it
-          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * rcp_fast(r1 * r2);
+          const float c = (d1.x * d2.x + d1.y * d2.y + d1.z * d2.z) * inv12;
           const float cdot = (d2.x * v1.x + d2.y * v1.y + d2.z * v1.z + d1.x * v2.x + d1.y * v2.y + d1.z * v2.z) * inv12 -
                              c * (v1.w * ir1 + v2.w * ir2);
           const float c95 = 0.95f * c;
@@ -1043,7 +991,8 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           }
           const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
           const float f1 = S.afc[ja], f2 = S.afc[ka];
-          const float C = f1 * f2, Cdot = S.adfc[ja] * v1.w * f2 + f1 * S.adfc[ka] * v2.w;
+          const float C = real ? f1 * f2 : 0.f;
+          const float Cdot = real ? S.adfc[ja] * v1.w * f2 + f1 * S.adfc[ka] * v2.w : 0.f;
           // 2 g C and 2 (gdot C + g Cdot) = g (dr (-4 eta rbdot C) + 2 Cdot), gdot = -2 eta dr g rbdot
           const float C2 = 2.f * C, a2 = -4.f * P.eta_a * rbdot * C, c2 = 2.f * Cdot;
 #pragma unroll
@@ -1053,54 +1002,30 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
             W.b.sg[m][lane] = g * C2;
             W.b.sgd[m][lane] = g * fmaf(dr, a2, c2);
           }
-          W.b.sp[lane] = pb;
-        } else {
-#pragma unroll
-          for (int sidx = 0; sidx < NSZ; sidx++) W.b.sf[sidx][lane] = W.b.sfd[sidx][lane] = 0.f;
-#pragma unroll
-          for (int m = 0; m < NSA; m++) W.b.sg[m][lane] = W.b.sgd[m][lane] = 0.f;
-          W.b.sp[lane] = -1;
+          if (opens) W.b.sp[lane] = W.tb.bq[idx] & 0xff;
         }
+        // blocks open only at slots that are multiples of four
+        const unsigned starts = __ballot_sync(FULL, opens);
         __syncwarp();
-        const int nt = min(32, T - base);
-        const float *fr = W.b.sf[s_my], *fdr = W.b.sfd[s_my], *gr = W.b.sg[m_my], *gdr = W.b.sgd[m_my];
-        for (int q = 0; q < nt; q += 4) {
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
           const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
           const float4 fdv = *reinterpret_cast<const float4 *>(fdr + q);
           const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
           const float4 gdv = *reinterpret_cast<const float4 *>(gdr + q);
-          const unsigned st4 = (starts >> q) & 0xfu;
-          if (st4 == 0u) {
-            racc = fmaf(fdv.x, gv.x, fmaf(fv.x, gdv.x, racc));
-            racc = fmaf(fdv.y, gv.y, fmaf(fv.y, gdv.y, racc));
-            racc = fmaf(fdv.z, gv.z, fmaf(fv.z, gdv.z, racc));
-            racc = fmaf(fdv.w, gv.w, fmaf(fv.w, gdv.w, racc));
-            raccf = fmaf(fv.x, gv.x, raccf);
-            raccf = fmaf(fv.y, gv.y, raccf);
-            raccf = fmaf(fv.z, gv.z, raccf);
-            raccf = fmaf(fv.w, gv.w, raccf);
-          } else {
-            const float fa[4] = {fv.x, fv.y, fv.z, fv.w}, fda[4] = {fdv.x, fdv.y, fdv.z, fdv.w};
-            const float ga[4] = {gv.x, gv.y, gv.z, gv.w}, gda[4] = {gdv.x, gdv.y, gdv.z, gdv.w};
-#pragma unroll
-            for (int uu = 0; uu < 4; uu++) {
-              if (q + uu >= nt) break;
-              if ((st4 >> uu) & 1u) {
-                const int pn = W.b.sp[q + uu];
-                if (run_p >= 0) put(run_p, racc, raccf);
-                for (int pp = run_p + 1; pp < pn; pp++) put(pp, 0.f, 0.f);
-                racc = raccf = 0.f;
-                run_p = pn;
-              }
-              racc = fmaf(fda[uu], ga[uu], fmaf(fa[uu], gda[uu], racc));
-              raccf = fmaf(fa[uu], ga[uu], raccf);
-            }
-          }
+          if ((starts >> q) & 1u) open(W.b.sp[q]);
+          r0 = fmaf(fdv.x, gv.x, fmaf(fv.x, gdv.x, r0));
+          r1 = fmaf(fdv.y, gv.y, fmaf(fv.y, gdv.y, r1));
+          r2 = fmaf(fdv.z, gv.z, fmaf(fv.z, gdv.z, r2));
+          r3 = fmaf(fdv.w, gv.w, fmaf(fv.w, gdv.w, r3));
+          q0 = fmaf(fv.x, gv.x, q0);
+          q1 = fmaf(fv.y, gv.y, q1);
+          q2 = fmaf(fv.z, gv.z, q2);
+          q3 = fmaf(fv.w, gv.w, q3);
         }
         __syncwarp();
       }
-      if (run_p >= 0) put(run_p, racc, raccf);
-      for (int pp = run_p + 1; pp < NPAIR; pp++) put(pp, 0.f, 0.f);
+      open(-1);
     }
     __syncwarp();
   }
