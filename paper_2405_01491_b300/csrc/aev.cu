@@ -410,30 +410,10 @@ __device__ __forceinline__ int build_blocks(BlockTable &W, int ca, int oa, int &
   return T;
 }
 
-// Slot base + lane of one batch (32 consecutive slots in block order; every block padded to a multiple of
-// four slots) for the lane: the table entry of its block (idx), its angular entries ja, ka, and whether it
-// opens its block; false for a padding slot (ja = ka = 0 then).  cur is the table entry holding the
-// batch's first slot (warp-uniform) and is advanced to the one holding its last; nblk the table's entries
-// before the one-past-the-last.  Within a block of one element (n entries) the pairs run along cyclic
-// diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds n/2 pairs); within a block
-// of two elements, j-major.
-__device__ __forceinline__ bool batch_triplet(const BlockTable &W, int base, int nblk, int &cur, int &idx, int &ja,
-                                              int &ka, bool &opens) {
-  const int lane = threadIdx.x & 31;
-  if (W.bt[cur + 1].x == base) cur++;   // a block opening at the batch's first slot
-  // the blocks opening inside the batch, as bits of the slot offsets (table entries one per lane)
-  unsigned bit = 0u;
-  if (lane <= nblk) {
-    const int o = W.bt[lane].x - base;
-    if (o > 0 && o < 32) bit = 1u << o;
-  }
-  const unsigned M = __reduce_or_sync(FULL, bit);
-  idx = cur + __popc(M & ((2u << lane) - 1u));
-  cur += __popc(M);
+// The pair of slot w of table entry idx (ja, ka: angular entries); false for a padding slot (ja = ka = 0)
+__device__ __forceinline__ bool block_pair(const BlockTable &W, int idx, int w, int &ja, int &ka) {
   const int4 bk = W.bt[idx];
-  const int w = base + lane - bk.x;
   const int cnt = W.bq[idx] >> 8;
-  opens = w == 0 && cnt > 0;
   const bool diag = (bk.y >> 16) != 0;
   const int n = bk.w, dv = diag ? n : bk.z, D = (n - 1) >> 1;
   int q = (int)((float)w * W.bi[idx]);   // w / dv, corrected below
@@ -455,6 +435,89 @@ __device__ __forceinline__ bool batch_triplet(const BlockTable &W, int base, int
   ja = real ? j0 + jrel : 0;
   ka = real ? j0 + krel : 0;
   return real;
+}
+
+// Slot base + lane of one batch (32 consecutive slots in block order; every block padded to a multiple of
+// four slots) for the lane: the table entry of its block (idx), its angular entries ja, ka, and whether it
+// opens its block; false for a padding slot (ja = ka = 0 then).  cur is the table entry holding the
+// batch's first slot (warp-uniform) and is advanced to the one holding its last; nblk the table's entries
+// before the one-past-the-last.  Within a block of one element (n entries) the pairs run along cyclic
+// diagonals {j, (j + d) mod n}, d = 1 .. n/2 (for even n the last diagonal holds n/2 pairs); within a block
+// of two elements, j-major.
+__device__ __forceinline__ bool batch_triplet(const BlockTable &W, int base, int nblk, int &cur, int &idx, int &ja,
+                                              int &ka, bool &opens) {
+  const int lane = threadIdx.x & 31;
+  if (W.bt[cur + 1].x == base) cur++;   // a block opening at the batch's first slot
+  // the blocks opening inside the batch, as bits of the slot offsets (table entries one per lane)
+  unsigned bit = 0u;
+  if (lane <= nblk) {
+    const int o = W.bt[lane].x - base;
+    if (o > 0 && o < 32) bit = 1u << o;
+  }
+  const unsigned M = __reduce_or_sync(FULL, bit);
+  idx = cur + __popc(M & ((2u << lane) - 1u));
+  cur += __popc(M);
+  const int w = base + lane - W.bt[idx].x;
+  opens = w == 0 && (W.bq[idx] >> 8) > 0;
+  return block_pair(W, idx, w, ja, ka);
+}
+
+// The lane's triplet (angular entries ja, ka) into the batch rows: 4 section powers and 8 Gaussians; a
+// padding slot's Gaussians are zero (its switch product -inf in the exponent)
+__device__ __forceinline__ void produce_triplet(FwdStage &W, const AevParams &P, bool real, int ja, int ka) {
+  const int lane = threadIdx.x & 31;
+  const float4 u1 = W.nb.au[ja], u2 = W.nb.au[ka];
+  const float c95 = 0.95f * (u1.x * u2.x + u1.y * u2.y + u1.z * u2.z);
+  const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+#pragma unroll
+  for (int s = 0; s < NSZ; s++) {
+    const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
+    W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
+  }
+  // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
+  const float rbar = u1.w + u2.w, lf = real ? W.nb.la[ja] + W.nb.la[ka] : __int_as_float(0xff800000);
+#pragma unroll
+  for (int m = 0; m < NSA; m++) {
+    const float dr = rbar - P.shf_a[m];
+    W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
+  }
+}
+
+// Radial slots of a staged row: lane (h, k) sums shift k over every other neighbour of each element
+// segment; elements without neighbours are skipped (their slots hold zeros already) unless zeros is set
+template <typename OutT>
+__device__ __forceinline__ void radial_row(const AevFwdArgs &A, const FwdStage &W, OutT *out, __nv_bfloat16 *lo,
+                                           int orr, bool zeros) {
+  const int lane = threadIdx.x & 31;
+  const AevParams &P = A.P;
+  const int h = lane >> 4, k = lane & 15;
+  const float Rk = P.shf_r[k], ce = P.eta_r_l2;
+#pragma unroll 1
+  for (int q = 0; q < NE; q++) {
+    const int t0 = __shfl_sync(FULL, orr, q), t1 = __shfl_sync(FULL, orr, q + 1);
+    if (t0 == t1 && !zeros) continue;
+    int t = t0 + h;
+    float a0 = 0.f, a1 = 0.f;
+    for (; t + 6 < t1; t += 8) {
+      const float2 v0 = W.nb.rr[t], v1 = W.nb.rr[t + 2], v2 = W.nb.rr[t + 4], v3 = W.nb.rr[t + 6];
+      const float d0 = v0.x - Rk, d1 = v1.x - Rk, d2 = v2.x - Rk, d3 = v3.x - Rk;
+      a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
+      a1 += exp2f_fast(fmaf(d1 * d1, ce, v1.y));
+      a0 += exp2f_fast(fmaf(d2 * d2, ce, v2.y));
+      a1 += exp2f_fast(fmaf(d3 * d3, ce, v3.y));
+    }
+    for (; t < t1; t += 2) {
+      const float2 v0 = W.nb.rr[t];
+      const float d0 = v0.x - Rk;
+      a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
+    }
+    float acc = a0 + a1;
+    acc += __shfl_xor_sync(FULL, acc, 16);
+    if (lane < 16) {
+      store_out<OutT>(out + q * NSR + k, acc, A.out_inv);
+      store_lo(lo, q * NSR + k, acc);
+    }
+  }
 }
 
 // One warp's share of the forward: rows wg, wg + nw, ..., staged in W (the kernel below, and the fused
@@ -480,37 +543,7 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
     zero_span(out, NAEV);
     if (lo) zero_span(lo, NAEV);
     __syncwarp();   // orders the zeros before the lanes' own stores below
-    // ---- radial: lane (h, k) sums shift k over every other neighbour of each element segment
-    {
-      const int h = lane >> 4, k = lane & 15;
-      const float Rk = P.shf_r[k], ce = P.eta_r_l2;
-#pragma unroll 1
-      for (int q = 0; q < NE; q++) {
-        const int t0 = __shfl_sync(FULL, orr, q), t1 = __shfl_sync(FULL, orr, q + 1);
-        if (t0 == t1) continue;
-        int t = t0 + h;
-        float a0 = 0.f, a1 = 0.f;
-        for (; t + 6 < t1; t += 8) {
-          const float2 v0 = W.nb.rr[t], v1 = W.nb.rr[t + 2], v2 = W.nb.rr[t + 4], v3 = W.nb.rr[t + 6];
-          const float d0 = v0.x - Rk, d1 = v1.x - Rk, d2 = v2.x - Rk, d3 = v3.x - Rk;
-          a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
-          a1 += exp2f_fast(fmaf(d1 * d1, ce, v1.y));
-          a0 += exp2f_fast(fmaf(d2 * d2, ce, v2.y));
-          a1 += exp2f_fast(fmaf(d3 * d3, ce, v3.y));
-        }
-        for (; t < t1; t += 2) {
-          const float2 v0 = W.nb.rr[t];
-          const float d0 = v0.x - Rk;
-          a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
-        }
-        float acc = a0 + a1;
-        acc += __shfl_xor_sync(FULL, acc, 16);
-        if (lane < 16) {
-          store_out<OutT>(out + q * NSR + k, acc, A.out_inv);
-          store_lo(lo, q * NSR + k, acc);
-        }
-      }
-    }
+    radial_row<OutT>(A, W, out, lo, orr, false);
     // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch,
     // enumerated block by block in slot order (element pair (a, b), a <= b), so a pair's 32 slots are
     // complete when its block ends.  The producer lane evaluates one triplet; lane (m, s) then sums
@@ -537,21 +570,7 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
         int idx, ja, ka;
         bool opens;
         const bool real = batch_triplet(W.tb, base, nblk, cur, idx, ja, ka, opens);
-        const float4 u1 = W.nb.au[ja], u2 = W.nb.au[ka];
-        const float c95 = 0.95f * (u1.x * u2.x + u1.y * u2.y + u1.z * u2.z);
-        const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
-#pragma unroll
-        for (int s = 0; s < NSZ; s++) {
-          const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-          W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
-        }
-        // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
-        const float rbar = u1.w + u2.w, lf = real ? W.nb.la[ja] + W.nb.la[ka] : __int_as_float(0xff800000);
-#pragma unroll
-        for (int m = 0; m < NSA; m++) {
-          const float dr = rbar - P.shf_a[m];
-          W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
-        }
+        produce_triplet(W, P, real, ja, ka);
         if (opens) W.sp[lane] = W.tb.bq[idx] & 0xff;
         // blocks open only at slots that are multiples of four
         const unsigned starts = __ballot_sync(FULL, opens);
@@ -569,6 +588,72 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
         __syncwarp();
       }
       if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
+    }
+    __syncwarp();
+  }
+}
+
+// The same rows with K warps per row (K > 1; for systems with fewer rows than warps): warp part 0 of a
+// row writes the radial slots and the zeros of element pairs without triplets, parts 1 .. K-1 take the
+// row's non-empty element-pair blocks in turn, each block's slots summed by one warp from its own batches
+template <typename OutT>
+__device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int nw, int K) {
+  const int lane = threadIdx.x & 31;
+  const AevParams &P = A.P;
+  const int part = wg % K, groups = nw / K;
+  if (wg >= groups * K) return;
+  const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  const int s_my = lane & 3, m_my = lane >> 2;
+  const float *fr = W.sf[s_my], *gr = W.sg[m_my];
+  for (int row = wg / K; row < nrows; row += groups) {
+    OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
+    __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
+    const int i = A.inv ? A.inv[row] : row;
+    int orr, oa, ca;
+    const bool ok = i >= 0 && stage_fwd(A.sa, P, i, W.nb, orr, oa, ca, A.st);
+    if (!ok) {
+      if (part == 0) {
+        for (int c = lane; c < NAEV; c += 32) {
+          store_out<OutT>(out + c, 0.f, A.out_inv);
+          store_lo(lo, c, 0.f);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    int nblk;
+    build_blocks(W.tb, ca, oa, nblk);
+    if (part == 0) {
+      radial_row<OutT>(A, W, out, lo, orr, true);
+      const unsigned present = __reduce_or_sync(FULL, lane < nblk ? 1u << (W.tb.bq[lane] & 0xff) : 0u);
+      for (int pp = 0; pp < NPAIR; pp++)
+        if (!((present >> pp) & 1u)) {
+          store_out<OutT>(out + NRAD + pp * 32 + lane, 0.f, A.out_inv);
+          store_lo(lo, NRAD + pp * 32 + lane, 0.f);
+        }
+    } else {
+      for (int e = part - 1; e < nblk; e += K - 1) {
+        const int s0 = W.tb.bt[e].x, s1 = W.tb.bt[e + 1].x, pb = W.tb.bq[e] & 0xff;
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+        for (int base = s0; base < s1; base += 32) {
+          int ja, ka;
+          const bool real = block_pair(W.tb, e, base - s0 + lane, ja, ka);
+          produce_triplet(W, P, real, ja, ka);
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 32; q += 4) {
+            const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
+            const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
+            r0 = fmaf(fv.x, gv.x, r0);
+            r1 = fmaf(fv.y, gv.y, r1);
+            r2 = fmaf(fv.z, gv.z, r2);
+            r3 = fmaf(fv.w, gv.w, r3);
+          }
+          __syncwarp();
+        }
+        store_out<OutT>(out + NRAD + pb * 32 + lane, (r0 + r1) + (r2 + r3), A.out_inv);
+        store_lo(lo, NRAD + pb * 32 + lane, (r0 + r1) + (r2 + r3));
+      }
     }
     __syncwarp();
   }
@@ -597,7 +682,10 @@ struct AevAdjArgs {
 // The dE/dAEV row is read through the L1 cache where it is used (4 KB per atom, re-read by the warp's
 // lanes): staging it in shared memory would cap the number of resident warps.
 // One warp's share of the adjoint: rows wg, wg + nw, ..., staged in W
-__device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &W, int wg, int nw) {
+// With K > 1 warps per row (systems with fewer rows than warps) warp part 0 of a row takes its radial
+// terms and parts 1 .. K-1 its angular batches in turn; each warp scatters what it summed (the forces and
+// virials are sums).
+__device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &W, int wg, int nw, int K = 1) {
   int lane = threadIdx.x & 31;
   NbrStage &S = W.nb;
   const AevParams &P = A.P;
@@ -606,19 +694,27 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
   if (lane == 0)
     for (int q = 0; q < 9; q++) vacc[q] = 0.0;
   int cur_mol = -1;
-  for (int row = wg; row < nrows; row += nw) {
+  const int part = wg % K, groups = nw / K;
+  if (wg >= groups * K) return;
+  const bool do_rad = part == 0, do_ang = K == 1 || part > 0;
+  const int apart = K == 1 ? 0 : part - 1, aparts = K == 1 ? 1 : K - 1;   // this warp's share of the batches
+  for (int row = wg / K; row < nrows; row += groups) {
     int i = A.inv ? A.inv[row] : row;
     if (i < 0) continue;
     const float *G = A.gaev + (size_t)row * NAEV;
     int orr, oa, cr, ca;
     if (!stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st)) continue;
     // the angular part of the dE/dAEV row into shared memory while the radial terms run
-    for (int c = lane; c < NPAIR * 8; c += 32) cp16(W.gs + 4 * c, G + NRAD + 4 * c);
-    cp_commit();
+    if (do_ang) {
+      for (int c = lane; c < NPAIR * 8; c += 32) cp16(W.gs + 4 * c, G + NRAD + 4 * c);
+      cp_commit();
+    }
     __syncwarp();
     // ---- radial: lane per entry, dE/dr = sum_k G[e*16+k] dT_k/dr
     const int nrad = __shfl_sync(FULL, orr, NE);
-    for (int t = lane; t < nrad; t += 32) {
+    if (!do_rad)
+      for (int t = lane; t < nrad; t += 32) W.gacc[t][0] = W.gacc[t][1] = W.gacc[t][2] = 0.f;
+    for (int t = lane; do_rad && t < nrad; t += 32) {
       const float4 d = S.rd[t];
       const float r = d.w;
       const float4 *Ge = reinterpret_cast<const float4 *>(G + S.re[t] * NSR);
@@ -665,9 +761,9 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
       };
       const bool own = n <= 32;
       float ax = 0.f, ay = 0.f, az = 0.f;   // lane e < n: entry e (own)
-      cp_wait0();
+      if (do_ang) cp_wait0();
       __syncwarp();
-      for (int base = 0; base < T; base += 32) {
+      for (int base = 32 * apart; do_ang && base < T; base += 32 * aparts) {
         const int t = min(base + lane, T - 1);
         int d, jc;
         if (t < D * n) {
@@ -796,6 +892,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     for (int q = 0; q < 9; q++) w[q] = 0.f;
     for (int t = lane; t < nrad; t += 32) {
       float g0 = W.gacc[t][0], g1 = W.gacc[t][1], g2 = W.gacc[t][2];
+      if (K > 1 && g0 == 0.f && g1 == 0.f && g2 == 0.f) continue;   // not this part's entry
       int j = S.rj[t];
       atomicAdd(&A.F[3 * (size_t)j + 0], -g0);
       atomicAdd(&A.F[3 * (size_t)j + 1], -g1);
@@ -1283,7 +1380,10 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   if (A.virial)
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 9 * A.NM; q += gridDim.x * blockDim.x) A.virial[q] = 0.0;
   // AEV rows (atom order)
-  aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw);
+  // a row per warp, or (fewer rows than warps) up to eight warps per row
+  const int Kw = min(8, max(1, nw / max(N, 1)));
+  if (Kw > 1) aev_forward_parts<float>(A.fa, S.fwd[warp], wg, nw, Kw);
+  else aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw);
   if (!grid_barrier(A.bar, A.st)) return;
   SmallDense &D = S.d;
   const int MH1 = M * H1;
@@ -1315,7 +1415,7 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   // forces and virials (a warp per atom, the first warps); the energies meanwhile on the last warps, a warp
   // per structure: lanes over its atoms, then a shuffle tree (a fixed order)
   __syncthreads();
-  aev_adjoint_rows(A.aa, S.adj[warp], wg, nw);
+  aev_adjoint_rows(A.aa, S.adj[warp], wg, nw, Kw);
   for (int m = nw - 1 - wg; m < A.NM; m += nw) {
     const int a0 = max(A.mol_offsets[m], 0), a1 = min(A.mol_offsets[m + 1], N);
     double e = 0.0;
