@@ -114,11 +114,6 @@ struct StageArgs {
   const MolGrid *grid;
 };
 
-// the lanes of a chunk whose element is q, from the three bit planes of the lanes' elements
-__device__ __forceinline__ unsigned elem_lanes(int q, unsigned b0, unsigned b1, unsigned b2) {
-  return (q & 1 ? b0 : ~b0) & (q & 2 ? b1 : ~b1) & (q & 4 ? b2 : ~b2);
-}
-
 // Stage atom i's neighbours; returns false when the atom has no structure, or (after posting
 // FNN_E_CAPACITY) when a list overflows.  The per-element counts are kept one element per lane: on return
 // lane q < NE holds the start of element q's radial (orr) and angular (oa) segment and their counts (cr,

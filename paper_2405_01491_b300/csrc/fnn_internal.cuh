@@ -121,6 +121,11 @@ __device__ __forceinline__ float switch_df(const AevParams &P, float r, float rc
   return -pi_rc * sn * cs;
 }
 
+// the lanes of a 32-entry chunk whose element is q, from the three bit planes of the lanes' elements
+__device__ __forceinline__ unsigned elem_lanes(int q, unsigned b0, unsigned b1, unsigned b2) {
+  return (q & 1 ? b0 : ~b0) & (q & 2 ? b1 : ~b1) & (q & 4 ? b2 : ~b2);
+}
+
 // per-structure cell-list geometry
 struct MolGrid {
   float ox, oy, oz;       // origin of the grid (gas phase: bounding-box minimum; periodic: 0)

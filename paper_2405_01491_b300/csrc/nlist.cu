@@ -426,10 +426,15 @@ __device__ MolGrid make_grid(const fnn_system &sys, int m, int n, int pbc, float
     g.ox = bb[0]; g.oy = bb[1]; g.oz = bb[2];
     for (int a = 0; a < 3; a++) ext[a] = (double)bb[3 + a] - (double)bb[a];
   }
+  // cell counts and spacings in float32 (the edge's 1e-4 margin covers their rounding); the band below
+  // stays in float64
   int d[3];
+  float fext[3];
+  const float fedge = (float)edge;
   for (int a = 0; a < 3; a++) {
-    double q = ext[a] / edge;
-    d[a] = (q >= 1.0 && q < 1e6) ? (int)floor(q) : 1;
+    fext[a] = (float)ext[a];
+    const float q = fext[a] / fedge;
+    d[a] = (q >= 1.f && q < 1e6f) ? (int)floorf(q) : 1;
   }
   long long limit = n > 0 ? 2LL * n : 1;
   while ((long long)d[0] * d[1] * d[2] > limit) {
@@ -450,13 +455,13 @@ __device__ MolGrid make_grid(const fnn_system &sys, int m, int n, int pbc, float
     double e = 4.0 * u * S;
     double tau = 2.0 * (3.4641016151377544 * e * R * 1.01 + 3.0 * e * e + 4.0 * u * R * R) + 1e-30;
     g.tau = (float)(tau * (1.0 + 1e-6));
-    g.iLx = g.pbc ? (float)(1.0 / (double)g.Lx) : 0.f;
-    g.iLy = g.pbc ? (float)(1.0 / (double)g.Ly) : 0.f;
-    g.iLz = g.pbc ? (float)(1.0 / (double)g.Lz) : 0.f;
+    g.iLx = g.pbc ? 1.f / g.Lx : 0.f;
+    g.iLy = g.pbc ? 1.f / g.Ly : 0.f;
+    g.iLz = g.pbc ? 1.f / g.Lz : 0.f;
   }
-  g.ix = ext[0] > 0 ? (float)(d[0] / ext[0]) : 0.f;
-  g.iy = ext[1] > 0 ? (float)(d[1] / ext[1]) : 0.f;
-  g.iz = ext[2] > 0 ? (float)(d[2] / ext[2]) : 0.f;
+  g.ix = fext[0] > 0.f ? (float)d[0] / fext[0] : 0.f;
+  g.iy = fext[1] > 0.f ? (float)d[1] / fext[1] : 0.f;
+  g.iz = fext[2] > 0.f ? (float)d[2] / fext[2] : 0.f;
   *cells = d[0] * d[1] * d[2];
   return g;
 }
@@ -955,33 +960,32 @@ __global__ void __launch_bounds__(256) k_pairs_compact(fnn_system sys, const Mol
         }
       }
 #pragma unroll
-      for (int c = 0; c < NCH; c++) ev[c] = 32 * c + lane < n ? (int)elem[jv[c]] : -1;
-      int off[NE];
-#pragma unroll
-      for (int q = 0; q < NE; q++) off[q] = 0;
+      for (int c = 0; c < NCH; c++) ev[c] = 32 * c + lane < n ? (int)elem[jv[c]] : 0;
+      // the counts one element per lane, from three ballots of the entries' element bits
+      int cnt = 0;
 #pragma unroll
       for (int c = 0; c < NCH; c++) {
         if (32 * c >= n) break;   // uniform over the warp
-#pragma unroll
-        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, ev[c] == q));
+        const unsigned vm = __ballot_sync(FULL, 32 * c + lane < n);
+        cnt += __popc(elem_lanes(lane, __ballot_sync(FULL, ev[c] & 1), __ballot_sync(FULL, ev[c] & 2),
+                                 __ballot_sync(FULL, ev[c] & 4)) & vm);
       }
-      int run = 0;   // counts -> starts
+      if (lane >= NE) cnt = 0;
+      int run = cnt;   // exclusive scan over lanes 0 .. NE - 1: lane q's next place for element q
 #pragma unroll
-      for (int q = 0; q < NE; q++) {
-        const int c = off[q];
-        off[q] = run;
-        run += c;
+      for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, run, o);
+        if (lane >= o) run += v;
       }
+      run -= cnt;
 #pragma unroll
       for (int c = 0; c < NCH; c++) {
         if (32 * c >= n) break;
-        int at = 0;
-#pragma unroll
-        for (int q = 0; q < NE; q++) {
-          const unsigned mq = __ballot_sync(FULL, ev[c] == q);
-          if (ev[c] == q) at = off[q] + __popc(mq & lt);
-          off[q] += __popc(mq);
-        }
+        const unsigned vm = __ballot_sync(FULL, 32 * c + lane < n);
+        const unsigned b0 = __ballot_sync(FULL, ev[c] & 1), b1 = __ballot_sync(FULL, ev[c] & 2),
+                       b2 = __ballot_sync(FULL, ev[c] & 4);
+        const int at = __shfl_sync(FULL, run, ev[c]) + __popc(elem_lanes(ev[c], b0, b1, b2) & vm & lt);
+        run += __popc(elem_lanes(lane, b0, b1, b2) & vm);
         if (32 * c + lane < n && dst + at < cap) {
           nbr[dst + at] = jv[c];
           shift[dst + at] = sv[c];
@@ -1170,40 +1174,40 @@ __global__ void __launch_bounds__(SMALL_NT, 1)
     }
     __syncwarp();
     if (sortable) {   // stable counting sort of the staged row by neighbour element
+      // (the counts one element per lane, from three ballots of the entries' element bits)
       constexpr int NCH = PAIR_STRIDE / 32;
       int jv[NCH], ev[NCH];
       char4 sv[NCH];
+      int cnt = 0;   // lane q < NE: entries of element q
 #pragma unroll
       for (int c = 0; c < NCH; c++) {
+        if (32 * c >= n) break;   // uniform over the warp
         const int k = 32 * c + lane;
         jv[c] = k < n ? S.stage_j[warp][k] : 0;
         sv[c] = k < n ? S.stage_s[warp][k] : make_char4(0, 0, 0, 0);
-        ev[c] = k < n ? (int)S.el[jv[c]] : -1;
+        ev[c] = k < n ? (int)S.el[jv[c]] : 0;
+        const unsigned vm = __ballot_sync(FULL, k < n);
+        cnt += __popc(elem_lanes(lane, __ballot_sync(FULL, ev[c] & 1), __ballot_sync(FULL, ev[c] & 2),
+                                 __ballot_sync(FULL, ev[c] & 4)) & vm);
       }
-      int off[NE];
+      if (lane >= NE) cnt = 0;
+      int run = cnt;   // exclusive scan over lanes 0 .. NE - 1: lane q's next place for element q
 #pragma unroll
-      for (int q = 0; q < NE; q++) off[q] = 0;
-#pragma unroll
-      for (int c = 0; c < NCH; c++)
-#pragma unroll
-        for (int q = 0; q < NE; q++) off[q] += __popc(__ballot_sync(FULL, ev[c] == q));
-      int run = 0;
-#pragma unroll
-      for (int q = 0; q < NE; q++) {
-        const int c = off[q];
-        off[q] = run;
-        run += c;
+      for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, run, o);
+        if (lane >= o) run += v;
       }
+      run -= cnt;
 #pragma unroll
       for (int c = 0; c < NCH; c++) {
-        int w = 0;
-#pragma unroll
-        for (int q = 0; q < NE; q++) {
-          const unsigned mq = __ballot_sync(FULL, ev[c] == q);
-          if (ev[c] == q) w = off[q] + __popc(mq & lt);
-          off[q] += __popc(mq);
-        }
-        if (ev[c] >= 0) {
+        if (32 * c >= n) break;
+        const int k = 32 * c + lane;
+        const unsigned vm = __ballot_sync(FULL, k < n);
+        const unsigned b0 = __ballot_sync(FULL, ev[c] & 1), b1 = __ballot_sync(FULL, ev[c] & 2),
+                       b2 = __ballot_sync(FULL, ev[c] & 4);
+        const int w = __shfl_sync(FULL, run, ev[c]) + __popc(elem_lanes(ev[c], b0, b1, b2) & vm & lt);
+        run += __popc(elem_lanes(lane, b0, b1, b2) & vm);
+        if (k < n) {
           nbr[dst + w] = jv[c];
           shift[dst + w] = sv[c];
         }
