@@ -1234,14 +1234,15 @@ __device__ bool small_task(const SmallEvalArgs &A, const int *ecount, const int 
 // copies of one K chunk [kc0, kc0 + kn) into buffer b: the rows' A values and the 32 columns of B (zeros past
 // ncol; every offset is a multiple of four floats, so each copy is 16 aligned bytes)
 __device__ __forceinline__ void small_stage(SmallDense &D, const float *A, int lda, int a_off, int R,
-                                            const float *B, int ldb, int c0, int ncol, int kc0, int kn) {
+                                            const float *B, int ldb, int c0, int ncol, int kc0, int kn, int cw) {
   const int kq = kn / 4;
   for (int q = threadIdx.x; q < R * kq; q += blockDim.x) {
     const int r = q / kq, k4 = (q - r * kq) * 4;
     cp16(&D.As[r][k4], A + (size_t)D.rows[r] * lda + a_off + kc0 + k4);
   }
-  for (int q = threadIdx.x; q < kn * 8; q += blockDim.x) {
-    const int k = q >> 3, c4 = (q & 7) * 4;
+  const int per = cw / 4;   // 16-byte copies per k row
+  for (int q = threadIdx.x; q < kn * per; q += blockDim.x) {
+    const int k = q / per, c4 = (q - k * per) * 4;
     if (c0 + c4 < ncol) cp16(&D.Bs[k][c4], B + (size_t)(kc0 + k) * ldb + c0 + c4);
     else *reinterpret_cast<float4 *>(&D.Bs[k][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -1252,8 +1253,11 @@ __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALP
 // CELU' from the activation h = CELU(z): 1 for z > 0, exp(z / alpha) = 1 + h / alpha otherwise
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : fmaf(h, CELU_INV_ALPHA, 1.f); }
 
-// One dense layer over every (member, element row group, 32-column chunk) task of the grid; K in staged
-// chunks, each warp a slice of every chunk, the warps' partial sums added in a fixed order.
+// One dense layer over every (member, element row group, column chunk) task of the grid; K in staged
+// chunks, each warp a slice of every chunk, the warps' partial sums added in a fixed order.  Chunks are 32
+// columns (a lane per column), or 16 when that leaves at least half of the blocks without a task (a lane
+// per column and half of the warp's K slice, the halves added by one shuffle); the third layer keeps 32
+// (its output-layer partial sums have a slot per 32 columns).
 // kind 0: out = CELU(A B + bias); 1: out = (A B) * CELU'(aux); 2: out = A B;
 // 3 (third layer): h = CELU(A B + bias), out = w4 CELU'(h) / M, and the output layer's sum of w4 h over the
 // chunk's columns into ysl[(row M + m) SE_YCH + chunk]
@@ -1263,15 +1267,20 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ec
                             int ncol, const float *bias, long long bias_me_stride, const float *aux, int ldaux,
                             int aux_member_off, float *out, int ldo, int o_member_off, int members, float *ysl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n_chunks = (ncol + 31) / 32;
+  int tasks32 = 0;
+  for (int e = 0; e < NE; e++) tasks32 += (ecount[e] + SE_RG - 1) / SE_RG;
+  tasks32 *= members * ((ncol + 31) / 32);
+  const int cw = (kind != 3 && 2 * tasks32 <= (int)gridDim.x) ? 16 : 32;
+  const int n_chunks = (ncol + cw - 1) / cw;
   const int nkc = (K + SE_KC - 1) / SE_KC;
+  const int col_l = cw == 32 ? lane : (lane & 15), kh = cw == 32 ? 0 : lane >> 4;   // column and K half of the lane
   for (int t = blockIdx.x;; t += gridDim.x) {
     SmallTask k;
     __syncthreads();
     const bool ok = small_task(A, ecount, estart, srow, t, n_chunks, members, k, D.rows);
     __syncthreads();
     if (!ok) break;
-    const int c0 = k.chunk * 32;
+    const int c0 = k.chunk * cw;
     const long long me = (long long)(k.m * NE + k.e);
     const float *B = Bb + me * b_me_stride;
     const int a_off = k.m * a_member_off;
@@ -1279,7 +1288,7 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ec
 #pragma unroll
     for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
     // the epilogue's operands travel with the first operand copies
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < cw / 4) {
       const int c4 = threadIdx.x * 4;
       if (c0 + c4 < ncol) {
         if (kind == 0 || kind == 3) cp16(&D.ep_bias[c4], bias + me * bias_me_stride + c0 + c4);
@@ -1287,18 +1296,20 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ec
       }
     }
     if (kind == 1)
-      for (int q = threadIdx.x; q < k.R * 8; q += blockDim.x) {
-        const int r = q >> 3, c4 = (q & 7) * 4;
+      for (int q = threadIdx.x; q < k.R * (cw / 4); q += blockDim.x) {
+        const int r = q / (cw / 4), c4 = (q - r * (cw / 4)) * 4;
         if (c0 + c4 < ncol) cp16(&D.ep_aux[r][c4], aux + (size_t)D.rows[r] * ldaux + k.m * aux_member_off + c0 + c4);
       }
     for (int c = 0; c < nkc; c++) {
       const int kc0 = c * SE_KC, kn = min(SE_KC, K - kc0);
-      small_stage(D, Ab, lda, a_off, k.R, B, ldb, c0, ncol, kc0, kn);
+      small_stage(D, Ab, lda, a_off, k.R, B, ldb, c0, ncol, kc0, kn, cw);
       cp_wait0();
       __syncthreads();
-      // warp w takes every SE_WARPS-th group of four k (interleaved: every warp busy for any kn)
-      for (int kk = 4 * warp; kk < kn; kk += 4 * SE_WARPS) {
-        const float b0 = D.Bs[kk][lane], b1 = D.Bs[kk + 1][lane], b2 = D.Bs[kk + 2][lane], b3 = D.Bs[kk + 3][lane];
+      // warp w (and K half kh) takes every SE_WARPS-th (2 SE_WARPS-th) group of four k (interleaved: every
+      // warp busy for any kn)
+      const int kst = cw == 32 ? 4 * SE_WARPS : 8 * SE_WARPS;
+      for (int kk = cw == 32 ? 4 * warp : 4 * (2 * warp + kh); kk < kn; kk += kst) {
+        const float b0 = D.Bs[kk][col_l], b1 = D.Bs[kk + 1][col_l], b2 = D.Bs[kk + 2][col_l], b3 = D.Bs[kk + 3][col_l];
 #pragma unroll
         for (int r = 0; r < SE_RG; r++) {
           if (r < k.R) {
@@ -1309,11 +1320,14 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ec
       }
       __syncthreads();   // before the buffers are staged again
     }
+    if (cw == 16)
+#pragma unroll
+      for (int r = 0; r < SE_RG; r++) acc[r] += __shfl_xor_sync(FULL, acc[r], 16);
 #pragma unroll
     for (int r = 0; r < SE_RG; r++) D.red[warp][r][lane] = acc[r];
     __syncthreads();
     for (int q = threadIdx.x; q < k.R * 32; q += blockDim.x) {
-      const int r = q >> 5, l = q & 31, col = c0 + l;
+      const int r = q >> 5, l = q & 31, col = l < cw ? c0 + l : ncol;
       float z = 0.f;
 #pragma unroll
       for (int w = 0; w < SE_WARPS; w++) z += D.red[w][r][l];   // fixed order
