@@ -1134,37 +1134,46 @@ constexpr int SE_WARPS = 8, SE_RG = 16;
 constexpr long long SE_BARRIER_LIMIT = 2000000000LL;   // clock64 cycles (about a second) per barrier wait
 
 struct GridBar {
-  unsigned count, gen, abort, pad;
+  unsigned count, gen, pad0, pad1;   // arrivals so far; barriers completed (bit 31: aborted)
 };
 
-// Every block arrives; the last one releases the others by advancing the generation.  A wait that runs out
-// posts FNN_E_TIMEOUT and raises abort.  Returns false once aborted (every block then leaves).
-__device__ bool grid_barrier(GridBar *b, DevStatus *st) {
+// Every block arrives (the count is cumulative over the launch, zeroed before it); the last arrival of
+// barrier k (phase, counted by the block) releases the others by advancing the generation to k + 1.  A wait
+// that runs out posts FNN_E_TIMEOUT and sets bit 31 of the generation, which every later wait sees.
+// Returns false once aborted (every block then leaves).
+__device__ bool grid_barrier(GridBar *b, DevStatus *st, unsigned &phase) {
+  __shared__ int ok_s;
+  const unsigned target = ++phase;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = *(volatile unsigned *)&b->gen;
+    bool ok = true;
     __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-      atomicExch(&b->count, 0u);
+    if (atomicAdd(&b->count, 1u) == gridDim.x * target - 1) {
       __threadfence();
-      atomicAdd(&b->gen, 1u);
+      ok = (atomicAdd(&b->gen, 1u) >> 31) == 0u;
     } else {
       const long long t0 = clock64();
-      unsigned cur;
       for (;;) {
+        unsigned cur;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&b->gen) : "memory");
-        if (cur != g) break;
+        if (cur >> 31) {
+          ok = false;
+          break;
+        }
+        if (cur >= target) break;
         if (clock64() - t0 > SE_BARRIER_LIMIT) {
           post_status(st, FNN_E_TIMEOUT, -2);
-          atomicExch(&b->abort, 1u);
+          atomicOr(&b->gen, 0x80000000u);
+          ok = false;
           break;
         }
       }
     }
     __threadfence();
+    ok_s = ok;
   }
   __syncthreads();
-  return *(volatile unsigned *)&b->abort == 0u;
+  return ok_s != 0;
 }
 
 struct SmallEvalArgs {
@@ -1368,6 +1377,7 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wg = blockIdx.x * SE_WARPS + warp, nw = gridDim.x * SE_WARPS;
   const int M = A.M, N = A.N;
+  unsigned phase = 0;   // grid barriers passed
   // element counts and the atoms in element order (every block; from the species order of the list)
   __shared__ int estart[NE + 1];
   __shared__ int srow[SMALL_BUILD_ATOMS];
@@ -1393,34 +1403,34 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   const int Kw = min(8, max(1, nw / max(N, 1)));
   if (Kw > 1) aev_forward_parts<float>(A.fa, S.fwd[warp], wg, nw, Kw);
   else aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   SmallDense &D = S.d;
   const int MH1 = M * H1;
   // first layer, all members fused: h1 = CELU(aev W1^T + b1), [N][M 256]
   small_layer(A, D, ecount, estart, srow, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0,
               0, A.h1, MH1, 0, 1, nullptr);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // second layer per member: h2 = CELU(h1_m W2^T + b2), [N][M 192]
   small_layer(A, D, ecount, estart, srow, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2,
               M * H2, H2, M, nullptr);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // third layer per member: h3 = CELU(h2_m W3^T + b3) -> g3 = (1/M) w4 CELU'(z3) and the output layer's
   // partial sums per column chunk (fixed slots, added in a fixed order with the energies)
   small_layer(A, D, ecount, estart, srow, 3, A.h2, M * H2, H2, H2, A.W3T, (long long)H2 * H3, H3, H3, A.b3, H3, nullptr, 0, 0, A.g3,
               M * H3, H3, M, A.ysl);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // third layer's input gradient: g2 = (g3 W3) * CELU'(h2)
   small_layer(A, D, ecount, estart, srow, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2,
               A.g2, M * H2, H2, M, nullptr);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // second layer's: g1 = (g2 W2) * CELU'(h1)
   small_layer(A, D, ecount, estart, srow, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1,
               A.g1, MH1, H1, M, nullptr);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // first layer's, summed over the members: dE/dAEV = g1 W1 (K = M 256 through the member-concatenated W1)
   small_layer(A, D, ecount, estart, srow, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
               A.gaev, NAEV, 0, 1, nullptr);
-  if (!grid_barrier(A.bar, A.st)) return;
+  if (!grid_barrier(A.bar, A.st, phase)) return;
   // forces and virials (a warp per atom, the first warps); the energies meanwhile on the last warps, a warp
   // per structure: lanes over its atoms, then a shuffle tree (a fixed order)
   __syncthreads();
