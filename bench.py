@@ -35,6 +35,8 @@ PRECISION_NOTE = {
               "accumulated in FP32; AEV, reductions and adjoint in FP32/FP64",
     "fp32": "networks on SIMT FP32 FFMA",
     "bf16": "networks in BF16 on tcgen05 with FP32 accumulation",
+    "bf16_fused": "the BF16 form with the AEV and the first layer in one kernel (64-row AEV tiles built in shared "
+                  "memory as the tcgen05 A operand)",
     "fp8": "networks in FP8 e4m3 on tcgen05 (kind::f8f6f4) with FP32 accumulation; per-layer scales "
            "(weights amax/448 per block, activations 2 amax/448 from an FP32 calibration evaluation)",
 }
@@ -64,6 +66,8 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
         return "hbm", n_atoms * (16 + (4032 if name.endswith("x3") else 2016)) + nnz * 8, "B", None
     if name == "aev_forward_fp8":   # e4m3 AEV row
         return "hbm", n_atoms * (16 + 1008) + nnz * 8, "B", None
+    if name == "aev_l1_bf16":       # fused AEV + first layer: the first layer's product (bf16 operands)
+        return "tensor", 2.0 * 1008 * 256 * M * n_atoms, "FLOP", None
     if name == "aev_adjoint":       # positions, list, dE/dAEV row read, forces written
         return "hbm", n_atoms * (16 + 4032 + 12) + nnz * 8, "B", None
     gemm = {"l1": 1008 * 256, "l2": 256 * 192, "l3": 192 * 160}
@@ -83,6 +87,7 @@ KERNEL_SOURCES = [  # kernel-name prefix -> the files that define it (with the s
     (("x3_l3_pair", "bf16_l3_pair"), ("tc_gemm.cuh", "tc_fused.cuh", "mlp_tc.cu")),
     (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "mlp_tc.cu")),
     (("f32_", "energy_reduce"), ("mlp_simt.cu",)),
+    (("aev_l1",), ("aev.cu", "tc_gemm.cuh")),
     (("aev_",), ("aev.cu",)),
     (("pairs_", "scan", "mol_setup", "atom_setup", "mol_grid", "check_", "bin", "scatter", "sort_cells", "elem_"),
      ("nlist.cu",)),
@@ -965,9 +970,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fnn", choices=["fnn", "reference"])
-    ap.add_argument("--precision", default="fp32x3", choices=["fp32", "fp32x3", "bf16", "fp8"],
+    ap.add_argument("--precision", default="fp32x3", choices=["fp32", "fp32x3", "bf16", "bf16_fused", "fp8"],
                     help="form whose throughput is the headline value")
-    ap.add_argument("--forms", default="fp32x3,fp32,bf16,fp8", help="forms timed and reported (comma separated)")
+    ap.add_argument("--forms", default="fp32x3,fp32,bf16,bf16_fused,fp8", help="forms timed and reported (comma separated)")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-md", action="store_true", help="skip the water-box MD measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1089,7 +1094,7 @@ def main():
     line = {"metric": METRIC, "value": world * s.n_atoms / (head["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp32x3": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp32x3": "f32", "bf16": "bf16", "bf16_fused": "bf16", "fp8": "e4m3"}[args.precision], "data": "synthetic",
             "config": arm_config(args.precision, nnz, world),
             "roofline": roof, "gpu_launches": int(head["launches"]),
             "e2e": {"value": world * s.n_atoms / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -66,9 +66,13 @@ typedef enum {
   FNN_FP32 = 0, /* network GEMMs in FP32 (SIMT FFMA), FP32 accumulation */
   FNN_BF16 = 1, /* network GEMMs in BF16 on tcgen05 tensor cores, FP32 accumulation */
   FNN_FP8 = 2,  /* network GEMMs in FP8 e4m3 with per-layer scales, FP32 accumulation */
-  FNN_FP32X3 = 3 /* FP32-accurate network GEMMs on tcgen05 tensor cores: every operand split into
+  FNN_FP32X3 = 3, /* FP32-accurate network GEMMs on tcgen05 tensor cores: every operand split into
                     bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated in FP32 (relative error
                     of a product about 2^-16, within the FP32 tolerances of the energies and forces) */
+  FNN_BF16_FUSED = 4 /* the FNN_BF16 arithmetic with the AEV and the first layer in one kernel (section
+                    II.E): each 64-row tile of species-sorted AEV rows is built in shared memory as bf16 and
+                    is the A operand of the first layer's tcgen05 products; the AEV never reaches global
+                    memory.  Energies and forces equal FNN_BF16's up to the order of FP32 sums. */
 } fnn_precision;
 
 /* Symmetry-function constants and ensemble size.  fnn_config_default() fills

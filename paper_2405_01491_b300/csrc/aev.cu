@@ -18,6 +18,7 @@
 #include <cuda_fp8.h>
 
 #include "fnn_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace fnn {
 
@@ -478,13 +479,28 @@ __device__ __forceinline__ void produce_triplet(FwdStage &W, const AevParams &P,
   }
 }
 
+// Where a row of the forward goes: a row of the AEV array in global memory (and of its low half when the
+// output is split into bf16 hi + lo)
+template <typename OutT>
+struct GlobalRow {
+  OutT *out;
+  __nv_bfloat16 *lo;
+  float inv;
+  __device__ __forceinline__ void zero() const {
+    zero_span(out, NAEV);
+    if (lo) zero_span(lo, NAEV);
+  }
+  __device__ __forceinline__ void put(int c, float v) const {
+    store_out<OutT>(out + c, v, inv);
+    store_lo(lo, c, v);
+  }
+};
+
 // Radial slots of a staged row: lane (h, k) sums shift k over every other neighbour of each element
 // segment; elements without neighbours are skipped (their slots hold zeros already) unless zeros is set
-template <typename OutT>
-__device__ __forceinline__ void radial_row(const AevFwdArgs &A, const FwdStage &W, OutT *out, __nv_bfloat16 *lo,
-                                           int orr, bool zeros) {
+template <typename Sink>
+__device__ __forceinline__ void radial_row(const AevParams &P, const FwdStage &W, const Sink &o, int orr, bool zeros) {
   const int lane = threadIdx.x & 31;
-  const AevParams &P = A.P;
   const int h = lane >> 4, k = lane & 15;
   const float Rk = P.shf_r[k], ce = P.eta_r_l2;
 #pragma unroll 1
@@ -508,10 +524,63 @@ __device__ __forceinline__ void radial_row(const AevFwdArgs &A, const FwdStage &
     }
     float acc = a0 + a1;
     acc += __shfl_xor_sync(FULL, acc, 16);
-    if (lane < 16) {
-      store_out<OutT>(out + q * NSR + k, acc, A.out_inv);
-      store_lo(lo, q * NSR + k, acc);
+    if (lane < 16) o.put(q * NSR + k, acc);
+  }
+}
+
+// The AEV row of atom i (i < 0: a padding row of zeros) into o, by one warp staged in W
+template <typename Sink>
+__device__ __forceinline__ void aev_row(const AevFwdArgs &A, FwdStage &W, int i, const Sink &o) {
+  const int lane = threadIdx.x & 31;
+  const AevParams &P = A.P;
+  int orr, oa, ca;
+  const bool ok = i >= 0 && stage_fwd(A.sa, P, i, W.nb, orr, oa, ca, A.st);
+  // every slot of an element (pair) without neighbours stays zero
+  o.zero();
+  __syncwarp();   // orders the zeros before the lanes' own stores below
+  if (!ok) return;
+  radial_row(P, W, o, orr, false);
+  // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch,
+  // enumerated block by block in slot order (element pair (a, b), a <= b), so a pair's 32 slots are
+  // complete when its block ends.  The producer lane evaluates one triplet; lane (m, s) then sums
+  // pow_s * gauss_m over the batch in four chains, which go to the output row when the block ends.
+  {
+    int nblk;
+    const int T = build_blocks(W.tb, ca, oa, nblk);
+    const int s_my = lane & 3, m_my = lane >> 2;
+    const float *fr = W.sf[s_my], *gr = W.sg[m_my];
+    int run_p = -1;          // slot block being summed (warp-uniform)
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+    auto put = [&](int pp, float v) { o.put(NRAD + pp * 32 + lane, v); };
+    auto open = [&](int pn) {
+      if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
+      r0 = r1 = r2 = r3 = 0.f;
+      run_p = pn;
+    };
+    int cur = 0;
+    for (int base = 0; base < T; base += 32) {
+      // every lane evaluates a triplet; a padding slot's Gaussians are zero (its switch product -inf)
+      int idx, ja, ka;
+      bool opens;
+      const bool real = batch_triplet(W.tb, base, nblk, cur, idx, ja, ka, opens);
+      produce_triplet(W, P, real, ja, ka);
+      if (opens) W.sp[lane] = W.tb.bq[idx] & 0xff;
+      // blocks open only at slots that are multiples of four
+      const unsigned starts = __ballot_sync(FULL, opens);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
+        const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
+        if ((starts >> q) & 1u) open(W.sp[q]);
+        r0 = fmaf(fv.x, gv.x, r0);
+        r1 = fmaf(fv.y, gv.y, r1);
+        r2 = fmaf(fv.z, gv.z, r2);
+        r3 = fmaf(fv.w, gv.w, r3);
+      }
+      __syncwarp();
     }
+    if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
   }
 }
 
@@ -519,71 +588,11 @@ __device__ __forceinline__ void radial_row(const AevFwdArgs &A, const FwdStage &
 // small-system kernel, call it)
 template <typename OutT>
 __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw) {
-  const int lane = threadIdx.x & 31;
-  const AevParams &P = A.P;
   const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
   for (int row = wg; row < nrows; row += nw) {
-    OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
-    __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
-    const int i = A.inv ? A.inv[row] : row;
-    int orr, oa, ca;
-    const bool ok = i >= 0 && stage_fwd(A.sa, P, i, W.nb, orr, oa, ca, A.st);
-    if (!ok) {
-      zero_span(out, NAEV);
-      if (lo) zero_span(lo, NAEV);
-      __syncwarp();
-      continue;
-    }
-    // every slot of an element (pair) without neighbours stays zero
-    zero_span(out, NAEV);
-    if (lo) zero_span(lo, NAEV);
-    __syncwarp();   // orders the zeros before the lanes' own stores below
-    radial_row<OutT>(A, W, out, lo, orr, false);
-    // ---- angular: every unordered pair j < k of the element-sorted angular list, 32 per batch,
-    // enumerated block by block in slot order (element pair (a, b), a <= b), so a pair's 32 slots are
-    // complete when its block ends.  The producer lane evaluates one triplet; lane (m, s) then sums
-    // pow_s * gauss_m over the batch in four chains, which go to the output row when the block ends.
-    {
-      int nblk;
-      const int T = build_blocks(W.tb, ca, oa, nblk);
-      const int s_my = lane & 3, m_my = lane >> 2;
-      const float *fr = W.sf[s_my], *gr = W.sg[m_my];
-      int run_p = -1;          // slot block being summed (warp-uniform)
-      float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
-      auto put = [&](int pp, float v) {
-        store_out<OutT>(out + NRAD + pp * 32 + lane, v, A.out_inv);
-        store_lo(lo, NRAD + pp * 32 + lane, v);
-      };
-      auto open = [&](int pn) {
-        if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
-        r0 = r1 = r2 = r3 = 0.f;
-        run_p = pn;
-      };
-      int cur = 0;
-      for (int base = 0; base < T; base += 32) {
-        // every lane evaluates a triplet; a padding slot's Gaussians are zero (its switch product -inf)
-        int idx, ja, ka;
-        bool opens;
-        const bool real = batch_triplet(W.tb, base, nblk, cur, idx, ja, ka, opens);
-        produce_triplet(W, P, real, ja, ka);
-        if (opens) W.sp[lane] = W.tb.bq[idx] & 0xff;
-        // blocks open only at slots that are multiples of four
-        const unsigned starts = __ballot_sync(FULL, opens);
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 32; q += 4) {
-          const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
-          const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
-          if ((starts >> q) & 1u) open(W.sp[q]);
-          r0 = fmaf(fv.x, gv.x, r0);
-          r1 = fmaf(fv.y, gv.y, r1);
-          r2 = fmaf(fv.z, gv.z, r2);
-          r3 = fmaf(fv.w, gv.w, r3);
-        }
-        __syncwarp();
-      }
-      if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
-    }
+    const GlobalRow<OutT> o{reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV,
+                            A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr, A.out_inv};
+    aev_row(A, W, A.inv ? A.inv[row] : row, o);
     __syncwarp();
   }
 }
@@ -619,7 +628,7 @@ __device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int 
     int nblk;
     build_blocks(W.tb, ca, oa, nblk);
     if (part == 0) {
-      radial_row<OutT>(A, W, out, lo, orr, true);
+      radial_row(P, W, GlobalRow<OutT>{out, lo, A.out_inv}, orr, true);
       const unsigned present = __reduce_or_sync(FULL, lane < nblk ? 1u << (W.tb.bq[lane] & 0xff) : 0u);
       for (int pp = 0; pp < NPAIR; pp++)
         if (!((present >> pp) & 1u)) {
@@ -659,6 +668,224 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
   __shared__ FwdStage smem[AEV_WARPS];
   const int wl = threadIdx.x >> 5;
   aev_forward_rows<OutT>(A, smem[wl], blockIdx.x * AEV_WARPS + wl, gridDim.x * AEV_WARPS);
+}
+
+// ------------------------------------------------------------------- fused AEV -> first layer (BF16)
+// The BF16 form's AEV and first layer in one kernel (section II.E: the networks read the AEV of each
+// atomic centre): a persistent CTA per SM takes 64-row tiles of the species-sorted rows.  Its worker warps
+// build the tile's AEV rows (the forward above, row by row) as bf16 straight into shared memory, in the
+// tensor core's K-major 128-byte-swizzled layout; one thread then issues the tile's products with every
+// member's first-layer weights (tcgen05.mma, M = 64, N = 256, weights streamed by TMA through a two-stage
+// ring), and the workers apply bias + CELU to each member's accumulator as it completes and store h1.  The
+// AEV never reaches global memory.  A 128-row tile would take 256 KB of shared memory as bf16, more than a
+// CTA has, so the tiles are 64 rows: an M = 64 accumulator holds row r in TMEM lane 32 (r / 16) + r % 16.
+// The AEV staging of the workers shares its space with the weight ring (the two phases of a tile do not
+// overlap: a tile's AEV must be complete before its first product).
+constexpr int FUSE_ROWS = 64;                 // rows of a tile (UMMA M)
+constexpr int FUSE_WORKERS = 16;              // AEV warps, then epilogue warps (four per TMEM lane quarter)
+constexpr int FUSE_THREADS = 32 * FUSE_WORKERS + 64;   // + the TMA warp and the MMA warp
+constexpr int FUSE_KCH = 16;                  // 64-element K chunks of a row: 1008 columns padded to 1024
+constexpr int FUSE_CHUNK = FUSE_ROWS * 128;   // bytes of one K chunk of the tile (8-row groups 1024 B apart)
+constexpr int FUSE_BST = H1 * 128;            // one weight stage: 256 rows x 64 K elements
+constexpr int FUSE_STAGES = 2;
+
+struct FuseSmem {
+  uint8_t A[FUSE_KCH * FUSE_CHUNK];           // the AEV tile, K chunk by K chunk (1024-byte aligned)
+  union {
+    uint8_t B[FUSE_STAGES][FUSE_BST];         // weight ring (products)
+    FwdStage W[FUSE_WORKERS];                 // AEV staging (rows)
+  } u;
+  uint64_t full[FUSE_STAGES], empty[FUSE_STAGES], acc_full[2], acc_empty[2], fin;
+  uint32_t tmem_base;
+  int abort_flag;
+  int next_row;                               // rows of the tile claimed by the workers
+};
+constexpr size_t fuse_smem_bytes() { return sizeof(FuseSmem) + 1024; }
+static_assert(sizeof(FuseSmem) + 1024 <= (size_t)tc::SMEM_LIMIT, "fused kernel shared memory");
+
+// Row r of the tile: column c at K chunk c / 64, byte 2 (c % 64) of the row's 128 bytes, 16-byte units
+// XOR-swizzled by r % 8 (the pattern TMA's 128-byte swizzle writes and the descriptor reads)
+struct TileRow {
+  uint8_t *tile;
+  int r;
+  __device__ __forceinline__ void zero() const {
+    const int lane = threadIdx.x & 31;
+    for (int u = lane; u < FUSE_KCH * 8; u += 32)
+      *reinterpret_cast<uint4 *>(tile + (u >> 3) * FUSE_CHUNK + r * 128 + (u & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __device__ __forceinline__ void put(int c, float v) const {
+    const int off = (c >> 6) * FUSE_CHUNK + r * 128 + ((((c >> 3) & 7) ^ (r & 7)) << 4) + ((c & 7) << 1);
+    *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16(v);
+  }
+};
+
+struct FuseArgs {
+  AevFwdArgs aev;            // inv and meta give the padded species-sorted rows
+  const int32_t *tile_elem;  // element of each 128-row tile (-1: none)
+  long long rows_cap;        // rows of h1 (a multiple of 128)
+  const float *bias;         // b1 [7][M * 256]
+  __nv_bfloat16 *h1;         // [rows][M][256]
+  int M;
+};
+
+__global__ void __launch_bounds__(FUSE_THREADS, 1) k_aev_l1(const __grid_constant__ CUtensorMap tmW1, FuseArgs p) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  FuseSmem &S = *reinterpret_cast<FuseSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int WT = FUSE_WORKERS, WM = FUSE_WORKERS + 1;   // TMA warp, MMA warp
+  volatile int *abort_flag = &S.abort_flag;
+  const int M = p.M;
+  const long long npad = min((long long)p.aev.meta[META_NPAD], p.rows_cap);
+  const int ntile = (int)(npad / FUSE_ROWS);
+  if (warp == WT && lane == 0) {
+    for (int s = 0; s < FUSE_STAGES; s++) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&S.acc_full[a], 1);
+      mbar_init(&S.acc_empty[a], WT);   // one arrival per worker warp
+    }
+    mbar_init(&S.fin, 1);
+    S.abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == WM) {
+    tmem_alloc(&S.tmem_base, 2 * H1);
+    tmem_relinquish();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = S.tmem_base;
+  long long g = 0;   // weight stages issued (TMA lane) / consumed (MMA lane)
+  int cnt = 0;       // accumulators issued (MMA lane) / drained (workers)
+  for (int t = (int)blockIdx.x; t < ntile; t += (int)gridDim.x) {
+    const int e = p.tile_elem[t >> 1];
+    if (e < 0) continue;   // the whole CTA skips
+    // ---- the tile's AEV rows, claimed one at a time by the workers
+    if (threadIdx.x == 0) S.next_row = 0;
+    __syncthreads();
+    if (warp < WT) {
+      for (;;) {
+        int rr = 0;
+        if (lane == 0) rr = atomicAdd(&S.next_row, 1);
+        rr = __shfl_sync(FULL, rr, 0);
+        if (rr >= FUSE_ROWS) break;
+        const long long row = (long long)t * FUSE_ROWS + rr;
+        aev_row(p.aev, S.u.W[warp], p.aev.inv[row], TileRow{S.A, rr});
+        __syncwarp();
+      }
+      fence_proxy_async();   // the tile and the staging, written by threads, next read or overwritten by the async proxy
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    // ---- the products: one accumulator per member
+    if (warp == WT) {
+      if (lane == 0) {
+        const long long g0 = g;
+        for (int m = 0; m < M && !*abort_flag; m++)
+          for (int kb = 0; kb < FUSE_KCH; kb++, g++) {
+            const int s = (int)(g % FUSE_STAGES);
+            if (g >= FUSE_STAGES && !mbar_wait(&S.empty[s], (uint32_t)(((g / FUSE_STAGES) - 1) & 1))) {
+              *abort_flag = 1;
+              break;
+            }
+            mbar_expect_tx(&S.full[s], (uint32_t)FUSE_BST);
+            tma_load_3d(S.u.B[s], &tmW1, &S.full[s], kb * 64, m * H1, e);
+          }
+        // after an abort, every load issued must land before the ring is reused or the CTA exits
+        if (*abort_flag)
+          for (long long q = max(g0, g - FUSE_STAGES); q < g; q++)
+            mbar_wait(&S.full[q % FUSE_STAGES], (uint32_t)((q / FUSE_STAGES) & 1));
+      }
+    } else if (warp == WM) {
+      if (lane == 0) {
+        const uint32_t idesc = idesc_bf16(FUSE_ROWS, H1), a0 = smem_u32(S.A);
+        for (int m = 0; m < M && !*abort_flag; m++) {
+          const int a = cnt & 1;
+          if (cnt >= 2 && !mbar_wait(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          fence_after();
+          const uint32_t d = tmem + (uint32_t)(a * H1);
+          for (int kb = 0; kb < FUSE_KCH; kb++, g++) {
+            const int s = (int)(g % FUSE_STAGES);
+            if (!mbar_wait(&S.full[s], (uint32_t)((g / FUSE_STAGES) & 1))) {
+              *abort_flag = 1;
+              break;
+            }
+            fence_after();
+            const uint32_t b0 = smem_u32(S.u.B[s]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+              mma_bf16(d, sdesc_sw128(a0 + kb * FUSE_CHUNK + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
+                       (kb | k) != 0 ? 1u : 0u);
+            mma_commit(&S.empty[s]);
+          }
+          if (*abort_flag) break;
+          mma_commit(&S.acc_full[a]);
+          cnt++;
+        }
+      }
+    } else {   // workers: bias + CELU of each member's accumulator, rows of lane quarter q, 64 columns each
+      const int q = warp & 3, part = warp >> 2;
+      const long long row = (long long)t * FUSE_ROWS + q * 16 + (lane & 15);
+      for (int m = 0; m < M; m++) {
+        const int a = cnt & 1;
+        const bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
+        fence_after();
+        if (!__all_sync(FULL, ok)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t tb = tmem + (uint32_t)(a * H1) + ((uint32_t)(q * 32) << 16);
+        const float *bias = p.bias + (long long)e * M * H1 + m * H1;
+        __nv_bfloat16 *out = p.h1 + (row * M + m) * H1;
+#pragma unroll 1
+        for (int c = part * 64; c < part * 64 + 64; c += 16) {
+          float v[16];
+          tmem_ld16(tb + c, v);   // lanes 16..31 of the quarter hold no rows of an M = 64 accumulator
+          if (lane < 16) {
+            alignas(16) __nv_bfloat16 hb[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c + j));
+              hb[j] = __float2bfloat16(celu_f(v[j] + bb.x));
+              hb[j + 1] = __float2bfloat16(celu_f(v[j + 1] + bb.y));
+              hb[j + 2] = __float2bfloat16(celu_f(v[j + 2] + bb.z));
+              hb[j + 3] = __float2bfloat16(celu_f(v[j + 3] + bb.w));
+            }
+            reinterpret_cast<uint4 *>(out + c)[0] = reinterpret_cast<const uint4 *>(hb)[0];
+            reinterpret_cast<uint4 *>(out + c)[1] = reinterpret_cast<const uint4 *>(hb)[1];
+          }
+        }
+        // the accumulator may be overwritten once every worker has read it
+        fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.acc_empty[a])) : "memory");
+        cnt++;
+      }
+    }
+    // every product of the tile has completed (the workers drained the last accumulator) before its AEV
+    // tile and the ring are overwritten by the next tile's rows
+    __syncthreads();
+    if (*abort_flag) break;
+  }
+  // every issued product must be complete before the TMEM is released (after an abort, MMAs may remain)
+  if (warp == WM && lane == 0) {
+    mma_commit(&S.fin);
+    if (!mbar_wait(&S.fin, 0)) *abort_flag = 1;
+  }
+  fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) post_status(p.aev.st, FNN_E_TIMEOUT, blockIdx.x);
+  if (warp == WM) {
+    fence_after();
+    tmem_dealloc(tmem, 2 * H1);
+  }
 }
 
 // ------------------------------------------------------------------------------------- adjoint
@@ -1518,6 +1745,37 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
     k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_bf16");
+}
+
+fnn_status launch_aev_l1_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const CUtensorMap *mW1,
+                              const float *b1cat, __nv_bfloat16 *h1, int M, cudaStream_t s) {
+  FuseArgs a;
+  a.aev.sa = stage_args(sys, nl);
+  a.aev.P = ctx->aev;
+  a.aev.out = nullptr;
+  a.aev.out_lo = nullptr;
+  a.aev.out_inv = 1.f;
+  a.aev.inv = nl->inv;
+  a.aev.meta = nl->meta;
+  a.aev.n_atoms = sys->n_atoms;
+  a.aev.st = ctx->status;
+  a.tile_elem = nl->tile_elem;
+  a.rows_cap = nl->pad_cap;
+  a.bias = b1cat;
+  a.h1 = h1;
+  a.M = M;
+  const long long tiles = nl->pad_cap / FUSE_ROWS;
+  if (tiles == 0) return FNN_OK;
+  static bool attr_set = false;
+  if (!attr_set) {
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(k_aev_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fuse_smem_bytes()));
+    attr_set = true;
+  }
+  {
+    FNN_KERNEL(ctx, "aev_l1_bf16", s);
+    k_aev_l1<<<(unsigned)(tiles < ctx->num_sms ? tiles : ctx->num_sms), FUSE_THREADS, fuse_smem_bytes(), s>>>(*mW1, a);
+  }
+  return check_launch(ctx, "aev_l1_bf16");
 }
 
 fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, uint8_t *out,

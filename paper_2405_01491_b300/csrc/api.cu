@@ -344,7 +344,8 @@ extern "C" fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, con
     ctx->last_error = "neighbour list was not built for this system";
     return FNN_E_STATE;
   }
-  if (prec != FNN_FP32 && prec != FNN_BF16 && prec != FNN_FP8 && prec != FNN_FP32X3) return FNN_E_INVALID;
+  if (prec != FNN_FP32 && prec != FNN_BF16 && prec != FNN_FP8 && prec != FNN_FP32X3 && prec != FNN_BF16_FUSED)
+    return FNN_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   fnn_status st;
   if ((st = ensure_workspace(ctx, nl->pad_cap))) return st;

@@ -402,6 +402,8 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
                                    __nv_bfloat16 *out_lo, const int32_t *inv, cudaStream_t s);
 fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, uint8_t *out,
                                   float out_inv, const int32_t *inv, cudaStream_t s);
+fnn_status launch_aev_l1_bf16(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const CUtensorMap *mW1,
+                              const float *b1cat, __nv_bfloat16 *h1, int M, cudaStream_t s);
 
 static fnn_status f8_workspace(fnn_ctx *ctx, size_t rows) {
   TcState *t = state(ctx);
@@ -495,7 +497,7 @@ namespace {
 // stream as soon as the output layer is done, overlapping the backward products.
 template <bool SPLIT>
 fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn_nlist *nl, double *E,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool l1_done = false) {
   constexpr int MODE = SPLIT ? tc::MODE_SPLIT : tc::MODE_BF16;
   const DeviceWeights &w = ctx->w;
   const Half &H = t->h[0], &L = t->h[SPLIT ? 1 : 0];
@@ -515,7 +517,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
   a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  {
+  if (!l1_done) {   // (h1 is already there when the fused AEV kernel computed it)
     Maps m1{&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1};
     m1.Bs = &H.sW1; m1.Bs_lo = &L.sW1;
     if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true, ctx, nm[0], m1, nullptr, a, dim3(M, tiles, 1), s)))
@@ -665,7 +667,8 @@ fnn_status fp8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *n
   return f8_calibrate(ctx, sys, nl, s);
 }
 
-// AEV (bf16, or hi/lo pairs) -> six tcgen05 GEMMs -> member-averaged energies; dE/dAEV (fp32) in ws.gaev
+// AEV (bf16, or hi/lo pairs) -> six tcgen05 GEMMs -> member-averaged energies; dE/dAEV (fp32) in ws.gaev.
+// FNN_BF16_FUSED computes the AEV and the first product in one kernel (aev.cu, k_aev_l1).
 fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, fnn_precision prec, double *E,
                      cudaStream_t s) {
   const bool split = prec == FNN_FP32X3;
@@ -683,6 +686,10 @@ fnn_status tc_energy(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, f
     return energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, s);
   }
   if ((st = tc_workspace(ctx, nl->pad_cap, split ? 2 : 1))) return st;
+  if (prec == FNN_BF16_FUSED) {   // AEV and first layer in one kernel, then the other five products
+    if ((st = launch_aev_l1_bf16(ctx, sys, nl, &t->h[0].mW1, ctx->w.b1cat, t->h[0].h1, t->M, s))) return st;
+    return run_layers<false>(ctx, t, sys, nl, E, s, true);
+  }
   if ((st = launch_aev_forward_bf16(ctx, sys, nl, t->h[0].aev, split ? t->h[1].aev : nullptr, nl->inv, s))) return st;
   return split ? run_layers<true>(ctx, t, sys, nl, E, s) : run_layers<false>(ctx, t, sys, nl, E, s);
 }

@@ -635,7 +635,7 @@ static void worker_main(fnn_server *S) {
 extern "C" fnn_status fnn_serve_create(fnn_server **out, fnn_ctx *ctx, size_t hbm_budget_bytes, fnn_precision prec,
                                        int32_t rebuild_every) {
   if (!out || !ctx || hbm_budget_bytes == 0 || rebuild_every < 1 ||
-      (prec != FNN_FP32 && prec != FNN_BF16 && prec != FNN_FP32X3))
+      (prec != FNN_FP32 && prec != FNN_BF16 && prec != FNN_FP32X3 && prec != FNN_BF16_FUSED))
     return FNN_E_INVALID;
   if (!ctx->has_weights) return FNN_E_STATE;
   fnn_server *S = new fnn_server();

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(HERE, "libfnn.so")
 FNN_OK, FNN_PENDING = 0, 1
 STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "E_INVALID", -2: "E_SPECIES", -3: "E_CELL", -4: "E_CAPACITY",
                 -5: "E_OOM", -6: "E_TIMEOUT", -7: "E_NONFINITE", -8: "E_CUDA", -9: "E_STATE"}
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32x3": 3}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32x3": 3, "bf16_fused": 4}
 
 
 class FnnError(RuntimeError):
