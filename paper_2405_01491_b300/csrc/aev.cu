@@ -675,19 +675,20 @@ __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(
 // atomic centre): a persistent CTA per SM takes 64-row tiles of the species-sorted rows.  Its worker warps
 // build the tile's AEV rows (the forward above, row by row) as bf16 straight into shared memory, in the
 // tensor core's K-major 128-byte-swizzled layout; one thread then issues the tile's products with every
-// member's first-layer weights (tcgen05.mma, M = 64, N = 256, weights streamed by TMA through a two-stage
-// ring), and the workers apply bias + CELU to each member's accumulator as it completes and store h1.  The
+// member's first-layer weights (tcgen05.mma, M = 64, N = 256, weights streamed by TMA through a three-stage
+// ring), and 16 of the workers apply bias + CELU to each member's accumulator as it completes and store h1.  The
 // AEV never reaches global memory.  A 128-row tile would take 256 KB of shared memory as bf16, more than a
 // CTA has, so the tiles are 64 rows: an M = 64 accumulator holds row r in TMEM lane 32 (r / 16) + r % 16.
 // The AEV staging of the workers shares its space with the weight ring (the two phases of a tile do not
 // overlap: a tile's AEV must be complete before its first product).
 constexpr int FUSE_ROWS = 64;                 // rows of a tile (UMMA M)
-constexpr int FUSE_WORKERS = 16;              // AEV warps, then epilogue warps (four per TMEM lane quarter)
+constexpr int FUSE_WORKERS = 18;              // AEV warps; the first 16 are then the epilogue warps
+constexpr int FUSE_EPI = 16;                  // (four per TMEM lane quarter)
 constexpr int FUSE_THREADS = 32 * FUSE_WORKERS + 64;   // + the TMA warp and the MMA warp
 constexpr int FUSE_KCH = 16;                  // 64-element K chunks of a row: 1008 columns padded to 1024
 constexpr int FUSE_CHUNK = FUSE_ROWS * 128;   // bytes of one K chunk of the tile (8-row groups 1024 B apart)
 constexpr int FUSE_BST = H1 * 128;            // one weight stage: 256 rows x 64 K elements
-constexpr int FUSE_STAGES = 2;
+constexpr int FUSE_STAGES = 3;
 
 struct FuseSmem {
   uint8_t A[FUSE_KCH * FUSE_CHUNK];           // the AEV tile, K chunk by K chunk (1024-byte aligned)
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1) k_aev_l1(const __grid_constan
     }
     for (int a = 0; a < 2; a++) {
       mbar_init(&S.acc_full[a], 1);
-      mbar_init(&S.acc_empty[a], WT);   // one arrival per worker warp
+      mbar_init(&S.acc_empty[a], FUSE_EPI);   // one arrival per epilogue warp
     }
     mbar_init(&S.fin, 1);
     S.abort_flag = 0;
@@ -830,7 +831,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1) k_aev_l1(const __grid_constan
           cnt++;
         }
       }
-    } else {   // workers: bias + CELU of each member's accumulator, rows of lane quarter q, 64 columns each
+    } else if (warp < FUSE_EPI) {   // bias + CELU of each member's accumulator, rows of lane quarter q, 64 columns each
       const int q = warp & 3, part = warp >> 2;
       const long long row = (long long)t * FUSE_ROWS + q * 16 + (lane & 15);
       for (int m = 0; m < M; m++) {
