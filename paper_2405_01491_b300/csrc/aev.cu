@@ -33,6 +33,14 @@ __device__ __forceinline__ float exp2f_fast(float x) {
   return y;
 }
 
+// log2 on the special-function unit (lg2.approx.ftz: about 2 ulp; the arguments are switch values in
+// [0, 1] and section bases above 0.1, and a zero switch value gives -inf, whose power of two is zero)
+__device__ __forceinline__ float log2_fast(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // reciprocal and square root on the special-function unit (rcp.approx / sqrt.approx: about 1 ulp; the
 // arguments are normal numbers: distances above 0.5 A, the section base above 0.1, sin theta' above 0.3)
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -259,11 +267,11 @@ __device__ bool stage_fwd(const StageArgs &A, const AevParams &P, int i, FwdNbr 
     }
   };
   auto put = [&](int pr, int pa, const Ent &t) {
-    S.rr[pr] = make_float2(t.r, __log2f(switch_f(P, t.r, P.rc_rad, P.inv_rc_rad)) - 2.f);
+    S.rr[pr] = make_float2(t.r, log2_fast(switch_f(P, t.r, P.rc_rad, P.inv_rc_rad)) - 2.f);
     if (pa >= 0) {
       const float ir = rcp_fast(t.r);
       S.au[pa] = make_float4(t.dx * ir, t.dy * ir, t.dz * ir, 0.5f * t.r);
-      S.la[pa] = __log2f(switch_f(P, t.r, P.rc_ang, P.inv_rc_ang)) + 0.5f;
+      S.la[pa] = log2_fast(switch_f(P, t.r, P.rc_ang, P.inv_rc_ang)) + 0.5f;
     }
   };
   const bool mine = lane < NE;   // lane q counts element q
@@ -468,7 +476,7 @@ __device__ __forceinline__ void produce_triplet(FwdStage &W, const AevParams &P,
 #pragma unroll
   for (int s = 0; s < NSZ; s++) {
     const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-    W.sf[s][lane] = exp2f_fast(P.zeta * __log2f(base_s));
+    W.sf[s][lane] = exp2f_fast(P.zeta * log2_fast(base_s));
   }
   // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
   const float rbar = u1.w + u2.w, lf = real ? W.nb.la[ja] + W.nb.la[ka] : __int_as_float(0xff800000);
@@ -1013,7 +1021,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
 #pragma unroll
         for (int s = 0; s < NSZ; s++) {
           const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-          const float f = exp2f_fast(P.zeta * __log2f(base_s));
+          const float f = exp2f_fast(P.zeta * log2_fast(base_s));
           fs[s] = f;
           // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
           dfs[s] = P.zeta * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[s], P.qcos_z[s]);
@@ -1249,7 +1257,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
         for (int t = off_r[q] + h; t < off_r[q + 1]; t += 2) {
           const float dr = S.rd[t].w - Rk;
           const float2 ft = W.rt[t];
-          const float gk = __expf(-P.eta_r * dr * dr);
+          const float gk = exp2f_fast(dr * dr * P.eta_r_l2);
           acc += gk * (-2.f * P.eta_r * dr * ft.x + ft.y);
           accf += gk * switch_f(P, S.rd[t].w, P.rc_rad, P.inv_rc_rad);
         }
@@ -1304,7 +1312,7 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
 #pragma unroll
           for (int sidx = 0; sidx < NSZ; sidx++) {
             const float base_s = fmaf(s95, P.hsin_z[sidx], fmaf(c95, P.hcos_z[sidx], 0.5f));
-            const float f = exp2f_fast(P.zeta * __log2f(base_s));
+            const float f = exp2f_fast(P.zeta * log2_fast(base_s));
             W.b.sf[sidx][lane] = f;
             // fdot = zeta f / base * 0.5 (0.95 cos + ds95 sin) * cdot
             W.b.sfd[sidx][lane] = zc * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[sidx], P.qcos_z[sidx]);

@@ -303,7 +303,15 @@ constexpr size_t smem_bytes() {
   return sizeof(Smem<NT, EPI, MODE, QUAD, KB>) + 1024;
 }
 
-__device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (__expf(z * CELU_INV_ALPHA) - 1.f); }
+// e^(z / alpha) as a power of two on the special-function unit (ex2.approx.ftz; z <= 0 where it is used, so
+// the result lies in [0, 1] and results below the normal range flush to zero)
+constexpr float CELU_EXP2 = CELU_INV_ALPHA * 1.4426950408889634f;   // log2(e) / alpha
+__device__ __forceinline__ float exp_celu(float z) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(z * CELU_EXP2));
+  return y;
+}
+__device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALPHA * (exp_celu(z) - 1.f); }
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 // OR of a predicate over the epilogue threads (named barrier 1): keeps their control flow uniform
@@ -677,7 +685,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int u = 0; u < 4; u++) {
               const float z = v[j + u] + zb[u];
-              const float ez = __expf(fminf(z, 0.f) * CELU_INV_ALPHA);
+              const float ez = exp_celu(fminf(z, 0.f));
               ysum += (z > 0.f ? z : CELU_ALPHA * (ez - 1.f)) * wv[u];
               f[j + u] = p.scale * wv[u] * (z > 0.f ? 1.f : ez);
             }

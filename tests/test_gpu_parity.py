@@ -105,7 +105,7 @@ def test_status_codes(fnn):
     assert fnn.sync(ctx)[0] == -1
 
 
-@pytest.mark.parametrize("name", ["gas24", "water216", "box300", "batch64"])
+@pytest.mark.parametrize("name", ["gas24", "water216", "box300", "batch64", "box1100", "mix23558"])
 def test_aev_parity(fnn, name):
     s = structure(name)
     ctx, ds, nl, _ = gpu_list(fnn, s, skin=0.5)
