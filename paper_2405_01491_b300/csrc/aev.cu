@@ -671,11 +671,24 @@ __device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int 
   }
 }
 
+// Warps per row (1 to 8) for nrows rows on nw warps: the kernels are launched as one wave of resident blocks
+// (up to eight warps' worth per row), and rows fewer than half the warps are each shared by several warps,
+// since a row's work is serial within its warp (the 648 atoms of a water box on 4,736 warps would leave most
+// of the GPU idle)
+__device__ __forceinline__ int row_parts(int nrows, int nw) {
+  const int k = nrows > 0 ? nw / nrows : 1;
+  return k < 2 ? 1 : (k > 8 ? 8 : k);
+}
+
 template <typename OutT>
 __global__ void __launch_bounds__(AEV_WARPS * 32, AEV_FWD_BLOCKS) k_aev_forward(AevFwdArgs A) {
   __shared__ FwdStage smem[AEV_WARPS];
-  const int wl = threadIdx.x >> 5;
-  aev_forward_rows<OutT>(A, smem[wl], blockIdx.x * AEV_WARPS + wl, gridDim.x * AEV_WARPS);
+  const int wl = threadIdx.x >> 5, nw = gridDim.x * AEV_WARPS;
+  const int K = row_parts(A.inv ? A.meta[META_NPAD] : A.n_atoms, nw);
+  if (K > 1)
+    aev_forward_parts<OutT>(A, smem[wl], blockIdx.x * AEV_WARPS + wl, nw, K);
+  else
+    aev_forward_rows<OutT>(A, smem[wl], blockIdx.x * AEV_WARPS + wl, nw);
 }
 
 // ------------------------------------------------------------------- fused AEV -> first layer (BF16)
@@ -1166,8 +1179,12 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
 
 __global__ void __launch_bounds__(ADJ_WARPS * 32, AEV_ADJ_BLOCKS) k_aev_adjoint(AevAdjArgs A) {
   __shared__ AdjStage smem[ADJ_WARPS];
-  const int wl = threadIdx.x >> 5;
-  aev_adjoint_rows(A, smem[wl], blockIdx.x * ADJ_WARPS + wl, gridDim.x * ADJ_WARPS);
+  const int wl = threadIdx.x >> 5, nw = gridDim.x * ADJ_WARPS;
+  const int K = row_parts(A.inv ? A.meta[META_NPAD] : A.n_atoms, nw);
+  if (K > 1)
+    aev_adjoint_rows(A, smem[wl], blockIdx.x * ADJ_WARPS + wl, nw, K);
+  else   // (a copy specialised for one warp per row)
+    aev_adjoint_rows(A, smem[wl], blockIdx.x * ADJ_WARPS + wl, nw, 1);
 }
 
 // ------------------------------------------------------------------------------- tangent (JVP)
@@ -1730,7 +1747,7 @@ fnn_status launch_aev_forward(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_forward", s);
-    k_aev_forward<float><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<float><<<aev_grid(ctx, rows * 8, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward");
 }
@@ -1751,7 +1768,7 @@ fnn_status launch_aev_forward_bf16(fnn_ctx *ctx, const fnn_system *sys, const fn
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, out_lo ? "aev_forward_x3" : "aev_forward_bf16", s);
-    k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<__nv_bfloat16><<<aev_grid(ctx, rows * 8, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_bf16");
 }
@@ -1803,7 +1820,7 @@ fnn_status launch_aev_forward_fp8(fnn_ctx *ctx, const fnn_system *sys, const fnn
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_forward_fp8", s);
-    k_aev_forward<__nv_fp8_e4m3><<<aev_grid(ctx, rows, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
+    k_aev_forward<__nv_fp8_e4m3><<<aev_grid(ctx, rows * 8, AEV_FWD_BLOCKS), AEV_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_forward_fp8");
 }
@@ -1824,7 +1841,7 @@ fnn_status launch_aev_adjoint(fnn_ctx *ctx, const fnn_system *sys, const fnn_nli
   if (rows == 0) return FNN_OK;
   {
     FNN_KERNEL(ctx, "aev_adjoint", s);
-    k_aev_adjoint<<<aev_grid(ctx, rows, AEV_ADJ_BLOCKS, ADJ_WARPS), ADJ_WARPS * 32, 0, s>>>(a);
+    k_aev_adjoint<<<aev_grid(ctx, rows * 8, AEV_ADJ_BLOCKS, ADJ_WARPS), ADJ_WARPS * 32, 0, s>>>(a);
   }
   return check_launch(ctx, "aev_adjoint");
 }

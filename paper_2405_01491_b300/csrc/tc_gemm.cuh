@@ -261,7 +261,8 @@ __device__ __forceinline__ TailSched tail_sched(const Args &p, int G, int nkb) {
   s.S = s.R ? min(G / s.R, nkb) : 0;
   return s;
 }
-// the same waves, the R partial-wave tiles cut into S = NT / nsub_w column strips when R S <= G (else S = 1)
+// the same waves, the R partial-wave tiles cut into S = NT / nsub_w column strips when R S <= G, else into
+// two strips of NT / 2 columns (whole nsub_w-row boxes) when 2 R <= G, else not cut (S = 1)
 __device__ __forceinline__ TailSched tail_sched_n(const Args &p, int G, int NTc) {
   TailSched s;
   s.nv = min(p.meta[META_NPAD] / BM, p.n_rowtiles);
@@ -269,7 +270,7 @@ __device__ __forceinline__ TailSched tail_sched_n(const Args &p, int G, int NTc)
   s.W = Tv / G;
   s.R = Tv - s.W * G;
   const int S = NTc / p.nsub_w;
-  s.S = s.R * S <= G ? S : 1;
+  s.S = s.R * S <= G ? S : ((NTc % (2 * p.nsub_w) == 0 && 2 * s.R <= G) ? 2 : 1);
   return s;
 }
 
@@ -418,8 +419,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         w.kb1 = (part + 1) * nkb_fixed / ts.S;
         w.atomic = true;
       } else if (ts.S > 1) {   // a column strip
-        w.c0 = part * p.nsub_w;
-        w.cw = p.nsub_w;
+        w.cw = NT / ts.S;
+        w.c0 = part * w.cw;
       }
     } else {
       return 0;
@@ -474,15 +475,23 @@ __global__ void __launch_bounds__(THREADS, 1)
             *abort_flag = 1;
             break;
           }
-          const bool strip = w.cw < NT;   // B rows nt NT + c0 .. + cw through the strip maps
+          const bool strip = w.cw < NT;   // B rows nt NT + c0 .. + cw through the strip maps (nsub_w-row boxes)
           const CUtensorMap *mb = strip ? &tmBs : &tmB, *mb_lo = strip ? &tmBs_lo : &tmB_lo;
           const int by = nt * NT + w.c0;
+          // the B rows of this item into dst: one box, or cw / nsub_w strip boxes one after another
+          auto load_b = [&](uint8_t *dst, const CUtensorMap *map, int kc) {
+            if (!strip) {
+              tma_load_3d(dst, map, &S.full[s], kc, by, b_grp);
+              return;
+            }
+            for (int h = 0; h < w.cw; h += p.nsub_w) tma_load_3d(dst + h * KB, map, &S.full[s], kc, by + h, b_grp);
+          };
           mbar_expect_tx(&S.full[s], (uint32_t)(SM::AQ * (BM + w.cw) * KB));
           if (QUAD) {   // hi and lo of both operands for one K chunk
             tma_load_3d(S.A[s], &tmA, &S.full[s], kb * BK, a_mid, rt * BM);
             tma_load_3d(S.A[s] + BM * KB, &tmA_lo, &S.full[s], kb * BK, a_mid, rt * BM);
-            tma_load_3d(S.B[s], mb, &S.full[s], kb * BK, by, b_grp);
-            tma_load_3d(S.B[s] + NT * KB, mb_lo, &S.full[s], kb * BK, by, b_grp);
+            load_b(S.B[s], mb, kb * BK);
+            load_b(S.B[s] + NT * KB, mb_lo, kb * BK);
           } else if (WG) {   // term 0 (A, B), then term 1 (A_lo, B_lo): BK rows x 64 features per box
             const int term = kb / nkb_seg, y = r0 + (kb - term * nkb_seg) * BK;
             const CUtensorMap *ma = term ? &tmA_lo : &tmA, *mbw = term ? &tmB_lo : &tmB;
@@ -494,7 +503,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           } else {
             const int seg = SPLIT ? kb / nkb_seg : 0, kk = SPLIT ? kb - seg * nkb_seg : kb;
             tma_load_3d(S.A[s], seg == 2 ? &tmA_lo : &tmA, &S.full[s], kk * BK, a_mid, rt * BM);
-            tma_load_3d(S.B[s], seg == 1 ? mb_lo : mb, &S.full[s], kk * BK, by, b_grp);
+            load_b(S.B[s], seg == 1 ? mb_lo : mb, kk * BK);
           }
           issued = g + 1;
         }
