@@ -110,3 +110,32 @@ def test_fused_graph_replay_matches_eager(fnn):
     fnn.check(ctx, "graph")
     np.testing.assert_allclose(g.E.cpu().numpy(), E0, rtol=0, atol=1e-6 * s.n_atoms)
     assert np.abs(g.F.cpu().numpy() - F0).max() <= 1e-4
+
+
+def test_fused_form_in_md_and_serving(fnn):
+    """The fused form drives device MD (graph blocks with conditional rebuilds) and the server like the unfused
+    BF16 form: the same energies along 12 steps of the water box, within the force scatter's rounding."""
+    import torch
+    s = structure("water216")
+    v0 = synth.maxwell_boltzmann(s.Z, 300.0, seed=7)
+    runs = {}
+    for form in ("bf16", "bf16_fused"):
+        ctx = fnn.Context(1, skin=1.0)
+        fnn.load_weights(ctx, weights(1))
+        ds = fnn.DeviceSystem.from_structures(s)
+        vel = torch.zeros((s.n_atoms, 4), dtype=torch.float32)
+        vel[:, :3] = torch.from_numpy(v0)
+        vel = vel.cuda()
+        nl = fnn.NeighborList(ctx)
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            E, _ = fnn.md_run(ctx, ds, vel, nl, form, 12, 0.5, 4, stream=stream)
+        fnn.check(ctx, "md_run", stream=stream)
+        srv = fnn.Server(ctx, 8 << 30, form, rebuild_every=4)
+        r = srv.poll(srv.submit(s, v0, 12, 0.5), timeout_s=120)
+        srv.close()
+        runs[form] = (E.cpu().numpy()[:, 0], r["energies"])
+    for k in range(2):
+        d = np.abs(runs["bf16"][k] - runs["bf16_fused"][k]).max() / s.n_atoms
+        assert d <= 1e-6, (k, d)
