@@ -170,12 +170,13 @@ fnn_status launch_l3_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *con
 
 template <int NT, int EPI, int MODE, bool QUAD = false, int KB = tc::BKB>
 fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, dim3 tiles, cudaStream_t s) {
-  // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid
+  // persistent launch: at most one CTA per SM over the (n tile, row tile, member) grid; a launch whose partial
+  // wave is split (K parts or column strips) takes every SM, the split's parts being spread over the grid
   a.n_ntiles = (int)tiles.x;
   a.n_rowtiles = (int)tiles.y;
   a.n_members = (int)tiles.z;
   const long long T = (long long)tiles.x * tiles.y * tiles.z;
-  dim3 grid((unsigned)(T < ctx->num_sms ? T : ctx->num_sms));
+  dim3 grid((unsigned)(T < ctx->num_sms && !a.tail_split && !a.tail_nsplit ? T : ctx->num_sms));
   static bool attr_set = false;
   const size_t sm = tc::smem_bytes<NT, EPI, MODE, QUAD, KB>();
   if (!attr_set) {
@@ -548,7 +549,7 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   az.n_ntiles = (NAEV + 255) / 256; az.n_rowtiles = (int)tiles; az.n_members = 1;
   az.N = NAEV; az.out = ctx->ws.gaev; az.ldo = NAEV; az.o_mstride = 0;
   az.tail_split = 1; az.meta = nl->meta; az.tile_elem = nl->tile_elem;
-  const int G1 = az.n_ntiles * az.n_rowtiles < ctx->num_sms ? az.n_ntiles * az.n_rowtiles : ctx->num_sms;
+  const int G1 = ctx->num_sms;   // the grid of the tail-split first-layer input gradient below
   const int nkb1 = SPLIT ? (M * H1 + 31) / 32 : (M * H1 + 63) / 64;   // K chunks: 64-byte rows (split), 128 (bf16)
   if ((st = side_fork(ctx, s)) || (st = energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, ctx->side)))
     return st;
