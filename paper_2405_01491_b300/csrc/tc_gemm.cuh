@@ -605,6 +605,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (SM::NBUF == 1 && gk >= 1) bulk_wait_read0();
         load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, w.c0 + 16 * part, rt, m);
       }
+      const float *bias = p.bias + e * p.bias_estride + m * p.bias_mstride + n0;
+      // the bias of this warp's pieces, read while the MMAs run: lane j holds column j of each piece (one
+      // value per piece, broadcast by shuffles below), so no load waits inside the drain
+      constexpr int NPB = (NT + 63) / 64;
+      float pre[NPB];
+      if (EPI == EPI_BIAS_CELU) {
+#pragma unroll
+        for (int i = 0; i < NPB; i++) {
+          const int c = w.c0 + 16 * part + 64 * i;
+          pre[i] = c < cend ? __ldg(bias + c + (lane & 15)) : 0.f;
+        }
+      }
       bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
       if (!__all_sync(0xffffffffu, ok)) {
@@ -616,12 +628,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       float ysum = 0.f;
       float sc = 1.f;   // dequantisation of the fp8 product
       if (F8) sc = p.a_scale * p.b_scale[(p.b_scale_by == 1 ? m : p.b_scale_by == 2 ? nt : 0) * NE + e];
-      const float *bias = p.bias + e * p.bias_estride + m * p.bias_mstride + n0;
       const float *w4 = p.w4 + e * p.w4_estride + m * p.w4_mstride + n0;
       const int oy = p.o_y == 1 ? m : p.o_y == 2 ? nt : 0;
       bool abort_now = false;
 #pragma unroll 1
       for (int c = w.c0 + 16 * part; c < w.c0 + w.cw; c += 64) {
+        float pb = 0.f;   // this piece's prefetched bias (lane j: column j)
+        if (EPI == EPI_BIAS_CELU) {
+          pb = pre[0];
+#pragma unroll
+          for (int i = 0; i + 1 < NPB; i++) pre[i] = pre[i + 1];
+        }
         float v[16];
         tmem_ld16(tbase + (c - w.c0), v);
         if (c >= ncols) continue;  // warp-uniform; ncols is a multiple of 16 in every use
@@ -678,13 +695,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int j = 0; j < 16; j++) f[j] = v[j];
         } else if (EPI == EPI_BIAS_CELU) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c + j));
-            f[j] = celu_f(v[j] + bb.x);
-            f[j + 1] = celu_f(v[j + 1] + bb.y);
-            f[j + 2] = celu_f(v[j + 2] + bb.z);
-            f[j + 3] = celu_f(v[j + 3] + bb.w);
-          }
+          for (int j = 0; j < 16; j++) f[j] = celu_f(v[j] + __shfl_sync(0xffffffffu, pb, j));
         } else if (EPI == EPI_L3) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4) {
