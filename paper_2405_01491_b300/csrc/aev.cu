@@ -594,13 +594,16 @@ __device__ __forceinline__ void aev_row(const AevFwdArgs &A, FwdStage &W, int i,
 
 // One warp's share of the forward: rows wg, wg + nw, ..., staged in W (the kernel below, and the fused
 // small-system kernel, call it)
+// (rl: when set, only the nrl rows rl[0 ..) -- atoms, without inv -- in place of every row)
 template <typename OutT>
-__device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw) {
-  const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
-  for (int row = wg; row < nrows; row += nw) {
+__device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &W, int wg, int nw,
+                                                 const int *rl = nullptr, int nrl = 0) {
+  const int nrows = rl ? nrl : (A.inv ? A.meta[META_NPAD] : A.n_atoms);
+  for (int q = wg; q < nrows; q += nw) {
+    const int row = rl ? rl[q] : q;
     const GlobalRow<OutT> o{reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV,
                             A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr, A.out_inv};
-    aev_row(A, W, A.inv ? A.inv[row] : row, o);
+    aev_row(A, W, A.inv && !rl ? A.inv[row] : row, o);
     __syncwarp();
   }
 }
@@ -609,18 +612,20 @@ __device__ __forceinline__ void aev_forward_rows(const AevFwdArgs &A, FwdStage &
 // row writes the radial slots and the zeros of element pairs without triplets, parts 1 .. K-1 take the
 // row's non-empty element-pair blocks in turn, each block's slots summed by one warp from its own batches
 template <typename OutT>
-__device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int nw, int K) {
+__device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int nw, int K, const int *rl = nullptr,
+                                  int nrl = 0) {
   const int lane = threadIdx.x & 31;
   const AevParams &P = A.P;
   const int part = wg % K, groups = nw / K;
   if (wg >= groups * K) return;
-  const int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  const int nrows = rl ? nrl : (A.inv ? A.meta[META_NPAD] : A.n_atoms);
   const int s_my = lane & 3, m_my = lane >> 2;
   const float *fr = W.sf[s_my], *gr = W.sg[m_my];
-  for (int row = wg / K; row < nrows; row += groups) {
+  for (int q = wg / K; q < nrows; q += groups) {
+    const int row = rl ? rl[q] : q;
     OutT *out = reinterpret_cast<OutT *>(A.out) + (size_t)row * NAEV;
     __nv_bfloat16 *lo = A.out_lo ? A.out_lo + (size_t)row * NAEV : nullptr;
-    const int i = A.inv ? A.inv[row] : row;
+    const int i = A.inv && !rl ? A.inv[row] : row;
     int orr, oa, ca;
     const bool ok = i >= 0 && stage_fwd(A.sa, P, i, W.nb, orr, oa, ca, A.st);
     if (!ok) {
@@ -929,11 +934,12 @@ struct AevAdjArgs {
 // With K > 1 warps per row (systems with fewer rows than warps) warp part 0 of a row takes its radial
 // terms and parts 1 .. K-1 its angular batches in turn; each warp scatters what it summed (the forces and
 // virials are sums).
-__device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &W, int wg, int nw, int K = 1) {
+__device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &W, int wg, int nw, int K = 1,
+                                                 const int *rl = nullptr, int nrl = 0) {
   int lane = threadIdx.x & 31;
   NbrStage &S = W.nb;
   const AevParams &P = A.P;
-  int nrows = A.inv ? A.meta[META_NPAD] : A.n_atoms;
+  const int nrows = rl ? nrl : (A.inv ? A.meta[META_NPAD] : A.n_atoms);
   double *vacc = W.vacc;
   if (lane == 0)
     for (int q = 0; q < 9; q++) vacc[q] = 0.0;
@@ -942,8 +948,9 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
   if (wg >= groups * K) return;
   const bool do_rad = part == 0, do_ang = K == 1 || part > 0;
   const int apart = K == 1 ? 0 : part - 1, aparts = K == 1 ? 1 : K - 1;   // this warp's share of the batches
-  for (int row = wg / K; row < nrows; row += groups) {
-    int i = A.inv ? A.inv[row] : row;
+  for (int q = wg / K; q < nrows; q += groups) {
+    const int row = rl ? rl[q] : q;
+    const int i = A.inv && !rl ? A.inv[row] : row;
     if (i < 0) continue;
     const float *G = A.gaev + (size_t)row * NAEV;
     int orr, oa, cr, ca;
@@ -1375,57 +1382,39 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
 }
 
 // ------------------------------------------------------------------------------ small systems
-// Energies, forces and virials of a small system (atoms x members at most SMALL_EVAL_ROWS) in one cooperative
-// launch: the AEV forward, the networks forward (members fused in the first layer) and backward to dE/dAEV in
-// FP32 FFMA, the AEV adjoint and the float64 energies, the stages separated by grid barriers.  A single
-// 128-row tensor-core tile would sit on one SM; here every dense layer is cut into tasks of (member, element,
-// up to 16 of its atoms, 32 output columns) spread over the grid, each reducing K across its 8 warps in a
-// fixed order, so the energies are deterministic.
+// Energies, forces and virials of a small system (atoms x members at most SMALL_EVAL_ROWS) in one launch of
+// thread-block clusters: the AEV forward, the networks forward (members fused in the first layer) and
+// backward to dE/dAEV in FP32 FFMA, and the AEV adjoint.  The atoms are cut into row groups (up to 16 atoms
+// of one element, in species order); a cluster owns whole row groups, so every stage of its rows reads only
+// what its own CTAs wrote and the stages are separated by cluster barriers (no grid-wide barrier).  Every
+// dense layer of a cluster is cut into tasks of (member, row group, 32 or 16 output columns) spread over its
+// CTAs, each reducing K across its 8 warps in a fixed order; the last CTA to finish sums the energies in a
+// fixed order, so they are deterministic.  A single 128-row tensor-core tile would sit on one SM.
 constexpr int SE_WARPS = 8, SE_RG = 16;
-constexpr long long SE_BARRIER_LIMIT = 2000000000LL;   // clock64 cycles (about a second) per barrier wait
+constexpr int SE_CL = 16;        // CTAs per cluster (one SM each)
+constexpr int SE_MAXCL = 4;      // clusters per launch
+constexpr int SE_MAXG = SMALL_BUILD_ATOMS / SE_RG + NE;   // row groups of a system, at most
 
 struct GridBar {
-  unsigned count, gen, pad0, pad1;   // arrivals so far; barriers completed (bit 31: aborted)
+  unsigned count, gen, pad0, pad1;   // CTAs finished (the last one sums the energies); zeroed before a launch
 };
 
-// Every block arrives (the count is cumulative over the launch, zeroed before it); the last arrival of
-// barrier k (phase, counted by the block) releases the others by advancing the generation to k + 1.  A wait
-// that runs out posts FNN_E_TIMEOUT and sets bit 31 of the generation, which every later wait sees.
-// Returns false once aborted (every block then leaves).
-__device__ bool grid_barrier(GridBar *b, DevStatus *st, unsigned &phase) {
-  __shared__ int ok_s;
-  const unsigned target = ++phase;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool ok = true;
-    __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x * target - 1) {
-      __threadfence();
-      ok = (atomicAdd(&b->gen, 1u) >> 31) == 0u;
-    } else {
-      const long long t0 = clock64();
-      for (;;) {
-        unsigned cur;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&b->gen) : "memory");
-        if (cur >> 31) {
-          ok = false;
-          break;
-        }
-        if (cur >= target) break;
-        if (clock64() - t0 > SE_BARRIER_LIMIT) {
-          post_status(st, FNN_E_TIMEOUT, -2);
-          atomicOr(&b->gen, 0x80000000u);
-          ok = false;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
+// every thread of every CTA of the cluster: arrive (release) and wait (acquire) at the cluster barrier, which
+// orders the CTAs' global-memory writes before the stage that reads them
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+
+// the row groups a cluster owns: element, first position in the species-sorted atom list, atoms
+struct SmallGroups {
+  int n;
+  int e[SE_MAXG], base[SE_MAXG], R[SE_MAXG];
+};
 
 struct SmallEvalArgs {
   AevFwdArgs fa;
@@ -1463,31 +1452,21 @@ union SmallShared {
   SmallDense d;
 };
 
-// Task t of a layer over the element row groups: member, element, row group (atoms rows[0..R)), column chunk.
+// Task t of a layer over a cluster's row groups: member, element, row group (atoms rows[0..R)), column chunk.
 struct SmallTask {
   int m, e, R, chunk;
 };
-__device__ bool small_task(const SmallEvalArgs &A, const int *ecount, const int *estart, const int *srow, int t,
-                           int n_chunks, int members, SmallTask &k, int *rows) {
-  int per_m = 0;
-  for (int e = 0; e < NE; e++) per_m += (ecount[e] + SE_RG - 1) / SE_RG * n_chunks;
+__device__ bool small_task(const SmallGroups &G, const int *srow, int t, int n_chunks, int members, SmallTask &k,
+                           int *rows) {
+  const int per_m = G.n * n_chunks;
   if (t >= per_m * members) return false;
   k.m = t / per_m;
-  int u = t - k.m * per_m;
-  for (int e = 0; e < NE; e++) {
-    const int g = (ecount[e] + SE_RG - 1) / SE_RG;
-    if (u < g * n_chunks) {
-      const int rg = u / n_chunks;
-      k.e = e;
-      k.chunk = u - rg * n_chunks;
-      k.R = min(SE_RG, ecount[e] - rg * SE_RG);
-      const int base = estart[e] + rg * SE_RG;
-      if (threadIdx.x < SE_RG) rows[threadIdx.x] = threadIdx.x < k.R ? srow[base + threadIdx.x] : 0;
-      return true;
-    }
-    u -= g * n_chunks;
-  }
-  return false;
+  const int u = t - k.m * per_m, gi = u / n_chunks;
+  k.chunk = u - gi * n_chunks;
+  k.e = G.e[gi];
+  k.R = G.R[gi];
+  if (threadIdx.x < SE_RG) rows[threadIdx.x] = threadIdx.x < k.R ? srow[G.base[gi] + threadIdx.x] : 0;
+  return true;
 }
 
 
@@ -1513,31 +1492,30 @@ __device__ __forceinline__ float celu_f(float z) { return z > 0.f ? z : CELU_ALP
 // CELU' from the activation h = CELU(z): 1 for z > 0, exp(z / alpha) = 1 + h / alpha otherwise
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : fmaf(h, CELU_INV_ALPHA, 1.f); }
 
-// One dense layer over every (member, element row group, column chunk) task of the grid; K in staged
-// chunks, each warp a slice of every chunk, the warps' partial sums added in a fixed order.  Chunks are 32
-// columns (a lane per column), or 16 when that leaves at least half of the blocks without a task (a lane
+// One dense layer over every (member, row group, column chunk) task of the cluster's row groups, spread over
+// its CTAs; K in staged chunks, each warp a slice of every chunk, the warps' partial sums added in a fixed
+// order.  Chunks are 32 columns (a lane per column), or 16 when that leaves at least half of the cluster's
+// CTAs without a task (a lane
 // per column and half of the warp's K slice, the halves added by one shuffle); the third layer keeps 32
 // (its output-layer partial sums have a slot per 32 columns).
 // kind 0: out = CELU(A B + bias); 1: out = (A B) * CELU'(aux); 2: out = A B;
 // 3 (third layer): h = CELU(A B + bias), out = w4 CELU'(h) / M, and the output layer's sum of w4 h over the
 // chunk's columns into ysl[(row M + m) SE_YCH + chunk]
-__device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ecount, const int *estart,
-                            const int *srow, int kind, const float *Ab,
+__device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const SmallGroups &G, const int *srow, int kind,
+                            const float *Ab,
                             int lda, int a_member_off, int K, const float *Bb, long long b_me_stride, int ldb,
                             int ncol, const float *bias, long long bias_me_stride, const float *aux, int ldaux,
                             int aux_member_off, float *out, int ldo, int o_member_off, int members, float *ysl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int tasks32 = 0;
-  for (int e = 0; e < NE; e++) tasks32 += (ecount[e] + SE_RG - 1) / SE_RG;
-  tasks32 *= members * ((ncol + 31) / 32);
-  const int cw = (kind != 3 && 2 * tasks32 <= (int)gridDim.x) ? 16 : 32;
+  const int tasks32 = G.n * members * ((ncol + 31) / 32);
+  const int cw = (kind != 3 && 2 * tasks32 <= SE_CL) ? 16 : 32;
   const int n_chunks = (ncol + cw - 1) / cw;
   const int nkc = (K + SE_KC - 1) / SE_KC;
   const int col_l = cw == 32 ? lane : (lane & 15), kh = cw == 32 ? 0 : lane >> 4;   // column and K half of the lane
-  for (int t = blockIdx.x;; t += gridDim.x) {
+  for (int t = cluster_rank();; t += SE_CL) {
     SmallTask k;
     __syncthreads();
-    const bool ok = small_task(A, ecount, estart, srow, t, n_chunks, members, k, D.rows);
+    const bool ok = small_task(G, srow, t, n_chunks, members, k, D.rows);
     __syncthreads();
     if (!ok) break;
     const int c0 = k.chunk * cw;
@@ -1624,14 +1602,16 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const int *ec
 __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A) {
   extern __shared__ __align__(16) unsigned char small_eval_dyn[];
   SmallShared &S = *reinterpret_cast<SmallShared *>(small_eval_dyn);
-  __shared__ int ecount[NE];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wg = blockIdx.x * SE_WARPS + warp, nw = gridDim.x * SE_WARPS;
   const int M = A.M, N = A.N;
-  unsigned phase = 0;   // grid barriers passed
-  // element counts and the atoms in element order (every block; from the species order of the list)
-  __shared__ int estart[NE + 1];
+  const int crank = cluster_rank(), cid = (int)blockIdx.x / SE_CL, ncl = (int)gridDim.x / SE_CL;
+  // element counts and the atoms in element order (every CTA; from the species order of the list)
+  __shared__ int ecount[NE], estart[NE + 1];
   __shared__ int srow[SMALL_BUILD_ATOMS];
+  // the row groups of this cluster (groups cid, cid + ncl, ... of the element-major list) and their atoms
+  __shared__ SmallGroups G;
+  __shared__ int crow[SMALL_BUILD_ATOMS];
+  __shared__ int n_crow, last_cta;
   if (threadIdx.x < NE) ecount[threadIdx.x] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&ecount[A.elem[i]], 1);
@@ -1639,54 +1619,77 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   if (threadIdx.x == 0) {
     estart[0] = 0;
     for (int e = 0; e < NE; e++) estart[e + 1] = estart[e] + ecount[e];
+    int g = 0, n = 0;
+    for (int e = 0; e < NE; e++)
+      for (int r0 = 0; r0 < ecount[e]; r0 += SE_RG, g++)
+        if (g % ncl == cid) {
+          G.e[n] = e;
+          G.base[n] = estart[e] + r0;
+          G.R[n] = min(SE_RG, ecount[e] - r0);
+          n++;
+        }
+    G.n = n;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int e = A.elem[i];
     srow[estart[e] + A.perm[i] - A.meta[META_SEG + e]] = i;
   }
-  // zero the accumulated outputs
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * N; q += gridDim.x * blockDim.x) A.F[q] = 0.f;
-  if (A.virial)
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 9 * A.NM; q += gridDim.x * blockDim.x) A.virial[q] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int q = 0; q < G.n; q++)
+      for (int r = 0; r < G.R[q]; r++) crow[n++] = srow[G.base[q] + r];
+    n_crow = n;
+  }
+  __syncthreads();
+  // the cluster's warps over its atoms: a row per warp, or (fewer rows than warps) up to eight warps per row
+  const int wg = crank * SE_WARPS + warp, nw = SE_CL * SE_WARPS;
+  const int Kw = min(8, max(1, nw / max(n_crow, 1)));
   // AEV rows (atom order)
-  // a row per warp, or (fewer rows than warps) up to eight warps per row
-  const int Kw = min(8, max(1, nw / max(N, 1)));
-  if (Kw > 1) aev_forward_parts<float>(A.fa, S.fwd[warp], wg, nw, Kw);
-  else aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  if (Kw > 1) aev_forward_parts<float>(A.fa, S.fwd[warp], wg, nw, Kw, crow, n_crow);
+  else aev_forward_rows<float>(A.fa, S.fwd[warp], wg, nw, crow, n_crow);
+  cluster_sync_all();
   SmallDense &D = S.d;
   const int MH1 = M * H1;
   // first layer, all members fused: h1 = CELU(aev W1^T + b1), [N][M 256]
-  small_layer(A, D, ecount, estart, srow, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0,
-              0, A.h1, MH1, 0, 1, nullptr);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  small_layer(A, D, G, srow, 0, A.aev, NAEV, 0, NAEV, A.W1T, (long long)NAEV * MH1, MH1, MH1, A.b1, MH1, nullptr, 0, 0,
+              A.h1, MH1, 0, 1, nullptr);
+  cluster_sync_all();
   // second layer per member: h2 = CELU(h1_m W2^T + b2), [N][M 192]
-  small_layer(A, D, ecount, estart, srow, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2,
-              M * H2, H2, M, nullptr);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  small_layer(A, D, G, srow, 0, A.h1, MH1, H1, H1, A.W2T, (long long)H1 * H2, H2, H2, A.b2, H2, nullptr, 0, 0, A.h2, M * H2,
+              H2, M, nullptr);
+  cluster_sync_all();
   // third layer per member: h3 = CELU(h2_m W3^T + b3) -> g3 = (1/M) w4 CELU'(z3) and the output layer's
   // partial sums per column chunk (fixed slots, added in a fixed order with the energies)
-  small_layer(A, D, ecount, estart, srow, 3, A.h2, M * H2, H2, H2, A.W3T, (long long)H2 * H3, H3, H3, A.b3, H3, nullptr, 0, 0, A.g3,
+  small_layer(A, D, G, srow, 3, A.h2, M * H2, H2, H2, A.W3T, (long long)H2 * H3, H3, H3, A.b3, H3, nullptr, 0, 0, A.g3,
               M * H3, H3, M, A.ysl);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  cluster_sync_all();
   // third layer's input gradient: g2 = (g3 W3) * CELU'(h2)
-  small_layer(A, D, ecount, estart, srow, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2,
-              A.g2, M * H2, H2, M, nullptr);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  small_layer(A, D, G, srow, 1, A.g3, M * H3, H3, H3, A.W3, (long long)H3 * H2, H2, H2, nullptr, 0, A.h2, M * H2, H2, A.g2,
+              M * H2, H2, M, nullptr);
+  cluster_sync_all();
   // second layer's: g1 = (g2 W2) * CELU'(h1)
-  small_layer(A, D, ecount, estart, srow, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1,
-              A.g1, MH1, H1, M, nullptr);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
+  small_layer(A, D, G, srow, 1, A.g2, M * H2, H2, H2, A.W2, (long long)H2 * H1, H1, H1, nullptr, 0, A.h1, MH1, H1, A.g1,
+              MH1, H1, M, nullptr);
+  cluster_sync_all();
   // first layer's, summed over the members: dE/dAEV = g1 W1 (K = M 256 through the member-concatenated W1)
-  small_layer(A, D, ecount, estart, srow, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
+  small_layer(A, D, G, srow, 2, A.g1, MH1, 0, MH1, A.W1, (long long)MH1 * NAEV, NAEV, NAEV, nullptr, 0, nullptr, 0, 0,
               A.gaev, NAEV, 0, 1, nullptr);
-  if (!grid_barrier(A.bar, A.st, phase)) return;
-  // forces and virials (a warp per atom, the first warps); the energies meanwhile on the last warps, a warp
-  // per structure: lanes over its atoms, then a shuffle tree (a fixed order)
+  cluster_sync_all();
+  // forces and virials of the cluster's atoms (F and the virials were zeroed before the launch)
+  aev_adjoint_rows(A.aa, S.adj[warp], wg, nw, Kw, crow, n_crow);
+  // the energies, by the last CTA to finish (every CTA's output-layer sums are written by then): a warp per
+  // structure, lanes over its atoms, then a shuffle tree (a fixed order)
   __syncthreads();
-  aev_adjoint_rows(A.aa, S.adj[warp], wg, nw, Kw);
-  for (int m = nw - 1 - wg; m < A.NM; m += nw) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_cta = atomicAdd(&A.bar->count, 1u) == gridDim.x - 1;
+    __threadfence();
+  }
+  __syncthreads();
+  if (!last_cta) return;
+  for (int m = warp; m < A.NM; m += SE_WARPS) {
     const int a0 = max(A.mol_offsets[m], 0), a1 = min(A.mol_offsets[m + 1], N);
     double e = 0.0;
     for (int i = a0 + lane; i < a1; i += 32) {
@@ -1694,7 +1697,7 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
       double yi = 0.0;
       for (int q = 0; q < M; q++) {
         float yq = A.b4[q * NE + el];
-        for (int c = 0; c < SE_YCH; c++) yq += A.ysl[((size_t)i * M + q) * SE_YCH + c];
+        for (int c = 0; c < SE_YCH; c++) yq += __ldcg(&A.ysl[((size_t)i * M + q) * SE_YCH + c]);
         yi += (double)yq;
       }
       e += yi / (double)M;
@@ -1705,6 +1708,14 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
     A.E[m] = e;
     if (!isfinite(e)) post_status(A.st, FNN_E_NONFINITE, -(long long)(m + 1));
   }
+}
+
+// before each evaluation: the finish count, the forces and the virials, which the clusters accumulate into
+__global__ void k_small_zero(GridBar *bar, float *F, int nf, double *virial, int nv) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) bar->count = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x) F[q] = 0.f;
+  if (virial)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += gridDim.x * blockDim.x) virial[q] = 0.0;
 }
 
 static StageArgs stage_args(const fnn_system *sys, const fnn_nlist *nl) {
@@ -1882,15 +1893,28 @@ fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlis
   // the barrier word, then the output-layer partial sums (atoms x members x chunks at most SMALL_EVAL_ROWS x 5)
   if (!ctx->grid_bar) FNN_CUDA_TRY(ctx, cudaMalloc(&ctx->grid_bar, 256 + (size_t)SMALL_EVAL_ROWS * SE_YCH * sizeof(float)));
   const size_t dyn = sizeof(SmallShared);
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(SE_WARPS * 32);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = SE_CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   static bool attr_set = false;
-  static int per_sm = 0;
+  static int max_clusters = 0;
   if (!attr_set) {
     FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(k_small_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_eval, SE_WARPS * 32, dyn));
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(k_small_eval, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cfg.gridDim = dim3(SE_CL * SE_MAXCL);
+    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&max_clusters, k_small_eval, &cfg));
     attr_set = true;
   }
-  if (per_sm < 1) {
-    ctx->last_error = "small-system kernel does not fit on an SM";
+  if (max_clusters < 1) {
+    ctx->last_error = "small-system kernel: no cluster of 16 CTAs fits on the device";
     return FNN_E_CUDA;
   }
   Workspace &ws = ctx->ws;
@@ -1945,22 +1969,16 @@ fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlis
   a.virial = virial;
   a.bar = reinterpret_cast<GridBar *>(ctx->grid_bar);
   a.st = ctx->status;
-  // a grid no larger than the widest layer needs (and co-resident: a cooperative launch)
+  // clusters: at most one per row group (an upper bound: ceil(N / 16) + 7), SE_MAXCL, and the clusters that fit
+  // at once (they never wait on one another, so fewer would still finish)
   const int row_groups = (N + SE_RG - 1) / SE_RG + NE;
-  int grid = row_groups * (NAEV + 31) / 32;
-  const int cap = per_sm * ctx->num_sms < 64 ? per_sm * ctx->num_sms : 64;   // fewer arrivals per barrier
-  if (grid > cap) grid = cap;
-  FNN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), s));
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(SE_WARPS * 32);
-  cfg.dynamicSmemBytes = dyn;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  int ncl = row_groups < SE_MAXCL ? row_groups : SE_MAXCL;
+  if (ncl > max_clusters) ncl = max_clusters;
+  {
+    FNN_KERNEL(ctx, "small_zero", s);
+    k_small_zero<<<1, 256, 0, s>>>(a.bar, F, 3 * N, virial, 9 * sys->n_mol);
+  }
+  cfg.gridDim = dim3(SE_CL * ncl);
   {
     FNN_KERNEL(ctx, "small_eval", s);
     FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_small_eval, a));
