@@ -1610,6 +1610,7 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
   __shared__ int srow[SMALL_BUILD_ATOMS];
   // the row groups of this cluster (groups cid, cid + ncl, ... of the element-major list) and their atoms
   __shared__ SmallGroups G;
+  __shared__ int goff[SE_MAXG];   // first position of each owned group in crow
   __shared__ int crow[SMALL_BUILD_ATOMS];
   __shared__ int n_crow, last_cta;
   if (threadIdx.x < NE) ecount[threadIdx.x] = 0;
@@ -1626,9 +1627,11 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
           G.e[n] = e;
           G.base[n] = estart[e] + r0;
           G.R[n] = min(SE_RG, ecount[e] - r0);
+          goff[n] = n == 0 ? 0 : goff[n - 1] + G.R[n - 1];
           n++;
         }
     G.n = n;
+    n_crow = n ? goff[n - 1] + G.R[n - 1] : 0;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -1636,12 +1639,8 @@ __global__ void __launch_bounds__(SE_WARPS * 32, 1) k_small_eval(SmallEvalArgs A
     srow[estart[e] + A.perm[i] - A.meta[META_SEG + e]] = i;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int n = 0;
-    for (int q = 0; q < G.n; q++)
-      for (int r = 0; r < G.R[q]; r++) crow[n++] = srow[G.base[q] + r];
-    n_crow = n;
-  }
+  for (int q = 0; q < G.n; q++)
+    for (int r = threadIdx.x; r < G.R[q]; r += blockDim.x) crow[goff[q] + r] = srow[G.base[q] + r];
   __syncthreads();
   // the cluster's warps over its atoms: a row per warp, or (fewer rows than warps) up to eight warps per row
   const int wg = crank * SE_WARPS + warp, nw = SE_CL * SE_WARPS;
