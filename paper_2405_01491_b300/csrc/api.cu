@@ -349,8 +349,9 @@ extern "C" fnn_status fnn_energy_forces(fnn_ctx *ctx, const fnn_system *sys, con
   cudaStream_t s = (cudaStream_t)stream;
   fnn_status st;
   if ((st = ensure_workspace(ctx, nl->pad_cap))) return st;
-  // small systems in the FP32 forms: one cooperative launch spread over the SMs (FP32 FFMA networks, exact
-  // FP32 products, so also for the FP32X3 form) instead of a pipeline of single-SM tensor-core tiles
+  // small systems in the FP32 forms: one launch of thread-block clusters spread over the SMs (FP32 FFMA
+  // networks, exact FP32 products, so also for the FP32X3 form) instead of a pipeline of single-SM
+  // tensor-core tiles
   if ((prec == FNN_FP32 || prec == FNN_FP32X3) && sys->n_atoms > 0 && sys->n_atoms <= SMALL_BUILD_ATOMS &&
       (long long)sys->n_atoms * ctx->cfg.n_members <= SMALL_EVAL_ROWS)
     return launch_small_eval(ctx, sys, nl, E, F, virial, s);

@@ -29,8 +29,8 @@ constexpr int ROW_TILE = 128;               // species segments are padded to th
 constexpr int PAIR_STRIDE = 128;
 constexpr int RAD_CAP = 160;                // neighbours within rc_rad handled per atom
 // systems of at most this many atoms (in at most SMALL_BUILD_MOL structures) have their list built by one
-// block (k_small_build), and the FP32 forms evaluated by one cooperative kernel when atoms x members is at
-// most SMALL_EVAL_ROWS (fnn_energy_forces)
+// block (k_small_build), and the FP32 forms evaluated by one kernel of thread-block clusters when atoms x
+// members is at most SMALL_EVAL_ROWS (fnn_energy_forces)
 constexpr int SMALL_BUILD_ATOMS = 256, SMALL_BUILD_MOL = 256, SMALL_EVAL_ROWS = 256;
 constexpr int ANG_CAP = 64;                 // neighbours within rc_ang handled per atom
 constexpr float CELU_ALPHA = 0.1f;
@@ -197,7 +197,7 @@ struct fnn_ctx {
   int num_sms = 148;
   fnn::DevStatus *status = nullptr;   // device
   int32_t *pinned_flag = nullptr;      // 64 pinned host bytes: device scalars read between eager MD steps
-  void *grid_bar = nullptr;            // the small-system kernel's grid barrier (device, cleared per launch)
+  void *grid_bar = nullptr;            // the small-system kernel's finish counter and output-layer sums (device)
   fnn::DeviceWeights w;
   bool has_weights = false;
   fnn::Workspace ws;
@@ -355,7 +355,7 @@ fnn_status energy_reduce(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *n
 fnn_status energy_reduce_rows(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, const float *ypart,
                               int ntile, double *E, cudaStream_t s);
 fnn_status ensure_workspace(fnn_ctx *ctx, size_t rows);
-// energies, forces and virials of a small system in one cooperative launch (FP32 networks), aev.cu
+// energies, forces and virials of a small system in one launch of thread-block clusters (FP32 networks), aev.cu
 fnn_status launch_small_eval(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *nl, double *E, float *F,
                              double *virial, cudaStream_t s);
 
