@@ -598,12 +598,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int n0 = nt * NT;
       const int ncols = min(NT, p.N - n0);
       nt_cur = nt;
-      // the first aux piece of the tile travels while its MMAs run
+      // the first aux pieces of the tile (two with two buffers: the loads stay two pieces ahead) travel
+      // while its MMAs run
       const int cend = min(ncols, w.c0 + w.cw);   // the item's columns (tile coordinates)
       if (EPI == EPI_DCELU && lane == 0 && w.c0 + 16 * part < cend) {
-        if (SM::NBUF == 2 && gk >= 2) bulk_wait_read1();
-        if (SM::NBUF == 1 && gk >= 1) bulk_wait_read0();
+        if (gk >= 1) bulk_wait_read0();   // the stores that last read the buffers
         load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, w.c0 + 16 * part, rt, m);
+        if (SM::NBUF == 2 && w.c0 + 16 * part + 64 < cend) load_aux((int)((gk + 1) & 1), w.c0 + 16 * part + 64, rt, m);
       }
       const float *bias = p.bias + e * p.bias_estride + m * p.bias_mstride + n0;
       // the bias of this warp's pieces, read while the MMAs run: lane j holds column j of each piece (one
@@ -767,11 +768,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_store_3d(&tmO, ob, x, oy, rt * BM + q * 32);
           if (SPLIT) tma_store_3d(&tmO_lo, ob + SM::WBUF, x, oy, rt * BM + q * 32);
           bulk_commit();
-          if (EPI == EPI_DCELU && c + 64 < cend) {   // this warp's next aux piece into the other buffer
-            if (SM::NBUF == 2) {
-              bulk_wait_read1();
-              load_aux(b ^ 1, c + 64, rt, m);
-            } else {   // one buffer: once this store has read it
+          if (EPI == EPI_DCELU) {
+            if (SM::NBUF == 2 && c + 128 < cend) {   // the piece after next into this buffer, once read
+              bulk_wait_read0();
+              load_aux(b, c + 128, rt, m);
+            } else if (SM::NBUF == 1 && c + 64 < cend) {   // one buffer: the next piece, once this store read it
               bulk_wait_read0();
               load_aux(0, c + 64, rt, m);
             }
