@@ -283,9 +283,13 @@ struct Smem {
   static constexpr int OB = (EPI == EPI_F32 || EPI == EPI_ATOMIC) ? 1 : (MODE == MODE_SPLIT ? 2 : 1);
   static constexpr int WBUF = 1024;                                             // 32 rows x 32 bytes
   // output buffers per warp: two (one fills while the other's store reads), one where the ring needs
-  // the space more (the split first layer: a fourth operand stage)
+  // the space more (the split first layer: a fourth operand stage); the CELU' epilogue's buffers also
+  // receive its aux pieces, loaded DCB pieces ahead (four for bf16 and fp8 operands; two for the split,
+  // where four would cost it an operand stage: 106 -> 125 us for its second-layer backward)
+  static constexpr int DCB = MODE == MODE_SPLIT ? 2 : 4;
   static constexpr int NBUF =
-      (MODE == MODE_SPLIT && EPI != EPI_F32 && EPI != EPI_ATOMIC && (EPI != EPI_DCELU || QUAD)) ? 1 : 2;
+      (EPI == EPI_DCELU && !QUAD) ? DCB
+                                  : ((MODE == MODE_SPLIT && EPI != EPI_F32 && EPI != EPI_ATOMIC && (EPI != EPI_DCELU || QUAD)) ? 1 : 2);
   static constexpr int OBYTES = OB ? EPI_WARPS * NBUF * OB * WBUF : 1024;
   static constexpr int FIXED = OBYTES + 1024 + 1024;
   static constexpr int AQ = QUAD ? 2 : 1;   // operand tiles per stage and side (hi, lo)
@@ -294,7 +298,7 @@ struct Smem {
   uint8_t A[STAGES][AQ * BM * KB];
   uint8_t B[STAGES][AQ * NT * KB];
   uint8_t O[OBYTES];
-  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin, aux_bar[EPI_WARPS][2];
+  uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], fin, aux_bar[EPI_WARPS][4];
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int a = 0; a < 2; a++) {
       mbar_init(&S.acc_full[a], 1);
       mbar_init(&S.acc_empty[a], EPI_WARPS);   // one arrival per epilogue warp
-      for (int w = 0; w < EPI_WARPS; w++) mbar_init(&S.aux_bar[w][a], 1);
+      for (int w = 0; w < EPI_WARPS; w++) mbar_init(&S.aux_bar[w][a], 1), mbar_init(&S.aux_bar[w][2 + a], 1);
     }
     mbar_init(&S.fin, 1);
     S.abort_flag = 0;
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int ew = warp - 2;                // epilogue warp index
     constexpr int PB = F8 ? 16 * 32 : 32 * 32;   // bytes of one 32 x 16 piece
     uint8_t *wb = S.O + (size_t)ew * SM::NBUF * SM::OB * SM::WBUF;   // this warp's buffers
-    uint32_t aux_phase[2] = {0u, 0u};
+    uint32_t aux_phase = 0u;                // bit b: the parity of buffer b's next aux load
     unsigned aux_out = 0;                   // lane 0: buffers with an aux load not yet consumed
     long long gk = 0;                       // pieces drained by this warp (buffer gk & 1)
     int cnt = 0;
@@ -598,13 +602,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int n0 = nt * NT;
       const int ncols = min(NT, p.N - n0);
       nt_cur = nt;
-      // the first aux pieces of the tile (two with two buffers: the loads stay two pieces ahead) travel
-      // while its MMAs run
+      // the first aux pieces of the tile, one per buffer (the loads stay NBUF pieces ahead), travel while
+      // its MMAs run
       const int cend = min(ncols, w.c0 + w.cw);   // the item's columns (tile coordinates)
       if (EPI == EPI_DCELU && lane == 0 && w.c0 + 16 * part < cend) {
         if (gk >= 1) bulk_wait_read0();   // the stores that last read the buffers
-        load_aux(SM::NBUF == 2 ? (int)(gk & 1) : 0, w.c0 + 16 * part, rt, m);
-        if (SM::NBUF == 2 && w.c0 + 16 * part + 64 < cend) load_aux((int)((gk + 1) & 1), w.c0 + 16 * part + 64, rt, m);
+#pragma unroll
+        for (int i = 0; i < SM::NBUF; i++)
+          if (w.c0 + 16 * part + 64 * i < cend) load_aux((int)((gk + i) % SM::NBUF), w.c0 + 16 * part + 64 * i, rt, m);
       }
       const float *bias = p.bias + e * p.bias_estride + m * p.bias_mstride + n0;
       // the bias of this warp's pieces, read while the MMAs run: lane j holds column j of each piece (one
@@ -672,11 +677,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           continue;
         }
-        const int b = SM::NBUF == 2 ? (int)(gk & 1) : 0;
+        const int b = (int)(gk % SM::NBUF);
         uint8_t *ob = wb + (size_t)b * SM::OB * SM::WBUF;
         if (EPI == EPI_DCELU) {
-          const bool got = mbar_wait(&S.aux_bar[ew][b], aux_phase[b]);
-          aux_phase[b] ^= 1u;
+          const bool got = mbar_wait(&S.aux_bar[ew][b], (aux_phase >> b) & 1u);
+          aux_phase ^= 1u << b;
           if (lane == 0) aux_out &= ~(1u << b);
           if (!__all_sync(0xffffffffu, got)) {
             abort_now = true;
@@ -768,14 +773,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_store_3d(&tmO, ob, x, oy, rt * BM + q * 32);
           if (SPLIT) tma_store_3d(&tmO_lo, ob + SM::WBUF, x, oy, rt * BM + q * 32);
           bulk_commit();
-          if (EPI == EPI_DCELU) {
-            if (SM::NBUF == 2 && c + 128 < cend) {   // the piece after next into this buffer, once read
-              bulk_wait_read0();
-              load_aux(b, c + 128, rt, m);
-            } else if (SM::NBUF == 1 && c + 64 < cend) {   // one buffer: the next piece, once this store read it
-              bulk_wait_read0();
-              load_aux(0, c + 64, rt, m);
-            }
+          if (EPI == EPI_DCELU && c + 64 * SM::NBUF < cend) {   // the piece NBUF on into this buffer, once read
+            bulk_wait_read0();
+            load_aux(b, c + 64 * SM::NBUF, rt, m);
           }
         }
         gk++;
@@ -794,9 +794,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       // nothing may still read or write this warp's buffers when the CTA exits
       bulk_wait_all();
-      for (int b = 0; b < 2; b++)
+      for (int b = 0; b < SM::NBUF; b++)
         if ((aux_out >> b) & 1u)
-          if (!mbar_wait(&S.aux_bar[ew][b], aux_phase[b])) *abort_flag = 1;
+          if (!mbar_wait(&S.aux_bar[ew][b], (aux_phase >> b) & 1u)) *abort_flag = 1;
     }
   }
   fence_before();
