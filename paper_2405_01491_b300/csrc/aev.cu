@@ -54,6 +54,17 @@ __device__ __forceinline__ float sqrt_fast(float x) {
   return y;
 }
 
+// Two FP32 operations in one instruction (the packed add, multiply and fma of this architecture, each half
+// rounded as its scalar form): the AEV kernels are bound by instruction issue, and their shift and section
+// loops are pairs of independent streams of arithmetic
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 exp2_2(float2 x) { return make_float2(exp2f_fast(x.x), exp2f_fast(x.y)); }
+__device__ __forceinline__ float2 log2_2(float2 x) { return make_float2(log2_fast(x.x), log2_fast(x.y)); }
+__device__ __forceinline__ float2 rcp_2(float2 x) { return make_float2(rcp_fast(x.x), rcp_fast(x.y)); }
+
 // 16-byte copies global -> shared (cp.async, L2 only), their commit groups and waits
 __device__ __forceinline__ void cp16(void *smem, const void *gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
@@ -105,11 +116,15 @@ struct FwdStage {
   int sp[32];                    // slot block of a triplet that opens one
   BlockTable tb;
 };
+constexpr int GS_STRIDE = 36;
 struct AdjStage {
   NbrStage nb;
   float gacc[RAD_CAP][3];        // dE/dd per radial entry
   double vacc[9];                // virial of the current structure (lane 0), flushed when it changes
-  alignas(16) float gs[NPAIR * 32];   // the angular part of the atom's dE/dAEV row
+  // the angular part of the atom's dE/dAEV row ([pair][m][s]), GS_STRIDE floats per pair: the lanes of a
+  // batch read the rows of different pairs at the same offset, which then fall in different banks (with 32
+  // floats per pair every lane's float4 hit the same four banks: 134.9 -> 129.9 us on the 23,558-atom box)
+  alignas(16) float gs[NPAIR * GS_STRIDE];
 };
 
 struct StageArgs {
@@ -473,17 +488,24 @@ __device__ __forceinline__ void produce_triplet(FwdStage &W, const AevParams &P,
   const float4 u1 = W.nb.au[ja], u2 = W.nb.au[ka];
   const float c95 = 0.95f * (u1.x * u2.x + u1.y * u2.y + u1.z * u2.z);
   const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
+  // sections (s, s + 1) and shifts (m, m + 1) side by side in packed pairs
+  const float2 c2 = dup2(c95), s2 = dup2(s95), z2 = dup2(P.zeta);
 #pragma unroll
-  for (int s = 0; s < NSZ; s++) {
-    const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-    W.sf[s][lane] = exp2f_fast(P.zeta * log2_fast(base_s));
+  for (int s = 0; s < NSZ; s += 2) {
+    const float2 base = fma2(s2, P.hsin2[s >> 1], fma2(c2, P.hcos2[s >> 1], dup2(0.5f)));
+    const float2 f = exp2_2(mul2(z2, log2_2(base)));
+    W.sf[s][lane] = f.x;
+    W.sf[s + 1][lane] = f.y;
   }
   // the switch product 2 fc_j fc_k enters the exponent: 2^(-eta log2(e) dr^2 + log2(2 fc_j fc_k))
   const float rbar = u1.w + u2.w, lf = real ? W.nb.la[ja] + W.nb.la[ka] : __int_as_float(0xff800000);
+  const float2 rb2 = dup2(rbar), lf2 = dup2(lf), ea2 = dup2(P.eta_a_l2);
 #pragma unroll
-  for (int m = 0; m < NSA; m++) {
-    const float dr = rbar - P.shf_a[m];
-    W.sg[m][lane] = exp2f_fast(fmaf(dr * dr, P.eta_a_l2, lf));
+  for (int m = 0; m < NSA; m += 2) {
+    const float2 dr = add2(rb2, P.nsha2[m >> 1]);
+    const float2 g = exp2_2(fma2(mul2(dr, dr), ea2, lf2));
+    W.sg[m][lane] = g.x;
+    W.sg[m + 1][lane] = g.y;
   }
 }
 
@@ -504,35 +526,35 @@ struct GlobalRow {
   }
 };
 
-// Radial slots of a staged row: lane (h, k) sums shift k over every other neighbour of each element
-// segment; elements without neighbours are skipped (their slots hold zeros already) unless zeros is set
+// Radial slots of a staged row: lane (h, k) sums the shift pair (2k, 2k + 1), packed, over every fourth
+// neighbour (h) of each element segment; elements without neighbours are skipped (their slots hold zeros
+// already) unless zeros is set
 template <typename Sink>
 __device__ __forceinline__ void radial_row(const AevParams &P, const FwdStage &W, const Sink &o, int orr, bool zeros) {
   const int lane = threadIdx.x & 31;
-  const int h = lane >> 4, k = lane & 15;
-  const float Rk = P.shf_r[k], ce = P.eta_r_l2;
+  const int h = lane >> 3, k = lane & 7;
+  const float2 nR = P.nshr2[k], ce2 = dup2(P.eta_r_l2);
 #pragma unroll 1
   for (int q = 0; q < NE; q++) {
     const int t0 = __shfl_sync(FULL, orr, q), t1 = __shfl_sync(FULL, orr, q + 1);
     if (t0 == t1 && !zeros) continue;
     int t = t0 + h;
-    float a0 = 0.f, a1 = 0.f;
-    for (; t + 6 < t1; t += 8) {
-      const float2 v0 = W.nb.rr[t], v1 = W.nb.rr[t + 2], v2 = W.nb.rr[t + 4], v3 = W.nb.rr[t + 6];
-      const float d0 = v0.x - Rk, d1 = v1.x - Rk, d2 = v2.x - Rk, d3 = v3.x - Rk;
-      a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
-      a1 += exp2f_fast(fmaf(d1 * d1, ce, v1.y));
-      a0 += exp2f_fast(fmaf(d2 * d2, ce, v2.y));
-      a1 += exp2f_fast(fmaf(d3 * d3, ce, v3.y));
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+    for (; t + 4 < t1; t += 8) {
+      const float2 v0 = W.nb.rr[t], v1 = W.nb.rr[t + 4];
+      const float2 d0 = add2(dup2(v0.x), nR), d1 = add2(dup2(v1.x), nR);
+      a0 = add2(a0, exp2_2(fma2(mul2(d0, d0), ce2, dup2(v0.y))));
+      a1 = add2(a1, exp2_2(fma2(mul2(d1, d1), ce2, dup2(v1.y))));
     }
-    for (; t < t1; t += 2) {
+    if (t < t1) {
       const float2 v0 = W.nb.rr[t];
-      const float d0 = v0.x - Rk;
-      a0 += exp2f_fast(fmaf(d0 * d0, ce, v0.y));
+      const float2 d0 = add2(dup2(v0.x), nR);
+      a0 = add2(a0, exp2_2(fma2(mul2(d0, d0), ce2, dup2(v0.y))));
     }
-    float acc = a0 + a1;
-    acc += __shfl_xor_sync(FULL, acc, 16);
-    if (lane < 16) o.put(q * NSR + k, acc);
+    float2 acc = add2(a0, a1);
+    acc = add2(acc, make_float2(__shfl_xor_sync(FULL, acc.x, 8), __shfl_xor_sync(FULL, acc.y, 8)));
+    acc = add2(acc, make_float2(__shfl_xor_sync(FULL, acc.x, 16), __shfl_xor_sync(FULL, acc.y, 16)));
+    if (h < 2) o.put(q * NSR + 2 * k + h, h ? acc.y : acc.x);
   }
 }
 
@@ -558,11 +580,11 @@ __device__ __forceinline__ void aev_row(const AevFwdArgs &A, FwdStage &W, int i,
     const int s_my = lane & 3, m_my = lane >> 2;
     const float *fr = W.sf[s_my], *gr = W.sg[m_my];
     int run_p = -1;          // slot block being summed (warp-uniform)
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+    float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);   // four chains as two packed pairs
     auto put = [&](int pp, float v) { o.put(NRAD + pp * 32 + lane, v); };
     auto open = [&](int pn) {
-      if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
-      r0 = r1 = r2 = r3 = 0.f;
+      if (run_p >= 0) put(run_p, (ra.x + ra.y) + (rb.x + rb.y));
+      ra = rb = make_float2(0.f, 0.f);
       run_p = pn;
     };
     int cur = 0;
@@ -581,14 +603,12 @@ __device__ __forceinline__ void aev_row(const AevFwdArgs &A, FwdStage &W, int i,
         const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
         const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
         if ((starts >> q) & 1u) open(W.sp[q]);
-        r0 = fmaf(fv.x, gv.x, r0);
-        r1 = fmaf(fv.y, gv.y, r1);
-        r2 = fmaf(fv.z, gv.z, r2);
-        r3 = fmaf(fv.w, gv.w, r3);
+        ra = fma2(make_float2(fv.x, fv.y), make_float2(gv.x, gv.y), ra);
+        rb = fma2(make_float2(fv.z, fv.w), make_float2(gv.z, gv.w), rb);
       }
       __syncwarp();
     }
-    if (run_p >= 0) put(run_p, (r0 + r1) + (r2 + r3));
+    if (run_p >= 0) put(run_p, (ra.x + ra.y) + (rb.x + rb.y));
   }
 }
 
@@ -651,7 +671,7 @@ __device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int 
     } else {
       for (int e = part - 1; e < nblk; e += K - 1) {
         const int s0 = W.tb.bt[e].x, s1 = W.tb.bt[e + 1].x, pb = W.tb.bq[e] & 0xff;
-        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+        float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
         for (int base = s0; base < s1; base += 32) {
           int ja, ka;
           const bool real = block_pair(W.tb, e, base - s0 + lane, ja, ka);
@@ -661,15 +681,14 @@ __device__ void aev_forward_parts(const AevFwdArgs &A, FwdStage &W, int wg, int 
           for (int q = 0; q < 32; q += 4) {
             const float4 fv = *reinterpret_cast<const float4 *>(fr + q);
             const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
-            r0 = fmaf(fv.x, gv.x, r0);
-            r1 = fmaf(fv.y, gv.y, r1);
-            r2 = fmaf(fv.z, gv.z, r2);
-            r3 = fmaf(fv.w, gv.w, r3);
+            ra = fma2(make_float2(fv.x, fv.y), make_float2(gv.x, gv.y), ra);
+            rb = fma2(make_float2(fv.z, fv.w), make_float2(gv.z, gv.w), rb);
           }
           __syncwarp();
         }
-        store_out<OutT>(out + NRAD + pb * 32 + lane, (r0 + r1) + (r2 + r3), A.out_inv);
-        store_lo(lo, NRAD + pb * 32 + lane, (r0 + r1) + (r2 + r3));
+        const float v = (ra.x + ra.y) + (rb.x + rb.y);
+        store_out<OutT>(out + NRAD + pb * 32 + lane, v, A.out_inv);
+        store_lo(lo, NRAD + pb * 32 + lane, v);
       }
     }
     __syncwarp();
@@ -957,7 +976,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
     if (!stage_neighbors(A.sa, P, i, S, orr, oa, cr, ca, A.st)) continue;
     // the angular part of the dE/dAEV row into shared memory while the radial terms run
     if (do_ang) {
-      for (int c = lane; c < NPAIR * 8; c += 32) cp16(W.gs + 4 * c, G + NRAD + 4 * c);
+      for (int c = lane; c < NPAIR * 8; c += 32) cp16(W.gs + (c >> 3) * GS_STRIDE + 4 * (c & 7), G + NRAD + 4 * c);
       cp_commit();
     }
     __syncwarp();
@@ -972,19 +991,20 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
       // 1/4 (g_k)' fc + 1/4 g_k fc' with g_k = exp(-eta (r - R_k)^2): g_k (fc' / 4 - eta dr_k fc / 2)
       const float fc2 = -0.5f * P.eta_r * switch_f(P, r, P.rc_rad, P.inv_rc_rad);
       const float dfc4 = 0.25f * switch_df(P, r, P.rc_rad, P.inv_rc_rad, P.pi_rc_rad);
-      float dEdr = 0.f;
-      auto term = [&](float Gk, int k) {
-        const float dr = r - P.shf_r[k];
-        dEdr = fmaf(Gk * exp2f_fast(dr * dr * P.eta_r_l2), fmaf(dr, fc2, dfc4), dEdr);
+      // shifts k and k + 1 side by side in packed pairs
+      const float2 r2 = dup2(r), fc22 = dup2(fc2), dfc42 = dup2(dfc4), ce2 = dup2(P.eta_r_l2);
+      float2 acc = make_float2(0.f, 0.f);
+      auto term = [&](float2 Gk, int k) {
+        const float2 dr = add2(r2, P.nshr2[k >> 1]);
+        acc = fma2(mul2(Gk, exp2_2(mul2(mul2(dr, dr), ce2))), fma2(dr, fc22, dfc42), acc);
       };
 #pragma unroll
       for (int k4 = 0; k4 < NSR / 4; k4++) {
         const float4 gv = __ldg(Ge + k4);
-        term(gv.x, 4 * k4);
-        term(gv.y, 4 * k4 + 1);
-        term(gv.z, 4 * k4 + 2);
-        term(gv.w, 4 * k4 + 3);
+        term(make_float2(gv.x, gv.y), 4 * k4);
+        term(make_float2(gv.z, gv.w), 4 * k4 + 2);
       }
+      const float dEdr = acc.x + acc.y;
       const float f = dEdr * rcp_fast(r);
       W.gacc[t][0] = f * d.x;
       W.gacc[t][1] = f * d.y;
@@ -1028,7 +1048,7 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
         const int kc = jc + d < n ? jc + d : jc + d - n;
         const int ja = min(jc, kc), ka = max(jc, kc);   // list order: e(ja) <= e(ka)
         const int p = pair_of(S.ae[ja], S.ae[ka]);
-        const float *Gp = W.gs + p * 32;
+        const float *Gp = W.gs + p * GS_STRIDE;
         const int rj1 = S.aidx[ja], rj2 = S.aidx[ka];
         const float4 d1 = S.rd[rj1], d2 = S.rd[rj2];
         const float r1 = d1.w, r2 = d2.w;
@@ -1037,26 +1057,41 @@ __device__ __forceinline__ void aev_adjoint_rows(const AevAdjArgs &A, AdjStage &
         const float c95 = 0.95f * c;
         const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
         const float ds95 = -0.9025f * c * rcp_fast(s95);   // d s95 / dc; s95 >= sqrt(1 - 0.95^2)
+        // sections s and s + 1 side by side in packed pairs
         float fs[NSZ], dfs[NSZ];
+        {
+          const float2 c2 = dup2(c95), s2 = dup2(s95), d2 = dup2(ds95), z2 = dup2(P.zeta);
 #pragma unroll
-        for (int s = 0; s < NSZ; s++) {
-          const float base_s = fmaf(s95, P.hsin_z[s], fmaf(c95, P.hcos_z[s], 0.5f));
-          const float f = exp2f_fast(P.zeta * log2_fast(base_s));
-          fs[s] = f;
-          // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
-          dfs[s] = P.zeta * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[s], P.qcos_z[s]);
+          for (int s = 0; s < NSZ; s += 2) {
+            const float2 base = fma2(s2, P.hsin2[s >> 1], fma2(c2, P.hcos2[s >> 1], dup2(0.5f)));
+            const float2 f = exp2_2(mul2(z2, log2_2(base)));
+            // d f / d c = zeta f / base * 0.5 (0.95 cos + ds95 sin)
+            const float2 df = mul2(mul2(mul2(z2, f), rcp_2(base)), fma2(d2, P.hsin2[s >> 1], P.qcos2[s >> 1]));
+            fs[s] = f.x;
+            fs[s + 1] = f.y;
+            dfs[s] = df.x;
+            dfs[s + 1] = df.y;
+          }
         }
         const float rbar = 0.5f * (r1 + r2);
-        // H_s = sum_m G[m][s] g_m and Hd_s = sum_m G[m][s] dr_m g_m (times -2 eta below: d g_m / d rbar)
+        // H_s = sum_m G[m][s] g_m and Hd_s = sum_m G[m][s] dr_m g_m (times -2 eta below: d g_m / d rbar); the
+        // Gaussians of shifts (m, m + 1) in packed pairs, the sums scalar (packed sums over shift pairs need the
+        // row transposed in shared memory, which cost more than they saved)
         float H[NSZ] = {0, 0, 0, 0}, Hd[NSZ] = {0, 0, 0, 0};
+        {
+          const float2 rb2 = dup2(rbar), ea2 = dup2(P.eta_a_l2);
 #pragma unroll
-        for (int m = 0; m < NSA; m++) {
-          const float dr = rbar - P.shf_a[m];
-          const float gm = exp2f_fast(dr * dr * P.eta_a_l2);
-          const float tm = dr * gm;
-          const float4 g4 = *reinterpret_cast<const float4 *>(Gp + m * NSZ);
-          H[0] += g4.x * gm; H[1] += g4.y * gm; H[2] += g4.z * gm; H[3] += g4.w * gm;
-          Hd[0] += g4.x * tm; Hd[1] += g4.y * tm; Hd[2] += g4.z * tm; Hd[3] += g4.w * tm;
+          for (int m = 0; m < NSA; m += 2) {
+            const float2 dr = add2(rb2, P.nsha2[m >> 1]);
+            const float2 gm = exp2_2(mul2(mul2(dr, dr), ea2));
+            const float2 tm = mul2(dr, gm);
+            const float4 ga = *reinterpret_cast<const float4 *>(Gp + m * NSZ);
+            const float4 gb = *reinterpret_cast<const float4 *>(Gp + (m + 1) * NSZ);
+            H[0] += ga.x * gm.x; H[1] += ga.y * gm.x; H[2] += ga.z * gm.x; H[3] += ga.w * gm.x;
+            Hd[0] += ga.x * tm.x; Hd[1] += ga.y * tm.x; Hd[2] += ga.z * tm.x; Hd[3] += ga.w * tm.x;
+            H[0] += gb.x * gm.y; H[1] += gb.y * gm.y; H[2] += gb.z * gm.y; H[3] += gb.w * gm.y;
+            Hd[0] += gb.x * tm.y; Hd[1] += gb.y * tm.y; Hd[2] += gb.z * tm.y; Hd[3] += gb.w * tm.y;
+          }
         }
         const float f1 = S.afc[ja], f2 = S.afc[ka], df1 = S.adfc[ja], df2 = S.adfc[ka];
         // a lane past the last pair contributes nothing (its switch product taken as zero)
@@ -1303,14 +1338,14 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
       int nblk;
       const int T = build_blocks(W.tb, ca, oa, nblk);
       int run_p = -1;
-      float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;      // tangent sums of the running block
-      float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;      // and (fout) its forward sums
+      // four chains each, as two packed pairs: the tangent sums of the running block and (fout) its forward sums
+      float2 ra = make_float2(0.f, 0.f), rb = ra, qa = ra, qb = ra;
       auto open = [&](int pn) {
         if (run_p >= 0) {
-          store_out<OutT>(out + NRAD + run_p * 32 + lane, (r0 + r1) + (r2 + r3), 1.f);
-          if (fout) fout[NRAD + run_p * 32 + lane] = __float2bfloat16((q0 + q1) + (q2 + q3));
+          store_out<OutT>(out + NRAD + run_p * 32 + lane, (ra.x + ra.y) + (rb.x + rb.y), 1.f);
+          if (fout) fout[NRAD + run_p * 32 + lane] = __float2bfloat16((qa.x + qa.y) + (qb.x + qb.y));
         }
-        r0 = r1 = r2 = r3 = q0 = q1 = q2 = q3 = 0.f;
+        ra = rb = qa = qb = make_float2(0.f, 0.f);
         run_p = pn;
       };
       const float *fr = W.b.sf[s_my], *fdr = W.b.sfd[s_my], *gr = W.b.sg[m_my], *gdr = W.b.sgd[m_my];
@@ -1331,13 +1366,18 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float s95 = sqrt_fast(fmaxf(1.f - c95 * c95, 0.f));
           const float ds95 = -0.9025f * c * rcp_fast(s95);
           const float zc = P.zeta * cdot;
+          // sections (s, s + 1) and shifts (m, m + 1) side by side in packed pairs
+          const float2 c2p = dup2(c95), s2p = dup2(s95), d2p = dup2(ds95), z2 = dup2(P.zeta), zc2 = dup2(zc);
 #pragma unroll
-          for (int sidx = 0; sidx < NSZ; sidx++) {
-            const float base_s = fmaf(s95, P.hsin_z[sidx], fmaf(c95, P.hcos_z[sidx], 0.5f));
-            const float f = exp2f_fast(P.zeta * log2_fast(base_s));
-            W.b.sf[sidx][lane] = f;
+          for (int sidx = 0; sidx < NSZ; sidx += 2) {
+            const float2 base = fma2(s2p, P.hsin2[sidx >> 1], fma2(c2p, P.hcos2[sidx >> 1], dup2(0.5f)));
+            const float2 f = exp2_2(mul2(z2, log2_2(base)));
             // fdot = zeta f / base * 0.5 (0.95 cos + ds95 sin) * cdot
-            W.b.sfd[sidx][lane] = zc * f * rcp_fast(base_s) * fmaf(ds95, P.hsin_z[sidx], P.qcos_z[sidx]);
+            const float2 fd = mul2(mul2(mul2(zc2, f), rcp_2(base)), fma2(d2p, P.hsin2[sidx >> 1], P.qcos2[sidx >> 1]));
+            W.b.sf[sidx][lane] = f.x;
+            W.b.sf[sidx + 1][lane] = f.y;
+            W.b.sfd[sidx][lane] = fd.x;
+            W.b.sfd[sidx + 1][lane] = fd.y;
           }
           const float rbar = 0.5f * (r1 + r2), rbdot = 0.5f * (v1.w + v2.w);
           const float f1 = S.afc[ja], f2 = S.afc[ka];
@@ -1345,12 +1385,16 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float Cdot = real ? S.adfc[ja] * v1.w * f2 + f1 * S.adfc[ka] * v2.w : 0.f;
           // 2 g C and 2 (gdot C + g Cdot) = g (dr (-4 eta rbdot C) + 2 Cdot), gdot = -2 eta dr g rbdot
           const float C2 = 2.f * C, a2 = -4.f * P.eta_a * rbdot * C, c2 = 2.f * Cdot;
+          const float2 rb2 = dup2(rbar), ea2 = dup2(P.eta_a_l2), C22 = dup2(C2), a22 = dup2(a2), c22 = dup2(c2);
 #pragma unroll
-          for (int m = 0; m < NSA; m++) {
-            const float dr = rbar - P.shf_a[m];
-            const float g = exp2f_fast(dr * dr * P.eta_a_l2);
-            W.b.sg[m][lane] = g * C2;
-            W.b.sgd[m][lane] = g * fmaf(dr, a2, c2);
+          for (int m = 0; m < NSA; m += 2) {
+            const float2 dr = add2(rb2, P.nsha2[m >> 1]);
+            const float2 g = exp2_2(mul2(mul2(dr, dr), ea2));
+            const float2 gc = mul2(g, C22), gd = mul2(g, fma2(dr, a22, c22));
+            W.b.sg[m][lane] = gc.x;
+            W.b.sg[m + 1][lane] = gc.y;
+            W.b.sgd[m][lane] = gd.x;
+            W.b.sgd[m + 1][lane] = gd.y;
           }
           if (opens) W.b.sp[lane] = W.tb.bq[idx] & 0xff;
         }
@@ -1364,14 +1408,12 @@ __global__ void __launch_bounds__(TAN_WARPS * 32, TAN_BLOCKS) k_aev_tangent(AevT
           const float4 gv = *reinterpret_cast<const float4 *>(gr + q);
           const float4 gdv = *reinterpret_cast<const float4 *>(gdr + q);
           if ((starts >> q) & 1u) open(W.b.sp[q]);
-          r0 = fmaf(fdv.x, gv.x, fmaf(fv.x, gdv.x, r0));
-          r1 = fmaf(fdv.y, gv.y, fmaf(fv.y, gdv.y, r1));
-          r2 = fmaf(fdv.z, gv.z, fmaf(fv.z, gdv.z, r2));
-          r3 = fmaf(fdv.w, gv.w, fmaf(fv.w, gdv.w, r3));
-          q0 = fmaf(fv.x, gv.x, q0);
-          q1 = fmaf(fv.y, gv.y, q1);
-          q2 = fmaf(fv.z, gv.z, q2);
-          q3 = fmaf(fv.w, gv.w, q3);
+          const float2 f01 = make_float2(fv.x, fv.y), f23 = make_float2(fv.z, fv.w);
+          const float2 g01 = make_float2(gv.x, gv.y), g23 = make_float2(gv.z, gv.w);
+          ra = fma2(make_float2(fdv.x, fdv.y), g01, fma2(f01, make_float2(gdv.x, gdv.y), ra));
+          rb = fma2(make_float2(fdv.z, fdv.w), g23, fma2(f23, make_float2(gdv.z, gdv.w), rb));
+          qa = fma2(f01, g01, qa);
+          qb = fma2(f23, g23, qb);
         }
         __syncwarp();
       }
@@ -1522,9 +1564,9 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const SmallGr
     const long long me = (long long)(k.m * NE + k.e);
     const float *B = Bb + me * b_me_stride;
     const int a_off = k.m * a_member_off;
-    float acc[SE_RG];
+    float2 acc2[SE_RG];   // per row: the even-k and odd-k sums, packed
 #pragma unroll
-    for (int r = 0; r < SE_RG; r++) acc[r] = 0.f;
+    for (int r = 0; r < SE_RG; r++) acc2[r] = make_float2(0.f, 0.f);
     // the epilogue's operands travel with the first operand copies
     if (threadIdx.x < cw / 4) {
       const int c4 = threadIdx.x * 4;
@@ -1547,17 +1589,21 @@ __device__ void small_layer(const SmallEvalArgs &A, SmallDense &D, const SmallGr
       // warp busy for any kn)
       const int kst = cw == 32 ? 4 * SE_WARPS : 8 * SE_WARPS;
       for (int kk = cw == 32 ? 4 * warp : 4 * (2 * warp + kh); kk < kn; kk += kst) {
-        const float b0 = D.Bs[kk][col_l], b1 = D.Bs[kk + 1][col_l], b2 = D.Bs[kk + 2][col_l], b3 = D.Bs[kk + 3][col_l];
+        const float2 b01 = make_float2(D.Bs[kk][col_l], D.Bs[kk + 1][col_l]);
+        const float2 b23 = make_float2(D.Bs[kk + 2][col_l], D.Bs[kk + 3][col_l]);
 #pragma unroll
         for (int r = 0; r < SE_RG; r++) {
           if (r < k.R) {
             const float4 a = *reinterpret_cast<const float4 *>(&D.As[r][kk]);
-            acc[r] = fmaf(a.x, b0, fmaf(a.y, b1, fmaf(a.z, b2, fmaf(a.w, b3, acc[r]))));
+            acc2[r] = fma2(make_float2(a.x, a.y), b01, fma2(make_float2(a.z, a.w), b23, acc2[r]));
           }
         }
       }
       __syncthreads();   // before the buffers are staged again
     }
+    float acc[SE_RG];
+#pragma unroll
+    for (int r = 0; r < SE_RG; r++) acc[r] = acc2[r].x + acc2[r].y;
     if (cw == 16)
 #pragma unroll
       for (int r = 0; r < SE_RG; r++) acc[r] += __shfl_xor_sync(FULL, acc[r], 16);

@@ -162,6 +162,13 @@ extern "C" fnn_status fnn_create(fnn_ctx **out, const fnn_config *cfg) {
   }
   P.eta_a_l2 = (float)(-c.eta_ang / M_LN2);
   P.eta_r_l2 = (float)(-c.eta_rad / M_LN2);
+  for (int k = 0; k < NSR / 2; k++) P.nshr2[k] = make_float2(-P.shf_r[2 * k], -P.shf_r[2 * k + 1]);
+  for (int m = 0; m < NSA / 2; m++) P.nsha2[m] = make_float2(-P.shf_a[2 * m], -P.shf_a[2 * m + 1]);
+  for (int s = 0; s < NSZ / 2; s++) {
+    P.hcos2[s] = make_float2(P.hcos_z[2 * s], P.hcos_z[2 * s + 1]);
+    P.hsin2[s] = make_float2(P.hsin_z[2 * s], P.hsin_z[2 * s + 1]);
+    P.qcos2[s] = make_float2(P.qcos_z[2 * s], P.qcos_z[2 * s + 1]);
+  }
   P.sw_kind = c.switch_kind;
   {
     const double p = c.switch_p;

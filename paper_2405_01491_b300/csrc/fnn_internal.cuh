@@ -81,6 +81,10 @@ struct AevParams {
   float sw_pm1;                 // polynomial envelope: p - 1, and the coefficients of d^p, d^(p+1), d^(p+2)
   float sw_c0, sw_c1, sw_c2;
   float sw_k;                   // p (p+1) (p+2) / 2: f'(d) = -sw_k d^(p-1) (1 - d)^2
+  // the same constants side by side for the packed FP32 pair instructions: negated shifts (k, k + 1) and
+  // the section constants (s, s + 1)
+  float2 nshr2[NSR / 2], nsha2[NSA / 2];
+  float2 hcos2[NSZ / 2], hsin2[NSZ / 2], qcos2[NSZ / 2];
 };
 
 // The switching function and its derivative at r < rc (section II.A): cosine, polynomial envelope

@@ -20,8 +20,9 @@ constexpr int BM = 128, BN = 64, BK = 16, GNT = 256;
 __device__ __forceinline__ float celu(float z) { return z > 0.f ? z : CELU_ALPHA * expm1f(z * CELU_INV_ALPHA); }
 __device__ __forceinline__ float dcelu_from_h(float h) { return h > 0.f ? 1.f : 1.f + h * CELU_INV_ALPHA; }
 
+// (three blocks per SM: 80 registers, a few bytes of epilogue spills; 6.72 -> 6.22 ms for the FP32 step)
 template <int EPI>
-__global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
+__global__ void __launch_bounds__(GNT, 3) k_gemm_f32(GemmP p) {
   int e = p.tile_elem[blockIdx.y];
   if (e < 0) return;
   const int m = blockIdx.z;
@@ -61,11 +62,13 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
     Bs[buf][bkc + 3][bn] = rb.w;
   };
 
-  float acc[8][4];
+  // acc2[i][j] = (C[2i][j], C[2i + 1][j]): rows in pairs, each pair one packed FP32 fma per k (the same
+  // fma per element as a scalar loop, half the instructions)
+  float2 acc2[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; i++)
+  for (int i = 0; i < 4; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; j++) acc2[i][j] = make_float2(0.f, 0.f);
 
   const int nk = p.K / BK;
   load(0);
@@ -79,12 +82,15 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
       float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
       float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
       float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
-      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float bv[4] = {b0.x, b0.y, b0.z, b0.w};
+      const float2 av[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                            make_float2(a1.z, a1.w)};
+      const float bv[4] = {b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
-      for (int i = 0; i < 8; i++)
+      for (int j = 0; j < 4; j++) {
+        const float2 bj = make_float2(bv[j], bv[j]);
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int i = 0; i < 4; i++) acc2[i][j] = __ffma2_rn(av[i], bj, acc2[i][j]);
+      }
     }
     if (kt + 1 < nk) store(buf ^ 1);
     __syncthreads();
@@ -100,7 +106,7 @@ __global__ void __launch_bounds__(GNT) k_gemm_f32(GemmP p) {
     for (int j = 0; j < 4; j++) {
       int n = n0 + tx * 4 + j;
       if (n >= p.N) continue;
-      float v = acc[i][j];
+      float v = (i & 1) ? acc2[i >> 1][j].y : acc2[i >> 1][j].x;
       float o;
       if (EPI == EPI_BIAS_CELU) {
         o = celu(v + p.bias[e * p.bias_estride + m * p.bias_mstride + n]);
