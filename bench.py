@@ -955,6 +955,28 @@ def kernel_table(prof, steps, n_atoms, nnz, M, form, pk):
     return kernels, roof
 
 
+def network_summary(kernels, steps, n_atoms, M, form, pk):
+    """Every network product of one form's step together: their algorithmic FLOPs (one product of 2 in out
+    FLOP per row and member and layer, forward and input gradient) over their summed kernel time, against
+    the tensor peak the kernel table uses (the FP32 form against the FFMA rate)."""
+    ms, flops = 0.0, 0.0
+    for name, v in kernels.items():
+        wk = kernel_work(name, n_atoms, 0, M)
+        if wk and wk[2] == "FLOP":
+            t = v["ms_per_launch"] * v["launches_per_step"]
+            ms += t
+            flops += wk[1] * v["launches_per_step"]
+    if ms <= 0:
+        return None
+    tf = flops / (ms * 1e-3) / 1e12
+    if form == "fp32":
+        peak = N_SM * FFMA_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    else:
+        peak = pk["bf16_tflops"] * (2 if form == "fp8" else 1)
+    return {"ms": round(ms, 4), "gflop": round(flops / 1e9, 2), "achieved_tflops": round(tf, 1),
+            "peak_tflops": round(peak, 1), "frac": round(tf / peak, 4)}
+
+
 def section(name, fn, *a, **kw):
     """An optional measurement: its result, or the error it raised (the JSON line is printed either way)."""
     try:
@@ -1084,7 +1106,9 @@ def main():
         ks, rf = kernel_table(r["prof"], args.steps, s.n_atoms, nnz, M, form, pk)
         entry = {"value": world * s.n_atoms / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "gpu_launches": r["launches"],
                  "dominant": rf, "kernel_ms": {k: round(v["ms_per_launch"] * v["launches_per_step"], 4)
-                                               for k, v in ks.items()}}
+                                               for k, v in ks.items()},
+                 "kernel_frac": {k: round(v["frac"], 4) for k, v in ks.items() if "frac" in v},
+                 "networks": network_summary(ks, args.steps, s.n_atoms, M, form, pk)}
         if ref is not None:
             entry["max_dE_per_atom"] = float(np.abs(r["E"] - ref.energy).max() / s.n_atoms)
             entry["max_dF"] = float(np.abs(r["F"] - ref.forces).max())
