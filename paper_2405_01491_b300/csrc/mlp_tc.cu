@@ -28,6 +28,7 @@
 
 #include "tc_fused.cuh"
 #include "tc_gemm.cuh"
+#include "tc_pair.cuh"
 
 namespace fnn {
 
@@ -188,6 +189,43 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, di
   tc::k_umma<NT, EPI, MODE, QUAD, KB><<<grid, tc::THREADS, sm, s>>>(
       *mp.A, *mp.B, *mp.A_lo, *mp.B_lo, *mp.O, *mp.O_lo, *mp.X, *mp.X_lo, mp.Bs ? *mp.Bs : *mp.B,
       mp.Bs_lo ? *mp.Bs_lo : *mp.B_lo, a);
+  return check_launch(ctx, name);
+}
+
+// The two-SM first-layer forward (tc_pair.cuh): clusters of two CTAs, persistent over the (member, row-tile
+// pair) items; as many clusters as fit at once, at most one CTA per SM.
+template <int MODE>
+fnn_status launch_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *A, const CUtensorMap *A_lo,
+                       const CUtensorMap *B, const CUtensorMap *B_lo, const CUtensorMap *O, const CUtensorMap *O_lo,
+                       const tc::PairArgs &a, cudaStream_t s) {
+  const size_t sm = tc::pair_smem_bytes<MODE>();
+  static bool attr_set = false;
+  static int max_cl = 0;
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (!attr_set) {
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cfg.gridDim = dim3((unsigned)(ctx->num_sms & ~1));
+    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&max_cl, tc::k_umma_pair<MODE>, &cfg));
+    attr_set = true;
+  }
+  if (max_cl < 1) {
+    ctx->last_error = "two-SM first layer: no cluster of two CTAs fits on the device";
+    return FNN_E_CUDA;
+  }
+  const int ncl = max_cl < ctx->num_sms / 2 ? max_cl : ctx->num_sms / 2;
+  cfg.gridDim = dim3((unsigned)(2 * ncl));
+  FNN_KERNEL(ctx, name, s);
+  FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, tc::k_umma_pair<MODE>, *A, *A_lo, *B, *B_lo, *O, *O_lo, a));
   return check_launch(ctx, name);
 }
 
@@ -494,6 +532,9 @@ static fnn_status f8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nl
 
 namespace {
 
+// The first-layer forward on two-SM tiles (k_umma_pair) rather than the one-SM persistent kernel
+constexpr bool L1_PAIR = true;
+
 // The six products (the third layer's two fused); the structure energies are reduced on the side
 // stream as soon as the output layer is done, overlapping the backward products.
 template <bool SPLIT>
@@ -518,7 +559,10 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
   a.o_xm = 0; a.o_y = 2;
   a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if (!l1_done) {   // (h1 is already there when the fused AEV kernel computed it)
+  if (!l1_done && L1_PAIR) {   // two-SM tiles: each CTA stages its rows and half of the member's weights
+    const tc::PairArgs pa{NAEV, M, nl->meta, w.b1cat, (long long)M * H1, ctx->status};
+    if ((st = launch_pair<MODE>(ctx, nm[0], &H.mAev, &L.mAev, &H.sW1, &L.sW1, &H.eH1, &L.eH1, pa, s))) return st;
+  } else if (!l1_done) {   // (h1 is already there when the fused AEV kernel computed it)
     Maps m1{&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1};
     m1.Bs = &H.sW1; m1.Bs_lo = &L.sW1;
     if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true, ctx, nm[0], m1, nullptr, a, dim3(M, tiles, 1), s)))
