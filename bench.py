@@ -85,7 +85,7 @@ def kernel_work(name: str, n_atoms: int, nnz: int, M: int):
 
 KERNEL_SOURCES = [  # kernel-name prefix -> the files that define it (with the shared internal header)
     (("x3_l3_pair", "bf16_l3_pair"), ("tc_gemm.cuh", "tc_fused.cuh", "mlp_tc.cu")),
-    (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "mlp_tc.cu")),
+    (("x3_", "bf16_", "fp8_", "tr16_"), ("tc_gemm.cuh", "tc_pair.cuh", "mlp_tc.cu")),
     (("f32_", "energy_reduce"), ("mlp_simt.cu",)),
     (("aev_l1",), ("aev.cu", "tc_gemm.cuh")),
     (("aev_",), ("aev.cu",)),

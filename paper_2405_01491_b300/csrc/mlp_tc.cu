@@ -1,7 +1,7 @@
 // Tensor-core (tcgen05) BF16 form of the per-element networks (section II.B) with FP32 accumulation.
 //
 // Same products as the FP32 form (mlp_simt.cu), on 128 x NT tiles of tc_gemm.cuh:
-//   L1  h1 = CELU(aev W1cat^T + b1)              NT = 256, N = M*256, K = 1008
+//   L1  h1 = CELU(aev W1cat^T + b1)              NT = 256, N = M*256, K = 1008 (two-SM tiles, tc_pair.cuh)
 //   L2  h2 = CELU(h1_m W2^T + b2)                NT = 192 per member
 //   L3  g3 = (1/M) w4 CELU'(z3), y_m = h3 . w4   NT = 160 per member (whole row in one tile)
 //   L3' g2 = (g3_m W3) * CELU'(z2)               NT = 192
@@ -532,9 +532,6 @@ static fnn_status f8_calibrate(fnn_ctx *ctx, const fnn_system *sys, const fnn_nl
 
 namespace {
 
-// The first-layer forward on two-SM tiles (k_umma_pair) rather than the one-SM persistent kernel
-constexpr bool L1_PAIR = true;
-
 // The six products (the third layer's two fused); the structure energies are reduced on the side
 // stream as soon as the output layer is done, overlapping the backward products.
 template <bool SPLIT>
@@ -555,18 +552,11 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   a.M = M;
   // the partial last wave of the bias + CELU and CELU' products is cut into 64-column strips
   a.tail_nsplit = 1; a.nsub_w = 64; a.meta = nl->meta;
-  // L1: all members at once; the n tile is the member
-  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
-  a.o_xm = 0; a.o_y = 2;
-  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if (!l1_done && L1_PAIR) {   // two-SM tiles: each CTA stages its rows and half of the member's weights
+  // L1: all members at once, the n tile being the member; on two-SM tiles, each CTA of a pair staging its
+  // rows and half of the member's weights (h1 is already there when the fused AEV kernel computed it)
+  if (!l1_done) {
     const tc::PairArgs pa{NAEV, M, nl->meta, w.b1cat, (long long)M * H1, ctx->status};
     if ((st = launch_pair<MODE>(ctx, nm[0], &H.mAev, &L.mAev, &H.sW1, &L.sW1, &H.eH1, &L.eH1, pa, s))) return st;
-  } else if (!l1_done) {   // (h1 is already there when the fused AEV kernel computed it)
-    Maps m1{&H.mAev, &H.mW1, &L.mAev, &L.mW1, &H.eH1, &L.eH1, &H.eH1, &L.eH1};
-    m1.Bs = &H.sW1; m1.Bs_lo = &L.sW1;
-    if ((st = launch_q<256, tc::EPI_BIAS_CELU, MODE>(true, ctx, nm[0], m1, nullptr, a, dim3(M, tiles, 1), s)))
-      return st;
   }
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
@@ -983,12 +973,10 @@ fnn_status tc_param_grads(fnn_ctx *ctx, const fnn_system *sys, const fnn_nlist *
   a.st = ctx->status;
   a.M = M;
   // ---- forward h1, h2, h3
-  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0; a.o_xm = 0; a.o_y = 2;
-  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  if ((st = launch<256, tc::EPI_BIAS_CELU, B16>(ctx, "tr16_l1_fwd",
-                                                {&H.mAev, &H.mW1, &H.mAev, &H.mW1, &H.eH1, &H.eH1, &H.eH1, &H.eH1}, a,
-                                                dim3(M, tiles, 1), s)))
-    return st;
+  {   // (two-SM tiles, as in the forward step)
+    const tc::PairArgs pa{NAEV, M, nl->meta, w.b1cat, (long long)M * H1, ctx->status};
+    if ((st = launch_pair<B16>(ctx, "tr16_l1_fwd", &H.mAev, &H.mAev, &H.sW1, &H.sW1, &H.eH1, &H.eH1, pa, s))) return st;
+  }
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1; a.o_y = 1;
   a.bias = w.b2; a.bias_estride = H2; a.bias_mstride = (long long)NE * H2;
   if ((st = launch<192, tc::EPI_BIAS_CELU, B16>(ctx, "tr16_l2_fwd",
