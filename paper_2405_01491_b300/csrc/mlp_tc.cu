@@ -83,6 +83,7 @@ struct F8 {
   uint8_t *wbuf = nullptr;
   uint8_t *W1 = nullptr, *W1T = nullptr, *W2 = nullptr, *W2T = nullptr, *W3 = nullptr, *W3T = nullptr;
   CUtensorMap mW1, mW1T, mW2, mW2T, mW3, mW3T;
+  CUtensorMap sW1;           // W1 with 64-row boxes (the two-SM first layer's weight halves)
   float *wscale = nullptr;   // device [6][M*7] in the order W1, W1T, W2, W2T, W3, W3T; W1T per element only
   uint8_t *abuf = nullptr;
   size_t rows = 0;
@@ -310,6 +311,7 @@ static fnn_status upload_f8_weights(fnn_ctx *ctx, TcState *t, const float *const
   const uint64_t G = (uint64_t)M * NE;
   const CUtensorMapDataType U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
   bool ok = encode3d(&f.mW1, f.W1, NAEV, (uint64_t)M * H1, NE, NAEV, (uint64_t)M * H1 * NAEV, 128, 256, 1, U8) &&
+            encode3d(&f.sW1, f.W1, NAEV, (uint64_t)M * H1, NE, NAEV, (uint64_t)M * H1 * NAEV, 128, 64, 1, U8) &&
             encode3d(&f.mW1T, f.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1, (uint64_t)NAEV * M * H1, 128, 256,
                      1, U8) &&
             encode3d(&f.mW2, f.W2, H1, H2, G, H1, (uint64_t)H2 * H1, 128, H2, 1, U8) &&
@@ -634,15 +636,12 @@ fnn_status run_layers_f8(fnn_ctx *ctx, TcState *t, const fnn_nlist *nl, cudaStre
   a.tile_elem = nl->tile_elem;
   a.st = ctx->status;
   a.M = M;
-  // L1: member = n tile
-  a.K = NAEV; a.N = M * H1; a.a_by_member = 0; a.b_by_member = 0;
-  a.o_xm = 0; a.o_y = 2;
-  a.bias = w.b1cat; a.bias_estride = (long long)M * H1; a.bias_mstride = 0;
-  a.a_scale = f.act[0]; a.b_scale = f.wscale; a.b_scale_by = 2; a.out_inv = 1.f / f.act[1];
-  if ((st = launch<256, tc::EPI_BIAS_CELU, MODE>(
-           ctx, "fp8_l1_fwd", {&f.mAev, &f.mW1, &f.mAev, &f.mW1, &f.eH1, &f.eH1, &f.eH1, &f.eH1}, a,
-           dim3(M, tiles, 1), s)))
-    return st;
+  // L1: member = n tile, on two-SM tiles (as the bf16 forms)
+  {
+    tc::PairArgs pa{NAEV, M, nl->meta, w.b1cat, (long long)M * H1, ctx->status};
+    pa.a_scale = f.act[0]; pa.b_scale = f.wscale; pa.out_inv = 1.f / f.act[1];
+    if ((st = launch_pair<MODE>(ctx, "fp8_l1_fwd", &f.mAev, &f.mAev, &f.sW1, &f.sW1, &f.eH1, &f.eH1, pa, s))) return st;
+  }
   // L2
   a.K = H1; a.N = H2; a.a_by_member = 1; a.b_by_member = 1;
   a.o_xm = 0; a.o_y = 1;

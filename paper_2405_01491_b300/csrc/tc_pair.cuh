@@ -8,8 +8,8 @@
 // its own 128 rows x 256 columns.  Per SM this is the work of the one-SM tile for two thirds of its operand
 // bytes: the one-SM first layer is bound by how many operand bytes an SM keeps in flight from L2, and a
 // stage here is 64 KB (split: hi and lo of both operands) instead of 96 KB, so three stages fit where two
-// did (bf16: 32 KB instead of 48, six stages).  The partial last wave's items are cut into two column halves
-// (N = 128) when there are clusters for all of them.
+// did (bf16 and e4m3: 32 KB instead of 48, six stages).  The partial last wave's items are cut into two
+// column halves (N = 128) when there are clusters for all of them.
 //   warp 0 (one lane, both CTAs)  TMA producer: its A rows and B half into its own ring, completion counted
 //                                 on the even CTA's stage barrier (the pair's expected bytes set there)
 //   warp 1 (both CTAs)            TMEM allocation for the pair; one lane of the even CTA issues the MMAs and
@@ -93,6 +93,14 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// the same with e4m3 operands (kind::f8f6f4, fp32 accumulation)
+__device__ __forceinline__ void mma_f8_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
 // arrive on the mbarrier at this offset in both CTAs of the pair once this thread's MMAs have completed
 __device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
   asm volatile(
@@ -118,11 +126,15 @@ struct PairArgs {
   const float *bias;           // bias + e * bias_estride + nt * 256 + c
   long long bias_estride;
   DevStatus *st;
+  // fp8 (MODE_F8): A = a8 * a_scale, B = b8 * b_scale[nt * 7 + e]; the output holds x * out_inv
+  float a_scale, out_inv;
+  const float *b_scale;
 };
 
 template <int MODE>
 struct PairSmem {
   static constexpr bool SPLIT = MODE == MODE_SPLIT;
+  // (rows of 128 bytes: 64 bf16 or 128 e4m3 elements of K)
   static constexpr int AQ = SPLIT ? 2 : 1;                 // hi and lo of each operand per stage
   static constexpr int OB = SPLIT ? 2 : 1;                 // output halves per buffer
   static constexpr int NBUF = SPLIT ? 1 : 2;               // output buffers per epilogue warp
@@ -192,11 +204,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_umma_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA_lo,
                 const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB_lo,
                 const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo, PairArgs p) {
-  static_assert(MODE == MODE_SPLIT || MODE == MODE_BF16, "bf16 operands or their three-term split");
+  static_assert(MODE == MODE_SPLIT || MODE == MODE_BF16 || MODE == MODE_F8, "bf16, its three-term split, or e4m3");
   using SM = PairSmem<MODE>;
   static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
-  constexpr bool SPLIT = SM::SPLIT;
-  constexpr int STAGES = SM::STAGES, KB = BKB, BK = KB / 2;
+  constexpr bool SPLIT = SM::SPLIT, F8 = MODE == MODE_F8;
+  constexpr int STAGES = SM::STAGES, KB = BKB, BK = F8 ? KB : KB / 2;   // K elements per stage
   extern __shared__ uint8_t smem_raw[];
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int it = 0; !*abort_flag; it++) {
         PairWork w;
         if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w)) break;
-        const uint32_t idesc = idesc_bf16(2 * BM, w.cw);
+        const uint32_t idesc = F8 ? idesc_e4m3(2 * BM, w.cw) : idesc_bf16(2 * BM, w.cw);
         const int a = cnt & 1;
         if (cnt >= 2 && !mbar_wait_cl(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
           *abort_flag = 1;
@@ -302,6 +314,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               mma_bf16_pair(d, ah, bh, idesc, acc);
               mma_bf16_pair(d, ah, bl, idesc, 1u);
               mma_bf16_pair(d, al, bh, idesc, 1u);
+            } else if (F8) {
+              mma_f8_pair(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, acc);
             } else {
               mma_bf16_pair(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, acc);
             }
@@ -335,6 +349,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float pre[PAIR_NT / 64];
 #pragma unroll
       for (int i = 0; i < PAIR_NT / 64; i++) pre[i] = i < npc ? __ldg(bias + 16 * part + 64 * i + (lane & 15)) : 0.f;
+      const float sc = F8 ? p.a_scale * p.b_scale[nt * NE + w.e] : 1.f;   // dequantisation of the fp8 product
       const bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
       if (!__all_sync(0xffffffffu, ok)) {
@@ -354,20 +369,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           __syncwarp();
           float f[16];
 #pragma unroll
-          for (int j = 0; j < 16; j++) f[j] = celu_f(v[j] + __shfl_sync(0xffffffffu, pre[i], j));
-          alignas(16) __nv_bfloat162 o2[8];
+          for (int j = 0; j < 16; j++) f[j] = celu_f((F8 ? v[j] * sc : v[j]) + __shfl_sync(0xffffffffu, pre[i], j));
+          if (F8) {  // saturating round-to-nearest e4m3 of x * out_inv
+            alignas(16) __nv_fp8x2_storage_t q8[8];
 #pragma unroll
-          for (int j = 0; j < 8; j++) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-          *reinterpret_cast<uint4 *>(ob + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
-          *reinterpret_cast<uint4 *>(ob + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
-          if (SPLIT) {  // low part: the rounding residual of the high part
+            for (int j = 0; j < 8; j++)
+              q8[j] = __nv_cvt_float2_to_fp8x2(make_float2(f[2 * j] * p.out_inv, f[2 * j + 1] * p.out_inv),
+                                               __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint4 *>(ob + lane * 16) = *reinterpret_cast<const uint4 *>(q8);
+          } else {
+            alignas(16) __nv_bfloat162 o2[8];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-              const float2 hi = __bfloat1622float2(o2[j]);
-              o2[j] = __floats2bfloat162_rn(f[2 * j] - hi.x, f[2 * j + 1] - hi.y);
+            for (int j = 0; j < 8; j++) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+            *reinterpret_cast<uint4 *>(ob + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
+            *reinterpret_cast<uint4 *>(ob + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
+            if (SPLIT) {  // low part: the rounding residual of the high part
+#pragma unroll
+              for (int j = 0; j < 8; j++) {
+                const float2 hi = __bfloat1622float2(o2[j]);
+                o2[j] = __floats2bfloat162_rn(f[2 * j] - hi.x, f[2 * j + 1] - hi.y);
+              }
+              *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
+              *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
             }
-            *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32) = *reinterpret_cast<const uint4 *>(o2);
-            *reinterpret_cast<uint4 *>(ob + SM::WBUF + lane * 32 + 16) = *reinterpret_cast<const uint4 *>(o2 + 4);
           }
           fence_proxy_async();
           __syncwarp();
