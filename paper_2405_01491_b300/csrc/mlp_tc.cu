@@ -72,8 +72,8 @@ struct Half {
   CUtensorMap eH1, eH2, eG3, eG2, eG1;         // epilogue maps: 32-row x 16-column pieces, unswizzled
   // 64-byte-row (64-byte swizzle) operand maps (the split first-layer input gradient, the fused third layer)
   CUtensorMap qW1T, qG1, qW3, qW3T, qH2;
-  // weights with 64-row boxes: the column strips of a product's partial last wave
-  CUtensorMap sW1, sW2, sW2T;
+  // weights with 64-row boxes: the column strips of a product's partial last wave, the two-SM tiles' halves
+  CUtensorMap sW1, sW2, sW2T, sW1T;
   // 64 rows x 64 features (MN-major operands of the weight gradients)
   CUtensorMap wAev, wH1, wH2;
 };
@@ -133,23 +133,8 @@ struct Maps {
   const CUtensorMap *Bs = nullptr, *Bs_lo = nullptr;   // B with strip-high boxes (tail column strips)
 };
 
-// zero the output tiles a tail-split EPI_F32 launch of grid G will add into (tail_sched): one block per tile
-// ZT_PARTS blocks of 64 threads per tile, each clearing BM / ZT_PARTS rows with 16-byte stores (the
-// output's columns and row stride are multiples of four floats)
+// tail-tile zeroing: ZT_PARTS blocks of 64 threads per 128-row tile, 16-byte stores
 constexpr int ZT_PARTS = 8;
-__global__ void __launch_bounds__(64) k_zero_tail(tc::Args p, int G, int nkb, int NT) {
-  const tc::TailSched ts = tc::tail_sched(p, G, nkb);
-  const int tile = (int)blockIdx.x / ZT_PARTS, part = (int)blockIdx.x % ZT_PARTS;
-  if (tile >= ts.R) return;
-  const int t = ts.W * G + tile;
-  const int nt = t % p.n_ntiles, rest = t / p.n_ntiles, rt = rest % ts.nv, m = rest / ts.nv;
-  const int c0 = nt * NT, n4 = min(NT, p.N - c0) / 4;
-  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int rr = 0; rr < tc::BM / ZT_PARTS; rr++) {
-    float *row = p.out + ((long long)rt * tc::BM + part * (tc::BM / ZT_PARTS) + rr) * p.ldo + m * p.o_mstride + c0;
-    for (int c4 = threadIdx.x; c4 < n4; c4 += 64) reinterpret_cast<float4 *>(row)[c4] = z;
-  }
-}
 
 // fused third layer (tc_fused.cuh): persistent over the (row tile, member) grid
 template <int MODE, int KB>
@@ -195,18 +180,16 @@ fnn_status launch(fnn_ctx *ctx, const char *name, const Maps &mp, tc::Args a, di
 
 // The two-SM first-layer forward (tc_pair.cuh): clusters of two CTAs, persistent over the (member, row-tile
 // pair) items; as many clusters as fit at once, at most one CTA per SM.
-template <int MODE>
-fnn_status launch_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *A, const CUtensorMap *A_lo,
-                       const CUtensorMap *B, const CUtensorMap *B_lo, const CUtensorMap *O, const CUtensorMap *O_lo,
-                       const tc::PairArgs &a, cudaStream_t s) {
-  const size_t sm = tc::pair_smem_bytes<MODE>();
+template <int MODE, int EPI = tc::EPI_BIAS_CELU>
+fnn_status pair_launch_config(fnn_ctx *ctx, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int &ncl,
+                              cudaStream_t s) {
+  const size_t sm = tc::pair_smem_bytes<MODE, EPI>();
   static bool attr_set = false;
   static int max_cl = 0;
-  cudaLaunchConfig_t cfg{};
+  cfg = cudaLaunchConfig_t{};
   cfg.blockDim = dim3(tc::THREADS);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
@@ -214,20 +197,56 @@ fnn_status launch_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *A, con
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (!attr_set) {
-    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    FNN_CUDA_TRY(ctx, cudaFuncSetAttribute(tc::k_umma_pair<MODE, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm));
     cfg.gridDim = dim3((unsigned)(ctx->num_sms & ~1));
-    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&max_cl, tc::k_umma_pair<MODE>, &cfg));
+    FNN_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&max_cl, tc::k_umma_pair<MODE, EPI>, &cfg));
     attr_set = true;
   }
   if (max_cl < 1) {
     ctx->last_error = "two-SM first layer: no cluster of two CTAs fits on the device";
     return FNN_E_CUDA;
   }
-  const int ncl = max_cl < ctx->num_sms / 2 ? max_cl : ctx->num_sms / 2;
+  ncl = max_cl < ctx->num_sms / 2 ? max_cl : ctx->num_sms / 2;
   cfg.gridDim = dim3((unsigned)(2 * ncl));
+  return FNN_OK;
+}
+template <int MODE, int EPI = tc::EPI_BIAS_CELU>
+fnn_status launch_pair(fnn_ctx *ctx, const char *name, const CUtensorMap *A, const CUtensorMap *A_lo,
+                       const CUtensorMap *B, const CUtensorMap *B_lo, const CUtensorMap *O, const CUtensorMap *O_lo,
+                       const tc::PairArgs &a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  int ncl;
+  fnn_status st;
+  if ((st = pair_launch_config<MODE, EPI>(ctx, cfg, attr, ncl, s))) return st;
   FNN_KERNEL(ctx, name, s);
-  FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, tc::k_umma_pair<MODE>, *A, *A_lo, *B, *B_lo, *O, *O_lo, a));
+  FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, tc::k_umma_pair<MODE, EPI>, *A, *A_lo, *B, *B_lo, *O, *O_lo, a));
   return check_launch(ctx, name);
+}
+
+// zero the tiles of the pair schedule's partial wave that a tail-split fp32 launch on ncl clusters adds its
+// K parts into (tc::pair_tail_sched): ZT_PARTS blocks of 64 threads per row tile of each tail item
+__global__ void __launch_bounds__(64) k_zero_tail_pair(const int32_t *meta, int n_nt, int ncl, int nkb, int N,
+                                                       float *out, long long ldo) {
+  int seg[NE + 1];
+  for (int e = 0; e <= NE; e++) seg[e] = meta[META_SEG + e];
+  int T = 0;
+  for (int e = 0; e < NE; e++) T += (seg[e + 1] / tc::BM - seg[e] / tc::BM + 1) / 2;
+  T *= n_nt;
+  const tc::PairTail ts = tc::pair_tail_sched(T, ncl, nkb);
+  const int item = (int)blockIdx.x / (2 * ZT_PARTS), half = ((int)blockIdx.x / ZT_PARTS) & 1,
+            part = (int)blockIdx.x % ZT_PARTS;
+  if (item >= ts.R) return;
+  int nt, rt0, e;
+  bool two;
+  if (!tc::pair_item(seg, n_nt, ts.W * ncl + item, nt, rt0, e, two) || (half && !two)) return;
+  const int rt = rt0 + half, c0 = nt * tc::PAIR_NT, n4 = min(tc::PAIR_NT, N - c0) / 4;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int rr = 0; rr < tc::BM / ZT_PARTS; rr++) {
+    float *row = out + ((long long)rt * tc::BM + part * (tc::BM / ZT_PARTS) + rr) * ldo + c0;
+    for (int c4 = threadIdx.x; c4 < n4; c4 += 64) reinterpret_cast<float4 *>(row)[c4] = z;
+  }
 }
 
 // the split with four-tile stages (hi and lo of both operands per K chunk) where quad is set
@@ -375,6 +394,8 @@ fnn_status upload_tc_weights(fnn_ctx *ctx, int M, const float *W1cat, const floa
          encode3d(&H.qW3, H.W3, H2, H3, G, H2 * 2, (uint64_t)H3 * H2 * 2, 32, H3, 1, BF, S64) &&
          encode3d(&H.qW3T, H.W3T, H3, H2, G, H3 * 2, (uint64_t)H2 * H3 * 2, 32, H2, 1, BF, S64) &&
          encode3d(&H.sW1, H.W1, NAEV, (uint64_t)M * H1, NE, NAEV * 2, (uint64_t)M * H1 * NAEV * 2, 64, 64, 1) &&
+         encode3d(&H.sW1T, H.W1T, (uint64_t)M * H1, NAEV, NE, (uint64_t)M * H1 * 2, (uint64_t)NAEV * M * H1 * 2, 64, 64,
+                  1) &&
          encode3d(&H.sW2, H.W2, H1, H2, G, H1 * 2, (uint64_t)H2 * H1 * 2, 64, 64, 1) &&
          encode3d(&H.sW2T, H.W2T, H2, H1, G, H2 * 2, (uint64_t)H1 * H2 * 2, 64, 64, 1);
     if (!ok) {
@@ -580,18 +601,18 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
     const CUtensorMap *maps[10] = {&H.qH2, &L.qH2, &H.qW3, &L.qW3, &H.qW3T, &L.qW3T, &H.eH2, &L.eH2, &H.eG2, &L.eG2};
     if ((st = launch_l3_pair<MODE, 64>(ctx, SPLIT ? "x3_l3_pair" : "bf16_l3_pair", maps, l, s))) return st;
   }
-  // side stream: the structure energies, and zeros for the first-layer input gradient's tail tiles
-  tc::Args az{};
-  az.n_ntiles = (NAEV + 255) / 256; az.n_rowtiles = (int)tiles; az.n_members = 1;
-  az.N = NAEV; az.out = ctx->ws.gaev; az.ldo = NAEV; az.o_mstride = 0;
-  az.tail_split = 1; az.meta = nl->meta; az.tile_elem = nl->tile_elem;
-  const int G1 = ctx->num_sms;   // the grid of the tail-split first-layer input gradient below
-  const int nkb1 = SPLIT ? (M * H1 + 31) / 32 : (M * H1 + 63) / 64;   // K chunks: 64-byte rows (split), 128 (bf16)
+  // side stream: the structure energies, and zeros for the tiles the first-layer input gradient's K parts
+  // (the partial wave of its two-SM schedule on ncl1 clusters) are added into
+  cudaLaunchConfig_t pcfg;
+  cudaLaunchAttribute pattr[1];
+  int ncl1;
+  if ((st = pair_launch_config<MODE, tc::EPI_F32>(ctx, pcfg, pattr, ncl1, s))) return st;
+  const int nt1 = (NAEV + 255) / 256, nkb1 = (M * H1 + 63) / 64;   // n tiles; K chunks of 64 elements
   if ((st = side_fork(ctx, s)) || (st = energy_reduce_rows(ctx, sys, nl, ctx->ws.ypart, 4, E, ctx->side)))
     return st;
   {
     FNN_KERNEL(ctx, "zero_tail", ctx->side);
-    k_zero_tail<<<G1 * ZT_PARTS, 64, 0, ctx->side>>>(az, G1, nkb1, 256);
+    k_zero_tail_pair<<<ncl1 * 2 * ZT_PARTS, 64, 0, ctx->side>>>(nl->meta, nt1, ncl1, nkb1, NAEV, ctx->ws.gaev, NAEV);
   }
   // L2 backward: g1 = (g2 W2) CELU'(h1), stored member-concatenated for the L1 backward
   a.K = H2; a.N = H1; a.o_xm = H1; a.o_y = 0; a.x_y = 1;
@@ -603,24 +624,22 @@ fnn_status run_layers(fnn_ctx *ctx, TcState *t, const fnn_system *sys, const fnn
   }
   a.tail_nsplit = 0;
   if ((st = side_join(ctx, s))) return st;
-  // L1 backward: K = M*256 sums the members; fp32 dE/dAEV for the adjoint; the partial last wave is
-  // split along K and added atomically into the tiles zeroed above
-  a.K = M * H1; a.N = NAEV; a.a_by_member = 0; a.b_by_member = 0;
-  a.out = ctx->ws.gaev; a.ldo = NAEV; a.o_mstride = 0; a.scale = 1.f;
-  a.tail_split = 1; a.meta = nl->meta;
-  // (split: 64-byte rows, four stages instead of two; measured faster here, slower for the forward first
-  // layer and for the bf16 form)
+  // L1 backward on two-SM tiles: K = M*256 sums the members; fp32 dE/dAEV for the adjoint; the partial last
+  // wave is split along K and added into the tiles zeroed above
   const CUtensorMap *og = gaev_map(ctx, t);
   if (!og) {
     ctx->last_error = "cuTensorMapEncodeTiled failed for the dE/dAEV map";
     return FNN_E_CUDA;
   }
-  const Maps q6{&H.qG1, &H.qW1T, &L.qG1, &L.qW1T, og, og, &H.mG1, &L.mG1};
-  if ((st = launch_q<256, tc::EPI_F32, MODE>(true, ctx, nm[5],
-                                             {&H.mG1, &H.mW1T, &L.mG1, &L.mW1T, og, og, &H.mG1, &L.mG1},
-                                             SPLIT ? &q6 : nullptr, a, dim3((NAEV + 255) / 256, tiles, 1), s)))
-    return st;
-  return FNN_OK;
+  tc::PairArgs pb{M * H1, nt1, nl->meta, w.b1cat, 0, ctx->status};
+  pb.N = NAEV;
+  pb.tail_split = 1;
+  {
+    FNN_KERNEL(ctx, nm[5], s);
+    FNN_CUDA_TRY(ctx, cudaLaunchKernelEx(&pcfg, tc::k_umma_pair<MODE, tc::EPI_F32>, H.mG1, L.mG1, H.sW1T, L.sW1T, *og,
+                                         *og, pb));
+  }
+  return check_launch(ctx, nm[5]);
 }
 
 // The six products with e4m3 operands; scales as described at the top of this file.

@@ -1,5 +1,6 @@
-// Two-SM (cta_group::2) form of the first-layer forward product h1 = CELU(aev W1cat^T + b1) (section
-// II.B), sm_103a.
+// Two-SM (cta_group::2) form of the first layer's products (section II.B), sm_103a: the forward
+// h1 = CELU(aev W1cat^T + b1) (EPI_BIAS_CELU; bf16, split or e4m3 operands) and the input gradient
+// dE/dAEV = g1 W1cat (EPI_F32; N = 1008 in four 256-column n tiles, fp32 out).
 //
 // A cluster of two CTAs (one SM each) computes a 256 x 256 tile: two 128-row tiles of one element's
 // species-sorted AEV rows against one member's 256 first-layer outputs.  Each CTA stages its own 128 A
@@ -9,13 +10,14 @@
 // bytes: the one-SM first layer is bound by how many operand bytes an SM keeps in flight from L2, and a
 // stage here is 64 KB (split: hi and lo of both operands) instead of 96 KB, so three stages fit where two
 // did (bf16 and e4m3: 32 KB instead of 48, six stages).  The partial last wave's items are cut into two
-// column halves (N = 128) when there are clusters for all of them.
+// column halves (N = 128) when there are clusters for all of them, or, for the fp32 input gradient, along K
+// into parts added by TMA reduce-add into tiles a side-stream kernel zeroed (its schedule is pair_tail_sched).
 //   warp 0 (one lane, both CTAs)  TMA producer: its A rows and B half into its own ring, completion counted
 //                                 on the even CTA's stage barrier (the pair's expected bytes set there)
 //   warp 1 (both CTAs)            TMEM allocation for the pair; one lane of the even CTA issues the MMAs and
 //                                 commits each stage's release and each accumulator to both CTAs' barriers
-//   warps 2-17 (both CTAs)        bias + CELU epilogue of the CTA's own rows (as the one-SM kernel), then an
-//                                 arrival on the even CTA's accumulator-free barrier
+//   warps 2-17 (both CTAs)        bias + CELU (or fp32) epilogue of the CTA's own rows (as the one-SM kernel),
+//                                 then an arrival on the even CTA's accumulator-free barrier
 // Pairs are two consecutive row tiles of one element; an element with an odd number of row tiles ends in a
 // pair whose second tile is absent (that CTA loads the first tile's rows again and stores nothing).
 // Every mbarrier wait is bounded; on timeout the CTA posts FNN_E_TIMEOUT and both CTAs meet at the final
@@ -129,16 +131,21 @@ struct PairArgs {
   // fp8 (MODE_F8): A = a8 * a_scale, B = b8 * b_scale[nt * 7 + e]; the output holds x * out_inv
   float a_scale, out_inv;
   const float *b_scale;
+  // EPI_F32 (the input gradient dE/dAEV = g1 W1cat): N valid output columns of the product, stored through
+  // the output map (32-row x 8-column fp32 boxes) at x = nt 256 + c; with tail_split the partial wave is cut
+  // along K and added into tiles zeroed beforehand
+  int N, tail_split;
 };
 
-template <int MODE>
+template <int MODE, int EPI = EPI_BIAS_CELU>
 struct PairSmem {
   static constexpr bool SPLIT = MODE == MODE_SPLIT;
   // (rows of 128 bytes: 64 bf16 or 128 e4m3 elements of K)
   static constexpr int AQ = SPLIT ? 2 : 1;                 // hi and lo of each operand per stage
-  static constexpr int OB = SPLIT ? 2 : 1;                 // output halves per buffer
-  static constexpr int NBUF = SPLIT ? 1 : 2;               // output buffers per epilogue warp
-  static constexpr int WBUF = 1024;                        // 32 rows x 16 bf16 columns
+  // output halves per buffer and buffers per epilogue warp (fp32 pieces of 32 rows x 8 columns: two buffers)
+  static constexpr int OB = (SPLIT && EPI != EPI_F32) ? 2 : 1;
+  static constexpr int NBUF = (SPLIT && EPI != EPI_F32) ? 1 : 2;
+  static constexpr int WBUF = 1024;                        // 32 rows x 16 bf16 (or 8 fp32) columns
   static constexpr int OBYTES = EPI_WARPS * NBUF * OB * WBUF;
   static constexpr int STAGE = AQ * (BM + PAIR_NH) * BKB;  // this CTA's bytes of one K chunk
   static constexpr int FIT = (SMEM_LIMIT - 1024 - OBYTES - 1024) / STAGE;
@@ -150,9 +157,9 @@ struct PairSmem {
   uint32_t tmem_base;
   int abort_flag;
 };
-template <int MODE>
+template <int MODE, int EPI = EPI_BIAS_CELU>
 constexpr size_t pair_smem_bytes() {
-  return sizeof(PairSmem<MODE>) + 1024;
+  return sizeof(PairSmem<MODE, EPI>) + 1024;
 }
 
 // item t of the pair schedule -> (n tile, the pair's first row tile, element, whether its second tile
@@ -173,18 +180,48 @@ __device__ __forceinline__ bool pair_item(const int seg[NE + 1], int n_nt, int t
   return false;
 }
 
-// Work item `it` of cluster cl among ncl: the T items' whole waves, then the R items of the partial wave cut
-// into two column halves (N = 128, each CTA staging 64 weight rows) when there are clusters for all halves.
+// Work item `it` of cluster cl among ncl: the T items' whole waves, then the R items of the partial wave.
+// Bias + CELU products cut those into two column halves (N = 128, each CTA staging 64 weight rows) when
+// there are clusters for all halves; fp32 products (ksplit) cut them along K into S = min(ncl / R, nkb)
+// parts, part cl % S of item W ncl + cl / S going to cluster cl < R S and added into its tile (zeroed
+// beforehand, pair_tail_sched).
 struct PairWork {
-  int nt, rt0, e, c0, cw;
-  bool two;
+  int nt, rt0, e, c0, cw, kb0, kb1;
+  bool two, atomic;
 };
-__device__ __forceinline__ bool pair_work(const int seg[NE + 1], int n_nt, int T, int cl, int ncl, int it, PairWork &w) {
+struct PairTail {
+  int W, R, S;
+};
+__device__ __forceinline__ PairTail pair_tail_sched(int T, int ncl, int nkb) {
+  PairTail s;
+  s.W = T / ncl;
+  s.R = T - s.W * ncl;
+  s.S = s.R ? min(ncl / s.R, nkb) : 0;
+  return s;
+}
+__device__ __forceinline__ bool pair_work(const int seg[NE + 1], int n_nt, int T, int cl, int ncl, int it, PairWork &w,
+                                          bool ksplit = false, int nkb = 0) {
   const int W = T / ncl, R = T - W * ncl;
   int t;
   w.c0 = 0;
   w.cw = PAIR_NT;
-  if (R == 0 || 2 * R > ncl) {
+  w.kb0 = 0;
+  w.kb1 = nkb;
+  w.atomic = false;
+  if (ksplit && R > 0) {
+    const PairTail ts = pair_tail_sched(T, ncl, nkb);
+    if (it < W) {
+      t = cl + it * ncl;
+    } else if (it == W && cl < ts.R * ts.S) {
+      const int part = cl % ts.S;
+      t = W * ncl + cl / ts.S;
+      w.kb0 = part * nkb / ts.S;
+      w.kb1 = (part + 1) * nkb / ts.S;
+      w.atomic = true;
+    } else {
+      return false;
+    }
+  } else if (ksplit || R == 0 || 2 * R > ncl) {
     t = cl + it * ncl;
     if (t >= T) return false;
   } else if (it < W) {
@@ -199,13 +236,15 @@ __device__ __forceinline__ bool pair_work(const int seg[NE + 1], int n_nt, int T
   return pair_item(seg, n_nt, t, w.nt, w.rt0, w.e, w.two);
 }
 
-template <int MODE>
+template <int MODE, int EPI = EPI_BIAS_CELU>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA_lo,
                 const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB_lo,
                 const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO_lo, PairArgs p) {
   static_assert(MODE == MODE_SPLIT || MODE == MODE_BF16 || MODE == MODE_F8, "bf16, its three-term split, or e4m3");
-  using SM = PairSmem<MODE>;
+  static_assert(EPI == EPI_BIAS_CELU || (EPI == EPI_F32 && MODE != MODE_F8), "bias + CELU, or the fp32 input gradient");
+  using SM = PairSmem<MODE, EPI>;
+  constexpr bool F32 = EPI == EPI_F32;
   static_assert(SM::STAGES >= 2 && sizeof(SM) + 1024 <= SMEM_LIMIT, "shared memory budget");
   constexpr bool SPLIT = SM::SPLIT, F8 = MODE == MODE_F8;
   constexpr int STAGES = SM::STAGES, KB = BKB, BK = F8 ? KB : KB / 2;   // K elements per stage
@@ -224,6 +263,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
   for (int e = 0; e < NE; e++) T += (seg[e + 1] / BM - seg[e] / BM + 1) / 2;
   T *= p.n_nt;
+  const bool ksplit = F32 && p.tail_split;
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -254,11 +294,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long issued = 0;
       for (int it = 0; !*abort_flag; it++) {
         PairWork w;
-        if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w)) break;
+        if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w, ksplit, nkb)) break;
         const int rt = (rank == 1 && w.two) ? w.rt0 + 1 : w.rt0;   // an absent second tile reloads the first's rows
         const int bh = w.cw / 2;                                    // weight rows staged by this CTA
         const int by = w.nt * PAIR_NT + w.c0 + (int)rank * bh;
-        for (int kb = 0; kb < nkb; kb++, g++) {
+        for (int kb = w.kb0; kb < w.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
           if (g >= STAGES && !mbar_wait(&S.empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
             *abort_flag = 1;
@@ -288,7 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int cnt = 0;
       for (int it = 0; !*abort_flag; it++) {
         PairWork w;
-        if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w)) break;
+        if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w, ksplit, nkb)) break;
         const uint32_t idesc = F8 ? idesc_e4m3(2 * BM, w.cw) : idesc_bf16(2 * BM, w.cw);
         const int a = cnt & 1;
         if (cnt >= 2 && !mbar_wait_cl(&S.acc_empty[a], (uint32_t)(((cnt >> 1) - 1) & 1))) {
@@ -297,7 +337,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(a * TMEM_COLS);
-        for (int kb = 0; kb < nkb; kb++, g++) {
+        for (int kb = w.kb0; kb < w.kb1; kb++, g++) {
           const int s = (int)(g % STAGES);
           if (!mbar_wait(&S.full[s], (uint32_t)((g / STAGES) & 1))) {
             *abort_flag = 1;
@@ -307,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(S.A[s]), b0 = smem_u32(S.B[s]);
 #pragma unroll
           for (int k = 0; k < KB / 32; k++) {
-            const uint32_t acc = (kb | k) != 0 ? 1u : 0u;
+            const uint32_t acc = (kb != w.kb0 || k != 0) ? 1u : 0u;   // the item's first K step starts the sum
             if (SPLIT) {   // hi hi + hi lo + lo hi of this K step
               const uint64_t ah = sdesc_sw128(a0 + 32 * k), al = sdesc_sw128(a0 + BM * KB + 32 * k);
               const uint64_t bh = sdesc_sw128(b0 + 32 * k), bl = sdesc_sw128(b0 + PAIR_NH * KB + 32 * k);
@@ -339,7 +379,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int cnt = 0;
     for (int it = 0;; it++) {
       PairWork w;
-      if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w)) break;
+      if (!pair_work(seg, p.n_nt, T, cl, ncl, it, w, ksplit, nkb)) break;
       const bool mine = rank == 0 || w.two;   // this CTA's tile exists
       const int rt = rank == 1 ? w.rt0 + 1 : w.rt0, nt = w.nt;
       const int a = cnt & 1;
@@ -348,7 +388,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float *bias = p.bias + w.e * p.bias_estride + nt * PAIR_NT + w.c0;
       float pre[PAIR_NT / 64];
 #pragma unroll
-      for (int i = 0; i < PAIR_NT / 64; i++) pre[i] = i < npc ? __ldg(bias + 16 * part + 64 * i + (lane & 15)) : 0.f;
+      for (int i = 0; i < PAIR_NT / 64; i++)
+        pre[i] = (!F32 && i < npc) ? __ldg(bias + 16 * part + 64 * i + (lane & 15)) : 0.f;
       const float sc = F8 ? p.a_scale * p.b_scale[nt * NE + w.e] : 1.f;   // dequantisation of the fp8 product
       const bool ok = mbar_wait(&S.acc_full[a], (uint32_t)((cnt >> 1) & 1));
       fence_after();
@@ -357,7 +398,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       const uint32_t tbase = tmem + (uint32_t)(a * TMEM_COLS) + ((uint32_t)(q * 32) << 16);
-      if (mine) {
+      if (mine && F32) {
+        // 32-row x 8-column fp32 pieces through this warp's two buffers, stored by TMA, or for a K part of a
+        // tail tile added into the tile zeroed beforehand; columns at or beyond N are not written
+        const int ncols = min(w.cw, p.N - nt * PAIR_NT - w.c0);
+#pragma unroll 1
+        for (int i = 0; i < npc; i++) {
+          const int c = 16 * part + 64 * i;
+          if (c >= ncols) break;   // warp-uniform; ncols is a multiple of 16
+          float v[16];
+          tmem_ld16(tbase + c, v);
+#pragma unroll
+          for (int hh = 0; hh < 2; hh++) {
+            uint8_t *ob = wb + (size_t)(gk & 1) * SM::WBUF;
+            if (lane == 0 && gk >= 2) bulk_wait_read1();   // the operation that last read this buffer
+            __syncwarp();
+            float4 *d4 = reinterpret_cast<float4 *>(ob + lane * 32);
+            d4[0] = make_float4(v[8 * hh], v[8 * hh + 1], v[8 * hh + 2], v[8 * hh + 3]);
+            d4[1] = make_float4(v[8 * hh + 4], v[8 * hh + 5], v[8 * hh + 6], v[8 * hh + 7]);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+              const int x = nt * PAIR_NT + w.c0 + c + 8 * hh;
+              if (w.atomic) tma_reduce_add_3d(&tmO, ob, x, 0, rt * BM + q * 32);
+              else tma_store_3d(&tmO, ob, x, 0, rt * BM + q * 32);
+              bulk_commit();
+            }
+            gk++;
+          }
+        }
+      } else if (mine) {
 #pragma unroll 1
         for (int i = 0; i < npc; i++) {
           const int c = 16 * part + 64 * i;   // column of the item (output column w.c0 + c)
