@@ -7,7 +7,7 @@
 //   L3' g2 = (g3_m W3) * CELU'(z2)               NT = 192
 //   (bf16 and split forms: L3 and L3' are one kernel, tc_fused.cuh, with g3 kept in TMEM)
 //   L2' g1 = (g2_m W2) * CELU'(z1)               NT = 256
-//   L1' dE/dAEV = g1 W1cat                       NT = 256, N = 1008, K = M*256, fp32 out
+//   L1' dE/dAEV = g1 W1cat                       NT = 256, N = 1008, K = M*256, fp32 out (two-SM tiles)
 // Activations between layers are bf16 in HBM; operands reach shared memory by TMA (3-D tensor maps
 // whose middle coordinate selects the member, so each member's K range ends in zero fill).  The split
 // (FP32X3) products stage hi and lo of both operands per K chunk and issue hi*hi + hi*lo + lo*hi from

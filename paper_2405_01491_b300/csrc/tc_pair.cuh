@@ -7,8 +7,9 @@
 // rows and half of the member's weight rows (128 of the 256 output columns); one thread of the even CTA
 // issues tcgen05.mma with M = 256, which reads both CTAs' shared memory and writes each CTA's TMEM with
 // its own 128 rows x 256 columns.  Per SM this is the work of the one-SM tile for two thirds of its operand
-// bytes: the one-SM first layer is bound by how many operand bytes an SM keeps in flight from L2, and a
-// stage here is 64 KB (split: hi and lo of both operands) instead of 96 KB, so three stages fit where two
+// bytes: the one-SM first layer is bound by the rate at which an SM stages operand bytes from L2 (41-51
+// bytes per cycle measured), and a stage here is 64 KB (split: hi and lo of both operands) instead of 96 KB,
+// so three stages fit where two
 // did (bf16 and e4m3: 32 KB instead of 48, six stages).  The partial last wave's items are cut into two
 // column halves (N = 128) when there are clusters for all of them, or, for the fp32 input gradient, along K
 // into parts added by TMA reduce-add into tiles a side-stream kernel zeroed (its schedule is pair_tail_sched).
